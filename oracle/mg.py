@@ -56,6 +56,7 @@ def lanczos_lambda_max(apply: Callable, dinv: np.ndarray, n_steps: int = EIG_CG_
     z = dinv * r
     p = z.copy()
     rz = r @ z
+    rz0 = rz
     alphas, betas = [], []
     for _ in range(n_steps):
         q = apply(p)
@@ -69,7 +70,7 @@ def lanczos_lambda_max(apply: Callable, dinv: np.ndarray, n_steps: int = EIG_CG_
         z = dinv * r
         rz_new = r @ z
         beta = rz_new / rz
-        if rz_new <= 1e-300:
+        if rz_new <= 1e-30 * rz0:  # Krylov space exhausted
             break
         betas.append(beta)
         p = z + beta * p
