@@ -1,0 +1,177 @@
+/*
+ * gcmg -- global-coarsening matrix-free multigrid on one GPU (sm_103a).
+ *
+ * C ABI of libgcmg.so.  It solves the Poisson problem -Lap u = f on the cube
+ * [lo, hi]^3 with homogeneous Dirichlet values, discretised by continuous
+ * Q_k elements (k = 1..4, Gauss-Lobatto support points, (k+1)^3 Gauss
+ * points per cell) on an octree mesh with hanging nodes, the set-up of Sec. 5
+ * of Munch, Heister, Prieto Saavedra & Kronbichler, "Efficient distributed
+ * matrix-free multigrid methods on locally refined meshes for FEM
+ * computations" (arXiv:2203.12292).
+ *
+ * Conventions for every entry point:
+ * - Return value: GCMG_OK (0) or a positive GCMG_ERR_* code; the message of
+ *   the last failure of the calling thread is gcmg_last_error().  No C++
+ *   exception crosses this interface.
+ * - Vectors: "device" pointers are CUDA device memory owned by the caller,
+ *   length n_free(level) of the level they belong to, in fp64 (double) or
+ *   fp32 (float) as the `fp64` flag says.  They hold the free DoFs only:
+ *   Dirichlet and hanging-node (constrained) values are not stored.  The
+ *   numbering is the library's; gcmg_level_dof_coords gives the support
+ *   point of every entry.
+ * - Work is queued on the handle's CUDA stream (gcmg_setup / gcmg_set_stream);
+ *   calls return without synchronising unless stated otherwise.
+ * - Handles own all set-up data; the caller destroys them.  A handle must
+ *   not be used from two threads at the same time.
+ */
+#ifndef GCMG_H
+#define GCMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GCMG_OK 0
+#define GCMG_ERR_ARG 1           /* invalid argument (level, size, null pointer, degree) */
+#define GCMG_ERR_CUDA 2          /* a CUDA call failed */
+#define GCMG_ERR_OOM 3           /* device or host allocation failed */
+#define GCMG_ERR_NOT_CONVERGED 4 /* CG reached maxit before the tolerance */
+#define GCMG_ERR_BREAKDOWN 5     /* CG breakdown: (p, Ap) <= 0 or a NaN */
+#define GCMG_ERR_INTERNAL 6      /* inconsistent mesh or set-up data */
+
+/* refinement predicates of one refinement step (Sec. 4, "Examples") */
+#define GCMG_PRED_ALL 0            /* every leaf */
+#define GCMG_PRED_OCTANT_CENTRE 1  /* leaf centre in the closed box [a, b]^3 */
+#define GCMG_PRED_SPHERE 2         /* leaf box meets the sphere |x - (a,a,a)| = b */
+#define GCMG_PRED_SHELL 3          /* a <= |leaf centre| <= b */
+#define GCMG_PRED_OCTANT_STRICT 4  /* all vertex coordinates in [a, b) */
+
+typedef struct gcmg_mesh gcmg_mesh;
+typedef struct gcmg_handle gcmg_handle;
+
+typedef struct {
+  int pred;
+  double a, b, c, d;
+} gcmg_refine_step;
+
+/*
+ * Octree mesh from one cell [lo, hi]^3 refined step by step; every step is
+ * completed by the closure that keeps leaves sharing a vertex within one
+ * level (Sec. 4, "Examples").  The global-coarsening hierarchy (Sec. 2.2:
+ * all cells coarsened at once, repeated down to one cell) is built here.
+ * `steps` is a host array of n_steps entries, read during the call only.
+ */
+int gcmg_mesh_create(double lo, double hi, int n_steps, const gcmg_refine_step* steps, gcmg_mesh** out);
+void gcmg_mesh_destroy(gcmg_mesh* mesh);
+/* number of global-coarsening levels (level 0 = one cell) */
+int gcmg_mesh_num_levels(const gcmg_mesh* mesh, int* n);
+/* number of cells of a global-coarsening level */
+int gcmg_mesh_level_cells(const gcmg_mesh* mesh, int level, int64_t* n_cells);
+/*
+ * Host-only DoF numbering of a global-coarsening level for degree k (no GPU
+ * needed): *n_free receives the number of free DoFs; if xyz is not NULL it
+ * receives their support points (3 * n_free doubles, x y z per DoF) in the
+ * library's numbering, the same as gcmg_level_dof_coords of a handle set up
+ * with the same mesh, degree and tile_cells (0 = default).
+ */
+int gcmg_mesh_dof_coords(const gcmg_mesh* mesh, int level, int degree, int tile_cells, int64_t* n_free, double* xyz);
+
+typedef struct {
+  int degree;              /* polynomial degree k of the finest level, 1..4 */
+  int p_coarsening;        /* 1: k -> floor(k/2) -> ... -> 1 on the finest mesh
+                              (Sec. 2.3), then geometric levels with k = 1 */
+  int mg_fp32;             /* 1: levels and V-cycle in fp32, 0: fp64 (Sec. 5) */
+  int cheb_degree;         /* Chebyshev degree (Sec. 3.3; 3 in Sec. 5) */
+  double smoothing_range;  /* lambda_min = lambda_max / range */
+  int eig_steps;           /* CG steps of the lambda_max estimate */
+  double eig_safety;       /* lambda_max = safety * estimate */
+  int tile_cells;          /* cells per tile, 0 = default per degree */
+} gcmg_config;
+
+int gcmg_config_default(gcmg_config* cfg);
+
+/*
+ * Set up all levels on the current CUDA device: DoF numbering, tiles and
+ * colours, transfer data, Jacobi diagonals (Eqs. 3-4), lambda_max estimates,
+ * the inverse of the level-0 matrix.  `stream` is a cudaStream_t (NULL =
+ * legacy default stream).  Synchronises the stream before returning.
+ */
+int gcmg_setup(const gcmg_mesh* mesh, const gcmg_config* cfg, void* stream, gcmg_handle** out);
+void gcmg_destroy(gcmg_handle* h);
+int gcmg_set_stream(gcmg_handle* h, void* stream);
+
+typedef struct {
+  int64_t n_free;    /* DoFs stored in vectors of this level */
+  int64_t n_cells;
+  int degree;
+  int n_tiles;
+  int n_colours;     /* tile colours = launches per cell loop */
+  int tile_cells;
+  int max_local;     /* largest tile-local DoF count */
+  int fp32;          /* level vectors of the V-cycle are fp32 */
+} gcmg_level_info;
+
+int gcmg_num_levels(const gcmg_handle* h, int* n);
+int gcmg_get_level_info(const gcmg_handle* h, int level, gcmg_level_info* info);
+/* support point (x, y, z) of every free DoF of a level into a host array of
+ * 3 * n_free doubles (synchronous) */
+int gcmg_level_dof_coords(const gcmg_handle* h, int level, double* xyz);
+
+/*
+ * dst = A_level src, the matrix-free operator of Eq. 2 (Laplace, constraints
+ * applied while gathering and scattering).  src, dst: device, n_free(level),
+ * distinct.  fp64 selects double or float arithmetic and storage.
+ */
+int gcmg_vmult(gcmg_handle* h, int level, int fp64, const void* src, void* dst);
+/* fp64 diagonal of A_level (Eqs. 3-4) into device memory */
+int gcmg_diagonal(gcmg_handle* h, int level, double* dst);
+/*
+ * b = C^T F on the finest level, F_i = (f, phi_i) by Gauss quadrature, with
+ * f = amp * sum_m cos(2 pi kappa_m . x + phi_m) (n_modes > 0; `modes` is a
+ * host array kappa_x, kappa_y, kappa_z, phi per mode) or f = 1 (n_modes = 0).
+ */
+int gcmg_rhs(gcmg_handle* h, int n_modes, const double* modes, double amp, double* b);
+/* lambda_max used by the Chebyshev smoother of a level (after the safety factor) */
+int gcmg_get_lambda(const gcmg_handle* h, int level, double* lam);
+int gcmg_set_lambda(gcmg_handle* h, int level, double lam);
+/*
+ * Chebyshev iteration around point Jacobi (Sec. 3.3) on a level:
+ * x <- smoother(A, x, b); zero_init = 1 ignores x on entry (Algorithm 2
+ * presmoothing).  Uses the level's work vectors.
+ */
+int gcmg_smooth(gcmg_handle* h, int level, int fp64, void* x, const void* b, int zero_init);
+/* fine += P coarse, Eqs. 5-7 (fine_level >= 1, coarse = fine_level - 1) */
+int gcmg_prolongate_add(gcmg_handle* h, int fine_level, int fp64, const void* coarse, void* fine);
+/* coarse += P^T fine (Sec. 3.5: R = P^T) */
+int gcmg_restrict_add(gcmg_handle* h, int fine_level, int fp64, const void* fine, void* coarse);
+/* x = A_0^{-1} b on level 0 (Sec. 3.4, exact fp64 solve) */
+int gcmg_coarse_solve(gcmg_handle* h, int fp64, const void* b, void* x);
+/*
+ * x = V-cycle(b) (Algorithms 1-2): b, x are fp64 device vectors of the
+ * finest level; the levels run in the configured precision.
+ */
+int gcmg_vcycle(gcmg_handle* h, const double* b, double* x);
+
+typedef struct {
+  int iterations;
+  double r0;            /* ||b||_2 */
+  double rel_residual;  /* ||b - A x||_2 / ||b||_2 of the CG recurrence */
+  int status;           /* GCMG_OK, GCMG_ERR_NOT_CONVERGED or GCMG_ERR_BREAKDOWN */
+} gcmg_solve_stats;
+
+/*
+ * CG preconditioned by one V-cycle (Sec. 2, Sec. 5), fp64 vectors and inner
+ * products, x_0 = 0, stops when ||b - A x||_2 <= rtol ||b||_2.  b, x: fp64
+ * device vectors of the finest level.  Synchronises the stream.
+ */
+int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int maxit, gcmg_solve_stats* stats);
+
+const char* gcmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GCMG_H */

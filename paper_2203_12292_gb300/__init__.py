@@ -1,0 +1,286 @@
+"""Python binding of libgcmg (global-coarsening matrix-free multigrid on one
+GB300).  Argument marshalling only: every step runs in the library's CUDA
+kernels; PyTorch provides device memory and the stream.
+
+The library is built in-tree by ``paper_2203_12292_gb300.build.build()``;
+importing this module does not build it, and every call fails loudly if the
+shared library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgcmg.so")
+
+_c_int, _c_double, _c_void_p, _c_int64 = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64
+
+PRED_ALL, PRED_OCTANT_CENTRE, PRED_SPHERE, PRED_SHELL, PRED_OCTANT_STRICT = 0, 1, 2, 3, 4
+
+ERRORS = {1: "GCMG_ERR_ARG", 2: "GCMG_ERR_CUDA", 3: "GCMG_ERR_OOM", 4: "GCMG_ERR_NOT_CONVERGED",
+          5: "GCMG_ERR_BREAKDOWN", 6: "GCMG_ERR_INTERNAL"}
+
+
+class GcmgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class RefineStep(ctypes.Structure):
+    _fields_ = [("pred", _c_int), ("a", _c_double), ("b", _c_double), ("c", _c_double), ("d", _c_double)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("degree", _c_int), ("p_coarsening", _c_int), ("mg_fp32", _c_int), ("cheb_degree", _c_int),
+                ("smoothing_range", _c_double), ("eig_steps", _c_int), ("eig_safety", _c_double),
+                ("tile_cells", _c_int)]
+
+
+class LevelInfo(ctypes.Structure):
+    _fields_ = [("n_free", _c_int64), ("n_cells", _c_int64), ("degree", _c_int), ("n_tiles", _c_int),
+                ("n_colours", _c_int), ("tile_cells", _c_int), ("max_local", _c_int), ("fp32", _c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iterations", _c_int), ("r0", _c_double), ("rel_residual", _c_double), ("status", _c_int)]
+
+
+_SIGS = {
+    "gcmg_last_error": (ctypes.c_char_p, []),
+    "gcmg_mesh_create": (_c_int, [_c_double, _c_double, _c_int, ctypes.POINTER(RefineStep), ctypes.POINTER(_c_void_p)]),
+    "gcmg_mesh_destroy": (None, [_c_void_p]),
+    "gcmg_mesh_num_levels": (_c_int, [_c_void_p, ctypes.POINTER(_c_int)]),
+    "gcmg_mesh_level_cells": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_int64)]),
+    "gcmg_mesh_dof_coords": (_c_int, [_c_void_p, _c_int, _c_int, _c_int, ctypes.POINTER(_c_int64), _c_void_p]),
+    "gcmg_config_default": (_c_int, [ctypes.POINTER(Config)]),
+    "gcmg_setup": (_c_int, [_c_void_p, ctypes.POINTER(Config), _c_void_p, ctypes.POINTER(_c_void_p)]),
+    "gcmg_destroy": (None, [_c_void_p]),
+    "gcmg_set_stream": (_c_int, [_c_void_p, _c_void_p]),
+    "gcmg_num_levels": (_c_int, [_c_void_p, ctypes.POINTER(_c_int)]),
+    "gcmg_get_level_info": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(LevelInfo)]),
+    "gcmg_level_dof_coords": (_c_int, [_c_void_p, _c_int, _c_void_p]),
+    "gcmg_vmult": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
+    "gcmg_diagonal": (_c_int, [_c_void_p, _c_int, _c_void_p]),
+    "gcmg_rhs": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_double, _c_void_p]),
+    "gcmg_get_lambda": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_double)]),
+    "gcmg_set_lambda": (_c_int, [_c_void_p, _c_int, _c_double]),
+    "gcmg_smooth": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p, _c_int]),
+    "gcmg_prolongate_add": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
+    "gcmg_restrict_add": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
+    "gcmg_coarse_solve": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p]),
+    "gcmg_vcycle": (_c_int, [_c_void_p, _c_void_p, _c_void_p]),
+    "gcmg_cg_solve": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_double, _c_int, ctypes.POINTER(SolveStats)]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libgcmg.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2203_12292_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> Sequence[str]:
+    return list(_SIGS)
+
+
+def _check(rc: int) -> None:
+    if rc != 0:
+        raise GcmgError(rc, lib().gcmg_last_error().decode())
+
+
+def _steps(steps: Sequence[Tuple]) -> ctypes.Array:
+    arr = (RefineStep * max(len(steps), 1))()
+    for i, s in enumerate(steps):
+        vals = list(s) + [0.0] * (5 - len(s))
+        arr[i] = RefineStep(int(vals[0]), *[float(v) for v in vals[1:5]])
+    return arr
+
+
+class Mesh:
+    """Octree mesh and its global-coarsening hierarchy (host only).
+
+    ``steps`` is a sequence of (pred, a, b[, c, d]) refinement steps."""
+
+    def __init__(self, lo: float, hi: float, steps: Sequence[Tuple]):
+        p = _c_void_p()
+        arr = _steps(steps)
+        _check(lib().gcmg_mesh_create(lo, hi, len(steps), arr, ctypes.byref(p)))
+        self._p = p
+
+    @classmethod
+    def from_recipe(cls, recipe) -> "Mesh":
+        return cls(recipe.lo, recipe.hi, [(s.pred, s.a, s.b, s.c, s.d) for s in recipe.steps])
+
+    def __del__(self):
+        if getattr(self, "_p", None) and _lib is not None:
+            _lib.gcmg_mesh_destroy(self._p)
+            self._p = None
+
+    @property
+    def num_levels(self) -> int:
+        n = _c_int()
+        _check(lib().gcmg_mesh_num_levels(self._p, ctypes.byref(n)))
+        return n.value
+
+    def level_cells(self, level: int) -> int:
+        n = _c_int64()
+        _check(lib().gcmg_mesh_level_cells(self._p, level, ctypes.byref(n)))
+        return n.value
+
+    def dof_coords(self, level: int, degree: int, tile_cells: int = 0) -> np.ndarray:
+        n = _c_int64()
+        _check(lib().gcmg_mesh_dof_coords(self._p, level, degree, tile_cells, ctypes.byref(n), None))
+        xyz = np.empty((n.value, 3), dtype=np.float64)
+        _check(lib().gcmg_mesh_dof_coords(self._p, level, degree, tile_cells, ctypes.byref(n),
+                                          xyz.ctypes.data_as(_c_void_p)))
+        return xyz
+
+
+def _ptr(t, n: Optional[int] = None, dtype=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"expected {n} entries, got {t.numel()}")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    return _c_void_p(t.data_ptr() if t.numel() else None)
+
+
+def _is64(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return 1
+    if t.dtype == torch.float32:
+        return 0
+    raise ValueError("vectors must be float32 or float64")
+
+
+class Multigrid:
+    """All levels of one problem on the current CUDA device, set up on the
+    current torch stream."""
+
+    def __init__(self, mesh: Mesh, degree: int, p_coarsening: bool = False, mg_fp32: bool = True,
+                 tile_cells: int = 0, cheb_degree: int = 3, smoothing_range: float = 20.0,
+                 eig_steps: int = 12, eig_safety: float = 1.2):
+        import torch
+        cfg = Config()
+        _check(lib().gcmg_config_default(ctypes.byref(cfg)))
+        cfg.degree, cfg.p_coarsening, cfg.mg_fp32 = degree, int(p_coarsening), int(mg_fp32)
+        cfg.tile_cells, cfg.cheb_degree, cfg.smoothing_range = tile_cells, cheb_degree, smoothing_range
+        cfg.eig_steps, cfg.eig_safety = eig_steps, eig_safety
+        self.mesh = mesh
+        self.stream = torch.cuda.current_stream()
+        h = _c_void_p()
+        _check(lib().gcmg_setup(mesh._p, ctypes.byref(cfg), _c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+        self.num_levels = self._num_levels()
+        self.info = [self.level_info(l) for l in range(self.num_levels)]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.gcmg_destroy(self._h)
+            self._h = None
+
+    def _num_levels(self) -> int:
+        n = _c_int()
+        _check(lib().gcmg_num_levels(self._h, ctypes.byref(n)))
+        return n.value
+
+    def level_info(self, level: int) -> LevelInfo:
+        info = LevelInfo()
+        _check(lib().gcmg_get_level_info(self._h, level, ctypes.byref(info)))
+        return info
+
+    def n_free(self, level: int = -1) -> int:
+        return self.info[level].n_free
+
+    @property
+    def finest(self) -> int:
+        return self.num_levels - 1
+
+    def dof_coords(self, level: int) -> np.ndarray:
+        xyz = np.empty((self.n_free(level), 3), dtype=np.float64)
+        _check(lib().gcmg_level_dof_coords(self._h, level, xyz.ctypes.data_as(_c_void_p)))
+        return xyz
+
+    def set_stream(self, stream) -> None:
+        self.stream = stream
+        _check(lib().gcmg_set_stream(self._h, _c_void_p(stream.cuda_stream)))
+
+    def vmult(self, level: int, src, dst) -> None:
+        n = self.n_free(level)
+        _check(lib().gcmg_vmult(self._h, level, _is64(src), _ptr(src, n, src.dtype), _ptr(dst, n, src.dtype)))
+
+    def diagonal(self, level: int):
+        import torch
+        d = torch.empty(self.n_free(level), dtype=torch.float64, device="cuda")
+        _check(lib().gcmg_diagonal(self._h, level, _ptr(d)))
+        return d
+
+    def rhs(self, fourier=None):
+        """b = C^T F on the finest level; ``fourier`` = (kappa (m,3), phi (m,), amp) or None for f = 1."""
+        import torch
+        b = torch.empty(self.n_free(self.finest), dtype=torch.float64, device="cuda")
+        if fourier is None:
+            _check(lib().gcmg_rhs(self._h, 0, None, 1.0, _ptr(b)))
+        else:
+            kappa, phi, amp = fourier
+            modes = np.ascontiguousarray(np.concatenate([np.asarray(kappa, np.float64),
+                                                         np.asarray(phi, np.float64)[:, None]], axis=1))
+            _check(lib().gcmg_rhs(self._h, len(phi), modes.ctypes.data_as(_c_void_p), float(amp), _ptr(b)))
+        return b
+
+    def get_lambda(self, level: int) -> float:
+        v = _c_double()
+        _check(lib().gcmg_get_lambda(self._h, level, ctypes.byref(v)))
+        return v.value
+
+    def set_lambda(self, level: int, lam: float) -> None:
+        _check(lib().gcmg_set_lambda(self._h, level, lam))
+
+    def smooth(self, level: int, x, b, zero_init: bool) -> None:
+        n = self.n_free(level)
+        _check(lib().gcmg_smooth(self._h, level, _is64(x), _ptr(x, n, x.dtype), _ptr(b, n, x.dtype), int(zero_init)))
+
+    def prolongate_add(self, fine_level: int, coarse, fine) -> None:
+        _check(lib().gcmg_prolongate_add(self._h, fine_level, _is64(fine), _ptr(coarse, self.n_free(fine_level - 1), fine.dtype),
+                                         _ptr(fine, self.n_free(fine_level), fine.dtype)))
+
+    def restrict_add(self, fine_level: int, fine, coarse) -> None:
+        _check(lib().gcmg_restrict_add(self._h, fine_level, _is64(fine), _ptr(fine, self.n_free(fine_level), fine.dtype),
+                                       _ptr(coarse, self.n_free(fine_level - 1), fine.dtype)))
+
+    def coarse_solve(self, b, x) -> None:
+        n = self.n_free(0)
+        _check(lib().gcmg_coarse_solve(self._h, _is64(b), _ptr(b, n, b.dtype), _ptr(x, n, b.dtype)))
+
+    def vcycle(self, b, x) -> None:
+        import torch
+        n = self.n_free(self.finest)
+        _check(lib().gcmg_vcycle(self._h, _ptr(b, n, torch.float64), _ptr(x, n, torch.float64)))
+
+    def cg_solve(self, b, x, rtol: float = 1e-8, maxit: int = 100, raise_on_fail: bool = True) -> SolveStats:
+        import torch
+        n = self.n_free(self.finest)
+        st = SolveStats()
+        rc = lib().gcmg_cg_solve(self._h, _ptr(b, n, torch.float64), _ptr(x, n, torch.float64), rtol, maxit,
+                                 ctypes.byref(st))
+        if rc != 0 and (raise_on_fail or rc not in (4, 5)):
+            _check(rc)
+        return st

@@ -1,0 +1,770 @@
+// C ABI of libgcmg: set-up of the multigrid levels and the orchestration of
+// the V-cycle (Algorithms 1-2) and of the preconditioned CG (Sec. 2).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "gcmg.h"
+#include "internal.h"
+#include "kernels.h"
+
+namespace gcmg {
+
+void upload_tables_cell();
+void upload_tables_transfer();
+
+namespace {
+
+thread_local std::string g_err;
+
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(e == cudaErrorMemoryAllocation ? GCMG_ERR_OOM : GCMG_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  void alloc(size_t n) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = n;
+    if (n) ck(cudaMalloc(&p, n), "cudaMalloc");
+  }
+  template <typename T>
+  void upload(const std::vector<T>& v, cudaStream_t s) {
+    alloc(v.size() * sizeof(T));
+    if (!v.empty()) ck(cudaMemcpyAsync(p, v.data(), bytes, cudaMemcpyHostToDevice, s), "upload");
+  }
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+struct LevelDev {
+  LevelHost host;
+  bool fp32 = true;
+  DevBuf tiles, colour_tiles, meta, foreign, subptr, perm, cell_ijk, gstart, own, mask;
+  DevBuf diag64, dinv64, dinv32;
+  DevBuf x, b, d, t;        // V-cycle vectors in level precision
+  DevBuf w64a, w64b, w64c;  // fp64 work vectors (set-up, fp64 smoothing through the API)
+  DevBuf w32a, w32b;        // fp32 work vectors (fp32 smoothing through the API)
+  CellLaunch cl{};
+  double lam = 1.0;
+  int64_t n() const { return host.n_free; }
+};
+
+struct TransferDev {
+  TransferHost host;
+  DevBuf fine_of, refined;
+  TransferLaunch tl{};
+};
+
+}  // namespace
+
+struct Handle {
+  cudaStream_t stream = nullptr;
+  gcmg_config cfg{};
+  std::vector<std::unique_ptr<LevelDev>> lev;
+  std::vector<std::unique_ptr<TransferDev>> tr;  // tr[l]: between levels l and l-1
+  DevBuf diag_tab[KMAX + 1];
+  DevBuf Ainv;
+  int n0 = 0;
+  DevBuf scratch, scal, modes;
+  DevBuf cg_r, cg_p, cg_q, cg_z;
+};
+
+namespace {
+
+int default_tile_cells(int k) {
+  switch (k) {
+    case 1: return 128;
+    case 2: return 64;
+    default: return 32;
+  }
+}
+
+void check_level(const Handle& h, int level) {
+  if (level < 0 || level >= (int)h.lev.size()) throw Error(GCMG_ERR_ARG, "level out of range");
+}
+
+void vmult(Handle& H, int l, bool fp64, const void* src, void* dst) {
+  LevelDev& L = *H.lev[l];
+  if (L.n() == 0) return;
+  launch_vmult(L.cl, fp64, src, dst, 0, H.stream);
+}
+
+double dot_host(Handle& H, const double* x, const double* y, int64_t n) {
+  if (n == 0) return 0.0;
+  launch_dot(x, y, n, H.scratch.as<double>(), H.scal.as<double>(), 8, DOT_STORE, H.stream);
+  double v = 0;
+  ck(cudaMemcpyAsync(&v, H.scal.as<double>() + 8, sizeof(double), cudaMemcpyDeviceToHost, H.stream), "dot");
+  ck(cudaStreamSynchronize(H.stream), "sync");
+  return v;
+}
+
+// largest eigenvalue of a symmetric tridiagonal matrix by Sturm bisection
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  const int m = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {
+    int c = 0;
+    double q = a[0] - x;
+    if (q < 0) ++c;
+    for (int i = 1; i < m; ++i) {
+      if (q == 0.0) q = 1e-300;
+      q = a[i] - x - b[i - 1] * b[i - 1] / q;
+      if (q < 0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= m)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return hi;
+}
+
+// lambda_max of D^{-1} A from the Lanczos tridiagonal matrix of
+// Jacobi-preconditioned CG on A y = 1 (set-up; fp64)
+double estimate_lambda(Handle& H, int l) {
+  LevelDev& L = *H.lev[l];
+  const int64_t n = L.n();
+  if (n == 0) return 1.0;
+  double* r = L.w64a.as<double>();
+  double* p = L.w64b.as<double>();
+  double* q = L.w64c.as<double>();
+  double* z = L.w64c.as<double>();  // z and q are never live together
+  launch_fill(r, 1.0, n, H.stream);
+  launch_pmul(z, L.dinv64.as<double>(), r, n, H.stream);
+  ck(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
+  double rz = dot_host(H, r, z, n);
+  const double rz0 = rz;
+  std::vector<double> alpha, beta;
+  for (int it = 0; it < H.cfg.eig_steps; ++it) {
+    vmult(H, l, true, p, q);
+    const double pq = dot_host(H, p, q, n);
+    if (!(pq > 0.0)) break;
+    const double a = rz / pq;
+    alpha.push_back(a);
+    launch_axpy(true, r, q, -a, n, H.stream);
+    launch_pmul(z, L.dinv64.as<double>(), r, n, H.stream);
+    const double rz_new = dot_host(H, r, z, n);
+    if (!(rz_new > 1e-30 * rz0)) break;  // Krylov space exhausted
+    const double bt = rz_new / rz;
+    beta.push_back(bt);
+    launch_xpby(p, z, bt, n, H.stream);
+    rz = rz_new;
+  }
+  const int m = (int)alpha.size();
+  if (m == 0) return 1.0;
+  std::vector<double> da(m), ob(std::max(m - 1, 0));
+  for (int i = 0; i < m; ++i) {
+    da[i] = 1.0 / alpha[i] + (i > 0 ? beta[i - 1] / alpha[i - 1] : 0.0);
+    if (i + 1 < m) ob[i] = std::sqrt(beta[i]) / alpha[i];
+  }
+  return tridiag_max_eig(da, ob);
+}
+
+void setup_coarse(Handle& H) {
+  LevelDev& L = *H.lev[0];
+  const int n = (int)L.n();
+  H.n0 = n;
+  if (n == 0) return;
+  std::vector<double> A((size_t)n * n), col(n);
+  double* e = L.w64a.as<double>();
+  double* y = L.w64b.as<double>();
+  for (int j = 0; j < n; ++j) {
+    std::vector<double> ej(n, 0.0);
+    ej[j] = 1.0;
+    ck(cudaMemcpyAsync(e, ej.data(), n * sizeof(double), cudaMemcpyHostToDevice, H.stream), "coarse");
+    vmult(H, 0, true, e, y);
+    ck(cudaMemcpyAsync(col.data(), y, n * sizeof(double), cudaMemcpyDeviceToHost, H.stream), "coarse");
+    ck(cudaStreamSynchronize(H.stream), "sync");
+    for (int i = 0; i < n; ++i) A[(size_t)i * n + j] = col[i];
+  }
+  // Cholesky A = L L^T and the explicit inverse (n <= (k-1)^3)
+  std::vector<double> Lc((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+      for (int m = 0; m < j; ++m) s -= Lc[(size_t)i * n + m] * Lc[(size_t)j * n + m];
+      if (i == j) {
+        if (!(s > 0)) throw Error(GCMG_ERR_INTERNAL, "level-0 matrix not positive definite");
+        Lc[(size_t)i * n + i] = std::sqrt(s);
+      } else {
+        Lc[(size_t)i * n + j] = s / Lc[(size_t)j * n + j];
+      }
+    }
+  std::vector<double> inv((size_t)n * n);
+  for (int c = 0; c < n; ++c) {
+    std::vector<double> v(n, 0.0);
+    v[c] = 1.0;
+    for (int i = 0; i < n; ++i) {
+      double s = v[i];
+      for (int m = 0; m < i; ++m) s -= Lc[(size_t)i * n + m] * v[m];
+      v[i] = s / Lc[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double s = v[i];
+      for (int m = i + 1; m < n; ++m) s -= Lc[(size_t)m * n + i] * v[m];
+      v[i] = s / Lc[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = v[i];
+  }
+  H.Ainv.upload(inv, H.stream);
+}
+
+// Chebyshev coefficients of step `it` (Saad, Iterative Methods, Alg. 12.1)
+struct ChebCoef {
+  double c1, c2;
+};
+std::vector<ChebCoef> cheb_coefs(double lam_max, double range, int degree) {
+  const double lmin = lam_max / range;
+  const double theta = 0.5 * (lam_max + lmin), delta = 0.5 * (lam_max - lmin);
+  std::vector<ChebCoef> c;
+  double rho = delta / theta;
+  c.push_back({0.0, 1.0 / theta});
+  for (int it = 1; it < degree; ++it) {
+    const double rn = 1.0 / (2.0 * theta / delta - rho);
+    c.push_back({rn * rho, 2.0 * rn / delta});
+    rho = rn;
+  }
+  return c;
+}
+
+// Chebyshev smoother on level l with vectors x, b, d, t (precision fp64)
+void smooth(Handle& H, int l, bool fp64, void* x, const void* b, void* d, void* t, const void* dinv, bool zero_init) {
+  LevelDev& L = *H.lev[l];
+  const int64_t n = L.n();
+  if (n == 0) return;
+  const auto c = cheb_coefs(L.lam, H.cfg.smoothing_range, H.cfg.cheb_degree);
+  size_t it = 0;
+  if (zero_init) {
+    launch_cheb_init(fp64, x, d, b, dinv, c[0].c2, n, H.stream);
+    it = 1;
+  }
+  for (; it < c.size(); ++it) {
+    vmult(H, l, fp64, x, t);
+    launch_cheb_step(fp64, x, d, b, t, dinv, c[it].c1, c[it].c2, n, H.stream);
+  }
+}
+
+void vcycle_level(Handle& H, int l) {
+  LevelDev& L = *H.lev[l];
+  const bool f64 = !L.fp32;
+  if (l == 0) {
+    if (H.n0) launch_coarse_solve(f64, H.Ainv.as<double>(), H.n0, L.b.p, L.x.p, H.stream);
+    return;
+  }
+  const void* dinv = f64 ? L.dinv64.p : L.dinv32.p;
+  smooth(H, l, f64, L.x.p, L.b.p, L.d.p, L.t.p, dinv, true);  // presmoothing
+  vmult(H, l, f64, L.x.p, L.t.p);                             // residual
+  launch_residual(f64, L.t.p, L.b.p, L.t.p, L.n(), H.stream);
+  LevelDev& C = *H.lev[l - 1];
+  launch_zero(!C.fp32, C.b.p, C.n(), H.stream);
+  if (C.n()) launch_restrict_add(H.tr[l]->tl, f64, L.t.p, C.b.p, H.stream);  // restriction
+  vcycle_level(H, l - 1);
+  if (C.n()) launch_prolongate_add(H.tr[l]->tl, f64, C.x.p, L.x.p, H.stream);  // prolongation
+  smooth(H, l, f64, L.x.p, L.b.p, L.d.p, L.t.p, dinv, false);  // postsmoothing
+}
+
+void vcycle(Handle& H, const double* b, double* x) {
+  const int top = (int)H.lev.size() - 1;
+  LevelDev& F = *H.lev[top];
+  if (F.fp32)
+    launch_cast(false, b, F.b.p, F.n(), H.stream);
+  else
+    ck(cudaMemcpyAsync(F.b.p, b, F.n() * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
+  vcycle_level(H, top);
+  if (F.fp32)
+    launch_cast(true, F.x.p, x, F.n(), H.stream);
+  else
+    ck(cudaMemcpyAsync(x, F.x.p, F.n() * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    f();
+    return GCMG_OK;
+  } catch (const Error& e) {
+    g_err = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_err = "host allocation failed";
+    return GCMG_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return GCMG_ERR_INTERNAL;
+  }
+}
+
+}  // namespace
+}  // namespace gcmg
+
+struct gcmg_mesh {
+  std::vector<gcmg::Octree> levels;  // coarsest (one cell) first
+  int lmax = 0;
+};
+
+struct gcmg_handle {
+  gcmg::Handle h;
+};
+
+using namespace gcmg;
+
+extern "C" {
+
+const char* gcmg_last_error(void) { return g_err.c_str(); }
+
+int gcmg_mesh_create(double lo, double hi, int n_steps, const gcmg_refine_step* steps, gcmg_mesh** out) {
+  return guarded([&] {
+    if (!out || (n_steps > 0 && !steps) || !(hi > lo) || n_steps < 0) throw Error(GCMG_ERR_ARG, "bad mesh arguments");
+    auto m = std::make_unique<gcmg_mesh>();
+    Octree t;
+    t.lo = lo;
+    t.hi = hi;
+    t.leaves.insert(cell_key(0, 0, 0, 0));
+    for (int i = 0; i < n_steps; ++i) {
+      if (steps[i].pred < 0 || steps[i].pred > 4) throw Error(GCMG_ERR_ARG, "unknown refinement predicate");
+      t.refine_step(RefineStep{steps[i].pred, steps[i].a, steps[i].b, steps[i].c, steps[i].d});
+      if (t.max_level() > 17) throw Error(GCMG_ERR_ARG, "mesh deeper than 17 levels");
+    }
+    m->lmax = t.max_level();
+    std::vector<Octree> lv{t};
+    while (lv.back().leaves.size() > 1) lv.push_back(coarsen_global(lv.back()));
+    std::reverse(lv.begin(), lv.end());
+    m->levels = std::move(lv);
+    *out = m.release();
+  });
+}
+
+void gcmg_mesh_destroy(gcmg_mesh* mesh) { delete mesh; }
+
+int gcmg_mesh_num_levels(const gcmg_mesh* mesh, int* n) {
+  return guarded([&] {
+    if (!mesh || !n) throw Error(GCMG_ERR_ARG, "null argument");
+    *n = (int)mesh->levels.size();
+  });
+}
+
+int gcmg_mesh_level_cells(const gcmg_mesh* mesh, int level, int64_t* n_cells) {
+  return guarded([&] {
+    if (!mesh || !n_cells || level < 0 || level >= (int)mesh->levels.size()) throw Error(GCMG_ERR_ARG, "bad level");
+    *n_cells = (int64_t)mesh->levels[level].leaves.size();
+  });
+}
+
+int gcmg_mesh_dof_coords(const gcmg_mesh* mesh, int level, int degree, int tile_cells, int64_t* n_free, double* xyz) {
+  return guarded([&] {
+    if (!mesh || !n_free || level < 0 || level >= (int)mesh->levels.size()) throw Error(GCMG_ERR_ARG, "bad level");
+    if (degree < 1 || degree > KMAX) throw Error(GCMG_ERR_ARG, "degree must be 1..4");
+    if (tile_cells < 0 || tile_cells > 255) throw Error(GCMG_ERR_ARG, "tile_cells must be 0..255");
+    LevelHost L;
+    build_level(mesh->levels[level], degree, tile_cells ? tile_cells : default_tile_cells(degree), mesh->lmax, L);
+    *n_free = L.n_free;
+    if (xyz) std::memcpy(xyz, L.dof_xyz_cache.data(), L.dof_xyz_cache.size() * sizeof(double));
+  });
+}
+
+int gcmg_config_default(gcmg_config* cfg) {
+  return guarded([&] {
+    if (!cfg) throw Error(GCMG_ERR_ARG, "null config");
+    cfg->degree = 1;
+    cfg->p_coarsening = 0;
+    cfg->mg_fp32 = 1;
+    cfg->cheb_degree = 3;
+    cfg->smoothing_range = 20.0;
+    cfg->eig_steps = 12;
+    cfg->eig_safety = 1.2;
+    cfg->tile_cells = 0;
+  });
+}
+
+int gcmg_setup(const gcmg_mesh* mesh, const gcmg_config* cfg, void* stream, gcmg_handle** out) {
+  return guarded([&] {
+    if (!mesh || !cfg || !out) throw Error(GCMG_ERR_ARG, "null argument");
+    if (cfg->degree < 1 || cfg->degree > KMAX) throw Error(GCMG_ERR_ARG, "degree must be 1..4");
+    if (cfg->cheb_degree < 1 || !(cfg->smoothing_range > 1.0) || cfg->eig_steps < 1)
+      throw Error(GCMG_ERR_ARG, "bad smoother parameters");
+    if (cfg->tile_cells < 0 || cfg->tile_cells > 255) throw Error(GCMG_ERR_ARG, "tile_cells must be 0..255");
+    int dev = 0;
+    ck(cudaGetDevice(&dev), "cudaGetDevice");
+    auto hh = std::make_unique<gcmg_handle>();
+    Handle& H = hh->h;
+    H.stream = static_cast<cudaStream_t>(stream);
+    H.cfg = *cfg;
+    upload_tables_cell();
+    upload_tables_transfer();
+    ck(cudaGetLastError(), "upload tables");
+    // level list: (mesh index, degree), coarsest first
+    std::vector<std::pair<int, int>> spec;
+    const int nm = (int)mesh->levels.size();
+    if (cfg->p_coarsening) {
+      for (int m = 0; m + 1 < nm; ++m) spec.push_back({m, 1});
+      std::vector<int> degs{cfg->degree};
+      while (degs.back() > 1) degs.push_back(degs.back() / 2);
+      for (auto it = degs.rbegin(); it != degs.rend(); ++it) spec.push_back({nm - 1, *it});
+    } else {
+      for (int m = 0; m < nm; ++m) spec.push_back({m, cfg->degree});
+    }
+    const int nl = (int)spec.size();
+    for (int l = 0; l < nl; ++l) {
+      auto L = std::make_unique<LevelDev>();
+      const int k = spec[l].second;
+      const int tc = cfg->tile_cells ? cfg->tile_cells : default_tile_cells(k);
+      build_level(mesh->levels[spec[l].first], k, tc, mesh->lmax, L->host);
+      L->fp32 = cfg->mg_fp32 != 0;
+      LevelHost& lh = L->host;
+      L->tiles.upload(lh.tiles, H.stream);
+      L->colour_tiles.upload(lh.colour_tiles, H.stream);
+      L->meta.upload(lh.meta, H.stream);
+      L->foreign.upload(lh.foreign, H.stream);
+      L->subptr.upload(lh.subptr, H.stream);
+      L->perm.upload(lh.perm, H.stream);
+      std::vector<int32_t> ijk(lh.cells.size() * 3);
+      for (size_t c = 0; c < lh.cells.size(); ++c) {
+        ijk[3 * c] = lh.cells[c].i;
+        ijk[3 * c + 1] = lh.cells[c].j;
+        ijk[3 * c + 2] = lh.cells[c].k;
+      }
+      L->cell_ijk.upload(ijk, H.stream);
+      L->gstart.upload(lh.gstart, H.stream);
+      L->own.upload(lh.own, H.stream);
+      L->mask.upload(lh.mask, H.stream);
+      CellLaunch& c = L->cl;
+      c.tiles = L->tiles.as<TileInfo>();
+      c.colour_tiles = L->colour_tiles.as<int32_t>();
+      c.colour_ptr = lh.colour_ptr.data();
+      c.n_colours = lh.n_colours;
+      c.meta = L->meta.as<CellMeta>();
+      c.foreign = L->foreign.as<int32_t>();
+      c.subptr = L->subptr.as<uint16_t>();
+      c.perm = L->perm.as<uint8_t>();
+      c.cell_ijk = L->cell_ijk.as<int32_t>();
+      c.k = k;
+      c.tc = tc;
+      c.max_local = lh.max_local;
+      c.lo = lh.lo;
+      c.dom = lh.hi - lh.lo;
+      const int64_t n = lh.n_free;
+      const size_t vb = L->fp32 ? sizeof(float) : sizeof(double);
+      L->x.alloc(n * vb);
+      L->b.alloc(n * vb);
+      L->d.alloc(n * vb);
+      L->t.alloc(n * vb);
+      L->w64a.alloc(n * sizeof(double));
+      L->w64b.alloc(n * sizeof(double));
+      L->w64c.alloc(n * sizeof(double));
+      L->w32a.alloc(n * sizeof(float));
+      L->w32b.alloc(n * sizeof(float));
+      L->diag64.alloc(n * sizeof(double));
+      L->dinv64.alloc(n * sizeof(double));
+      L->dinv32.alloc(n * sizeof(float));
+      H.lev.push_back(std::move(L));
+    }
+    H.tr.resize(nl);
+    for (int l = 1; l < nl; ++l) {
+      auto T = std::make_unique<TransferDev>();
+      LevelHost& fh = H.lev[l]->host;
+      LevelHost& ch = H.lev[l - 1]->host;
+      if (spec[l].first == spec[l - 1].first)
+        build_transfer_p(fh, ch, T->host);
+      else
+        build_transfer_h(fh, ch, T->host);
+      T->fine_of.upload(T->host.fine_of, H.stream);
+      T->refined.upload(T->host.refined, H.stream);
+      TransferLaunch& t = T->tl;
+      t.kind = T->host.kind;
+      t.kf = fh.k;
+      t.kc = ch.k;
+      t.n_coarse = (int)ch.cells.size();
+      t.fine_of = T->fine_of.as<int32_t>();
+      t.refined = T->refined.as<uint8_t>();
+      t.gstart_f = H.lev[l]->gstart.as<int32_t>();
+      t.own_f = H.lev[l]->own.as<uint32_t>();
+      t.gstart_c = H.lev[l - 1]->gstart.as<int32_t>();
+      t.mask_c = H.lev[l - 1]->mask.as<uint16_t>();
+      t.coarse = H.lev[l - 1]->cl;
+      H.tr[l] = std::move(T);
+    }
+    H.scratch.alloc(DOT_BLOCKS * sizeof(double));
+    H.scal.alloc(16 * sizeof(double));
+    ck(cudaMemsetAsync(H.scal.p, 0, 16 * sizeof(double), H.stream), "memset");
+    // Jacobi diagonals (Eqs. 3-4)
+    for (int l = 0; l < nl; ++l) {
+      const int k = spec[l].second;
+      if (!H.diag_tab[k].p) {
+        const int n3 = (k + 1) * (k + 1) * (k + 1);
+        H.diag_tab[k].alloc((size_t)512 * n3 * sizeof(double));
+        launch_diag_table(k, H.diag_tab[k].as<double>(), H.stream);
+      }
+      LevelDev& L = *H.lev[l];
+      if (L.n() == 0) continue;
+      launch_diag(L.cl, H.diag_tab[k].as<double>(), L.diag64.as<double>(), H.stream);
+      launch_invert(L.diag64.as<double>(), L.dinv64.as<double>(), L.dinv32.as<float>(), L.n(), H.stream);
+    }
+    ck(cudaGetLastError(), "diagonal");
+    setup_coarse(H);
+    for (int l = 1; l < nl; ++l) H.lev[l]->lam = cfg->eig_safety * estimate_lambda(H, l);
+    const int64_t nf = H.lev.back()->n();
+    H.cg_r.alloc(nf * sizeof(double));
+    H.cg_p.alloc(nf * sizeof(double));
+    H.cg_q.alloc(nf * sizeof(double));
+    H.cg_z.alloc(nf * sizeof(double));
+    ck(cudaStreamSynchronize(H.stream), "setup");
+    ck(cudaGetLastError(), "setup");
+    *out = hh.release();
+  });
+}
+
+void gcmg_destroy(gcmg_handle* h) { delete h; }
+
+int gcmg_set_stream(gcmg_handle* h, void* stream) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    h->h.stream = static_cast<cudaStream_t>(stream);
+  });
+}
+
+int gcmg_num_levels(const gcmg_handle* h, int* n) {
+  return guarded([&] {
+    if (!h || !n) throw Error(GCMG_ERR_ARG, "null argument");
+    *n = (int)h->h.lev.size();
+  });
+}
+
+int gcmg_get_level_info(const gcmg_handle* h, int level, gcmg_level_info* info) {
+  return guarded([&] {
+    if (!h || !info) throw Error(GCMG_ERR_ARG, "null argument");
+    check_level(h->h, level);
+    const LevelDev& L = *h->h.lev[level];
+    info->n_free = L.host.n_free;
+    info->n_cells = (int64_t)L.host.cells.size();
+    info->degree = L.host.k;
+    info->n_tiles = (int)L.host.tiles.size();
+    info->n_colours = L.host.n_colours;
+    info->tile_cells = L.host.tile_cells;
+    info->max_local = L.host.max_local;
+    info->fp32 = L.fp32 ? 1 : 0;
+  });
+}
+
+int gcmg_level_dof_coords(const gcmg_handle* h, int level, double* xyz) {
+  return guarded([&] {
+    if (!h || !xyz) throw Error(GCMG_ERR_ARG, "null argument");
+    check_level(h->h, level);
+    const auto& v = h->h.lev[level]->host.dof_xyz_cache;
+    std::memcpy(xyz, v.data(), v.size() * sizeof(double));
+  });
+}
+
+int gcmg_vmult(gcmg_handle* h, int level, int fp64, const void* src, void* dst) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    check_level(h->h, level);
+    if (h->h.lev[level]->n() == 0) return;
+    if (!src || !dst || src == dst) throw Error(GCMG_ERR_ARG, "bad vectors");
+    vmult(h->h, level, fp64 != 0, src, dst);
+    ck(cudaGetLastError(), "vmult");
+  });
+}
+
+int gcmg_diagonal(gcmg_handle* h, int level, double* dst) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    check_level(h->h, level);
+    LevelDev& L = *h->h.lev[level];
+    if (L.n() && !dst) throw Error(GCMG_ERR_ARG, "bad vector");
+    if (L.n())
+      ck(cudaMemcpyAsync(dst, L.diag64.p, L.n() * sizeof(double), cudaMemcpyDeviceToDevice, h->h.stream), "copy");
+  });
+}
+
+int gcmg_rhs(gcmg_handle* h, int n_modes, const double* modes, double amp, double* b) {
+  return guarded([&] {
+    if (!h || n_modes < 0 || (n_modes > 0 && !modes)) throw Error(GCMG_ERR_ARG, "bad arguments");
+    Handle& H = h->h;
+    LevelDev& L = *H.lev.back();
+    if (L.n() && !b) throw Error(GCMG_ERR_ARG, "bad vector");
+    if (n_modes > 0) {
+      std::vector<double> v(modes, modes + 4 * n_modes);
+      H.modes.upload(v, H.stream);
+    }
+    RhsDesc f{n_modes ? H.modes.as<double>() : nullptr, n_modes, amp};
+    if (L.n()) launch_rhs(L.cl, f, b, H.stream);
+    ck(cudaStreamSynchronize(H.stream), "rhs");
+  });
+}
+
+int gcmg_get_lambda(const gcmg_handle* h, int level, double* lam) {
+  return guarded([&] {
+    if (!h || !lam) throw Error(GCMG_ERR_ARG, "null argument");
+    check_level(h->h, level);
+    *lam = h->h.lev[level]->lam;
+  });
+}
+
+int gcmg_set_lambda(gcmg_handle* h, int level, double lam) {
+  return guarded([&] {
+    if (!h || !(lam > 0)) throw Error(GCMG_ERR_ARG, "bad lambda");
+    check_level(h->h, level);
+    h->h.lev[level]->lam = lam;
+  });
+}
+
+int gcmg_smooth(gcmg_handle* h, int level, int fp64, void* x, const void* b, int zero_init) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    check_level(h->h, level);
+    LevelDev& L = *h->h.lev[level];
+    if (L.n() == 0) return;
+    if (!x || !b) throw Error(GCMG_ERR_ARG, "bad vectors");
+    if (fp64)
+      smooth(h->h, level, true, x, b, L.w64a.p, L.w64b.p, L.dinv64.p, zero_init != 0);
+    else
+      smooth(h->h, level, false, x, b, L.w32a.p, L.w32b.p, L.dinv32.p, zero_init != 0);
+    ck(cudaGetLastError(), "smooth");
+  });
+}
+
+int gcmg_prolongate_add(gcmg_handle* h, int fine_level, int fp64, const void* coarse, void* fine) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    if (fine_level < 1) throw Error(GCMG_ERR_ARG, "fine_level must be >= 1");
+    check_level(h->h, fine_level);
+    if (h->h.lev[fine_level - 1]->n() == 0 || h->h.lev[fine_level]->n() == 0) return;
+    if (!coarse || !fine) throw Error(GCMG_ERR_ARG, "bad vectors");
+    if (h->h.lev[fine_level - 1]->n())
+      launch_prolongate_add(h->h.tr[fine_level]->tl, fp64 != 0, coarse, fine, h->h.stream);
+    ck(cudaGetLastError(), "prolongate");
+  });
+}
+
+int gcmg_restrict_add(gcmg_handle* h, int fine_level, int fp64, const void* fine, void* coarse) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    if (fine_level < 1) throw Error(GCMG_ERR_ARG, "fine_level must be >= 1");
+    check_level(h->h, fine_level);
+    if (h->h.lev[fine_level - 1]->n() == 0 || h->h.lev[fine_level]->n() == 0) return;
+    if (!coarse || !fine) throw Error(GCMG_ERR_ARG, "bad vectors");
+    if (h->h.lev[fine_level - 1]->n())
+      launch_restrict_add(h->h.tr[fine_level]->tl, fp64 != 0, fine, coarse, h->h.stream);
+    ck(cudaGetLastError(), "restrict");
+  });
+}
+
+int gcmg_coarse_solve(gcmg_handle* h, int fp64, const void* b, void* x) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    if (h->h.n0 && (!b || !x)) throw Error(GCMG_ERR_ARG, "bad vectors");
+    if (h->h.n0) launch_coarse_solve(fp64 != 0, h->h.Ainv.as<double>(), h->h.n0, b, x, h->h.stream);
+    ck(cudaGetLastError(), "coarse solve");
+  });
+}
+
+int gcmg_vcycle(gcmg_handle* h, const double* b, double* x) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    if (h->h.lev.back()->n() == 0) return;
+    if (!b || !x) throw Error(GCMG_ERR_ARG, "bad vectors");
+    vcycle(h->h, b, x);
+    ck(cudaGetLastError(), "vcycle");
+  });
+}
+
+int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int maxit, gcmg_solve_stats* stats) {
+  int status = GCMG_OK;
+  int rc = guarded([&] {
+    if (!h || !(rtol > 0) || maxit < 0) throw Error(GCMG_ERR_ARG, "bad arguments");
+    Handle& H = h->h;
+    const int top = (int)H.lev.size() - 1;
+    const int64_t n = H.lev[top]->n();
+    if (n == 0) {
+      if (stats) *stats = gcmg_solve_stats{0, 0.0, 0.0, GCMG_OK};
+      return;
+    }
+    if (!b || !x) throw Error(GCMG_ERR_ARG, "bad vectors");
+    double* r = H.cg_r.as<double>();
+    double* p = H.cg_p.as<double>();
+    double* q = H.cg_q.as<double>();
+    double* z = H.cg_z.as<double>();
+    double* S = H.scal.as<double>();
+    cudaStream_t s = H.stream;
+    gcmg_solve_stats st{0, 0.0, 0.0, GCMG_OK};
+    launch_zero(true, x, n, s);
+    ck(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    const double nb = std::sqrt(dot_host(H, r, r, n));
+    st.r0 = nb;
+    if (nb == 0.0 || n == 0) {
+      if (stats) *stats = st;
+      return;
+    }
+    vcycle(H, r, z);
+    launch_dot(r, z, n, H.scratch.as<double>(), S, 0, DOT_STORE, s);  // rz
+    ck(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    double rr = nb * nb;
+    int it = 0;
+    for (it = 1; it <= maxit; ++it) {
+      vmult(H, top, true, p, q);
+      launch_dot(p, q, n, H.scratch.as<double>(), S, 0, DOT_ALPHA, s);
+      launch_cg_update_xr(x, r, p, q, S, n, H.scratch.as<double>(), S, s);
+      double hs[6];
+      ck(cudaMemcpyAsync(hs, S, sizeof(hs), cudaMemcpyDeviceToHost, s), "scalars");
+      ck(cudaStreamSynchronize(s), "cg");
+      if (!(hs[1] > 0.0) || std::isnan(hs[2])) {
+        status = GCMG_ERR_BREAKDOWN;
+        break;
+      }
+      rr = hs[2];
+      if (std::sqrt(rr) <= rtol * nb) break;
+      vcycle(H, r, z);
+      launch_dot(r, z, n, H.scratch.as<double>(), S, 0, DOT_BETA, s);
+      launch_cg_update_p(p, z, S, n, s);
+    }
+    if (it > maxit) {
+      it = maxit;
+      status = GCMG_ERR_NOT_CONVERGED;
+    }
+    st.iterations = it;
+    st.rel_residual = std::sqrt(rr) / nb;
+    st.status = status;
+    ck(cudaStreamSynchronize(s), "cg");
+    ck(cudaGetLastError(), "cg");
+    if (stats) *stats = st;
+  });
+  if (rc != GCMG_OK) return rc;
+  if (status != GCMG_OK) g_err = status == GCMG_ERR_BREAKDOWN ? "CG breakdown" : "CG did not converge";
+  return status;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Launch interface of the CUDA kernels of libgcmg (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace gcmg {
+
+enum CellMode { MODE_VMULT = 0, MODE_RHS = 1, MODE_DIAG = 2 };
+
+// arguments of the tile kernels (operator, right-hand side, diagonal)
+struct CellLaunch {
+  const TileInfo* tiles;
+  const int32_t* colour_tiles;  // all tiles sorted by colour
+  const int32_t* colour_ptr;    // host array, n_colours + 1
+  int n_colours;
+  const CellMeta* meta;
+  const int32_t* foreign;
+  const uint16_t* subptr;
+  const uint8_t* perm;
+  const int32_t* cell_ijk;  // per cell i, j, k (right-hand side only)
+  int k;
+  int tc;
+  int max_local;
+  double lo, dom;
+  size_t smem_bytes;
+};
+
+struct RhsDesc {
+  const double* modes;  // per mode: kappa_x, kappa_y, kappa_z, phi
+  int n_modes;          // 0: f = 1
+  double amp;
+};
+
+// dst = A src (add = 0) or dst += A src (add = 1), precision by `fp64`
+void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, int add, cudaStream_t s);
+void launch_rhs(const CellLaunch& L, const RhsDesc& f, double* dst, cudaStream_t s);
+void launch_diag(const CellLaunch& L, const double* diag_tab, double* dst, cudaStream_t s);
+// diag_tab[m * (k+1)^3 + j] = (C_m^T A_ref C_m)_{jj} for all 512 masks m
+void launch_diag_table(int k, double* diag_tab, cudaStream_t s);
+size_t cell_smem_bytes(int k, bool fp64, int tc, int max_local);
+
+// transfer between levels; fine_of/refined per coarse cell
+struct TransferLaunch {
+  int kind;  // 0 = h, 1 = p
+  int kf, kc;
+  int n_coarse;
+  const int32_t* fine_of;
+  const uint8_t* refined;
+  const int32_t* gstart_f;  // fine cells x 27
+  const uint32_t* own_f;    // fine cells
+  const int32_t* gstart_c;  // coarse cells x 27
+  const uint16_t* mask_c;   // coarse cells
+  CellLaunch coarse;        // coarse level tiles (restriction scatter)
+};
+void launch_prolongate_add(const TransferLaunch& T, bool fp64, const void* coarse, void* fine, cudaStream_t s);
+void launch_restrict_add(const TransferLaunch& T, bool fp64, const void* fine, void* coarse, cudaStream_t s);
+
+// vector kernels
+void upload_tables();
+void launch_cast(bool to64, const void* src, void* dst, int64_t n, cudaStream_t s);
+void launch_zero(bool fp64, void* x, int64_t n, cudaStream_t s);
+void launch_invert(const double* d, double* inv64, float* inv32, int64_t n, cudaStream_t s);
+void launch_cheb_init(bool fp64, void* x, void* d, const void* b, const void* dinv, double c2, int64_t n, cudaStream_t s);
+void launch_cheb_step(bool fp64, void* x, void* d, const void* b, const void* Ax, const void* dinv, double c1,
+                      double c2, int64_t n, cudaStream_t s);
+void launch_residual(bool fp64, void* r, const void* b, const void* Ax, int64_t n, cudaStream_t s);
+void launch_axpy(bool fp64, void* y, const void* x, double a, int64_t n, cudaStream_t s);
+void launch_fill(double* x, double v, int64_t n, cudaStream_t s);
+void launch_pmul(double* z, const double* a, const double* b, int64_t n, cudaStream_t s);
+// p = z + beta p (host scalar)
+void launch_xpby(double* p, const double* z, double beta, int64_t n, cudaStream_t s);
+void launch_coarse_solve(bool fp64, const double* Ainv, int n, const void* b, void* x, cudaStream_t s);
+
+// deterministic fp64 dot products: partial sums into `scratch` (DOT_BLOCKS
+// doubles), then one block combines them in fixed order
+constexpr int DOT_BLOCKS = 304;
+enum DotOp { DOT_STORE = 0, DOT_ALPHA = 1, DOT_BETA = 2 };
+void launch_dot(const double* x, const double* y, int64_t n, double* scratch, double* scal, int slot, int op,
+                cudaStream_t s);
+// CG updates with device scalars: scal[0] = rz, [1] = pq, [2] = rr, [3] = alpha, [4] = beta, [5] = rz_new
+void launch_cg_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, int64_t n,
+                         double* scratch, double* scal_out, cudaStream_t s);
+void launch_cg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t s);
+
+}  // namespace gcmg

@@ -1,0 +1,480 @@
+// Transfer kernels between two levels (Sec. 3.5, Eqs. 5-7).
+//
+// Prolongation, cell loop over the coarse cells (coarse-side identification):
+//   x_f += sum_e S_e^(f) W_e^(f) P_e^(f,c) C_e^(c) G_e^(c) x_c
+// * G^(c), C^(c): gather the coarse cell values with the hanging-node
+//   interpolation, exactly as in the operator (same tables, same mask);
+// * P_e per category (Eq. 7): geometric coarsening has two categories,
+//   "refined" (the element prolongation onto the 2k+1 nodes per direction of
+//   the eight children, a tensor product of 1D matrices) and "not refined"
+//   (identity); polynomial coarsening has one (degree k/2 -> k, 1D matrices);
+// * W^(f): every fine DoF receives equal values from all cells that share it
+//   (continuity of the coarse function), so the valence weighting is realised
+//   as owner selection: exactly one (fine cell, slot) writes each fine DoF,
+//   constrained fine DoFs are skipped.  Writes never collide: no atomics.
+// Restriction is the exact transpose (R = P^T): the owner gathers the fine
+// value, the transposed 1D matrices and C^T follow, and the coarse cells add
+// into the coarse vector through the coarse level's tiles, colour by colour.
+#include "device.cuh"
+#include "kernels.h"
+
+namespace gcmg {
+
+GCMG_DEFINE_UPLOAD(upload_tables_transfer)
+
+namespace {
+
+constexpr int TP = 8;  // coarse cells expanded at a time
+
+template <int KT, int WHICH, typename T>
+__device__ __forceinline__ T pm(int i, int a) {
+  return WHICH == 0 ? tab<T>(KT).Ph[i][a] : tab<T>(KT).Pp[i][a];
+}
+
+// apply the 1D matrix P along axis D: input extents (e0, e1, e2) with
+// e_D = NI, output extent along D = NO.  TRANS: out[a] = sum_i P[i][a] in[i]
+template <int KT, int WHICH, int NI, int NO, int D, bool TRANS, typename T>
+__device__ __forceinline__ void tsweep(const T* in, T* out, int e0, int e1, int e2, int ncells, int in_cs,
+                                       int out_cs, const uint8_t* act) {
+  const int nl = (D == 0) ? e1 * e2 : (D == 1 ? e0 * e2 : e0 * e1);
+  for (int t = threadIdx.x; t < ncells * nl; t += blockDim.x) {
+    const int cell = t / nl, r = t - cell * nl;
+    if (act && !act[cell]) continue;
+    int ib, is, ob, os;
+    if (D == 0) {
+      const int y = r % e1, z = r / e1;
+      ib = e0 * (y + e1 * z);
+      is = 1;
+      ob = NO * (y + e1 * z);
+      os = 1;
+    } else if (D == 1) {
+      const int x = r % e0, z = r / e0;
+      ib = x + e0 * e1 * z;
+      is = e0;
+      ob = x + e0 * NO * z;
+      os = e0;
+    } else {
+      const int x = r % e0, y = r / e0;
+      ib = x + e0 * y;
+      is = e0 * e1;
+      ob = ib;
+      os = is;
+    }
+    const T* pi = in + cell * in_cs + ib;
+    T* po = out + cell * out_cs + ob;
+    T v[NI];
+#pragma unroll
+    for (int a = 0; a < NI; ++a) v[a] = pi[a * is];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      T s = 0;
+#pragma unroll
+      for (int a = 0; a < NI; ++a) s += (TRANS ? pm<KT, WHICH, T>(a, o) : pm<KT, WHICH, T>(o, a)) * v[a];
+      po[o * os] = s;
+    }
+  }
+}
+
+template <typename T>
+struct TArgs {
+  int n_coarse;
+  const int32_t* fine_of;
+  const uint8_t* refined;
+  const int32_t* gstart_f;
+  const uint32_t* own_f;
+  const int32_t* gstart_c;
+  const uint16_t* mask_c;
+  const T* src;
+  T* dst;
+  // restriction: coarse tiles
+  const TileInfo* tiles;
+  const int32_t* tile_list;
+  const CellMeta* meta;
+  const int32_t* foreign;
+  const uint16_t* subptr;
+  const uint8_t* perm;
+  int tc;
+  int max_local;
+};
+
+// ---------------------------------------------------------------------------
+// geometric (h) transfer, degree K on both levels
+// ---------------------------------------------------------------------------
+template <int K, typename T>
+__global__ void __launch_bounds__(BLOCK) prolong_h(TArgs<T> A) {
+  constexpr int N = K + 1, N3 = N * N * N, M = 2 * K + 1, M3 = M * M * M;
+  constexpr int S1 = M * N * N, S2 = M * M * N;
+  __shared__ uint16_t sm_mask[TP];
+  __shared__ uint8_t sm_ref[TP];
+  __shared__ int32_t sm_fine[TP];
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* cb = reinterpret_cast<T*>(smem);
+  T* e1 = cb + TP * N3;
+  T* e2 = e1 + TP * S1;
+  T* e3 = e2 + TP * S2;
+  const int c0 = blockIdx.x * TP;
+  const int nc = min(TP, A.n_coarse - c0);
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    sm_mask[c] = A.mask_c[c0 + c];
+    sm_ref[c] = A.refined[c0 + c];
+    sm_fine[c] = A.fine_of[c0 + c];
+  }
+  for (int t = threadIdx.x; t < nc * N3; t += blockDim.x) {
+    const int cell = t / N3, n = t - cell * N3;
+    int slot, off;
+    node_slot<K>(n % N, (n / N) % N, n / (N * N), slot, off);
+    const int32_t g = A.gstart_c[(size_t)(c0 + cell) * NSLOT + slot];
+    cb[t] = g < 0 ? T(0) : A.src[g + off];
+  }
+  __syncthreads();
+  hanging_all<K, false>(cb, sm_mask, nc);
+  tsweep<K, 0, N, M, 0, false>(cb, e1, N, N, N, nc, N3, S1, sm_ref);
+  __syncthreads();
+  tsweep<K, 0, N, M, 1, false>(e1, e2, M, N, N, nc, S1, S2, sm_ref);
+  __syncthreads();
+  tsweep<K, 0, N, M, 2, false>(e2, e3, M, M, N, nc, S2, M3, sm_ref);
+  __syncthreads();
+  for (int t = threadIdx.x; t < nc * 8 * N3; t += blockDim.x) {
+    const int cell = t / (8 * N3), r = t - cell * 8 * N3;
+    const int q = r / N3, n = r - q * N3;
+    const int a = n % N, b = (n / N) % N, c = n / (N * N);
+    T val;
+    int f;
+    if (sm_ref[cell]) {
+      f = sm_fine[cell] + q;
+      const int gi = (q & 1) * K + a, gj = ((q >> 1) & 1) * K + b, gk = (q >> 2) * K + c;
+      val = e3[cell * M3 + gi + M * (gj + M * gk)];
+    } else {
+      if (q) continue;
+      f = sm_fine[cell];
+      val = cb[cell * N3 + n];
+    }
+    int slot, off;
+    node_slot<K>(a, b, c, slot, off);
+    if ((A.own_f[f] >> slot) & 1u) {
+      const int32_t g = A.gstart_f[(size_t)f * NSLOT + slot];
+      A.dst[g + off] += val;
+    }
+  }
+}
+
+// shared part of the restriction kernels: C^T, scatter into the coarse
+// tile's accumulator by sub-colour, add into the coarse vector
+template <int KC, typename T>
+__device__ __forceinline__ void restrict_finish(const TArgs<T>& A, const TileInfo& ti, const CellMeta* sm_meta,
+                                                const uint16_t* sm_mask, T* cb, T* ys) {
+  constexpr int N = KC + 1, N2 = N * N, N3 = N2 * N;
+  hanging_all<KC, true>(cb, sm_mask, ti.n_cells);
+  for (int s = 0; s < ti.n_sub; ++s) {
+    const int q0 = A.subptr[ti.sub_begin + s], q1 = A.subptr[ti.sub_begin + s + 1];
+    for (int t = threadIdx.x; t < (q1 - q0) * N2; t += blockDim.x) {
+      const int q = q0 + t / N2, r = t % N2;
+      const int cell = A.perm[ti.cell_begin + q];
+      const int b = r % N, c = r / N;
+      const uint16_t* ls = sm_meta[cell].ls;
+      const T* in = cb + cell * N3 + N * r;
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        int slot, off;
+        node_slot<KC>(a, b, c, slot, off);
+        const uint16_t l = ls[slot];
+        if (l != LS_NONE) ys[l + off] += in[a];
+      }
+    }
+    __syncthreads();
+  }
+  T* dst = A.dst + ti.dof_begin;
+  for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) dst[i] += ys[i];
+  const int32_t* fl = A.foreign + ti.foreign_begin;
+  for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) A.dst[fl[i]] += ys[ti.n_owned + i];
+}
+
+template <int K, typename T>
+__global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
+  constexpr int N = K + 1, N3 = N * N * N, M = 2 * K + 1, M3 = M * M * M;
+  constexpr int S1 = M * N * N, S2 = M * M * N;
+  __shared__ uint8_t sm_ref[256];
+  __shared__ int32_t sm_fine[256];
+  __shared__ uint16_t sm_mask[256];
+  extern __shared__ __align__(16) unsigned char smem[];
+  CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem);
+  T* cb = reinterpret_cast<T*>(smem + (size_t)A.tc * sizeof(CellMeta));
+  T* e1 = cb + A.tc * N3;
+  T* e2 = e1 + TP * S1;
+  T* e3 = e2 + TP * S2;
+  T* ys = e3 + TP * M3;
+  const TileInfo ti = A.tiles[A.tile_list[blockIdx.x]];
+  const int nc = ti.n_cells;
+  {
+    const uint4* g = reinterpret_cast<const uint4*>(A.meta + ti.cell_begin);
+    uint4* s = reinterpret_cast<uint4*>(sm_meta);
+    for (int i = threadIdx.x; i < nc * 4; i += blockDim.x) s[i] = g[i];
+  }
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    sm_ref[c] = A.refined[ti.cell_begin + c];
+    sm_fine[c] = A.fine_of[ti.cell_begin + c];
+    sm_mask[c] = A.mask_c[ti.cell_begin + c];
+  }
+  for (int i = threadIdx.x; i < ti.n_owned + ti.n_foreign; i += blockDim.x) ys[i] = T(0);
+  for (int i = threadIdx.x; i < nc * N3; i += blockDim.x) cb[i] = T(0);
+  __syncthreads();
+  for (int c0 = 0; c0 < nc; c0 += TP) {
+    const int np = min(TP, nc - c0);
+    for (int i = threadIdx.x; i < np * M3; i += blockDim.x) e3[i] = T(0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < np * 8 * N3; t += blockDim.x) {
+      const int cl = t / (8 * N3), r = t - cl * 8 * N3;
+      const int cell = c0 + cl;
+      const int q = r / N3, n = r - q * N3;
+      const int a = n % N, b = (n / N) % N, c = n / (N * N);
+      int f;
+      if (sm_ref[cell])
+        f = sm_fine[cell] + q;
+      else if (q == 0)
+        f = sm_fine[cell];
+      else
+        continue;
+      int slot, off;
+      node_slot<K>(a, b, c, slot, off);
+      if (!((A.own_f[f] >> slot) & 1u)) continue;
+      const T val = A.src[A.gstart_f[(size_t)f * NSLOT + slot] + off];
+      if (sm_ref[cell]) {
+        const int gi = (q & 1) * K + a, gj = ((q >> 1) & 1) * K + b, gk = (q >> 2) * K + c;
+        e3[cl * M3 + gi + M * (gj + M * gk)] = val;
+      } else {
+        cb[cell * N3 + n] = val;
+      }
+    }
+    __syncthreads();
+    const uint8_t* act = sm_ref + c0;
+    tsweep<K, 0, M, N, 2, true>(e3, e2, M, M, M, np, M3, S2, act);
+    __syncthreads();
+    tsweep<K, 0, M, N, 1, true>(e2, e1, M, M, N, np, S2, S1, act);
+    __syncthreads();
+    tsweep<K, 0, M, N, 0, true>(e1, cb + c0 * N3, M, N, N, np, S1, N3, act);
+    __syncthreads();
+  }
+  restrict_finish<K>(A, ti, sm_meta, sm_mask, cb, ys);
+}
+
+// ---------------------------------------------------------------------------
+// polynomial (p) transfer on one mesh, degree KF -> KC = KF / 2
+// ---------------------------------------------------------------------------
+template <int KF, typename T>
+__global__ void __launch_bounds__(BLOCK) prolong_p(TArgs<T> A) {
+  constexpr int KC = KF / 2, NF = KF + 1, NC = KC + 1;
+  constexpr int NC3 = NC * NC * NC, NF3 = NF * NF * NF, S1 = NF * NC * NC, S2 = NF * NF * NC;
+  __shared__ uint16_t sm_mask[TP];
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* cb = reinterpret_cast<T*>(smem);
+  T* e1 = cb + TP * NC3;
+  T* e2 = e1 + TP * S1;
+  T* e3 = e2 + TP * S2;
+  const int c0 = blockIdx.x * TP;
+  const int nc = min(TP, A.n_coarse - c0);
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) sm_mask[c] = A.mask_c[c0 + c];
+  for (int t = threadIdx.x; t < nc * NC3; t += blockDim.x) {
+    const int cell = t / NC3, n = t - cell * NC3;
+    int slot, off;
+    node_slot<KC>(n % NC, (n / NC) % NC, n / (NC * NC), slot, off);
+    const int32_t g = A.gstart_c[(size_t)(c0 + cell) * NSLOT + slot];
+    cb[t] = g < 0 ? T(0) : A.src[g + off];
+  }
+  __syncthreads();
+  hanging_all<KC, false>(cb, sm_mask, nc);
+  tsweep<KF, 1, NC, NF, 0, false>(cb, e1, NC, NC, NC, nc, NC3, S1, nullptr);
+  __syncthreads();
+  tsweep<KF, 1, NC, NF, 1, false>(e1, e2, NF, NC, NC, nc, S1, S2, nullptr);
+  __syncthreads();
+  tsweep<KF, 1, NC, NF, 2, false>(e2, e3, NF, NF, NC, nc, S2, NF3, nullptr);
+  __syncthreads();
+  for (int t = threadIdx.x; t < nc * NF3; t += blockDim.x) {
+    const int cell = t / NF3, n = t - cell * NF3;
+    const int f = c0 + cell;
+    int slot, off;
+    node_slot<KF>(n % NF, (n / NF) % NF, n / (NF * NF), slot, off);
+    if ((A.own_f[f] >> slot) & 1u) A.dst[A.gstart_f[(size_t)f * NSLOT + slot] + off] += e3[t];
+  }
+}
+
+template <int KF, typename T>
+__global__ void __launch_bounds__(BLOCK) restrict_p(TArgs<T> A) {
+  constexpr int KC = KF / 2, NF = KF + 1, NC = KC + 1;
+  constexpr int NC3 = NC * NC * NC, NF3 = NF * NF * NF, S1 = NF * NC * NC, S2 = NF * NF * NC;
+  __shared__ uint16_t sm_mask[256];
+  extern __shared__ __align__(16) unsigned char smem[];
+  CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem);
+  T* cb = reinterpret_cast<T*>(smem + (size_t)A.tc * sizeof(CellMeta));
+  T* e1 = cb + A.tc * NC3;
+  T* e2 = e1 + TP * S1;
+  T* e3 = e2 + TP * S2;
+  T* ys = e3 + TP * NF3;
+  const TileInfo ti = A.tiles[A.tile_list[blockIdx.x]];
+  const int nc = ti.n_cells;
+  {
+    const uint4* g = reinterpret_cast<const uint4*>(A.meta + ti.cell_begin);
+    uint4* s = reinterpret_cast<uint4*>(sm_meta);
+    for (int i = threadIdx.x; i < nc * 4; i += blockDim.x) s[i] = g[i];
+  }
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) sm_mask[c] = A.mask_c[ti.cell_begin + c];
+  for (int i = threadIdx.x; i < ti.n_owned + ti.n_foreign; i += blockDim.x) ys[i] = T(0);
+  __syncthreads();
+  for (int c0 = 0; c0 < nc; c0 += TP) {
+    const int np = min(TP, nc - c0);
+    for (int t = threadIdx.x; t < np * NF3; t += blockDim.x) {
+      const int cl = t / NF3, n = t - cl * NF3;
+      const int f = ti.cell_begin + c0 + cl;
+      int slot, off;
+      node_slot<KF>(n % NF, (n / NF) % NF, n / (NF * NF), slot, off);
+      e3[t] = ((A.own_f[f] >> slot) & 1u) ? A.src[A.gstart_f[(size_t)f * NSLOT + slot] + off] : T(0);
+    }
+    __syncthreads();
+    tsweep<KF, 1, NF, NC, 2, true>(e3, e2, NF, NF, NF, np, NF3, S2, nullptr);
+    __syncthreads();
+    tsweep<KF, 1, NF, NC, 1, true>(e2, e1, NF, NF, NC, np, S2, S1, nullptr);
+    __syncthreads();
+    tsweep<KF, 1, NF, NC, 0, true>(e1, cb + c0 * NC3, NF, NC, NC, np, S1, NC3, nullptr);
+    __syncthreads();
+  }
+  restrict_finish<KC>(A, ti, sm_meta, sm_mask, cb, ys);
+}
+
+template <typename T>
+TArgs<T> targs(const TransferLaunch& L) {
+  TArgs<T> A{};
+  A.n_coarse = L.n_coarse;
+  A.fine_of = L.fine_of;
+  A.refined = L.refined;
+  A.gstart_f = L.gstart_f;
+  A.own_f = L.own_f;
+  A.gstart_c = L.gstart_c;
+  A.mask_c = L.mask_c;
+  A.tiles = L.coarse.tiles;
+  A.meta = L.coarse.meta;
+  A.foreign = L.coarse.foreign;
+  A.subptr = L.coarse.subptr;
+  A.perm = L.coarse.perm;
+  A.tc = L.coarse.tc;
+  A.max_local = L.coarse.max_local;
+  return A;
+}
+
+template <typename K_>
+void set_smem(K_ kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int K, typename T>
+void prolong_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
+  constexpr int N = K + 1, M = 2 * K + 1;
+  const size_t sm = (size_t)TP * (N * N * N + M * N * N + M * M * N + M * M * M) * sizeof(T);
+  set_smem(prolong_h<K, T>, sm);
+  TArgs<T> A = targs<T>(L);
+  A.src = src;
+  A.dst = dst;
+  const int nb = (L.n_coarse + TP - 1) / TP;
+  prolong_h<K, T><<<nb, BLOCK, sm, s>>>(A);
+}
+
+template <int K, typename T>
+void restrict_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
+  constexpr int N = K + 1, M = 2 * K + 1;
+  const size_t sm = (size_t)L.coarse.tc * sizeof(CellMeta) +
+                    ((size_t)L.coarse.tc * N * N * N + TP * (M * N * N + M * M * N + M * M * M) + L.coarse.max_local) *
+                        sizeof(T);
+  set_smem(restrict_h<K, T>, sm);
+  TArgs<T> A = targs<T>(L);
+  A.src = src;
+  A.dst = dst;
+  for (int c = 0; c < L.coarse.n_colours; ++c) {
+    const int n = L.coarse.colour_ptr[c + 1] - L.coarse.colour_ptr[c];
+    if (!n) continue;
+    A.tile_list = L.coarse.colour_tiles + L.coarse.colour_ptr[c];
+    restrict_h<K, T><<<n, BLOCK, sm, s>>>(A);
+  }
+}
+
+template <int KF, typename T>
+void prolong_p_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
+  constexpr int NF = KF + 1, NC = KF / 2 + 1;
+  const size_t sm = (size_t)TP * (NC * NC * NC + NF * NC * NC + NF * NF * NC + NF * NF * NF) * sizeof(T);
+  set_smem(prolong_p<KF, T>, sm);
+  TArgs<T> A = targs<T>(L);
+  A.src = src;
+  A.dst = dst;
+  const int nb = (L.n_coarse + TP - 1) / TP;
+  prolong_p<KF, T><<<nb, BLOCK, sm, s>>>(A);
+}
+
+template <int KF, typename T>
+void restrict_p_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
+  constexpr int NF = KF + 1, NC = KF / 2 + 1;
+  const size_t sm = (size_t)L.coarse.tc * sizeof(CellMeta) +
+                    ((size_t)L.coarse.tc * NC * NC * NC + TP * (NF * NC * NC + NF * NF * NC + NF * NF * NF) +
+                     L.coarse.max_local) *
+                        sizeof(T);
+  set_smem(restrict_p<KF, T>, sm);
+  TArgs<T> A = targs<T>(L);
+  A.src = src;
+  A.dst = dst;
+  for (int c = 0; c < L.coarse.n_colours; ++c) {
+    const int n = L.coarse.colour_ptr[c + 1] - L.coarse.colour_ptr[c];
+    if (!n) continue;
+    A.tile_list = L.coarse.colour_tiles + L.coarse.colour_ptr[c];
+    restrict_p<KF, T><<<n, BLOCK, sm, s>>>(A);
+  }
+}
+
+template <typename T>
+void prolong_any(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
+  if (L.kind == 0) {
+    switch (L.kf) {
+      case 1: prolong_h_run<1>(L, src, dst, s); break;
+      case 2: prolong_h_run<2>(L, src, dst, s); break;
+      case 3: prolong_h_run<3>(L, src, dst, s); break;
+      case 4: prolong_h_run<4>(L, src, dst, s); break;
+    }
+  } else {
+    switch (L.kf) {
+      case 2: prolong_p_run<2>(L, src, dst, s); break;
+      case 3: prolong_p_run<3>(L, src, dst, s); break;
+      case 4: prolong_p_run<4>(L, src, dst, s); break;
+    }
+  }
+}
+
+template <typename T>
+void restrict_any(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
+  if (L.kind == 0) {
+    switch (L.kf) {
+      case 1: restrict_h_run<1>(L, src, dst, s); break;
+      case 2: restrict_h_run<2>(L, src, dst, s); break;
+      case 3: restrict_h_run<3>(L, src, dst, s); break;
+      case 4: restrict_h_run<4>(L, src, dst, s); break;
+    }
+  } else {
+    switch (L.kf) {
+      case 2: restrict_p_run<2>(L, src, dst, s); break;
+      case 3: restrict_p_run<3>(L, src, dst, s); break;
+      case 4: restrict_p_run<4>(L, src, dst, s); break;
+    }
+  }
+}
+
+}  // namespace
+
+void launch_prolongate_add(const TransferLaunch& L, bool fp64, const void* coarse, void* fine, cudaStream_t s) {
+  if (fp64)
+    prolong_any<double>(L, static_cast<const double*>(coarse), static_cast<double*>(fine), s);
+  else
+    prolong_any<float>(L, static_cast<const float*>(coarse), static_cast<float*>(fine), s);
+}
+
+void launch_restrict_add(const TransferLaunch& L, bool fp64, const void* fine, void* coarse, cudaStream_t s) {
+  if (fp64)
+    restrict_any<double>(L, static_cast<const double*>(fine), static_cast<double*>(coarse), s);
+  else
+    restrict_any<float>(L, static_cast<const float*>(fine), static_cast<float*>(coarse), s);
+}
+
+}  // namespace gcmg

@@ -1,0 +1,275 @@
+// Vector kernels of the smoother, the V-cycle and CG.
+//
+// * Chebyshev iteration around point Jacobi (Sec. 3.3): one fused pass per
+//   step, d <- c1 d + c2 D^{-1} (b - A x), x <- x + d (c1 = 0 starts the
+//   recurrence).  Reads b, Ax, D^{-1}, d, x and writes d, x.
+// * Algorithm 1: casts between the fp64 CG vectors and the fp32 levels.
+// * Sec. 3.4: the level-0 solve is a dense product with the inverse of the
+//   (small, fp64) level-0 matrix.
+// * CG (Sec. 2): fp64 inner products, reduced deterministically in two
+//   stages (fixed grid, fixed order), scalars kept on the device.
+#include "device.cuh"
+#include "kernels.h"
+
+namespace gcmg {
+
+namespace {
+
+inline int grid_for(int64_t n) {
+  int64_t g = (n + BLOCK - 1) / BLOCK;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)std::max<int64_t>(g, 1);
+}
+
+template <typename A, typename B>
+__global__ void cast_kernel(const A* src, B* dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (B)src[i];
+}
+
+template <typename T>
+__global__ void zero_kernel(T* x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = T(0);
+}
+
+__global__ void invert_kernel(const double* d, double* i64, float* i32, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = 1.0 / d[i];
+    if (i64) i64[i] = v;
+    if (i32) i32[i] = (float)v;
+  }
+}
+
+template <typename T>
+__global__ void cheb_init_kernel(T* x, T* d, const T* b, const T* dinv, T c2, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T v = c2 * dinv[i] * b[i];
+    d[i] = v;
+    x[i] = v;
+  }
+}
+
+template <typename T, bool FIRST>
+__global__ void cheb_step_kernel(T* x, T* d, const T* b, const T* Ax, const T* dinv, T c1, T c2, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T r = b[i] - Ax[i];
+    const T v = FIRST ? c2 * dinv[i] * r : c1 * d[i] + c2 * dinv[i] * r;
+    d[i] = v;
+    x[i] += v;
+  }
+}
+
+template <typename T>
+__global__ void residual_kernel(T* r, const T* b, const T* Ax, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = b[i] - Ax[i];
+}
+
+template <typename T>
+__global__ void axpy_kernel(T* y, const T* x, T a, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+
+template <typename T>
+__global__ void coarse_kernel(const double* Ainv, int n, const T* b, T* x) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += Ainv[(size_t)i * n + j] * (double)b[j];
+    x[i] = (T)s;
+  }
+}
+
+// block sum in a fixed order (tree over the block)
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = BLOCK / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// each block sums a fixed contiguous chunk: the result does not depend on
+// scheduling
+__global__ void __launch_bounds__(BLOCK) dot_partial(const double* x, const double* y, int64_t n, double* part) {
+  __shared__ double sh[BLOCK];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  double s = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += BLOCK) s += x[i] * y[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(BLOCK) dot_final(const double* part, int np, double* scal, int slot, int op) {
+  __shared__ double sh[BLOCK];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += BLOCK) s += part[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    if (op == DOT_STORE) {
+      scal[slot] = s;
+    } else if (op == DOT_ALPHA) {  // pq, alpha = rz / pq
+      scal[1] = s;
+      scal[3] = scal[0] / s;
+    } else {  // rz_new, beta = rz_new / rz, rz <- rz_new
+      scal[5] = s;
+      scal[4] = s / scal[0];
+      scal[0] = s;
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q, partial sums of r.r
+__global__ void __launch_bounds__(BLOCK) cg_xr_kernel(double* x, double* r, const double* p, const double* q,
+                                                      const double* scal, int64_t n, double* part) {
+  __shared__ double sh[BLOCK];
+  const double alpha = scal[3];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  double s = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += BLOCK) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    s += ri * ri;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void cg_p_kernel(double* p, const double* z, const double* scal, int64_t n) {
+  const double beta = scal[4];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+__global__ void fill_kernel(double* x, double v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+__global__ void pmul_kernel(double* z, const double* a, const double* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] = a[i] * b[i];
+}
+
+__global__ void xpby_kernel(double* p, const double* z, double beta, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+}  // namespace
+
+void launch_fill(double* x, double v, int64_t n, cudaStream_t s) {
+  if (n > 0) fill_kernel<<<grid_for(n), BLOCK, 0, s>>>(x, v, n);
+}
+
+void launch_pmul(double* z, const double* a, const double* b, int64_t n, cudaStream_t s) {
+  if (n > 0) pmul_kernel<<<grid_for(n), BLOCK, 0, s>>>(z, a, b, n);
+}
+
+void launch_xpby(double* p, const double* z, double beta, int64_t n, cudaStream_t s) {
+  if (n > 0) xpby_kernel<<<grid_for(n), BLOCK, 0, s>>>(p, z, beta, n);
+}
+
+void launch_cast(bool to64, const void* src, void* dst, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  if (to64)
+    cast_kernel<float, double><<<grid_for(n), BLOCK, 0, s>>>(static_cast<const float*>(src), static_cast<double*>(dst), n);
+  else
+    cast_kernel<double, float><<<grid_for(n), BLOCK, 0, s>>>(static_cast<const double*>(src), static_cast<float*>(dst), n);
+}
+
+void launch_zero(bool fp64, void* x, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  if (fp64)
+    zero_kernel<double><<<grid_for(n), BLOCK, 0, s>>>(static_cast<double*>(x), n);
+  else
+    zero_kernel<float><<<grid_for(n), BLOCK, 0, s>>>(static_cast<float*>(x), n);
+}
+
+void launch_invert(const double* d, double* inv64, float* inv32, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  invert_kernel<<<grid_for(n), BLOCK, 0, s>>>(d, inv64, inv32, n);
+}
+
+void launch_cheb_init(bool fp64, void* x, void* d, const void* b, const void* dinv, double c2, int64_t n,
+                      cudaStream_t s) {
+  if (n <= 0) return;
+  if (fp64)
+    cheb_init_kernel<double><<<grid_for(n), BLOCK, 0, s>>>((double*)x, (double*)d, (const double*)b,
+                                                            (const double*)dinv, c2, n);
+  else
+    cheb_init_kernel<float><<<grid_for(n), BLOCK, 0, s>>>((float*)x, (float*)d, (const float*)b, (const float*)dinv,
+                                                           (float)c2, n);
+}
+
+void launch_cheb_step(bool fp64, void* x, void* d, const void* b, const void* Ax, const void* dinv, double c1,
+                      double c2, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  const bool first = (c1 == 0.0);
+  if (fp64) {
+    if (first)
+      cheb_step_kernel<double, true><<<grid_for(n), BLOCK, 0, s>>>((double*)x, (double*)d, (const double*)b,
+                                                                   (const double*)Ax, (const double*)dinv, c1, c2, n);
+    else
+      cheb_step_kernel<double, false><<<grid_for(n), BLOCK, 0, s>>>((double*)x, (double*)d, (const double*)b,
+                                                                    (const double*)Ax, (const double*)dinv, c1, c2, n);
+  } else {
+    if (first)
+      cheb_step_kernel<float, true><<<grid_for(n), BLOCK, 0, s>>>((float*)x, (float*)d, (const float*)b,
+                                                                  (const float*)Ax, (const float*)dinv, (float)c1,
+                                                                  (float)c2, n);
+    else
+      cheb_step_kernel<float, false><<<grid_for(n), BLOCK, 0, s>>>((float*)x, (float*)d, (const float*)b,
+                                                                   (const float*)Ax, (const float*)dinv, (float)c1,
+                                                                   (float)c2, n);
+  }
+}
+
+void launch_residual(bool fp64, void* r, const void* b, const void* Ax, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  if (fp64)
+    residual_kernel<double><<<grid_for(n), BLOCK, 0, s>>>((double*)r, (const double*)b, (const double*)Ax, n);
+  else
+    residual_kernel<float><<<grid_for(n), BLOCK, 0, s>>>((float*)r, (const float*)b, (const float*)Ax, n);
+}
+
+void launch_axpy(bool fp64, void* y, const void* x, double a, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  if (fp64)
+    axpy_kernel<double><<<grid_for(n), BLOCK, 0, s>>>((double*)y, (const double*)x, a, n);
+  else
+    axpy_kernel<float><<<grid_for(n), BLOCK, 0, s>>>((float*)y, (const float*)x, (float)a, n);
+}
+
+void launch_coarse_solve(bool fp64, const double* Ainv, int n, const void* b, void* x, cudaStream_t s) {
+  if (n <= 0) return;
+  if (fp64)
+    coarse_kernel<double><<<1, BLOCK, 0, s>>>(Ainv, n, (const double*)b, (double*)x);
+  else
+    coarse_kernel<float><<<1, BLOCK, 0, s>>>(Ainv, n, (const float*)b, (float*)x);
+}
+
+void launch_dot(const double* x, const double* y, int64_t n, double* scratch, double* scal, int slot, int op,
+                cudaStream_t s) {
+  dot_partial<<<DOT_BLOCKS, BLOCK, 0, s>>>(x, y, n, scratch);
+  dot_final<<<1, BLOCK, 0, s>>>(scratch, DOT_BLOCKS, scal, slot, op);
+}
+
+void launch_cg_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, int64_t n,
+                         double* scratch, double* scal_out, cudaStream_t s) {
+  cg_xr_kernel<<<DOT_BLOCKS, BLOCK, 0, s>>>(x, r, p, q, scal, n, scratch);
+  dot_final<<<1, BLOCK, 0, s>>>(scratch, DOT_BLOCKS, scal_out, 2, DOT_STORE);
+}
+
+void launch_cg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  cg_p_kernel<<<grid_for(n), BLOCK, 0, s>>>(p, z, scal, n);
+}
+
+}  // namespace gcmg

@@ -1,0 +1,408 @@
+// DoF numbering and cell/tile metadata of one multigrid level (host set-up).
+//
+// Sec. 3.1-3.2: constraints (Dirichlet and hanging nodes) are applied while
+// the cell values are set up; following the special-purpose algorithm the
+// paper uses, the DoF map G_e of a cell with a hanging face or edge points to
+// the DoFs of the constraining (coarse) face or edge, and the cell kernel
+// interpolates in place (Sec. 3.2, hanging-node application).
+//
+// Layout chosen for one GPU:
+// * DoFs live on the 27 geometric entities of a hexahedron (8 vertices,
+//   12 edges, 6 faces, interior; 1, k-1, (k-1)^2, (k-1)^3 DoFs).  The DoFs of
+//   one entity are contiguous, so a cell is described by 27 entity starts.
+//   Dirichlet entities carry no DoFs (vectors hold free DoFs only).
+// * Cells are in Morton order and grouped into tiles of `tile_cells`
+//   consecutive cells.  Tiles that share an entity get different colours;
+//   each entity is owned by the touching tile of the lowest colour and the
+//   DoFs owned by one tile are numbered contiguously.  A cell kernel launched
+//   colour by colour can then write its owned DoFs with plain stores and add
+//   into the foreign ones without atomics (deterministic results).
+// * Inside a tile, cells that share an entity get different sub-colours; the
+//   shared-memory accumulation runs sub-colour by sub-colour.
+#include <algorithm>
+#include <stdexcept>
+
+#include "internal.h"
+
+namespace gcmg {
+
+namespace {
+
+constexpr uint64_t NO_ENTITY = ~0ull;
+
+inline uint64_t ekey(int type, int dir, int logs, uint32_t x, uint32_t y, uint32_t z) {
+  return ((uint64_t)type << 61) | ((uint64_t)dir << 59) | ((uint64_t)logs << 54) | ((uint64_t)x << 36) |
+         ((uint64_t)y << 18) | (uint64_t)z;
+}
+
+struct EntityGeom {
+  int32_t corner[3];
+  int32_t size;
+  uint8_t cls[3];
+};
+
+int ipow(int b, int e) {
+  int r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+}  // namespace
+
+static uint16_t cell_mask(const Octree& mesh, const Cell& c) {
+  if (c.l == 0) return 0;
+  const int idx[3] = {c.i, c.j, c.k};
+  const int p[3] = {c.i & 1, c.j & 1, c.k & 1};
+  const int n = 1 << c.l;
+  uint16_t m = (uint16_t)(p[0] | (p[1] << 1) | (p[2] << 2));
+  auto coarser = [&](const int* q) {
+    for (int d = 0; d < 3; ++d)
+      if (q[d] < 0 || q[d] >= n) return false;
+    int lv = mesh.leaf_level(c.l, q[0], q[1], q[2]);
+    return lv >= 0 && lv < c.l;
+  };
+  for (int d = 0; d < 3; ++d) {
+    int q[3] = {idx[0], idx[1], idx[2]};
+    q[d] += p[d] ? 1 : -1;
+    if (coarser(q)) m |= (uint16_t)(1u << (3 + d));
+  }
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    const int s1 = p[t1] ? 1 : -1, s2 = p[t2] ? 1 : -1;
+    int qa[3] = {idx[0], idx[1], idx[2]}, qb[3] = {idx[0], idx[1], idx[2]}, qc[3] = {idx[0], idx[1], idx[2]};
+    qa[t1] += s1;
+    qb[t2] += s2;
+    qc[t1] += s1;
+    qc[t2] += s2;
+    if (coarser(qa) || coarser(qb) || coarser(qc)) m |= (uint16_t)(1u << (6 + d));
+  }
+  return m;
+}
+
+// is slot (cx,cy,cz) on a hanging face or hanging edge of a cell with mask m?
+static bool slot_hanging(uint16_t m, const int* cl) {
+  const int p[3] = {m & 1, (m >> 1) & 1, (m >> 2) & 1};
+  for (int d = 0; d < 3; ++d)
+    if ((m >> (3 + d)) & 1)
+      if (cl[d] == 2 * p[d]) return true;
+  for (int d = 0; d < 3; ++d)
+    if ((m >> (6 + d)) & 1) {
+      const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+      if (cl[t1] == 2 * p[t1] && cl[t2] == 2 * p[t2]) return true;
+    }
+  return false;
+}
+
+void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L) {
+  if (LM > 17) throw std::runtime_error("mesh too deep (max level 17)");
+  L.k = k;
+  L.lo = mesh.lo;
+  L.hi = mesh.hi;
+  L.lmax_lattice = LM;
+  L.tile_cells = tile_cells;
+  L.cells = mesh.leaves_morton();
+  const int nc = (int)L.cells.size();
+  const int top = 1 << LM;
+  L.mask.assign(nc, 0);
+
+  // entity of every slot
+  std::vector<int32_t> eid((size_t)nc * NSLOT, -1);
+  std::vector<uint8_t> hang_slot((size_t)nc * NSLOT, 0);
+  std::unordered_map<uint64_t, int32_t> emap;
+  emap.reserve((size_t)nc * 8);
+  std::vector<int32_t> endofs;
+  std::vector<EntityGeom> egeom;
+  for (int ci = 0; ci < nc; ++ci) {
+    const Cell& c = L.cells[ci];
+    const uint16_t m = cell_mask(mesh, c);
+    L.mask[ci] = m;
+    const int idx[3] = {c.i, c.j, c.k};
+    for (int s = 0; s < NSLOT; ++s) {
+      const int cl[3] = {s % 3, (s / 3) % 3, s / 9};
+      const bool hang = slot_hanging(m, cl);
+      int X[3], size, logs;
+      if (hang) {
+        logs = LM - c.l + 1;
+        size = 1 << logs;
+        for (int d = 0; d < 3; ++d) X[d] = (idx[d] >> 1) << logs;
+      } else {
+        logs = LM - c.l;
+        size = 1 << logs;
+        for (int d = 0; d < 3; ++d) X[d] = idx[d] << logs;
+      }
+      int corner[3], ndim = 0, dir = 0;
+      bool bnd = false;
+      for (int d = 0; d < 3; ++d) {
+        corner[d] = X[d] + (cl[d] == 2 ? size : 0);
+        if (cl[d] == 1) ++ndim;
+        else if (corner[d] == 0 || corner[d] == top) bnd = true;
+      }
+      if (ndim == 1) {
+        for (int d = 0; d < 3; ++d)
+          if (cl[d] == 1) dir = d;
+      } else if (ndim == 2) {
+        for (int d = 0; d < 3; ++d)
+          if (cl[d] != 1) dir = d;
+      }
+      hang_slot[(size_t)ci * NSLOT + s] = hang;
+      const int nd = ipow(k - 1, ndim);
+      if (bnd || nd == 0) continue;
+      const uint64_t key = ekey(ndim, dir, ndim == 0 ? 0 : logs, corner[0], corner[1], corner[2]);
+      auto it = emap.find(key);
+      int32_t e;
+      if (it == emap.end()) {
+        e = (int32_t)endofs.size();
+        emap.emplace(key, e);
+        endofs.push_back(nd);
+        EntityGeom g;
+        for (int d = 0; d < 3; ++d) {
+          g.corner[d] = corner[d];
+          g.cls[d] = (uint8_t)cl[d];
+        }
+        g.size = size;
+        egeom.push_back(g);
+      } else {
+        e = it->second;
+      }
+      eid[(size_t)ci * NSLOT + s] = e;
+    }
+  }
+  const int ne = (int)endofs.size();
+
+  // tiles and their colours
+  const int nt = (nc + tile_cells - 1) / tile_cells;
+  std::vector<std::vector<int32_t>> etiles(ne);
+  for (int t = 0; t < nt; ++t) {
+    const int c0 = t * tile_cells, c1 = std::min(nc, c0 + tile_cells);
+    for (int ci = c0; ci < c1; ++ci)
+      for (int s = 0; s < NSLOT; ++s) {
+        int32_t e = eid[(size_t)ci * NSLOT + s];
+        if (e < 0) continue;
+        auto& v = etiles[e];
+        if (v.empty() || v.back() != t) v.push_back(t);
+      }
+  }
+  std::vector<int32_t> colour(nt, -1);
+  {
+    std::vector<std::vector<int32_t>> adj(nt);
+    for (int e = 0; e < ne; ++e) {
+      auto& v = etiles[e];
+      for (size_t a = 0; a < v.size(); ++a)
+        for (size_t b = a + 1; b < v.size(); ++b) {
+          adj[v[a]].push_back(v[b]);
+          adj[v[b]].push_back(v[a]);
+        }
+    }
+    std::vector<int32_t> used;
+    for (int t = 0; t < nt; ++t) {
+      used.clear();
+      for (int32_t u : adj[t])
+        if (colour[u] >= 0) used.push_back(colour[u]);
+      std::sort(used.begin(), used.end());
+      int c = 0;
+      for (int32_t u : used) {
+        if (u == c) ++c;
+        else if (u > c) break;
+      }
+      colour[t] = c;
+    }
+  }
+  L.n_colours = 0;
+  for (int t = 0; t < nt; ++t) L.n_colours = std::max(L.n_colours, colour[t] + 1);
+  // owner tile of every entity: the touching tile of the lowest colour
+  std::vector<int32_t> owner(ne, -1);
+  for (int e = 0; e < ne; ++e) {
+    int best = -1;
+    for (int32_t t : etiles[e])
+      if (best < 0 || colour[t] < colour[best] || (colour[t] == colour[best] && t < best)) best = t;
+    owner[e] = best;
+  }
+  // DoF numbering: tile by tile, the entities each tile owns
+  std::vector<int32_t> estart(ne, -1);
+  int64_t next = 0;
+  L.tiles.assign(nt, TileInfo{});
+  L.meta.assign(nc, CellMeta{});
+  L.foreign.clear();
+  L.subptr.clear();
+  L.perm.assign(nc, 0);
+  L.max_local = 0;
+  L.max_sub = 0;
+  std::vector<int32_t> lstart_of(ne, -1);
+  for (int t = 0; t < nt; ++t) {
+    const int c0 = t * tile_cells, c1 = std::min(nc, c0 + tile_cells);
+    TileInfo& T = L.tiles[t];
+    T.cell_begin = c0;
+    T.n_cells = c1 - c0;
+    T.dof_begin = (int32_t)next;
+    for (int ci = c0; ci < c1; ++ci)
+      for (int s = 0; s < NSLOT; ++s) {
+        int32_t e = eid[(size_t)ci * NSLOT + s];
+        if (e >= 0 && owner[e] == t && estart[e] < 0) {
+          estart[e] = (int32_t)next;
+          next += endofs[e];
+        }
+      }
+    if (next > 0x7FFFFFFF) throw std::runtime_error("too many DoFs for 32-bit indices");
+    T.n_owned = (int32_t)(next - T.dof_begin);
+    // tile-local numbering: owned entities at their offset, foreign ones after
+    T.foreign_begin = (int32_t)L.foreign.size();
+    int32_t local_next = T.n_owned;
+    std::vector<int32_t> touched;
+    for (int ci = c0; ci < c1; ++ci)
+      for (int s = 0; s < NSLOT; ++s) {
+        int32_t e = eid[(size_t)ci * NSLOT + s];
+        if (e < 0 || lstart_of[e] >= 0) continue;
+        touched.push_back(e);
+        if (owner[e] == t) {
+          lstart_of[e] = estart[e] - T.dof_begin;
+        } else {
+          lstart_of[e] = local_next;
+          local_next += endofs[e];
+          for (int q = 0; q < endofs[e]; ++q) L.foreign.push_back(estart[e] + q);
+        }
+      }
+    T.n_foreign = local_next - T.n_owned;
+    if (local_next >= (int)LS_NONE) throw std::runtime_error("tile too large for 16-bit local indices");
+    L.max_local = std::max(L.max_local, (int)local_next);
+    for (int ci = c0; ci < c1; ++ci) {
+      CellMeta& cm = L.meta[ci];
+      for (int s = 0; s < NSLOT; ++s) {
+        int32_t e = eid[(size_t)ci * NSLOT + s];
+        cm.ls[s] = e < 0 ? LS_NONE : (uint16_t)lstart_of[e];
+      }
+      cm.mask = L.mask[ci];
+      cm.level = (uint8_t)L.cells[ci].l;
+    }
+    // sub-colours of the cells inside the tile (greedy, in cell order)
+    const int n = c1 - c0;
+    std::vector<int> sub(n, -1);
+    int nsub = 0;
+    {
+      std::unordered_map<int32_t, std::vector<int>> ecells;
+      std::vector<char> used;
+      for (int a = 0; a < n; ++a) {
+        used.assign(n + 1, 0);
+        for (int s = 0; s < NSLOT; ++s) {
+          int32_t e = eid[(size_t)(c0 + a) * NSLOT + s];
+          if (e < 0) continue;
+          auto it = ecells.find(e);
+          if (it != ecells.end())
+            for (int b : it->second) used[sub[b]] = 1;
+        }
+        int c = 0;
+        while (used[c]) ++c;
+        sub[a] = c;
+        nsub = std::max(nsub, c + 1);
+        for (int s = 0; s < NSLOT; ++s) {
+          int32_t e = eid[(size_t)(c0 + a) * NSLOT + s];
+          if (e < 0) continue;
+          auto& v = ecells[e];
+          if (v.empty() || v.back() != a) v.push_back(a);
+        }
+      }
+    }
+    T.sub_begin = (int32_t)L.subptr.size();
+    T.n_sub = nsub;
+    L.max_sub = std::max(L.max_sub, nsub);
+    int pos = 0;
+    for (int c = 0; c < nsub; ++c) {
+      L.subptr.push_back((uint16_t)pos);
+      for (int a = 0; a < n; ++a)
+        if (sub[a] == c) L.perm[c0 + pos++] = (uint8_t)a;
+    }
+    L.subptr.push_back((uint16_t)pos);
+    for (int32_t e : touched) lstart_of[e] = -1;
+  }
+  L.n_free = next;
+  // colour lists
+  L.colour_ptr.assign(L.n_colours + 1, 0);
+  for (int t = 0; t < nt; ++t) L.colour_ptr[colour[t] + 1]++;
+  for (int c = 0; c < L.n_colours; ++c) L.colour_ptr[c + 1] += L.colour_ptr[c];
+  L.colour_tiles.assign(nt, 0);
+  {
+    std::vector<int32_t> fill(L.colour_ptr.begin(), L.colour_ptr.end() - 1);
+    for (int t = 0; t < nt; ++t) L.colour_tiles[fill[colour[t]]++] = t;
+  }
+  // global starts and transfer ownership (first non-hanging reference wins)
+  L.gstart.assign((size_t)nc * NSLOT, -1);
+  L.own.assign(nc, 0u);
+  std::vector<char> owned(ne, 0);
+  for (int ci = 0; ci < nc; ++ci)
+    for (int s = 0; s < NSLOT; ++s) {
+      int32_t e = eid[(size_t)ci * NSLOT + s];
+      if (e < 0) continue;
+      L.gstart[(size_t)ci * NSLOT + s] = estart[e];
+      if (!hang_slot[(size_t)ci * NSLOT + s] && !owned[e]) {
+        owned[e] = 1;
+        L.own[ci] |= 1u << s;
+      }
+    }
+  for (int e = 0; e < ne; ++e)
+    if (!owned[e]) throw std::runtime_error("entity without a non-hanging reference");
+  // keep entity geometry for coordinates: store in the cells' order
+  L.dof_xyz_cache.clear();
+  L.dof_xyz_cache.resize((size_t)L.n_free * 3);
+  const Basis1D& b = basis(k);
+  const double hl = (L.hi - L.lo) / double(top);
+  for (int e = 0; e < ne; ++e) {
+    const EntityGeom& g = egeom[e];
+    int free_axes[3], nf = 0;
+    for (int d = 0; d < 3; ++d)
+      if (g.cls[d] == 1) free_axes[nf++] = d;
+    for (int q = 0; q < endofs[e]; ++q) {
+      double x[3];
+      for (int d = 0; d < 3; ++d) x[d] = L.lo + g.corner[d] * hl;
+      int r = q;
+      for (int a = 0; a < nf; ++a) {
+        int ia = r % (k - 1);
+        r /= (k - 1);
+        x[free_axes[a]] = L.lo + (g.corner[free_axes[a]] + g.size * b.xi[ia + 1]) * hl;
+      }
+      for (int d = 0; d < 3; ++d) L.dof_xyz_cache[((size_t)estart[e] + q) * 3 + d] = x[d];
+    }
+  }
+}
+
+void LevelHost::dof_coordinates(std::vector<double>& xyz) const { xyz = dof_xyz_cache; }
+
+void build_transfer_h(const LevelHost& fine, const LevelHost& coarse, TransferHost& T) {
+  T.kind = 0;
+  std::unordered_map<uint64_t, int32_t> fidx;
+  fidx.reserve(fine.cells.size() * 2);
+  for (size_t i = 0; i < fine.cells.size(); ++i) {
+    const Cell& c = fine.cells[i];
+    fidx.emplace(cell_key(c.l, c.i, c.j, c.k), (int32_t)i);
+  }
+  const size_t nc = coarse.cells.size();
+  T.fine_of.assign(nc, -1);
+  T.refined.assign(nc, 0);
+  for (size_t ci = 0; ci < nc; ++ci) {
+    const Cell& c = coarse.cells[ci];
+    auto it = fidx.find(cell_key(c.l, c.i, c.j, c.k));
+    if (it != fidx.end()) {
+      T.fine_of[ci] = it->second;
+      continue;
+    }
+    auto ch = fidx.find(cell_key(c.l + 1, 2 * c.i, 2 * c.j, 2 * c.k));
+    if (ch == fidx.end()) throw std::runtime_error("levels are not nested");
+    // the eight children are consecutive in Morton order
+    for (int q = 0; q < 8; ++q) {
+      const Cell& f = fine.cells[ch->second + q];
+      if (f.l != c.l + 1 || (f.i >> 1) != c.i || (f.j >> 1) != c.j || (f.k >> 1) != c.k ||
+          (f.i & 1) != (q & 1) || (f.j & 1) != ((q >> 1) & 1) || (f.k & 1) != (q >> 2))
+        throw std::runtime_error("children not consecutive in Morton order");
+    }
+    T.fine_of[ci] = ch->second;
+    T.refined[ci] = 1;
+  }
+}
+
+void build_transfer_p(const LevelHost& fine, const LevelHost& coarse, TransferHost& T) {
+  if (fine.cells.size() != coarse.cells.size()) throw std::runtime_error("p-transfer needs one mesh");
+  T.kind = 1;
+  T.fine_of.resize(coarse.cells.size());
+  T.refined.assign(coarse.cells.size(), 0);
+  for (size_t i = 0; i < coarse.cells.size(); ++i) T.fine_of[i] = (int32_t)i;
+}
+
+}  // namespace gcmg

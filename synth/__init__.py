@@ -203,3 +203,25 @@ def batch_recipes(seed: int = 12292, n: int = 256):
         rhs_seed = rng.next_u64() & 0x7FFFFFFF
         out.append((k, depth, extra, rhs_seed))
     return out
+
+
+# --------------------------------------------------------------------------
+# position-keyed random values: the same input vector for any DoF numbering
+# --------------------------------------------------------------------------
+
+def point_values(xyz: np.ndarray, seed: int, resolution_bits: int = 20) -> np.ndarray:
+    """Uniform values in [-1, 1) attached to points: each coordinate is
+    rounded to a multiple of 2^-resolution_bits, the three integers are mixed
+    with SplitMix64's finaliser together with the seed.  Two programs that
+    number the same support points differently get the same vector."""
+    q = np.rint(np.asarray(xyz, dtype=np.float64) * float(1 << resolution_bits)).astype(np.int64)
+    mask = np.uint64(MASK64)
+    with np.errstate(over="ignore"):
+        h = np.full(len(q), np.uint64(seed & MASK64), dtype=np.uint64)
+        for d in range(3):
+            h = h ^ q[:, d].astype(np.uint64)
+            h = h + np.uint64(0x9E3779B97F4A7C15)
+            h = (h ^ (h >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+            h = (h ^ (h >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+            h = (h ^ (h >> np.uint64(31))) & mask
+    return -1.0 + 2.0 * (h >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
