@@ -1,0 +1,312 @@
+"""Benchmark: global-coarsening matrix-free multigrid on one GB300 per rank.
+
+Workload: Poisson -Lap u = f on [0,1]^3, Q4, one cell refined globally 5
+times and twice more in the octant x, y, z < 1/2 (296,535 cells, 8 levels,
+18,740,987 free DoFs), f = seeded Gaussian random field (8 Fourier modes,
+seed 2203).
+
+One step = one pass of the whole hot path: CG in fp64 preconditioned by one
+fp32 V-cycle per iteration (Chebyshev(3)/Jacobi smoothing, residual,
+restriction, exact level-0 solve, prolongation on every level), from x = 0 to
+a relative residual of 1e-8, with b already resident in HBM.
+
+value = fine-level fp32 operator throughput n_free / t_vmult (GDoF/s),
+t_vmult = mean duration of the fine-level operator applications inside the
+timed solves, from CUDA events on the library's stream.  Solve times of the
+mixed (fp32 V-cycle) and plain fp64 (fp64 V-cycle) variants are reported
+beside it.  Under torchrun every rank solves its own copy (replicas, weak
+scaling); value sums the ranks.
+
+--impl reference times the oracle (plain CPU implementation, test
+infrastructure) on a bounded sample of the workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = synth.WORKLOAD_Q4_OCTANT
+METRIC = "fine-level vmult GDoF/s; solve time to 1e-8 rel. res., mixed/learned vs FP64"
+# algorithmic bytes per DoF of one operator application: source and
+# destination vector plus the per-cell metadata (roofline model of the
+# workload, per free DoF)
+BYTES_PER_DOF = {"fp32": 9.8, "fp64": 17.8}
+SAMPLE = synth.cube_octant(4, 2)  # 1/8 of the workload's cells, same recipe family
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def oracle_vmult_sample(seconds: float = 6.0):
+    """Time the oracle's fp64 cell-by-cell operator on the sample mesh."""
+    from oracle import mesh as omesh, space as ospace
+
+    s = ospace.Space(omesh.build_mesh(SAMPLE), WORKLOAD.degree)
+    x = synth.point_values(s.free_coordinates(), 1)
+    s.apply(x)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        s.apply(x)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el > seconds:
+            break
+    cores = os.cpu_count() or 1
+    return {"value": s.n_free * reps / el / 1e9, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+            "sample": f"fp64 cell-by-cell operator of the oracle on {SAMPLE.name} (Q4, {s.nc} cells, "
+                      f"{s.n_free} free DoFs, 1/8 of the workload), {reps} applications"}
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the
+    timed region (read only)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.proc = None
+        self.device = device
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    from oracle import mesh as omesh, space as ospace
+
+    s = ospace.Space(omesh.build_mesh(SAMPLE), WORKLOAD.degree)
+    x = synth.point_values(s.free_coordinates(), 1)
+    for _ in range(args.warmup):
+        s.apply(x)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        s.apply(x)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * float(np.mean(times))
+    value = s.n_free / (ms * 1e-3) / 1e9
+    cores = os.cpu_count() or 1
+    line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"oracle sample: {SAMPLE.name}, Q4, {s.nc} cells, {s.n_free} free DoFs "
+                                   f"(1/8 of {WORKLOAD.name})"},
+            "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+                             "sample": f"one fp64 operator application per step on {SAMPLE.name}"},
+            "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "setup_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gcmg", choices=["gcmg", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_2203_12292_gb300 import build as gbuild
+
+    if rank == 0:
+        gbuild.build()
+    barrier()
+    import paper_2203_12292_gb300 as g
+
+    # cpu baseline first (no GPU work in flight), rank 0 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_vmult_sample()
+
+    t0 = time.perf_counter()
+    mesh = g.Mesh.from_recipe(WORKLOAD.recipe)
+    mg = g.Multigrid(mesh, WORKLOAD.degree, mg_fp32=True)
+    setup_s = time.perf_counter() - t0
+    L = mg.finest
+    n = mg.n_free(L)
+    f = synth.fourier_rhs(WORKLOAD.rhs_seed)
+    b = mg.rhs((f.kappa, f.phi, f.amp))
+    x = torch.zeros_like(b)
+    stream = mg.stream
+
+    def step():
+        return mg.cg_solve(b, x, 1e-8, 100)
+
+    for _ in range(args.warmup):
+        st = step()
+    torch.cuda.synchronize()
+    mg.set_profiling(True)
+    launches0 = g.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        st = step()
+        iters.append(st.iterations)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = g.launch_count() - launches0
+    ms_total = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    cnt, vms = mg.profile(L, "vmult")
+    cnt64, vms64 = mg.profile(L, "cg_vmult")
+    stage_ms = {s: mg.profile(L, s)[1] / args.steps for s in g.STAGES}
+    coarse_ms = sum(mg.profile(l, s)[1] for l in range(L) for s in g.STAGES) / args.steps
+    mg.set_profiling(False)
+    t_vmult = vms / cnt  # ms
+    value = n / (t_vmult * 1e-3) / 1e9
+    value64 = n / (vms64 / cnt64 * 1e-3) / 1e9
+    if dist is not None:
+        t = torch.tensor([value], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t)
+        value = float(t.item())
+
+    # plain fp64 variant (fp64 V-cycle) of the same solve
+    mg64 = g.Multigrid(mesh, WORKLOAD.degree, mg_fp32=False)
+    x64 = torch.zeros_like(b)
+    mg64.cg_solve(b, x64, 1e-8, 100)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    st64 = mg64.cg_solve(b, x64, 1e-8, 100)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1)
+    sol_diff = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+    del mg64
+
+    # end to end through the C ABI with pinned host buffers
+    hsrc = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    hdst = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    hsrc.copy_(torch.from_numpy(synth.uniform_vector(n, 3).astype(np.float32)))
+    hs, hd = hsrc.numpy(), hdst.numpy()
+    for _ in range(2):
+        mg.vmult_host(L, hs, hd)
+    reps = max(args.steps, 5)
+    t = time.perf_counter()
+    for _ in range(reps):
+        mg.vmult_host(L, hs, hd)
+    e2e_s = (time.perf_counter() - t) / reps
+
+    hbm, peak_kind = peaks()
+    achieved = BYTES_PER_DOF["fp32"] * n / (t_vmult * 1e-3) / 1e9
+    traffic = None
+    if rank == 0:
+        res = {
+            "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 V-cycle / f64 CG", "data": "synthetic",
+            "config": {"workload": WORKLOAD.name, "degree": WORKLOAD.degree, "cells": mg.level_info(L).n_cells,
+                       "n_free": n, "levels": mg.num_levels, "rhs": "8 Fourier modes, seed 2203",
+                       "rtol": 1e-8, "l2": "inputs larger than L2 (finest level vectors and metadata > 129 MB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "kernel": "cell_kernel<4,float> (fine-level operator, all colour launches)",
+                         "peak_kind": peak_kind, "bytes_per_dof": BYTES_PER_DOF["fp32"]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": n / e2e_s / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 4 * n,
+                    "d2h_bytes_per_step": 4 * n, "call": "gcmg_vmult_host, pinned host buffers, fp32"},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "solve": {"mixed_ms": ms_step, "mixed_iterations": iters[-1], "mixed_rel_residual": st.rel_residual,
+                      "fp64_ms": fp64_ms, "fp64_iterations": st64.iterations,
+                      "fp64_rel_residual": st64.rel_residual, "speedup_mixed_vs_fp64": fp64_ms / ms_step,
+                      "solution_rel_diff_mixed_vs_fp64": sol_diff},
+            "vmult": {"fp32_ms": t_vmult, "fp32_gdofs": value / world, "fp64_ms": vms64 / cnt64,
+                      "fp64_gdofs": value64},
+            "stage_ms_per_step_finest": stage_ms, "coarser_levels_ms_per_step": coarse_ms,
+            "setup_s": setup_s,
+        }
+        print(json.dumps(res), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

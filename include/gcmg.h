@@ -77,6 +77,15 @@ int gcmg_mesh_level_cells(const gcmg_mesh* mesh, int level, int64_t* n_cells);
  * with the same mesh, degree and tile_cells (0 = default).
  */
 int gcmg_mesh_dof_coords(const gcmg_mesh* mesh, int level, int degree, int tile_cells, int64_t* n_free, double* xyz);
+/*
+ * Host-only check of the tile data of a level (what the kernels rely on):
+ * tiles and owned DoF ranges partition cells and DoFs, tile-local indices
+ * stay in range and map to the right DoFs, no two cells of one sub-colour
+ * and no two tiles of one colour share a DoF, every foreign DoF is owned by
+ * a tile of a lower colour, every DoF has exactly one transfer owner.
+ * Returns GCMG_OK or GCMG_ERR_INTERNAL with the failed invariant.
+ */
+int gcmg_mesh_check_level(const gcmg_mesh* mesh, int level, int degree, int tile_cells);
 
 typedef struct {
   int degree;              /* polynomial degree k of the finest level, 1..4 */
@@ -154,6 +163,28 @@ int gcmg_coarse_solve(gcmg_handle* h, int fp64, const void* b, void* x);
  */
 int gcmg_vcycle(gcmg_handle* h, const double* b, double* x);
 
+/*
+ * Same operator with host vectors: copies src (host, n_free values) to the
+ * device, applies the operator, copies the result into dst (host) and
+ * synchronises.  Pinned host memory gives full copy bandwidth.
+ */
+int gcmg_vmult_host(gcmg_handle* h, int level, int fp64, const void* src, void* dst);
+
+/* stages of the per-level timers (CUDA events on the handle's stream) */
+#define GCMG_STAGE_VMULT 0       /* each operator application of the V-cycle levels */
+#define GCMG_STAGE_PRESMOOTH 1   /* Algorithm 2 presmoothing (its operator applications included) */
+#define GCMG_STAGE_RESIDUAL 2
+#define GCMG_STAGE_RESTRICT 3
+#define GCMG_STAGE_COARSE 4
+#define GCMG_STAGE_PROLONGATE 5
+#define GCMG_STAGE_POSTSMOOTH 6
+#define GCMG_STAGE_CG_VMULT 7    /* fp64 operator of CG on the finest level */
+#define GCMG_STAGE_CG_VECTOR 8   /* CG inner products, updates, precision casts */
+/* switch the timers on/off; both reset the accumulated times */
+int gcmg_set_profiling(gcmg_handle* h, int on);
+/* accumulated launches and milliseconds of one (level, stage); synchronises */
+int gcmg_get_profile(gcmg_handle* h, int level, int stage, int64_t* count, double* ms);
+
 typedef struct {
   int iterations;
   double r0;            /* ||b||_2 */
@@ -169,6 +200,8 @@ typedef struct {
 int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int maxit, gcmg_solve_stats* stats);
 
 const char* gcmg_last_error(void);
+/* number of CUDA kernel launches issued by this library since it was loaded */
+int64_t gcmg_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,9 @@ _c_int, _c_double, _c_void_p, _c_int64 = ctypes.c_int, ctypes.c_double, ctypes.c
 
 PRED_ALL, PRED_OCTANT_CENTRE, PRED_SPHERE, PRED_SHELL, PRED_OCTANT_STRICT = 0, 1, 2, 3, 4
 
+STAGES = ["vmult", "presmooth", "residual", "restrict", "coarse", "prolongate", "postsmooth", "cg_vmult",
+          "cg_vector"]
+
 ERRORS = {1: "GCMG_ERR_ARG", 2: "GCMG_ERR_CUDA", 3: "GCMG_ERR_OOM", 4: "GCMG_ERR_NOT_CONVERGED",
           5: "GCMG_ERR_BREAKDOWN", 6: "GCMG_ERR_INTERNAL"}
 
@@ -51,11 +54,13 @@ class SolveStats(ctypes.Structure):
 
 _SIGS = {
     "gcmg_last_error": (ctypes.c_char_p, []),
+    "gcmg_launch_count": (_c_int64, []),
     "gcmg_mesh_create": (_c_int, [_c_double, _c_double, _c_int, ctypes.POINTER(RefineStep), ctypes.POINTER(_c_void_p)]),
     "gcmg_mesh_destroy": (None, [_c_void_p]),
     "gcmg_mesh_num_levels": (_c_int, [_c_void_p, ctypes.POINTER(_c_int)]),
     "gcmg_mesh_level_cells": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_int64)]),
     "gcmg_mesh_dof_coords": (_c_int, [_c_void_p, _c_int, _c_int, _c_int, ctypes.POINTER(_c_int64), _c_void_p]),
+    "gcmg_mesh_check_level": (_c_int, [_c_void_p, _c_int, _c_int, _c_int]),
     "gcmg_config_default": (_c_int, [ctypes.POINTER(Config)]),
     "gcmg_setup": (_c_int, [_c_void_p, ctypes.POINTER(Config), _c_void_p, ctypes.POINTER(_c_void_p)]),
     "gcmg_destroy": (None, [_c_void_p]),
@@ -64,6 +69,9 @@ _SIGS = {
     "gcmg_get_level_info": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(LevelInfo)]),
     "gcmg_level_dof_coords": (_c_int, [_c_void_p, _c_int, _c_void_p]),
     "gcmg_vmult": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
+    "gcmg_vmult_host": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
+    "gcmg_set_profiling": (_c_int, [_c_void_p, _c_int]),
+    "gcmg_get_profile": (_c_int, [_c_void_p, _c_int, _c_int, ctypes.POINTER(_c_int64), ctypes.POINTER(_c_double)]),
     "gcmg_diagonal": (_c_int, [_c_void_p, _c_int, _c_void_p]),
     "gcmg_rhs": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_double, _c_void_p]),
     "gcmg_get_lambda": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_double)]),
@@ -92,6 +100,11 @@ def lib() -> ctypes.CDLL:
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def launch_count() -> int:
+    """Kernel launches issued by libgcmg so far."""
+    return int(lib().gcmg_launch_count())
 
 
 def exported_symbols() -> Sequence[str]:
@@ -141,6 +154,10 @@ class Mesh:
         n = _c_int64()
         _check(lib().gcmg_mesh_level_cells(self._p, level, ctypes.byref(n)))
         return n.value
+
+    def check_level(self, level: int, degree: int, tile_cells: int = 0) -> None:
+        """Validate the tile data of a level on the host (raises GcmgError)."""
+        _check(lib().gcmg_mesh_check_level(self._p, level, degree, tile_cells))
 
     def dof_coords(self, level: int, degree: int, tile_cells: int = 0) -> np.ndarray:
         n = _c_int64()
@@ -226,6 +243,25 @@ class Multigrid:
     def vmult(self, level: int, src, dst) -> None:
         n = self.n_free(level)
         _check(lib().gcmg_vmult(self._h, level, _is64(src), _ptr(src, n, src.dtype), _ptr(dst, n, src.dtype)))
+
+    def vmult_host(self, level: int, src: np.ndarray, dst: np.ndarray) -> None:
+        """Operator with host (numpy) vectors; copies in and out, synchronous."""
+        n = self.n_free(level)
+        if src.dtype not in (np.float32, np.float64) or dst.dtype != src.dtype or len(src) != n or len(dst) != n:
+            raise ValueError("host vectors must be float32/float64 of length n_free")
+        if not (src.flags.c_contiguous and dst.flags.c_contiguous):
+            raise ValueError("host vectors must be contiguous")
+        _check(lib().gcmg_vmult_host(self._h, level, int(src.dtype == np.float64), src.ctypes.data_as(_c_void_p),
+                                     dst.ctypes.data_as(_c_void_p)))
+
+    def set_profiling(self, on: bool) -> None:
+        _check(lib().gcmg_set_profiling(self._h, int(on)))
+
+    def profile(self, level: int, stage: str):
+        """(launch count, milliseconds) accumulated for a level and stage."""
+        c, ms = _c_int64(), _c_double()
+        _check(lib().gcmg_get_profile(self._h, level, STAGES.index(stage), ctypes.byref(c), ctypes.byref(ms)))
+        return c.value, ms.value
 
     def diagonal(self, level: int):
         import torch

@@ -1,6 +1,7 @@
 // C ABI of libgcmg: set-up of the multigrid levels and the orchestration of
 // the V-cycle (Algorithms 1-2) and of the preconditioned CG (Sec. 2).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -17,6 +18,9 @@ namespace gcmg {
 
 void upload_tables_cell();
 void upload_tables_transfer();
+
+static std::atomic<long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
 
@@ -82,8 +86,32 @@ struct TransferDev {
 
 }  // namespace
 
+// CUDA-event timers per (level, stage): the per-level, per-stage profile of
+// a V-cycle (presmoothing, residual, restriction, coarse solve, prolongation,
+// postsmoothing) plus operator applications and CG vector work.
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int level = 0, stage = 0;
+  };
+  std::vector<Rec> pool;
+  size_t used = 0;
+  std::vector<double> ms;
+  std::vector<int64_t> cnt;
+  int nlev = 0;
+  ~Profiler() {
+    for (auto& r : pool) {
+      if (r.a) cudaEventDestroy(r.a);
+      if (r.b) cudaEventDestroy(r.b);
+    }
+  }
+};
+constexpr int NSTAGE = 9;
+
 struct Handle {
   cudaStream_t stream = nullptr;
+  Profiler prof;
   gcmg_config cfg{};
   std::vector<std::unique_ptr<LevelDev>> lev;
   std::vector<std::unique_ptr<TransferDev>> tr;  // tr[l]: between levels l and l-1
@@ -108,10 +136,51 @@ void check_level(const Handle& h, int level) {
   if (level < 0 || level >= (int)h.lev.size()) throw Error(GCMG_ERR_ARG, "level out of range");
 }
 
-void vmult(Handle& H, int l, bool fp64, const void* src, void* dst) {
+void prof_flush(Handle& H) {
+  Profiler& P = H.prof;
+  if (!P.used) return;
+  ck(cudaEventSynchronize(P.pool[P.used - 1].b), "profile");
+  for (size_t i = 0; i < P.used; ++i) {
+    float t = 0.f;
+    ck(cudaEventElapsedTime(&t, P.pool[i].a, P.pool[i].b), "profile");
+    const size_t idx = (size_t)P.pool[i].level * NSTAGE + P.pool[i].stage;
+    P.ms[idx] += t;
+    P.cnt[idx] += 1;
+  }
+  P.used = 0;
+}
+
+// returns a record index, or -1 when profiling is off
+int prof_begin(Handle& H, int level, int stage) {
+  Profiler& P = H.prof;
+  if (!P.on) return -1;
+  if (P.used == P.pool.size()) {
+    if (P.pool.size() >= 8192) prof_flush(H);
+    if (P.used == P.pool.size()) {
+      Profiler::Rec r;
+      ck(cudaEventCreate(&r.a), "event");
+      ck(cudaEventCreate(&r.b), "event");
+      P.pool.push_back(r);
+    }
+  }
+  Profiler::Rec& r = P.pool[P.used];
+  r.level = level;
+  r.stage = stage;
+  ck(cudaEventRecord(r.a, H.stream), "event");
+  return (int)P.used++;
+}
+
+void prof_end(Handle& H, int rec) {
+  if (rec < 0) return;
+  ck(cudaEventRecord(H.prof.pool[rec].b, H.stream), "event");
+}
+
+void vmult(Handle& H, int l, bool fp64, const void* src, void* dst, int stage = GCMG_STAGE_VMULT) {
   LevelDev& L = *H.lev[l];
   if (L.n() == 0) return;
+  const int r = prof_begin(H, l, stage);
   launch_vmult(L.cl, fp64, src, dst, 0, H.stream);
+  prof_end(H, r);
 }
 
 double dot_host(Handle& H, const double* x, const double* y, int64_t n) {
@@ -282,33 +351,49 @@ void vcycle_level(Handle& H, int l) {
   LevelDev& L = *H.lev[l];
   const bool f64 = !L.fp32;
   if (l == 0) {
+    const int r = prof_begin(H, 0, GCMG_STAGE_COARSE);
     if (H.n0) launch_coarse_solve(f64, H.Ainv.as<double>(), H.n0, L.b.p, L.x.p, H.stream);
+    prof_end(H, r);
     return;
   }
   const void* dinv = f64 ? L.dinv64.p : L.dinv32.p;
+  int r = prof_begin(H, l, GCMG_STAGE_PRESMOOTH);
   smooth(H, l, f64, L.x.p, L.b.p, L.d.p, L.t.p, dinv, true);  // presmoothing
-  vmult(H, l, f64, L.x.p, L.t.p);                             // residual
+  prof_end(H, r);
+  r = prof_begin(H, l, GCMG_STAGE_RESIDUAL);
+  vmult(H, l, f64, L.x.p, L.t.p);  // residual
   launch_residual(f64, L.t.p, L.b.p, L.t.p, L.n(), H.stream);
+  prof_end(H, r);
   LevelDev& C = *H.lev[l - 1];
+  r = prof_begin(H, l, GCMG_STAGE_RESTRICT);
   launch_zero(!C.fp32, C.b.p, C.n(), H.stream);
   if (C.n()) launch_restrict_add(H.tr[l]->tl, f64, L.t.p, C.b.p, H.stream);  // restriction
+  prof_end(H, r);
   vcycle_level(H, l - 1);
+  r = prof_begin(H, l, GCMG_STAGE_PROLONGATE);
   if (C.n()) launch_prolongate_add(H.tr[l]->tl, f64, C.x.p, L.x.p, H.stream);  // prolongation
+  prof_end(H, r);
+  r = prof_begin(H, l, GCMG_STAGE_POSTSMOOTH);
   smooth(H, l, f64, L.x.p, L.b.p, L.d.p, L.t.p, dinv, false);  // postsmoothing
+  prof_end(H, r);
 }
 
 void vcycle(Handle& H, const double* b, double* x) {
   const int top = (int)H.lev.size() - 1;
   LevelDev& F = *H.lev[top];
+  int r = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);
   if (F.fp32)
     launch_cast(false, b, F.b.p, F.n(), H.stream);
   else
     ck(cudaMemcpyAsync(F.b.p, b, F.n() * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
+  prof_end(H, r);
   vcycle_level(H, top);
+  r = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);
   if (F.fp32)
     launch_cast(true, F.x.p, x, F.n(), H.stream);
   else
     ck(cudaMemcpyAsync(x, F.x.p, F.n() * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
+  prof_end(H, r);
 }
 
 template <typename F>
@@ -345,6 +430,8 @@ using namespace gcmg;
 extern "C" {
 
 const char* gcmg_last_error(void) { return g_err.c_str(); }
+
+int64_t gcmg_launch_count(void) { return (int64_t)g_launches.load(); }
 
 int gcmg_mesh_create(double lo, double hi, int n_steps, const gcmg_refine_step* steps, gcmg_mesh** out) {
   return guarded([&] {
@@ -393,6 +480,21 @@ int gcmg_mesh_dof_coords(const gcmg_mesh* mesh, int level, int degree, int tile_
     build_level(mesh->levels[level], degree, tile_cells ? tile_cells : default_tile_cells(degree), mesh->lmax, L);
     *n_free = L.n_free;
     if (xyz) std::memcpy(xyz, L.dof_xyz_cache.data(), L.dof_xyz_cache.size() * sizeof(double));
+  });
+}
+
+int gcmg_mesh_check_level(const gcmg_mesh* mesh, int level, int degree, int tile_cells) {
+  return guarded([&] {
+    if (!mesh || level < 0 || level >= (int)mesh->levels.size()) throw Error(GCMG_ERR_ARG, "bad level");
+    if (degree < 1 || degree > KMAX) throw Error(GCMG_ERR_ARG, "degree must be 1..4");
+    if (tile_cells < 0 || tile_cells > 255) throw Error(GCMG_ERR_ARG, "tile_cells must be 0..255");
+    LevelHost L;
+    build_level(mesh->levels[level], degree, tile_cells ? tile_cells : default_tile_cells(degree), mesh->lmax, L);
+    try {
+      validate_level(L);
+    } catch (const std::exception& e) {
+      throw Error(GCMG_ERR_INTERNAL, e.what());
+    }
   });
 }
 
@@ -588,6 +690,52 @@ int gcmg_level_dof_coords(const gcmg_handle* h, int level, double* xyz) {
   });
 }
 
+int gcmg_set_profiling(gcmg_handle* h, int on) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    Profiler& P = h->h.prof;
+    prof_flush(h->h);
+    P.on = on != 0;
+    P.nlev = (int)h->h.lev.size();
+    P.ms.assign((size_t)P.nlev * NSTAGE, 0.0);
+    P.cnt.assign((size_t)P.nlev * NSTAGE, 0);
+  });
+}
+
+int gcmg_get_profile(gcmg_handle* h, int level, int stage, int64_t* count, double* ms) {
+  return guarded([&] {
+    if (!h || !count || !ms || stage < 0 || stage >= NSTAGE) throw Error(GCMG_ERR_ARG, "bad arguments");
+    check_level(h->h, level);
+    prof_flush(h->h);
+    Profiler& P = h->h.prof;
+    if (P.ms.empty()) {
+      *count = 0;
+      *ms = 0.0;
+      return;
+    }
+    *count = P.cnt[(size_t)level * NSTAGE + stage];
+    *ms = P.ms[(size_t)level * NSTAGE + stage];
+  });
+}
+
+int gcmg_vmult_host(gcmg_handle* h, int level, int fp64, const void* src, void* dst) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    check_level(h->h, level);
+    Handle& H = h->h;
+    LevelDev& L = *H.lev[level];
+    if (L.n() == 0) return;
+    if (!src || !dst) throw Error(GCMG_ERR_ARG, "bad vectors");
+    const size_t bytes = L.n() * (fp64 ? sizeof(double) : sizeof(float));
+    void* a = fp64 ? L.w64a.p : L.w32a.p;
+    void* b = fp64 ? L.w64b.p : L.w32b.p;
+    ck(cudaMemcpyAsync(a, src, bytes, cudaMemcpyHostToDevice, H.stream), "copy in");
+    vmult(H, level, fp64 != 0, a, b);
+    ck(cudaMemcpyAsync(dst, b, bytes, cudaMemcpyDeviceToHost, H.stream), "copy out");
+    ck(cudaStreamSynchronize(H.stream), "vmult_host");
+  });
+}
+
 int gcmg_vmult(gcmg_handle* h, int level, int fp64, const void* src, void* dst) {
   return guarded([&] {
     if (!h) throw Error(GCMG_ERR_ARG, "null handle");
@@ -735,9 +883,11 @@ int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int m
     double rr = nb * nb;
     int it = 0;
     for (it = 1; it <= maxit; ++it) {
-      vmult(H, top, true, p, q);
+      vmult(H, top, true, p, q, GCMG_STAGE_CG_VMULT);
+      const int pr = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);
       launch_dot(p, q, n, H.scratch.as<double>(), S, 0, DOT_ALPHA, s);
       launch_cg_update_xr(x, r, p, q, S, n, H.scratch.as<double>(), S, s);
+      prof_end(H, pr);
       double hs[6];
       ck(cudaMemcpyAsync(hs, S, sizeof(hs), cudaMemcpyDeviceToHost, s), "scalars");
       ck(cudaStreamSynchronize(s), "cg");
@@ -748,8 +898,10 @@ int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int m
       rr = hs[2];
       if (std::sqrt(rr) <= rtol * nb) break;
       vcycle(H, r, z);
+      const int pz = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);
       launch_dot(r, z, n, H.scratch.as<double>(), S, 0, DOT_BETA, s);
       launch_cg_update_p(p, z, S, n, s);
+      prof_end(H, pz);
     }
     if (it > maxit) {
       it = maxit;

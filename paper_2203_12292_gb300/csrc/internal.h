@@ -128,6 +128,7 @@ struct LevelHost {
 };
 
 void build_level(const Octree& mesh, int k, int tile_cells, int lmax_lattice, LevelHost& L);
+void validate_level(const LevelHost& L);
 
 // transfer between a fine level and the next coarser one
 struct TransferHost {

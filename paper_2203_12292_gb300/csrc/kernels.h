@@ -9,6 +9,9 @@
 
 namespace gcmg {
 
+// count of kernel launches issued by the library (all host threads)
+void note_launches(int n);
+
 enum CellMode { MODE_VMULT = 0, MODE_RHS = 1, MODE_DIAG = 2 };
 
 // arguments of the tile kernels (operator, right-hand side, diagonal)

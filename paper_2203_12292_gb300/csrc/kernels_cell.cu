@@ -254,7 +254,7 @@ void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
     const int n = L.colour_ptr[c + 1] - L.colour_ptr[c];
     if (n == 0) continue;
     A.tile_list = L.colour_tiles + L.colour_ptr[c];
-    cell_kernel<K, T, MODE><<<n, BLOCK, sm, s>>>(A);
+    { cell_kernel<K, T, MODE><<<n, BLOCK, sm, s>>>(A); note_launches(1); }
   }
 }
 
@@ -330,10 +330,10 @@ void launch_diag_table(int k, double* tab_out, cudaStream_t s) {
   const size_t sm = (((size_t)tc * 10 + 15) & ~(size_t)15) + (size_t)tc * n3 * sizeof(double);
   const int nb = (512 * n3 + tc - 1) / tc;
   switch (k) {
-    case 1: diag_table_kernel<1><<<nb, BLOCK, sm, s>>>(tab_out, tc); break;
-    case 2: diag_table_kernel<2><<<nb, BLOCK, sm, s>>>(tab_out, tc); break;
-    case 3: diag_table_kernel<3><<<nb, BLOCK, sm, s>>>(tab_out, tc); break;
-    case 4: diag_table_kernel<4><<<nb, BLOCK, sm, s>>>(tab_out, tc); break;
+    { case 1: diag_table_kernel<1><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
+    { case 2: diag_table_kernel<2><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
+    { case 3: diag_table_kernel<3><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
+    { case 4: diag_table_kernel<4><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
     default: break;
   }
 }

@@ -373,7 +373,7 @@ void prolong_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s
   A.src = src;
   A.dst = dst;
   const int nb = (L.n_coarse + TP - 1) / TP;
-  prolong_h<K, T><<<nb, BLOCK, sm, s>>>(A);
+  { prolong_h<K, T><<<nb, BLOCK, sm, s>>>(A); note_launches(1); }
 }
 
 template <int K, typename T>
@@ -390,7 +390,7 @@ void restrict_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t 
     const int n = L.coarse.colour_ptr[c + 1] - L.coarse.colour_ptr[c];
     if (!n) continue;
     A.tile_list = L.coarse.colour_tiles + L.coarse.colour_ptr[c];
-    restrict_h<K, T><<<n, BLOCK, sm, s>>>(A);
+    { restrict_h<K, T><<<n, BLOCK, sm, s>>>(A); note_launches(1); }
   }
 }
 
@@ -403,7 +403,7 @@ void prolong_p_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s
   A.src = src;
   A.dst = dst;
   const int nb = (L.n_coarse + TP - 1) / TP;
-  prolong_p<KF, T><<<nb, BLOCK, sm, s>>>(A);
+  { prolong_p<KF, T><<<nb, BLOCK, sm, s>>>(A); note_launches(1); }
 }
 
 template <int KF, typename T>
@@ -421,7 +421,7 @@ void restrict_p_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t 
     const int n = L.coarse.colour_ptr[c + 1] - L.coarse.colour_ptr[c];
     if (!n) continue;
     A.tile_list = L.coarse.colour_tiles + L.coarse.colour_ptr[c];
-    restrict_p<KF, T><<<n, BLOCK, sm, s>>>(A);
+    { restrict_p<KF, T><<<n, BLOCK, sm, s>>>(A); note_launches(1); }
   }
 }
 

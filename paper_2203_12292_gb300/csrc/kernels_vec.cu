@@ -165,47 +165,47 @@ __global__ void xpby_kernel(double* p, const double* z, double beta, int64_t n) 
 }  // namespace
 
 void launch_fill(double* x, double v, int64_t n, cudaStream_t s) {
-  if (n > 0) fill_kernel<<<grid_for(n), BLOCK, 0, s>>>(x, v, n);
+  if (n > 0) { fill_kernel<<<grid_for(n), BLOCK, 0, s>>>(x, v, n); note_launches(1); }
 }
 
 void launch_pmul(double* z, const double* a, const double* b, int64_t n, cudaStream_t s) {
-  if (n > 0) pmul_kernel<<<grid_for(n), BLOCK, 0, s>>>(z, a, b, n);
+  if (n > 0) { pmul_kernel<<<grid_for(n), BLOCK, 0, s>>>(z, a, b, n); note_launches(1); }
 }
 
 void launch_xpby(double* p, const double* z, double beta, int64_t n, cudaStream_t s) {
-  if (n > 0) xpby_kernel<<<grid_for(n), BLOCK, 0, s>>>(p, z, beta, n);
+  if (n > 0) { xpby_kernel<<<grid_for(n), BLOCK, 0, s>>>(p, z, beta, n); note_launches(1); }
 }
 
 void launch_cast(bool to64, const void* src, void* dst, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   if (to64)
-    cast_kernel<float, double><<<grid_for(n), BLOCK, 0, s>>>(static_cast<const float*>(src), static_cast<double*>(dst), n);
+    { cast_kernel<float, double><<<grid_for(n), BLOCK, 0, s>>>(static_cast<const float*>(src), static_cast<double*>(dst), n); note_launches(1); }
   else
-    cast_kernel<double, float><<<grid_for(n), BLOCK, 0, s>>>(static_cast<const double*>(src), static_cast<float*>(dst), n);
+    { cast_kernel<double, float><<<grid_for(n), BLOCK, 0, s>>>(static_cast<const double*>(src), static_cast<float*>(dst), n); note_launches(1); }
 }
 
 void launch_zero(bool fp64, void* x, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   if (fp64)
-    zero_kernel<double><<<grid_for(n), BLOCK, 0, s>>>(static_cast<double*>(x), n);
+    { zero_kernel<double><<<grid_for(n), BLOCK, 0, s>>>(static_cast<double*>(x), n); note_launches(1); }
   else
-    zero_kernel<float><<<grid_for(n), BLOCK, 0, s>>>(static_cast<float*>(x), n);
+    { zero_kernel<float><<<grid_for(n), BLOCK, 0, s>>>(static_cast<float*>(x), n); note_launches(1); }
 }
 
 void launch_invert(const double* d, double* inv64, float* inv32, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
-  invert_kernel<<<grid_for(n), BLOCK, 0, s>>>(d, inv64, inv32, n);
+  { invert_kernel<<<grid_for(n), BLOCK, 0, s>>>(d, inv64, inv32, n); note_launches(1); }
 }
 
 void launch_cheb_init(bool fp64, void* x, void* d, const void* b, const void* dinv, double c2, int64_t n,
                       cudaStream_t s) {
   if (n <= 0) return;
   if (fp64)
-    cheb_init_kernel<double><<<grid_for(n), BLOCK, 0, s>>>((double*)x, (double*)d, (const double*)b,
-                                                            (const double*)dinv, c2, n);
+    { cheb_init_kernel<double><<<grid_for(n), BLOCK, 0, s>>>((double*)x, (double*)d, (const double*)b,
+                                                            (const double*)dinv, c2, n); note_launches(1); }
   else
-    cheb_init_kernel<float><<<grid_for(n), BLOCK, 0, s>>>((float*)x, (float*)d, (const float*)b, (const float*)dinv,
-                                                           (float)c2, n);
+    { cheb_init_kernel<float><<<grid_for(n), BLOCK, 0, s>>>((float*)x, (float*)d, (const float*)b, (const float*)dinv,
+                                                           (float)c2, n); note_launches(1); }
 }
 
 void launch_cheb_step(bool fp64, void* x, void* d, const void* b, const void* Ax, const void* dinv, double c1,
@@ -214,62 +214,62 @@ void launch_cheb_step(bool fp64, void* x, void* d, const void* b, const void* Ax
   const bool first = (c1 == 0.0);
   if (fp64) {
     if (first)
-      cheb_step_kernel<double, true><<<grid_for(n), BLOCK, 0, s>>>((double*)x, (double*)d, (const double*)b,
-                                                                   (const double*)Ax, (const double*)dinv, c1, c2, n);
+      { cheb_step_kernel<double, true><<<grid_for(n), BLOCK, 0, s>>>((double*)x, (double*)d, (const double*)b,
+                                                                   (const double*)Ax, (const double*)dinv, c1, c2, n); note_launches(1); }
     else
-      cheb_step_kernel<double, false><<<grid_for(n), BLOCK, 0, s>>>((double*)x, (double*)d, (const double*)b,
-                                                                    (const double*)Ax, (const double*)dinv, c1, c2, n);
+      { cheb_step_kernel<double, false><<<grid_for(n), BLOCK, 0, s>>>((double*)x, (double*)d, (const double*)b,
+                                                                    (const double*)Ax, (const double*)dinv, c1, c2, n); note_launches(1); }
   } else {
     if (first)
-      cheb_step_kernel<float, true><<<grid_for(n), BLOCK, 0, s>>>((float*)x, (float*)d, (const float*)b,
+      { cheb_step_kernel<float, true><<<grid_for(n), BLOCK, 0, s>>>((float*)x, (float*)d, (const float*)b,
                                                                   (const float*)Ax, (const float*)dinv, (float)c1,
-                                                                  (float)c2, n);
+                                                                  (float)c2, n); note_launches(1); }
     else
-      cheb_step_kernel<float, false><<<grid_for(n), BLOCK, 0, s>>>((float*)x, (float*)d, (const float*)b,
+      { cheb_step_kernel<float, false><<<grid_for(n), BLOCK, 0, s>>>((float*)x, (float*)d, (const float*)b,
                                                                    (const float*)Ax, (const float*)dinv, (float)c1,
-                                                                   (float)c2, n);
+                                                                   (float)c2, n); note_launches(1); }
   }
 }
 
 void launch_residual(bool fp64, void* r, const void* b, const void* Ax, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   if (fp64)
-    residual_kernel<double><<<grid_for(n), BLOCK, 0, s>>>((double*)r, (const double*)b, (const double*)Ax, n);
+    { residual_kernel<double><<<grid_for(n), BLOCK, 0, s>>>((double*)r, (const double*)b, (const double*)Ax, n); note_launches(1); }
   else
-    residual_kernel<float><<<grid_for(n), BLOCK, 0, s>>>((float*)r, (const float*)b, (const float*)Ax, n);
+    { residual_kernel<float><<<grid_for(n), BLOCK, 0, s>>>((float*)r, (const float*)b, (const float*)Ax, n); note_launches(1); }
 }
 
 void launch_axpy(bool fp64, void* y, const void* x, double a, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   if (fp64)
-    axpy_kernel<double><<<grid_for(n), BLOCK, 0, s>>>((double*)y, (const double*)x, a, n);
+    { axpy_kernel<double><<<grid_for(n), BLOCK, 0, s>>>((double*)y, (const double*)x, a, n); note_launches(1); }
   else
-    axpy_kernel<float><<<grid_for(n), BLOCK, 0, s>>>((float*)y, (const float*)x, (float)a, n);
+    { axpy_kernel<float><<<grid_for(n), BLOCK, 0, s>>>((float*)y, (const float*)x, (float)a, n); note_launches(1); }
 }
 
 void launch_coarse_solve(bool fp64, const double* Ainv, int n, const void* b, void* x, cudaStream_t s) {
   if (n <= 0) return;
   if (fp64)
-    coarse_kernel<double><<<1, BLOCK, 0, s>>>(Ainv, n, (const double*)b, (double*)x);
+    { coarse_kernel<double><<<1, BLOCK, 0, s>>>(Ainv, n, (const double*)b, (double*)x); note_launches(1); }
   else
-    coarse_kernel<float><<<1, BLOCK, 0, s>>>(Ainv, n, (const float*)b, (float*)x);
+    { coarse_kernel<float><<<1, BLOCK, 0, s>>>(Ainv, n, (const float*)b, (float*)x); note_launches(1); }
 }
 
 void launch_dot(const double* x, const double* y, int64_t n, double* scratch, double* scal, int slot, int op,
                 cudaStream_t s) {
-  dot_partial<<<DOT_BLOCKS, BLOCK, 0, s>>>(x, y, n, scratch);
-  dot_final<<<1, BLOCK, 0, s>>>(scratch, DOT_BLOCKS, scal, slot, op);
+  { dot_partial<<<DOT_BLOCKS, BLOCK, 0, s>>>(x, y, n, scratch); note_launches(1); }
+  { dot_final<<<1, BLOCK, 0, s>>>(scratch, DOT_BLOCKS, scal, slot, op); note_launches(1); }
 }
 
 void launch_cg_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, int64_t n,
                          double* scratch, double* scal_out, cudaStream_t s) {
-  cg_xr_kernel<<<DOT_BLOCKS, BLOCK, 0, s>>>(x, r, p, q, scal, n, scratch);
-  dot_final<<<1, BLOCK, 0, s>>>(scratch, DOT_BLOCKS, scal_out, 2, DOT_STORE);
+  { cg_xr_kernel<<<DOT_BLOCKS, BLOCK, 0, s>>>(x, r, p, q, scal, n, scratch); note_launches(1); }
+  { dot_final<<<1, BLOCK, 0, s>>>(scratch, DOT_BLOCKS, scal_out, 2, DOT_STORE); note_launches(1); }
 }
 
 void launch_cg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
-  cg_p_kernel<<<grid_for(n), BLOCK, 0, s>>>(p, z, scal, n);
+  { cg_p_kernel<<<grid_for(n), BLOCK, 0, s>>>(p, z, scal, n); note_launches(1); }
 }
 
 }  // namespace gcmg

@@ -228,6 +228,8 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
   L.max_local = 0;
   L.max_sub = 0;
   std::vector<int32_t> lstart_of(ne, -1);
+  // pass 1: every tile numbers the entities it owns (all tiles first, so that
+  // foreign entities owned by later tiles have their numbers in pass 2)
   for (int t = 0; t < nt; ++t) {
     const int c0 = t * tile_cells, c1 = std::min(nc, c0 + tile_cells);
     TileInfo& T = L.tiles[t];
@@ -244,6 +246,13 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
       }
     if (next > 0x7FFFFFFF) throw std::runtime_error("too many DoFs for 32-bit indices");
     T.n_owned = (int32_t)(next - T.dof_begin);
+  }
+  for (int e = 0; e < ne; ++e)
+    if (estart[e] < 0) throw std::runtime_error("entity without an owner tile");
+  // pass 2: tile-local numbering, sub-colours
+  for (int t = 0; t < nt; ++t) {
+    const int c0 = t * tile_cells, c1 = std::min(nc, c0 + tile_cells);
+    TileInfo& T = L.tiles[t];
     // tile-local numbering: owned entities at their offset, foreign ones after
     T.foreign_begin = (int32_t)L.foreign.size();
     int32_t local_next = T.n_owned;
@@ -364,6 +373,101 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
 }
 
 void LevelHost::dof_coordinates(std::vector<double>& xyz) const { xyz = dof_xyz_cache; }
+
+// Check every invariant the tile kernels rely on; throws with a message.
+void validate_level(const LevelHost& L) {
+  auto fail = [](const std::string& m) { throw std::runtime_error("level check: " + m); };
+  const int nc = (int)L.cells.size();
+  const int nt = (int)L.tiles.size();
+  const int k = L.k;
+  auto ndofs = [k](int s) {
+    int nd = 0;
+    if (s % 3 == 1) ++nd;
+    if ((s / 3) % 3 == 1) ++nd;
+    if (s / 9 == 1) ++nd;
+    return ipow(k - 1, nd);
+  };
+  std::vector<int32_t> tile_colour(nt, -1);
+  for (int c = 0; c < L.n_colours; ++c)
+    for (int i = L.colour_ptr[c]; i < L.colour_ptr[c + 1]; ++i) {
+      const int t = L.colour_tiles[i];
+      if (t < 0 || t >= nt || tile_colour[t] >= 0) fail("colour lists do not partition the tiles");
+      tile_colour[t] = c;
+    }
+  for (int t = 0; t < nt; ++t)
+    if (tile_colour[t] < 0) fail("tile without colour");
+  int64_t next = 0;
+  int cnext = 0;
+  std::vector<int32_t> owner_tile(L.n_free, -1);
+  for (int t = 0; t < nt; ++t) {
+    const TileInfo& T = L.tiles[t];
+    if (T.cell_begin != cnext || T.n_cells < 1 || T.n_cells > L.tile_cells) fail("tiles do not partition the cells");
+    cnext += T.n_cells;
+    if (T.dof_begin != next || T.n_owned < 0) fail("owned ranges do not partition the DoFs");
+    for (int i = 0; i < T.n_owned; ++i) owner_tile[T.dof_begin + i] = t;
+    next += T.n_owned;
+    if (T.n_owned + T.n_foreign > L.max_local || L.max_local >= (int)LS_NONE) fail("local size");
+  }
+  if (cnext != nc || next != L.n_free) fail("tiles do not cover cells/DoFs");
+  std::vector<int32_t> lastw(L.n_free, -1);  // tile that last touched a DoF, per colour sweep
+  for (int c = 0; c < L.n_colours; ++c)
+    for (int i = L.colour_ptr[c]; i < L.colour_ptr[c + 1]; ++i) {
+      const int t = L.colour_tiles[i];
+      const TileInfo& T = L.tiles[t];
+      const int nloc = T.n_owned + T.n_foreign;
+      std::vector<int64_t> l2g(nloc);
+      for (int q = 0; q < T.n_owned; ++q) l2g[q] = T.dof_begin + q;
+      for (int q = 0; q < T.n_foreign; ++q) {
+        const int32_t g = L.foreign[T.foreign_begin + q];
+        if (g < 0 || g >= L.n_free) fail("foreign index out of range");
+        if (owner_tile[g] == t) fail("foreign DoF owned by its own tile");
+        if (tile_colour[owner_tile[g]] >= c) fail("foreign DoF owned by a tile of equal or higher colour");
+        l2g[T.n_owned + q] = g;
+      }
+      // cells: local/global consistency and sub-colours
+      const int n = T.n_cells;
+      if (T.n_sub < 1 || L.subptr[T.sub_begin] != 0 || L.subptr[T.sub_begin + T.n_sub] != n) fail("sub-colour offsets");
+      std::vector<char> seen(n, 0);
+      std::vector<int> local_sub(nloc, -1);
+      for (int sc = 0; sc < T.n_sub; ++sc)
+        for (int q = L.subptr[T.sub_begin + sc]; q < L.subptr[T.sub_begin + sc + 1]; ++q) {
+          const int a = L.perm[T.cell_begin + q];
+          if (a >= n || seen[a]) fail("sub-colour permutation");
+          seen[a] = 1;
+          const int ci = T.cell_begin + a;
+          for (int s = 0; s < NSLOT; ++s) {
+            const uint16_t ls = L.meta[ci].ls[s];
+            const int32_t gs = L.gstart[(size_t)ci * NSLOT + s];
+            if ((ls == LS_NONE) != (gs < 0)) fail("local and global maps disagree on a slot");
+            if (ls == LS_NONE) continue;
+            for (int o = 0; o < ndofs(s); ++o) {
+              if (ls + o >= nloc) fail("local index out of range");
+              if (l2g[ls + o] != gs + o) fail("local index maps to the wrong DoF");
+              if (local_sub[ls + o] == sc) fail("two cells of one sub-colour share a DoF");
+              local_sub[ls + o] = sc;
+            }
+          }
+        }
+      // tiles of one colour never share a DoF
+      for (int q = 0; q < nloc; ++q) {
+        const int64_t g = l2g[q];
+        if (lastw[g] >= 0 && lastw[g] != t && tile_colour[lastw[g]] == c) fail("tiles of one colour share a DoF");
+        lastw[g] = t;
+      }
+    }
+  // transfer ownership: every DoF owned by exactly one (cell, slot)
+  std::vector<int8_t> owned(L.n_free, 0);
+  for (int ci = 0; ci < nc; ++ci)
+    for (int s = 0; s < NSLOT; ++s)
+      if ((L.own[ci] >> s) & 1u) {
+        const int32_t gs = L.gstart[(size_t)ci * NSLOT + s];
+        if (gs < 0) fail("owned slot without DoFs");
+        for (int o = 0; o < ndofs(s); ++o)
+          if (owned[gs + o]++) fail("DoF owned twice for the transfer");
+      }
+  for (int64_t g = 0; g < L.n_free; ++g)
+    if (!owned[g]) fail("DoF without a transfer owner");
+}
 
 void build_transfer_h(const LevelHost& fine, const LevelHost& coarse, TransferHost& T) {
   T.kind = 0;

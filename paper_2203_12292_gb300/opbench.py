@@ -1,0 +1,67 @@
+"""Operator microbenchmark: time the matrix-free operator of one level.
+
+    python -m paper_2203_12292_gb300.opbench [--workload q4octant] [--level -1]
+        [--dtype f32|f64] [--reps 20] [--tile-cells 0]
+
+The timed applications run inside an NVTX range named "opbench", so a
+profiler can select exactly them.  Prints one JSON line (ms per application,
+GDoF/s).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = {"q4octant": synth.WORKLOAD_Q4_OCTANT, "q2octant": synth.WORKLOAD_Q2_OCTANT,
+             "q4sphere": synth.WORKLOAD_Q4_SPHERE}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="q4octant", choices=sorted(WORKLOADS))
+    ap.add_argument("--level", type=int, default=-1)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--tile-cells", type=int, default=0)
+    a = ap.parse_args(argv)
+    import torch
+
+    from . import Mesh, Multigrid, build as b
+
+    b.build()
+    w = WORKLOADS[a.workload]
+    mesh = Mesh.from_recipe(w.recipe)
+    mg = Multigrid(mesh, w.degree, p_coarsening=w.p_coarsening, mg_fp32=True, tile_cells=a.tile_cells)
+    lev = a.level if a.level >= 0 else mg.num_levels + a.level
+    n = mg.n_free(lev)
+    dt = torch.float32 if a.dtype == "f32" else torch.float64
+    x = torch.rand(n, dtype=dt, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        mg.vmult(lev, x, y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("opbench")
+    e0.record()
+    for _ in range(a.reps):
+        mg.vmult(lev, x, y)
+    e1.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    info = mg.level_info(lev)
+    print(json.dumps({"workload": w.name, "level": lev, "dtype": a.dtype, "n_free": n, "cells": info.n_cells,
+                      "tiles": info.n_tiles, "colours": info.n_colours, "tile_cells": info.tile_cells,
+                      "ms": ms, "gdofs": n / ms / 1e6}))
+
+
+if __name__ == "__main__":
+    main()

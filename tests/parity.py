@@ -7,6 +7,8 @@ def match(xyz_a: np.ndarray, xyz_b: np.ndarray, tol: float = 1e-10) -> np.ndarra
     """perm such that xyz_a[i] == xyz_b[perm[i]] (within tol); asserts a
     bijection."""
     assert xyz_a.shape == xyz_b.shape, (xyz_a.shape, xyz_b.shape)
+    if len(xyz_a) == 0:
+        return np.zeros(0, dtype=np.int64)
     ka = np.round(xyz_a / tol).astype(np.int64)
     kb = np.round(xyz_b / tol).astype(np.int64)
     ia = np.lexsort(ka.T[::-1])

@@ -90,3 +90,19 @@ def test_point_values_are_numbering_independent():
     p = np.random.default_rng(1).permutation(1000)
     assert np.array_equal(synth.point_values(xyz[p], 5), v[p])
     assert -1 <= v.min() and v.max() < 1 and abs(v.mean()) < 0.1
+
+
+@pytest.mark.parametrize("rec,k,tc", [
+    (synth.octant(3), 1, 0), (synth.octant(4), 2, 0), (synth.octant(4), 4, 0), (synth.octant(5), 3, 0),
+    (synth.cube_octant(3, 1), 2, 0), (synth.sphere(5), 4, 0), (synth.shell(5), 2, 0), (synth.octant(4), 4, 3),
+    (synth.octant(4), 1, 255), (synth.cube_octant(2, 2), 4, 17)], ids=str)
+def test_tile_invariants_all_levels(gcmg, rec, k, tc):
+    m = gcmg.Mesh.from_recipe(rec)
+    for l in range(m.num_levels):
+        m.check_level(l, k, tc)
+
+
+@pytest.mark.slow
+def test_tile_invariants_q4_octant_workload(gcmg):
+    m = gcmg.Mesh.from_recipe(synth.WORKLOAD_Q4_OCTANT.recipe)
+    m.check_level(m.num_levels - 1, 4)
