@@ -164,6 +164,15 @@ int gcmg_coarse_solve(gcmg_handle* h, int fp64, const void* b, void* x);
 int gcmg_vcycle(gcmg_handle* h, const double* b, double* x);
 
 /*
+ * *result = x . y in fp64 (CG inner products, Sec. 2): x, y device arrays of
+ * n doubles, result a device pointer to one double.  Deterministic: every
+ * block sums a fixed contiguous chunk into the handle's partial-sum buffer
+ * and one block adds the partials in a fixed order, so repeated calls give
+ * identical bits.  Asynchronous on the handle's stream.
+ */
+int gcmg_dot(gcmg_handle* h, const double* x, const double* y, int64_t n, double* result);
+
+/*
  * Same operator with host vectors: copies src (host, n_free values) to the
  * device, applies the operator, copies the result into dst (host) and
  * synchronises.  Pinned host memory gives full copy bandwidth.

@@ -70,6 +70,7 @@ _SIGS = {
     "gcmg_level_dof_coords": (_c_int, [_c_void_p, _c_int, _c_void_p]),
     "gcmg_vmult": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
     "gcmg_vmult_host": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
+    "gcmg_dot": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int64, _c_void_p]),
     "gcmg_set_profiling": (_c_int, [_c_void_p, _c_int]),
     "gcmg_get_profile": (_c_int, [_c_void_p, _c_int, _c_int, ctypes.POINTER(_c_int64), ctypes.POINTER(_c_double)]),
     "gcmg_diagonal": (_c_int, [_c_void_p, _c_int, _c_void_p]),
@@ -253,6 +254,15 @@ class Multigrid:
             raise ValueError("host vectors must be contiguous")
         _check(lib().gcmg_vmult_host(self._h, level, int(src.dtype == np.float64), src.ctypes.data_as(_c_void_p),
                                      dst.ctypes.data_as(_c_void_p)))
+
+    def dot(self, x, y, out=None):
+        """fp64 inner product on the device (deterministic); returns a 1-element tensor."""
+        import torch
+        n = x.numel()
+        if out is None:
+            out = torch.empty(1, dtype=torch.float64, device="cuda")
+        _check(lib().gcmg_dot(self._h, _ptr(x, n, torch.float64), _ptr(y, n, torch.float64), n, _ptr(out, 1)))
+        return out
 
     def set_profiling(self, on: bool) -> None:
         _check(lib().gcmg_set_profiling(self._h, int(on)))

@@ -718,6 +718,19 @@ int gcmg_get_profile(gcmg_handle* h, int level, int stage, int64_t* count, doubl
   });
 }
 
+int gcmg_dot(gcmg_handle* h, const double* x, const double* y, int64_t n, double* result) {
+  return guarded([&] {
+    if (!h || !result || n < 0 || (n > 0 && (!x || !y))) throw Error(GCMG_ERR_ARG, "bad arguments");
+    Handle& H = h->h;
+    if (n == 0) {
+      ck(cudaMemsetAsync(result, 0, sizeof(double), H.stream), "memset");
+      return;
+    }
+    launch_dot(x, y, n, H.scratch.as<double>(), result, 0, DOT_STORE, H.stream);
+    ck(cudaGetLastError(), "dot");
+  });
+}
+
 int gcmg_vmult_host(gcmg_handle* h, int level, int fp64, const void* src, void* dst) {
   return guarded([&] {
     if (!h) throw Error(GCMG_ERR_ARG, "null handle");

@@ -257,3 +257,15 @@ def test_single_cell_q1_has_no_dofs(gcmg):
     b = torch.zeros(0, dtype=torch.float64, device="cuda")
     st = mg.cg_solve(b, torch.zeros_like(b), 1e-8, 10)
     assert st.iterations == 0
+
+
+@pytest.mark.parametrize("n", [1, 255, 1000, 304 * 256 + 17, 3_000_001])
+def test_dot_fp64(gcmg, n):
+    mg = gcmg.Multigrid(gcmg.Mesh(0.0, 1.0, [(0,)]), 2)
+    x = torch.tensor(synth.uniform_vector(n, 1), dtype=torch.float64, device="cuda")
+    y = torch.tensor(synth.uniform_vector(n, 2), dtype=torch.float64, device="cuda")
+    r1 = mg.dot(x, y).item()
+    r2 = mg.dot(x, y).item()
+    ref = float(np.dot(synth.uniform_vector(n, 1), synth.uniform_vector(n, 2)))
+    assert r1 == r2  # deterministic
+    assert abs(r1 - ref) <= 1e-13 * max(1.0, np.sqrt(n))
