@@ -173,6 +173,32 @@ int gcmg_vcycle(gcmg_handle* h, const double* b, double* x);
 int gcmg_dot(gcmg_handle* h, const double* x, const double* y, int64_t n, double* result);
 
 /*
+ * The same fp64 inner product for callers that cannot allocate device
+ * memory: no handle, no cudaMalloc/cudaFree, no allocating library call.
+ * Such callers include code that runs while stream capture is recording a
+ * graph (an allocation would synchronise the device and invalidate the
+ * capture), plugins embedded in an application that owns and pre-reserves
+ * all of the GPU's memory, and real-time loops where a failed or slow
+ * allocation is not acceptable.  The paper has no counterpart of this entry
+ * point; it is a service of this library.
+ *
+ * x, y: device arrays of n doubles; result: device pointer to one double;
+ * stream: a cudaStream_t (NULL = legacy default stream).  The partial sums
+ * (one per 8192 consecutive elements, added in a fixed order, so the result
+ * is reproducible bit for bit) are kept in a fixed 512 KiB device array
+ * inside the library, one per GPU that loads it, held until the process
+ * exits.  Hence n <= 65536 * 8192 = 536,870,912; larger n is rejected with
+ * GCMG_ERR_ARG and a message.
+ *
+ * The first call on a device looks up that device's array (with the device
+ * current); make that first call before any stream capture.  All calls on
+ * one device share the array and it keeps the last call's partial sums:
+ * calls that overlap on the GPU (other streams, other host threads) race
+ * and must be ordered by the caller.  Asynchronous on `stream`.
+ */
+int gcmg_dot_noalloc(const double* x, const double* y, int64_t n, double* result, void* stream);
+
+/*
  * Same operator with host vectors: copies src (host, n_free values) to the
  * device, applies the operator, copies the result into dst (host) and
  * synchronises.  Pinned host memory gives full copy bandwidth.

@@ -71,6 +71,7 @@ _SIGS = {
     "gcmg_vmult": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
     "gcmg_vmult_host": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
     "gcmg_dot": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int64, _c_void_p]),
+    "gcmg_dot_noalloc": (_c_int, [_c_void_p, _c_void_p, _c_int64, _c_void_p, _c_void_p]),
     "gcmg_set_profiling": (_c_int, [_c_void_p, _c_int]),
     "gcmg_get_profile": (_c_int, [_c_void_p, _c_int, _c_int, ctypes.POINTER(_c_int64), ctypes.POINTER(_c_double)]),
     "gcmg_diagonal": (_c_int, [_c_void_p, _c_int, _c_void_p]),

@@ -731,6 +731,16 @@ int gcmg_dot(gcmg_handle* h, const double* x, const double* y, int64_t n, double
   });
 }
 
+int gcmg_dot_noalloc(const double* x, const double* y, int64_t n, double* result, void* stream) {
+  return guarded([&] {
+    if (!result || n < 0 || (n > 0 && (!x || !y))) throw Error(GCMG_ERR_ARG, "bad arguments");
+    if (n > dot_noalloc_max_n())
+      throw Error(GCMG_ERR_ARG, "gcmg_dot_noalloc: n = " + std::to_string(n) + " exceeds the maximum " +
+                                    std::to_string(dot_noalloc_max_n()) + " (fixed partial-sum array)");
+    ck(launch_dot_noalloc(x, y, n, result, static_cast<cudaStream_t>(stream)), "gcmg_dot_noalloc");
+  });
+}
+
 int gcmg_vmult_host(gcmg_handle* h, int level, int fp64, const void* src, void* dst) {
   return guarded([&] {
     if (!h) throw Error(GCMG_ERR_ARG, "null handle");

@@ -84,6 +84,10 @@ constexpr int DOT_BLOCKS = 304;
 enum DotOp { DOT_STORE = 0, DOT_ALPHA = 1, DOT_BETA = 2 };
 void launch_dot(const double* x, const double* y, int64_t n, double* scratch, double* scal, int slot, int op,
                 cudaStream_t s);
+// inner product with the partial sums in a fixed device array (no allocation);
+// n <= dot_noalloc_max_n()
+int64_t dot_noalloc_max_n();
+cudaError_t launch_dot_noalloc(const double* x, const double* y, int64_t n, double* result, cudaStream_t s);
 // CG updates with device scalars: scal[0] = rz, [1] = pq, [2] = rr, [3] = alpha, [4] = beta, [5] = rz_new
 void launch_cg_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, int64_t n,
                          double* scratch, double* scal_out, cudaStream_t s);

@@ -8,6 +8,9 @@
 //   (small, fp64) level-0 matrix.
 // * CG (Sec. 2): fp64 inner products, reduced deterministically in two
 //   stages (fixed grid, fixed order), scalars kept on the device.
+#include <mutex>
+#include <string>
+
 #include "device.cuh"
 #include "kernels.h"
 
@@ -265,6 +268,75 @@ void launch_cg_update_xr(double* x, double* r, const double* p, const double* q,
                          double* scratch, double* scal_out, cudaStream_t s) {
   { cg_xr_kernel<<<DOT_BLOCKS, BLOCK, 0, s>>>(x, r, p, q, scal, n, scratch); note_launches(1); }
   { dot_final<<<1, BLOCK, 0, s>>>(scratch, DOT_BLOCKS, scal_out, 2, DOT_STORE); note_launches(1); }
+}
+
+// ---------------------------------------------------------------------------
+// Inner product without any device allocation: the partial sums live in a
+// fixed device array of this translation unit instead of a buffer that a
+// handle allocates.  One partial per NOALLOC_CHUNK consecutive elements,
+// summed in a fixed order, so results are reproducible bit for bit.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t NOALLOC_CHUNK = 8192;
+constexpr int NOALLOC_MAX_PARTIALS = 65536;  // 512 KiB per device
+constexpr int MAX_DEVICES = 64;
+
+static __device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_PARTIALS];
+
+__global__ void __launch_bounds__(BLOCK) dot_chunk_partial(const double* x, const double* y, int64_t n, double* part) {
+  __shared__ double sh[BLOCK];
+  const int64_t i0 = (int64_t)blockIdx.x * NOALLOC_CHUNK;
+  const int64_t i1 = min(n, i0 + NOALLOC_CHUNK);
+  double s = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += BLOCK) s += x[i] * y[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(BLOCK) dot_chunk_final(const double* part, int np, double* result) {
+  __shared__ double sh[BLOCK];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += BLOCK) s += part[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *result = s;
+}
+
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[MAX_DEVICES] = {};
+
+}  // namespace
+
+int64_t dot_noalloc_max_n() { return NOALLOC_CHUNK * (int64_t)NOALLOC_MAX_PARTIALS; }
+
+// Device address of this device's partial-sum array.  Looked up once per
+// device, with that device current, on the first call; host code must not
+// pass the symbol itself to a kernel (it is a host-side stand-in).
+static cudaError_t noalloc_partials(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    double* p = nullptr;
+    e = cudaGetSymbolAddress((void**)&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+cudaError_t launch_dot_noalloc(const double* x, const double* y, int64_t n, double* result, cudaStream_t s) {
+  double* part = nullptr;
+  cudaError_t e = noalloc_partials(&part);
+  if (e != cudaSuccess) return e;
+  if (n == 0) return cudaMemsetAsync(result, 0, sizeof(double), s);
+  const int np = (int)((n + NOALLOC_CHUNK - 1) / NOALLOC_CHUNK);
+  { dot_chunk_partial<<<np, BLOCK, 0, s>>>(x, y, n, part); note_launches(1); }
+  { dot_chunk_final<<<1, BLOCK, 0, s>>>(part, np, result); note_launches(1); }
+  return cudaGetLastError();
 }
 
 void launch_cg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t s) {
