@@ -116,10 +116,10 @@ typedef struct {
   int64_t n_cells;
   int degree;
   int n_tiles;
-  int n_colours;     /* tile colours = launches per cell loop */
   int tile_cells;
   int max_local;     /* largest tile-local DoF count */
   int fp32;          /* level vectors of the V-cycle are fp32 */
+  int64_t n_halo;    /* DoFs that receive contributions from more than one tile */
 } gcmg_level_info;
 
 int gcmg_num_levels(const gcmg_handle* h, int* n);

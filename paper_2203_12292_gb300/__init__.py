@@ -45,7 +45,7 @@ class Config(ctypes.Structure):
 
 class LevelInfo(ctypes.Structure):
     _fields_ = [("n_free", _c_int64), ("n_cells", _c_int64), ("degree", _c_int), ("n_tiles", _c_int),
-                ("n_colours", _c_int), ("tile_cells", _c_int), ("max_local", _c_int), ("fp32", _c_int)]
+                ("tile_cells", _c_int), ("max_local", _c_int), ("fp32", _c_int), ("n_halo", _c_int64)]
 
 
 class SolveStats(ctypes.Structure):

@@ -68,7 +68,8 @@ struct DevBuf {
 struct LevelDev {
   LevelHost host;
   bool fp32 = true;
-  DevBuf tiles, colour_tiles, meta, foreign, subptr, perm, cell_ijk, gstart, own, mask;
+  DevBuf tiles, meta, foreign, subptr, perm, cell_ijk, gstart, own, mask;
+  DevBuf halo, halo_dofs, halo_ptr, halo_src;
   DevBuf diag64, dinv64, dinv32;
   DevBuf x, b, d, t;        // V-cycle vectors in level precision
   DevBuf w64a, w64b, w64c;  // fp64 work vectors (set-up, fp64 smoothing through the API)
@@ -124,13 +125,7 @@ struct Handle {
 
 namespace {
 
-int default_tile_cells(int k) {
-  switch (k) {
-    case 1: return 128;
-    case 2: return 64;
-    default: return 32;
-  }
-}
+int default_tile_cells(int) { return 128; }
 
 void check_level(const Handle& h, int level) {
   if (level < 0 || level >= (int)h.lev.size()) throw Error(GCMG_ERR_ARG, "level out of range");
@@ -548,7 +543,10 @@ int gcmg_setup(const gcmg_mesh* mesh, const gcmg_config* cfg, void* stream, gcmg
       L->fp32 = cfg->mg_fp32 != 0;
       LevelHost& lh = L->host;
       L->tiles.upload(lh.tiles, H.stream);
-      L->colour_tiles.upload(lh.colour_tiles, H.stream);
+      L->halo.alloc(lh.foreign.size() * sizeof(double));
+      L->halo_dofs.upload(lh.halo_dofs, H.stream);
+      L->halo_ptr.upload(lh.halo_ptr, H.stream);
+      L->halo_src.upload(lh.halo_src, H.stream);
       L->meta.upload(lh.meta, H.stream);
       L->foreign.upload(lh.foreign, H.stream);
       L->subptr.upload(lh.subptr, H.stream);
@@ -565,9 +563,12 @@ int gcmg_setup(const gcmg_mesh* mesh, const gcmg_config* cfg, void* stream, gcmg
       L->mask.upload(lh.mask, H.stream);
       CellLaunch& c = L->cl;
       c.tiles = L->tiles.as<TileInfo>();
-      c.colour_tiles = L->colour_tiles.as<int32_t>();
-      c.colour_ptr = lh.colour_ptr.data();
-      c.n_colours = lh.n_colours;
+      c.n_tiles = (int)lh.tiles.size();
+      c.halo = L->halo.p;
+      c.halo_dofs = L->halo_dofs.as<int32_t>();
+      c.halo_ptr = L->halo_ptr.as<int32_t>();
+      c.halo_src = L->halo_src.as<int32_t>();
+      c.n_halo = (int)lh.halo_dofs.size();
       c.meta = L->meta.as<CellMeta>();
       c.foreign = L->foreign.as<int32_t>();
       c.subptr = L->subptr.as<uint16_t>();
@@ -674,7 +675,7 @@ int gcmg_get_level_info(const gcmg_handle* h, int level, gcmg_level_info* info) 
     info->n_cells = (int64_t)L.host.cells.size();
     info->degree = L.host.k;
     info->n_tiles = (int)L.host.tiles.size();
-    info->n_colours = L.host.n_colours;
+    info->n_halo = (int64_t)L.host.halo_dofs.size();
     info->tile_cells = L.host.tile_cells;
     info->max_local = L.host.max_local;
     info->fp32 = L.fp32 ? 1 : 0;

@@ -6,7 +6,9 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
+#include <stdexcept>
 
 #include "internal.h"
 
@@ -23,6 +25,9 @@ struct DevTables {
   T gq[NMAX], gw[NMAX];     // Gauss points and weights on [0,1]
   T Ph[2 * KMAX + 1][NMAX]; // h-prolongation onto the 2k+1 child nodes
   T Pp[NMAX][NMAX];         // p-prolongation from degree floor(k/2) to k
+  T Be[NMAX][NMAX];         // rows of B reordered: symmetric modes first, then antisymmetric
+  T lame[NMAX];             // eigenvalues in the same order
+  T lam3[(KMAX + 1) * (KMAX + 1) * (KMAX + 1)];  // lame[a] + lame[b] + lame[c], a fastest
 };
 
 // every translation unit holds its own copy of the tables (no relocatable
@@ -65,9 +70,39 @@ static inline void fill_tables(DevTables<double>* td, DevTables<float>* tf) {
     for (int i = 0; i < 2 * KMAX + 1; ++i)
       for (int j = 0; j < NMAX; ++j) d.Ph[i][j] = b.Ph[i][j];
     if (k >= 2) p_prolongation(k, k / 2, d.Pp);
+    {
+      // even-odd order of the modes: rows of B are symmetric or antisymmetric
+      // under x -> 1 - x (the 1D pencil (K, M) is persymmetric)
+      const int n = k + 1;
+      int order[NMAX], ne = 0, no = 0, odd[NMAX];
+      for (int r = 0; r < n; ++r) {
+        double se = 0, so = 0, mx = 0;
+        for (int j = 0; j < n; ++j) {
+          se = std::max(se, std::fabs(b.B[r][j] - b.B[r][n - 1 - j]));
+          so = std::max(so, std::fabs(b.B[r][j] + b.B[r][n - 1 - j]));
+          mx = std::max(mx, std::fabs(b.B[r][j]));
+        }
+        if (se <= 1e-9 * mx)
+          order[ne++] = r;
+        else if (so <= 1e-9 * mx)
+          odd[no++] = r;
+        else
+          throw std::runtime_error("basis mode without parity");
+      }
+      if (ne != (n + 1) / 2 || no != n / 2) throw std::runtime_error("unexpected mode parities");
+      for (int i = 0; i < no; ++i) order[ne + i] = odd[i];
+      for (int r = 0; r < n; ++r) {
+        d.lame[r] = b.lam[order[r]];
+        for (int j = 0; j < n; ++j) d.Be[r][j] = b.B[order[r]][j];
+      }
+      for (int c = 0; c < n; ++c)
+        for (int bb = 0; bb < n; ++bb)
+          for (int a = 0; a < n; ++a) d.lam3[a + n * (bb + n * c)] = d.lame[a] + d.lame[bb] + d.lame[c];
+    }
     DevTables<float>& f = tf[k];
     const double* src = reinterpret_cast<const double*>(&d);
     float* dstf = reinterpret_cast<float*>(&f);
+    static_assert(sizeof(DevTables<double>) == 2 * sizeof(DevTables<float>), "table layout");
     for (size_t i = 0; i < sizeof(DevTables<double>) / sizeof(double); ++i) dstf[i] = (float)src[i];
   }
 }
@@ -254,6 +289,97 @@ __device__ __forceinline__ void cell_laplace(T* cb, const T* sm_h, int ncells) {
   __syncthreads();
   sweep_B<K, 0, true>(cb, ncells);
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// register-resident sweeps for one cell held by one thread (array u of
+// N^3 values, compile-time indices only so that u stays in registers)
+// ---------------------------------------------------------------------------
+
+// forward transform with B along a line (BASE + i*STRIDE), even-odd form:
+// symmetric modes from the sums u_j + u_{N-1-j}, antisymmetric ones from
+// the differences; results stored in mode order (symmetric modes first)
+template <int N, int BASE, int STRIDE, typename T>
+__device__ __forceinline__ void eo_forward(T* u, const T (&Be)[NMAX][NMAX]) {
+  constexpr int NH = N / 2, NE = (N + 1) / 2;
+  T e[NE], o[NH > 0 ? NH : 1];
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    e[j] = u[BASE + j * STRIDE] + u[BASE + (N - 1 - j) * STRIDE];
+    o[j] = u[BASE + j * STRIDE] - u[BASE + (N - 1 - j) * STRIDE];
+  }
+  if (N % 2) e[NH] = u[BASE + NH * STRIDE];
+#pragma unroll
+  for (int r = 0; r < NE; ++r) {
+    T s = (N % 2) ? Be[r][NH] * e[NH] : T(0);
+#pragma unroll
+    for (int j = 0; j < NH; ++j) s += Be[r][j] * e[j];
+    u[BASE + r * STRIDE] = s;
+  }
+#pragma unroll
+  for (int r = 0; r < NH; ++r) {
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < NH; ++j) s += Be[NE + r][j] * o[j];
+    u[BASE + (NE + r) * STRIDE] = s;
+  }
+}
+
+// backward transform with B^T (modes in mode order -> nodal values)
+template <int N, int BASE, int STRIDE, typename T>
+__device__ __forceinline__ void eo_backward(T* u, const T (&Be)[NMAX][NMAX]) {
+  constexpr int NH = N / 2, NE = (N + 1) / 2;
+  T E[NE], O[NH > 0 ? NH : 1];
+#pragma unroll
+  for (int j = 0; j < NE; ++j) {
+    T s = T(0);
+#pragma unroll
+    for (int r = 0; r < NE; ++r) s += Be[r][j] * u[BASE + r * STRIDE];
+    E[j] = s;
+  }
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    T s = T(0);
+#pragma unroll
+    for (int r = 0; r < NH; ++r) s += Be[NE + r][j] * u[BASE + (NE + r) * STRIDE];
+    O[j] = s;
+  }
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    u[BASE + j * STRIDE] = E[j] + O[j];
+    u[BASE + (N - 1 - j) * STRIDE] = E[j] - O[j];
+  }
+  if (N % 2) u[BASE + NH * STRIDE] = E[NH];
+}
+
+template <int N, int D, bool FWD, int L = 0, typename T>
+__device__ __forceinline__ void eo_sweep(T* u, const T (&Be)[NMAX][NMAX]) {
+  if constexpr (L < N * N) {
+    constexpr int a = L % N, b = L / N;
+    constexpr int BASE = (D == 0) ? N * (a + N * b) : (D == 1 ? a + N * N * b : a + N * b);
+    constexpr int STRIDE = (D == 0) ? 1 : (D == 1 ? N : N * N);
+    if (FWD)
+      eo_forward<N, BASE, STRIDE>(u, Be);
+    else
+      eo_backward<N, BASE, STRIDE>(u, Be);
+    eo_sweep<N, D, FWD, L + 1>(u, Be);
+  }
+}
+
+// the cell operator h (K x M x M + M x K x M + M x M x K) on one cell in
+// registers: B in x, y, z, scale by h (lam_a + lam_b + lam_c), B^T back
+template <int K, typename T>
+__device__ __forceinline__ void cell_laplace_regs(T* u, T h) {
+  constexpr int N = K + 1, N3 = N * N * N;
+  const DevTables<T>& tb = tab<T>(K);
+  eo_sweep<N, 0, true>(u, tb.Be);
+  eo_sweep<N, 1, true>(u, tb.Be);
+  eo_sweep<N, 2, true>(u, tb.Be);
+#pragma unroll
+  for (int n = 0; n < N3; ++n) u[n] *= h * tb.lam3[n];
+  eo_sweep<N, 2, false>(u, tb.Be);
+  eo_sweep<N, 1, false>(u, tb.Be);
+  eo_sweep<N, 0, false>(u, tb.Be);
 }
 
 }  // namespace gcmg

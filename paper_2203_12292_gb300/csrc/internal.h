@@ -33,7 +33,8 @@ struct CellMeta {
   uint16_t ls[NSLOT];  // tile-local start of each slot's DoFs, LS_NONE = none
   uint16_t mask;
   uint8_t level;
-  uint8_t pad[7];
+  uint8_t sub;         // sub-colour inside the tile
+  uint8_t pad[6];
 };
 static_assert(sizeof(CellMeta) == 64, "CellMeta must be 64 bytes");
 
@@ -111,16 +112,16 @@ struct LevelHost {
   std::vector<uint32_t> own;       // per cell: 27-bit mask, slot entity is owned by this cell (transfer)
   int64_t n_free = 0;
   // tiles
-  int tile_cells = 32;
+  int tile_cells = 128;
   std::vector<TileInfo> tiles;
   std::vector<CellMeta> meta;      // per cell
   std::vector<int32_t> foreign;    // foreign DoF global indices, per tile contiguous
   std::vector<uint16_t> subptr;    // per tile: n_sub+1 offsets into the tile's permuted cell list
   std::vector<uint8_t> perm;       // per cell (tile order): local cell index in sub-colour order
-  std::vector<int32_t> colour_ptr; // tile colours: tiles of colour c are colour_tiles[colour_ptr[c]..]
-  std::vector<int32_t> colour_tiles;
+  std::vector<int32_t> halo_dofs;  // DoFs that receive contributions from other tiles (increasing)
+  std::vector<int32_t> halo_ptr;   // per halo DoF: range into halo_src
+  std::vector<int32_t> halo_src;   // foreign-slot indices (positions in `foreign`)
   int max_local = 0;               // max tile-local DoF count
-  int n_colours = 0;
   int max_sub = 0;
   // dof coordinates (host) for checks
   std::vector<double> dof_xyz_cache;

@@ -17,19 +17,23 @@ enum CellMode { MODE_VMULT = 0, MODE_RHS = 1, MODE_DIAG = 2 };
 // arguments of the tile kernels (operator, right-hand side, diagonal)
 struct CellLaunch {
   const TileInfo* tiles;
-  const int32_t* colour_tiles;  // all tiles sorted by colour
-  const int32_t* colour_ptr;    // host array, n_colours + 1
-  int n_colours;
+  int n_tiles;
   const CellMeta* meta;
   const int32_t* foreign;
   const uint16_t* subptr;
   const uint8_t* perm;
   const int32_t* cell_ijk;  // per cell i, j, k (right-hand side only)
+  // halo: one slot per (tile, foreign DoF); per halo DoF the slots to add
+  void* halo;  // n_foreign_total values of the launch precision
+  const int32_t* halo_dofs;
+  const int32_t* halo_ptr;
+  const int32_t* halo_src;
+  int n_halo;
   int k;
   int tc;
   int max_local;
+  int use_lines;  // 1: fp32 operator with the line-parallel kernel
   double lo, dom;
-  size_t smem_bytes;
 };
 
 struct RhsDesc {
@@ -44,6 +48,8 @@ void launch_rhs(const CellLaunch& L, const RhsDesc& f, double* dst, cudaStream_t
 void launch_diag(const CellLaunch& L, const double* diag_tab, double* dst, cudaStream_t s);
 // diag_tab[m * (k+1)^3 + j] = (C_m^T A_ref C_m)_{jj} for all 512 masks m
 void launch_diag_table(int k, double* diag_tab, cudaStream_t s);
+// second pass of every tile loop: dst[g] += halo slots of g, fixed order
+void launch_halo_add(const CellLaunch& L, bool fp64, void* dst, cudaStream_t s);
 size_t cell_smem_bytes(int k, bool fp64, int tc, int max_local);
 
 // transfer between levels; fine_of/refined per coarse cell

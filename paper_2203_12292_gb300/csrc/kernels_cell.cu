@@ -14,14 +14,20 @@
 //      direction (Sec. 3.2, hanging-node application);
 //   4. S^T Q S: for an axis-parallel cube the Laplace cell operator equals
 //      h (K x M x M + M x K x M + M x M x K); it is applied in the fast
-//      diagonalisation form h B^T^{(x)3} diag(lam_a+lam_b+lam_c) B^{(x)3}:
-//      six 1D sweeps, the middle two fused with the scaling in registers;
+//      diagonalisation form h B^T^{(x)3} diag(lam_a+lam_b+lam_c) B^{(x)3};
 //   5. C_e^T, then G_e^T into a shared-memory accumulator, sub-colour by
-//      sub-colour (cells sharing an entity never add at the same time);
-//   6. owned DoFs are written with plain coalesced stores, foreign DoFs are
-//      added; tiles are launched colour by colour, the owner of a DoF having
-//      the lowest colour, so no atomics are needed and results are
-//      bit-reproducible.
+//      sub-colour (cells that share an entity never add at the same time);
+//   6. owned DoFs are written with plain coalesced stores; contributions to
+//      DoFs owned by other tiles go to this tile's halo slots, which a second
+//      kernel adds in a fixed order.  No atomics: results are reproducible
+//      bit for bit.
+//
+// Two implementations of steps 2-5:
+// * cell_kernel: one 1D line per thread, cells in shared memory, processed in
+//   chunks (fp64 operator, right-hand side, diagonal);
+// * vmult_regs: one cell per thread with all (k+1)^3 values in registers and
+//   the sweeps in even-odd form (fp32 operator of the V-cycle).
+#include <algorithm>
 #include <cstdio>
 
 #include "device.cuh"
@@ -33,10 +39,11 @@ GCMG_DEFINE_UPLOAD(upload_tables_cell)
 
 namespace {
 
+constexpr int CHUNK = 32;  // cells per shared-memory chunk of cell_kernel
+
 template <typename T>
 struct CellArgs {
   const TileInfo* tiles;
-  const int32_t* tile_list;
   const CellMeta* meta;
   const int32_t* foreign;
   const uint16_t* subptr;
@@ -44,6 +51,7 @@ struct CellArgs {
   const int32_t* cell_ijk;
   const T* src;
   T* dst;
+  T* halo;
   double lo, dom;
   int tc;
   int max_local;
@@ -55,7 +63,7 @@ struct CellArgs {
 };
 
 struct SmemLayout {
-  size_t meta, h, mask, cb, xs, ys, total;
+  size_t meta, h, mask, cell, cb, xs, ys, total;
 };
 
 template <typename T>
@@ -65,18 +73,47 @@ __host__ __device__ inline SmemLayout smem_layout(int n3, int tc, int max_local)
   L.meta = o;
   o += (size_t)tc * sizeof(CellMeta);
   L.h = o;
-  o += (size_t)tc * sizeof(T);
+  o += (size_t)CHUNK * sizeof(T);
   L.mask = o;
-  o += (size_t)tc * sizeof(uint16_t);
+  o += (size_t)CHUNK * sizeof(uint16_t);
+  L.cell = o;
+  o += (size_t)CHUNK * sizeof(uint16_t);
   o = (o + 15) & ~(size_t)15;
   L.cb = o;
-  o += (size_t)tc * n3 * sizeof(T);
+  o += (size_t)CHUNK * n3 * sizeof(T);
   L.xs = o;
   o += (size_t)max_local * sizeof(T);
   L.ys = o;
   o += (size_t)max_local * sizeof(T);
   L.total = (o + 15) & ~(size_t)15;
   return L;
+}
+
+// stage the tile's cell metadata (64 B per cell, 16-byte loads)
+__device__ __forceinline__ void load_meta(CellMeta* sm_meta, const CellMeta* meta, int cell_begin, int nc) {
+  const uint4* g = reinterpret_cast<const uint4*>(meta + cell_begin);
+  uint4* s = reinterpret_cast<uint4*>(sm_meta);
+  for (int i = threadIdx.x; i < nc * 4; i += blockDim.x) s[i] = g[i];
+}
+
+template <typename T>
+__device__ __forceinline__ void load_tile_dofs(T* xs, const T* src, const int32_t* foreign, const TileInfo& ti) {
+  const T* s = src + ti.dof_begin;
+  for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) xs[i] = s[i];
+  const int32_t* fl = foreign + ti.foreign_begin;
+  for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) xs[ti.n_owned + i] = src[fl[i]];
+}
+
+// owned DoFs: plain stores (or additions); foreign DoFs: into the halo slots
+template <typename T>
+__device__ __forceinline__ void write_tile_dofs(T* dst, T* halo, const T* ys, const TileInfo& ti, int add) {
+  T* d = dst + ti.dof_begin;
+  if (add)
+    for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) d[i] += ys[i];
+  else
+    for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) d[i] = ys[i];
+  T* h = halo + ti.foreign_begin;
+  for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) h[i] = ys[ti.n_owned + i];
 }
 
 template <int K, typename T, int MODE>
@@ -87,126 +124,249 @@ __global__ void __launch_bounds__(BLOCK) cell_kernel(CellArgs<T> A) {
   CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem + SL.meta);
   T* sm_h = reinterpret_cast<T*>(smem + SL.h);
   uint16_t* sm_mask = reinterpret_cast<uint16_t*>(smem + SL.mask);
+  uint16_t* sm_cell = reinterpret_cast<uint16_t*>(smem + SL.cell);
   T* cb = reinterpret_cast<T*>(smem + SL.cb);
   T* xs = reinterpret_cast<T*>(smem + SL.xs);
   T* ys = reinterpret_cast<T*>(smem + SL.ys);
 
-  const TileInfo ti = A.tiles[A.tile_list[blockIdx.x]];
+  const TileInfo ti = A.tiles[blockIdx.x];
   const int nc = ti.n_cells;
   const int nloc = ti.n_owned + ti.n_foreign;
-  {
-    const uint4* g = reinterpret_cast<const uint4*>(A.meta + ti.cell_begin);
-    uint4* s = reinterpret_cast<uint4*>(sm_meta);
-    for (int i = threadIdx.x; i < nc * 4; i += blockDim.x) s[i] = g[i];
-  }
-  if (MODE == MODE_VMULT) {
-    const T* src = A.src + ti.dof_begin;
-    for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) xs[i] = src[i];
-    const int32_t* fl = A.foreign + ti.foreign_begin;
-    for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) xs[ti.n_owned + i] = A.src[fl[i]];
-  }
+  load_meta(sm_meta, A.meta, ti.cell_begin, nc);
+  if (MODE == MODE_VMULT) load_tile_dofs(xs, A.src, A.foreign, ti);
   for (int i = threadIdx.x; i < nloc; i += blockDim.x) ys[i] = T(0);
-  __syncthreads();
-  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-    sm_mask[c] = sm_meta[c].mask;
-    sm_h[c] = (T)ldexp(A.dom, -(int)sm_meta[c].level);
-  }
-  if (MODE == MODE_VMULT) {
-    // G_e: gather x-lines of every cell
-    for (int t = threadIdx.x; t < nc * N2; t += blockDim.x) {
-      const int cell = t / N2, r = t - cell * N2;
-      const int b = r % N, c = r / N;
-      const uint16_t* ls = sm_meta[cell].ls;
-      T* out = cb + cell * N3 + N * r;
+  // chunks of CHUNK cells in sub-colour order
+  for (int c0 = 0; c0 < nc; c0 += CHUNK) {
+    const int nch = min(CHUNK, nc - c0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < nch; j += blockDim.x) {
+      const int cell = A.perm[ti.cell_begin + c0 + j];
+      sm_cell[j] = (uint16_t)cell;
+      sm_mask[j] = sm_meta[cell].mask;
+      sm_h[j] = (T)ldexp(A.dom, -(int)sm_meta[cell].level);
+    }
+    __syncthreads();
+    if (MODE == MODE_VMULT) {
+      // G_e: gather x-lines of every cell of the chunk
+      for (int t = threadIdx.x; t < nch * N2; t += blockDim.x) {
+        const int j = t / N2, r = t - j * N2;
+        const int b = r % N, c = r / N;
+        const uint16_t* ls = sm_meta[sm_cell[j]].ls;
+        T* out = cb + j * N3 + N * r;
 #pragma unroll
-      for (int a = 0; a < N; ++a) {
-        int slot, off;
-        node_slot<K>(a, b, c, slot, off);
-        const uint16_t l = ls[slot];
-        out[a] = (l == LS_NONE) ? T(0) : xs[l + off];
-      }
-    }
-  } else if (MODE == MODE_DIAG) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < nc * N3; t += blockDim.x) {
-      const int cell = t / N3, n = t - cell * N3;
-      cb[t] = (T)(A.diag_tab[(sm_mask[cell] & 0x1FF) * N3 + n]) * sm_h[cell];
-    }
-  } else {  // MODE_RHS: h^3 w_q f(x_q) at the Gauss points, then S^T
-    __syncthreads();
-    const DevTables<T>& tb = tab<T>(K);
-    for (int t = threadIdx.x; t < nc * N3; t += blockDim.x) {
-      const int cell = t / N3, n = t - cell * N3;
-      const int qa = n % N, qb = (n / N) % N, qc = n / N2;
-      const int ci = ti.cell_begin + cell;
-      const double h = ldexp(A.dom, -(int)sm_meta[cell].level);
-      const double x = A.lo + h * (A.cell_ijk[3 * ci + 0] + (double)tab<double>(K).gq[qa]);
-      const double y = A.lo + h * (A.cell_ijk[3 * ci + 1] + (double)tab<double>(K).gq[qb]);
-      const double z = A.lo + h * (A.cell_ijk[3 * ci + 2] + (double)tab<double>(K).gq[qc]);
-      double f = 1.0;
-      if (A.n_modes > 0) {
-        f = 0.0;
-        for (int m = 0; m < A.n_modes; ++m) {
-          const double* md = A.modes + 4 * m;
-          f += cos(2.0 * M_PI * (md[0] * x + md[1] * y + md[2] * z) + md[3]);
+        for (int a = 0; a < N; ++a) {
+          int slot, off;
+          node_slot<K>(a, b, c, slot, off);
+          const uint16_t l = ls[slot];
+          out[a] = (l == LS_NONE) ? T(0) : xs[l + off];
         }
-        f *= A.amp;
       }
-      const double w = tab<double>(K).gw[qa] * tab<double>(K).gw[qb] * tab<double>(K).gw[qc];
-      cb[t] = (T)(w * h * h * h * f);
+    } else if (MODE == MODE_DIAG) {
+      for (int t = threadIdx.x; t < nch * N3; t += blockDim.x) {
+        const int j = t / N3, n = t - j * N3;
+        cb[t] = (T)(A.diag_tab[(sm_mask[j] & 0x1FF) * N3 + n]) * sm_h[j];
+      }
+    } else {  // MODE_RHS: h^3 w_q f(x_q) at the Gauss points, then S^T
+      for (int t = threadIdx.x; t < nch * N3; t += blockDim.x) {
+        const int j = t / N3, n = t - j * N3;
+        const int qa = n % N, qb = (n / N) % N, qc = n / N2;
+        const int ci = ti.cell_begin + sm_cell[j];
+        const double h = ldexp(A.dom, -(int)sm_meta[sm_cell[j]].level);
+        const double x = A.lo + h * (A.cell_ijk[3 * ci + 0] + (double)tab<double>(K).gq[qa]);
+        const double y = A.lo + h * (A.cell_ijk[3 * ci + 1] + (double)tab<double>(K).gq[qb]);
+        const double z = A.lo + h * (A.cell_ijk[3 * ci + 2] + (double)tab<double>(K).gq[qc]);
+        double f = 1.0;
+        if (A.n_modes > 0) {
+          f = 0.0;
+          for (int m = 0; m < A.n_modes; ++m) {
+            const double* md = A.modes + 4 * m;
+            f += cos(2.0 * M_PI * (md[0] * x + md[1] * y + md[2] * z) + md[3]);
+          }
+          f *= A.amp;
+        }
+        const double w = tab<double>(K).gw[qa] * tab<double>(K).gw[qb] * tab<double>(K).gw[qc];
+        cb[t] = (T)(w * h * h * h * f);
+      }
+      __syncthreads();
+      const DevTables<T>& tb = tab<T>(K);
+      for (int t = threadIdx.x; t < nch * N2; t += blockDim.x) {
+        const int j = t / N2, r = t - j * N2;
+        line_apply<N, 1, true>(cb + j * N3 + N * r, tb.Pq);
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < nch * N2; t += blockDim.x) {
+        const int j = t / N2, r = t - j * N2;
+        int base, u, v;
+        line_geom<N, 1>(r, base, u, v);
+        line_apply<N, N, true>(cb + j * N3 + base, tb.Pq);
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < nch * N2; t += blockDim.x) {
+        const int j = t / N2, r = t - j * N2;
+        line_apply<N, N2, true>(cb + j * N3 + r, tb.Pq);
+      }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nc * N2; t += blockDim.x) {
-      const int cell = t / N2, r = t - cell * N2;
-      line_apply<N, 1, true>(cb + cell * N3 + N * r, tb.Pq);
+    if (MODE == MODE_VMULT) {
+      hanging_all<K, false>(cb, sm_mask, nch);  // C_e
+      cell_laplace<K>(cb, sm_h, nch);           // S^T Q S
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < nc * N2; t += blockDim.x) {
-      const int cell = t / N2, r = t - cell * N2;
-      int base, u, v;
-      line_geom<N, 1>(r, base, u, v);
-      line_apply<N, N, true>(cb + cell * N3 + base, tb.Pq);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < nc * N2; t += blockDim.x) {
-      const int cell = t / N2, r = t - cell * N2;
-      line_apply<N, N2, true>(cb + cell * N3 + r, tb.Pq);
+    if (MODE != MODE_DIAG) hanging_all<K, true>(cb, sm_mask, nch);  // C_e^T
+    // G_e^T into the shared accumulator, sub-colour by sub-colour
+    for (int s = 0; s < ti.n_sub; ++s) {
+      const int q0 = max(c0, (int)A.subptr[ti.sub_begin + s]);
+      const int q1 = min(c0 + nch, (int)A.subptr[ti.sub_begin + s + 1]);
+      if (q1 <= q0) continue;
+      for (int t = threadIdx.x; t < (q1 - q0) * N2; t += blockDim.x) {
+        const int j = q0 - c0 + t / N2, r = t % N2;
+        const int b = r % N, c = r / N;
+        const uint16_t* ls = sm_meta[sm_cell[j]].ls;
+        const T* in = cb + j * N3 + N * r;
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+          int slot, off;
+          node_slot<K>(a, b, c, slot, off);
+          const uint16_t l = ls[slot];
+          if (l != LS_NONE) ys[l + off] += in[a];
+        }
+      }
+      __syncthreads();
     }
   }
   __syncthreads();
-  if (MODE == MODE_VMULT) {
-    hanging_all<K, false>(cb, sm_mask, nc);  // C_e
-    cell_laplace<K>(cb, sm_h, nc);           // S^T Q S
-  }
-  if (MODE != MODE_DIAG) hanging_all<K, true>(cb, sm_mask, nc);  // C_e^T
-  // G_e^T into the shared accumulator, sub-colour by sub-colour
-  for (int s = 0; s < ti.n_sub; ++s) {
-    const int q0 = A.subptr[ti.sub_begin + s], q1 = A.subptr[ti.sub_begin + s + 1];
-    for (int t = threadIdx.x; t < (q1 - q0) * N2; t += blockDim.x) {
-      const int q = q0 + t / N2, r = t % N2;
-      const int cell = A.perm[ti.cell_begin + q];
-      const int b = r % N, c = r / N;
-      const uint16_t* ls = sm_meta[cell].ls;
-      const T* in = cb + cell * N3 + N * r;
+  write_tile_dofs(A.dst, A.halo, ys, ti, A.add);
+}
+
+// ---------------------------------------------------------------------------
+// fp32 operator, one cell per thread, values in registers
+// ---------------------------------------------------------------------------
+
+// hanging-node interpolation of one cell, done by the whole warp through a
+// small shared-memory scratch (the owner lane writes its values, the lanes
+// apply the direction-wise line interpolation, the owner reads back)
+template <int K, bool TRANS>
+__device__ __forceinline__ void hanging_warp(float* u, uint16_t mask, bool active, float* scratch) {
+  constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
+  const int lane = threadIdx.x & 31;
+  unsigned pending = __ballot_sync(0xffffffffu, active && (mask & MASK_HANG));
+  while (pending) {
+    const int owner = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const uint16_t m = __shfl_sync(0xffffffffu, mask, owner);
+    if (lane == owner) {
 #pragma unroll
-      for (int a = 0; a < N; ++a) {
+      for (int n = 0; n < N3; ++n) scratch[n] = u[n];
+    }
+    __syncwarp();
+    const DevTables<float>& tb = tab<float>(K);
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+      const int D = TRANS ? 2 - dd : dd;
+      const int stride = D == 0 ? 1 : (D == 1 ? N : N2);
+      const int p = (m >> D) & 1;
+      for (int r = lane; r < N2; r += 32) {
+        const int uu = r % N, vv = r / N;
+        int base;
+        bool hang;
+        if (D == 0) {
+          base = N * r;
+          hang = line_hangs<K, 0>(m, uu, vv);
+        } else if (D == 1) {
+          base = uu + N2 * vv;
+          hang = line_hangs<K, 1>(m, uu, vv);
+        } else {
+          base = r;
+          hang = line_hangs<K, 2>(m, uu, vv);
+        }
+        if (!hang) continue;
+        float v[N];
+#pragma unroll
+        for (int a = 0; a < N; ++a) v[a] = scratch[base + a * stride];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          float s = 0.f;
+#pragma unroll
+          for (int a = 0; a < N; ++a) s += (TRANS ? tb.I[p][a][i] : tb.I[p][i][a]) * v[a];
+          scratch[base + i * stride] = s;
+        }
+      }
+      __syncwarp();
+    }
+    if (lane == owner) {
+#pragma unroll
+      for (int n = 0; n < N3; ++n) u[n] = scratch[n];
+    }
+    __syncwarp();
+  }
+}
+
+template <int K>
+constexpr int regs_block() {
+  return 128;
+}
+
+template <int K>
+__global__ void __launch_bounds__(128, (K >= 4 ? 3 : 4)) vmult_regs(CellArgs<float> A) {
+  constexpr int N = K + 1, N3 = N * N * N;
+  extern __shared__ __align__(16) unsigned char smem[];
+  CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem);
+  float* scratch = reinterpret_cast<float*>(smem + (size_t)A.tc * sizeof(CellMeta));  // 4 warps x N3
+  float* buf = scratch + 4 * N3;  // tile DoFs: input, then the accumulator
+  const TileInfo ti = A.tiles[blockIdx.x];
+  const int nc = ti.n_cells;
+  const int nloc = ti.n_owned + ti.n_foreign;
+  load_meta(sm_meta, A.meta, ti.cell_begin, nc);
+  load_tile_dofs(buf, A.src, A.foreign, ti);
+  __syncthreads();
+  const int q = threadIdx.x;
+  const bool active = q < nc;
+  const int cell = active ? A.perm[ti.cell_begin + q] : 0;
+  float u[N3];
+  const uint16_t* ls = sm_meta[cell].ls;
+  const uint16_t mask = active ? sm_meta[cell].mask : 0;
+  // G_e
+#pragma unroll
+  for (int n = 0; n < N3; ++n) {
+    int slot, off;
+    node_slot<K>(n % N, (n / N) % N, n / (N * N), slot, off);
+    const uint16_t l = ls[slot];
+    u[n] = (active && l != LS_NONE) ? buf[l + off] : 0.f;
+  }
+  __syncthreads();  // the tile DoFs are no longer needed: reuse as accumulator
+  for (int i = threadIdx.x; i < nloc; i += blockDim.x) buf[i] = 0.f;
+  float* ws = scratch + (threadIdx.x >> 5) * N3;
+  hanging_warp<K, false>(u, mask, active, ws);  // C_e
+  const float h = active ? ldexpf((float)A.dom, -(int)sm_meta[cell].level) : 0.f;
+  cell_laplace_regs<K>(u, h);                    // S^T Q S
+  hanging_warp<K, true>(u, mask, active, ws);   // C_e^T
+  __syncthreads();
+  // G_e^T, sub-colour by sub-colour (threads are in sub-colour order)
+  const int my_sub = active ? sm_meta[cell].sub : -1;
+  for (int s = 0; s < ti.n_sub; ++s) {
+    if (my_sub == s) {
+#pragma unroll
+      for (int n = 0; n < N3; ++n) {
         int slot, off;
-        node_slot<K>(a, b, c, slot, off);
+        node_slot<K>(n % N, (n / N) % N, n / (N * N), slot, off);
         const uint16_t l = ls[slot];
-        if (l != LS_NONE) ys[l + off] += in[a];
+        if (l != LS_NONE) buf[l + off] += u[n];
       }
     }
     __syncthreads();
   }
-  // write back: owned DoFs (contiguous) stored, foreign DoFs added
-  {
-    T* dst = A.dst + ti.dof_begin;
-    if (A.add)
-      for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) dst[i] += ys[i];
-    else
-      for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) dst[i] = ys[i];
-    const int32_t* fl = A.foreign + ti.foreign_begin;
-    for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) A.dst[fl[i]] += ys[ti.n_owned + i];
+  write_tile_dofs(A.dst, A.halo, buf, ti, A.add);
+}
+
+// second pass: every DoF that other tiles contributed to adds its halo slots
+// in a fixed order
+template <typename T>
+__global__ void halo_add_kernel(T* dst, const T* halo, const int32_t* dofs, const int32_t* ptr,
+                                const int32_t* src, int nh) {
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nh; u += gridDim.x * blockDim.x) {
+    const int32_t g = dofs[u];
+    T s = dst[g];
+    for (int e = ptr[u]; e < ptr[u + 1]; ++e) s += halo[src[e]];
+    dst[g] = s;
   }
 }
 
@@ -240,22 +400,43 @@ __global__ void __launch_bounds__(BLOCK) diag_table_kernel(double* out, int tc) 
   }
 }
 
+template <typename KERN>
+void ensure_smem(KERN kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T>
+void run_halo(const CellLaunch& L, T* dst, cudaStream_t s) {
+  if (L.n_halo == 0) return;
+  const int nb = std::min((L.n_halo + BLOCK - 1) / BLOCK, 152 * 8);
+  {
+    halo_add_kernel<T><<<nb, BLOCK, 0, s>>>(dst, static_cast<const T*>(L.halo), L.halo_dofs, L.halo_ptr,
+                                           L.halo_src, L.n_halo);
+    note_launches(1);
+  }
+}
+
 template <int K, typename T, int MODE>
 void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
   const size_t sm = smem_layout<T>((K + 1) * (K + 1) * (K + 1), L.tc, L.max_local).total;
-  static bool attr_set = false;
-  static size_t attr_bytes = 0;
-  if (!attr_set || attr_bytes < sm) {
-    cudaFuncSetAttribute(cell_kernel<K, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(sm, (size_t)48 * 1024));
-    attr_set = true;
-    attr_bytes = std::max(sm, (size_t)48 * 1024);
+  ensure_smem(cell_kernel<K, T, MODE>, sm);
+  {
+    cell_kernel<K, T, MODE><<<L.n_tiles, BLOCK, sm, s>>>(A);
+    note_launches(1);
   }
-  for (int c = 0; c < L.n_colours; ++c) {
-    const int n = L.colour_ptr[c + 1] - L.colour_ptr[c];
-    if (n == 0) continue;
-    A.tile_list = L.colour_tiles + L.colour_ptr[c];
-    { cell_kernel<K, T, MODE><<<n, BLOCK, sm, s>>>(A); note_launches(1); }
+  run_halo<T>(L, A.dst, s);
+}
+
+template <int K>
+void run_regs(const CellLaunch& L, CellArgs<float> A, cudaStream_t s) {
+  constexpr int N3 = (K + 1) * (K + 1) * (K + 1);
+  const size_t sm = (size_t)L.tc * sizeof(CellMeta) + (4 * N3 + (size_t)L.max_local) * sizeof(float);
+  ensure_smem(vmult_regs<K>, sm);
+  {
+    vmult_regs<K><<<L.n_tiles, 128, sm, s>>>(A);
+    note_launches(1);
   }
+  run_halo<float>(L, A.dst, s);
 }
 
 template <typename T>
@@ -267,6 +448,7 @@ CellArgs<T> make_args(const CellLaunch& L) {
   A.subptr = L.subptr;
   A.perm = L.perm;
   A.cell_ijk = L.cell_ijk;
+  A.halo = static_cast<T*>(L.halo);
   A.lo = L.lo;
   A.dom = L.dom;
   A.tc = L.tc;
@@ -293,6 +475,7 @@ size_t cell_smem_bytes(int k, bool fp64, int tc, int max_local) {
 }
 
 void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, int add, cudaStream_t s) {
+  if (L.n_tiles == 0) return;
   if (fp64) {
     CellArgs<double> A = make_args<double>(L);
     A.src = static_cast<const double*>(src);
@@ -304,11 +487,22 @@ void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, in
     A.src = static_cast<const float*>(src);
     A.dst = static_cast<float*>(dst);
     A.add = add;
-    dispatch<float, MODE_VMULT>(L, A, s);
+    if (L.tc > 128 || L.use_lines) {
+      dispatch<float, MODE_VMULT>(L, A, s);
+      return;
+    }
+    switch (L.k) {
+      case 1: run_regs<1>(L, A, s); break;
+      case 2: run_regs<2>(L, A, s); break;
+      case 3: run_regs<3>(L, A, s); break;
+      case 4: run_regs<4>(L, A, s); break;
+      default: break;
+    }
   }
 }
 
 void launch_rhs(const CellLaunch& L, const RhsDesc& f, double* dst, cudaStream_t s) {
+  if (L.n_tiles == 0) return;
   CellArgs<double> A = make_args<double>(L);
   A.dst = dst;
   A.modes = f.modes;
@@ -318,10 +512,18 @@ void launch_rhs(const CellLaunch& L, const RhsDesc& f, double* dst, cudaStream_t
 }
 
 void launch_diag(const CellLaunch& L, const double* diag_tab, double* dst, cudaStream_t s) {
+  if (L.n_tiles == 0) return;
   CellArgs<double> A = make_args<double>(L);
   A.dst = dst;
   A.diag_tab = diag_tab;
   dispatch<double, MODE_DIAG>(L, A, s);
+}
+
+void launch_halo_add(const CellLaunch& L, bool fp64, void* dst, cudaStream_t s) {
+  if (fp64)
+    run_halo<double>(L, static_cast<double*>(dst), s);
+  else
+    run_halo<float>(L, static_cast<float*>(dst), s);
 }
 
 void launch_diag_table(int k, double* tab_out, cudaStream_t s) {
@@ -330,10 +532,10 @@ void launch_diag_table(int k, double* tab_out, cudaStream_t s) {
   const size_t sm = (((size_t)tc * 10 + 15) & ~(size_t)15) + (size_t)tc * n3 * sizeof(double);
   const int nb = (512 * n3 + tc - 1) / tc;
   switch (k) {
-    { case 1: diag_table_kernel<1><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
-    { case 2: diag_table_kernel<2><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
-    { case 3: diag_table_kernel<3><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
-    { case 4: diag_table_kernel<4><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
+    case 1: { diag_table_kernel<1><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
+    case 2: { diag_table_kernel<2><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
+    case 3: { diag_table_kernel<3><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
+    case 4: { diag_table_kernel<4><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
     default: break;
   }
 }

@@ -88,7 +88,7 @@ struct TArgs {
   T* dst;
   // restriction: coarse tiles
   const TileInfo* tiles;
-  const int32_t* tile_list;
+  T* halo;
   const CellMeta* meta;
   const int32_t* foreign;
   const uint16_t* subptr;
@@ -158,21 +158,21 @@ __global__ void __launch_bounds__(BLOCK) prolong_h(TArgs<T> A) {
   }
 }
 
-// shared part of the restriction kernels: C^T, scatter into the coarse
-// tile's accumulator by sub-colour, add into the coarse vector
+// scatter the chunk's coarse cells (positions c0.. in sub-colour order) into
+// the tile accumulator, sub-colour by sub-colour
 template <int KC, typename T>
-__device__ __forceinline__ void restrict_finish(const TArgs<T>& A, const TileInfo& ti, const CellMeta* sm_meta,
-                                                const uint16_t* sm_mask, T* cb, T* ys) {
+__device__ __forceinline__ void restrict_scatter(const TArgs<T>& A, const TileInfo& ti, const CellMeta* sm_meta,
+                                                 const uint16_t* sm_cell, int c0, int np, const T* cb, T* ys) {
   constexpr int N = KC + 1, N2 = N * N, N3 = N2 * N;
-  hanging_all<KC, true>(cb, sm_mask, ti.n_cells);
   for (int s = 0; s < ti.n_sub; ++s) {
-    const int q0 = A.subptr[ti.sub_begin + s], q1 = A.subptr[ti.sub_begin + s + 1];
+    const int q0 = max(c0, (int)A.subptr[ti.sub_begin + s]);
+    const int q1 = min(c0 + np, (int)A.subptr[ti.sub_begin + s + 1]);
+    if (q1 <= q0) continue;
     for (int t = threadIdx.x; t < (q1 - q0) * N2; t += blockDim.x) {
-      const int q = q0 + t / N2, r = t % N2;
-      const int cell = A.perm[ti.cell_begin + q];
+      const int j = q0 - c0 + t / N2, r = t % N2;
       const int b = r % N, c = r / N;
-      const uint16_t* ls = sm_meta[cell].ls;
-      const T* in = cb + cell * N3 + N * r;
+      const uint16_t* ls = sm_meta[sm_cell[j]].ls;
+      const T* in = cb + j * N3 + N * r;
 #pragma unroll
       for (int a = 0; a < N; ++a) {
         int slot, off;
@@ -183,78 +183,86 @@ __device__ __forceinline__ void restrict_finish(const TArgs<T>& A, const TileInf
     }
     __syncthreads();
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void restrict_write(const TArgs<T>& A, const TileInfo& ti, const T* ys) {
   T* dst = A.dst + ti.dof_begin;
   for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) dst[i] += ys[i];
-  const int32_t* fl = A.foreign + ti.foreign_begin;
-  for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) A.dst[fl[i]] += ys[ti.n_owned + i];
+  T* h = A.halo + ti.foreign_begin;
+  for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) h[i] = ys[ti.n_owned + i];
 }
 
 template <int K, typename T>
 __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
   constexpr int N = K + 1, N3 = N * N * N, M = 2 * K + 1, M3 = M * M * M;
   constexpr int S1 = M * N * N, S2 = M * M * N;
-  __shared__ uint8_t sm_ref[256];
-  __shared__ int32_t sm_fine[256];
-  __shared__ uint16_t sm_mask[256];
+  __shared__ uint8_t sm_ref[TP];
+  __shared__ int32_t sm_fine[TP];
+  __shared__ uint16_t sm_mask[TP];
+  __shared__ uint16_t sm_cell[TP];
   extern __shared__ __align__(16) unsigned char smem[];
   CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem);
   T* cb = reinterpret_cast<T*>(smem + (size_t)A.tc * sizeof(CellMeta));
-  T* e1 = cb + A.tc * N3;
+  T* e1 = cb + TP * N3;
   T* e2 = e1 + TP * S1;
   T* e3 = e2 + TP * S2;
   T* ys = e3 + TP * M3;
-  const TileInfo ti = A.tiles[A.tile_list[blockIdx.x]];
+  const TileInfo ti = A.tiles[blockIdx.x];
   const int nc = ti.n_cells;
   {
     const uint4* g = reinterpret_cast<const uint4*>(A.meta + ti.cell_begin);
     uint4* s = reinterpret_cast<uint4*>(sm_meta);
     for (int i = threadIdx.x; i < nc * 4; i += blockDim.x) s[i] = g[i];
   }
-  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-    sm_ref[c] = A.refined[ti.cell_begin + c];
-    sm_fine[c] = A.fine_of[ti.cell_begin + c];
-    sm_mask[c] = A.mask_c[ti.cell_begin + c];
-  }
   for (int i = threadIdx.x; i < ti.n_owned + ti.n_foreign; i += blockDim.x) ys[i] = T(0);
-  for (int i = threadIdx.x; i < nc * N3; i += blockDim.x) cb[i] = T(0);
-  __syncthreads();
   for (int c0 = 0; c0 < nc; c0 += TP) {
     const int np = min(TP, nc - c0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+      const int cell = A.perm[ti.cell_begin + c0 + j];
+      sm_cell[j] = (uint16_t)cell;
+      sm_ref[j] = A.refined[ti.cell_begin + cell];
+      sm_fine[j] = A.fine_of[ti.cell_begin + cell];
+      sm_mask[j] = A.mask_c[ti.cell_begin + cell];
+    }
     for (int i = threadIdx.x; i < np * M3; i += blockDim.x) e3[i] = T(0);
+    for (int i = threadIdx.x; i < np * N3; i += blockDim.x) cb[i] = T(0);
     __syncthreads();
     for (int t = threadIdx.x; t < np * 8 * N3; t += blockDim.x) {
-      const int cl = t / (8 * N3), r = t - cl * 8 * N3;
-      const int cell = c0 + cl;
+      const int j = t / (8 * N3), r = t - j * 8 * N3;
       const int q = r / N3, n = r - q * N3;
       const int a = n % N, b = (n / N) % N, c = n / (N * N);
       int f;
-      if (sm_ref[cell])
-        f = sm_fine[cell] + q;
+      if (sm_ref[j])
+        f = sm_fine[j] + q;
       else if (q == 0)
-        f = sm_fine[cell];
+        f = sm_fine[j];
       else
         continue;
       int slot, off;
       node_slot<K>(a, b, c, slot, off);
       if (!((A.own_f[f] >> slot) & 1u)) continue;
       const T val = A.src[A.gstart_f[(size_t)f * NSLOT + slot] + off];
-      if (sm_ref[cell]) {
+      if (sm_ref[j]) {
         const int gi = (q & 1) * K + a, gj = ((q >> 1) & 1) * K + b, gk = (q >> 2) * K + c;
-        e3[cl * M3 + gi + M * (gj + M * gk)] = val;
+        e3[j * M3 + gi + M * (gj + M * gk)] = val;
       } else {
-        cb[cell * N3 + n] = val;
+        cb[j * N3 + n] = val;
       }
     }
     __syncthreads();
-    const uint8_t* act = sm_ref + c0;
-    tsweep<K, 0, M, N, 2, true>(e3, e2, M, M, M, np, M3, S2, act);
+    tsweep<K, 0, M, N, 2, true>(e3, e2, M, M, M, np, M3, S2, sm_ref);
     __syncthreads();
-    tsweep<K, 0, M, N, 1, true>(e2, e1, M, M, N, np, S2, S1, act);
+    tsweep<K, 0, M, N, 1, true>(e2, e1, M, M, N, np, S2, S1, sm_ref);
     __syncthreads();
-    tsweep<K, 0, M, N, 0, true>(e1, cb + c0 * N3, M, N, N, np, S1, N3, act);
+    tsweep<K, 0, M, N, 0, true>(e1, cb, M, N, N, np, S1, N3, sm_ref);
     __syncthreads();
+    hanging_all<K, true>(cb, sm_mask, np);  // C^(c)T
+    restrict_scatter<K>(A, ti, sm_meta, sm_cell, c0, np, cb, ys);
   }
-  restrict_finish<K>(A, ti, sm_meta, sm_mask, cb, ys);
+  __syncthreads();
+  restrict_write(A, ti, ys);
 }
 
 // ---------------------------------------------------------------------------
@@ -301,29 +309,35 @@ template <int KF, typename T>
 __global__ void __launch_bounds__(BLOCK) restrict_p(TArgs<T> A) {
   constexpr int KC = KF / 2, NF = KF + 1, NC = KC + 1;
   constexpr int NC3 = NC * NC * NC, NF3 = NF * NF * NF, S1 = NF * NC * NC, S2 = NF * NF * NC;
-  __shared__ uint16_t sm_mask[256];
+  __shared__ uint16_t sm_mask[TP];
+  __shared__ uint16_t sm_cell[TP];
   extern __shared__ __align__(16) unsigned char smem[];
   CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem);
   T* cb = reinterpret_cast<T*>(smem + (size_t)A.tc * sizeof(CellMeta));
-  T* e1 = cb + A.tc * NC3;
+  T* e1 = cb + TP * NC3;
   T* e2 = e1 + TP * S1;
   T* e3 = e2 + TP * S2;
   T* ys = e3 + TP * NF3;
-  const TileInfo ti = A.tiles[A.tile_list[blockIdx.x]];
+  const TileInfo ti = A.tiles[blockIdx.x];
   const int nc = ti.n_cells;
   {
     const uint4* g = reinterpret_cast<const uint4*>(A.meta + ti.cell_begin);
     uint4* s = reinterpret_cast<uint4*>(sm_meta);
     for (int i = threadIdx.x; i < nc * 4; i += blockDim.x) s[i] = g[i];
   }
-  for (int c = threadIdx.x; c < nc; c += blockDim.x) sm_mask[c] = A.mask_c[ti.cell_begin + c];
   for (int i = threadIdx.x; i < ti.n_owned + ti.n_foreign; i += blockDim.x) ys[i] = T(0);
-  __syncthreads();
   for (int c0 = 0; c0 < nc; c0 += TP) {
     const int np = min(TP, nc - c0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < np; j += blockDim.x) {
+      const int cell = A.perm[ti.cell_begin + c0 + j];
+      sm_cell[j] = (uint16_t)cell;
+      sm_mask[j] = A.mask_c[ti.cell_begin + cell];
+    }
+    __syncthreads();
     for (int t = threadIdx.x; t < np * NF3; t += blockDim.x) {
-      const int cl = t / NF3, n = t - cl * NF3;
-      const int f = ti.cell_begin + c0 + cl;
+      const int j = t / NF3, n = t - j * NF3;
+      const int f = ti.cell_begin + sm_cell[j];
       int slot, off;
       node_slot<KF>(n % NF, (n / NF) % NF, n / (NF * NF), slot, off);
       e3[t] = ((A.own_f[f] >> slot) & 1u) ? A.src[A.gstart_f[(size_t)f * NSLOT + slot] + off] : T(0);
@@ -333,10 +347,13 @@ __global__ void __launch_bounds__(BLOCK) restrict_p(TArgs<T> A) {
     __syncthreads();
     tsweep<KF, 1, NF, NC, 1, true>(e2, e1, NF, NF, NC, np, S2, S1, nullptr);
     __syncthreads();
-    tsweep<KF, 1, NF, NC, 0, true>(e1, cb + c0 * NC3, NF, NC, NC, np, S1, NC3, nullptr);
+    tsweep<KF, 1, NF, NC, 0, true>(e1, cb, NF, NC, NC, np, S1, NC3, nullptr);
     __syncthreads();
+    hanging_all<KC, true>(cb, sm_mask, np);
+    restrict_scatter<KC>(A, ti, sm_meta, sm_cell, c0, np, cb, ys);
   }
-  restrict_finish<KC>(A, ti, sm_meta, sm_mask, cb, ys);
+  __syncthreads();
+  restrict_write(A, ti, ys);
 }
 
 template <typename T>
@@ -350,6 +367,7 @@ TArgs<T> targs(const TransferLaunch& L) {
   A.gstart_c = L.gstart_c;
   A.mask_c = L.mask_c;
   A.tiles = L.coarse.tiles;
+  A.halo = static_cast<T*>(L.coarse.halo);
   A.meta = L.coarse.meta;
   A.foreign = L.coarse.foreign;
   A.subptr = L.coarse.subptr;
@@ -380,18 +398,13 @@ template <int K, typename T>
 void restrict_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
   constexpr int N = K + 1, M = 2 * K + 1;
   const size_t sm = (size_t)L.coarse.tc * sizeof(CellMeta) +
-                    ((size_t)L.coarse.tc * N * N * N + TP * (M * N * N + M * M * N + M * M * M) + L.coarse.max_local) *
-                        sizeof(T);
+                    ((size_t)TP * (N * N * N + M * N * N + M * M * N + M * M * M) + L.coarse.max_local) * sizeof(T);
   set_smem(restrict_h<K, T>, sm);
   TArgs<T> A = targs<T>(L);
   A.src = src;
   A.dst = dst;
-  for (int c = 0; c < L.coarse.n_colours; ++c) {
-    const int n = L.coarse.colour_ptr[c + 1] - L.coarse.colour_ptr[c];
-    if (!n) continue;
-    A.tile_list = L.coarse.colour_tiles + L.coarse.colour_ptr[c];
-    { restrict_h<K, T><<<n, BLOCK, sm, s>>>(A); note_launches(1); }
-  }
+  { restrict_h<K, T><<<L.coarse.n_tiles, BLOCK, sm, s>>>(A); note_launches(1); }
+  launch_halo_add(L.coarse, sizeof(T) == 8, dst, s);
 }
 
 template <int KF, typename T>
@@ -410,19 +423,14 @@ template <int KF, typename T>
 void restrict_p_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
   constexpr int NF = KF + 1, NC = KF / 2 + 1;
   const size_t sm = (size_t)L.coarse.tc * sizeof(CellMeta) +
-                    ((size_t)L.coarse.tc * NC * NC * NC + TP * (NF * NC * NC + NF * NF * NC + NF * NF * NF) +
-                     L.coarse.max_local) *
+                    ((size_t)TP * (NC * NC * NC + NF * NC * NC + NF * NF * NC + NF * NF * NF) + L.coarse.max_local) *
                         sizeof(T);
   set_smem(restrict_p<KF, T>, sm);
   TArgs<T> A = targs<T>(L);
   A.src = src;
   A.dst = dst;
-  for (int c = 0; c < L.coarse.n_colours; ++c) {
-    const int n = L.coarse.colour_ptr[c + 1] - L.coarse.colour_ptr[c];
-    if (!n) continue;
-    A.tile_list = L.coarse.colour_tiles + L.coarse.colour_ptr[c];
-    { restrict_p<KF, T><<<n, BLOCK, sm, s>>>(A); note_launches(1); }
-  }
+  { restrict_p<KF, T><<<L.coarse.n_tiles, BLOCK, sm, s>>>(A); note_launches(1); }
+  launch_halo_add(L.coarse, sizeof(T) == 8, dst, s);
 }
 
 template <typename T>

@@ -12,13 +12,15 @@
 //   one entity are contiguous, so a cell is described by 27 entity starts.
 //   Dirichlet entities carry no DoFs (vectors hold free DoFs only).
 // * Cells are in Morton order and grouped into tiles of `tile_cells`
-//   consecutive cells.  Tiles that share an entity get different colours;
-//   each entity is owned by the touching tile of the lowest colour and the
-//   DoFs owned by one tile are numbered contiguously.  A cell kernel launched
-//   colour by colour can then write its owned DoFs with plain stores and add
-//   into the foreign ones without atomics (deterministic results).
+//   consecutive cells.  Each entity is owned by the first tile that touches
+//   it and the DoFs owned by one tile are numbered contiguously.  A cell
+//   kernel writes its owned DoFs with plain stores and its contributions to
+//   the other (foreign) DoFs into one halo slot each; a second kernel adds
+//   the halo slots of every DoF in a fixed order.  No atomics: results are
+//   reproducible bit for bit.
 // * Inside a tile, cells that share an entity get different sub-colours; the
-//   shared-memory accumulation runs sub-colour by sub-colour.
+//   shared-memory accumulation runs sub-colour by sub-colour, and the cells
+//   are permuted so that each sub-colour is contiguous.
 #include <algorithm>
 #include <stdexcept>
 
@@ -169,55 +171,21 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
   }
   const int ne = (int)endofs.size();
 
-  // tiles and their colours
+  // Tiles of consecutive cells.  Every entity is owned by the first tile that
+  // touches it (Morton order); the DoFs a tile owns are numbered
+  // contiguously.  A tile adds its contributions to DoFs owned by other
+  // tiles ("foreign" DoFs) into a halo buffer, one slot per (tile, foreign
+  // DoF); a second pass adds the halo slots of every DoF in a fixed order.
   const int nt = (nc + tile_cells - 1) / tile_cells;
-  std::vector<std::vector<int32_t>> etiles(ne);
+  std::vector<int32_t> owner(ne, -1);
   for (int t = 0; t < nt; ++t) {
     const int c0 = t * tile_cells, c1 = std::min(nc, c0 + tile_cells);
     for (int ci = c0; ci < c1; ++ci)
       for (int s = 0; s < NSLOT; ++s) {
         int32_t e = eid[(size_t)ci * NSLOT + s];
-        if (e < 0) continue;
-        auto& v = etiles[e];
-        if (v.empty() || v.back() != t) v.push_back(t);
+        if (e >= 0 && owner[e] < 0) owner[e] = t;
       }
   }
-  std::vector<int32_t> colour(nt, -1);
-  {
-    std::vector<std::vector<int32_t>> adj(nt);
-    for (int e = 0; e < ne; ++e) {
-      auto& v = etiles[e];
-      for (size_t a = 0; a < v.size(); ++a)
-        for (size_t b = a + 1; b < v.size(); ++b) {
-          adj[v[a]].push_back(v[b]);
-          adj[v[b]].push_back(v[a]);
-        }
-    }
-    std::vector<int32_t> used;
-    for (int t = 0; t < nt; ++t) {
-      used.clear();
-      for (int32_t u : adj[t])
-        if (colour[u] >= 0) used.push_back(colour[u]);
-      std::sort(used.begin(), used.end());
-      int c = 0;
-      for (int32_t u : used) {
-        if (u == c) ++c;
-        else if (u > c) break;
-      }
-      colour[t] = c;
-    }
-  }
-  L.n_colours = 0;
-  for (int t = 0; t < nt; ++t) L.n_colours = std::max(L.n_colours, colour[t] + 1);
-  // owner tile of every entity: the touching tile of the lowest colour
-  std::vector<int32_t> owner(ne, -1);
-  for (int e = 0; e < ne; ++e) {
-    int best = -1;
-    for (int32_t t : etiles[e])
-      if (best < 0 || colour[t] < colour[best] || (colour[t] == colour[best] && t < best)) best = t;
-    owner[e] = best;
-  }
-  // DoF numbering: tile by tile, the entities each tile owns
   std::vector<int32_t> estart(ne, -1);
   int64_t next = 0;
   L.tiles.assign(nt, TileInfo{});
@@ -228,8 +196,6 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
   L.max_local = 0;
   L.max_sub = 0;
   std::vector<int32_t> lstart_of(ne, -1);
-  // pass 1: every tile numbers the entities it owns (all tiles first, so that
-  // foreign entities owned by later tiles have their numbers in pass 2)
   for (int t = 0; t < nt; ++t) {
     const int c0 = t * tile_cells, c1 = std::min(nc, c0 + tile_cells);
     TileInfo& T = L.tiles[t];
@@ -246,13 +212,6 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
       }
     if (next > 0x7FFFFFFF) throw std::runtime_error("too many DoFs for 32-bit indices");
     T.n_owned = (int32_t)(next - T.dof_begin);
-  }
-  for (int e = 0; e < ne; ++e)
-    if (estart[e] < 0) throw std::runtime_error("entity without an owner tile");
-  // pass 2: tile-local numbering, sub-colours
-  for (int t = 0; t < nt; ++t) {
-    const int c0 = t * tile_cells, c1 = std::min(nc, c0 + tile_cells);
-    TileInfo& T = L.tiles[t];
     // tile-local numbering: owned entities at their offset, foreign ones after
     T.foreign_begin = (int32_t)L.foreign.size();
     int32_t local_next = T.n_owned;
@@ -273,15 +232,6 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
     T.n_foreign = local_next - T.n_owned;
     if (local_next >= (int)LS_NONE) throw std::runtime_error("tile too large for 16-bit local indices");
     L.max_local = std::max(L.max_local, (int)local_next);
-    for (int ci = c0; ci < c1; ++ci) {
-      CellMeta& cm = L.meta[ci];
-      for (int s = 0; s < NSLOT; ++s) {
-        int32_t e = eid[(size_t)ci * NSLOT + s];
-        cm.ls[s] = e < 0 ? LS_NONE : (uint16_t)lstart_of[e];
-      }
-      cm.mask = L.mask[ci];
-      cm.level = (uint8_t)L.cells[ci].l;
-    }
     // sub-colours of the cells inside the tile (greedy, in cell order)
     const int n = c1 - c0;
     std::vector<int> sub(n, -1);
@@ -289,24 +239,24 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
     {
       std::unordered_map<int32_t, std::vector<int>> ecells;
       std::vector<char> used;
-      for (int a = 0; a < n; ++a) {
+      for (int a2 = 0; a2 < n; ++a2) {
         used.assign(n + 1, 0);
         for (int s = 0; s < NSLOT; ++s) {
-          int32_t e = eid[(size_t)(c0 + a) * NSLOT + s];
+          int32_t e = eid[(size_t)(c0 + a2) * NSLOT + s];
           if (e < 0) continue;
           auto it = ecells.find(e);
           if (it != ecells.end())
-            for (int b : it->second) used[sub[b]] = 1;
+            for (int b2 : it->second) used[sub[b2]] = 1;
         }
         int c = 0;
         while (used[c]) ++c;
-        sub[a] = c;
+        sub[a2] = c;
         nsub = std::max(nsub, c + 1);
         for (int s = 0; s < NSLOT; ++s) {
-          int32_t e = eid[(size_t)(c0 + a) * NSLOT + s];
+          int32_t e = eid[(size_t)(c0 + a2) * NSLOT + s];
           if (e < 0) continue;
           auto& v = ecells[e];
-          if (v.empty() || v.back() != a) v.push_back(a);
+          if (v.empty() || v.back() != a2) v.push_back(a2);
         }
       }
     }
@@ -316,21 +266,45 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
     int pos = 0;
     for (int c = 0; c < nsub; ++c) {
       L.subptr.push_back((uint16_t)pos);
-      for (int a = 0; a < n; ++a)
-        if (sub[a] == c) L.perm[c0 + pos++] = (uint8_t)a;
+      for (int a2 = 0; a2 < n; ++a2)
+        if (sub[a2] == c) L.perm[c0 + pos++] = (uint8_t)a2;
     }
     L.subptr.push_back((uint16_t)pos);
+    for (int ci = c0; ci < c1; ++ci) {
+      CellMeta& cm = L.meta[ci];
+      for (int s = 0; s < NSLOT; ++s) {
+        int32_t e = eid[(size_t)ci * NSLOT + s];
+        cm.ls[s] = e < 0 ? LS_NONE : (uint16_t)lstart_of[e];
+      }
+      cm.mask = L.mask[ci];
+      cm.level = (uint8_t)L.cells[ci].l;
+      cm.sub = (uint8_t)sub[ci - c0];
+    }
     for (int32_t e : touched) lstart_of[e] = -1;
   }
   L.n_free = next;
-  // colour lists
-  L.colour_ptr.assign(L.n_colours + 1, 0);
-  for (int t = 0; t < nt; ++t) L.colour_ptr[colour[t] + 1]++;
-  for (int c = 0; c < L.n_colours; ++c) L.colour_ptr[c + 1] += L.colour_ptr[c];
-  L.colour_tiles.assign(nt, 0);
+  for (int e = 0; e < ne; ++e)
+    if (estart[e] < 0) throw std::runtime_error("entity without an owner tile");
+  // halo: the foreign slots of every DoF, grouped by DoF in slot order
   {
-    std::vector<int32_t> fill(L.colour_ptr.begin(), L.colour_ptr.end() - 1);
-    for (int t = 0; t < nt; ++t) L.colour_tiles[fill[colour[t]]++] = t;
+    const int64_t nf = (int64_t)L.foreign.size();
+    std::vector<int32_t> order(nf);
+    for (int64_t i = 0; i < nf; ++i) order[i] = (int32_t)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a2, int32_t b2) { return L.foreign[a2] < L.foreign[b2]; });
+    L.halo_dofs.clear();
+    L.halo_ptr.assign(1, 0);
+    L.halo_src.assign(nf, 0);
+    for (int64_t i = 0; i < nf; ++i) {
+      const int32_t g = L.foreign[order[i]];
+      if (L.halo_dofs.empty() || L.halo_dofs.back() != g) {
+        if (!L.halo_dofs.empty()) L.halo_ptr.push_back((int32_t)i);
+        L.halo_dofs.push_back(g);
+      }
+      L.halo_src[i] = order[i];
+    }
+    L.halo_ptr.push_back((int32_t)nf);
+    if (L.halo_dofs.empty()) L.halo_ptr.assign(1, 0);
   }
   // global starts and transfer ownership (first non-hanging reference wins)
   L.gstart.assign((size_t)nc * NSLOT, -1);
@@ -387,15 +361,6 @@ void validate_level(const LevelHost& L) {
     if (s / 9 == 1) ++nd;
     return ipow(k - 1, nd);
   };
-  std::vector<int32_t> tile_colour(nt, -1);
-  for (int c = 0; c < L.n_colours; ++c)
-    for (int i = L.colour_ptr[c]; i < L.colour_ptr[c + 1]; ++i) {
-      const int t = L.colour_tiles[i];
-      if (t < 0 || t >= nt || tile_colour[t] >= 0) fail("colour lists do not partition the tiles");
-      tile_colour[t] = c;
-    }
-  for (int t = 0; t < nt; ++t)
-    if (tile_colour[t] < 0) fail("tile without colour");
   int64_t next = 0;
   int cnext = 0;
   std::vector<int32_t> owner_tile(L.n_free, -1);
@@ -407,54 +372,59 @@ void validate_level(const LevelHost& L) {
     for (int i = 0; i < T.n_owned; ++i) owner_tile[T.dof_begin + i] = t;
     next += T.n_owned;
     if (T.n_owned + T.n_foreign > L.max_local || L.max_local >= (int)LS_NONE) fail("local size");
+    if (t + 1 < nt && L.tiles[t + 1].foreign_begin != T.foreign_begin + T.n_foreign) fail("foreign lists not contiguous");
   }
   if (cnext != nc || next != L.n_free) fail("tiles do not cover cells/DoFs");
-  std::vector<int32_t> lastw(L.n_free, -1);  // tile that last touched a DoF, per colour sweep
-  for (int c = 0; c < L.n_colours; ++c)
-    for (int i = L.colour_ptr[c]; i < L.colour_ptr[c + 1]; ++i) {
-      const int t = L.colour_tiles[i];
-      const TileInfo& T = L.tiles[t];
-      const int nloc = T.n_owned + T.n_foreign;
-      std::vector<int64_t> l2g(nloc);
-      for (int q = 0; q < T.n_owned; ++q) l2g[q] = T.dof_begin + q;
-      for (int q = 0; q < T.n_foreign; ++q) {
-        const int32_t g = L.foreign[T.foreign_begin + q];
-        if (g < 0 || g >= L.n_free) fail("foreign index out of range");
-        if (owner_tile[g] == t) fail("foreign DoF owned by its own tile");
-        if (tile_colour[owner_tile[g]] >= c) fail("foreign DoF owned by a tile of equal or higher colour");
-        l2g[T.n_owned + q] = g;
-      }
-      // cells: local/global consistency and sub-colours
-      const int n = T.n_cells;
-      if (T.n_sub < 1 || L.subptr[T.sub_begin] != 0 || L.subptr[T.sub_begin + T.n_sub] != n) fail("sub-colour offsets");
-      std::vector<char> seen(n, 0);
-      std::vector<int> local_sub(nloc, -1);
-      for (int sc = 0; sc < T.n_sub; ++sc)
-        for (int q = L.subptr[T.sub_begin + sc]; q < L.subptr[T.sub_begin + sc + 1]; ++q) {
-          const int a = L.perm[T.cell_begin + q];
-          if (a >= n || seen[a]) fail("sub-colour permutation");
-          seen[a] = 1;
-          const int ci = T.cell_begin + a;
-          for (int s = 0; s < NSLOT; ++s) {
-            const uint16_t ls = L.meta[ci].ls[s];
-            const int32_t gs = L.gstart[(size_t)ci * NSLOT + s];
-            if ((ls == LS_NONE) != (gs < 0)) fail("local and global maps disagree on a slot");
-            if (ls == LS_NONE) continue;
-            for (int o = 0; o < ndofs(s); ++o) {
-              if (ls + o >= nloc) fail("local index out of range");
-              if (l2g[ls + o] != gs + o) fail("local index maps to the wrong DoF");
-              if (local_sub[ls + o] == sc) fail("two cells of one sub-colour share a DoF");
-              local_sub[ls + o] = sc;
-            }
+  for (int t = 0; t < nt; ++t) {
+    const TileInfo& T = L.tiles[t];
+    const int nloc = T.n_owned + T.n_foreign;
+    std::vector<int64_t> l2g(nloc);
+    for (int q = 0; q < T.n_owned; ++q) l2g[q] = T.dof_begin + q;
+    for (int q = 0; q < T.n_foreign; ++q) {
+      const int32_t g = L.foreign[T.foreign_begin + q];
+      if (g < 0 || g >= L.n_free) fail("foreign index out of range");
+      if (owner_tile[g] == t) fail("foreign DoF owned by its own tile");
+      l2g[T.n_owned + q] = g;
+    }
+    const int n = T.n_cells;
+    if (T.n_sub < 1 || L.subptr[T.sub_begin] != 0 || L.subptr[T.sub_begin + T.n_sub] != n) fail("sub-colour offsets");
+    std::vector<char> seen(n, 0);
+    std::vector<int> local_sub(nloc, -1);
+    for (int sc = 0; sc < T.n_sub; ++sc)
+      for (int q = L.subptr[T.sub_begin + sc]; q < L.subptr[T.sub_begin + sc + 1]; ++q) {
+        const int a = L.perm[T.cell_begin + q];
+        if (a >= n || seen[a]) fail("sub-colour permutation");
+        seen[a] = 1;
+        const int ci = T.cell_begin + a;
+        if (L.meta[ci].sub != sc) fail("cell sub-colour disagrees with the permutation");
+        for (int s = 0; s < NSLOT; ++s) {
+          const uint16_t ls = L.meta[ci].ls[s];
+          const int32_t gs = L.gstart[(size_t)ci * NSLOT + s];
+          if ((ls == LS_NONE) != (gs < 0)) fail("local and global maps disagree on a slot");
+          if (ls == LS_NONE) continue;
+          for (int o = 0; o < ndofs(s); ++o) {
+            if (ls + o >= nloc) fail("local index out of range");
+            if (l2g[ls + o] != gs + o) fail("local index maps to the wrong DoF");
+            if (local_sub[ls + o] == sc) fail("two cells of one sub-colour share a DoF");
+            local_sub[ls + o] = sc;
           }
         }
-      // tiles of one colour never share a DoF
-      for (int q = 0; q < nloc; ++q) {
-        const int64_t g = l2g[q];
-        if (lastw[g] >= 0 && lastw[g] != t && tile_colour[lastw[g]] == c) fail("tiles of one colour share a DoF");
-        lastw[g] = t;
       }
+  }
+  // halo: every foreign slot appears exactly once, grouped under its DoF
+  const int64_t nf = (int64_t)L.foreign.size();
+  std::vector<char> hit(nf, 0);
+  const int64_t nh = (int64_t)L.halo_dofs.size();
+  if ((int64_t)L.halo_ptr.size() != nh + 1 || L.halo_ptr[0] != 0 || L.halo_ptr[nh] != nf) fail("halo offsets");
+  for (int64_t u = 0; u < nh; ++u) {
+    if (u > 0 && L.halo_dofs[u] <= L.halo_dofs[u - 1]) fail("halo DoFs not increasing");
+    for (int32_t e = L.halo_ptr[u]; e < L.halo_ptr[u + 1]; ++e) {
+      const int32_t src = L.halo_src[e];
+      if (src < 0 || src >= nf || hit[src]) fail("halo slot used twice or out of range");
+      hit[src] = 1;
+      if (L.foreign[src] != L.halo_dofs[u]) fail("halo slot under the wrong DoF");
     }
+  }
   // transfer ownership: every DoF owned by exactly one (cell, slot)
   std::vector<int8_t> owned(L.n_free, 0);
   for (int ci = 0; ci < nc; ++ci)

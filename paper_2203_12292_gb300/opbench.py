@@ -59,7 +59,7 @@ def main(argv=None):
     ms = e0.elapsed_time(e1) / a.reps
     info = mg.level_info(lev)
     print(json.dumps({"workload": w.name, "level": lev, "dtype": a.dtype, "n_free": n, "cells": info.n_cells,
-                      "tiles": info.n_tiles, "colours": info.n_colours, "tile_cells": info.tile_cells,
+                      "tiles": info.n_tiles, "halo_dofs": info.n_halo, "tile_cells": info.tile_cells,
                       "ms": ms, "gdofs": n / ms / 1e6}))
 
 
