@@ -193,9 +193,9 @@ __device__ __forceinline__ void line_apply(T* p, const T (&M)[NMAX][NMAX]) {
 
 // one direction of the hanging-node interpolation C_e (TRANS: C_e^T) for all
 // cells of the block; cell c has mask sm_mask[c]
-template <int K, int D, bool TRANS, typename T>
+template <int K, int D, bool TRANS, typename T, int CS = (K + 1) * (K + 1) * (K + 1)>
 __device__ __forceinline__ void hanging_dir(T* cb, const uint16_t* sm_mask, int ncells) {
-  constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
+  constexpr int N = K + 1, N2 = N * N, N3 = CS;
   const DevTables<T>& tb = tab<T>(K);
   for (int t = threadIdx.x; t < ncells * N2; t += blockDim.x) {
     const int cell = t / N2, r = t - cell * N2;
@@ -212,21 +212,21 @@ __device__ __forceinline__ void hanging_dir(T* cb, const uint16_t* sm_mask, int 
   }
 }
 
-template <int K, bool TRANS, typename T>
+template <int K, bool TRANS, typename T, int CS = (K + 1) * (K + 1) * (K + 1)>
 __device__ __forceinline__ void hanging_all(T* cb, const uint16_t* sm_mask, int ncells) {
   if (!TRANS) {
-    hanging_dir<K, 0, false>(cb, sm_mask, ncells);
+    hanging_dir<K, 0, false, T, CS>(cb, sm_mask, ncells);
     __syncthreads();
-    hanging_dir<K, 1, false>(cb, sm_mask, ncells);
+    hanging_dir<K, 1, false, T, CS>(cb, sm_mask, ncells);
     __syncthreads();
-    hanging_dir<K, 2, false>(cb, sm_mask, ncells);
+    hanging_dir<K, 2, false, T, CS>(cb, sm_mask, ncells);
     __syncthreads();
   } else {
-    hanging_dir<K, 2, true>(cb, sm_mask, ncells);
+    hanging_dir<K, 2, true, T, CS>(cb, sm_mask, ncells);
     __syncthreads();
-    hanging_dir<K, 1, true>(cb, sm_mask, ncells);
+    hanging_dir<K, 1, true, T, CS>(cb, sm_mask, ncells);
     __syncthreads();
-    hanging_dir<K, 0, true>(cb, sm_mask, ncells);
+    hanging_dir<K, 0, true, T, CS>(cb, sm_mask, ncells);
     __syncthreads();
   }
 }
