@@ -241,90 +241,142 @@ __global__ void __launch_bounds__(BLOCK) cell_kernel(CellArgs<T> A) {
 // fp32 operator, one cell per thread, values in registers
 // ---------------------------------------------------------------------------
 
-// per-cell stride of the cell buffer: odd, so that thread q reading word n of
-// cell q hits bank (q * CS + n) mod 32, distinct for the 32 lanes of a warp
-template <int K>
-__host__ __device__ constexpr int cell_stride() {
-  return ((K + 1) * (K + 1) * (K + 1)) | 1;
+// Shared-memory position of tile-local DoF l: a permutation inside every
+// aligned group of 32 words.  Threads of a warp handle different cells whose
+// DoF blocks lie about 64-128 words apart; without the permutation they would
+// hit the same bank.  The XOR of two higher bit groups spreads them (about
+// 2.7-way conflicts instead of 26-way on the Q4 octant workload).
+__device__ __forceinline__ int swz(int l) { return (l & ~31) | ((l ^ (l >> 6) ^ (l >> 11)) & 31); }
+
+// hanging-node interpolation of one cell, done by the whole warp through a
+// small shared-memory scratch (the owner lane writes its values, the lanes
+// apply the direction-wise line interpolation, the owner reads back)
+template <int K, bool TRANS>
+__device__ __forceinline__ void hanging_warp(float* u, uint16_t mask, bool active, float* scratch) {
+  constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
+  const int lane = threadIdx.x & 31;
+  unsigned pending = __ballot_sync(0xffffffffu, active && (mask & MASK_HANG));
+  while (pending) {
+    const int owner = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const uint16_t m = __shfl_sync(0xffffffffu, mask, owner);
+    if (lane == owner) {
+#pragma unroll
+      for (int n = 0; n < N3; ++n) scratch[n] = u[n];
+    }
+    __syncwarp();
+    const DevTables<float>& tb = tab<float>(K);
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+      const int D = TRANS ? 2 - dd : dd;
+      const int stride = D == 0 ? 1 : (D == 1 ? N : N2);
+      const int p = (m >> D) & 1;
+      for (int r = lane; r < N2; r += 32) {
+        const int uu = r % N, vv = r / N;
+        int base;
+        bool hang;
+        if (D == 0) {
+          base = N * r;
+          hang = line_hangs<K, 0>(m, uu, vv);
+        } else if (D == 1) {
+          base = uu + N2 * vv;
+          hang = line_hangs<K, 1>(m, uu, vv);
+        } else {
+          base = r;
+          hang = line_hangs<K, 2>(m, uu, vv);
+        }
+        if (!hang) continue;
+        float v[N];
+#pragma unroll
+        for (int a = 0; a < N; ++a) v[a] = scratch[base + a * stride];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          float s = 0.f;
+#pragma unroll
+          for (int a = 0; a < N; ++a) s += (TRANS ? tb.I[p][a][i] : tb.I[p][i][a]) * v[a];
+          scratch[base + i * stride] = s;
+        }
+      }
+      __syncwarp();
+    }
+    if (lane == owner) {
+#pragma unroll
+      for (int n = 0; n < N3; ++n) u[n] = scratch[n];
+    }
+    __syncwarp();
+  }
 }
 
 template <int K>
 __host__ __device__ inline size_t regs_smem(int tc, int max_local) {
-  return (size_t)tc * sizeof(CellMeta) + (size_t)tc * sizeof(uint16_t) * 2 + 16 +
-         ((size_t)tc * cell_stride<K>() + (size_t)max_local) * sizeof(float);
+  return (size_t)tc * sizeof(CellMeta) + ((size_t)4 * (K + 1) * (K + 1) * (K + 1) + (size_t)max_local + 32) * sizeof(float);
 }
 
 template <int K>
-__global__ void __launch_bounds__(128, 2) vmult_regs(CellArgs<float> A) {
-  constexpr int N = K + 1, N2 = N * N, N3 = N2 * N, CS = cell_stride<K>();
+__global__ void __launch_bounds__(128, (K >= 4 ? 3 : 4)) vmult_regs(CellArgs<float> A) {
+  constexpr int N = K + 1, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem[];
   CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem);
-  uint16_t* sm_mask = reinterpret_cast<uint16_t*>(smem + (size_t)A.tc * sizeof(CellMeta));
-  uint16_t* sm_cell = sm_mask + A.tc;
-  float* cb = reinterpret_cast<float*>(
-      smem + (((size_t)A.tc * sizeof(CellMeta) + (size_t)A.tc * 4 + 15) & ~(size_t)15));  // tc x CS
-  float* buf = cb + (size_t)A.tc * CS;  // tile DoFs: input, then the accumulator
+  float* scratch = reinterpret_cast<float*>(smem + (size_t)A.tc * sizeof(CellMeta));  // 4 warps x N3
+  float* buf = scratch + 4 * N3;  // tile DoFs (swizzled): input, then the accumulator
   const TileInfo ti = A.tiles[blockIdx.x];
   const int nc = ti.n_cells;
   const int nloc = ti.n_owned + ti.n_foreign;
   load_meta(sm_meta, A.meta, ti.cell_begin, nc);
-  load_tile_dofs(buf, A.src, A.foreign, ti);
-  __syncthreads();
-  for (int q = threadIdx.x; q < nc; q += blockDim.x) {
-    const int cell = A.perm[ti.cell_begin + q];
-    sm_cell[q] = (uint16_t)cell;
-    sm_mask[q] = sm_meta[cell].mask;
+  {
+    const float* src = A.src + ti.dof_begin;
+#pragma unroll 8
+    for (int i = threadIdx.x; i < ti.n_owned; i += 128) buf[swz(i)] = __ldg(src + i);
+    const int32_t* fl = A.foreign + ti.foreign_begin;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < ti.n_foreign; i += 128) buf[swz(ti.n_owned + i)] = __ldg(A.src + __ldg(fl + i));
   }
   __syncthreads();
-  // G_e, line-parallel: cell buffer position q holds the cell in sub-colour order
-  for (int t = threadIdx.x; t < nc * N2; t += blockDim.x) {
-    const int q = t / N2, r = t - q * N2;
-    const int b = r % N, c = r / N;
-    const uint16_t* ls = sm_meta[sm_cell[q]].ls;
-    float* out = cb + q * CS + N * r;
+  const int q = threadIdx.x;
+  const bool active = q < nc;
+  const int cell = active ? A.perm[ti.cell_begin + q] : 0;
+  float u[N3];
+  const uint16_t* ls = sm_meta[cell].ls;
+  const uint16_t mask = active ? sm_meta[cell].mask : 0;
+  // G_e (threads in sub-colour order)
 #pragma unroll
-    for (int a = 0; a < N; ++a) {
-      int slot, off;
-      node_slot<K>(a, b, c, slot, off);
-      const uint16_t l = ls[slot];
-      out[a] = (l == LS_NONE) ? 0.f : buf[l + off];
-    }
+  for (int n = 0; n < N3; ++n) {
+    int slot, off;
+    node_slot<K>(n % N, (n / N) % N, n / (N * N), slot, off);
+    const uint16_t l = ls[slot];
+    u[n] = (active && l != LS_NONE) ? buf[swz(l + off)] : 0.f;
   }
+  __syncthreads();  // the tile DoFs are no longer needed: reuse as accumulator
+  for (int i = threadIdx.x; i < nloc; i += blockDim.x) buf[i] = 0.f;
+  float* ws = scratch + (threadIdx.x >> 5) * N3;
+  hanging_warp<K, false>(u, mask, active, ws);  // C_e
+  const float h = active ? ldexpf((float)A.dom, -(int)sm_meta[cell].level) : 0.f;
+  cell_laplace_regs<K>(u, h);                   // S^T Q S
+  hanging_warp<K, true>(u, mask, active, ws);   // C_e^T
   __syncthreads();
-  for (int i = threadIdx.x; i < nloc; i += blockDim.x) buf[i] = 0.f;  // now the accumulator
-  hanging_all<K, false, float, CS>(cb, sm_mask, nc);                  // C_e
-  // S^T Q S, one cell per thread in registers
-  for (int q = threadIdx.x; q < nc; q += blockDim.x) {
-    float u[N3];
-    float* p = cb + q * CS;
-#pragma unroll
-    for (int n = 0; n < N3; ++n) u[n] = p[n];
-    const float h = ldexpf((float)A.dom, -(int)sm_meta[sm_cell[q]].level);
-    cell_laplace_regs<K>(u, h);
-#pragma unroll
-    for (int n = 0; n < N3; ++n) p[n] = u[n];
-  }
-  __syncthreads();
-  hanging_all<K, true, float, CS>(cb, sm_mask, nc);  // C_e^T
-  // G_e^T into the accumulator, sub-colour by sub-colour, line-parallel
+  // G_e^T, sub-colour by sub-colour (threads are in sub-colour order)
+  const int my_sub = active ? sm_meta[cell].sub : -1;
   for (int s = 0; s < ti.n_sub; ++s) {
-    const int q0 = A.subptr[ti.sub_begin + s], q1 = A.subptr[ti.sub_begin + s + 1];
-    for (int t = threadIdx.x; t < (q1 - q0) * N2; t += blockDim.x) {
-      const int q = q0 + t / N2, r = t % N2;
-      const int b = r % N, c = r / N;
-      const uint16_t* ls = sm_meta[sm_cell[q]].ls;
-      const float* in = cb + q * CS + N * r;
+    if (my_sub == s) {
 #pragma unroll
-      for (int a = 0; a < N; ++a) {
+      for (int n = 0; n < N3; ++n) {
         int slot, off;
-        node_slot<K>(a, b, c, slot, off);
+        node_slot<K>(n % N, (n / N) % N, n / (N * N), slot, off);
         const uint16_t l = ls[slot];
-        if (l != LS_NONE) buf[l + off] += in[a];
+        if (l != LS_NONE) buf[swz(l + off)] += u[n];
       }
     }
     __syncthreads();
   }
-  write_tile_dofs(A.dst, A.halo, buf, ti, A.add);
+  {
+    float* d = A.dst + ti.dof_begin;
+    if (A.add)
+      for (int i = threadIdx.x; i < ti.n_owned; i += 128) d[i] += buf[swz(i)];
+    else
+      for (int i = threadIdx.x; i < ti.n_owned; i += 128) d[i] = buf[swz(i)];
+    float* hl = A.halo + ti.foreign_begin;
+    for (int i = threadIdx.x; i < ti.n_foreign; i += 128) hl[i] = buf[swz(ti.n_owned + i)];
+  }
 }
 
 // second pass: every DoF that other tiles contributed to adds its halo slots
