@@ -309,20 +309,79 @@ __device__ __forceinline__ void hanging_warp(float* u, uint16_t mask, bool activ
 
 template <int K>
 __host__ __device__ inline size_t regs_smem(int tc, int max_local) {
-  return (size_t)tc * sizeof(CellMeta) + ((size_t)4 * (K + 1) * (K + 1) * (K + 1) + (size_t)max_local + 32) * sizeof(float);
+  return (size_t)tc * (NSLOT + 3) * sizeof(uint16_t) + 16 +
+         ((size_t)4 * (K + 1) * (K + 1) * (K + 1) + (size_t)max_local + 32) * sizeof(float);
+}
+
+// 27-bit set of the slots of a cell that lie on a hanging face or edge
+__device__ __forceinline__ uint32_t hanging_slots(uint16_t m) {
+  uint32_t hs = 0;
+  if (!(m & MASK_HANG)) return 0;
+  const int p0 = m & 1, p1 = (m >> 1) & 1, p2 = (m >> 2) & 1;
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) {
+    const int c0 = s % 3, c1 = (s / 3) % 3, c2 = s / 9;
+    bool h = (((m >> 3) & 1) && c0 == 2 * p0) || (((m >> 4) & 1) && c1 == 2 * p1) ||
+             (((m >> 5) & 1) && c2 == 2 * p2) || (((m >> 6) & 1) && c1 == 2 * p1 && c2 == 2 * p2) ||
+             (((m >> 7) & 1) && c0 == 2 * p0 && c2 == 2 * p2) || (((m >> 8) & 1) && c0 == 2 * p0 && c1 == 2 * p1);
+    if (h) hs |= 1u << s;
+  }
+  return hs;
+}
+
+// G_e^T for the nodes of side step SIG: coordinate == K along the "high"
+// axes of SIG, < K along the others.  Two cells that share an entity through
+// regular (non-hanging) slots see it from opposite sides along at least one
+// axis, so no two lanes add to the same DoF within one step.
+template <int K, int SIG, int NODE = 0>
+__device__ __forceinline__ void scatter_side(float* buf, const float* u, const uint16_t* sm_ls, int tc, int q,
+                                             uint32_t skip) {
+  constexpr int N = K + 1, N3 = N * N * N;
+  if constexpr (NODE < N3) {
+    constexpr int a = NODE % N, b = (NODE / N) % N, c = NODE / (N * N);
+    constexpr bool in = ((SIG & 1) ? a == K : a < K) && ((SIG & 2) ? b == K : b < K) && ((SIG & 4) ? c == K : c < K);
+    if constexpr (in) {
+      constexpr int ca = a == 0 ? 0 : (a == K ? 2 : 1), cb = b == 0 ? 0 : (b == K ? 2 : 1),
+                    cc = c == 0 ? 0 : (c == K ? 2 : 1);
+      constexpr int slot = ca + 3 * cb + 9 * cc;
+      constexpr int off = (ca == 1 ? (a - 1) : 0) + (cb == 1 ? (b - 1) * (ca == 1 ? (K - 1) : 1) : 0) +
+                          (cc == 1 ? (c - 1) * ((ca == 1 ? (K - 1) : 1) * (cb == 1 ? (K - 1) : 1)) : 0);
+      const uint16_t l = sm_ls[slot * tc + q];
+      if (l != LS_NONE && !((skip >> slot) & 1u)) buf[swz(l + off)] += u[NODE];
+    }
+    scatter_side<K, SIG, NODE + 1>(buf, u, sm_ls, tc, q, skip);
+  }
 }
 
 template <int K>
 __global__ void __launch_bounds__(128, (K >= 4 ? 3 : 4)) vmult_regs(CellArgs<float> A) {
   constexpr int N = K + 1, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem[];
-  CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem);
-  float* scratch = reinterpret_cast<float*>(smem + (size_t)A.tc * sizeof(CellMeta));  // 4 warps x N3
+  const int tc = A.tc;
+  uint16_t* sm_ls = reinterpret_cast<uint16_t*>(smem);  // [slot][position]
+  uint16_t* sm_mask = sm_ls + NSLOT * tc;
+  uint16_t* sm_lev = sm_mask + tc;
+  uint16_t* sm_sub = sm_lev + tc;
+  float* scratch = reinterpret_cast<float*>(smem + (((size_t)tc * (NSLOT + 3) * 2 + 15) & ~(size_t)15));
   float* buf = scratch + 4 * N3;  // tile DoFs (swizzled): input, then the accumulator
+  __shared__ int any_hanging;
   const TileInfo ti = A.tiles[blockIdx.x];
   const int nc = ti.n_cells;
   const int nloc = ti.n_owned + ti.n_foreign;
-  load_meta(sm_meta, A.meta, ti.cell_begin, nc);
+  if (threadIdx.x == 0) any_hanging = 0;
+  // metadata, transposed to [slot][cell] so that lanes read consecutive words
+  for (int i = threadIdx.x; i < nc * 32; i += 128) {
+    const int cell = i >> 5, w = i & 31;
+    const uint16_t v = reinterpret_cast<const uint16_t*>(A.meta + ti.cell_begin + cell)[w];
+    if (w < NSLOT)
+      sm_ls[w * tc + cell] = v;
+    else if (w == NSLOT)
+      sm_mask[cell] = v;
+    else if (w == NSLOT + 1) {
+      sm_lev[cell] = v & 0xFF;
+      sm_sub[cell] = v >> 8;
+    }
+  }
   {
     const float* src = A.src + ti.dof_begin;
 #pragma unroll 8
@@ -332,41 +391,63 @@ __global__ void __launch_bounds__(128, (K >= 4 ? 3 : 4)) vmult_regs(CellArgs<flo
     for (int i = threadIdx.x; i < ti.n_foreign; i += 128) buf[swz(ti.n_owned + i)] = __ldg(A.src + __ldg(fl + i));
   }
   __syncthreads();
-  const int q = threadIdx.x;
+  const int q = threadIdx.x;  // thread q handles cell q of the tile (Morton order)
   const bool active = q < nc;
-  const int cell = active ? A.perm[ti.cell_begin + q] : 0;
+  const int qq = active ? q : 0;
   float u[N3];
-  const uint16_t* ls = sm_meta[cell].ls;
-  const uint16_t mask = active ? sm_meta[cell].mask : 0;
-  // G_e (threads in sub-colour order)
+  const uint16_t mask = active ? sm_mask[qq] : 0;
+  // G_e
 #pragma unroll
   for (int n = 0; n < N3; ++n) {
     int slot, off;
     node_slot<K>(n % N, (n / N) % N, n / (N * N), slot, off);
-    const uint16_t l = ls[slot];
+    const uint16_t l = sm_ls[slot * tc + qq];
     u[n] = (active && l != LS_NONE) ? buf[swz(l + off)] : 0.f;
   }
   __syncthreads();  // the tile DoFs are no longer needed: reuse as accumulator
-  for (int i = threadIdx.x; i < nloc; i += blockDim.x) buf[i] = 0.f;
+  // the swizzle permutes inside groups of 32: clear the whole last group
+  for (int i = threadIdx.x; i < ((nloc + 31) & ~31); i += blockDim.x) buf[i] = 0.f;
+  if (mask & MASK_HANG) any_hanging = 1;
   float* ws = scratch + (threadIdx.x >> 5) * N3;
   hanging_warp<K, false>(u, mask, active, ws);  // C_e
-  const float h = active ? ldexpf((float)A.dom, -(int)sm_meta[cell].level) : 0.f;
+  const float h = active ? ldexpf((float)A.dom, -(int)sm_lev[qq]) : 0.f;
   cell_laplace_regs<K>(u, h);                   // S^T Q S
   hanging_warp<K, true>(u, mask, active, ws);   // C_e^T
+  const uint32_t hs = hanging_slots(mask);
+  const uint32_t skip = active ? hs : 0x7FFFFFFu;
   __syncthreads();
-  // G_e^T, sub-colour by sub-colour (threads are in sub-colour order)
-  const int my_sub = active ? sm_meta[cell].sub : -1;
-  for (int s = 0; s < ti.n_sub; ++s) {
-    if (my_sub == s) {
+  // G_e^T: regular slots in eight side steps, all lanes at once
+  scatter_side<K, 0>(buf, u, sm_ls, tc, qq, skip);
+  __syncthreads();
+  scatter_side<K, 1>(buf, u, sm_ls, tc, qq, skip);
+  __syncthreads();
+  scatter_side<K, 2>(buf, u, sm_ls, tc, qq, skip);
+  __syncthreads();
+  scatter_side<K, 3>(buf, u, sm_ls, tc, qq, skip);
+  __syncthreads();
+  scatter_side<K, 4>(buf, u, sm_ls, tc, qq, skip);
+  __syncthreads();
+  scatter_side<K, 5>(buf, u, sm_ls, tc, qq, skip);
+  __syncthreads();
+  scatter_side<K, 6>(buf, u, sm_ls, tc, qq, skip);
+  __syncthreads();
+  scatter_side<K, 7>(buf, u, sm_ls, tc, qq, skip);
+  __syncthreads();
+  // hanging slots (several fine cells reach one coarse entity): sub-colours
+  if (any_hanging) {
+    const int my_sub = (active && hs) ? sm_sub[qq] : -1;
+    for (int sc = 0; sc < ti.n_sub; ++sc) {
+      if (my_sub == sc) {
 #pragma unroll
-      for (int n = 0; n < N3; ++n) {
-        int slot, off;
-        node_slot<K>(n % N, (n / N) % N, n / (N * N), slot, off);
-        const uint16_t l = ls[slot];
-        if (l != LS_NONE) buf[swz(l + off)] += u[n];
+        for (int n = 0; n < N3; ++n) {
+          int slot, off;
+          node_slot<K>(n % N, (n / N) % N, n / (N * N), slot, off);
+          const uint16_t l = sm_ls[slot * tc + qq];
+          if (l != LS_NONE && ((hs >> slot) & 1u)) buf[swz(l + off)] += u[n];
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
   {
     float* d = A.dst + ti.dof_begin;
