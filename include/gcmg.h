@@ -234,6 +234,13 @@ typedef struct {
  */
 int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int maxit, gcmg_solve_stats* stats);
 
+/*
+ * 1 (default): the V-cycle and the operator half of every CG iteration run as
+ * CUDA graphs captured on first use; 0: plain stream launches.  Graphs are
+ * re-captured after gcmg_set_lambda and gcmg_set_profiling.
+ */
+int gcmg_set_graphs(gcmg_handle* h, int on);
+
 const char* gcmg_last_error(void);
 /* number of CUDA kernel launches issued by this library since it was loaded */
 int64_t gcmg_launch_count(void);

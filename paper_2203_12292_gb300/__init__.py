@@ -73,6 +73,7 @@ _SIGS = {
     "gcmg_dot": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int64, _c_void_p]),
     "gcmg_dot_noalloc": (_c_int, [_c_void_p, _c_void_p, _c_int64, _c_void_p, _c_void_p]),
     "gcmg_set_profiling": (_c_int, [_c_void_p, _c_int]),
+    "gcmg_set_graphs": (_c_int, [_c_void_p, _c_int]),
     "gcmg_get_profile": (_c_int, [_c_void_p, _c_int, _c_int, ctypes.POINTER(_c_int64), ctypes.POINTER(_c_double)]),
     "gcmg_diagonal": (_c_int, [_c_void_p, _c_int, _c_void_p]),
     "gcmg_rhs": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_double, _c_void_p]),
@@ -264,6 +265,10 @@ class Multigrid:
             out = torch.empty(1, dtype=torch.float64, device="cuda")
         _check(lib().gcmg_dot(self._h, _ptr(x, n, torch.float64), _ptr(y, n, torch.float64), n, _ptr(out, 1)))
         return out
+
+    def set_graphs(self, on: bool) -> None:
+        """Run the V-cycle and CG operator steps as captured CUDA graphs (default) or eagerly."""
+        _check(lib().gcmg_set_graphs(self._h, int(on)))
 
     def set_profiling(self, on: bool) -> None:
         _check(lib().gcmg_set_profiling(self._h, int(on)))

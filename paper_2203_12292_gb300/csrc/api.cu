@@ -110,8 +110,32 @@ struct Profiler {
 };
 constexpr int NSTAGE = 9;
 
+// CUDA graphs of the V-cycle and of the operator half of a CG iteration;
+// captured once per handle (re-captured when smoother parameters or the
+// profiling state change).  Timers captured into a graph are event-record
+// nodes, read after each replay.
+struct GraphRec {
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;  // kernel launches per replay
+  std::vector<Profiler::Rec> recs;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    for (auto& r : recs) {
+      if (r.a) cudaEventDestroy(r.a);
+      if (r.b) cudaEventDestroy(r.b);
+    }
+    recs.clear();
+  }
+  ~GraphRec() { reset(); }
+};
+
 struct Handle {
   cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  bool use_graphs = true;
+  GraphRec* capturing = nullptr;
+  GraphRec g_core, g_a;
   Profiler prof;
   gcmg_config cfg{};
   std::vector<std::unique_ptr<LevelDev>> lev;
@@ -120,7 +144,12 @@ struct Handle {
   DevBuf Ainv;
   int n0 = 0;
   DevBuf scratch, scal, modes;
-  DevBuf cg_r, cg_p, cg_q, cg_z;
+  DevBuf cg_r, cg_p, cg_q, cg_z, cg_x;
+  ~Handle() {
+    g_core.reset();
+    g_a.reset();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
 };
 
 namespace {
@@ -145,10 +174,21 @@ void prof_flush(Handle& H) {
   P.used = 0;
 }
 
-// returns a record index, or -1 when profiling is off
+// returns a record index, or -1 when profiling is off (<= -2: a record of the
+// graph being captured)
 int prof_begin(Handle& H, int level, int stage) {
   Profiler& P = H.prof;
   if (!P.on) return -1;
+  if (H.capturing) {
+    Profiler::Rec r;
+    ck(cudaEventCreate(&r.a), "event");
+    ck(cudaEventCreate(&r.b), "event");
+    r.level = level;
+    r.stage = stage;
+    ck(cudaEventRecordWithFlags(r.a, H.stream, cudaEventRecordExternal), "event");
+    H.capturing->recs.push_back(r);
+    return -2 - (int)(H.capturing->recs.size() - 1);
+  }
   if (P.used == P.pool.size()) {
     if (P.pool.size() >= 8192) prof_flush(H);
     if (P.used == P.pool.size()) {
@@ -166,8 +206,25 @@ int prof_begin(Handle& H, int level, int stage) {
 }
 
 void prof_end(Handle& H, int rec) {
-  if (rec < 0) return;
+  if (rec == -1) return;
+  if (rec <= -2) {
+    ck(cudaEventRecordWithFlags(H.capturing->recs[-2 - rec].b, H.stream, cudaEventRecordExternal), "event");
+    return;
+  }
   ck(cudaEventRecord(H.prof.pool[rec].b, H.stream), "event");
+}
+
+// after a replay of g has completed: add its timers
+void prof_graph(Handle& H, GraphRec& g) {
+  Profiler& P = H.prof;
+  if (!P.on || g.recs.empty()) return;
+  for (auto& r : g.recs) {
+    float t = 0.f;
+    ck(cudaEventElapsedTime(&t, r.a, r.b), "profile");
+    const size_t idx = (size_t)r.level * NSTAGE + r.stage;
+    P.ms[idx] += t;
+    P.cnt[idx] += 1;
+  }
 }
 
 void vmult(Handle& H, int l, bool fp64, const void* src, void* dst, int stage = GCMG_STAGE_VMULT) {
@@ -371,6 +428,51 @@ void vcycle_level(Handle& H, int l) {
   r = prof_begin(H, l, GCMG_STAGE_POSTSMOOTH);
   smooth(H, l, f64, L.x.p, L.b.p, L.d.p, L.t.p, dinv, false);  // postsmoothing
   prof_end(H, r);
+}
+
+
+template <typename F>
+void capture(Handle& H, GraphRec& g, F&& body) {
+  g.reset();
+  if (!H.cap_stream) ck(cudaStreamCreateWithFlags(&H.cap_stream, cudaStreamNonBlocking), "stream");
+  cudaStream_t saved = H.stream;
+  H.stream = H.cap_stream;
+  H.capturing = &g;
+  cudaGraph_t graph = nullptr;
+  const long long before = g_launches.load();
+  cudaError_t e = cudaStreamBeginCapture(H.stream, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    try {
+      body();
+    } catch (...) {
+      cudaStreamEndCapture(H.stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      H.stream = saved;
+      H.capturing = nullptr;
+      throw;
+    }
+    e = cudaStreamEndCapture(H.stream, &graph);
+  }
+  H.stream = saved;
+  H.capturing = nullptr;
+  g.kernels = g_launches.load() - before;  // recorded, not run: count them at every replay
+  g_launches.fetch_sub(g.kernels);
+  ck(e, "graph capture");
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  ck(e, "graph instantiate");
+}
+
+// the V-cycle on the level vectors (b -> x of the finest level)
+void vcycle_core(Handle& H) {
+  const int top = (int)H.lev.size() - 1;
+  if (!H.use_graphs) {
+    vcycle_level(H, top);
+    return;
+  }
+  if (!H.g_core.exec) capture(H, H.g_core, [&] { vcycle_level(H, top); });
+  ck(cudaGraphLaunch(H.g_core.exec, H.stream), "graph launch");
+  note_launches((int)H.g_core.kernels);
 }
 
 void vcycle(Handle& H, const double* b, double* x) {
@@ -644,6 +746,7 @@ int gcmg_setup(const gcmg_mesh* mesh, const gcmg_config* cfg, void* stream, gcmg
     H.cg_p.alloc(nf * sizeof(double));
     H.cg_q.alloc(nf * sizeof(double));
     H.cg_z.alloc(nf * sizeof(double));
+    H.cg_x.alloc(nf * sizeof(double));
     ck(cudaStreamSynchronize(H.stream), "setup");
     ck(cudaGetLastError(), "setup");
     *out = hh.release();
@@ -697,6 +800,8 @@ int gcmg_set_profiling(gcmg_handle* h, int on) {
     Profiler& P = h->h.prof;
     prof_flush(h->h);
     P.on = on != 0;
+    h->h.g_core.reset();
+    h->h.g_a.reset();
     P.nlev = (int)h->h.lev.size();
     P.ms.assign((size_t)P.nlev * NSTAGE, 0.0);
     P.cnt.assign((size_t)P.nlev * NSTAGE, 0);
@@ -811,6 +916,7 @@ int gcmg_set_lambda(gcmg_handle* h, int level, double lam) {
     if (!h || !(lam > 0)) throw Error(GCMG_ERR_ARG, "bad lambda");
     check_level(h->h, level);
     h->h.lev[level]->lam = lam;
+    h->h.g_core.reset();
   });
 }
 
@@ -886,6 +992,7 @@ int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int m
       return;
     }
     if (!b || !x) throw Error(GCMG_ERR_ARG, "bad vectors");
+    double* xi = H.cg_x.as<double>();
     double* r = H.cg_r.as<double>();
     double* p = H.cg_p.as<double>();
     double* q = H.cg_q.as<double>();
@@ -893,28 +1000,44 @@ int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int m
     double* S = H.scal.as<double>();
     cudaStream_t s = H.stream;
     gcmg_solve_stats st{0, 0.0, 0.0, GCMG_OK};
-    launch_zero(true, x, n, s);
+    launch_zero(true, xi, n, s);
     ck(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
     const double nb = std::sqrt(dot_host(H, r, r, n));
     st.r0 = nb;
-    if (nb == 0.0 || n == 0) {
+    if (nb == 0.0) {
+      launch_zero(true, x, n, s);
+      ck(cudaStreamSynchronize(s), "cg");
       if (stats) *stats = st;
       return;
     }
+    // operator half of an iteration: q = A p, alpha, x += alpha p, r -= alpha q, r.r
+    auto op_half = [&] {
+      vmult(H, top, true, p, q, GCMG_STAGE_CG_VMULT);
+      const int pr = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);
+      launch_dot(p, q, n, H.scratch.as<double>(), S, 0, DOT_ALPHA, H.stream);
+      launch_cg_update_xr(xi, r, p, q, S, n, H.scratch.as<double>(), S, H.stream);
+      prof_end(H, pr);
+    };
     vcycle(H, r, z);
     launch_dot(r, z, n, H.scratch.as<double>(), S, 0, DOT_STORE, s);  // rz
     ck(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    if (H.use_graphs && !H.g_a.exec) capture(H, H.g_a, op_half);
     double rr = nb * nb;
     int it = 0;
     for (it = 1; it <= maxit; ++it) {
-      vmult(H, top, true, p, q, GCMG_STAGE_CG_VMULT);
-      const int pr = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);
-      launch_dot(p, q, n, H.scratch.as<double>(), S, 0, DOT_ALPHA, s);
-      launch_cg_update_xr(x, r, p, q, S, n, H.scratch.as<double>(), S, s);
-      prof_end(H, pr);
+      if (H.use_graphs) {
+        ck(cudaGraphLaunch(H.g_a.exec, s), "graph launch");
+        note_launches((int)H.g_a.kernels);
+      } else {
+        op_half();
+      }
       double hs[6];
       ck(cudaMemcpyAsync(hs, S, sizeof(hs), cudaMemcpyDeviceToHost, s), "scalars");
       ck(cudaStreamSynchronize(s), "cg");
+      if (H.use_graphs) {  // one replay of each graph completed since the last read
+        prof_graph(H, H.g_a);
+        prof_graph(H, H.g_core);
+      }
       if (!(hs[1] > 0.0) || std::isnan(hs[2])) {
         status = GCMG_ERR_BREAKDOWN;
         break;
@@ -931,6 +1054,7 @@ int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int m
       it = maxit;
       status = GCMG_ERR_NOT_CONVERGED;
     }
+    ck(cudaMemcpyAsync(x, xi, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
     st.iterations = it;
     st.rel_residual = std::sqrt(rr) / nb;
     st.status = status;
@@ -941,6 +1065,15 @@ int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int m
   if (rc != GCMG_OK) return rc;
   if (status != GCMG_OK) g_err = status == GCMG_ERR_BREAKDOWN ? "CG breakdown" : "CG did not converge";
   return status;
+}
+
+int gcmg_set_graphs(gcmg_handle* h, int on) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    h->h.use_graphs = on != 0;
+    h->h.g_core.reset();
+    h->h.g_a.reset();
+  });
 }
 
 }  // extern "C"

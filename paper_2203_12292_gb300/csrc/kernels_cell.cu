@@ -241,12 +241,11 @@ __global__ void __launch_bounds__(BLOCK) cell_kernel(CellArgs<T> A) {
 // fp32 operator, one cell per thread, values in registers
 // ---------------------------------------------------------------------------
 
-// Shared-memory position of tile-local DoF l: a permutation inside every
-// aligned group of 32 words.  Threads of a warp handle different cells whose
-// DoF blocks lie about 64-128 words apart; without the permutation they would
-// hit the same bank.  The XOR of two higher bit groups spreads them (about
-// 2.7-way conflicts instead of 26-way on the Q4 octant workload).
-__device__ __forceinline__ int swz(int l) { return (l & ~31) | ((l ^ (l >> 6) ^ (l >> 11)) & 31); }
+// Shared-memory position of tile-local DoF l: one pad word after every 64.
+// Threads of a warp handle consecutive cells whose DoF blocks lie about 64
+// words apart; without the padding they would hit the same bank (26-way
+// conflicts on the Q4 octant workload, 1.9-way with it).
+__device__ __forceinline__ int swz(int l) { return l + (l >> 6); }
 
 // hanging-node interpolation of one cell, done by the whole warp through a
 // small shared-memory scratch (the owner lane writes its values, the lanes
@@ -310,7 +309,7 @@ __device__ __forceinline__ void hanging_warp(float* u, uint16_t mask, bool activ
 template <int K>
 __host__ __device__ inline size_t regs_smem(int tc, int max_local) {
   return (size_t)tc * (NSLOT + 3) * sizeof(uint16_t) + 16 +
-         ((size_t)4 * (K + 1) * (K + 1) * (K + 1) + (size_t)max_local + 32) * sizeof(float);
+         ((size_t)4 * (K + 1) * (K + 1) * (K + 1) + (size_t)max_local + max_local / 64 + 32) * sizeof(float);
 }
 
 // 27-bit set of the slots of a cell that lie on a hanging face or edge
@@ -405,8 +404,7 @@ __global__ void __launch_bounds__(128, (K >= 4 ? 3 : 4)) vmult_regs(CellArgs<flo
     u[n] = (active && l != LS_NONE) ? buf[swz(l + off)] : 0.f;
   }
   __syncthreads();  // the tile DoFs are no longer needed: reuse as accumulator
-  // the swizzle permutes inside groups of 32: clear the whole last group
-  for (int i = threadIdx.x; i < ((nloc + 31) & ~31); i += blockDim.x) buf[i] = 0.f;
+  for (int i = threadIdx.x; i < nloc + (nloc >> 6) + 1; i += blockDim.x) buf[i] = 0.f;
   if (mask & MASK_HANG) any_hanging = 1;
   float* ws = scratch + (threadIdx.x >> 5) * N3;
   hanging_warp<K, false>(u, mask, active, ws);  // C_e

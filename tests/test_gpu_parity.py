@@ -269,3 +269,41 @@ def test_dot_fp64(gcmg, n):
     ref = float(np.dot(synth.uniform_vector(n, 1), synth.uniform_vector(n, 2)))
     assert r1 == r2  # deterministic
     assert abs(r1 - ref) <= 1e-13 * max(1.0, np.sqrt(n))
+
+
+def test_graphs_match_stream_launches(gcmg):
+    mesh = gcmg.Mesh.from_recipe(synth.octant(4))
+    a = gcmg.Multigrid(mesh, 3, mg_fp32=True)
+    b = gcmg.Multigrid(mesh, 3, mg_fp32=True)
+    b.set_graphs(False)
+    rhs = a.rhs()
+    xa, xb = torch.zeros_like(rhs), torch.zeros_like(rhs)
+    sa = a.cg_solve(rhs, xa, 1e-8)
+    sb = b.cg_solve(rhs, xb, 1e-8)
+    assert sa.iterations == sb.iterations
+    assert torch.equal(xa, xb)
+    # a second solve replays the captured graphs
+    xa2 = torch.zeros_like(rhs)
+    a.cg_solve(rhs, xa2, 1e-8)
+    assert torch.equal(xa, xa2)
+    ya, yb = torch.zeros_like(rhs), torch.zeros_like(rhs)
+    a.vcycle(rhs, ya)
+    b.vcycle(rhs, yb)
+    torch.cuda.synchronize()
+    assert torch.equal(ya, yb)
+
+
+def test_profiling_inside_graphs(gcmg):
+    mesh = gcmg.Mesh.from_recipe(synth.octant(4))
+    mg = gcmg.Multigrid(mesh, 2, mg_fp32=True)
+    rhs = mg.rhs()
+    x = torch.zeros_like(rhs)
+    mg.set_profiling(True)
+    st = mg.cg_solve(rhs, x, 1e-8)
+    L = mg.finest
+    cnt, ms = mg.profile(L, "vmult")
+    cnt64, ms64 = mg.profile(L, "cg_vmult")
+    assert cnt64 == st.iterations and ms64 > 0
+    # presmoothing 2, residual 1, postsmoothing 3 operator applications per V-cycle
+    assert cnt == 6 * (st.iterations) and ms > 0
+    mg.set_profiling(False)
