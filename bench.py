@@ -238,6 +238,15 @@ def main():
     cnt64, vms64 = mg.profile(L, "cg_vmult")
     stage_ms = {s: mg.profile(L, s)[1] / args.steps for s in g.STAGES}
     coarse_ms = sum(mg.profile(l, s)[1] for l in range(L) for s in g.STAGES) / args.steps
+    per_level = []
+    for l in range(mg.num_levels):
+        row = {"level": l, "n_free": mg.n_free(l), "cells": mg.level_info(l).n_cells}
+        for s_ in ("vmult", "presmooth", "residual", "restrict", "coarse", "prolongate", "postsmooth"):
+            c_, m_ = mg.profile(l, s_)
+            row[s_ + "_ms"] = m_ / args.steps
+            if s_ == "vmult":
+                row["vmult_calls"] = c_ / args.steps
+        per_level.append(row)
     mg.set_profiling(False)
     t_vmult = vms / cnt  # ms
     value = n / (t_vmult * 1e-3) / 1e9
@@ -301,6 +310,7 @@ def main():
             "vmult": {"fp32_ms": t_vmult, "fp32_gdofs": value / world, "fp64_ms": vms64 / cnt64,
                       "fp64_gdofs": value64},
             "stage_ms_per_step_finest": stage_ms, "coarser_levels_ms_per_step": coarse_ms,
+            "per_level_ms_per_step": per_level,
             "setup_s": setup_s,
         }
         print(json.dumps(res), flush=True)
