@@ -154,7 +154,7 @@ struct Handle {
 
 namespace {
 
-int default_tile_cells(int) { return 128; }
+int default_tile_cells(int) { return 64; }
 
 void check_level(const Handle& h, int level) {
   if (level < 0 || level >= (int)h.lev.size()) throw Error(GCMG_ERR_ARG, "level out of range");

@@ -352,24 +352,246 @@ __device__ __forceinline__ void scatter_side(float* buf, const float* u, const u
   }
 }
 
+// ---------------------------------------------------------------------------
+// fp32 operator, N = k+1 threads per cell: thread c of a cell holds the
+// z-slab c (N^2 values) in registers; x and y sweeps run in registers, the z
+// sweeps after a transpose through the cell's shared-memory region (the N
+// threads of a cell sit in one warp, so the transposes need only warp
+// synchronisation).  Small code, about 60 registers per thread.
+// ---------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(128, (K >= 4 ? 3 : 4)) vmult_regs(CellArgs<float> A) {
-  constexpr int N = K + 1, N3 = N * N * N;
+struct SlabGeom {
+  static constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
+  static constexpr int CPW = 32 / N;  // cells per warp
+};
+
+template <int K>
+__host__ __device__ inline int slab_warps(int tc) {
+  return (tc + SlabGeom<K>::CPW - 1) / SlabGeom<K>::CPW;
+}
+
+template <int K>
+__host__ __device__ inline size_t slab_smem(int tc, int max_local) {
+  constexpr int N3 = SlabGeom<K>::N3;
+  return (size_t)tc * (NSLOT + 3) * sizeof(uint16_t) + 16 +
+         ((size_t)N3 + (size_t)(tc + 1) * N3 + (size_t)max_local + max_local / 64 + 32) * sizeof(float);
+}
+
+// slot (runtime class along z) and offset of node (a, b, c)
+template <int K, int a, int b>
+__device__ __forceinline__ void slab_slot(int c, int cc, int& slot, int& off) {
+  constexpr int ca = a == 0 ? 0 : (a == K ? 2 : 1), cb = b == 0 ? 0 : (b == K ? 2 : 1);
+  constexpr int m1 = ca == 1 ? (K - 1) : 1;
+  constexpr int m2 = m1 * (cb == 1 ? (K - 1) : 1);
+  constexpr int o0 = (ca == 1 ? a - 1 : 0) + (cb == 1 ? (b - 1) * m1 : 0);
+  slot = ca + 3 * cb + 9 * cc;
+  off = o0 + (cc == 1 ? (c - 1) * m2 : 0);
+}
+
+template <int K, int P = 0>
+__device__ __forceinline__ void slab_gather(float* sv, const float* buf, const uint16_t* sm_ls, int tc, int q, int c,
+                                            int cc, bool active) {
+  constexpr int N = K + 1;
+  if constexpr (P < N * N) {
+    int slot, off;
+    slab_slot<K, P % N, P / N>(c, cc, slot, off);
+    const uint16_t l = sm_ls[slot * tc + q];
+    sv[P] = (active && l != LS_NONE) ? buf[swz(l + off)] : 0.f;
+    slab_gather<K, P + 1>(sv, buf, sm_ls, tc, q, c, cc, active);
+  }
+}
+
+// add the slab's nodes of side step SIG (see scatter_side) to the accumulator
+template <int K, int SIG, int P = 0>
+__device__ __forceinline__ void slab_scatter(float* buf, const float* sv, const uint16_t* sm_ls, int tc, int q, int c,
+                                             int cc, uint32_t skip) {
+  constexpr int N = K + 1;
+  if constexpr (P < N * N) {
+    constexpr int a = P % N, b = P / N;
+    constexpr bool in = ((SIG & 1) ? a == K : a < K) && ((SIG & 2) ? b == K : b < K);
+    if constexpr (in) {
+      int slot, off;
+      slab_slot<K, a, b>(c, cc, slot, off);
+      const uint16_t l = sm_ls[slot * tc + q];
+      if (l != LS_NONE && !((skip >> slot) & 1u)) buf[swz(l + off)] += sv[P];
+    }
+    slab_scatter<K, SIG, P + 1>(buf, sv, sm_ls, tc, q, c, cc, skip);
+  }
+}
+
+template <int K, bool HANG_ONLY, int P = 0>
+__device__ __forceinline__ void slab_scatter_hanging(float* buf, const float* sv, const uint16_t* sm_ls, int tc,
+                                                     int q, int c, int cc, uint32_t hs) {
+  constexpr int N = K + 1;
+  if constexpr (P < N * N) {
+    int slot, off;
+    slab_slot<K, P % N, P / N>(c, cc, slot, off);
+    const uint16_t l = sm_ls[slot * tc + q];
+    if (l != LS_NONE && ((hs >> slot) & 1u)) buf[swz(l + off)] += sv[P];
+    slab_scatter_hanging<K, HANG_ONLY, P + 1>(buf, sv, sm_ls, tc, q, c, cc, hs);
+  }
+}
+
+// apply a 1D interpolation matrix (runtime child side p) to a register line
+template <int N, int BASE, int STRIDE, bool TRANS>
+__device__ __forceinline__ void interp_line(float* v, const float (&I)[NMAX][NMAX]) {
+  float t[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) t[a] = v[BASE + a * STRIDE];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < N; ++a) s += (TRANS ? I[a][i] : I[i][a]) * t[a];
+    v[BASE + i * STRIDE] = s;
+  }
+}
+
+// C_x and C_y (or their transposes, in reverse order) on the slab of thread c
+template <int K, bool TRANS>
+__device__ __forceinline__ void slab_hanging_xy(float* sv, uint16_t m, int c) {
+  constexpr int N = K + 1;
+  const DevTables<float>& tb = tab<float>(K);
+  const int px = m & 1, py = (m >> 1) & 1;
+  const float(&Ix)[NMAX][NMAX] = px ? tb.I[1] : tb.I[0];
+  const float(&Iy)[NMAX][NMAX] = py ? tb.I[1] : tb.I[0];
+  if (!TRANS) {
+#pragma unroll
+    for (int b = 0; b < N; ++b)  // x-lines (b, c)
+      if (line_hangs<K, 0>(m, b, c)) {
+        if (b == 0) interp_line<N, 0, 1, false>(sv, Ix);
+        else if (b == 1) interp_line<N, N, 1, false>(sv, Ix);
+        else if (b == 2) interp_line<N, (2 < N ? 2 : 0) * N, 1, false>(sv, Ix);
+        else if (b == 3) interp_line<N, (3 < N ? 3 : 0) * N, 1, false>(sv, Ix);
+        else interp_line<N, (4 < N ? 4 : 0) * N, 1, false>(sv, Ix);
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < N; ++a)  // y-lines (a, c)
+    if (line_hangs<K, 1>(m, a, c)) {
+      if (a == 0) interp_line<N, 0, N, TRANS>(sv, Iy);
+      else if (a == 1) interp_line<N, 1, N, TRANS>(sv, Iy);
+      else if (a == 2) interp_line<N, (2 < N ? 2 : 0), N, TRANS>(sv, Iy);
+      else if (a == 3) interp_line<N, (3 < N ? 3 : 0), N, TRANS>(sv, Iy);
+      else interp_line<N, (4 < N ? 4 : 0), N, TRANS>(sv, Iy);
+    }
+  if (TRANS) {
+#pragma unroll
+    for (int b = 0; b < N; ++b)
+      if (line_hangs<K, 0>(m, b, c)) {
+        if (b == 0) interp_line<N, 0, 1, true>(sv, Ix);
+        else if (b == 1) interp_line<N, N, 1, true>(sv, Ix);
+        else if (b == 2) interp_line<N, (2 < N ? 2 : 0) * N, 1, true>(sv, Ix);
+        else if (b == 3) interp_line<N, (3 < N ? 3 : 0) * N, 1, true>(sv, Ix);
+        else interp_line<N, (4 < N ? 4 : 0) * N, 1, true>(sv, Ix);
+      }
+  }
+}
+
+// C_z (or its transpose) on the z-lines held by thread t in the z layout
+template <int K, bool TRANS>
+__device__ __forceinline__ void slab_hanging_z(float* zv, uint16_t m, int t) {
+  constexpr int N = K + 1;
+  const DevTables<float>& tb = tab<float>(K);
+  const float(&Iz)[NMAX][NMAX] = ((m >> 2) & 1) ? tb.I[1] : tb.I[0];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int pr = t * N + i, a = pr % N, b = pr / N;
+    if (line_hangs<K, 2>(m, a, b)) {
+      if (i == 0) interp_line<N, 0, 1, TRANS>(zv, Iz);
+      else if (i == 1) interp_line<N, N, 1, TRANS>(zv, Iz);
+      else if (i == 2) interp_line<N, (2 < N ? 2 : 0) * N, 1, TRANS>(zv, Iz);
+      else if (i == 3) interp_line<N, (3 < N ? 3 : 0) * N, 1, TRANS>(zv, Iz);
+      else interp_line<N, (4 < N ? 4 : 0) * N, 1, TRANS>(zv, Iz);
+    }
+  }
+}
+
+// slab layout (thread c: nodes (a, b, c)) <-> z layout (thread t: z-lines of
+// the pairs a + N b = t N + i, stored as zv[i N + c]) through the cell region
+template <int K>
+__device__ __forceinline__ void to_z(const float* sv, float* zv, float* reg, int c) {
+  constexpr int N = K + 1, N2 = N * N;
+#pragma unroll
+  for (int p = 0; p < N2; ++p) reg[p + N2 * c] = sv[p];
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int z = 0; z < N; ++z) zv[i * N + z] = reg[c * N + i + N2 * z];
+  __syncwarp();
+}
+
+template <int K>
+__device__ __forceinline__ void to_slab(const float* zv, float* sv, float* reg, int c) {
+  constexpr int N = K + 1, N2 = N * N;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int z = 0; z < N; ++z) reg[c * N + i + N2 * z] = zv[i * N + z];
+  __syncwarp();
+#pragma unroll
+  for (int p = 0; p < N2; ++p) sv[p] = reg[p + N2 * c];
+  __syncwarp();
+}
+
+template <int N, int L = 0>
+__device__ __forceinline__ void slab_sweeps_xy(float* sv, const float (&Be)[NMAX][NMAX], bool fwd) {
+  if constexpr (L < N) {
+    if (fwd) {
+      eo_forward<N, L * N, 1>(sv, Be);  // x-line b = L
+    } else {
+      eo_backward<N, L, N>(sv, Be);  // y-line a = L
+    }
+    slab_sweeps_xy<N, L + 1>(sv, Be, fwd);
+  }
+}
+
+template <int N, int L = 0>
+__device__ __forceinline__ void slab_sweeps_yx(float* sv, const float (&Be)[NMAX][NMAX], bool fwd) {
+  if constexpr (L < N) {
+    if (fwd) {
+      eo_forward<N, L, N>(sv, Be);  // y-line a = L
+    } else {
+      eo_backward<N, L * N, 1>(sv, Be);  // x-line b = L
+    }
+    slab_sweeps_yx<N, L + 1>(sv, Be, fwd);
+  }
+}
+
+template <int N, int L = 0>
+__device__ __forceinline__ void z_lines(float* zv, const float (&Be)[NMAX][NMAX], const float* lam3, int t, float h) {
+  if constexpr (L < N) {
+    eo_forward<N, L * N, 1>(zv, Be);
+    const int pr = t * N + L;  // mode pair (a, b) of this line
+#pragma unroll
+    for (int z = 0; z < N; ++z) zv[L * N + z] *= h * lam3[pr + N * N * z];
+    eo_backward<N, L * N, 1>(zv, Be);
+    z_lines<N, L + 1>(zv, Be, lam3, t, h);
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(11 * 32, 2) vmult_slab(CellArgs<float> A) {
+  using G = SlabGeom<K>;
+  constexpr int N = G::N, N2 = G::N2, N3 = G::N3, CPW = G::CPW;
   extern __shared__ __align__(16) unsigned char smem[];
   const int tc = A.tc;
-  uint16_t* sm_ls = reinterpret_cast<uint16_t*>(smem);  // [slot][position]
+  uint16_t* sm_ls = reinterpret_cast<uint16_t*>(smem);  // [slot][cell]
   uint16_t* sm_mask = sm_ls + NSLOT * tc;
   uint16_t* sm_lev = sm_mask + tc;
   uint16_t* sm_sub = sm_lev + tc;
-  float* scratch = reinterpret_cast<float*>(smem + (((size_t)tc * (NSLOT + 3) * 2 + 15) & ~(size_t)15));
-  float* buf = scratch + 4 * N3;  // tile DoFs (swizzled): input, then the accumulator
+  float* lam3 = reinterpret_cast<float*>(smem + (((size_t)tc * (NSLOT + 3) * 2 + 15) & ~(size_t)15));
+  float* creg = lam3 + N3;           // per-cell transposition regions, (tc + 1) x N3
+  float* buf = creg + (tc + 1) * N3;  // tile DoFs (padded): input, then the accumulator
   __shared__ int any_hanging;
   const TileInfo ti = A.tiles[blockIdx.x];
   const int nc = ti.n_cells;
   const int nloc = ti.n_owned + ti.n_foreign;
+  const int nthr = blockDim.x;
   if (threadIdx.x == 0) any_hanging = 0;
-  // metadata, transposed to [slot][cell] so that lanes read consecutive words
-  for (int i = threadIdx.x; i < nc * 32; i += 128) {
+  for (int i = threadIdx.x; i < N3; i += nthr) lam3[i] = tab<float>(K).lam3[i];
+  for (int i = threadIdx.x; i < nc * 32; i += nthr) {
     const int cell = i >> 5, w = i & 31;
     const uint16_t v = reinterpret_cast<const uint16_t*>(A.meta + ti.cell_begin + cell)[w];
     if (w < NSLOT)
@@ -383,78 +605,84 @@ __global__ void __launch_bounds__(128, (K >= 4 ? 3 : 4)) vmult_regs(CellArgs<flo
   }
   {
     const float* src = A.src + ti.dof_begin;
-#pragma unroll 8
-    for (int i = threadIdx.x; i < ti.n_owned; i += 128) buf[swz(i)] = __ldg(src + i);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < ti.n_owned; i += nthr) buf[swz(i)] = __ldg(src + i);
     const int32_t* fl = A.foreign + ti.foreign_begin;
 #pragma unroll 4
-    for (int i = threadIdx.x; i < ti.n_foreign; i += 128) buf[swz(ti.n_owned + i)] = __ldg(A.src + __ldg(fl + i));
+    for (int i = threadIdx.x; i < ti.n_foreign; i += nthr) buf[swz(ti.n_owned + i)] = __ldg(A.src + __ldg(fl + i));
   }
   __syncthreads();
-  const int q = threadIdx.x;  // thread q handles cell q of the tile (Morton order)
-  const bool active = q < nc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = lane / N, c = lane - j * N;  // cell in warp, slab index
+  const int q = warp * CPW + j;
+  const bool active = (j < CPW) && (q < nc);
   const int qq = active ? q : 0;
-  float u[N3];
-  const uint16_t mask = active ? sm_mask[qq] : 0;
-  // G_e
-#pragma unroll
-  for (int n = 0; n < N3; ++n) {
-    int slot, off;
-    node_slot<K>(n % N, (n / N) % N, n / (N * N), slot, off);
-    const uint16_t l = sm_ls[slot * tc + qq];
-    u[n] = (active && l != LS_NONE) ? buf[swz(l + off)] : 0.f;
-  }
+  const int cc = c == 0 ? 0 : (c == K ? 2 : 1);
+  const uint16_t m = active ? sm_mask[qq] : 0;
+  float* reg = creg + (active ? q : tc) * N3;  // idle lanes use a spare region
+  float sv[N2], zv[N2];
+  slab_gather<K>(sv, buf, sm_ls, tc, qq, c, cc, active);  // G_e
   __syncthreads();  // the tile DoFs are no longer needed: reuse as accumulator
-  for (int i = threadIdx.x; i < nloc + (nloc >> 6) + 1; i += blockDim.x) buf[i] = 0.f;
-  if (mask & MASK_HANG) any_hanging = 1;
-  float* ws = scratch + (threadIdx.x >> 5) * N3;
-  hanging_warp<K, false>(u, mask, active, ws);  // C_e
+  for (int i = threadIdx.x; i < nloc + (nloc >> 6) + 1; i += nthr) buf[i] = 0.f;
+  if (m & MASK_HANG) any_hanging = 1;
+  const DevTables<float>& tb = tab<float>(K);
+  const bool hz = (m & MASK_HANG) != 0;  // C_e needs the z layout too
+  if (__any_sync(0xffffffffu, hz && active)) {
+    to_z<K>(sv, zv, reg, c);
+    if (hz) slab_hanging_z<K, false>(zv, m, c);
+    to_slab<K>(zv, sv, reg, c);
+    if (hz) slab_hanging_xy<K, false>(sv, m, c);
+  }
+  slab_sweeps_xy<N>(sv, tb.Be, true);   // B along x
+  slab_sweeps_yx<N>(sv, tb.Be, true);   // B along y
+  to_z<K>(sv, zv, reg, c);
   const float h = active ? ldexpf((float)A.dom, -(int)sm_lev[qq]) : 0.f;
-  cell_laplace_regs<K>(u, h);                   // S^T Q S
-  hanging_warp<K, true>(u, mask, active, ws);   // C_e^T
-  const uint32_t hs = hanging_slots(mask);
+  z_lines<N>(zv, tb.Be, lam3, c, h);    // B, h (lam_a + lam_b + lam_c), B^T along z
+  to_slab<K>(zv, sv, reg, c);
+  slab_sweeps_yx<N>(sv, tb.Be, false);  // B^T along y
+  slab_sweeps_xy<N>(sv, tb.Be, false);  // B^T along x
+  if (__any_sync(0xffffffffu, hz && active)) {
+    if (hz) slab_hanging_xy<K, true>(sv, m, c);
+    to_z<K>(sv, zv, reg, c);
+    if (hz) slab_hanging_z<K, true>(zv, m, c);
+    to_slab<K>(zv, sv, reg, c);
+  }
+  const uint32_t hs = hanging_slots(m);
   const uint32_t skip = active ? hs : 0x7FFFFFFu;
+  const bool zlo = c < K;
   __syncthreads();
-  // G_e^T: regular slots in eight side steps, all lanes at once
-  scatter_side<K, 0>(buf, u, sm_ls, tc, qq, skip);
+  // G_e^T in eight side steps (the z side is fixed by the slab index)
+  if (zlo) slab_scatter<K, 0>(buf, sv, sm_ls, tc, qq, c, cc, skip);
   __syncthreads();
-  scatter_side<K, 1>(buf, u, sm_ls, tc, qq, skip);
+  if (zlo) slab_scatter<K, 1>(buf, sv, sm_ls, tc, qq, c, cc, skip);
   __syncthreads();
-  scatter_side<K, 2>(buf, u, sm_ls, tc, qq, skip);
+  if (zlo) slab_scatter<K, 2>(buf, sv, sm_ls, tc, qq, c, cc, skip);
   __syncthreads();
-  scatter_side<K, 3>(buf, u, sm_ls, tc, qq, skip);
+  if (zlo) slab_scatter<K, 3>(buf, sv, sm_ls, tc, qq, c, cc, skip);
   __syncthreads();
-  scatter_side<K, 4>(buf, u, sm_ls, tc, qq, skip);
+  if (!zlo) slab_scatter<K, 0>(buf, sv, sm_ls, tc, qq, c, cc, skip);
   __syncthreads();
-  scatter_side<K, 5>(buf, u, sm_ls, tc, qq, skip);
+  if (!zlo) slab_scatter<K, 1>(buf, sv, sm_ls, tc, qq, c, cc, skip);
   __syncthreads();
-  scatter_side<K, 6>(buf, u, sm_ls, tc, qq, skip);
+  if (!zlo) slab_scatter<K, 2>(buf, sv, sm_ls, tc, qq, c, cc, skip);
   __syncthreads();
-  scatter_side<K, 7>(buf, u, sm_ls, tc, qq, skip);
+  if (!zlo) slab_scatter<K, 3>(buf, sv, sm_ls, tc, qq, c, cc, skip);
   __syncthreads();
-  // hanging slots (several fine cells reach one coarse entity): sub-colours
-  if (any_hanging) {
+  if (any_hanging) {  // hanging slots: several fine cells reach one coarse entity
     const int my_sub = (active && hs) ? sm_sub[qq] : -1;
     for (int sc = 0; sc < ti.n_sub; ++sc) {
-      if (my_sub == sc) {
-#pragma unroll
-        for (int n = 0; n < N3; ++n) {
-          int slot, off;
-          node_slot<K>(n % N, (n / N) % N, n / (N * N), slot, off);
-          const uint16_t l = sm_ls[slot * tc + qq];
-          if (l != LS_NONE && ((hs >> slot) & 1u)) buf[swz(l + off)] += u[n];
-        }
-      }
+      if (my_sub == sc) slab_scatter_hanging<K, true>(buf, sv, sm_ls, tc, qq, c, cc, hs);
       __syncthreads();
     }
   }
   {
     float* d = A.dst + ti.dof_begin;
     if (A.add)
-      for (int i = threadIdx.x; i < ti.n_owned; i += 128) d[i] += buf[swz(i)];
+      for (int i = threadIdx.x; i < ti.n_owned; i += nthr) d[i] += buf[swz(i)];
     else
-      for (int i = threadIdx.x; i < ti.n_owned; i += 128) d[i] = buf[swz(i)];
+      for (int i = threadIdx.x; i < ti.n_owned; i += nthr) d[i] = buf[swz(i)];
     float* hl = A.halo + ti.foreign_begin;
-    for (int i = threadIdx.x; i < ti.n_foreign; i += 128) hl[i] = buf[swz(ti.n_owned + i)];
+    for (int i = threadIdx.x; i < ti.n_foreign; i += nthr) hl[i] = buf[swz(ti.n_owned + i)];
   }
 }
 
@@ -530,10 +758,10 @@ void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
 
 template <int K>
 void run_regs(const CellLaunch& L, CellArgs<float> A, cudaStream_t s) {
-  const size_t sm = regs_smem<K>(L.tc, L.max_local);
-  ensure_smem(vmult_regs<K>, sm);
+  const size_t sm = slab_smem<K>(L.tc, L.max_local);
+  ensure_smem(vmult_slab<K>, sm);
   {
-    vmult_regs<K><<<L.n_tiles, 128, sm, s>>>(A);
+    vmult_slab<K><<<L.n_tiles, slab_warps<K>(L.tc) * 32, sm, s>>>(A);
     note_launches(1);
   }
   run_halo<float>(L, A.dst, s);
@@ -587,7 +815,7 @@ void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, in
     A.src = static_cast<const float*>(src);
     A.dst = static_cast<float*>(dst);
     A.add = add;
-    if (L.tc > 128 || L.use_lines) {
+    if (L.tc > 64 || L.use_lines) {
       dispatch<float, MODE_VMULT>(L, A, s);
       return;
     }
