@@ -432,9 +432,10 @@ __device__ __forceinline__ void slab_scatter_hanging(float* buf, const float* sv
   }
 }
 
-// apply a 1D interpolation matrix (runtime child side p) to a register line
-template <int N, int BASE, int STRIDE, bool TRANS>
-__device__ __forceinline__ void interp_line(float* v, const float (&I)[NMAX][NMAX]) {
+// apply the child-side interpolation matrix I[P] to a register line
+template <int N, int BASE, int STRIDE, bool TRANS, int P>
+__device__ __forceinline__ void interp_line_p(float* v) {
+  const DevTables<float>& tb = tab<float>(N - 1);
   float t[N];
 #pragma unroll
   for (int a = 0; a < N; ++a) t[a] = v[BASE + a * STRIDE];
@@ -442,48 +443,55 @@ __device__ __forceinline__ void interp_line(float* v, const float (&I)[NMAX][NMA
   for (int i = 0; i < N; ++i) {
     float s = 0.f;
 #pragma unroll
-    for (int a = 0; a < N; ++a) s += (TRANS ? I[a][i] : I[i][a]) * t[a];
+    for (int a = 0; a < N; ++a) s += (TRANS ? tb.I[P][a][i] : tb.I[P][i][a]) * t[a];
     v[BASE + i * STRIDE] = s;
   }
+}
+
+// the child side p is a runtime value: branch so that the table index stays
+// a compile-time constant (constant-bank operands, no generic loads)
+template <int N, int BASE, int STRIDE, bool TRANS>
+__device__ __forceinline__ void interp_line(float* v, int p) {
+  if (p)
+    interp_line_p<N, BASE, STRIDE, TRANS, 1>(v);
+  else
+    interp_line_p<N, BASE, STRIDE, TRANS, 0>(v);
 }
 
 // C_x and C_y (or their transposes, in reverse order) on the slab of thread c
 template <int K, bool TRANS>
 __device__ __forceinline__ void slab_hanging_xy(float* sv, uint16_t m, int c) {
   constexpr int N = K + 1;
-  const DevTables<float>& tb = tab<float>(K);
   const int px = m & 1, py = (m >> 1) & 1;
-  const float(&Ix)[NMAX][NMAX] = px ? tb.I[1] : tb.I[0];
-  const float(&Iy)[NMAX][NMAX] = py ? tb.I[1] : tb.I[0];
   if (!TRANS) {
 #pragma unroll
     for (int b = 0; b < N; ++b)  // x-lines (b, c)
       if (line_hangs<K, 0>(m, b, c)) {
-        if (b == 0) interp_line<N, 0, 1, false>(sv, Ix);
-        else if (b == 1) interp_line<N, N, 1, false>(sv, Ix);
-        else if (b == 2) interp_line<N, (2 < N ? 2 : 0) * N, 1, false>(sv, Ix);
-        else if (b == 3) interp_line<N, (3 < N ? 3 : 0) * N, 1, false>(sv, Ix);
-        else interp_line<N, (4 < N ? 4 : 0) * N, 1, false>(sv, Ix);
+        if (b == 0) interp_line<N, 0, 1, false>(sv, px);
+        else if (b == 1) interp_line<N, N, 1, false>(sv, px);
+        else if (b == 2) interp_line<N, (2 < N ? 2 : 0) * N, 1, false>(sv, px);
+        else if (b == 3) interp_line<N, (3 < N ? 3 : 0) * N, 1, false>(sv, px);
+        else interp_line<N, (4 < N ? 4 : 0) * N, 1, false>(sv, px);
       }
   }
 #pragma unroll
   for (int a = 0; a < N; ++a)  // y-lines (a, c)
     if (line_hangs<K, 1>(m, a, c)) {
-      if (a == 0) interp_line<N, 0, N, TRANS>(sv, Iy);
-      else if (a == 1) interp_line<N, 1, N, TRANS>(sv, Iy);
-      else if (a == 2) interp_line<N, (2 < N ? 2 : 0), N, TRANS>(sv, Iy);
-      else if (a == 3) interp_line<N, (3 < N ? 3 : 0), N, TRANS>(sv, Iy);
-      else interp_line<N, (4 < N ? 4 : 0), N, TRANS>(sv, Iy);
+      if (a == 0) interp_line<N, 0, N, TRANS>(sv, py);
+      else if (a == 1) interp_line<N, 1, N, TRANS>(sv, py);
+      else if (a == 2) interp_line<N, (2 < N ? 2 : 0), N, TRANS>(sv, py);
+      else if (a == 3) interp_line<N, (3 < N ? 3 : 0), N, TRANS>(sv, py);
+      else interp_line<N, (4 < N ? 4 : 0), N, TRANS>(sv, py);
     }
   if (TRANS) {
 #pragma unroll
     for (int b = 0; b < N; ++b)
       if (line_hangs<K, 0>(m, b, c)) {
-        if (b == 0) interp_line<N, 0, 1, true>(sv, Ix);
-        else if (b == 1) interp_line<N, N, 1, true>(sv, Ix);
-        else if (b == 2) interp_line<N, (2 < N ? 2 : 0) * N, 1, true>(sv, Ix);
-        else if (b == 3) interp_line<N, (3 < N ? 3 : 0) * N, 1, true>(sv, Ix);
-        else interp_line<N, (4 < N ? 4 : 0) * N, 1, true>(sv, Ix);
+        if (b == 0) interp_line<N, 0, 1, true>(sv, px);
+        else if (b == 1) interp_line<N, N, 1, true>(sv, px);
+        else if (b == 2) interp_line<N, (2 < N ? 2 : 0) * N, 1, true>(sv, px);
+        else if (b == 3) interp_line<N, (3 < N ? 3 : 0) * N, 1, true>(sv, px);
+        else interp_line<N, (4 < N ? 4 : 0) * N, 1, true>(sv, px);
       }
   }
 }
@@ -492,17 +500,16 @@ __device__ __forceinline__ void slab_hanging_xy(float* sv, uint16_t m, int c) {
 template <int K, bool TRANS>
 __device__ __forceinline__ void slab_hanging_z(float* zv, uint16_t m, int t) {
   constexpr int N = K + 1;
-  const DevTables<float>& tb = tab<float>(K);
-  const float(&Iz)[NMAX][NMAX] = ((m >> 2) & 1) ? tb.I[1] : tb.I[0];
+  const int pz = (m >> 2) & 1;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     const int pr = t * N + i, a = pr % N, b = pr / N;
     if (line_hangs<K, 2>(m, a, b)) {
-      if (i == 0) interp_line<N, 0, 1, TRANS>(zv, Iz);
-      else if (i == 1) interp_line<N, N, 1, TRANS>(zv, Iz);
-      else if (i == 2) interp_line<N, (2 < N ? 2 : 0) * N, 1, TRANS>(zv, Iz);
-      else if (i == 3) interp_line<N, (3 < N ? 3 : 0) * N, 1, TRANS>(zv, Iz);
-      else interp_line<N, (4 < N ? 4 : 0) * N, 1, TRANS>(zv, Iz);
+      if (i == 0) interp_line<N, 0, 1, TRANS>(zv, pz);
+      else if (i == 1) interp_line<N, N, 1, TRANS>(zv, pz);
+      else if (i == 2) interp_line<N, (2 < N ? 2 : 0) * N, 1, TRANS>(zv, pz);
+      else if (i == 3) interp_line<N, (3 < N ? 3 : 0) * N, 1, TRANS>(zv, pz);
+      else interp_line<N, (4 < N ? 4 : 0) * N, 1, TRANS>(zv, pz);
     }
   }
 }

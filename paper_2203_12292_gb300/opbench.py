@@ -21,7 +21,8 @@ if ROOT not in sys.path:
 import synth  # noqa: E402
 
 WORKLOADS = {"q4octant": synth.WORKLOAD_Q4_OCTANT, "q2octant": synth.WORKLOAD_Q2_OCTANT,
-             "q4sphere": synth.WORKLOAD_Q4_SPHERE}
+             "q4sphere": synth.WORKLOAD_Q4_SPHERE,
+             "q4uniform": synth.Workload("Q4 uniform cube, 6 refinements (262,144 cells)", synth.uniform_cube(6), 4, 0)}
 
 
 def main(argv=None):
