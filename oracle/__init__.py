@@ -21,7 +21,9 @@ What it computes, each part a plain definition written out in fp64:
                 fine one and restriction as its transpose (Sec. 3.5, Eq. 5).
 * ``mg``        Chebyshev/point-Jacobi smoother (Sec. 3.3), exact coarse
                 solve (Sec. 3.4), V-cycle (Algorithms 1-2), PCG (Sec. 2).
-* ``mlp``       per-cell MLP smoother forward/backward in fp64 loops.
+* ``mlp``       learned per-cell smoother, an extension outside the paper:
+                network forward/backward, loss, Adam, cell features, owner-
+                selected correction, optional bf16 operand rounding.
 
 Parity status: every function is pinned by a test in ``tests/test_oracle_*``
 against values the paper prints or closed forms; see the module headers.

@@ -121,6 +121,8 @@ class Level:
     chol: object = None
     dtype: type = np.float64
     A32: object = None
+    learned: Optional[Callable] = None  # residual -> correction (learned smoother)
+    learned_mode: str = "augment"       # "augment": after postsmoothing; "replace": instead of it
 
     def apply64(self, x):
         """The fp64 operator."""
@@ -190,7 +192,12 @@ def vcycle(levels: List[Level], l: int, b: np.ndarray) -> np.ndarray:
     bc = P.T @ r                                                   # restriction
     xc = vcycle(levels, l - 1, bc)                                 # recursion
     x = x + P @ xc                                                 # prolongation
-    return chebyshev(lev.apply, dinv, b, x, lev.lam_max)          # postsmoothing
+    if lev.learned is not None and lev.learned_mode == "replace":
+        return x + lev.learned(b - lev.apply(x)).astype(dt)        # learned step only
+    x = chebyshev(lev.apply, dinv, b, x, lev.lam_max)             # postsmoothing
+    if lev.learned is not None:
+        x = x + lev.learned(b - lev.apply(x)).astype(dt)           # learned step after it
+    return x
 
 
 def set_precision(levels: List[Level], dtype) -> None:
@@ -216,8 +223,12 @@ class SolveResult:
     residuals: List[float] = field(default_factory=list)
 
 
-def pcg(apply: Callable, b: np.ndarray, precond: Callable, rtol: float, maxit: int = 200) -> SolveResult:
-    """Preconditioned CG from x = 0, stopped when ||b - A x||_2 <= rtol ||b||_2."""
+def pcg(apply: Callable, b: np.ndarray, precond: Callable, rtol: float, maxit: int = 200,
+        flexible: bool = False) -> SolveResult:
+    """Preconditioned CG from x = 0, stopped when ||b - A x||_2 <= rtol ||b||_2.
+    flexible: beta = r_{k+1}.(z_{k+1} - z_k) / r_k.z_k (Notay, SIAM J. Sci.
+    Comput. 22 (2000), flexible CG with one stored direction), the variant
+    for a preconditioner that is not a fixed linear map."""
     x = np.zeros_like(b)
     r = b.copy()
     nb = np.linalg.norm(b)
@@ -236,14 +247,16 @@ def pcg(apply: Callable, b: np.ndarray, precond: Callable, rtol: float, maxit: i
         res.append(nr)
         if nr <= rtol * nb:
             return SolveResult(x, it, res)
+        cross = r @ z if flexible else 0.0
         z = precond(r)
         rz_new = r @ z
-        p = z + (rz_new / rz) * p
+        p = z + ((rz_new - cross) / rz) * p
         rz = rz_new
     return SolveResult(x, maxit, res)
 
 
-def solve(levels: List[Level], b: np.ndarray, rtol: float, mg_dtype=np.float64, maxit: int = 200) -> SolveResult:
+def solve(levels: List[Level], b: np.ndarray, rtol: float, mg_dtype=np.float64, maxit: int = 200,
+          flexible: bool = False) -> SolveResult:
     """CG in fp64 preconditioned by one V-cycle in ``mg_dtype``."""
     set_precision(levels, mg_dtype)
-    return pcg(levels[-1].apply64, b, lambda r: multigrid_vcycle(levels, r, mg_dtype), rtol, maxit)
+    return pcg(levels[-1].apply64, b, lambda r: multigrid_vcycle(levels, r, mg_dtype), rtol, maxit, flexible)

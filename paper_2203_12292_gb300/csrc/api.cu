@@ -484,7 +484,7 @@ void vcycle(Handle& H, const double* b, double* x) {
   else
     ck(cudaMemcpyAsync(F.b.p, b, F.n() * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
   prof_end(H, r);
-  vcycle_level(H, top);
+  vcycle_core(H);
   r = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);
   if (F.fp32)
     launch_cast(true, F.x.p, x, F.n(), H.stream);

@@ -225,3 +225,40 @@ def point_values(xyz: np.ndarray, seed: int, resolution_bits: int = 20) -> np.nd
             h = (h ^ (h >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
             h = (h ^ (h >> np.uint64(31))) & mask
     return -1.0 + 2.0 * (h >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
+# --------------------------------------------------------------------------
+# learned smoother: network size, initial parameters, sample orders
+# --------------------------------------------------------------------------
+
+MLP_HIDDEN = 128
+
+
+def mlp_shape(k: int):
+    """(n_in, n_hidden, n_out) of the per-cell network for degree k: the
+    residual and the diagonal at the (k+1)^3 support points in, the
+    correction at them out."""
+    n3 = (k + 1) ** 3
+    return 2 * n3, MLP_HIDDEN, n3
+
+
+def mlp_init(n_in: int, n_h: int, n_out: int, seed: int) -> np.ndarray:
+    """Initial packed parameters (W1, b1, W2, b2, W3, b3; matrices row-major,
+    one row per output unit), each entry uniform in +-1/sqrt(fan_in), rounded
+    to float32."""
+    parts = []
+    for i, (rows, fan_in) in enumerate([(n_h, n_in), (n_h, n_h), (n_out, n_h)]):
+        bound = 1.0 / np.sqrt(fan_in)
+        parts.append(uniform_vector(rows * fan_in, seed * 8 + 2 * i + 1, -bound, bound))
+        parts.append(uniform_vector(rows, seed * 8 + 2 * i + 2, -bound, bound))
+    return np.concatenate(parts).astype(np.float32).astype(np.float64)
+
+
+def sample_order(n_samples: int, epochs: int, seed: int) -> np.ndarray:
+    """Concatenated random permutations of range(n_samples), one per epoch:
+    the order that sorts SplitMix64 keys (stable for equal keys)."""
+    out = np.empty(n_samples * epochs, dtype=np.int32)
+    for e in range(epochs):
+        keys = splitmix64_array(seed * 1000003 + e, n_samples)
+        out[e * n_samples:(e + 1) * n_samples] = np.argsort(keys, kind="stable")
+    return out
