@@ -215,6 +215,7 @@ int gcmg_vmult_host(gcmg_handle* h, int level, int fp64, const void* src, void* 
 #define GCMG_STAGE_POSTSMOOTH 6
 #define GCMG_STAGE_CG_VMULT 7    /* fp64 operator of CG on the finest level */
 #define GCMG_STAGE_CG_VECTOR 8   /* CG inner products, updates, precision casts */
+#define GCMG_STAGE_LEARNED 9     /* learned smoother: its residual and correction */
 /* switch the timers on/off; both reset the accumulated times */
 int gcmg_set_profiling(gcmg_handle* h, int on);
 /* accumulated launches and milliseconds of one (level, stage); synchronises */
@@ -240,6 +241,92 @@ int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int m
  * re-captured after gcmg_set_lambda and gcmg_set_profiling.
  */
 int gcmg_set_graphs(gcmg_handle* h, int on);
+
+/* ------------------------------------------------------------------------
+ * Learned per-cell smoother.  An extension outside the paper, whose smoother
+ * is Chebyshev around point Jacobi (Sec. 3.3); Chebyshev stays the default.
+ *
+ * Network: y = W3 g(W2 g(W1 x + b1) + b2) + b3, g the exact GELU
+ * z (1 + erf(z / sqrt 2)) / 2.  Parameters are packed fp32 in the order W1
+ * (n_hidden x n_in, row-major, one row per output unit), b1, W2 (n_hidden x
+ * n_hidden), b2, W3 (n_out x n_hidden), b3.  Every matrix product takes
+ * bf16 operands (round to nearest even) and accumulates in fp32.
+ *
+ * Cell features of cell e (Q_k, n3 = (k+1)^3 support points, lexicographic
+ * with x fastest): r_e, d_e = values of the residual and of diag(A) at the
+ * cell's support points, hanging points interpolated (C_e G_e of Eq. 2),
+ * s_e = |r_e|_2, h_e the cell size, a_k the mean diagonal entry of the
+ * unit-cell Laplace matrix; x_e = [r_e / s_e, d_e / (h_e a_k)] (2 n3 values,
+ * the first n3 zero where s_e = 0).  Correction c_e = y(x_e) s_e / (h_e a_k);
+ * every free DoF takes c_e of its owner cell: the first cell in Morton order
+ * in which it is a support point off the faces and edges that border a
+ * coarser cell.  The inference kernel is specialised for Q4 with
+ * (n_in, n_hidden, n_out) = (250, 128, 125).
+ * ------------------------------------------------------------------------ */
+typedef struct gcmg_mlp gcmg_mlp;
+
+/* network with zero parameters; sizes 1..4096 */
+int gcmg_mlp_create(int n_in, int n_hidden, int n_out, gcmg_mlp** out);
+void gcmg_mlp_destroy(gcmg_mlp* net);
+int gcmg_mlp_num_params(const gcmg_mlp* net, int64_t* n);
+/* copy packed parameters from / to device memory; set resets Adam's state */
+int gcmg_mlp_set_params(gcmg_mlp* net, const float* params, void* stream);
+int gcmg_mlp_get_params(const gcmg_mlp* net, float* params, void* stream);
+/* Y (n x n_out, fp32 device) = network(X) (n x n_in, fp32 device) */
+int gcmg_mlp_forward(gcmg_mlp* net, const float* X, int64_t n, float* Y, void* stream);
+/*
+ * Loss L = |Y - T|^2 / (2n) over n <= 2^20 rows and dL/dparams (packed like
+ * the parameters) by back-propagation; grad: device array of num_params
+ * floats; loss: device pointer to one float or NULL.
+ */
+int gcmg_mlp_gradient(gcmg_mlp* net, const float* X, const float* T, int64_t n, float* grad, float* loss,
+                      void* stream);
+/*
+ * Adam (Kingma & Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected)
+ * on consecutive batches of `batch` rows: step s uses the rows
+ * order[s * batch .. (s+1) * batch) of X (n_samples x n_in) and T
+ * (n_samples x n_out); n_order / batch steps.  losses (device, one float per
+ * step, may be NULL) receives each step's loss before its update.  All
+ * arrays are device memory; asynchronous on `stream`.
+ */
+int gcmg_mlp_train(gcmg_mlp* net, const float* X, const float* T, int64_t n_samples, const int32_t* order,
+                   int64_t n_order, int batch, float lr, float* losses, void* stream);
+
+/* (l, i, j, k) of every cell of a level in the library's cell order: host
+ * array of 4 * n_cells int32 */
+int gcmg_level_cells(const gcmg_handle* h, int level, int32_t* lijk);
+/*
+ * out[c * n3 + j] = value of the fp64 device vector x (n_free(level)) at
+ * support point j of cell cells[c] (hanging points interpolated, Dirichlet
+ * points 0).  cells: device int32 array of n_cells indices, or NULL for all
+ * cells in order; out: fp64 device array.
+ */
+int gcmg_cell_gather(gcmg_handle* h, int level, const double* x, int64_t n_cells, const int32_t* cells,
+                     double* out);
+/*
+ * Training rows of the cells `cells` (device int32, n_cells) from an iterate
+ * x, the right-hand side b and a reference solution xstar (fp64 device
+ * vectors of the level): with r = b - A x and e = xstar - x, X (n_cells x
+ * 2 n3) = the cell features x_e of r, T (n_cells x n3) = e_e h_e a_k / s_e
+ * (zero where s_e = 0).  xstar and T may both be NULL.  Uses the level's
+ * fp64 work vectors; synchronises the stream.
+ */
+int gcmg_mlp_samples(gcmg_handle* h, int level, const double* b, const double* x, const double* xstar,
+                     int64_t n_cells, const int32_t* cells, float* X, float* T);
+/* x += the owner-selected corrections of `net` for the residual r (Q4 only) */
+int gcmg_mlp_correct(gcmg_handle* h, int level, const gcmg_mlp* net, int fp64, const void* r, void* x);
+
+#define GCMG_SMOOTHER_CHEBYSHEV 0   /* Chebyshev around point Jacobi (default) */
+#define GCMG_SMOOTHER_MLP_AUGMENT 1 /* postsmoothing, then one learned correction */
+#define GCMG_SMOOTHER_MLP_REPLACE 2 /* the learned correction instead of postsmoothing */
+/*
+ * Smoother of one level of the V-cycle (level >= 1, Q4 for the learned
+ * kinds).  The handle keeps a copy of the network's current parameters, so
+ * later training does not change it.  With a learned kind on any level the
+ * preconditioner is no longer a fixed linear map and gcmg_cg_solve switches
+ * to flexible CG (beta = r_{k+1}.(z_{k+1} - z_k) / r_k.z_k, Notay 2000).
+ */
+int gcmg_set_smoother(gcmg_handle* h, int level, int kind, const gcmg_mlp* net);
 
 const char* gcmg_last_error(void);
 /* number of CUDA kernel launches issued by this library since it was loaded */

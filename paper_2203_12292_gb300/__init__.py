@@ -21,7 +21,9 @@ _c_int, _c_double, _c_void_p, _c_int64 = ctypes.c_int, ctypes.c_double, ctypes.c
 PRED_ALL, PRED_OCTANT_CENTRE, PRED_SPHERE, PRED_SHELL, PRED_OCTANT_STRICT = 0, 1, 2, 3, 4
 
 STAGES = ["vmult", "presmooth", "residual", "restrict", "coarse", "prolongate", "postsmooth", "cg_vmult",
-          "cg_vector"]
+          "cg_vector", "learned"]
+
+SMOOTHER_CHEBYSHEV, SMOOTHER_MLP_AUGMENT, SMOOTHER_MLP_REPLACE = 0, 1, 2
 
 ERRORS = {1: "GCMG_ERR_ARG", 2: "GCMG_ERR_CUDA", 3: "GCMG_ERR_OOM", 4: "GCMG_ERR_NOT_CONVERGED",
           5: "GCMG_ERR_BREAKDOWN", 6: "GCMG_ERR_INTERNAL"}
@@ -85,6 +87,21 @@ _SIGS = {
     "gcmg_coarse_solve": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p]),
     "gcmg_vcycle": (_c_int, [_c_void_p, _c_void_p, _c_void_p]),
     "gcmg_cg_solve": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_double, _c_int, ctypes.POINTER(SolveStats)]),
+    "gcmg_mlp_create": (_c_int, [_c_int, _c_int, _c_int, ctypes.POINTER(_c_void_p)]),
+    "gcmg_mlp_destroy": (None, [_c_void_p]),
+    "gcmg_mlp_num_params": (_c_int, [_c_void_p, ctypes.POINTER(_c_int64)]),
+    "gcmg_mlp_set_params": (_c_int, [_c_void_p, _c_void_p, _c_void_p]),
+    "gcmg_mlp_get_params": (_c_int, [_c_void_p, _c_void_p, _c_void_p]),
+    "gcmg_mlp_forward": (_c_int, [_c_void_p, _c_void_p, _c_int64, _c_void_p, _c_void_p]),
+    "gcmg_mlp_gradient": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int64, _c_void_p, _c_void_p, _c_void_p]),
+    "gcmg_mlp_train": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int64, _c_void_p, _c_int64, _c_int,
+                                ctypes.c_float, _c_void_p, _c_void_p]),
+    "gcmg_level_cells": (_c_int, [_c_void_p, _c_int, _c_void_p]),
+    "gcmg_cell_gather": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_int64, _c_void_p, _c_void_p]),
+    "gcmg_mlp_samples": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p, _c_void_p, _c_int64, _c_void_p,
+                                  _c_void_p, _c_void_p]),
+    "gcmg_mlp_correct": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_int, _c_void_p, _c_void_p]),
+    "gcmg_set_smoother": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p]),
 }
 
 _lib = None
@@ -336,3 +353,113 @@ class Multigrid:
         if rc != 0 and (raise_on_fail or rc not in (4, 5)):
             _check(rc)
         return st
+
+    # ---- learned smoother --------------------------------------------------
+    def n_cells(self, level: int) -> int:
+        return self.info[level].n_cells
+
+    def level_cells(self, level: int) -> np.ndarray:
+        """(l, i, j, k) of every cell in the library's cell order."""
+        out = np.empty((self.n_cells(level), 4), dtype=np.int32)
+        _check(lib().gcmg_level_cells(self._h, level, out.ctypes.data_as(_c_void_p)))
+        return out
+
+    def cell_gather(self, level: int, x, cells=None):
+        """Values of the fp64 vector x at the support points of the cells
+        (all cells when ``cells`` is None): (n_cells, (k+1)^3) fp64 tensor."""
+        import torch
+        n3 = (self.info[level].degree + 1) ** 3
+        nc = self.n_cells(level) if cells is None else cells.numel()
+        out = torch.empty((nc, n3), dtype=torch.float64, device="cuda")
+        cp = None if cells is None else _ptr(cells, nc, torch.int32)
+        _check(lib().gcmg_cell_gather(self._h, level, _ptr(x, self.n_free(level), torch.float64), nc, cp,
+                                      _ptr(out)))
+        return out
+
+    def mlp_samples(self, level: int, b, x, xstar, cells):
+        """Training rows (X, T) of the cells from the residual b - A x and the
+        error xstar - x (fp64 vectors; xstar None gives T = None)."""
+        import torch
+        n3 = (self.info[level].degree + 1) ** 3
+        nc = cells.numel()
+        X = torch.empty((nc, 2 * n3), dtype=torch.float32, device="cuda")
+        T = torch.empty((nc, n3), dtype=torch.float32, device="cuda") if xstar is not None else None
+        n = self.n_free(level)
+        _check(lib().gcmg_mlp_samples(self._h, level, _ptr(b, n, torch.float64), _ptr(x, n, torch.float64),
+                                      None if xstar is None else _ptr(xstar, n, torch.float64), nc,
+                                      _ptr(cells, nc, torch.int32), _ptr(X), None if T is None else _ptr(T)))
+        return X, T
+
+    def mlp_correct(self, level: int, net: "MLP", r, x) -> None:
+        """x += the learned correction of ``net`` for the residual r."""
+        n = self.n_free(level)
+        _check(lib().gcmg_mlp_correct(self._h, level, net._p, _is64(x), _ptr(r, n, x.dtype), _ptr(x, n, x.dtype)))
+
+    def set_smoother(self, level: int, kind: int, net: "Optional[MLP]" = None) -> None:
+        _check(lib().gcmg_set_smoother(self._h, level, kind, None if net is None else net._p))
+
+
+class MLP:
+    """Per-cell network of the learned smoother (device parameters, Adam state)."""
+
+    def __init__(self, n_in: int, n_hidden: int, n_out: int):
+        p = _c_void_p()
+        _check(lib().gcmg_mlp_create(n_in, n_hidden, n_out, ctypes.byref(p)))
+        self._p = p
+        self.shape = (n_in, n_hidden, n_out)
+
+    def __del__(self):
+        if getattr(self, "_p", None) and _lib is not None:
+            _lib.gcmg_mlp_destroy(self._p)
+            self._p = None
+
+    @property
+    def num_params(self) -> int:
+        n = _c_int64()
+        _check(lib().gcmg_mlp_num_params(self._p, ctypes.byref(n)))
+        return n.value
+
+    def _stream(self):
+        import torch
+        return _c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def set_params(self, theta) -> None:
+        import torch
+        _check(lib().gcmg_mlp_set_params(self._p, _ptr(theta, self.num_params, torch.float32), self._stream()))
+
+    def get_params(self):
+        import torch
+        out = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        _check(lib().gcmg_mlp_get_params(self._p, _ptr(out), self._stream()))
+        return out
+
+    def forward(self, X):
+        import torch
+        n = X.shape[0]
+        Y = torch.empty((n, self.shape[2]), dtype=torch.float32, device="cuda")
+        _check(lib().gcmg_mlp_forward(self._p, _ptr(X, n * self.shape[0], torch.float32), n, _ptr(Y),
+                                      self._stream()))
+        return Y
+
+    def gradient(self, X, T):
+        """(loss tensor (1,), gradient tensor (num_params,))."""
+        import torch
+        n = X.shape[0]
+        g = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        L = torch.empty(1, dtype=torch.float32, device="cuda")
+        _check(lib().gcmg_mlp_gradient(self._p, _ptr(X, n * self.shape[0], torch.float32),
+                                       _ptr(T, n * self.shape[2], torch.float32), n, _ptr(g), _ptr(L),
+                                       self._stream()))
+        return L, g
+
+    def train(self, X, T, order, batch: int, lr: float = 1e-3):
+        """Adam over consecutive batches of ``order``; returns the per-step losses."""
+        import torch
+        n = X.shape[0]
+        steps = order.numel() // batch
+        losses = torch.empty(max(steps, 1), dtype=torch.float32, device="cuda")
+        _check(lib().gcmg_mlp_train(self._p, _ptr(X, n * self.shape[0], torch.float32),
+                                    _ptr(T, n * self.shape[2], torch.float32), n,
+                                    _ptr(order, order.numel(), torch.int32), order.numel(), batch, float(lr),
+                                    _ptr(losses), self._stream()))
+        return losses[:steps]

@@ -11,59 +11,21 @@
 #include <vector>
 
 #include "gcmg.h"
+#include "host.h"
 #include "internal.h"
 #include "kernels.h"
+#include "mlp_net.h"
 
 namespace gcmg {
 
 void upload_tables_cell();
 void upload_tables_transfer();
+void upload_tables_mlp();
 
 static std::atomic<long long> g_launches{0};
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
-
-thread_local std::string g_err;
-
-struct Error : std::runtime_error {
-  int code;
-  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
-};
-
-void ck(cudaError_t e, const char* what) {
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    throw Error(e == cudaErrorMemoryAllocation ? GCMG_ERR_OOM : GCMG_ERR_CUDA,
-                std::string(what) + ": " + cudaGetErrorString(e));
-  }
-}
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-  DevBuf() = default;
-  DevBuf(const DevBuf&) = delete;
-  DevBuf& operator=(const DevBuf&) = delete;
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
-  void alloc(size_t n) {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = n;
-    if (n) ck(cudaMalloc(&p, n), "cudaMalloc");
-  }
-  template <typename T>
-  void upload(const std::vector<T>& v, cudaStream_t s) {
-    alloc(v.size() * sizeof(T));
-    if (!v.empty()) ck(cudaMemcpyAsync(p, v.data(), bytes, cudaMemcpyHostToDevice, s), "upload");
-  }
-  template <typename T>
-  T* as() const {
-    return static_cast<T*>(p);
-  }
-};
 
 struct LevelDev {
   LevelHost host;
@@ -76,6 +38,9 @@ struct LevelDev {
   DevBuf w32a, w32b;        // fp32 work vectors (fp32 smoothing through the API)
   CellLaunch cl{};
   double lam = 1.0;
+  // learned smoother: kind, parameter copy, bf16 diagonal features per cell
+  int smoother = GCMG_SMOOTHER_CHEBYSHEV;
+  DevBuf mlp_params, dfeat;
   int64_t n() const { return host.n_free; }
 };
 
@@ -108,7 +73,7 @@ struct Profiler {
     }
   }
 };
-constexpr int NSTAGE = 9;
+constexpr int NSTAGE = 10;
 
 // CUDA graphs of the V-cycle and of the operator half of a CG iteration;
 // captured once per handle (re-captured when smoother parameters or the
@@ -399,6 +364,64 @@ void smooth(Handle& H, int l, bool fp64, void* x, const void* b, void* d, void* 
   }
 }
 
+// a_k: mean diagonal entry of the unit-cell Laplace matrix, from the 1D
+// matrices: diag(K x M x M + M x K x M + M x M x K) averages to 3 tr K (tr M)^2 / n^3
+double mean_ref_diag(int k) {
+  const Basis1D& b = basis(k);
+  double tk = 0, tm = 0;
+  for (int i = 0; i <= k; ++i) {
+    tk += b.K[i][i];
+    tm += b.M[i][i];
+  }
+  const double n = k + 1;
+  return 3.0 * tk * tm * tm / (n * n * n);
+}
+
+// bf16 diagonal features of every cell of level l (once per level)
+void ensure_dfeat(Handle& H, int l) {
+  LevelDev& L = *H.lev[l];
+  if (L.dfeat.p) return;
+  const int k = L.host.k, n3 = (k + 1) * (k + 1) * (k + 1);
+  const int64_t nc = (int64_t)L.host.cells.size();
+  DevBuf tmp;
+  tmp.alloc((size_t)nc * n3 * sizeof(double));
+  launch_cell_gather(k, L.diag64.as<double>(), nullptr, nc, L.gstart.as<int32_t>(), L.meta.as<CellMeta>(),
+                     tmp.as<double>(), H.stream);
+  L.dfeat.alloc((size_t)nc * MLP_DF * sizeof(uint16_t));
+  launch_mlp_dfeat(tmp.as<double>(), nc, n3, L.meta.as<CellMeta>(), L.cl.dom, mean_ref_diag(k), L.dfeat.p, H.stream);
+  ck(cudaStreamSynchronize(H.stream), "diagonal features");
+}
+
+void mlp_correct(Handle& H, int l, const float* params, bool fp64, const void* r, void* x) {
+  LevelDev& L = *H.lev[l];
+  MlpFused P{params,
+             L.dfeat.as<uint16_t>(),
+             L.gstart.as<int32_t>(),
+             L.own.as<uint32_t>(),
+             L.meta.as<CellMeta>(),
+             (int64_t)L.host.cells.size(),
+             L.cl.dom,
+             mean_ref_diag(L.host.k)};
+  ck(launch_mlp_correct(P, fp64, r, x, H.stream), "learned correction");
+}
+
+// residual of level l into t, then x += learned correction
+void learned_step(Handle& H, int l) {
+  LevelDev& L = *H.lev[l];
+  const bool f64 = !L.fp32;
+  const int r = prof_begin(H, l, GCMG_STAGE_LEARNED);
+  vmult(H, l, f64, L.x.p, L.t.p);
+  launch_residual(f64, L.t.p, L.b.p, L.t.p, L.n(), H.stream);
+  mlp_correct(H, l, L.mlp_params.as<float>(), f64, L.t.p, L.x.p);
+  prof_end(H, r);
+}
+
+bool any_learned(const Handle& H) {
+  for (const auto& L : H.lev)
+    if (L->smoother != GCMG_SMOOTHER_CHEBYSHEV) return true;
+  return false;
+}
+
 void vcycle_level(Handle& H, int l) {
   LevelDev& L = *H.lev[l];
   const bool f64 = !L.fp32;
@@ -425,9 +448,14 @@ void vcycle_level(Handle& H, int l) {
   r = prof_begin(H, l, GCMG_STAGE_PROLONGATE);
   if (C.n()) launch_prolongate_add(H.tr[l]->tl, f64, C.x.p, L.x.p, H.stream);  // prolongation
   prof_end(H, r);
+  if (L.smoother == GCMG_SMOOTHER_MLP_REPLACE) {
+    learned_step(H, l);  // learned correction instead of postsmoothing
+    return;
+  }
   r = prof_begin(H, l, GCMG_STAGE_POSTSMOOTH);
   smooth(H, l, f64, L.x.p, L.b.p, L.d.p, L.t.p, dinv, false);  // postsmoothing
   prof_end(H, r);
+  if (L.smoother == GCMG_SMOOTHER_MLP_AUGMENT) learned_step(H, l);
 }
 
 
@@ -493,22 +521,6 @@ void vcycle(Handle& H, const double* b, double* x) {
   prof_end(H, r);
 }
 
-template <typename F>
-int guarded(F&& f) {
-  try {
-    f();
-    return GCMG_OK;
-  } catch (const Error& e) {
-    g_err = e.what();
-    return e.code;
-  } catch (const std::bad_alloc&) {
-    g_err = "host allocation failed";
-    return GCMG_ERR_OOM;
-  } catch (const std::exception& e) {
-    g_err = e.what();
-    return GCMG_ERR_INTERNAL;
-  }
-}
 
 }  // namespace
 }  // namespace gcmg
@@ -624,6 +636,7 @@ int gcmg_setup(const gcmg_mesh* mesh, const gcmg_config* cfg, void* stream, gcmg
     H.cfg = *cfg;
     upload_tables_cell();
     upload_tables_transfer();
+    upload_tables_mlp();
     ck(cudaGetLastError(), "upload tables");
     // level list: (mesh index, degree), coarsest first
     std::vector<std::pair<int, int>> spec;
@@ -1018,6 +1031,7 @@ int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int m
       launch_cg_update_xr(xi, r, p, q, S, n, H.scratch.as<double>(), S, H.stream);
       prof_end(H, pr);
     };
+    const bool flexible = any_learned(H);
     vcycle(H, r, z);
     launch_dot(r, z, n, H.scratch.as<double>(), S, 0, DOT_STORE, s);  // rz
     ck(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
@@ -1044,9 +1058,14 @@ int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int m
       }
       rr = hs[2];
       if (std::sqrt(rr) <= rtol * nb) break;
+      if (flexible) {  // r_{k+1} . z_k before z is overwritten
+        const int pc = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);
+        launch_dot(r, z, n, H.scratch.as<double>(), S, 6, DOT_STORE, s);
+        prof_end(H, pc);
+      }
       vcycle(H, r, z);
       const int pz = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);
-      launch_dot(r, z, n, H.scratch.as<double>(), S, 0, DOT_BETA, s);
+      launch_dot(r, z, n, H.scratch.as<double>(), S, 0, flexible ? DOT_BETA_FLEX : DOT_BETA, s);
       launch_cg_update_p(p, z, S, n, s);
       prof_end(H, pz);
     }
@@ -1065,6 +1084,111 @@ int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int m
   if (rc != GCMG_OK) return rc;
   if (status != GCMG_OK) g_err = status == GCMG_ERR_BREAKDOWN ? "CG breakdown" : "CG did not converge";
   return status;
+}
+
+int gcmg_level_cells(const gcmg_handle* h, int level, int32_t* lijk) {
+  return guarded([&] {
+    if (!h || !lijk) throw Error(GCMG_ERR_ARG, "null argument");
+    check_level(h->h, level);
+    const auto& cells = h->h.lev[level]->host.cells;
+    for (size_t c = 0; c < cells.size(); ++c) {
+      lijk[4 * c] = cells[c].l;
+      lijk[4 * c + 1] = cells[c].i;
+      lijk[4 * c + 2] = cells[c].j;
+      lijk[4 * c + 3] = cells[c].k;
+    }
+  });
+}
+
+int gcmg_cell_gather(gcmg_handle* h, int level, const double* x, int64_t n_cells, const int32_t* cells,
+                     double* out) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    check_level(h->h, level);
+    LevelDev& L = *h->h.lev[level];
+    if (n_cells < 0 || (!cells && n_cells > (int64_t)L.host.cells.size())) throw Error(GCMG_ERR_ARG, "bad cell count");
+    if (n_cells == 0) return;
+    if (!x || !out) throw Error(GCMG_ERR_ARG, "bad vectors");
+    launch_cell_gather(L.host.k, x, cells, n_cells, L.gstart.as<int32_t>(), L.meta.as<CellMeta>(), out,
+                       h->h.stream);
+    ck(cudaGetLastError(), "cell gather");
+  });
+}
+
+int gcmg_mlp_samples(gcmg_handle* h, int level, const double* b, const double* x, const double* xstar,
+                     int64_t n_cells, const int32_t* cells, float* X, float* T) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    check_level(h->h, level);
+    Handle& H = h->h;
+    LevelDev& L = *H.lev[level];
+    if (n_cells < 0 || (!cells && n_cells > (int64_t)L.host.cells.size())) throw Error(GCMG_ERR_ARG, "bad cell count");
+    if (n_cells == 0 || L.n() == 0) return;
+    if (!b || !x || !X || (T && !xstar)) throw Error(GCMG_ERR_ARG, "bad vectors");
+    const int k = L.host.k, n3 = (k + 1) * (k + 1) * (k + 1);
+    const int64_t n = L.n();
+    double* r = L.w64a.as<double>();
+    double* e = L.w64b.as<double>();
+    vmult(H, level, true, x, r);  // r = b - A x
+    launch_residual(true, r, b, r, n, H.stream);
+    if (T) {  // e = xstar - x
+      ck(cudaMemcpyAsync(e, xstar, n * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
+      launch_axpy(true, e, x, -1.0, n, H.stream);
+    }
+    DevBuf R, E, D;
+    R.alloc((size_t)n_cells * n3 * sizeof(double));
+    D.alloc((size_t)n_cells * n3 * sizeof(double));
+    if (T) E.alloc((size_t)n_cells * n3 * sizeof(double));
+    const int32_t* gs = L.gstart.as<int32_t>();
+    const CellMeta* meta = L.meta.as<CellMeta>();
+    launch_cell_gather(k, r, cells, n_cells, gs, meta, R.as<double>(), H.stream);
+    launch_cell_gather(k, L.diag64.as<double>(), cells, n_cells, gs, meta, D.as<double>(), H.stream);
+    if (T) launch_cell_gather(k, e, cells, n_cells, gs, meta, E.as<double>(), H.stream);
+    launch_mlp_samples(R.as<double>(), T ? E.as<double>() : nullptr, D.as<double>(), cells, n_cells, n3, meta,
+                       L.cl.dom, mean_ref_diag(k), X, T, H.stream);
+    ck(cudaStreamSynchronize(H.stream), "samples");  // the temporaries are freed on return
+  });
+}
+
+static void check_q4_net(const LevelDev& L, const gcmg_mlp* net) {
+  if (!net) throw Error(GCMG_ERR_ARG, "null network");
+  if (L.host.k != 4) throw Error(GCMG_ERR_ARG, "the learned smoother runs on Q4 levels only");
+  const MlpNet& N = net->net;
+  if (N.n_in != 250 || N.n_h != 128 || N.n_out != 125)
+    throw Error(GCMG_ERR_ARG, "the Q4 learned smoother needs a 250-128-128-125 network");
+}
+
+int gcmg_mlp_correct(gcmg_handle* h, int level, const gcmg_mlp* net, int fp64, const void* r, void* x) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    check_level(h->h, level);
+    LevelDev& L = *h->h.lev[level];
+    check_q4_net(L, net);
+    if (L.n() == 0) return;
+    if (!r || !x) throw Error(GCMG_ERR_ARG, "bad vectors");
+    ensure_dfeat(h->h, level);
+    mlp_correct(h->h, level, net->net.params.as<float>(), fp64 != 0, r, x);
+  });
+}
+
+int gcmg_set_smoother(gcmg_handle* h, int level, int kind, const gcmg_mlp* net) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    check_level(h->h, level);
+    if (level < 1) throw Error(GCMG_ERR_ARG, "level 0 is solved exactly");
+    if (kind < GCMG_SMOOTHER_CHEBYSHEV || kind > GCMG_SMOOTHER_MLP_REPLACE) throw Error(GCMG_ERR_ARG, "unknown smoother");
+    Handle& H = h->h;
+    LevelDev& L = *H.lev[level];
+    if (kind != GCMG_SMOOTHER_CHEBYSHEV) {
+      check_q4_net(L, net);
+      ensure_dfeat(H, level);
+      const size_t b = net->net.n_params * sizeof(float);
+      if (L.mlp_params.bytes != b) L.mlp_params.alloc(b);
+      ck(cudaMemcpyAsync(L.mlp_params.p, net->net.params.p, b, cudaMemcpyDeviceToDevice, H.stream), "copy");
+    }
+    L.smoother = kind;
+    H.g_core.reset();
+  });
 }
 
 int gcmg_set_graphs(gcmg_handle* h, int on) {

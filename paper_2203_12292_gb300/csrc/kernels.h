@@ -87,16 +87,71 @@ void launch_coarse_solve(bool fp64, const double* Ainv, int n, const void* b, vo
 // deterministic fp64 dot products: partial sums into `scratch` (DOT_BLOCKS
 // doubles), then one block combines them in fixed order
 constexpr int DOT_BLOCKS = 304;
-enum DotOp { DOT_STORE = 0, DOT_ALPHA = 1, DOT_BETA = 2 };
+enum DotOp { DOT_STORE = 0, DOT_ALPHA = 1, DOT_BETA = 2, DOT_BETA_FLEX = 3 };
 void launch_dot(const double* x, const double* y, int64_t n, double* scratch, double* scal, int slot, int op,
                 cudaStream_t s);
 // inner product with the partial sums in a fixed device array (no allocation);
 // n <= dot_noalloc_max_n()
 int64_t dot_noalloc_max_n();
 cudaError_t launch_dot_noalloc(const double* x, const double* y, int64_t n, double* result, cudaStream_t s);
-// CG updates with device scalars: scal[0] = rz, [1] = pq, [2] = rr, [3] = alpha, [4] = beta, [5] = rz_new
+// CG updates with device scalars: scal[0] = rz, [1] = pq, [2] = rr, [3] = alpha, [4] = beta, [5] = rz_new,
+// [6] = r_{k+1}.z_k of flexible CG
 void launch_cg_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, int64_t n,
                          double* scratch, double* scal_out, cudaStream_t s);
 void launch_cg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// learned per-cell smoother
+// ---------------------------------------------------------------------------
+constexpr int MLP_DF = 128;  // bf16 diagonal features stored per cell (Q4: 125 + 3 zeros)
+constexpr float MLP_BETA1 = 0.9f, MLP_BETA2 = 0.999f, MLP_EPS = 1e-8f;
+
+// out[c][j] = (C_e G_e v)_j for the cells `cells` (null: 0..n-1), fp64
+void launch_cell_gather(int k, const double* v, const int32_t* cells, int64_t n, const int32_t* gstart,
+                        const CellMeta* meta, double* out, cudaStream_t s);
+// training rows from gathered cell values R (residual), E (error, may be
+// null), D (diagonal): X = [R / |R|, D / (h a)], T = E h a / |R|
+void launch_mlp_samples(const double* R, const double* E, const double* D, const int32_t* cells, int64_t n, int n3,
+                        const CellMeta* meta, double dom, double abar, float* X, float* T, cudaStream_t s);
+// bf16 rows of MLP_DF diagonal features per cell (all cells of a level)
+void launch_mlp_dfeat(const double* D, int64_t n, int n3, const CellMeta* meta, double dom, double abar, void* out,
+                      cudaStream_t s);
+
+// C[m][n] = sum_k A(m, k) B(k, n) (+ bias[n]) with bf16 operands and fp32
+// accumulation; A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn]
+struct GemmArgs {
+  const float* A;
+  int64_t sam, sak;
+  const float* B;
+  int64_t sbk, sbn;
+  float* C;
+  int64_t ldc;
+  const float* bias;
+  int M, N, K;
+};
+void launch_gemm_bf16(const GemmArgs& g, cudaStream_t s);
+void launch_gelu(const float* Z, float* H, int64_t n, cudaStream_t s);
+void launch_gelu_bwd(const float* dH, const float* Z, float* dZ, int64_t n, cudaStream_t s);
+// dY = (Y - T) / B, *loss = |Y - T|^2 / (2B)
+void launch_mse(const float* Y, const float* T, float* dY, int64_t n, int B, float* loss, cudaStream_t s);
+void launch_colsum(const float* X, int M, int N, float* out, cudaStream_t s);
+void launch_gather_rows(const float* X, int64_t ld, const int32_t* idx, int B, float* out, cudaStream_t s);
+// Adam with bias corrections bc1 = 1 - beta1^t, bc2 = 1 - beta2^t
+void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float bc1, float bc2,
+                 cudaStream_t s);
+
+// fused per-cell correction x += owner-selected MLP(r) for Q4 (250-128-128-125)
+struct MlpFused {
+  const float* params;     // packed fp32 parameters
+  const uint16_t* dfeat;   // bf16 diagonal features, MLP_DF per cell
+  const int32_t* gstart;   // cells x 27
+  const uint32_t* own;     // per cell: owned slots
+  const CellMeta* meta;
+  int64_t n_cells;
+  double dom;              // edge length of the domain
+  double abar;             // mean diagonal entry of the unit-cell matrix
+};
+size_t mlp_fused_smem_bytes();
+cudaError_t launch_mlp_correct(const MlpFused& P, bool fp64, const void* r, void* x, cudaStream_t s);
 
 }  // namespace gcmg

@@ -118,9 +118,13 @@ __global__ void __launch_bounds__(BLOCK) dot_final(const double* part, int np, d
     } else if (op == DOT_ALPHA) {  // pq, alpha = rz / pq
       scal[1] = s;
       scal[3] = scal[0] / s;
-    } else {  // rz_new, beta = rz_new / rz, rz <- rz_new
+    } else if (op == DOT_BETA) {  // rz_new, beta = rz_new / rz, rz <- rz_new
       scal[5] = s;
       scal[4] = s / scal[0];
+      scal[0] = s;
+    } else {  // flexible CG: beta = (rz_new - r_{k+1}.z_k) / rz, rz <- rz_new
+      scal[5] = s;
+      scal[4] = (s - scal[6]) / scal[0];
       scal[0] = s;
     }
   }
