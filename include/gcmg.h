@@ -162,6 +162,14 @@ int gcmg_coarse_solve(gcmg_handle* h, int fp64, const void* b, void* x);
  * finest level; the levels run in the configured precision.
  */
 int gcmg_vcycle(gcmg_handle* h, const double* b, double* x);
+/*
+ * The same V-cycle stopped on the finest level right after the prolongation
+ * (Algorithm 2 without the finest postsmoothing): the coarse-grid corrected
+ * iterate, the state the postsmoother (or a learned step) acts on.
+ */
+int gcmg_vcycle_cgc(gcmg_handle* h, const double* b, double* x);
+/* r = b - A x on a level (vectors of the level, precision by fp64; r != x) */
+int gcmg_residual(gcmg_handle* h, int level, int fp64, const void* b, const void* x, void* r);
 
 /*
  * *result = x . y in fp64 (CG inner products, Sec. 2): x, y device arrays of
@@ -275,22 +283,26 @@ int gcmg_mlp_get_params(const gcmg_mlp* net, float* params, void* stream);
 /* Y (n x n_out, fp32 device) = network(X) (n x n_in, fp32 device) */
 int gcmg_mlp_forward(gcmg_mlp* net, const float* X, int64_t n, float* Y, void* stream);
 /*
- * Loss L = |Y - T|^2 / (2n) over n <= 2^20 rows and dL/dparams (packed like
- * the parameters) by back-propagation; grad: device array of num_params
- * floats; loss: device pointer to one float or NULL.
+ * Loss L = sum_i w_i |Y_i - T_i|^2 / (2 sum_i w_i) over n <= 2^20 rows
+ * (W: device array of n row weights, or NULL for all 1: the mean squared
+ * error) and dL/dparams (packed like the parameters) by back-propagation;
+ * grad: device array of num_params floats; loss: device pointer to one float
+ * or NULL.
  */
-int gcmg_mlp_gradient(gcmg_mlp* net, const float* X, const float* T, int64_t n, float* grad, float* loss,
-                      void* stream);
+int gcmg_mlp_gradient(gcmg_mlp* net, const float* X, const float* T, const float* W, int64_t n, float* grad,
+                      float* loss, void* stream);
 /*
  * Adam (Kingma & Ba 2015; beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected)
- * on consecutive batches of `batch` rows: step s uses the rows
- * order[s * batch .. (s+1) * batch) of X (n_samples x n_in) and T
- * (n_samples x n_out); n_order / batch steps.  losses (device, one float per
- * step, may be NULL) receives each step's loss before its update.  All
- * arrays are device memory; asynchronous on `stream`.
+ * on the loss of gcmg_mlp_gradient over consecutive batches of `batch`
+ * rows: step s uses the rows order[s * batch .. (s+1) * batch) of X
+ * (n_samples x n_in), T (n_samples x n_out) and W (n_samples, or NULL);
+ * n_order / batch steps; every order entry must lie in [0, n_samples).
+ * losses (device, one float per step, may be NULL) receives each step's
+ * loss before its update.  All arrays are device memory; asynchronous on
+ * `stream`.
  */
-int gcmg_mlp_train(gcmg_mlp* net, const float* X, const float* T, int64_t n_samples, const int32_t* order,
-                   int64_t n_order, int batch, float lr, float* losses, void* stream);
+int gcmg_mlp_train(gcmg_mlp* net, const float* X, const float* T, const float* W, int64_t n_samples,
+                   const int32_t* order, int64_t n_order, int batch, float lr, float* losses, void* stream);
 
 /* (l, i, j, k) of every cell of a level in the library's cell order: host
  * array of 4 * n_cells int32 */
@@ -308,11 +320,13 @@ int gcmg_cell_gather(gcmg_handle* h, int level, const double* x, int64_t n_cells
  * x, the right-hand side b and a reference solution xstar (fp64 device
  * vectors of the level): with r = b - A x and e = xstar - x, X (n_cells x
  * 2 n3) = the cell features x_e of r, T (n_cells x n3) = e_e h_e a_k / s_e
- * (zero where s_e = 0).  xstar and T may both be NULL.  Uses the level's
- * fp64 work vectors; synchronises the stream.
+ * (zero where s_e = 0), W (n_cells) = (s_e / (h_e a_k))^2, the weight that
+ * turns the error of y into the error of the correction.  xstar and T may
+ * both be NULL; W may be NULL.  Cell indices must lie in [0, n_cells of the
+ * level).  Uses the level's fp64 work vectors; synchronises the stream.
  */
 int gcmg_mlp_samples(gcmg_handle* h, int level, const double* b, const double* x, const double* xstar,
-                     int64_t n_cells, const int32_t* cells, float* X, float* T);
+                     int64_t n_cells, const int32_t* cells, float* X, float* T, float* W);
 /* x += the owner-selected corrections of `net` for the residual r (Q4 only) */
 int gcmg_mlp_correct(gcmg_handle* h, int level, const gcmg_mlp* net, int fp64, const void* r, void* x);
 

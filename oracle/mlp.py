@@ -11,7 +11,8 @@ network   y = W3 g(W2 g(W1 x + b1) + b2) + b3 with g the exact GELU,
           g(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2.  W1 is n_h x n_in,
           W2 n_h x n_h, W3 n_out x n_h (one row per output unit).  Packed
           parameter vector: W1, b1, W2, b2, W3, b3, matrices row-major.
-loss      L = 1/(2B) sum_b ||y_b - t_b||^2 over a batch of B samples.
+loss      L = sum_b w_b ||y_b - t_b||^2 / (2 sum_b w_b) over a batch of B
+          samples with weights w_b (all 1: the plain mean squared error).
 Adam      Kingma & Ba (2015), Algorithm 1: beta1 0.9, beta2 0.999, eps 1e-8,
           bias-corrected moments.
 features  for cell e with the cell values r_e = (C r)|_e of the residual and
@@ -19,7 +20,9 @@ features  for cell e with the cell values r_e = (C r)|_e of the residual and
           (lexicographic, x fastest): s_e = ||r_e||_2 and
           x_e = [r_e / s_e, d_e / (h_e a_k)], a_k the mean diagonal entry of
           the Laplace matrix of the unit cell (x_e = [0, ...] when s_e = 0).
-target    t_e = e_e h_e a_k / s_e for the cell values e_e of the error.
+target    t_e = e_e h_e a_k / s_e for the cell values e_e of the error, and
+          weight w_e = (s_e / (h_e a_k))^2, so that w_e ||y - t_e||^2 =
+          ||c_e - e_e||^2 is the squared error of the correction itself.
 correction c_e = y(x_e) s_e / (h_e a_k): a positively 1-homogeneous map of
           the residual.  Free value i receives c_{o(i)} at its node in its
           owner cell o(i) (the weighting W_e of the transfer, realised as a
@@ -118,18 +121,19 @@ def forward(shape: Shape, theta: np.ndarray, X: np.ndarray, bf16: bool = False):
     return Y, dict(X=X, Z1=Z1, H1=H1, Z2=Z2, H2=H2)
 
 
-def loss(Y: np.ndarray, T: np.ndarray) -> float:
-    return float(0.5 * np.sum((Y - T) ** 2) / Y.shape[0])
+def loss(Y: np.ndarray, T: np.ndarray, W=None) -> float:
+    w = np.ones(Y.shape[0]) if W is None else np.asarray(W, dtype=np.float64)
+    return float(0.5 * np.sum(w[:, None] * (Y - T) ** 2) / np.sum(w))
 
 
-def loss_and_grad(shape: Shape, theta: np.ndarray, X: np.ndarray, T: np.ndarray, bf16: bool = False):
+def loss_and_grad(shape: Shape, theta: np.ndarray, X: np.ndarray, T: np.ndarray, bf16: bool = False, W=None):
     """L and dL/dtheta (packed like theta), by the chain rule backwards
     through the three layers."""
     q = round_bf16 if bf16 else (lambda a: np.asarray(a, dtype=np.float64))
     p = unpack(shape, theta)
     Y, c = forward(shape, theta, X, bf16)
-    B = Y.shape[0]
-    dY = (Y - T) / B
+    w = np.ones(Y.shape[0]) if W is None else np.asarray(W, dtype=np.float64)
+    dY = w[:, None] * (Y - T) / np.sum(w)
     g = {}
     g["W3"] = q(dY).T @ q(c["H2"])
     g["b3"] = dY.sum(axis=0)
@@ -139,7 +143,7 @@ def loss_and_grad(shape: Shape, theta: np.ndarray, X: np.ndarray, T: np.ndarray,
     dZ1 = (q(dZ2) @ q(p["W2"])) * gelu_grad(c["Z1"])
     g["W1"] = q(dZ1).T @ q(c["X"])
     g["b1"] = dZ1.sum(axis=0)
-    return loss(Y, T), pack(shape, g)
+    return loss(Y, T, w), pack(shape, g)
 
 
 def adam_step(theta, grad, m, v, t: int, lr: float):
@@ -152,7 +156,7 @@ def adam_step(theta, grad, m, v, t: int, lr: float):
 
 
 def train(shape: Shape, theta: np.ndarray, X: np.ndarray, T: np.ndarray, order: np.ndarray, batch: int,
-          lr: float, bf16: bool = False):
+          lr: float, bf16: bool = False, W=None):
     """Adam on consecutive batches of the sample order; returns the final
     parameters and the loss of every step (before its update)."""
     theta = np.asarray(theta, dtype=np.float64).copy()
@@ -161,7 +165,7 @@ def train(shape: Shape, theta: np.ndarray, X: np.ndarray, T: np.ndarray, order: 
     losses = []
     for s in range(len(order) // batch):
         idx = order[s * batch:(s + 1) * batch]
-        L, g = loss_and_grad(shape, theta, X[idx], T[idx], bf16)
+        L, g = loss_and_grad(shape, theta, X[idx], T[idx], bf16, None if W is None else np.asarray(W)[idx])
         losses.append(L)
         theta, m, v = adam_step(theta, g, m, v, s + 1, lr)
     return theta, np.array(losses)
@@ -192,6 +196,13 @@ def cell_features(space, r: np.ndarray, diag: np.ndarray):
     xr = np.where(s[:, None] > 0, re / safe[:, None], 0.0)
     X = np.concatenate([xr, de / (space.h[:, None] * a)], axis=1)
     return X, s
+
+
+def cell_weights(space, r: np.ndarray) -> np.ndarray:
+    """w_e = (s_e / (h_e a_k))^2."""
+    a = mean_reference_diagonal(space.k)
+    s = np.linalg.norm(cell_values(space, r), axis=1)
+    return (s / (space.h * a)) ** 2
 
 
 def cell_targets(space, r: np.ndarray, e: np.ndarray) -> np.ndarray:

@@ -86,6 +86,8 @@ _SIGS = {
     "gcmg_restrict_add": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
     "gcmg_coarse_solve": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p]),
     "gcmg_vcycle": (_c_int, [_c_void_p, _c_void_p, _c_void_p]),
+    "gcmg_vcycle_cgc": (_c_int, [_c_void_p, _c_void_p, _c_void_p]),
+    "gcmg_residual": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p, _c_void_p]),
     "gcmg_cg_solve": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_double, _c_int, ctypes.POINTER(SolveStats)]),
     "gcmg_mlp_create": (_c_int, [_c_int, _c_int, _c_int, ctypes.POINTER(_c_void_p)]),
     "gcmg_mlp_destroy": (None, [_c_void_p]),
@@ -93,13 +95,14 @@ _SIGS = {
     "gcmg_mlp_set_params": (_c_int, [_c_void_p, _c_void_p, _c_void_p]),
     "gcmg_mlp_get_params": (_c_int, [_c_void_p, _c_void_p, _c_void_p]),
     "gcmg_mlp_forward": (_c_int, [_c_void_p, _c_void_p, _c_int64, _c_void_p, _c_void_p]),
-    "gcmg_mlp_gradient": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int64, _c_void_p, _c_void_p, _c_void_p]),
-    "gcmg_mlp_train": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int64, _c_void_p, _c_int64, _c_int,
+    "gcmg_mlp_gradient": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_int64, _c_void_p, _c_void_p,
+                                   _c_void_p]),
+    "gcmg_mlp_train": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_int64, _c_void_p, _c_int64, _c_int,
                                 ctypes.c_float, _c_void_p, _c_void_p]),
     "gcmg_level_cells": (_c_int, [_c_void_p, _c_int, _c_void_p]),
     "gcmg_cell_gather": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_int64, _c_void_p, _c_void_p]),
     "gcmg_mlp_samples": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p, _c_void_p, _c_int64, _c_void_p,
-                                  _c_void_p, _c_void_p]),
+                                  _c_void_p, _c_void_p, _c_void_p]),
     "gcmg_mlp_correct": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_int, _c_void_p, _c_void_p]),
     "gcmg_set_smoother": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p]),
 }
@@ -344,6 +347,18 @@ class Multigrid:
         n = self.n_free(self.finest)
         _check(lib().gcmg_vcycle(self._h, _ptr(b, n, torch.float64), _ptr(x, n, torch.float64)))
 
+    def vcycle_cgc(self, b, x) -> None:
+        """V-cycle stopped after the finest-level prolongation (coarse-grid corrected iterate)."""
+        import torch
+        n = self.n_free(self.finest)
+        _check(lib().gcmg_vcycle_cgc(self._h, _ptr(b, n, torch.float64), _ptr(x, n, torch.float64)))
+
+    def residual(self, level: int, b, x, r) -> None:
+        """r = b - A x on a level."""
+        n = self.n_free(level)
+        _check(lib().gcmg_residual(self._h, level, _is64(x), _ptr(b, n, x.dtype), _ptr(x, n, x.dtype),
+                                   _ptr(r, n, x.dtype)))
+
     def cg_solve(self, b, x, rtol: float = 1e-8, maxit: int = 100, raise_on_fail: bool = True) -> SolveStats:
         import torch
         n = self.n_free(self.finest)
@@ -358,6 +373,10 @@ class Multigrid:
     def n_cells(self, level: int) -> int:
         return self.info[level].n_cells
 
+    def _check_cells(self, level: int, cells) -> None:
+        if cells.numel() and (int(cells.min()) < 0 or int(cells.max()) >= self.n_cells(level)):
+            raise ValueError("cell index out of range")
+
     def level_cells(self, level: int) -> np.ndarray:
         """(l, i, j, k) of every cell in the library's cell order."""
         out = np.empty((self.n_cells(level), 4), dtype=np.int32)
@@ -370,6 +389,8 @@ class Multigrid:
         import torch
         n3 = (self.info[level].degree + 1) ** 3
         nc = self.n_cells(level) if cells is None else cells.numel()
+        if cells is not None:
+            self._check_cells(level, cells)
         out = torch.empty((nc, n3), dtype=torch.float64, device="cuda")
         cp = None if cells is None else _ptr(cells, nc, torch.int32)
         _check(lib().gcmg_cell_gather(self._h, level, _ptr(x, self.n_free(level), torch.float64), nc, cp,
@@ -377,18 +398,21 @@ class Multigrid:
         return out
 
     def mlp_samples(self, level: int, b, x, xstar, cells):
-        """Training rows (X, T) of the cells from the residual b - A x and the
-        error xstar - x (fp64 vectors; xstar None gives T = None)."""
+        """Training rows (X, T, W) of the cells from the residual b - A x and
+        the error xstar - x (fp64 vectors; xstar None gives T = None)."""
         import torch
+        self._check_cells(level, cells)
         n3 = (self.info[level].degree + 1) ** 3
         nc = cells.numel()
         X = torch.empty((nc, 2 * n3), dtype=torch.float32, device="cuda")
         T = torch.empty((nc, n3), dtype=torch.float32, device="cuda") if xstar is not None else None
+        W = torch.empty(nc, dtype=torch.float32, device="cuda")
         n = self.n_free(level)
         _check(lib().gcmg_mlp_samples(self._h, level, _ptr(b, n, torch.float64), _ptr(x, n, torch.float64),
                                       None if xstar is None else _ptr(xstar, n, torch.float64), nc,
-                                      _ptr(cells, nc, torch.int32), _ptr(X), None if T is None else _ptr(T)))
-        return X, T
+                                      _ptr(cells, nc, torch.int32), _ptr(X), None if T is None else _ptr(T),
+                                      _ptr(W)))
+        return X, T, W
 
     def mlp_correct(self, level: int, net: "MLP", r, x) -> None:
         """x += the learned correction of ``net`` for the residual r."""
@@ -441,25 +465,29 @@ class MLP:
                                       self._stream()))
         return Y
 
-    def gradient(self, X, T):
-        """(loss tensor (1,), gradient tensor (num_params,))."""
+    def gradient(self, X, T, W=None):
+        """(loss tensor (1,), gradient tensor (num_params,)); W: row weights or None."""
         import torch
         n = X.shape[0]
         g = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
         L = torch.empty(1, dtype=torch.float32, device="cuda")
         _check(lib().gcmg_mlp_gradient(self._p, _ptr(X, n * self.shape[0], torch.float32),
-                                       _ptr(T, n * self.shape[2], torch.float32), n, _ptr(g), _ptr(L),
+                                       _ptr(T, n * self.shape[2], torch.float32),
+                                       None if W is None else _ptr(W, n, torch.float32), n, _ptr(g), _ptr(L),
                                        self._stream()))
         return L, g
 
-    def train(self, X, T, order, batch: int, lr: float = 1e-3):
+    def train(self, X, T, order, batch: int, lr: float = 1e-3, W=None):
         """Adam over consecutive batches of ``order``; returns the per-step losses."""
         import torch
         n = X.shape[0]
+        if order.numel() and (int(order.min()) < 0 or int(order.max()) >= n):
+            raise ValueError("sample order out of range")
         steps = order.numel() // batch
         losses = torch.empty(max(steps, 1), dtype=torch.float32, device="cuda")
         _check(lib().gcmg_mlp_train(self._p, _ptr(X, n * self.shape[0], torch.float32),
-                                    _ptr(T, n * self.shape[2], torch.float32), n,
+                                    _ptr(T, n * self.shape[2], torch.float32),
+                                    None if W is None else _ptr(W, n, torch.float32), n,
                                     _ptr(order, order.numel(), torch.int32), order.numel(), batch, float(lr),
                                     _ptr(losses), self._stream()))
         return losses[:steps]

@@ -40,7 +40,7 @@ struct LevelDev {
   double lam = 1.0;
   // learned smoother: kind, parameter copy, bf16 diagonal features per cell
   int smoother = GCMG_SMOOTHER_CHEBYSHEV;
-  DevBuf mlp_params, dfeat;
+  DevBuf mlp_image, dfeat;  // packed bf16 weights of the fused kernel
   int64_t n() const { return host.n_free; }
 };
 
@@ -97,6 +97,7 @@ struct GraphRec {
 
 struct Handle {
   cudaStream_t stream = nullptr;
+  bool stop_after_cgc = false;  // finest level: return after the prolongation
   cudaStream_t cap_stream = nullptr;
   bool use_graphs = true;
   GraphRec* capturing = nullptr;
@@ -110,6 +111,7 @@ struct Handle {
   int n0 = 0;
   DevBuf scratch, scal, modes;
   DevBuf cg_r, cg_p, cg_q, cg_z, cg_x;
+  DevBuf mlp_scratch;  // weight image of gcmg_mlp_correct calls
   ~Handle() {
     g_core.reset();
     g_a.reset();
@@ -392,9 +394,9 @@ void ensure_dfeat(Handle& H, int l) {
   ck(cudaStreamSynchronize(H.stream), "diagonal features");
 }
 
-void mlp_correct(Handle& H, int l, const float* params, bool fp64, const void* r, void* x) {
+void mlp_correct(Handle& H, int l, const void* image, bool fp64, const void* r, void* x) {
   LevelDev& L = *H.lev[l];
-  MlpFused P{params,
+  MlpFused P{image,
              L.dfeat.as<uint16_t>(),
              L.gstart.as<int32_t>(),
              L.own.as<uint32_t>(),
@@ -412,7 +414,7 @@ void learned_step(Handle& H, int l) {
   const int r = prof_begin(H, l, GCMG_STAGE_LEARNED);
   vmult(H, l, f64, L.x.p, L.t.p);
   launch_residual(f64, L.t.p, L.b.p, L.t.p, L.n(), H.stream);
-  mlp_correct(H, l, L.mlp_params.as<float>(), f64, L.t.p, L.x.p);
+  mlp_correct(H, l, L.mlp_image.p, f64, L.t.p, L.x.p);
   prof_end(H, r);
 }
 
@@ -448,6 +450,7 @@ void vcycle_level(Handle& H, int l) {
   r = prof_begin(H, l, GCMG_STAGE_PROLONGATE);
   if (C.n()) launch_prolongate_add(H.tr[l]->tl, f64, C.x.p, L.x.p, H.stream);  // prolongation
   prof_end(H, r);
+  if (H.stop_after_cgc && l == (int)H.lev.size() - 1) return;
   if (L.smoother == GCMG_SMOOTHER_MLP_REPLACE) {
     learned_step(H, l);  // learned correction instead of postsmoothing
     return;
@@ -889,6 +892,47 @@ int gcmg_vmult(gcmg_handle* h, int level, int fp64, const void* src, void* dst) 
   });
 }
 
+int gcmg_residual(gcmg_handle* h, int level, int fp64, const void* b, const void* x, void* r) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    check_level(h->h, level);
+    const int64_t n = h->h.lev[level]->n();
+    if (n == 0) return;
+    if (!b || !x || !r || x == r) throw Error(GCMG_ERR_ARG, "bad vectors");
+    vmult(h->h, level, fp64 != 0, x, r);
+    launch_residual(fp64 != 0, r, b, r, n, h->h.stream);
+    ck(cudaGetLastError(), "residual");
+  });
+}
+
+int gcmg_vcycle_cgc(gcmg_handle* h, const double* b, double* x) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    Handle& H = h->h;
+    const int top = (int)H.lev.size() - 1;
+    LevelDev& F = *H.lev[top];
+    if (F.n() == 0) return;
+    if (!b || !x) throw Error(GCMG_ERR_ARG, "bad vectors");
+    if (F.fp32)
+      launch_cast(false, b, F.b.p, F.n(), H.stream);
+    else
+      ck(cudaMemcpyAsync(F.b.p, b, F.n() * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
+    H.stop_after_cgc = true;  // plain launches: the captured graph holds the full cycle
+    try {
+      vcycle_level(H, top);
+    } catch (...) {
+      H.stop_after_cgc = false;
+      throw;
+    }
+    H.stop_after_cgc = false;
+    if (F.fp32)
+      launch_cast(true, F.x.p, x, F.n(), H.stream);
+    else
+      ck(cudaMemcpyAsync(x, F.x.p, F.n() * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
+    ck(cudaGetLastError(), "vcycle");
+  });
+}
+
 int gcmg_diagonal(gcmg_handle* h, int level, double* dst) {
   return guarded([&] {
     if (!h) throw Error(GCMG_ERR_ARG, "null handle");
@@ -1116,7 +1160,7 @@ int gcmg_cell_gather(gcmg_handle* h, int level, const double* x, int64_t n_cells
 }
 
 int gcmg_mlp_samples(gcmg_handle* h, int level, const double* b, const double* x, const double* xstar,
-                     int64_t n_cells, const int32_t* cells, float* X, float* T) {
+                     int64_t n_cells, const int32_t* cells, float* X, float* T, float* W) {
   return guarded([&] {
     if (!h) throw Error(GCMG_ERR_ARG, "null handle");
     check_level(h->h, level);
@@ -1145,7 +1189,7 @@ int gcmg_mlp_samples(gcmg_handle* h, int level, const double* b, const double* x
     launch_cell_gather(k, L.diag64.as<double>(), cells, n_cells, gs, meta, D.as<double>(), H.stream);
     if (T) launch_cell_gather(k, e, cells, n_cells, gs, meta, E.as<double>(), H.stream);
     launch_mlp_samples(R.as<double>(), T ? E.as<double>() : nullptr, D.as<double>(), cells, n_cells, n3, meta,
-                       L.cl.dom, mean_ref_diag(k), X, T, H.stream);
+                       L.cl.dom, mean_ref_diag(k), X, T, W, H.stream);
     ck(cudaStreamSynchronize(H.stream), "samples");  // the temporaries are freed on return
   });
 }
@@ -1167,7 +1211,10 @@ int gcmg_mlp_correct(gcmg_handle* h, int level, const gcmg_mlp* net, int fp64, c
     if (L.n() == 0) return;
     if (!r || !x) throw Error(GCMG_ERR_ARG, "bad vectors");
     ensure_dfeat(h->h, level);
-    mlp_correct(h->h, level, net->net.params.as<float>(), fp64 != 0, r, x);
+    Handle& H = h->h;
+    if (!H.mlp_scratch.p) H.mlp_scratch.alloc(mlp_image_bytes());
+    launch_mlp_pack(net->net.params.as<float>(), H.mlp_scratch.p, H.stream);
+    mlp_correct(H, level, H.mlp_scratch.p, fp64 != 0, r, x);
   });
 }
 
@@ -1182,9 +1229,8 @@ int gcmg_set_smoother(gcmg_handle* h, int level, int kind, const gcmg_mlp* net) 
     if (kind != GCMG_SMOOTHER_CHEBYSHEV) {
       check_q4_net(L, net);
       ensure_dfeat(H, level);
-      const size_t b = net->net.n_params * sizeof(float);
-      if (L.mlp_params.bytes != b) L.mlp_params.alloc(b);
-      ck(cudaMemcpyAsync(L.mlp_params.p, net->net.params.p, b, cudaMemcpyDeviceToDevice, H.stream), "copy");
+      if (!L.mlp_image.p) L.mlp_image.alloc(mlp_image_bytes());
+      launch_mlp_pack(net->net.params.as<float>(), L.mlp_image.p, H.stream);
     }
     L.smoother = kind;
     H.g_core.reset();

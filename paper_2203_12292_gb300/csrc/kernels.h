@@ -110,9 +110,10 @@ constexpr float MLP_BETA1 = 0.9f, MLP_BETA2 = 0.999f, MLP_EPS = 1e-8f;
 void launch_cell_gather(int k, const double* v, const int32_t* cells, int64_t n, const int32_t* gstart,
                         const CellMeta* meta, double* out, cudaStream_t s);
 // training rows from gathered cell values R (residual), E (error, may be
-// null), D (diagonal): X = [R / |R|, D / (h a)], T = E h a / |R|
+// null), D (diagonal): X = [R / |R|, D / (h a)], T = E h a / |R|,
+// W = (|R| / (h a))^2 (T, W may be null)
 void launch_mlp_samples(const double* R, const double* E, const double* D, const int32_t* cells, int64_t n, int n3,
-                        const CellMeta* meta, double dom, double abar, float* X, float* T, cudaStream_t s);
+                        const CellMeta* meta, double dom, double abar, float* X, float* T, float* W, cudaStream_t s);
 // bf16 rows of MLP_DF diagonal features per cell (all cells of a level)
 void launch_mlp_dfeat(const double* D, int64_t n, int n3, const CellMeta* meta, double dom, double abar, void* out,
                       cudaStream_t s);
@@ -132,8 +133,10 @@ struct GemmArgs {
 void launch_gemm_bf16(const GemmArgs& g, cudaStream_t s);
 void launch_gelu(const float* Z, float* H, int64_t n, cudaStream_t s);
 void launch_gelu_bwd(const float* dH, const float* Z, float* dZ, int64_t n, cudaStream_t s);
-// dY = (Y - T) / B, *loss = |Y - T|^2 / (2B)
-void launch_mse(const float* Y, const float* T, float* dY, int64_t n, int B, float* loss, cudaStream_t s);
+// B rows of m outputs, weights W (null: 1): dY = w (Y - T) / sum w,
+// *loss = sum w |Y - T|^2 / (2 sum w)
+void launch_mse(const float* Y, const float* T, const float* W, float* dY, int B, int m, float* loss,
+                cudaStream_t s);
 void launch_colsum(const float* X, int M, int N, float* out, cudaStream_t s);
 void launch_gather_rows(const float* X, int64_t ld, const int32_t* idx, int B, float* out, cudaStream_t s);
 // Adam with bias corrections bc1 = 1 - beta1^t, bc2 = 1 - beta2^t
@@ -142,7 +145,7 @@ void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float 
 
 // fused per-cell correction x += owner-selected MLP(r) for Q4 (250-128-128-125)
 struct MlpFused {
-  const float* params;     // packed fp32 parameters
+  const void* wimg;        // packed bf16 weight image (launch_mlp_pack), 16-byte aligned
   const uint16_t* dfeat;   // bf16 diagonal features, MLP_DF per cell
   const int32_t* gstart;   // cells x 27
   const uint32_t* own;     // per cell: owned slots
@@ -152,6 +155,9 @@ struct MlpFused {
   double abar;             // mean diagonal entry of the unit-cell matrix
 };
 size_t mlp_fused_smem_bytes();
+size_t mlp_image_bytes();
+// weight image of a 250-128-128-125 network from its packed fp32 parameters
+void launch_mlp_pack(const float* params, void* image, cudaStream_t s);
 cudaError_t launch_mlp_correct(const MlpFused& P, bool fp64, const void* r, void* x, cudaStream_t s);
 
 }  // namespace gcmg

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) cell_gather_kernel(const double* v, const
 
 // training samples from gathered cell values: one warp per sample
 __global__ void samples_kernel(const double* R, const double* E, const double* D, const int32_t* cells, int64_t n,
-                               int n3, const CellMeta* meta, double dom, double abar, float* X, float* T) {
+                               int n3, const CellMeta* meta, double dom, double abar, float* X, float* T, float* W) {
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= n) return;
@@ -121,6 +121,7 @@ __global__ void samples_kernel(const double* R, const double* E, const double* D
   const double h = dom / (double)(1u << meta[cell].level);
   const double sinv = s > 0.0 ? 1.0 / s : 0.0;
   const double ts = s > 0.0 ? h * abar / s : 0.0;
+  if (W && lane == 0) W[w] = (float)((s / (h * abar)) * (s / (h * abar)));
   for (int j = lane; j < n3; j += 32) {
     X[w * 2 * n3 + j] = (float)(r[j] * sinv);
     X[w * 2 * n3 + n3 + j] = (float)(D[w * n3 + j] / (h * abar));
@@ -188,24 +189,38 @@ __global__ void gelu_bwd_kernel(const float* dH, const float* Z, float* dZ, int6
     dZ[i] = dH[i] * gelu_grad_f(Z[i]);
 }
 
-// dY = (Y - T) / B and L = sum (Y - T)^2 / (2B): one block, fixed order
-__global__ void __launch_bounds__(256) loss_kernel(const float* Y, const float* T, float* dY, int64_t n, int B,
-                                                   float* loss) {
-  __shared__ float sh[256];
-  float s = 0.0f;
-  const float inv = 1.0f / (float)B;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const float d = Y[i] - T[i];
-    dY[i] = d * inv;
-    s += d * d;
-  }
+__device__ float block_sum256(float s, float* sh) {
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0 && loss) *loss = 0.5f * sh[0] * inv;
+  const float r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// weighted squared error over B rows of m outputs (W null: all weights 1):
+// dY = w (Y - T) / sum w, L = sum w |Y - T|^2 / (2 sum w); one block, fixed order
+__global__ void __launch_bounds__(256) loss_kernel(const float* Y, const float* T, const float* W, float* dY, int B,
+                                                   int m, float* loss) {
+  __shared__ float sh[256];
+  float sw = 0.0f;
+  if (W)
+    for (int b = threadIdx.x; b < B; b += blockDim.x) sw += W[b];
+  sw = W ? block_sum256(sw, sh) : (float)B;
+  const float inv = sw > 0.0f ? 1.0f / sw : 0.0f;
+  float s = 0.0f;
+  const int64_t n = (int64_t)B * m;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const float w = W ? W[i / m] : 1.0f;
+    const float d = Y[i] - T[i];
+    dY[i] = w * d * inv;
+    s += w * d * d;
+  }
+  s = block_sum256(s, sh);
+  if (threadIdx.x == 0 && loss) *loss = 0.5f * s * inv;
 }
 
 // out[j] = sum_i X[i][j] (rows in order)
@@ -238,33 +253,68 @@ __global__ void adam_kernel(float* p, const float* g, float* m, float* v, int64_
 // fused inference for Q4: 250 -> 128 -> 128 -> 125
 // ---------------------------------------------------------------------------
 constexpr int FK = 4, FN3 = 125, FC = 64, FT = 512;  // degree, nodes, cells per batch, threads
-constexpr int XS = 264, HS = 136;                     // row strides (bf16) of X / W1 and of H / W2 / W3
+constexpr int XS = 264, HS = 136, SS = 128;           // row strides: X / W1 (bf16), H / W2 / W3 (bf16), staging (fp32)
+// shared memory = [weight image (W1, W2, W3 bf16, biases fp32) | X | H | staging | per-cell data]
 constexpr size_t F_W1 = 0;
 constexpr size_t F_W2 = F_W1 + 128 * XS * 2;
 constexpr size_t F_W3 = F_W2 + 128 * HS * 2;
-constexpr size_t F_X = F_W3 + 128 * HS * 2;
+constexpr size_t F_B = F_W3 + 128 * HS * 2;
+constexpr size_t F_IMG = F_B + 3 * 128 * 4;  // bytes of the packed weight image
+constexpr size_t F_X = F_IMG;
 constexpr size_t F_H = F_X + FC * XS * 2;
 constexpr size_t F_ST = F_H + FC * HS * 2;
-constexpr size_t F_B = F_ST + FC * 128 * 4;
-constexpr size_t F_SC = F_B + 3 * 128 * 4;
+constexpr size_t F_SC = F_ST + FC * SS * 4;
 constexpr size_t F_SI = F_SC + FC * 4;
 constexpr size_t F_GS = F_SI + FC * 4;
 constexpr size_t F_OWN = F_GS + FC * NSLOT * 4;
 constexpr size_t F_MK = F_OWN + FC * 4;
 constexpr size_t F_BYTES = F_MK + FC * 2;
 static_assert(F_BYTES <= 232448, "fused MLP kernel exceeds the shared memory of a CTA");
-static_assert(F_X % 16 == 0 && (XS * 2) % 16 == 0, "16-byte aligned feature rows");
+static_assert(F_IMG % 16 == 0 && F_X % 16 == 0 && (XS * 2) % 16 == 0, "16-byte aligned rows");
+constexpr int GPT = (FC * FN3 + FT - 1) / FT;  // gathered values per thread and batch
+constexpr int GH = 8;                            // of them in flight at once
+
+// packed bf16 weight image in the shared-memory layout of the fused kernel
+// (feature columns: residual 0..124, diagonal 128..252; padding zero)
+__global__ void mlp_pack_kernel(const float* __restrict__ P, unsigned char* img) {
+  const float* W1 = P;
+  const float* b1 = W1 + 128 * 250;
+  const float* W2 = b1 + 128;
+  const float* b2 = W2 + 128 * 128;
+  const float* W3 = b2 + 128;
+  const float* b3 = W3 + 125 * 128;
+  bf16* W1s = reinterpret_cast<bf16*>(img + F_W1);
+  bf16* W2s = reinterpret_cast<bf16*>(img + F_W2);
+  bf16* W3s = reinterpret_cast<bf16*>(img + F_W3);
+  float* bs = reinterpret_cast<float*>(img + F_B);
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 128 * XS; e += stride) {
+    const int n = e / XS, k = e - n * XS;
+    const float v = k < 125 ? W1[n * 250 + k] : ((k >= 128 && k < 253) ? W1[n * 250 + k - 3] : 0.0f);
+    W1s[e] = __float2bfloat16_rn(v);
+  }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 128 * HS; e += stride) {
+    const int n = e / HS, k = e - n * HS;
+    W2s[e] = __float2bfloat16_rn(k < 128 ? W2[n * 128 + k] : 0.0f);
+    W3s[e] = __float2bfloat16_rn((k < 128 && n < 125) ? W3[n * 128 + k] : 0.0f);
+  }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 128; e += stride) {
+    bs[e] = b1[e];
+    bs[128 + e] = b2[e];
+    bs[256 + e] = e < 125 ? b3[e] : 0.0f;
+  }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T* __restrict__ r, T* x) {
   extern __shared__ __align__(16) unsigned char smem[];
-  bf16* W1s = reinterpret_cast<bf16*>(smem + F_W1);
-  bf16* W2s = reinterpret_cast<bf16*>(smem + F_W2);
-  bf16* W3s = reinterpret_cast<bf16*>(smem + F_W3);
+  const bf16* W1s = reinterpret_cast<const bf16*>(smem + F_W1);
+  const bf16* W2s = reinterpret_cast<const bf16*>(smem + F_W2);
+  const bf16* W3s = reinterpret_cast<const bf16*>(smem + F_W3);
+  const float* bs = reinterpret_cast<const float*>(smem + F_B);
   bf16* Xs = reinterpret_cast<bf16*>(smem + F_X);
   bf16* Hs = reinterpret_cast<bf16*>(smem + F_H);
   float* St = reinterpret_cast<float*>(smem + F_ST);
-  float* bs = reinterpret_cast<float*>(smem + F_B);
   float* sc = reinterpret_cast<float*>(smem + F_SC);
   float* si = reinterpret_cast<float*>(smem + F_SI);
   int32_t* gs = reinterpret_cast<int32_t*>(smem + F_GS);
@@ -272,27 +322,21 @@ __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T*
   uint16_t* mk = reinterpret_cast<uint16_t*>(smem + F_MK);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // weights, bf16, once per CTA; feature columns: residual 0..124, diagonal 128..252
-  const float* W1 = P.params;
-  const float* b1 = W1 + 128 * 250;
-  const float* W2 = b1 + 128;
-  const float* b2 = W2 + 128 * 128;
-  const float* W3 = b2 + 128;
-  const float* b3 = W3 + 125 * 128;
-  for (int e = tid; e < 128 * 256; e += FT) {
-    const int n = e >> 8, k = e & 255;
-    const float v = k < 125 ? W1[n * 250 + k] : ((k >= 128 && k < 253) ? W1[n * 250 + k - 3] : 0.0f);
-    W1s[n * XS + k] = __float2bfloat16_rn(v);
-  }
-  for (int e = tid; e < 128 * 128; e += FT) {
-    const int n = e >> 7, k = e & 127;
-    W2s[n * HS + k] = __float2bfloat16_rn(W2[n * 128 + k]);
-    W3s[n * HS + k] = __float2bfloat16_rn(n < 125 ? W3[n * 128 + k] : 0.0f);
-  }
-  for (int e = tid; e < 128; e += FT) {
-    bs[e] = b1[e];
-    bs[128 + e] = b2[e];
-    bs[256 + e] = e < 125 ? b3[e] : 0.0f;
+  // the packed weight image, once per CTA (16-byte copies, all in flight)
+  {
+    constexpr int NV = (int)(F_IMG / 16), PER = (NV + FT - 1) / FT, CH = 6;
+    const uint4* src = reinterpret_cast<const uint4*>(P.wimg);
+    uint4* dst = reinterpret_cast<uint4*>(smem);
+#pragma unroll 1
+    for (int u0 = 0; u0 < PER; u0 += CH) {
+      uint4 v[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (u0 + u < PER && tid + (u0 + u) * FT < NV) v[u] = src[tid + (u0 + u) * FT];
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (u0 + u < PER && tid + (u0 + u) * FT < NV) dst[tid + (u0 + u) * FT] = v[u];
+    }
   }
 
   const int rb = warp & 3, cq = warp >> 2;  // rows 16 rb .., columns 32 cq ..
@@ -307,23 +351,39 @@ __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T*
       own[tid] = tid < nc ? P.own[c0 + tid] : 0u;
     }
     __syncthreads();
-    // gather the residual at the 125 nodes of every cell (16 loads in flight per thread)
-#pragma unroll 4
-    for (int e = tid; e < FC * FN3; e += FT) {
-      const int i = e / FN3, j = e - i * FN3;
-      int slot, off;
-      node_slot<FK>(j % 5, (j / 5) % 5, j / 25, slot, off);
-      const int32_t base = gs[i * NSLOT + slot];
-      St[i * 128 + j] = base >= 0 ? (float)r[base + off] : 0.0f;
+    // gather the residual at the 125 nodes of every cell (GH loads in flight per thread)
+#pragma unroll 1
+    for (int u0 = 0; u0 < GPT; u0 += GH) {
+      float v[GH];
+#pragma unroll
+      for (int u = 0; u < GH; ++u) {
+        const int e = tid + (u0 + u) * FT;
+        v[u] = 0.0f;
+        if (e < FC * FN3) {
+          const int i = e / FN3, j = e - i * FN3;
+          int slot, off;
+          node_slot<FK>(j % 5, (j / 5) % 5, j / 25, slot, off);
+          const int32_t base = gs[i * NSLOT + slot];
+          if (base >= 0) v[u] = (float)r[base + off];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < GH; ++u) {
+        const int e = tid + (u0 + u) * FT;
+        if (e < FC * FN3) {
+          const int i = e / FN3, j = e - i * FN3;
+          St[i * SS + j] = v[u];
+        }
+      }
     }
     const int hang = __syncthreads_or(tid < nc && (mk[tid] & MASK_HANG));
-    if (hang) hanging_all<FK, false, float, 128>(St, mk, nc);
+    if (hang) hanging_all<FK, false, float, SS>(St, mk, nc);
     // cell norms and scales: warp w handles cells 4w .. 4w + 3
 #pragma unroll
     for (int q = 0; q < FC / (FT / 32); ++q) {
       const int i = warp * (FC / (FT / 32)) + q;
       float ss = 0.0f;
-      for (int j = lane; j < FN3; j += 32) ss += St[i * 128 + j] * St[i * 128 + j];
+      for (int j = lane; j < FN3; j += 32) ss += St[i * SS + j] * St[i * SS + j];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
       if (lane == 0) {
@@ -337,8 +397,8 @@ __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T*
     // features: bf16(r / s) in columns 0..127, the diagonal features in 128..255
     for (int e = tid; e < FC * 64; e += FT) {
       const int i = e >> 6, j = (e & 63) * 2;
-      const float v0 = j < FN3 ? St[i * 128 + j] * si[i] : 0.0f;
-      const float v1 = j + 1 < FN3 ? St[i * 128 + j + 1] * si[i] : 0.0f;
+      const float v0 = j < FN3 ? St[i * SS + j] * si[i] : 0.0f;
+      const float v1 = j + 1 < FN3 ? St[i * SS + j + 1] * si[i] : 0.0f;
       *reinterpret_cast<uint32_t*>(Xs + i * XS + j) = pack_bf16(v0, v1);
     }
     for (int e = tid; e < FC * 16; e += FT) {
@@ -385,20 +445,34 @@ __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T*
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int col = cq * 32 + nt * 8 + 2 * t4 + (e & 1), row = rb * 16 + g + (e >> 1) * 8;
-          if (col < FN3) St[row * 128 + col] = (acc[nt][e] + bs[256 + col]) * sc[row];
+          if (col < FN3) St[row * SS + col] = (acc[nt][e] + bs[256 + col]) * sc[row];
         }
     }
     __syncthreads();
-    // owner-selected update of x
-#pragma unroll 4
-    for (int e = tid; e < FC * FN3; e += FT) {
-      const int i = e / FN3, j = e - i * FN3;
-      if (i >= nc) continue;
-      int slot, off;
-      node_slot<FK>(j % 5, (j / 5) % 5, j / 25, slot, off);
-      if ((own[i] >> slot) & 1u) {
-        const int32_t base = gs[i * NSLOT + slot];
-        x[base + off] += (T)St[i * 128 + j];
+    // owner-selected update of x (GH loads in flight per thread)
+#pragma unroll 1
+    for (int u0 = 0; u0 < GPT; u0 += GH) {
+      int idx[GH];
+      T xv[GH];
+#pragma unroll
+      for (int u = 0; u < GH; ++u) {
+        const int e = tid + (u0 + u) * FT;
+        idx[u] = -1;
+        if (e < FC * FN3) {
+          const int i = e / FN3, j = e - i * FN3;
+          int slot, off;
+          node_slot<FK>(j % 5, (j / 5) % 5, j / 25, slot, off);
+          if (i < nc && ((own[i] >> slot) & 1u)) idx[u] = gs[i * NSLOT + slot] + off;
+        }
+        if (idx[u] >= 0) xv[u] = x[idx[u]];
+      }
+#pragma unroll
+      for (int u = 0; u < GH; ++u) {
+        const int e = tid + (u0 + u) * FT;
+        if (idx[u] >= 0) {
+          const int i = e / FN3, j = e - i * FN3;
+          x[idx[u]] = xv[u] + (T)St[i * SS + j];
+        }
       }
     }
     __syncthreads();
@@ -428,9 +502,9 @@ void launch_cell_gather(int k, const double* v, const int32_t* cells, int64_t n,
 }
 
 void launch_mlp_samples(const double* R, const double* E, const double* D, const int32_t* cells, int64_t n, int n3,
-                        const CellMeta* meta, double dom, double abar, float* X, float* T, cudaStream_t s) {
+                        const CellMeta* meta, double dom, double abar, float* X, float* T, float* W, cudaStream_t s) {
   if (n <= 0) return;
-  samples_kernel<<<(int)((n * 32 + 255) / 256), 256, 0, s>>>(R, E, D, cells, n, n3, meta, dom, abar, X, T);
+  samples_kernel<<<(int)((n * 32 + 255) / 256), 256, 0, s>>>(R, E, D, cells, n, n3, meta, dom, abar, X, T, W);
   note_launches(1);
 }
 
@@ -458,8 +532,9 @@ void launch_gelu_bwd(const float* dH, const float* Z, float* dZ, int64_t n, cuda
   note_launches(1);
 }
 
-void launch_mse(const float* Y, const float* T, float* dY, int64_t n, int B, float* loss, cudaStream_t s) {
-  loss_kernel<<<1, 256, 0, s>>>(Y, T, dY, n, B, loss);
+void launch_mse(const float* Y, const float* T, const float* W, float* dY, int B, int m, float* loss,
+                cudaStream_t s) {
+  loss_kernel<<<1, 256, 0, s>>>(Y, T, W, dY, B, m, loss);
   note_launches(1);
 }
 
@@ -481,6 +556,12 @@ void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float 
 }
 
 size_t mlp_fused_smem_bytes() { return F_BYTES; }
+size_t mlp_image_bytes() { return F_IMG; }
+
+void launch_mlp_pack(const float* params, void* image, cudaStream_t s) {
+  mlp_pack_kernel<<<64, 256, 0, s>>>(params, static_cast<unsigned char*>(image));
+  note_launches(1);
+}
 
 cudaError_t launch_mlp_correct(const MlpFused& P, bool fp64, const void* r, void* x, cudaStream_t s) {
   if (P.n_cells <= 0) return cudaSuccess;

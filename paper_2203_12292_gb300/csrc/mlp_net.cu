@@ -17,6 +17,7 @@ void MlpNet::reserve(int64_t rows) {
   const int64_t w = std::max(n_h, std::max(n_in, n_out));
   Xb.alloc(rows * n_in * sizeof(float));
   Tb.alloc(rows * n_out * sizeof(float));
+  Wb.alloc(rows * sizeof(float));
   Z1.alloc(rows * n_h * sizeof(float));
   H1.alloc(rows * n_h * sizeof(float));
   Z2.alloc(rows * n_h * sizeof(float));
@@ -45,11 +46,11 @@ void MlpNet::forward(const float* X, int64_t rows, float* Yout, cudaStream_t s) 
   linear(H2.as<float>(), rows, n_h, P + oW3(), P + ob3(), n_out, Yout, s);
 }
 
-void MlpNet::gradient(const float* X, const float* T, int B, float* loss_out, cudaStream_t s) {
+void MlpNet::gradient(const float* X, const float* T, const float* W, int B, float* loss_out, cudaStream_t s) {
   const float* P = params.as<float>();
   float* G = grad.as<float>();
   forward(X, B, Y.as<float>(), s);
-  launch_mse(Y.as<float>(), T, dY.as<float>(), (int64_t)B * n_out, B, loss_out, s);
+  launch_mse(Y.as<float>(), T, W, dY.as<float>(), B, n_out, loss_out, s);
   // layer 3: gW3 = dY^T H2, gb3 = sum dY, dH2 = dY W3
   launch_gemm_bf16(GemmArgs{dY.as<float>(), 1, n_out, H2.as<float>(), n_h, 1, G + oW3(), n_h, nullptr, n_out, n_h, B}, s);
   launch_colsum(dY.as<float>(), B, n_out, G + ob3(), s);
@@ -149,21 +150,21 @@ int gcmg_mlp_forward(gcmg_mlp* net, const float* X, int64_t n, float* Y, void* s
   });
 }
 
-int gcmg_mlp_gradient(gcmg_mlp* net, const float* X, const float* T, int64_t n, float* grad, float* loss,
-                      void* stream) {
+int gcmg_mlp_gradient(gcmg_mlp* net, const float* X, const float* T, const float* W, int64_t n, float* grad,
+                      float* loss, void* stream) {
   return guarded([&] {
     if (!net || !X || !T || !grad || n <= 0 || n > (1 << 20)) throw Error(GCMG_ERR_ARG, "bad arguments");
     MlpNet& N = net->net;
     cudaStream_t s = as_stream(stream);
     N.reserve(n);
-    N.gradient(X, T, (int)n, loss ? loss : N.loss.as<float>(), s);
+    N.gradient(X, T, W, (int)n, loss ? loss : N.loss.as<float>(), s);
     ck(cudaMemcpyAsync(grad, N.grad.p, N.n_params * sizeof(float), cudaMemcpyDeviceToDevice, s), "copy");
     ck(cudaGetLastError(), "mlp gradient");
   });
 }
 
-int gcmg_mlp_train(gcmg_mlp* net, const float* X, const float* T, int64_t n_samples, const int32_t* order,
-                   int64_t n_order, int batch, float lr, float* losses, void* stream) {
+int gcmg_mlp_train(gcmg_mlp* net, const float* X, const float* T, const float* W, int64_t n_samples,
+                   const int32_t* order, int64_t n_order, int batch, float lr, float* losses, void* stream) {
   return guarded([&] {
     if (!net || !X || !T || !order || n_samples <= 0 || batch <= 0 || batch > 65536 || n_order < batch ||
         !(lr > 0.0f))
@@ -176,7 +177,9 @@ int gcmg_mlp_train(gcmg_mlp* net, const float* X, const float* T, int64_t n_samp
       const int32_t* idx = order + st * batch;
       launch_gather_rows(X, N.n_in, idx, batch, N.Xb.as<float>(), s);
       launch_gather_rows(T, N.n_out, idx, batch, N.Tb.as<float>(), s);
-      N.gradient(N.Xb.as<float>(), N.Tb.as<float>(), batch, losses ? losses + st : N.loss.as<float>(), s);
+      if (W) launch_gather_rows(W, 1, idx, batch, N.Wb.as<float>(), s);
+      N.gradient(N.Xb.as<float>(), N.Tb.as<float>(), W ? N.Wb.as<float>() : nullptr, batch,
+                 losses ? losses + st : N.loss.as<float>(), s);
       N.adam(lr, s);
     }
     ck(cudaGetLastError(), "mlp train");

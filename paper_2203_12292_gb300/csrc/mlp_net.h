@@ -16,7 +16,7 @@ struct MlpNet {
   int64_t steps = 0;  // Adam steps taken since the parameters were set
   // work buffers for `cap` rows
   int64_t cap = 0;
-  DevBuf Xb, Tb, Z1, H1, Z2, H2, Y, dY, dA, dB, loss;
+  DevBuf Xb, Tb, Wb, Z1, H1, Z2, H2, Y, dY, dA, dB, loss;
 
   // offsets of W1, b1, W2, b2, W3, b3 in the packed parameter vector
   int64_t oW1() const { return 0; }
@@ -29,8 +29,9 @@ struct MlpNet {
   void reserve(int64_t rows);
   // Y = network(X) for `rows` rows (rows <= cap); keeps Z1, H1, Z2, H2
   void forward(const float* X, int64_t rows, float* Y, cudaStream_t s);
-  // loss and gradient (into `grad`) of 1/(2B) |Y - T|^2 over B rows
-  void gradient(const float* X, const float* T, int B, float* loss, cudaStream_t s);
+  // loss and gradient (into `grad`) of sum w |Y - T|^2 / (2 sum w) over B
+  // rows (W null: all weights 1)
+  void gradient(const float* X, const float* T, const float* W, int B, float* loss, cudaStream_t s);
   void adam(float lr, cudaStream_t s);
 };
 

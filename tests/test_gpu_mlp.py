@@ -88,15 +88,19 @@ def test_cell_gather(gcmg, k):
 def test_samples(q4):
     b, x, xs = q4.gvec(1), q4.gvec(2), q4.gvec(3)
     cells = torch.arange(q4.gm.n_cells(q4.L), dtype=torch.int32, device="cuda")
-    X, T = q4.gm.mlp_samples(q4.L, b, x, xs, cells)
+    X, T, W = q4.gm.mlp_samples(q4.L, b, x, xs, cells)
     s = q4.space
     r = q4.ovec(1) - s.apply(q4.ovec(2))
     Xo, _ = omlp.cell_features(s, r, s.diagonal())
     To = omlp.cell_targets(s, r, q4.ovec(3) - q4.ovec(2))
+    Wo = omlp.cell_weights(s, r)
     assert rel_err(X.cpu().numpy(), Xo[q4.cell_map]) < 1e-6
     assert rel_err(T.cpu().numpy(), To[q4.cell_map]) < 1e-6
-    X2, T2 = q4.gm.mlp_samples(q4.L, b, x, None, cells)
-    assert T2 is None and torch.equal(X, X2)
+    assert rel_err(W.cpu().numpy(), Wo[q4.cell_map]) < 1e-6
+    X2, T2, W2 = q4.gm.mlp_samples(q4.L, b, x, None, cells)
+    assert T2 is None and torch.equal(X, X2) and torch.equal(W, W2)
+    with pytest.raises(ValueError):
+        q4.gm.mlp_samples(q4.L, b, x, xs, torch.tensor([0, q4.gm.n_cells(q4.L)], dtype=torch.int32, device="cuda"))
 
 
 def test_forward(gcmg):
@@ -111,19 +115,22 @@ def test_forward(gcmg):
     assert rel_err(Y, Ye) < 3e-2
 
 
-@pytest.mark.parametrize("sizes", [(250, 128, 125, 64), (54, 128, 27, 200), (7, 33, 5, 3)])
+@pytest.mark.parametrize("sizes", [(250, 128, 125, 64, False), (250, 128, 125, 64, True), (54, 128, 27, 200, True),
+                                   (7, 33, 5, 3, False)])
 def test_gradient(gcmg, sizes):
-    n_in, n_h, n_out, B = sizes
+    n_in, n_h, n_out, B, weighted = sizes
     shape = omlp.Shape(n_in, n_h, n_out)
     theta = synth.mlp_init(n_in, n_h, n_out, 13)
     X = synth.uniform_vector(B * n_in, 14).reshape(B, n_in).astype(np.float32).astype(np.float64)
     T = synth.uniform_vector(B * n_out, 15).reshape(B, n_out).astype(np.float32).astype(np.float64)
+    W = synth.uniform_vector(B, 16, 0.0, 5.0).astype(np.float32).astype(np.float64) if weighted else None
     net = gcmg.MLP(n_in, n_h, n_out)
     net.set_params(torch.tensor(theta, dtype=torch.float32, device="cuda"))
     L, g = net.gradient(torch.tensor(X, dtype=torch.float32, device="cuda"),
-                        torch.tensor(T, dtype=torch.float32, device="cuda"))
-    Lb, gb = omlp.loss_and_grad(shape, theta, X, T, bf16=True)
-    Le, ge = omlp.loss_and_grad(shape, theta, X, T)
+                        torch.tensor(T, dtype=torch.float32, device="cuda"),
+                        None if W is None else torch.tensor(W, dtype=torch.float32, device="cuda"))
+    Lb, gb = omlp.loss_and_grad(shape, theta, X, T, bf16=True, W=W)
+    Le, ge = omlp.loss_and_grad(shape, theta, X, T, W=W)
     g = g.double().cpu().numpy()
     assert abs(L.item() - Lb) <= 5e-3 * Lb
     assert rel_err(g, gb) < 5e-3
@@ -144,11 +151,13 @@ def test_training_steps(gcmg):
     W = synth.uniform_vector(250 * 125, 23).reshape(250, 125) / 16
     T = (np.tanh(X @ W)).astype(np.float32).astype(np.float64)
     order = synth.sample_order(n, 3, 24)
+    W = synth.uniform_vector(n, 25, 0.5, 2.0).astype(np.float32).astype(np.float64)
     net = _net(gcmg, theta)
     losses = net.train(torch.tensor(X, dtype=torch.float32, device="cuda"),
                        torch.tensor(T, dtype=torch.float32, device="cuda"),
-                       torch.tensor(order, device="cuda"), 32, 1e-3).double().cpu().numpy()
-    theta_o, losses_o = omlp.train(shape, theta, X, T, order, 32, 1e-3, bf16=True)
+                       torch.tensor(order, device="cuda"), 32, 1e-3,
+                       W=torch.tensor(W, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    theta_o, losses_o = omlp.train(shape, theta, X, T, order, 32, 1e-3, bf16=True, W=W)
     assert len(losses) == len(losses_o) == 24
     assert np.abs(losses - losses_o).max() <= 2e-2 * losses_o.max()
     assert losses[-4:].mean() < losses[:4].mean()

@@ -91,6 +91,32 @@ def test_gradient_matches_finite_differences(sizes):
         assert abs(fd - g[i]) <= 1e-7 * max(1.0, np.abs(g).max()), (i, fd, g[i])
 
 
+def test_weighted_loss():
+    shape, theta, X, T = _small(4, 6, 5, 4, 9)
+    W = synth.uniform_vector(9, 50, 0.1, 3.0)
+    L1, g1 = mlp.loss_and_grad(shape, theta, X, T)
+    L2, g2 = mlp.loss_and_grad(shape, theta, X, T, W=np.ones(9))
+    assert L1 == L2 and np.array_equal(g1, g2)
+    # invariant under scaling all weights
+    La, ga = mlp.loss_and_grad(shape, theta, X, T, W=W)
+    Lb, gb = mlp.loss_and_grad(shape, theta, X, T, W=7.5 * W)
+    assert abs(La - Lb) < 1e-14 * La and np.abs(ga - gb).max() < 1e-14 * np.abs(ga).max()
+    # integer weights = repeated rows
+    Wi = np.array([1, 2, 1, 3, 1, 1, 2, 1, 1], dtype=float)
+    rep = np.repeat(np.arange(9), Wi.astype(int))
+    Lr, gr = mlp.loss_and_grad(shape, theta, X[rep], T[rep])
+    Lw, gw = mlp.loss_and_grad(shape, theta, X, T, W=Wi)
+    assert abs(Lr - Lw) < 1e-14 and np.abs(gr - gw).max() < 1e-14
+    # finite differences with weights
+    h = 1e-6
+    for i in range(0, len(theta), 7):
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (mlp.loss_and_grad(shape, tp, X, T, W=W)[0] - mlp.loss_and_grad(shape, tm, X, T, W=W)[0]) / (2 * h)
+        assert abs(fd - ga[i]) <= 1e-7 * max(1.0, np.abs(ga).max())
+
+
 def test_bf16_mode_close_to_exact():
     shape, theta, X, T = _small(3, 250, 128, 125, 16)
     Y, _ = mlp.forward(shape, theta, X)
@@ -266,6 +292,12 @@ def test_features_and_targets():
     # the target maps back to the error through the correction scaling
     ee = (s.C @ e)[s.cell_nodes]
     assert np.allclose(T[nz] * (se[nz] / (s.h[nz] * a))[:, None], ee[nz], rtol=0, atol=1e-13)
+    # weighted target error = error of the correction itself
+    W = mlp.cell_weights(s, r)
+    Y = synth.uniform_vector(T.size, 3).reshape(T.shape)
+    C = Y * (se / (s.h * a))[:, None]
+    assert np.allclose(W[nz] * np.sum((Y[nz] - T[nz]) ** 2, axis=1), np.sum((C[nz] - ee[nz]) ** 2, axis=1),
+                       rtol=1e-12, atol=0)
 
 
 # ---------------------------------------------------------------------------
