@@ -97,6 +97,8 @@ typedef struct {
   int eig_steps;           /* CG steps of the lambda_max estimate */
   double eig_safety;       /* lambda_max = safety * estimate */
   int tile_cells;          /* cells per tile, 0 = default per degree */
+  int cell_kernel;         /* fp32 operator kernel: 0 = slab threads per cell
+                              (tiles <= 64 cells), 1 = line-parallel kernel */
 } gcmg_config;
 
 int gcmg_config_default(gcmg_config* cfg);
@@ -341,6 +343,62 @@ int gcmg_mlp_correct(gcmg_handle* h, int level, const gcmg_mlp* net, int fp64, c
  * to flexible CG (beta = r_{k+1}.(z_{k+1} - z_k) / r_k.z_k, Notay 2000).
  */
 int gcmg_set_smoother(gcmg_handle* h, int level, int kind, const gcmg_mlp* net);
+
+/* ------------------------------------------------------------------------
+ * Batches of independent problems (an extension: the paper solves one
+ * problem per run).  Every problem has its own handle; one CUDA graph holds
+ * all of them, each as CG prologue -> conditional WHILE node (body: one CG
+ * iteration with its V-cycle and a device-side convergence check that sets
+ * the node's condition) -> epilogue, so one graph launch solves the whole
+ * batch with no host round trip; the problems are independent branches and
+ * run concurrently.
+ * ------------------------------------------------------------------------ */
+typedef struct gcmg_batch gcmg_batch;
+
+typedef struct {
+  int degree;
+  int tile_cells;   /* cells per tile */
+  int cell_kernel;  /* gcmg_config.cell_kernel */
+  double gdofs;     /* measured operator throughput (free DoFs per ns) */
+} gcmg_tuning;
+
+/*
+ * Autotuner of the operator: for one degree, times the finest-level
+ * operator (fp32 when mg_fp32, else fp64) on the probe mesh for every
+ * candidate tile size (32, 64, 128 cells) and thread mapping (slab threads
+ * per cell, line-parallel) over `reps` applications with CUDA events and
+ * returns the fastest in *best; all (optional, >= 5 entries) and n_all get
+ * every candidate.  Synchronises `stream`.
+ */
+int gcmg_autotune(const gcmg_mesh* probe, int degree, int mg_fp32, int reps, void* stream, gcmg_tuning* best,
+                  gcmg_tuning* all, int* n_all);
+/*
+ * Set-up of n problems (meshes[i], cfgs[i]); the host set-up runs on
+ * n_threads threads (0: 16).  The meshes must outlive the call only.
+ */
+int gcmg_batch_create(int n, const gcmg_mesh* const* meshes, const gcmg_config* cfgs, int n_threads, void* stream,
+                      gcmg_batch** out);
+void gcmg_batch_destroy(gcmg_batch* b);
+int gcmg_batch_size(const gcmg_batch* b, int* n);
+/* the handle of problem i (owned by the batch): right-hand sides, sizes */
+int gcmg_batch_handle(gcmg_batch* b, int i, gcmg_handle** h);
+/*
+ * CG with one V-cycle per iteration for every problem (as gcmg_cg_solve;
+ * maxit >= 1): b[i], x[i] fp64 device vectors of problem i (host arrays of
+ * n device pointers); stats: host array of n entries or NULL.  The graph is
+ * built on the first call and re-used while the pointers, rtol and maxit
+ * stay the same.  Synchronises the batch's stream.
+ */
+int gcmg_batch_cg_solve(gcmg_batch* b, const double* const* rhs, double* const* x, double rtol, int maxit,
+                        gcmg_solve_stats* stats);
+
+/*
+ * Host utility: out[i] = a uniform value in [-1, 1) attached to the point
+ * xyz[3i..3i+2] (coordinates rounded to multiples of 2^-20, mixed with the
+ * SplitMix64 output function), independent of any numbering.  The
+ * eigenvalue estimate starts from 1 + these values with seed 2203.
+ */
+int gcmg_point_values(const double* xyz, int64_t n, uint64_t seed, double* out);
 
 const char* gcmg_last_error(void);
 /* number of CUDA kernel launches issued by this library since it was loaded */

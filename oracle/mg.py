@@ -18,7 +18,11 @@ Follows:
 
 Readings where the paper is silent (Chebyshev parameters): the largest
 eigenvalue of D^{-1}A is estimated from the Lanczos tridiagonal matrix of 12
-Jacobi-preconditioned CG steps on A y = 1 (starting from y = 0); the
+Jacobi-preconditioned CG steps on A y = s (starting from y = 0), s the
+all-ones vector plus a seeded perturbation 1 + u(x), u the position-keyed
+uniform values of synth.point_values (a smooth start vector alone misses the
+top of the spectrum on uniform meshes and the smoother then amplifies
+it); the
 smoother works on [1.2 lam / 20, 1.2 lam]; the recurrence is the
 three-term Chebyshev acceleration of Saad (Iterative Methods for Sparse
 Linear Systems, 2nd ed., Algorithm 12.1), so that degree 3 costs 2 operator
@@ -34,6 +38,8 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
+import synth
+
 from . import mesh as omesh
 from .space import Space
 from .transfer import prolongation_matrix
@@ -44,13 +50,15 @@ SMOOTHING_RANGE = 20.0
 CHEB_DEGREE = 3
 
 
-def lanczos_lambda_max(apply: Callable, dinv: np.ndarray, n_steps: int = EIG_CG_STEPS) -> float:
+def lanczos_lambda_max(apply: Callable, dinv: np.ndarray, n_steps: int = EIG_CG_STEPS,
+                       start: Optional[np.ndarray] = None) -> float:
     """Largest eigenvalue of the Lanczos tridiagonal matrix built from the
-    coefficients alpha_k, beta_k of Jacobi-preconditioned CG on A y = 1."""
+    coefficients alpha_k, beta_k of Jacobi-preconditioned CG on A y = start
+    (all ones when not given)."""
     n = len(dinv)
     if n == 0:
         return 1.0
-    b = np.ones(n)
+    b = np.ones(n) if start is None else np.asarray(start, dtype=np.float64)
     x = np.zeros(n)
     r = b.copy()
     z = dinv * r
@@ -168,7 +176,8 @@ def build_levels(fine_mesh: omesh.Mesh, k: int, p_coarsening: bool = False,
         if lam_max is not None:
             lev.lam_max = lam_max[idx]
         else:
-            lev.lam_max = EIG_SAFETY * lanczos_lambda_max(lev.apply64, 1.0 / lev.diag)
+            start = 1.0 + synth.point_values(lev.space.free_coordinates(), synth.LANCZOS_START_SEED)
+            lev.lam_max = EIG_SAFETY * lanczos_lambda_max(lev.apply64, 1.0 / lev.diag, start=start)
     return levels
 
 

@@ -42,7 +42,7 @@ class RefineStep(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("degree", _c_int), ("p_coarsening", _c_int), ("mg_fp32", _c_int), ("cheb_degree", _c_int),
                 ("smoothing_range", _c_double), ("eig_steps", _c_int), ("eig_safety", _c_double),
-                ("tile_cells", _c_int)]
+                ("tile_cells", _c_int), ("cell_kernel", _c_int)]
 
 
 class LevelInfo(ctypes.Structure):
@@ -52,6 +52,10 @@ class LevelInfo(ctypes.Structure):
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", _c_int), ("r0", _c_double), ("rel_residual", _c_double), ("status", _c_int)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("degree", _c_int), ("tile_cells", _c_int), ("cell_kernel", _c_int), ("gdofs", _c_double)]
 
 
 _SIGS = {
@@ -105,6 +109,16 @@ _SIGS = {
                                   _c_void_p, _c_void_p, _c_void_p]),
     "gcmg_mlp_correct": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_int, _c_void_p, _c_void_p]),
     "gcmg_set_smoother": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p]),
+    "gcmg_point_values": (_c_int, [_c_void_p, _c_int64, ctypes.c_uint64, _c_void_p]),
+    "gcmg_autotune": (_c_int, [_c_void_p, _c_int, _c_int, _c_int, _c_void_p, ctypes.POINTER(Tuning),
+                               ctypes.POINTER(Tuning), ctypes.POINTER(_c_int)]),
+    "gcmg_batch_create": (_c_int, [_c_int, ctypes.POINTER(_c_void_p), ctypes.POINTER(Config), _c_int, _c_void_p,
+                                   ctypes.POINTER(_c_void_p)]),
+    "gcmg_batch_destroy": (None, [_c_void_p]),
+    "gcmg_batch_size": (_c_int, [_c_void_p, ctypes.POINTER(_c_int)]),
+    "gcmg_batch_handle": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_void_p)]),
+    "gcmg_batch_cg_solve": (_c_int, [_c_void_p, ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p), _c_double,
+                                     _c_int, ctypes.POINTER(SolveStats)]),
 }
 
 _lib = None
@@ -211,31 +225,42 @@ def _is64(t) -> int:
     raise ValueError("vectors must be float32 or float64")
 
 
+def make_config(degree: int, p_coarsening: bool = False, mg_fp32: bool = True, tile_cells: int = 0,
+                cheb_degree: int = 3, smoothing_range: float = 20.0, eig_steps: int = 12, eig_safety: float = 1.2,
+                cell_kernel: int = 0) -> Config:
+    cfg = Config()
+    _check(lib().gcmg_config_default(ctypes.byref(cfg)))
+    cfg.degree, cfg.p_coarsening, cfg.mg_fp32 = degree, int(p_coarsening), int(mg_fp32)
+    cfg.tile_cells, cfg.cheb_degree, cfg.smoothing_range = tile_cells, cheb_degree, smoothing_range
+    cfg.eig_steps, cfg.eig_safety, cfg.cell_kernel = eig_steps, eig_safety, cell_kernel
+    return cfg
+
+
 class Multigrid:
     """All levels of one problem on the current CUDA device, set up on the
     current torch stream."""
 
     def __init__(self, mesh: Mesh, degree: int, p_coarsening: bool = False, mg_fp32: bool = True,
                  tile_cells: int = 0, cheb_degree: int = 3, smoothing_range: float = 20.0,
-                 eig_steps: int = 12, eig_safety: float = 1.2):
+                 eig_steps: int = 12, eig_safety: float = 1.2, cell_kernel: int = 0, _handle=None, _owner=None):
         import torch
-        cfg = Config()
-        _check(lib().gcmg_config_default(ctypes.byref(cfg)))
-        cfg.degree, cfg.p_coarsening, cfg.mg_fp32 = degree, int(p_coarsening), int(mg_fp32)
-        cfg.tile_cells, cfg.cheb_degree, cfg.smoothing_range = tile_cells, cheb_degree, smoothing_range
-        cfg.eig_steps, cfg.eig_safety = eig_steps, eig_safety
         self.mesh = mesh
         self.stream = torch.cuda.current_stream()
-        h = _c_void_p()
-        _check(lib().gcmg_setup(mesh._p, ctypes.byref(cfg), _c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
-        self._h = h
+        if _handle is not None:  # a handle owned by a Batch
+            self._h, self._owned, self._owner = _handle, False, _owner
+        else:
+            cfg = make_config(degree, p_coarsening, mg_fp32, tile_cells, cheb_degree, smoothing_range, eig_steps,
+                              eig_safety, cell_kernel)
+            h = _c_void_p()
+            _check(lib().gcmg_setup(mesh._p, ctypes.byref(cfg), _c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+            self._h, self._owned = h, True
         self.num_levels = self._num_levels()
         self.info = [self.level_info(l) for l in range(self.num_levels)]
 
     def __del__(self):
-        if getattr(self, "_h", None) and _lib is not None:
+        if getattr(self, "_h", None) and getattr(self, "_owned", False) and _lib is not None:
             _lib.gcmg_destroy(self._h)
-            self._h = None
+        self._h = None
 
     def _num_levels(self) -> int:
         n = _c_int()
@@ -491,3 +516,67 @@ class MLP:
                                     _ptr(order, order.numel(), torch.int32), order.numel(), batch, float(lr),
                                     _ptr(losses), self._stream()))
         return losses[:steps]
+
+
+def point_values(xyz: np.ndarray, seed: int) -> np.ndarray:
+    """Position-keyed uniform values in [-1, 1) computed by the library."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    out = np.empty(len(xyz), dtype=np.float64)
+    _check(lib().gcmg_point_values(xyz.ctypes.data_as(_c_void_p), len(xyz), seed, out.ctypes.data_as(_c_void_p)))
+    return out
+
+
+def autotune(probe: Mesh, degree: int, mg_fp32: bool = True, reps: int = 20):
+    """(best, all candidates) of the operator autotuner for one degree."""
+    import torch
+    best = Tuning()
+    allc = (Tuning * 8)()
+    n = _c_int()
+    _check(lib().gcmg_autotune(probe._p, degree, int(mg_fp32), reps, _c_void_p(torch.cuda.current_stream().cuda_stream),
+                               ctypes.byref(best), allc, ctypes.byref(n)))
+    return best, [allc[i] for i in range(n.value)]
+
+
+class Batch:
+    """Independent problems set up together and solved by one graph launch."""
+
+    def __init__(self, meshes: Sequence[Mesh], configs: Sequence[Config], n_threads: int = 0):
+        import torch
+        n = len(meshes)
+        arr = (_c_void_p * n)(*[m._p for m in meshes])
+        cfgs = (Config * n)(*configs)
+        self.stream = torch.cuda.current_stream()
+        p = _c_void_p()
+        _check(lib().gcmg_batch_create(n, arr, cfgs, n_threads, _c_void_p(self.stream.cuda_stream), ctypes.byref(p)))
+        self._p = p
+        self.meshes = list(meshes)
+        self.problems = []
+        for i in range(n):
+            h = _c_void_p()
+            _check(lib().gcmg_batch_handle(p, i, ctypes.byref(h)))
+            self.problems.append(Multigrid(meshes[i], configs[i].degree, _handle=h, _owner=self))
+
+    def __del__(self):
+        if getattr(self, "_p", None) and _lib is not None:
+            for m in getattr(self, "problems", []):
+                m._h = None
+            _lib.gcmg_batch_destroy(self._p)
+            self._p = None
+
+    def __len__(self) -> int:
+        return len(self.problems)
+
+    def cg_solve(self, bs, xs, rtol: float = 1e-8, maxit: int = 100):
+        """CG to rtol for every problem in one graph launch; returns the per-problem stats."""
+        import torch
+        n = len(self.problems)
+        assert len(bs) == n and len(xs) == n
+        for m, b, x in zip(self.problems, bs, xs):
+            nf = m.n_free(m.finest)
+            _ptr(b, nf, torch.float64)
+            _ptr(x, nf, torch.float64)
+        barr = (_c_void_p * n)(*[b.data_ptr() if b.numel() else None for b in bs])
+        xarr = (_c_void_p * n)(*[x.data_ptr() if x.numel() else None for x in xs])
+        st = (SolveStats * n)()
+        _check(lib().gcmg_batch_cg_solve(self._p, barr, xarr, rtol, maxit, st))
+        return [st[i] for i in range(n)]

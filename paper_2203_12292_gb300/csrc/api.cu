@@ -6,15 +6,13 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
 
-#include "gcmg.h"
-#include "host.h"
-#include "internal.h"
-#include "kernels.h"
-#include "mlp_net.h"
+#include "handle.h"
+#include "splitmix.h"
 
 namespace gcmg {
 
@@ -24,102 +22,8 @@ void upload_tables_mlp();
 
 static std::atomic<long long> g_launches{0};
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_counter() { return g_launches.load(); }
 
-namespace {
-
-struct LevelDev {
-  LevelHost host;
-  bool fp32 = true;
-  DevBuf tiles, meta, foreign, subptr, perm, cell_ijk, gstart, own, mask;
-  DevBuf halo, halo_dofs, halo_ptr, halo_src;
-  DevBuf diag64, dinv64, dinv32;
-  DevBuf x, b, d, t;        // V-cycle vectors in level precision
-  DevBuf w64a, w64b, w64c;  // fp64 work vectors (set-up, fp64 smoothing through the API)
-  DevBuf w32a, w32b;        // fp32 work vectors (fp32 smoothing through the API)
-  CellLaunch cl{};
-  double lam = 1.0;
-  // learned smoother: kind, parameter copy, bf16 diagonal features per cell
-  int smoother = GCMG_SMOOTHER_CHEBYSHEV;
-  DevBuf mlp_image, dfeat;  // packed bf16 weights of the fused kernel
-  int64_t n() const { return host.n_free; }
-};
-
-struct TransferDev {
-  TransferHost host;
-  DevBuf fine_of, refined;
-  TransferLaunch tl{};
-};
-
-}  // namespace
-
-// CUDA-event timers per (level, stage): the per-level, per-stage profile of
-// a V-cycle (presmoothing, residual, restriction, coarse solve, prolongation,
-// postsmoothing) plus operator applications and CG vector work.
-struct Profiler {
-  bool on = false;
-  struct Rec {
-    cudaEvent_t a = nullptr, b = nullptr;
-    int level = 0, stage = 0;
-  };
-  std::vector<Rec> pool;
-  size_t used = 0;
-  std::vector<double> ms;
-  std::vector<int64_t> cnt;
-  int nlev = 0;
-  ~Profiler() {
-    for (auto& r : pool) {
-      if (r.a) cudaEventDestroy(r.a);
-      if (r.b) cudaEventDestroy(r.b);
-    }
-  }
-};
-constexpr int NSTAGE = 10;
-
-// CUDA graphs of the V-cycle and of the operator half of a CG iteration;
-// captured once per handle (re-captured when smoother parameters or the
-// profiling state change).  Timers captured into a graph are event-record
-// nodes, read after each replay.
-struct GraphRec {
-  cudaGraphExec_t exec = nullptr;
-  long long kernels = 0;  // kernel launches per replay
-  std::vector<Profiler::Rec> recs;
-  void reset() {
-    if (exec) cudaGraphExecDestroy(exec);
-    exec = nullptr;
-    for (auto& r : recs) {
-      if (r.a) cudaEventDestroy(r.a);
-      if (r.b) cudaEventDestroy(r.b);
-    }
-    recs.clear();
-  }
-  ~GraphRec() { reset(); }
-};
-
-struct Handle {
-  cudaStream_t stream = nullptr;
-  bool stop_after_cgc = false;  // finest level: return after the prolongation
-  cudaStream_t cap_stream = nullptr;
-  bool use_graphs = true;
-  GraphRec* capturing = nullptr;
-  GraphRec g_core, g_a;
-  Profiler prof;
-  gcmg_config cfg{};
-  std::vector<std::unique_ptr<LevelDev>> lev;
-  std::vector<std::unique_ptr<TransferDev>> tr;  // tr[l]: between levels l and l-1
-  DevBuf diag_tab[KMAX + 1];
-  DevBuf Ainv;
-  int n0 = 0;
-  DevBuf scratch, scal, modes;
-  DevBuf cg_r, cg_p, cg_q, cg_z, cg_x;
-  DevBuf mlp_scratch;  // weight image of gcmg_mlp_correct calls
-  ~Handle() {
-    g_core.reset();
-    g_a.reset();
-    if (cap_stream) cudaStreamDestroy(cap_stream);
-  }
-};
-
-namespace {
 
 int default_tile_cells(int) { return 64; }
 
@@ -194,7 +98,7 @@ void prof_graph(Handle& H, GraphRec& g) {
   }
 }
 
-void vmult(Handle& H, int l, bool fp64, const void* src, void* dst, int stage = GCMG_STAGE_VMULT) {
+void vmult(Handle& H, int l, bool fp64, const void* src, void* dst, int stage) {
   LevelDev& L = *H.lev[l];
   if (L.n() == 0) return;
   const int r = prof_begin(H, l, stage);
@@ -251,7 +155,13 @@ double estimate_lambda(Handle& H, int l) {
   double* p = L.w64b.as<double>();
   double* q = L.w64c.as<double>();
   double* z = L.w64c.as<double>();  // z and q are never live together
-  launch_fill(r, 1.0, n, H.stream);
+  {  // start vector: all ones plus a seeded position-keyed perturbation
+    std::vector<double> s0(n);
+    const double* xyz = L.host.dof_xyz_cache.data();
+    for (int64_t i = 0; i < n; ++i) s0[i] = 1.0 + point_value(xyz + 3 * i, LANCZOS_START_SEED);
+    ck(cudaMemcpyAsync(r, s0.data(), n * sizeof(double), cudaMemcpyHostToDevice, H.stream), "upload");
+    ck(cudaStreamSynchronize(H.stream), "upload");  // s0 is freed on return
+  }
   launch_pmul(z, L.dinv64.as<double>(), r, n, H.stream);
   ck(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
   double rz = dot_host(H, r, z, n);
@@ -525,17 +435,160 @@ void vcycle(Handle& H, const double* b, double* x) {
 }
 
 
-}  // namespace
+void check_config(const gcmg_config* cfg) {
+  if (cfg->degree < 1 || cfg->degree > KMAX) throw Error(GCMG_ERR_ARG, "degree must be 1..4");
+  if (cfg->cheb_degree < 1 || !(cfg->smoothing_range > 1.0) || cfg->eig_steps < 1)
+    throw Error(GCMG_ERR_ARG, "bad smoother parameters");
+  if (cfg->tile_cells < 0 || cfg->tile_cells > 255) throw Error(GCMG_ERR_ARG, "tile_cells must be 0..255");
+  if (cfg->cell_kernel < 0 || cfg->cell_kernel > 1) throw Error(GCMG_ERR_ARG, "cell_kernel must be 0 or 1");
+}
+
+// the per-degree constant tables of every translation unit, once per device
+void upload_all_tables() {
+  static std::mutex mu;
+  static std::vector<char> done;
+  int dev = 0;
+  ck(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(mu);
+  if ((int)done.size() <= dev) done.resize(dev + 1, 0);
+  if (done[dev]) return;
+  upload_tables_cell();
+  upload_tables_transfer();
+  upload_tables_mlp();
+  ck(cudaDeviceSynchronize(), "upload tables");
+  done[dev] = 1;
+}
+
+void setup_handle(Handle& H, const std::vector<Octree>& meshes, int lmax, const gcmg_config& cfg) {
+  H.cfg = cfg;
+  // level list: (mesh index, degree), coarsest first
+  std::vector<std::pair<int, int>> spec;
+  const int nm = (int)meshes.size();
+  if (cfg.p_coarsening) {
+    for (int m = 0; m + 1 < nm; ++m) spec.push_back({m, 1});
+    std::vector<int> degs{cfg.degree};
+    while (degs.back() > 1) degs.push_back(degs.back() / 2);
+    for (auto it = degs.rbegin(); it != degs.rend(); ++it) spec.push_back({nm - 1, *it});
+  } else {
+    for (int m = 0; m < nm; ++m) spec.push_back({m, cfg.degree});
+  }
+  const int nl = (int)spec.size();
+  for (int l = 0; l < nl; ++l) {
+    auto L = std::make_unique<LevelDev>();
+    const int k = spec[l].second;
+    const int tc = cfg.tile_cells ? cfg.tile_cells : default_tile_cells(k);
+    build_level(meshes[spec[l].first], k, tc, lmax, L->host);
+    L->fp32 = cfg.mg_fp32 != 0;
+    L->cl.use_lines = cfg.cell_kernel == 1;
+    LevelHost& lh = L->host;
+    L->tiles.upload(lh.tiles, H.stream);
+    L->halo.alloc(lh.foreign.size() * sizeof(double));
+    L->halo_dofs.upload(lh.halo_dofs, H.stream);
+    L->halo_ptr.upload(lh.halo_ptr, H.stream);
+    L->halo_src.upload(lh.halo_src, H.stream);
+    L->meta.upload(lh.meta, H.stream);
+    L->foreign.upload(lh.foreign, H.stream);
+    L->subptr.upload(lh.subptr, H.stream);
+    L->perm.upload(lh.perm, H.stream);
+    std::vector<int32_t> ijk(lh.cells.size() * 3);
+    for (size_t c = 0; c < lh.cells.size(); ++c) {
+      ijk[3 * c] = lh.cells[c].i;
+      ijk[3 * c + 1] = lh.cells[c].j;
+      ijk[3 * c + 2] = lh.cells[c].k;
+    }
+    L->cell_ijk.upload(ijk, H.stream);
+    L->gstart.upload(lh.gstart, H.stream);
+    L->own.upload(lh.own, H.stream);
+    L->mask.upload(lh.mask, H.stream);
+    CellLaunch& c = L->cl;
+    c.tiles = L->tiles.as<TileInfo>();
+    c.n_tiles = (int)lh.tiles.size();
+    c.halo = L->halo.p;
+    c.halo_dofs = L->halo_dofs.as<int32_t>();
+    c.halo_ptr = L->halo_ptr.as<int32_t>();
+    c.halo_src = L->halo_src.as<int32_t>();
+    c.n_halo = (int)lh.halo_dofs.size();
+    c.meta = L->meta.as<CellMeta>();
+    c.foreign = L->foreign.as<int32_t>();
+    c.subptr = L->subptr.as<uint16_t>();
+    c.perm = L->perm.as<uint8_t>();
+    c.cell_ijk = L->cell_ijk.as<int32_t>();
+    c.k = k;
+    c.tc = tc;
+    c.max_local = lh.max_local;
+    c.lo = lh.lo;
+    c.dom = lh.hi - lh.lo;
+    const int64_t n = lh.n_free;
+    const size_t vb = L->fp32 ? sizeof(float) : sizeof(double);
+    L->x.alloc(n * vb);
+    L->b.alloc(n * vb);
+    L->d.alloc(n * vb);
+    L->t.alloc(n * vb);
+    L->w64a.alloc(n * sizeof(double));
+    L->w64b.alloc(n * sizeof(double));
+    L->w64c.alloc(n * sizeof(double));
+    L->w32a.alloc(n * sizeof(float));
+    L->w32b.alloc(n * sizeof(float));
+    L->diag64.alloc(n * sizeof(double));
+    L->dinv64.alloc(n * sizeof(double));
+    L->dinv32.alloc(n * sizeof(float));
+    H.lev.push_back(std::move(L));
+  }
+  H.tr.resize(nl);
+  for (int l = 1; l < nl; ++l) {
+    auto T = std::make_unique<TransferDev>();
+    LevelHost& fh = H.lev[l]->host;
+    LevelHost& ch = H.lev[l - 1]->host;
+    if (spec[l].first == spec[l - 1].first)
+      build_transfer_p(fh, ch, T->host);
+    else
+      build_transfer_h(fh, ch, T->host);
+    T->fine_of.upload(T->host.fine_of, H.stream);
+    T->refined.upload(T->host.refined, H.stream);
+    TransferLaunch& t = T->tl;
+    t.kind = T->host.kind;
+    t.kf = fh.k;
+    t.kc = ch.k;
+    t.n_coarse = (int)ch.cells.size();
+    t.fine_of = T->fine_of.as<int32_t>();
+    t.refined = T->refined.as<uint8_t>();
+    t.gstart_f = H.lev[l]->gstart.as<int32_t>();
+    t.own_f = H.lev[l]->own.as<uint32_t>();
+    t.gstart_c = H.lev[l - 1]->gstart.as<int32_t>();
+    t.mask_c = H.lev[l - 1]->mask.as<uint16_t>();
+    t.coarse = H.lev[l - 1]->cl;
+    H.tr[l] = std::move(T);
+  }
+  H.scratch.alloc(DOT_BLOCKS * sizeof(double));
+  H.scal.alloc(16 * sizeof(double));
+  ck(cudaMemsetAsync(H.scal.p, 0, 16 * sizeof(double), H.stream), "memset");
+  // Jacobi diagonals (Eqs. 3-4)
+  for (int l = 0; l < nl; ++l) {
+    const int k = spec[l].second;
+    if (!H.diag_tab[k].p) {
+      const int n3 = (k + 1) * (k + 1) * (k + 1);
+      H.diag_tab[k].alloc((size_t)512 * n3 * sizeof(double));
+      launch_diag_table(k, H.diag_tab[k].as<double>(), H.stream);
+    }
+    LevelDev& L = *H.lev[l];
+    if (L.n() == 0) continue;
+    launch_diag(L.cl, H.diag_tab[k].as<double>(), L.diag64.as<double>(), H.stream);
+    launch_invert(L.diag64.as<double>(), L.dinv64.as<double>(), L.dinv32.as<float>(), L.n(), H.stream);
+  }
+  ck(cudaGetLastError(), "diagonal");
+  setup_coarse(H);
+  for (int l = 1; l < nl; ++l) H.lev[l]->lam = cfg.eig_safety * estimate_lambda(H, l);
+  const int64_t nf = H.lev.back()->n();
+  H.cg_r.alloc(nf * sizeof(double));
+  H.cg_p.alloc(nf * sizeof(double));
+  H.cg_q.alloc(nf * sizeof(double));
+  H.cg_z.alloc(nf * sizeof(double));
+  H.cg_x.alloc(nf * sizeof(double));
+  ck(cudaStreamSynchronize(H.stream), "setup");
+  ck(cudaGetLastError(), "setup");
+}
+
 }  // namespace gcmg
-
-struct gcmg_mesh {
-  std::vector<gcmg::Octree> levels;  // coarsest (one cell) first
-  int lmax = 0;
-};
-
-struct gcmg_handle {
-  gcmg::Handle h;
-};
 
 using namespace gcmg;
 
@@ -621,150 +674,18 @@ int gcmg_config_default(gcmg_config* cfg) {
     cfg->eig_steps = 12;
     cfg->eig_safety = 1.2;
     cfg->tile_cells = 0;
+    cfg->cell_kernel = 0;
   });
 }
 
 int gcmg_setup(const gcmg_mesh* mesh, const gcmg_config* cfg, void* stream, gcmg_handle** out) {
   return guarded([&] {
     if (!mesh || !cfg || !out) throw Error(GCMG_ERR_ARG, "null argument");
-    if (cfg->degree < 1 || cfg->degree > KMAX) throw Error(GCMG_ERR_ARG, "degree must be 1..4");
-    if (cfg->cheb_degree < 1 || !(cfg->smoothing_range > 1.0) || cfg->eig_steps < 1)
-      throw Error(GCMG_ERR_ARG, "bad smoother parameters");
-    if (cfg->tile_cells < 0 || cfg->tile_cells > 255) throw Error(GCMG_ERR_ARG, "tile_cells must be 0..255");
-    int dev = 0;
-    ck(cudaGetDevice(&dev), "cudaGetDevice");
+    check_config(cfg);
+    upload_all_tables();
     auto hh = std::make_unique<gcmg_handle>();
-    Handle& H = hh->h;
-    H.stream = static_cast<cudaStream_t>(stream);
-    H.cfg = *cfg;
-    upload_tables_cell();
-    upload_tables_transfer();
-    upload_tables_mlp();
-    ck(cudaGetLastError(), "upload tables");
-    // level list: (mesh index, degree), coarsest first
-    std::vector<std::pair<int, int>> spec;
-    const int nm = (int)mesh->levels.size();
-    if (cfg->p_coarsening) {
-      for (int m = 0; m + 1 < nm; ++m) spec.push_back({m, 1});
-      std::vector<int> degs{cfg->degree};
-      while (degs.back() > 1) degs.push_back(degs.back() / 2);
-      for (auto it = degs.rbegin(); it != degs.rend(); ++it) spec.push_back({nm - 1, *it});
-    } else {
-      for (int m = 0; m < nm; ++m) spec.push_back({m, cfg->degree});
-    }
-    const int nl = (int)spec.size();
-    for (int l = 0; l < nl; ++l) {
-      auto L = std::make_unique<LevelDev>();
-      const int k = spec[l].second;
-      const int tc = cfg->tile_cells ? cfg->tile_cells : default_tile_cells(k);
-      build_level(mesh->levels[spec[l].first], k, tc, mesh->lmax, L->host);
-      L->fp32 = cfg->mg_fp32 != 0;
-      LevelHost& lh = L->host;
-      L->tiles.upload(lh.tiles, H.stream);
-      L->halo.alloc(lh.foreign.size() * sizeof(double));
-      L->halo_dofs.upload(lh.halo_dofs, H.stream);
-      L->halo_ptr.upload(lh.halo_ptr, H.stream);
-      L->halo_src.upload(lh.halo_src, H.stream);
-      L->meta.upload(lh.meta, H.stream);
-      L->foreign.upload(lh.foreign, H.stream);
-      L->subptr.upload(lh.subptr, H.stream);
-      L->perm.upload(lh.perm, H.stream);
-      std::vector<int32_t> ijk(lh.cells.size() * 3);
-      for (size_t c = 0; c < lh.cells.size(); ++c) {
-        ijk[3 * c] = lh.cells[c].i;
-        ijk[3 * c + 1] = lh.cells[c].j;
-        ijk[3 * c + 2] = lh.cells[c].k;
-      }
-      L->cell_ijk.upload(ijk, H.stream);
-      L->gstart.upload(lh.gstart, H.stream);
-      L->own.upload(lh.own, H.stream);
-      L->mask.upload(lh.mask, H.stream);
-      CellLaunch& c = L->cl;
-      c.tiles = L->tiles.as<TileInfo>();
-      c.n_tiles = (int)lh.tiles.size();
-      c.halo = L->halo.p;
-      c.halo_dofs = L->halo_dofs.as<int32_t>();
-      c.halo_ptr = L->halo_ptr.as<int32_t>();
-      c.halo_src = L->halo_src.as<int32_t>();
-      c.n_halo = (int)lh.halo_dofs.size();
-      c.meta = L->meta.as<CellMeta>();
-      c.foreign = L->foreign.as<int32_t>();
-      c.subptr = L->subptr.as<uint16_t>();
-      c.perm = L->perm.as<uint8_t>();
-      c.cell_ijk = L->cell_ijk.as<int32_t>();
-      c.k = k;
-      c.tc = tc;
-      c.max_local = lh.max_local;
-      c.lo = lh.lo;
-      c.dom = lh.hi - lh.lo;
-      const int64_t n = lh.n_free;
-      const size_t vb = L->fp32 ? sizeof(float) : sizeof(double);
-      L->x.alloc(n * vb);
-      L->b.alloc(n * vb);
-      L->d.alloc(n * vb);
-      L->t.alloc(n * vb);
-      L->w64a.alloc(n * sizeof(double));
-      L->w64b.alloc(n * sizeof(double));
-      L->w64c.alloc(n * sizeof(double));
-      L->w32a.alloc(n * sizeof(float));
-      L->w32b.alloc(n * sizeof(float));
-      L->diag64.alloc(n * sizeof(double));
-      L->dinv64.alloc(n * sizeof(double));
-      L->dinv32.alloc(n * sizeof(float));
-      H.lev.push_back(std::move(L));
-    }
-    H.tr.resize(nl);
-    for (int l = 1; l < nl; ++l) {
-      auto T = std::make_unique<TransferDev>();
-      LevelHost& fh = H.lev[l]->host;
-      LevelHost& ch = H.lev[l - 1]->host;
-      if (spec[l].first == spec[l - 1].first)
-        build_transfer_p(fh, ch, T->host);
-      else
-        build_transfer_h(fh, ch, T->host);
-      T->fine_of.upload(T->host.fine_of, H.stream);
-      T->refined.upload(T->host.refined, H.stream);
-      TransferLaunch& t = T->tl;
-      t.kind = T->host.kind;
-      t.kf = fh.k;
-      t.kc = ch.k;
-      t.n_coarse = (int)ch.cells.size();
-      t.fine_of = T->fine_of.as<int32_t>();
-      t.refined = T->refined.as<uint8_t>();
-      t.gstart_f = H.lev[l]->gstart.as<int32_t>();
-      t.own_f = H.lev[l]->own.as<uint32_t>();
-      t.gstart_c = H.lev[l - 1]->gstart.as<int32_t>();
-      t.mask_c = H.lev[l - 1]->mask.as<uint16_t>();
-      t.coarse = H.lev[l - 1]->cl;
-      H.tr[l] = std::move(T);
-    }
-    H.scratch.alloc(DOT_BLOCKS * sizeof(double));
-    H.scal.alloc(16 * sizeof(double));
-    ck(cudaMemsetAsync(H.scal.p, 0, 16 * sizeof(double), H.stream), "memset");
-    // Jacobi diagonals (Eqs. 3-4)
-    for (int l = 0; l < nl; ++l) {
-      const int k = spec[l].second;
-      if (!H.diag_tab[k].p) {
-        const int n3 = (k + 1) * (k + 1) * (k + 1);
-        H.diag_tab[k].alloc((size_t)512 * n3 * sizeof(double));
-        launch_diag_table(k, H.diag_tab[k].as<double>(), H.stream);
-      }
-      LevelDev& L = *H.lev[l];
-      if (L.n() == 0) continue;
-      launch_diag(L.cl, H.diag_tab[k].as<double>(), L.diag64.as<double>(), H.stream);
-      launch_invert(L.diag64.as<double>(), L.dinv64.as<double>(), L.dinv32.as<float>(), L.n(), H.stream);
-    }
-    ck(cudaGetLastError(), "diagonal");
-    setup_coarse(H);
-    for (int l = 1; l < nl; ++l) H.lev[l]->lam = cfg->eig_safety * estimate_lambda(H, l);
-    const int64_t nf = H.lev.back()->n();
-    H.cg_r.alloc(nf * sizeof(double));
-    H.cg_p.alloc(nf * sizeof(double));
-    H.cg_q.alloc(nf * sizeof(double));
-    H.cg_z.alloc(nf * sizeof(double));
-    H.cg_x.alloc(nf * sizeof(double));
-    ck(cudaStreamSynchronize(H.stream), "setup");
-    ck(cudaGetLastError(), "setup");
+    hh->h.stream = static_cast<cudaStream_t>(stream);
+    setup_handle(hh->h, mesh->levels, mesh->lmax, *cfg);
     *out = hh.release();
   });
 }
@@ -1234,6 +1155,13 @@ int gcmg_set_smoother(gcmg_handle* h, int level, int kind, const gcmg_mlp* net) 
     }
     L.smoother = kind;
     H.g_core.reset();
+  });
+}
+
+int gcmg_point_values(const double* xyz, int64_t n, uint64_t seed, double* out) {
+  return guarded([&] {
+    if (n < 0 || (n && (!xyz || !out))) throw Error(GCMG_ERR_ARG, "bad arguments");
+    for (int64_t i = 0; i < n; ++i) out[i] = point_value(xyz + 3 * i, seed);
   });
 }
 

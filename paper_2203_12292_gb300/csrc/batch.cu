@@ -1,0 +1,368 @@
+// Batches of independent Poisson problems solved by one CUDA-graph launch,
+// and the autotuner of the operator's tile size and thread mapping per
+// polynomial degree.  The paper solves one problem per run; batching many
+// uneven problems on one GPU is an extension.
+//
+// Every problem keeps its own handle (levels, transfers, vectors).  One
+// graph holds, for every problem, the CG prologue, a conditional WHILE node
+// whose body is one CG iteration (V-cycle, beta, p update, operator, alpha,
+// x/r update, convergence check), and an epilogue; the check kernel of each
+// iteration sets the node's condition on the device, so the whole batch
+// runs to convergence without a host round trip.  Problems are independent
+// branches of the graph and run concurrently.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "handle.h"
+
+struct gcmg_batch {
+  std::vector<std::unique_ptr<gcmg_handle>> probs;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // the graph is specific to its arguments
+  std::vector<const double*> key_b;
+  std::vector<double*> key_x;
+  double key_rtol = -1.0;
+  int key_maxit = -1;
+  gcmg::DevBuf stats;  // per problem: iterations, rr, |b|^2, status
+  std::vector<long long> pro_kernels, body_kernels;
+  ~gcmg_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+namespace gcmg {
+
+long long launch_counter();
+
+namespace {
+
+struct CgVecs {
+  int64_t n;
+  double *x, *r, *p, *q, *z, *S, *scratch;
+};
+
+CgVecs vecs(Handle& H) {
+  const int top = (int)H.lev.size() - 1;
+  return CgVecs{H.lev[top]->n(),        H.cg_x.as<double>(), H.cg_r.as<double>(), H.cg_p.as<double>(),
+                H.cg_q.as<double>(),    H.cg_z.as<double>(), H.scal.as<double>(), H.scratch.as<double>()};
+}
+
+// V-cycle of Algorithms 1-2 as plain kernel launches (captured by the caller)
+void vcycle_kernels(Handle& H, const double* b, double* x) {
+  const int top = (int)H.lev.size() - 1;
+  LevelDev& F = *H.lev[top];
+  if (F.fp32)
+    launch_cast(false, b, F.b.p, F.n(), H.stream);
+  else
+    launch_copy(b, F.b.as<double>(), F.n(), H.stream);
+  vcycle_level(H, top);
+  if (F.fp32)
+    launch_cast(true, F.x.p, x, F.n(), H.stream);
+  else
+    launch_copy(F.x.as<double>(), x, F.n(), H.stream);
+}
+
+// q = A p, alpha = rz / pq, x += alpha p, r -= alpha q, rr
+void op_half(Handle& H, const CgVecs& v) {
+  vmult(H, (int)H.lev.size() - 1, true, v.p, v.q, GCMG_STAGE_CG_VMULT);
+  launch_dot(v.p, v.q, v.n, v.scratch, v.S, 0, DOT_ALPHA, H.stream);
+  launch_cg_update_xr(v.x, v.r, v.p, v.q, v.S, v.n, v.scratch, v.S, H.stream);
+}
+
+void cg_prologue(Handle& H, const double* b, double rtol2, int maxit, cudaGraphConditionalHandle hc) {
+  const CgVecs v = vecs(H);
+  launch_zero(true, v.x, v.n, H.stream);
+  launch_copy(b, v.r, v.n, H.stream);
+  launch_dot(v.r, v.r, v.n, v.scratch, v.S, 7, DOT_STORE, H.stream);
+  launch_scalar_set(v.S, 8, 0.0, H.stream);
+  vcycle_kernels(H, v.r, v.z);
+  launch_dot(v.r, v.z, v.n, v.scratch, v.S, 0, DOT_STORE, H.stream);
+  launch_copy(v.z, v.p, v.n, H.stream);
+  op_half(H, v);
+  launch_cg_check(hc, v.S, maxit, rtol2, H.stream);
+}
+
+void cg_body(Handle& H, double rtol2, int maxit, cudaGraphConditionalHandle hc) {
+  const CgVecs v = vecs(H);
+  const bool flexible = any_learned(H);
+  if (flexible) launch_dot(v.r, v.z, v.n, v.scratch, v.S, 6, DOT_STORE, H.stream);
+  vcycle_kernels(H, v.r, v.z);
+  launch_dot(v.r, v.z, v.n, v.scratch, v.S, 0, flexible ? DOT_BETA_FLEX : DOT_BETA, H.stream);
+  launch_cg_update_p(v.p, v.z, v.S, v.n, H.stream);
+  op_half(H, v);
+  launch_cg_check(hc, v.S, maxit, rtol2, H.stream);
+}
+
+// capture of launches on stream cs; returns the number of kernels recorded
+template <typename F>
+long long record(Handle& H, cudaStream_t cs, F&& body) {
+  cudaStream_t saved = H.stream;
+  const bool prof = H.prof.on;
+  H.stream = cs;
+  H.prof.on = false;  // event nodes are not allowed inside conditional bodies
+  const long long before = launch_counter();
+  try {
+    body();
+  } catch (...) {
+    H.stream = saved;
+    H.prof.on = prof;
+    throw;
+  }
+  H.stream = saved;
+  H.prof.on = prof;
+  const long long k = launch_counter() - before;
+  note_launches((int)-k);  // recorded, not run
+  return k;
+}
+
+void build_graph(gcmg_batch& B, const double* const* b, double* const* x, double rtol, int maxit) {
+  if (B.exec) cudaGraphExecDestroy(B.exec);
+  B.exec = nullptr;
+  const int np = (int)B.probs.size();
+  const double rtol2 = rtol * rtol;
+  cudaStream_t cs = B.cap;
+  cudaGraph_t G = nullptr;
+  ck(cudaGraphCreate(&G, 0), "graph create");
+  B.pro_kernels.assign(np, 0);
+  B.body_kernels.assign(np, 0);
+  double* stats = B.stats.as<double>();
+  try {
+    for (int i = 0; i < np; ++i) {
+      Handle& H = B.probs[i]->h;
+      const CgVecs v = vecs(H);
+      cudaGraph_t body = nullptr;
+      cudaGraphConditionalHandle hc = 0;
+      ck(cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed), "capture");
+      if (v.n == 0) {
+        B.pro_kernels[i] = record(H, cs, [&] {
+          launch_scalar_set(v.S, 7, 0.0, cs);
+          launch_scalar_set(v.S, 8, 0.0, cs);
+          launch_cg_stats(v.S, rtol2, stats + 4 * i, cs);
+        });
+      } else {
+        ck(cudaGraphConditionalHandleCreate(&hc, G, 0, 0), "conditional handle");
+        B.pro_kernels[i] = record(H, cs, [&] { cg_prologue(H, b[i], rtol2, maxit, hc); });
+        // the WHILE node after the prologue, then the epilogue after it
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* edges = nullptr;
+        size_t nd = 0;
+        ck(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &deps, &edges, &nd), "capture info");
+        cudaGraphNodeParams prm = {};
+        prm.type = cudaGraphNodeTypeConditional;
+        prm.conditional.handle = hc;
+        prm.conditional.type = cudaGraphCondTypeWhile;
+        prm.conditional.size = 1;
+        cudaGraphNode_t wn;
+        ck(cudaGraphAddNode(&wn, G, deps, edges, nd, &prm), "while node");
+        body = prm.conditional.phGraph_out[0];
+        ck(cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies),
+           "capture dependencies");
+        B.pro_kernels[i] += record(H, cs, [&] {
+          launch_copy(v.x, x[i], v.n, cs);
+          launch_cg_stats(v.S, rtol2, stats + 4 * i, cs);
+        });
+      }
+      cudaGraph_t g_out = nullptr;
+      ck(cudaStreamEndCapture(cs, &g_out), "end capture");
+      if (body) {
+        ck(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed), "capture");
+        B.body_kernels[i] = record(H, cs, [&] { cg_body(H, rtol2, maxit, hc); });
+        ck(cudaStreamEndCapture(cs, &g_out), "end capture");
+      }
+    }
+  } catch (...) {
+    cudaStreamCaptureStatus st;
+    if (cudaStreamIsCapturing(cs, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(cs, &g);
+    }
+    cudaGraphDestroy(G);
+    throw;
+  }
+  const cudaError_t e = cudaGraphInstantiate(&B.exec, G, 0);
+  cudaGraphDestroy(G);
+  ck(e, "graph instantiate");
+}
+
+// fp32 (or fp64) operator of the finest level: GDoF/s over `reps` applications
+double time_vmult(Handle& H, bool fp64, int reps) {
+  const int top = (int)H.lev.size() - 1;
+  LevelDev& F = *H.lev[top];
+  const int64_t n = F.n();
+  if (n == 0) return 0.0;
+  DevBuf x, y;
+  x.alloc(n * (fp64 ? 8 : 4));
+  y.alloc(n * (fp64 ? 8 : 4));
+  ck(cudaMemsetAsync(x.p, 0, x.bytes, H.stream), "memset");
+  for (int i = 0; i < 3; ++i) vmult(H, top, fp64, x.p, y.p);
+  cudaEvent_t a, b;
+  ck(cudaEventCreate(&a), "event");
+  ck(cudaEventCreate(&b), "event");
+  ck(cudaEventRecord(a, H.stream), "event");
+  for (int i = 0; i < reps; ++i) vmult(H, top, fp64, x.p, y.p);
+  ck(cudaEventRecord(b, H.stream), "event");
+  ck(cudaEventSynchronize(b), "event");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return (double)n * reps / (ms * 1e6);
+}
+
+}  // namespace
+}  // namespace gcmg
+
+using namespace gcmg;
+
+extern "C" {
+
+int gcmg_autotune(const gcmg_mesh* probe, int degree, int mg_fp32, int reps, void* stream, gcmg_tuning* best,
+                  gcmg_tuning* all, int* n_all) {
+  return guarded([&] {
+    if (!probe || !best || degree < 1 || degree > KMAX || reps < 1) throw Error(GCMG_ERR_ARG, "bad arguments");
+    upload_all_tables();
+    // candidates: tile size x thread mapping (the slab mapping needs tiles of <= 64 cells)
+    const int cand[5][2] = {{32, 0}, {64, 0}, {32, 1}, {64, 1}, {128, 1}};
+    const int nc = mg_fp32 ? 5 : 3;  // fp64 always runs the line-parallel kernel
+    const int (*list)[2] = mg_fp32 ? cand : cand + 2;
+    gcmg_tuning top{degree, 0, 0, -1.0};
+    for (int c = 0; c < nc; ++c) {
+      gcmg_config cfg;
+      gcmg_config_default(&cfg);
+      cfg.degree = degree;
+      cfg.mg_fp32 = mg_fp32;
+      cfg.tile_cells = list[c][0];
+      cfg.cell_kernel = list[c][1];
+      Handle H;
+      H.stream = static_cast<cudaStream_t>(stream);
+      setup_handle(H, probe->levels, probe->lmax, cfg);
+      const gcmg_tuning t{degree, cfg.tile_cells, cfg.cell_kernel, time_vmult(H, mg_fp32 == 0, reps)};
+      if (all) all[c] = t;
+      if (t.gdofs > top.gdofs) top = t;
+    }
+    if (n_all) *n_all = nc;
+    *best = top;
+  });
+}
+
+int gcmg_batch_create(int n, const gcmg_mesh* const* meshes, const gcmg_config* cfgs, int n_threads, void* stream,
+                      gcmg_batch** out) {
+  return guarded([&] {
+    if (n <= 0 || !meshes || !cfgs || !out) throw Error(GCMG_ERR_ARG, "bad arguments");
+    for (int i = 0; i < n; ++i) {
+      if (!meshes[i]) throw Error(GCMG_ERR_ARG, "null mesh");
+      check_config(&cfgs[i]);
+    }
+    upload_all_tables();
+    int dev = 0;
+    ck(cudaGetDevice(&dev), "cudaGetDevice");
+    auto B = std::make_unique<gcmg_batch>();
+    B->stream = static_cast<cudaStream_t>(stream);
+    B->probs.resize(n);
+    const int nt = std::max(1, std::min(n_threads > 0 ? n_threads : 16, n));
+    std::atomic<int> next{0};
+    std::vector<int> codes(nt, GCMG_OK);
+    std::vector<std::string> msgs(nt);
+    // host set-up of the problems in parallel; every worker queues its device
+    // work on a stream of its own
+    auto worker = [&](int t) {
+      cudaStream_t s = nullptr;
+      try {
+        ck(cudaSetDevice(dev), "cudaSetDevice");
+        ck(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "stream");
+        for (int i; (i = next.fetch_add(1)) < n;) {
+          auto h = std::make_unique<gcmg_handle>();
+          h->h.stream = s;
+          setup_handle(h->h, meshes[i]->levels, meshes[i]->lmax, cfgs[i]);
+          B->probs[i] = std::move(h);
+        }
+        ck(cudaStreamSynchronize(s), "setup");
+      } catch (const Error& e) {
+        codes[t] = e.code;
+        msgs[t] = e.what();
+        next.store(n);
+      } catch (const std::exception& e) {
+        codes[t] = GCMG_ERR_INTERNAL;
+        msgs[t] = e.what();
+        next.store(n);
+      }
+      if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(worker, t);
+    worker(0);
+    for (auto& t : th) t.join();
+    for (int t = 0; t < nt; ++t)
+      if (codes[t] != GCMG_OK) throw Error(codes[t], msgs[t]);
+    for (auto& h : B->probs) h->h.stream = B->stream;
+    ck(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking), "stream");
+    B->stats.alloc((size_t)n * 4 * sizeof(double));
+    *out = B.release();
+  });
+}
+
+void gcmg_batch_destroy(gcmg_batch* b) { delete b; }
+
+int gcmg_batch_size(const gcmg_batch* b, int* n) {
+  return guarded([&] {
+    if (!b || !n) throw Error(GCMG_ERR_ARG, "null argument");
+    *n = (int)b->probs.size();
+  });
+}
+
+int gcmg_batch_handle(gcmg_batch* b, int i, gcmg_handle** h) {
+  return guarded([&] {
+    if (!b || !h || i < 0 || i >= (int)b->probs.size()) throw Error(GCMG_ERR_ARG, "bad arguments");
+    *h = b->probs[i].get();
+  });
+}
+
+int gcmg_batch_cg_solve(gcmg_batch* b, const double* const* rhs, double* const* x, double rtol, int maxit,
+                        gcmg_solve_stats* stats) {
+  return guarded([&] {
+    if (!b || !rhs || !x || !(rtol > 0) || maxit < 1) throw Error(GCMG_ERR_ARG, "bad arguments");
+    const int np = (int)b->probs.size();
+    for (int i = 0; i < np; ++i) {
+      if (b->probs[i]->h.lev.back()->n() && (!rhs[i] || !x[i])) throw Error(GCMG_ERR_ARG, "bad vectors");
+      b->probs[i]->h.stream = b->stream;
+    }
+    const bool same = b->exec && b->key_rtol == rtol && b->key_maxit == maxit &&
+                      std::equal(b->key_b.begin(), b->key_b.end(), rhs) && std::equal(b->key_x.begin(), b->key_x.end(), x);
+    if (!same) {
+      build_graph(*b, rhs, x, rtol, maxit);
+      b->key_b.assign(rhs, rhs + np);
+      b->key_x.assign(x, x + np);
+      b->key_rtol = rtol;
+      b->key_maxit = maxit;
+    }
+    ck(cudaGraphLaunch(b->exec, b->stream), "graph launch");
+    std::vector<double> h((size_t)np * 4);
+    ck(cudaMemcpyAsync(h.data(), b->stats.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "stats");
+    ck(cudaStreamSynchronize(b->stream), "batch solve");
+    long long kernels = 0;
+    for (int i = 0; i < np; ++i) {
+      const int it = (int)h[4 * i];
+      kernels += b->pro_kernels[i] + (it > 1 ? (long long)(it - 1) * b->body_kernels[i] : 0);
+      if (stats) {
+        const double nb2 = h[4 * i + 2];
+        stats[i] = gcmg_solve_stats{it, std::sqrt(nb2), nb2 > 0 ? std::sqrt(h[4 * i + 1] / nb2) : 0.0,
+                                    (int)h[4 * i + 3]};
+      }
+    }
+    note_launches((int)std::min<long long>(kernels, 1LL << 30));
+  });
+}
+
+}  // extern "C"

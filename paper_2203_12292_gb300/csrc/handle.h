@@ -1,0 +1,128 @@
+// Internal state of a libgcmg handle (levels, transfers, timers, graphs)
+// and the orchestration steps shared by the C ABI translation units.
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include "gcmg.h"
+#include "host.h"
+#include "internal.h"
+#include "kernels.h"
+#include "mlp_net.h"
+
+namespace gcmg {
+
+struct LevelDev {
+  LevelHost host;
+  bool fp32 = true;
+  DevBuf tiles, meta, foreign, subptr, perm, cell_ijk, gstart, own, mask;
+  DevBuf halo, halo_dofs, halo_ptr, halo_src;
+  DevBuf diag64, dinv64, dinv32;
+  DevBuf x, b, d, t;        // V-cycle vectors in level precision
+  DevBuf w64a, w64b, w64c;  // fp64 work vectors (set-up, fp64 smoothing through the API)
+  DevBuf w32a, w32b;        // fp32 work vectors (fp32 smoothing through the API)
+  CellLaunch cl{};
+  double lam = 1.0;
+  // learned smoother: kind, parameter copy, bf16 diagonal features per cell
+  int smoother = GCMG_SMOOTHER_CHEBYSHEV;
+  DevBuf mlp_image, dfeat;  // packed bf16 weights of the fused kernel
+  int64_t n() const { return host.n_free; }
+};
+
+struct TransferDev {
+  TransferHost host;
+  DevBuf fine_of, refined;
+  TransferLaunch tl{};
+};
+
+
+// CUDA-event timers per (level, stage): the per-level, per-stage profile of
+// a V-cycle (presmoothing, residual, restriction, coarse solve, prolongation,
+// postsmoothing) plus operator applications and CG vector work.
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int level = 0, stage = 0;
+  };
+  std::vector<Rec> pool;
+  size_t used = 0;
+  std::vector<double> ms;
+  std::vector<int64_t> cnt;
+  int nlev = 0;
+  ~Profiler() {
+    for (auto& r : pool) {
+      if (r.a) cudaEventDestroy(r.a);
+      if (r.b) cudaEventDestroy(r.b);
+    }
+  }
+};
+constexpr int NSTAGE = 10;
+
+// CUDA graphs of the V-cycle and of the operator half of a CG iteration;
+// captured once per handle (re-captured when smoother parameters or the
+// profiling state change).  Timers captured into a graph are event-record
+// nodes, read after each replay.
+struct GraphRec {
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;  // kernel launches per replay
+  std::vector<Profiler::Rec> recs;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    for (auto& r : recs) {
+      if (r.a) cudaEventDestroy(r.a);
+      if (r.b) cudaEventDestroy(r.b);
+    }
+    recs.clear();
+  }
+  ~GraphRec() { reset(); }
+};
+
+struct Handle {
+  cudaStream_t stream = nullptr;
+  bool stop_after_cgc = false;  // finest level: return after the prolongation
+  cudaStream_t cap_stream = nullptr;
+  bool use_graphs = true;
+  GraphRec* capturing = nullptr;
+  GraphRec g_core, g_a;
+  Profiler prof;
+  gcmg_config cfg{};
+  std::vector<std::unique_ptr<LevelDev>> lev;
+  std::vector<std::unique_ptr<TransferDev>> tr;  // tr[l]: between levels l and l-1
+  DevBuf diag_tab[KMAX + 1];
+  DevBuf Ainv;
+  int n0 = 0;
+  DevBuf scratch, scal, modes;
+  DevBuf cg_r, cg_p, cg_q, cg_z, cg_x;
+  DevBuf mlp_scratch;  // weight image of gcmg_mlp_correct calls
+  ~Handle() {
+    g_core.reset();
+    g_a.reset();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
+};
+
+// set-up of all levels, transfers, diagonals, coarse factor and eigenvalue
+// estimates of one problem (Sec. 5 set-up); throws Error
+void setup_handle(Handle& H, const std::vector<Octree>& meshes, int lmax, const gcmg_config& cfg);
+void upload_all_tables();
+void check_config(const gcmg_config* cfg);
+void check_level(const Handle& h, int level);
+int prof_begin(Handle& H, int level, int stage);
+void prof_end(Handle& H, int rec);
+void vmult(Handle& H, int l, bool fp64, const void* src, void* dst, int stage = GCMG_STAGE_VMULT);
+void vcycle_level(Handle& H, int l);
+bool any_learned(const Handle& H);
+
+}  // namespace gcmg
+
+struct gcmg_mesh {
+  std::vector<gcmg::Octree> levels;  // coarsest (one cell) first
+  int lmax = 0;
+};
+
+struct gcmg_handle {
+  gcmg::Handle h;
+};

@@ -99,6 +99,13 @@ cudaError_t launch_dot_noalloc(const double* x, const double* y, int64_t n, doub
 void launch_cg_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, int64_t n,
                          double* scratch, double* scal_out, cudaStream_t s);
 void launch_cg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t s);
+// CG inside a graph: scal[7] = |b|^2, scal[8] = iterations; the check kernel
+// counts an iteration and sets the while-node condition h; the stats kernel
+// writes (iterations, rr, |b|^2, status) to out
+void launch_cg_check(cudaGraphConditionalHandle h, double* scal, int maxit, double rtol2, cudaStream_t s);
+void launch_cg_stats(const double* scal, double rtol2, double* out, cudaStream_t s);
+void launch_scalar_set(double* scal, int slot, double v, cudaStream_t s);
+void launch_copy(const double* src, double* dst, int64_t n, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // learned per-cell smoother

@@ -12,6 +12,7 @@
 #include <string>
 
 #include "device.cuh"
+#include "gcmg.h"
 #include "kernels.h"
 
 namespace gcmg {
@@ -115,9 +116,9 @@ __global__ void __launch_bounds__(BLOCK) dot_final(const double* part, int np, d
   if (threadIdx.x == 0) {
     if (op == DOT_STORE) {
       scal[slot] = s;
-    } else if (op == DOT_ALPHA) {  // pq, alpha = rz / pq
+    } else if (op == DOT_ALPHA) {  // pq, alpha = rz / pq (0 when pq = 0: zero right-hand side)
       scal[1] = s;
-      scal[3] = scal[0] / s;
+      scal[3] = s != 0.0 ? scal[0] / s : 0.0;
     } else if (op == DOT_BETA) {  // rz_new, beta = rz_new / rz, rz <- rz_new
       scal[5] = s;
       scal[4] = s / scal[0];
@@ -167,6 +168,38 @@ __global__ void pmul_kernel(double* z, const double* a, const double* b, int64_t
 __global__ void xpby_kernel(double* p, const double* z, double beta, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = z[i] + beta * p[i];
+}
+
+
+// device-side control of a CG solve inside a CUDA graph: the iteration count
+// lives in scal[8]; the loop continues while it < maxit, the residual is above
+// the tolerance and (p, Ap) > 0 (a NaN residual stops it as well)
+__global__ void cg_check_kernel(cudaGraphConditionalHandle h, double* scal, int maxit, double rtol2) {
+  const double it = scal[8] + 1.0;
+  scal[8] = it;
+  const double rr = scal[2], nb2 = scal[7], pq = scal[1];
+  const bool go = (it < (double)maxit) && (rr > rtol2 * nb2) && (pq > 0.0);
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void cg_stats_kernel(const double* scal, double rtol2, double* out) {
+  const double it = scal[8], rr = scal[2], nb2 = scal[7], pq = scal[1];
+  double status = GCMG_ERR_NOT_CONVERGED;
+  if (nb2 == 0.0 || rr <= rtol2 * nb2)
+    status = GCMG_OK;
+  else if (!(pq > 0.0) || rr != rr)
+    status = GCMG_ERR_BREAKDOWN;
+  out[0] = nb2 == 0.0 ? 0.0 : it;
+  out[1] = rr;
+  out[2] = nb2;
+  out[3] = status;
+}
+
+__global__ void scalar_set_kernel(double* scal, int slot, double v) { scal[slot] = v; }
+
+__global__ void copy_kernel(const double* src, double* dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
 }
 
 }  // namespace
@@ -346,6 +379,27 @@ cudaError_t launch_dot_noalloc(const double* x, const double* y, int64_t n, doub
 void launch_cg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   { cg_p_kernel<<<grid_for(n), BLOCK, 0, s>>>(p, z, scal, n); note_launches(1); }
+}
+
+void launch_cg_check(cudaGraphConditionalHandle h, double* scal, int maxit, double rtol2, cudaStream_t s) {
+  cg_check_kernel<<<1, 1, 0, s>>>(h, scal, maxit, rtol2);
+  note_launches(1);
+}
+
+void launch_cg_stats(const double* scal, double rtol2, double* out, cudaStream_t s) {
+  cg_stats_kernel<<<1, 1, 0, s>>>(scal, rtol2, out);
+  note_launches(1);
+}
+
+void launch_scalar_set(double* scal, int slot, double v, cudaStream_t s) {
+  scalar_set_kernel<<<1, 1, 0, s>>>(scal, slot, v);
+  note_launches(1);
+}
+
+void launch_copy(const double* src, double* dst, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  copy_kernel<<<grid_for(n), BLOCK, 0, s>>>(src, dst, n);
+  note_launches(1);
 }
 
 }  // namespace gcmg

@@ -209,6 +209,11 @@ def batch_recipes(seed: int = 12292, n: int = 256):
 # position-keyed random values: the same input vector for any DoF numbering
 # --------------------------------------------------------------------------
 
+# seed of the perturbation of the Lanczos start vector of the eigenvalue
+# estimate (both the oracle and the library use 1 + point_values(x, seed))
+LANCZOS_START_SEED = 2203
+
+
 def point_values(xyz: np.ndarray, seed: int, resolution_bits: int = 20) -> np.ndarray:
     """Uniform values in [-1, 1) attached to points: each coordinate is
     rounded to a multiple of 2^-resolution_bits, the three integers are mixed
