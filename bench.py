@@ -14,8 +14,20 @@ value = fine-level fp32 operator throughput n_free / t_vmult (GDoF/s),
 t_vmult = mean duration of the fine-level operator applications inside the
 timed solves, from CUDA events on the library's stream.  Solve times of the
 mixed (fp32 V-cycle) and plain fp64 (fp64 V-cycle) variants are reported
-beside it.  Under torchrun every rank solves its own copy (replicas, weak
-scaling); value sums the ranks.
+beside it, and two further parts of the method:
+
+* learned: the per-cell network smoother trained on the GPU from the plain
+  solver's V-cycle states (8 training right-hand sides), then the A/B
+  comparison of time to 1e-8 with Chebyshev only / Chebyshev plus the
+  learned step / the learned step instead of postsmoothing; the variant kept
+  is the fastest that converges;
+* batch: 256 independent problems of uneven degree and size (degree 1..4,
+  depth 2..5, 0..2 octant levels, Fourier right-hand sides, one SplitMix64
+  stream with seed 12292), operator tile size and thread mapping from the
+  autotuner, solved to 1e-8 by one CUDA-graph launch.
+
+Under torchrun every rank solves its own copy (replicas, weak scaling);
+value sums the ranks.
 
 --impl reference times the oracle (plain CPU implementation, test
 infrastructure) on a bounded sample of the workload on the host cores.
@@ -43,6 +55,10 @@ METRIC = "fine-level vmult GDoF/s; solve time to 1e-8 rel. res., mixed/learned v
 # destination vector plus the per-cell metadata (roofline model of the
 # workload, per free DoF)
 BYTES_PER_DOF = {"fp32": 9.8, "fp64": 17.8}
+# DRAM bytes (read + write) of one launch of the fine-level tile kernel on
+# this workload from an ncu capture (profiles/); 0 = not captured for the
+# current kernel
+VMULT_TRAFFIC_BYTES = 0.0
 SAMPLE = synth.cube_octant(4, 2)  # 1/8 of the workload's cells, same recipe family
 
 
@@ -152,6 +168,71 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(g, mg, mg64):
+    """Train the learned smoother on the GPU and compare time to 1e-8."""
+    import torch
+    from paper_2203_12292_gb300 import learned as lrn
+
+    tr = lrn.train(mg64, epochs=100)
+    cmp = lrn.compare(mg, tr.net, rhs_seed=WORKLOAD.rhs_seed, rtol=1e-8, repeats=2, maxit=60)
+    mg.set_smoother(mg.finest, g.SMOOTHER_CHEBYSHEV)
+    return {"train_rows": tr.n_train, "val_rows": tr.n_val, "val_loss": tr.val_mse,
+            "val_loss_zero_correction": tr.val_mse_zero, "val_loss_initial_network": tr.val_mse_init,
+            "data_s": tr.seconds_data, "train_s": tr.seconds_train,
+            "variants": [v.__dict__ for v in cmp["variants"]], "kept": cmp["kept"],
+            "network": "250-128-128-125 GELU, bf16 operands, fp32 accumulation"}
+
+
+def run_batch(g, seed: int = 12292, n: int = 256):
+    """256 uneven problems solved to 1e-8 by one graph launch."""
+    import torch
+
+    rec = synth.batch_recipes(seed, n)
+    t0 = time.perf_counter()
+    meshes = {}
+    for k, d, e, _ in rec:
+        if (d, e) not in meshes:
+            meshes[(d, e)] = g.Mesh.from_recipe(synth.cube_octant(d, e))
+    probe = g.Mesh.from_recipe(synth.cube_octant(4, 1))
+    tuning = {}
+    for k in sorted({r[0] for r in rec}):
+        best, _ = g.autotune(probe, k, True, 10)
+        tuning[k] = best
+    t1 = time.perf_counter()
+    cfgs = [g.make_config(k, mg_fp32=True, tile_cells=tuning[k].tile_cells, cell_kernel=tuning[k].cell_kernel)
+            for k, _, _, _ in rec]
+    B = g.Batch([meshes[(d, e)] for _, d, e, _ in rec], cfgs)
+    t2 = time.perf_counter()
+    bs = []
+    for i, (_, _, _, s) in enumerate(rec):
+        f = synth.fourier_rhs(s)
+        bs.append(B.problems[i].rhs((f.kappa, f.phi, f.amp)))
+    xs = [torch.zeros_like(b) for b in bs]
+    dofs = int(sum(b.numel() for b in bs))
+    st = B.cg_solve(bs, xs, 1e-8, 100)  # builds and launches the graph
+    torch.cuda.synchronize()
+    launches0 = g.launch_count()
+    times = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(B.stream)
+        st = B.cg_solve(bs, xs, 1e-8, 100)
+        e1.record(B.stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    its = [s_.iterations for s_ in st]
+    out = {"problems": n, "dofs": dofs, "solve_ms": ms, "solve_ms_all": times,
+           "gdofs_solved_per_s": dofs / (ms * 1e-3) / 1e9, "iterations_min": min(its), "iterations_max": max(its),
+           "all_converged": all(s_.status == 0 for s_ in st), "graph_launches_per_solve": 1,
+           "kernels_per_solve": (g.launch_count() - launches0) // 3,
+           "tuning": {k: {"tile_cells": t.tile_cells, "cell_kernel": t.cell_kernel, "gdofs": t.gdofs}
+                      for k, t in tuning.items()},
+           "tune_s": t1 - t0, "setup_s": t2 - t1}
+    del B
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -159,6 +240,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gcmg", choices=["gcmg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="stream launches instead of CUDA graphs (for per-kernel profiler launch lists)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -197,6 +282,8 @@ def main():
     t0 = time.perf_counter()
     mesh = g.Mesh.from_recipe(WORKLOAD.recipe)
     mg = g.Multigrid(mesh, WORKLOAD.degree, mg_fp32=True)
+    if args.no_graphs:
+        mg.set_graphs(False)
     setup_s = time.perf_counter() - t0
     L = mg.finest
     n = mg.n_free(L)
@@ -258,6 +345,8 @@ def main():
 
     # plain fp64 variant (fp64 V-cycle) of the same solve
     mg64 = g.Multigrid(mesh, WORKLOAD.degree, mg_fp32=False)
+    if args.no_graphs:
+        mg64.set_graphs(False)
     x64 = torch.zeros_like(b)
     mg64.cg_solve(b, x64, 1e-8, 100)
     torch.cuda.synchronize()
@@ -267,6 +356,10 @@ def main():
     torch.cuda.synchronize()
     fp64_ms = e0.elapsed_time(e1)
     sol_diff = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+
+    learned = None
+    if not args.no_learned:
+        learned = run_learned(g, mg, mg64)
     del mg64
 
     # end to end through the C ABI with pinned host buffers
@@ -282,9 +375,13 @@ def main():
         mg.vmult_host(L, hs, hd)
     e2e_s = (time.perf_counter() - t) / reps
 
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(g)
+
     hbm, peak_kind = peaks()
     achieved = BYTES_PER_DOF["fp32"] * n / (t_vmult * 1e-3) / 1e9
-    traffic = None
+    traffic = VMULT_TRAFFIC_BYTES if VMULT_TRAFFIC_BYTES > 0 else None
     if rank == 0:
         res = {
             "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
@@ -296,8 +393,11 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": "cell_kernel<4,float> (fine-level operator, all colour launches)",
-                         "peak_kind": peak_kind, "bytes_per_dof": BYTES_PER_DOF["fp32"]},
+                         "kernel": "cell_kernel<4,float> line-parallel tile kernel + halo pass "
+                                   "(fine-level fp32 operator, 32-cell tiles)",
+                         "peak_kind": peak_kind, "bytes_per_dof": BYTES_PER_DOF["fp32"],
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the tile kernel, "
+                                           "one launch on this workload"},
             "cpu_baseline": cpu,
             "e2e": {"value": n / e2e_s / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 4 * n,
                     "d2h_bytes_per_step": 4 * n, "call": "gcmg_vmult_host, pinned host buffers, fp32"},
@@ -312,6 +412,8 @@ def main():
             "stage_ms_per_step_finest": stage_ms, "coarser_levels_ms_per_step": coarse_ms,
             "per_level_ms_per_step": per_level,
             "setup_s": setup_s,
+            "learned": learned,
+            "batch": batch,
         }
         print(json.dumps(res), flush=True)
     if dist is not None:

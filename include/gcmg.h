@@ -96,9 +96,11 @@ typedef struct {
   double smoothing_range;  /* lambda_min = lambda_max / range */
   int eig_steps;           /* CG steps of the lambda_max estimate */
   double eig_safety;       /* lambda_max = safety * estimate */
-  int tile_cells;          /* cells per tile, 0 = default per degree */
-  int cell_kernel;         /* fp32 operator kernel: 0 = slab threads per cell
-                              (tiles <= 64 cells), 1 = line-parallel kernel */
+  int tile_cells;          /* cells per tile, 0 = default (32) */
+  int cell_kernel;         /* fp32 operator kernel: 0 = default (line-parallel),
+                              1 = line-parallel (one thread per 1D line of
+                              a cell), 2 = slab threads (k+1 threads per
+                              cell, z-slabs in registers; tiles <= 64 cells) */
 } gcmg_config;
 
 int gcmg_config_default(gcmg_config* cfg);

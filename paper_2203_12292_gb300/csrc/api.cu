@@ -25,7 +25,9 @@ void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); 
 long long launch_counter() { return g_launches.load(); }
 
 
-int default_tile_cells(int) { return 64; }
+// cells per tile when the configuration leaves it open (the autotuner's
+// choice for every degree on GB300: 32-cell tiles, line-parallel kernel)
+int default_tile_cells(int) { return 32; }
 
 void check_level(const Handle& h, int level) {
   if (level < 0 || level >= (int)h.lev.size()) throw Error(GCMG_ERR_ARG, "level out of range");
@@ -440,7 +442,7 @@ void check_config(const gcmg_config* cfg) {
   if (cfg->cheb_degree < 1 || !(cfg->smoothing_range > 1.0) || cfg->eig_steps < 1)
     throw Error(GCMG_ERR_ARG, "bad smoother parameters");
   if (cfg->tile_cells < 0 || cfg->tile_cells > 255) throw Error(GCMG_ERR_ARG, "tile_cells must be 0..255");
-  if (cfg->cell_kernel < 0 || cfg->cell_kernel > 1) throw Error(GCMG_ERR_ARG, "cell_kernel must be 0 or 1");
+  if (cfg->cell_kernel < 0 || cfg->cell_kernel > 2) throw Error(GCMG_ERR_ARG, "cell_kernel must be 0, 1 or 2");
 }
 
 // the per-degree constant tables of every translation unit, once per device
@@ -479,7 +481,7 @@ void setup_handle(Handle& H, const std::vector<Octree>& meshes, int lmax, const 
     const int tc = cfg.tile_cells ? cfg.tile_cells : default_tile_cells(k);
     build_level(meshes[spec[l].first], k, tc, lmax, L->host);
     L->fp32 = cfg.mg_fp32 != 0;
-    L->cl.use_lines = cfg.cell_kernel == 1;
+    L->cl.use_lines = cfg.cell_kernel != 2;
     LevelHost& lh = L->host;
     L->tiles.upload(lh.tiles, H.stream);
     L->halo.alloc(lh.foreign.size() * sizeof(double));

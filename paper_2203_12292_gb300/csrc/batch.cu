@@ -231,7 +231,7 @@ int gcmg_autotune(const gcmg_mesh* probe, int degree, int mg_fp32, int reps, voi
     if (!probe || !best || degree < 1 || degree > KMAX || reps < 1) throw Error(GCMG_ERR_ARG, "bad arguments");
     upload_all_tables();
     // candidates: tile size x thread mapping (the slab mapping needs tiles of <= 64 cells)
-    const int cand[5][2] = {{32, 0}, {64, 0}, {32, 1}, {64, 1}, {128, 1}};
+    const int cand[5][2] = {{32, 2}, {64, 2}, {32, 1}, {64, 1}, {128, 1}};
     const int nc = mg_fp32 ? 5 : 3;  // fp64 always runs the line-parallel kernel
     const int (*list)[2] = mg_fp32 ? cand : cand + 2;
     gcmg_tuning top{degree, 0, 0, -1.0};

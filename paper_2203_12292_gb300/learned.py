@@ -127,7 +127,8 @@ class Variant:
     ms: float
 
 
-def compare(mg: Multigrid, net: MLP, rhs_seed: int = 2203, rtol: float = 1e-8, repeats: int = 3) -> Dict:
+def compare(mg: Multigrid, net: MLP, rhs_seed: int = 2203, rtol: float = 1e-8, repeats: int = 3,
+            maxit: int = 200) -> Dict:
     """Solve times of Chebyshev / augment / replace on one right-hand side;
     the finest level's smoother is left at the fastest variant."""
     import torch
@@ -143,7 +144,7 @@ def compare(mg: Multigrid, net: MLP, rhs_seed: int = 2203, rtol: float = 1e-8, r
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            st = mg.cg_solve(b, x, rtol, maxit=200, raise_on_fail=False)
+            st = mg.cg_solve(b, x, rtol, maxit=maxit, raise_on_fail=False)
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)

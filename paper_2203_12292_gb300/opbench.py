@@ -1,7 +1,7 @@
 """Operator microbenchmark: time the matrix-free operator of one level.
 
     python -m paper_2203_12292_gb300.opbench [--workload q4octant] [--level -1]
-        [--dtype f32|f64] [--reps 20] [--tile-cells 0]
+        [--dtype f32|f64] [--reps 20] [--tile-cells 0] [--cell-kernel 0|1|2]
 
 The timed applications run inside an NVTX range named "opbench", so a
 profiler can select exactly them.  Prints one JSON line (ms per application,
@@ -32,6 +32,7 @@ def main(argv=None):
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--tile-cells", type=int, default=0)
+    ap.add_argument("--cell-kernel", type=int, default=0, choices=[0, 1, 2])
     a = ap.parse_args(argv)
     import torch
 
@@ -40,7 +41,8 @@ def main(argv=None):
     b.build()
     w = WORKLOADS[a.workload]
     mesh = Mesh.from_recipe(w.recipe)
-    mg = Multigrid(mesh, w.degree, p_coarsening=w.p_coarsening, mg_fp32=True, tile_cells=a.tile_cells)
+    mg = Multigrid(mesh, w.degree, p_coarsening=w.p_coarsening, mg_fp32=True, tile_cells=a.tile_cells,
+                   cell_kernel=a.cell_kernel)
     lev = a.level if a.level >= 0 else mg.num_levels + a.level
     n = mg.n_free(lev)
     dt = torch.float32 if a.dtype == "f32" else torch.float64
@@ -61,6 +63,7 @@ def main(argv=None):
     info = mg.level_info(lev)
     print(json.dumps({"workload": w.name, "level": lev, "dtype": a.dtype, "n_free": n, "cells": info.n_cells,
                       "tiles": info.n_tiles, "halo_dofs": info.n_halo, "tile_cells": info.tile_cells,
+                      "cell_kernel": a.cell_kernel,
                       "ms": ms, "gdofs": n / ms / 1e6}))
 
 

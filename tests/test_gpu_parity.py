@@ -28,10 +28,11 @@ torch = pytest.importorskip("torch")
 
 
 class Case:
-    def __init__(self, gcmg, rec, k, p=False, fp32=False, tile_cells=0):
+    def __init__(self, gcmg, rec, k, p=False, fp32=False, tile_cells=0, cell_kernel=0):
         self.rec, self.k = rec, k
         self.mesh = gcmg.Mesh.from_recipe(rec)
-        self.mg = gcmg.Multigrid(self.mesh, k, p_coarsening=p, mg_fp32=fp32, tile_cells=tile_cells)
+        self.mg = gcmg.Multigrid(self.mesh, k, p_coarsening=p, mg_fp32=fp32, tile_cells=tile_cells,
+                                 cell_kernel=cell_kernel)
         self.levels = omg.build_levels(omesh.build_mesh(rec), k, p_coarsening=p, assembled=(k <= 2))
         assert self.mg.num_levels == len(self.levels)
         self.xyz = [self.mg.dof_coords(l) for l in range(self.mg.num_levels)]
@@ -307,3 +308,20 @@ def test_profiling_inside_graphs(gcmg):
     # presmoothing 2, residual 1, postsmoothing 3 operator applications per V-cycle
     assert cnt == 6 * (st.iterations) and ms > 0
     mg.set_profiling(False)
+
+
+@pytest.mark.parametrize("rec,k", [(synth.octant(3), 4), (synth.cube_octant(3, 1), 2), (synth.sphere(4), 3)],
+                         ids=["octant3-Q4", "cube3+1-Q2", "sphere4-Q3"])
+@pytest.mark.parametrize("tc", [32, 64])
+def test_vmult_fp32_slab_kernel(gcmg, rec, k, tc):
+    """The slab-thread mapping (k+1 threads per cell) computes the same operator."""
+    c = Case(gcmg, rec, k, tile_cells=tc, cell_kernel=2)
+    for l in range(c.mg.num_levels):
+        if c.mg.n_free(l) == 0:
+            continue
+        x = c.gvec(l, 700 + l, torch.float32)
+        y = torch.empty_like(x)
+        c.mg.vmult(l, x, y)
+        torch.cuda.synchronize()
+        ref = c.levels[l].apply64(c.ovec(l, 700 + l).astype(np.float32).astype(np.float64))
+        assert c.cmp(l, y, ref) < 2e-6, l
