@@ -276,21 +276,6 @@ __device__ __forceinline__ void sweep_z_scale(T* cb, const T* sm_h, int ncells) 
   }
 }
 
-// the cell operator h (K x M x M + M x K x M + M x M x K) on all cells
-template <int K, typename T>
-__device__ __forceinline__ void cell_laplace(T* cb, const T* sm_h, int ncells) {
-  sweep_B<K, 0, false>(cb, ncells);
-  __syncthreads();
-  sweep_B<K, 1, false>(cb, ncells);
-  __syncthreads();
-  sweep_z_scale<K>(cb, sm_h, ncells);
-  __syncthreads();
-  sweep_B<K, 1, true>(cb, ncells);
-  __syncthreads();
-  sweep_B<K, 0, true>(cb, ncells);
-  __syncthreads();
-}
-
 // ---------------------------------------------------------------------------
 // register-resident sweeps for one cell held by one thread (array u of
 // N^3 values, compile-time indices only so that u stays in registers)
@@ -380,6 +365,78 @@ __device__ __forceinline__ void cell_laplace_regs(T* u, T h) {
   eo_sweep<N, 2, false>(u, tb.Be);
   eo_sweep<N, 1, false>(u, tb.Be);
   eo_sweep<N, 0, false>(u, tb.Be);
+}
+
+// block-cooperative even-odd sweep along direction D for all cells (one
+// thread per line): FWD applies B (nodal values -> modes in mode order),
+// otherwise B^T (modes -> nodal values)
+template <int K, int D, bool FWD, typename T>
+__device__ __forceinline__ void sweep_eo(T* cb, int ncells) {
+  constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
+  const DevTables<T>& tb = tab<T>(K);
+  for (int t = threadIdx.x; t < ncells * N2; t += blockDim.x) {
+    const int cell = t / N2, r = t - cell * N2;
+    int base, u, v;
+    line_geom<N, D>(r, base, u, v);
+    T* p = cb + cell * N3 + base;
+    if (FWD)
+      eo_forward<N, 0, line_stride<N, D>()>(p, tb.Be);
+    else
+      eo_backward<N, 0, line_stride<N, D>()>(p, tb.Be);
+  }
+}
+
+// z lines in registers: forward even-odd transform, scaling by
+// h (lam_a + lam_b + lam_c) (mode order), backward transform
+template <int K, typename T>
+__device__ __forceinline__ void sweep_z_scale_eo(T* cb, const T* sm_h, int ncells) {
+  constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
+  const DevTables<T>& tb = tab<T>(K);
+  for (int t = threadIdx.x; t < ncells * N2; t += blockDim.x) {
+    const int cell = t / N2, r = t - cell * N2;
+    T* p = cb + cell * N3 + r;
+    T v[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] = p[c * N2];
+    eo_forward<N, 0, 1>(v, tb.Be);
+    const T hab = sm_h[cell];
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] *= hab * tb.lam3[r + N2 * c];
+    eo_backward<N, 0, 1>(v, tb.Be);
+#pragma unroll
+    for (int c = 0; c < N; ++c) p[c * N2] = v[c];
+  }
+}
+
+// the cell operator h (K x M x M + M x K x M + M x M x K) on all cells of
+// the block, fast-diagonalisation form.  fp64 (bound by the FP64 pipe on
+// GB300) takes the even-odd sweeps, which halve the multiplications; fp32
+// (bound by instruction issue) is faster with the plain 5x5 sweeps
+template <int K, typename T>
+__device__ __forceinline__ void cell_laplace(T* cb, const T* sm_h, int ncells) {
+  if constexpr (sizeof(T) == 8) {
+    sweep_eo<K, 0, true>(cb, ncells);
+    __syncthreads();
+    sweep_eo<K, 1, true>(cb, ncells);
+    __syncthreads();
+    sweep_z_scale_eo<K>(cb, sm_h, ncells);
+    __syncthreads();
+    sweep_eo<K, 1, false>(cb, ncells);
+    __syncthreads();
+    sweep_eo<K, 0, false>(cb, ncells);
+    __syncthreads();
+  } else {
+    sweep_B<K, 0, false>(cb, ncells);
+    __syncthreads();
+    sweep_B<K, 1, false>(cb, ncells);
+    __syncthreads();
+    sweep_z_scale<K>(cb, sm_h, ncells);
+    __syncthreads();
+    sweep_B<K, 1, true>(cb, ncells);
+    __syncthreads();
+    sweep_B<K, 0, true>(cb, ncells);
+    __syncthreads();
+  }
 }
 
 }  // namespace gcmg

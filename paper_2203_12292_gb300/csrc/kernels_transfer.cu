@@ -201,6 +201,8 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
   __shared__ int32_t sm_fine[TP];
   __shared__ uint16_t sm_mask[TP];
   __shared__ uint16_t sm_cell[TP];
+  __shared__ uint32_t sm_own[TP * 8];          // ownership masks of the fine cells
+  __shared__ int32_t sm_gs[TP * 8 * NSLOT];    // their global slot starts (-1: none)
   extern __shared__ __align__(16) unsigned char smem[];
   CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem);
   T* cb = reinterpret_cast<T*>(smem + (size_t)A.tc * sizeof(CellMeta));
@@ -229,26 +231,50 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
     for (int i = threadIdx.x; i < np * M3; i += blockDim.x) e3[i] = T(0);
     for (int i = threadIdx.x; i < np * N3; i += blockDim.x) cb[i] = T(0);
     __syncthreads();
-    for (int t = threadIdx.x; t < np * 8 * N3; t += blockDim.x) {
-      const int j = t / (8 * N3), r = t - j * 8 * N3;
-      const int q = r / N3, n = r - q * N3;
-      const int a = n % N, b = (n / N) % N, c = n / (N * N);
-      int f;
-      if (sm_ref[j])
-        f = sm_fine[j] + q;
-      else if (q == 0)
-        f = sm_fine[j];
-      else
-        continue;
-      int slot, off;
-      node_slot<K>(a, b, c, slot, off);
-      if (!((A.own_f[f] >> slot) & 1u)) continue;
-      const T val = A.src[A.gstart_f[(size_t)f * NSLOT + slot] + off];
-      if (sm_ref[j]) {
-        const int gi = (q & 1) * K + a, gj = ((q >> 1) & 1) * K + b, gk = (q >> 2) * K + c;
-        e3[j * M3 + gi + M * (gj + M * gk)] = val;
-      } else {
-        cb[j * N3 + n] = val;
+    // the fine cells' slot starts and ownership, coalesced (children of a
+    // refined coarse cell are consecutive fine cells)
+    for (int t = threadIdx.x; t < np * 8 * NSLOT; t += blockDim.x) {
+      const int jq = t / NSLOT, slot = t - jq * NSLOT, j = jq >> 3, q = jq & 7;
+      const bool use = sm_ref[j] || q == 0;
+      const int f = sm_fine[j] + q;
+      sm_gs[t] = use ? A.gstart_f[(size_t)f * NSLOT + slot] : -1;
+      if (slot == 0) sm_own[jq] = use ? A.own_f[f] : 0u;
+    }
+    __syncthreads();
+    // gather the owned fine values (RG loads in flight per thread)
+    constexpr int RG = 8;
+    const int ntot = np * 8 * N3;
+    for (int t0 = threadIdx.x; t0 < ntot; t0 += RG * BLOCK) {
+      T val[RG];
+      int dst[RG];
+#pragma unroll
+      for (int u = 0; u < RG; ++u) {
+        const int t = t0 + u * BLOCK;
+        dst[u] = -1;
+        if (t < ntot) {
+          const int j = t / (8 * N3), r = t - j * 8 * N3;
+          const int q = r / N3, n = r - q * N3;
+          const int a = n % N, b = (n / N) % N, c = n / (N * N);
+          int slot, off;
+          node_slot<K>(a, b, c, slot, off);
+          if ((sm_own[j * 8 + q] >> slot) & 1u) {
+            val[u] = A.src[sm_gs[(j * 8 + q) * NSLOT + slot] + off];
+            if (sm_ref[j]) {
+              const int gi = (q & 1) * K + a, gj = ((q >> 1) & 1) * K + b, gk = (q >> 2) * K + c;
+              dst[u] = j * M3 + gi + M * (gj + M * gk);
+            } else {
+              dst[u] = TP * M3 + j * N3 + n;  // marks the identity category: into cb
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < RG; ++u) {
+        if (dst[u] < 0) continue;
+        if (dst[u] >= TP * M3)
+          cb[dst[u] - TP * M3] = val[u];
+        else
+          e3[dst[u]] = val[u];
       }
     }
     __syncthreads();
