@@ -96,7 +96,9 @@ typedef struct {
   double smoothing_range;  /* lambda_min = lambda_max / range */
   int eig_steps;           /* CG steps of the lambda_max estimate */
   double eig_safety;       /* lambda_max = safety * estimate */
-  int tile_cells;          /* cells per tile, 0 = default (32) */
+  int tile_cells;          /* cells per tile on large levels, 0 = default (32);
+                              levels with fewer than 2 * 152 tiles of that
+                              size use halved tiles (down to 8 cells) */
   int cell_kernel;         /* fp32 operator kernel: 0 = default (line-parallel),
                               1 = line-parallel (one thread per 1D line of
                               a cell), 2 = slab threads (k+1 threads per

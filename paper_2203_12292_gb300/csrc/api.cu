@@ -25,9 +25,15 @@ void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); 
 long long launch_counter() { return g_launches.load(); }
 
 
-// cells per tile when the configuration leaves it open (the autotuner's
-// choice for every degree on GB300: 32-cell tiles, line-parallel kernel)
-int default_tile_cells(int) { return 32; }
+// cells per tile of a level: the configured size (default 32, the
+// autotuner's choice for every degree on GB300), halved while the level would
+// give fewer than two tiles per SM (at least 8 cells per tile): small levels
+// are latency-bound and finish sooner with more, shorter tiles
+int tile_cells_for(int configured, size_t n_cells) {
+  int tc = configured ? configured : 32;
+  while (tc > 8 && n_cells < (size_t)2 * 152 * tc) tc /= 2;
+  return tc;
+}
 
 void check_level(const Handle& h, int level) {
   if (level < 0 || level >= (int)h.lev.size()) throw Error(GCMG_ERR_ARG, "level out of range");
@@ -478,7 +484,7 @@ void setup_handle(Handle& H, const std::vector<Octree>& meshes, int lmax, const 
   for (int l = 0; l < nl; ++l) {
     auto L = std::make_unique<LevelDev>();
     const int k = spec[l].second;
-    const int tc = cfg.tile_cells ? cfg.tile_cells : default_tile_cells(k);
+    const int tc = tile_cells_for(cfg.tile_cells, meshes[spec[l].first].leaves.size());
     build_level(meshes[spec[l].first], k, tc, lmax, L->host);
     L->fp32 = cfg.mg_fp32 != 0;
     L->cl.use_lines = cfg.cell_kernel != 2;
@@ -644,7 +650,8 @@ int gcmg_mesh_dof_coords(const gcmg_mesh* mesh, int level, int degree, int tile_
     if (degree < 1 || degree > KMAX) throw Error(GCMG_ERR_ARG, "degree must be 1..4");
     if (tile_cells < 0 || tile_cells > 255) throw Error(GCMG_ERR_ARG, "tile_cells must be 0..255");
     LevelHost L;
-    build_level(mesh->levels[level], degree, tile_cells ? tile_cells : default_tile_cells(degree), mesh->lmax, L);
+    build_level(mesh->levels[level], degree, tile_cells_for(tile_cells, mesh->levels[level].leaves.size()),
+                mesh->lmax, L);
     *n_free = L.n_free;
     if (xyz) std::memcpy(xyz, L.dof_xyz_cache.data(), L.dof_xyz_cache.size() * sizeof(double));
   });
@@ -656,7 +663,8 @@ int gcmg_mesh_check_level(const gcmg_mesh* mesh, int level, int degree, int tile
     if (degree < 1 || degree > KMAX) throw Error(GCMG_ERR_ARG, "degree must be 1..4");
     if (tile_cells < 0 || tile_cells > 255) throw Error(GCMG_ERR_ARG, "tile_cells must be 0..255");
     LevelHost L;
-    build_level(mesh->levels[level], degree, tile_cells ? tile_cells : default_tile_cells(degree), mesh->lmax, L);
+    build_level(mesh->levels[level], degree, tile_cells_for(tile_cells, mesh->levels[level].leaves.size()),
+                mesh->lmax, L);
     try {
       validate_level(L);
     } catch (const std::exception& e) {

@@ -250,15 +250,19 @@ template <int K, typename T>
 __device__ __forceinline__ void sweep_z_scale(T* cb, const T* sm_h, int ncells) {
   constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
   const DevTables<T>& tb = tab<T>(K);
+  // lam_a + lam_b per z line in shared memory: indexing the constant table
+  // with the thread's (a, b) would serialise the warp's constant reads
+  __shared__ T s_lab[N2];
+  for (int r = threadIdx.x; r < N2; r += blockDim.x) s_lab[r] = tb.lam[r % N] + tb.lam[r / N];
+  __syncthreads();
   for (int t = threadIdx.x; t < ncells * N2; t += blockDim.x) {
     const int cell = t / N2, r = t - cell * N2;
-    const int a = r % N, b = r / N;
     T* p = cb + cell * N3 + r;
     T v[N], w[N];
 #pragma unroll
     for (int c = 0; c < N; ++c) v[c] = p[c * N2];
     const T hab = sm_h[cell];
-    const T lab = tb.lam[a] + tb.lam[b];
+    const T lab = s_lab[r];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       T s = 0;
@@ -392,6 +396,11 @@ template <int K, typename T>
 __device__ __forceinline__ void sweep_z_scale_eo(T* cb, const T* sm_h, int ncells) {
   constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
   const DevTables<T>& tb = tab<T>(K);
+  // the eigenvalue sums in shared memory: indexing the constant table with
+  // the thread's line would serialise the warp's constant reads
+  __shared__ T s_lam3[N3];
+  for (int i = threadIdx.x; i < N3; i += blockDim.x) s_lam3[i] = tb.lam3[i];
+  __syncthreads();
   for (int t = threadIdx.x; t < ncells * N2; t += blockDim.x) {
     const int cell = t / N2, r = t - cell * N2;
     T* p = cb + cell * N3 + r;
@@ -401,7 +410,7 @@ __device__ __forceinline__ void sweep_z_scale_eo(T* cb, const T* sm_h, int ncell
     eo_forward<N, 0, 1>(v, tb.Be);
     const T hab = sm_h[cell];
 #pragma unroll
-    for (int c = 0; c < N; ++c) v[c] *= hab * tb.lam3[r + N2 * c];
+    for (int c = 0; c < N; ++c) v[c] *= hab * s_lam3[r + N2 * c];
     eo_backward<N, 0, 1>(v, tb.Be);
 #pragma unroll
     for (int c = 0; c < N; ++c) p[c * N2] = v[c];
@@ -412,9 +421,11 @@ __device__ __forceinline__ void sweep_z_scale_eo(T* cb, const T* sm_h, int ncell
 // the block, fast-diagonalisation form.  fp64 (bound by the FP64 pipe on
 // GB300) takes the even-odd sweeps, which halve the multiplications; fp32
 // (bound by instruction issue) is faster with the plain 5x5 sweeps
+constexpr bool FP32_EVEN_ODD = false;
+
 template <int K, typename T>
 __device__ __forceinline__ void cell_laplace(T* cb, const T* sm_h, int ncells) {
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (sizeof(T) == 8 || FP32_EVEN_ODD) {
     sweep_eo<K, 0, true>(cb, ncells);
     __syncthreads();
     sweep_eo<K, 1, true>(cb, ncells);
