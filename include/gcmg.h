@@ -103,6 +103,8 @@ typedef struct {
                               1 = line-parallel (one thread per 1D line of
                               a cell), 2 = slab threads (k+1 threads per
                               cell, z-slabs in registers; tiles <= 64 cells) */
+  int cell_threads;        /* threads per CTA of the line-parallel fp32 operator:
+                              0 = default (256), 128, 256, 384 or 512 */
 } gcmg_config;
 
 int gcmg_config_default(gcmg_config* cfg);
@@ -363,6 +365,7 @@ typedef struct {
   int degree;
   int tile_cells;   /* cells per tile */
   int cell_kernel;  /* gcmg_config.cell_kernel */
+  int cell_threads; /* gcmg_config.cell_threads */
   double gdofs;     /* measured operator throughput (free DoFs per ns) */
 } gcmg_tuning;
 

@@ -42,7 +42,7 @@ class RefineStep(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("degree", _c_int), ("p_coarsening", _c_int), ("mg_fp32", _c_int), ("cheb_degree", _c_int),
                 ("smoothing_range", _c_double), ("eig_steps", _c_int), ("eig_safety", _c_double),
-                ("tile_cells", _c_int), ("cell_kernel", _c_int)]
+                ("tile_cells", _c_int), ("cell_kernel", _c_int), ("cell_threads", _c_int)]
 
 
 class LevelInfo(ctypes.Structure):
@@ -55,7 +55,8 @@ class SolveStats(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("degree", _c_int), ("tile_cells", _c_int), ("cell_kernel", _c_int), ("gdofs", _c_double)]
+    _fields_ = [("degree", _c_int), ("tile_cells", _c_int), ("cell_kernel", _c_int), ("cell_threads", _c_int),
+                ("gdofs", _c_double)]
 
 
 _SIGS = {
@@ -227,12 +228,13 @@ def _is64(t) -> int:
 
 def make_config(degree: int, p_coarsening: bool = False, mg_fp32: bool = True, tile_cells: int = 0,
                 cheb_degree: int = 3, smoothing_range: float = 20.0, eig_steps: int = 12, eig_safety: float = 1.2,
-                cell_kernel: int = 0) -> Config:
+                cell_kernel: int = 0, cell_threads: int = 0) -> Config:
     cfg = Config()
     _check(lib().gcmg_config_default(ctypes.byref(cfg)))
     cfg.degree, cfg.p_coarsening, cfg.mg_fp32 = degree, int(p_coarsening), int(mg_fp32)
     cfg.tile_cells, cfg.cheb_degree, cfg.smoothing_range = tile_cells, cheb_degree, smoothing_range
     cfg.eig_steps, cfg.eig_safety, cfg.cell_kernel = eig_steps, eig_safety, cell_kernel
+    cfg.cell_threads = cell_threads
     return cfg
 
 
@@ -242,7 +244,8 @@ class Multigrid:
 
     def __init__(self, mesh: Mesh, degree: int, p_coarsening: bool = False, mg_fp32: bool = True,
                  tile_cells: int = 0, cheb_degree: int = 3, smoothing_range: float = 20.0,
-                 eig_steps: int = 12, eig_safety: float = 1.2, cell_kernel: int = 0, _handle=None, _owner=None):
+                 eig_steps: int = 12, eig_safety: float = 1.2, cell_kernel: int = 0, cell_threads: int = 0,
+                 _handle=None, _owner=None):
         import torch
         self.mesh = mesh
         self.stream = torch.cuda.current_stream()
@@ -250,7 +253,7 @@ class Multigrid:
             self._h, self._owned, self._owner = _handle, False, _owner
         else:
             cfg = make_config(degree, p_coarsening, mg_fp32, tile_cells, cheb_degree, smoothing_range, eig_steps,
-                              eig_safety, cell_kernel)
+                              eig_safety, cell_kernel, cell_threads)
             h = _c_void_p()
             _check(lib().gcmg_setup(mesh._p, ctypes.byref(cfg), _c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
             self._h, self._owned = h, True

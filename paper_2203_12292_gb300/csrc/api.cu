@@ -449,6 +449,9 @@ void check_config(const gcmg_config* cfg) {
     throw Error(GCMG_ERR_ARG, "bad smoother parameters");
   if (cfg->tile_cells < 0 || cfg->tile_cells > 255) throw Error(GCMG_ERR_ARG, "tile_cells must be 0..255");
   if (cfg->cell_kernel < 0 || cfg->cell_kernel > 2) throw Error(GCMG_ERR_ARG, "cell_kernel must be 0, 1 or 2");
+  if (cfg->cell_threads != 0 && cfg->cell_threads != 128 && cfg->cell_threads != 256 && cfg->cell_threads != 384 &&
+      cfg->cell_threads != 512)
+    throw Error(GCMG_ERR_ARG, "cell_threads must be 0, 128, 256, 384 or 512");
 }
 
 // the per-degree constant tables of every translation unit, once per device
@@ -488,6 +491,7 @@ void setup_handle(Handle& H, const std::vector<Octree>& meshes, int lmax, const 
     build_level(meshes[spec[l].first], k, tc, lmax, L->host);
     L->fp32 = cfg.mg_fp32 != 0;
     L->cl.use_lines = cfg.cell_kernel != 2;
+    L->cl.threads = cfg.cell_threads ? cfg.cell_threads : 256;
     LevelHost& lh = L->host;
     L->tiles.upload(lh.tiles, H.stream);
     L->halo.alloc(lh.foreign.size() * sizeof(double));
@@ -685,6 +689,7 @@ int gcmg_config_default(gcmg_config* cfg) {
     cfg->eig_safety = 1.2;
     cfg->tile_cells = 0;
     cfg->cell_kernel = 0;
+    cfg->cell_threads = 0;
   });
 }
 

@@ -234,7 +234,7 @@ int gcmg_autotune(const gcmg_mesh* probe, int degree, int mg_fp32, int reps, voi
     const int cand[5][2] = {{32, 2}, {64, 2}, {32, 1}, {64, 1}, {128, 1}};
     const int nc = mg_fp32 ? 5 : 3;  // fp64 always runs the line-parallel kernel
     const int (*list)[2] = mg_fp32 ? cand : cand + 2;
-    gcmg_tuning top{degree, 0, 0, -1.0};
+    gcmg_tuning top{degree, 0, 0, 0, -1.0};
     for (int c = 0; c < nc; ++c) {
       gcmg_config cfg;
       gcmg_config_default(&cfg);
@@ -245,7 +245,7 @@ int gcmg_autotune(const gcmg_mesh* probe, int degree, int mg_fp32, int reps, voi
       Handle H;
       H.stream = static_cast<cudaStream_t>(stream);
       setup_handle(H, probe->levels, probe->lmax, cfg);
-      const gcmg_tuning t{degree, cfg.tile_cells, cfg.cell_kernel, time_vmult(H, mg_fp32 == 0, reps)};
+      const gcmg_tuning t{degree, cfg.tile_cells, cfg.cell_kernel, cfg.cell_threads, time_vmult(H, mg_fp32 == 0, reps)};
       if (all) all[c] = t;
       if (t.gdofs > top.gdofs) top = t;
     }

@@ -33,6 +33,7 @@ struct CellLaunch {
   int tc;
   int max_local;
   int use_lines;  // 1: fp32 operator with the line-parallel kernel
+  int threads;    // threads per CTA of the line-parallel operator kernel (128, 256, 384 or 512)
   double lo, dom;
 };
 

@@ -116,8 +116,8 @@ __device__ __forceinline__ void write_tile_dofs(T* dst, T* halo, const T* ys, co
   for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) h[i] = ys[ti.n_owned + i];
 }
 
-template <int K, typename T, int MODE>
-__global__ void __launch_bounds__(BLOCK) cell_kernel(CellArgs<T> A) {
+template <int K, typename T, int MODE, int NT = BLOCK>
+__global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
   constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout SL = smem_layout<T>(N3, A.tc, A.max_local);
@@ -752,14 +752,26 @@ void run_halo(const CellLaunch& L, T* dst, cudaStream_t s) {
   }
 }
 
+template <int K, typename T, int MODE, int NT>
+void launch_cells_nt(const CellLaunch& L, CellArgs<T> A, size_t sm, cudaStream_t s) {
+  ensure_smem(cell_kernel<K, T, MODE, NT>, sm);
+  cell_kernel<K, T, MODE, NT><<<L.n_tiles, NT, sm, s>>>(A);
+  note_launches(1);
+}
+
 template <int K, typename T, int MODE>
 void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
   const size_t sm = smem_layout<T>((K + 1) * (K + 1) * (K + 1), L.tc, L.max_local).total;
-  ensure_smem(cell_kernel<K, T, MODE>, sm);
-  {
-    cell_kernel<K, T, MODE><<<L.n_tiles, BLOCK, sm, s>>>(A);
-    note_launches(1);
-  }
+  // the thread count is a tuning parameter of the fp32 operator only
+  const int nt = (MODE == MODE_VMULT && sizeof(T) == 4) ? L.threads : BLOCK;
+  if (nt == 128)
+    launch_cells_nt<K, T, MODE, 128>(L, A, sm, s);
+  else if (nt == 384)
+    launch_cells_nt<K, T, MODE, 384>(L, A, sm, s);
+  else if (nt == 512)
+    launch_cells_nt<K, T, MODE, 512>(L, A, sm, s);
+  else
+    launch_cells_nt<K, T, MODE, BLOCK>(L, A, sm, s);
   run_halo<T>(L, A.dst, s);
 }
 

@@ -33,6 +33,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--tile-cells", type=int, default=0)
     ap.add_argument("--cell-kernel", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--cell-threads", type=int, default=0, choices=[0, 128, 256, 384, 512])
     a = ap.parse_args(argv)
     import torch
 
@@ -42,7 +43,7 @@ def main(argv=None):
     w = WORKLOADS[a.workload]
     mesh = Mesh.from_recipe(w.recipe)
     mg = Multigrid(mesh, w.degree, p_coarsening=w.p_coarsening, mg_fp32=True, tile_cells=a.tile_cells,
-                   cell_kernel=a.cell_kernel)
+                   cell_kernel=a.cell_kernel, cell_threads=a.cell_threads)
     lev = a.level if a.level >= 0 else mg.num_levels + a.level
     n = mg.n_free(lev)
     dt = torch.float32 if a.dtype == "f32" else torch.float64
@@ -63,7 +64,7 @@ def main(argv=None):
     info = mg.level_info(lev)
     print(json.dumps({"workload": w.name, "level": lev, "dtype": a.dtype, "n_free": n, "cells": info.n_cells,
                       "tiles": info.n_tiles, "halo_dofs": info.n_halo, "tile_cells": info.tile_cells,
-                      "cell_kernel": a.cell_kernel,
+                      "cell_kernel": a.cell_kernel, "cell_threads": a.cell_threads,
                       "ms": ms, "gdofs": n / ms / 1e6}))
 
 
