@@ -238,6 +238,168 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
 }
 
 // ---------------------------------------------------------------------------
+// operator for tiles of at most CHUNK cells (the default configuration):
+// every thread owns the same lines of the tile in every phase (line l of the
+// tile = cell l / (k+1)^2, position l % (k+1)^2), so their cell and offsets
+// are computed once per tile; the hanging-node passes are skipped for tiles
+// without hanging cells; the accumulation runs sub-colour by sub-colour from
+// the cells' sub-colour numbers.
+// ---------------------------------------------------------------------------
+template <int K, typename T>
+__global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
+  constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SmemLayout SL = smem_layout<T>(N3, A.tc, A.max_local);
+  CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem + SL.meta);
+  T* sm_h = reinterpret_cast<T*>(smem + SL.h);
+  uint16_t* sm_mask = reinterpret_cast<uint16_t*>(smem + SL.mask);
+  uint16_t* sm_cell = reinterpret_cast<uint16_t*>(smem + SL.cell);
+  T* cb = reinterpret_cast<T*>(smem + SL.cb);
+  T* xs = reinterpret_cast<T*>(smem + SL.xs);
+  T* ys = reinterpret_cast<T*>(smem + SL.ys);
+  __shared__ uint8_t sm_sub[CHUNK];
+  __shared__ T s_lab[N2];
+  const DevTables<T>& tb = tab<T>(K);
+
+  const TileInfo ti = A.tiles[blockIdx.x];
+  const int nc = ti.n_cells;  // <= CHUNK
+  const int nl = nc * N2;     // x-lines of the tile
+  const int nloc = ti.n_owned + ti.n_foreign;
+  load_meta(sm_meta, A.meta, ti.cell_begin, nc);
+  load_tile_dofs(xs, A.src, A.foreign, ti);
+  for (int i = threadIdx.x; i < nloc; i += BLOCK) ys[i] = T(0);
+  constexpr bool EO = sizeof(T) == 8;  // fp64: even-odd sweeps (FP64 pipe bound), modes in mode order
+  for (int r = threadIdx.x; r < N2; r += BLOCK)
+    s_lab[r] = EO ? tb.lame[r % N] + tb.lame[r / N] : tb.lam[r % N] + tb.lam[r / N];
+  __syncthreads();
+  int hang = 0;
+  if (threadIdx.x < nc) {
+    const int cell = A.perm[ti.cell_begin + threadIdx.x];
+    const CellMeta& m = sm_meta[cell];
+    sm_cell[threadIdx.x] = (uint16_t)cell;
+    sm_mask[threadIdx.x] = m.mask;
+    sm_sub[threadIdx.x] = m.sub;
+    sm_h[threadIdx.x] = (T)ldexp(A.dom, -(int)m.level);
+    hang = (m.mask & MASK_HANG) != 0;
+  }
+  hang = __syncthreads_or(hang);
+
+  // G_e: gather the x-lines (line t of the tile = cell t / N2, position r = b + N c)
+#pragma unroll 1
+  for (int t = threadIdx.x; t < nl; t += BLOCK) {
+    const int j = t / N2, r = t - j * N2;
+    const int b = r % N, c = r / N;
+    const uint16_t* ls = sm_meta[sm_cell[j]].ls;
+    T* out = cb + j * N3 + N * r;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      int slot, off;
+      node_slot<K>(a, b, c, slot, off);
+      const uint16_t l = ls[slot];
+      out[a] = (l == LS_NONE) ? T(0) : xs[l + off];
+    }
+  }
+  __syncthreads();
+  hanging_all<K, false>(cb, sm_mask, hang ? nc : 0);  // C_e (no work without hanging cells)
+
+  // S^T Q S: x, y forward, z forward/scale/backward, y, x backward
+#pragma unroll 1
+  for (int t = threadIdx.x; t < nl; t += BLOCK) {
+    T* p = cb + (t / N2) * N3 + N * (t % N2);
+    if (EO)
+      eo_forward<N, 0, 1>(p, tb.Be);
+    else
+      line_apply<N, 1, false>(p, tb.B);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int t = threadIdx.x; t < nl; t += BLOCK) {
+    const int j = t / N2, r = t - j * N2;
+    T* p = cb + j * N3 + r % N + N2 * (r / N);
+    if (EO)
+      eo_forward<N, 0, N>(p, tb.Be);
+    else
+      line_apply<N, N, false>(p, tb.B);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int t = threadIdx.x; t < nl; t += BLOCK) {
+    const int j = t / N2, r = t - j * N2;
+    T* p = cb + j * N3 + r;
+    T v[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] = p[c * N2];
+    const T hab = sm_h[j], lab = s_lab[r];
+    if (EO) {
+      eo_forward<N, 0, 1>(v, tb.Be);
+#pragma unroll
+      for (int c = 0; c < N; ++c) v[c] *= hab * (tb.lame[c] + lab);
+      eo_backward<N, 0, 1>(v, tb.Be);
+    } else {
+      T w[N];
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        T sum = 0;
+#pragma unroll
+        for (int c = 0; c < N; ++c) sum += tb.B[q][c] * v[c];
+        w[q] = sum * hab * (lab + tb.lam[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        T sum = 0;
+#pragma unroll
+        for (int c = 0; c < N; ++c) sum += tb.B[c][q] * w[c];
+        v[q] = sum;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < N; ++c) p[c * N2] = v[c];
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int t = threadIdx.x; t < nl; t += BLOCK) {
+    const int j = t / N2, r = t - j * N2;
+    T* p = cb + j * N3 + r % N + N2 * (r / N);
+    if (EO)
+      eo_backward<N, 0, N>(p, tb.Be);
+    else
+      line_apply<N, N, true>(p, tb.B);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int t = threadIdx.x; t < nl; t += BLOCK) {
+    T* p = cb + (t / N2) * N3 + N * (t % N2);
+    if (EO)
+      eo_backward<N, 0, 1>(p, tb.Be);
+    else
+      line_apply<N, 1, true>(p, tb.B);
+  }
+  __syncthreads();
+  hanging_all<K, true>(cb, sm_mask, hang ? nc : 0);  // C_e^T
+
+  // G_e^T into the tile accumulator, sub-colour by sub-colour
+  for (int sc = 0; sc < ti.n_sub; ++sc) {
+#pragma unroll 1
+    for (int t = threadIdx.x; t < nl; t += BLOCK) {
+      const int j = t / N2;
+      if (sm_sub[j] != sc) continue;
+      const int r = t - j * N2, b = r % N, c = r / N;
+      const uint16_t* ls = sm_meta[sm_cell[j]].ls;
+      const T* in = cb + j * N3 + N * r;
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        int slot, off;
+        node_slot<K>(a, b, c, slot, off);
+        const uint16_t l = ls[slot];
+        if (l != LS_NONE) ys[l + off] += in[a];
+      }
+    }
+    __syncthreads();
+  }
+  write_tile_dofs(A.dst, A.halo, ys, ti, A.add);
+}
+
+// ---------------------------------------------------------------------------
 // fp32 operator, one cell per thread, values in registers
 // ---------------------------------------------------------------------------
 
@@ -762,6 +924,13 @@ void launch_cells_nt(const CellLaunch& L, CellArgs<T> A, size_t sm, cudaStream_t
 template <int K, typename T, int MODE>
 void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
   const size_t sm = smem_layout<T>((K + 1) * (K + 1) * (K + 1), L.tc, L.max_local).total;
+  if (MODE == MODE_VMULT && L.tc <= CHUNK && (sizeof(T) == 8 || L.threads == BLOCK)) {
+    ensure_smem(vmult_lines<K, T>, sm);
+    vmult_lines<K, T><<<L.n_tiles, BLOCK, sm, s>>>(A);
+    note_launches(1);
+    run_halo<T>(L, A.dst, s);
+    return;
+  }
   // the thread count is a tuning parameter of the fp32 operator only
   const int nt = (MODE == MODE_VMULT && sizeof(T) == 4) ? L.threads : BLOCK;
   if (nt == 128)
