@@ -393,7 +393,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": "cell_kernel<4,float> line-parallel tile kernel + halo pass "
+                         "kernel": "vmult_lines<4,float> line-parallel tile kernel + halo pass "
                                    "(fine-level fp32 operator, 32-cell tiles)",
                          "peak_kind": peak_kind, "bytes_per_dof": BYTES_PER_DOF["fp32"],
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the tile kernel, "

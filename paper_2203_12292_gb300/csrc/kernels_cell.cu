@@ -259,11 +259,17 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
   T* ys = reinterpret_cast<T*>(smem + SL.ys);
   __shared__ uint8_t sm_sub[CHUNK];
   __shared__ T s_lab[N2];
+  __shared__ uint16_t s_so[N3];  // per local node: entity slot | offset << 5
   const DevTables<T>& tb = tab<T>(K);
 
   const TileInfo ti = A.tiles[blockIdx.x];
   const int nc = ti.n_cells;  // <= CHUNK
   const int nl = nc * N2;     // x-lines of the tile
+  for (int n = threadIdx.x; n < N3; n += BLOCK) {
+    int slot, off;
+    node_slot<K>(n % N, (n / N) % N, n / N2, slot, off);
+    s_so[n] = (uint16_t)(slot | (off << 5));
+  }
   const int nloc = ti.n_owned + ti.n_foreign;
   load_meta(sm_meta, A.meta, ti.cell_begin, nc);
   load_tile_dofs(xs, A.src, A.foreign, ti);
@@ -288,15 +294,13 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
 #pragma unroll 1
   for (int t = threadIdx.x; t < nl; t += BLOCK) {
     const int j = t / N2, r = t - j * N2;
-    const int b = r % N, c = r / N;
     const uint16_t* ls = sm_meta[sm_cell[j]].ls;
     T* out = cb + j * N3 + N * r;
 #pragma unroll
     for (int a = 0; a < N; ++a) {
-      int slot, off;
-      node_slot<K>(a, b, c, slot, off);
-      const uint16_t l = ls[slot];
-      out[a] = (l == LS_NONE) ? T(0) : xs[l + off];
+      const int so = s_so[N * r + a];
+      const uint16_t l = ls[so & 31];
+      out[a] = (l == LS_NONE) ? T(0) : xs[l + (so >> 5)];
     }
   }
   __syncthreads();
@@ -383,15 +387,14 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
     for (int t = threadIdx.x; t < nl; t += BLOCK) {
       const int j = t / N2;
       if (sm_sub[j] != sc) continue;
-      const int r = t - j * N2, b = r % N, c = r / N;
+      const int r = t - j * N2;
       const uint16_t* ls = sm_meta[sm_cell[j]].ls;
       const T* in = cb + j * N3 + N * r;
 #pragma unroll
       for (int a = 0; a < N; ++a) {
-        int slot, off;
-        node_slot<K>(a, b, c, slot, off);
-        const uint16_t l = ls[slot];
-        if (l != LS_NONE) ys[l + off] += in[a];
+        const int so = s_so[N * r + a];
+        const uint16_t l = ls[so & 31];
+        if (l != LS_NONE) ys[l + (so >> 5)] += in[a];
       }
     }
     __syncthreads();

@@ -203,6 +203,8 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
   __shared__ uint16_t sm_cell[TP];
   __shared__ uint32_t sm_own[TP * 8];          // ownership masks of the fine cells
   __shared__ int32_t sm_gs[TP * 8 * NSLOT];    // their global slot starts (-1: none)
+  __shared__ uint16_t s_so[N3];                // per local node: entity slot | offset << 5
+  __shared__ uint16_t s_e3[8 * N3];            // child q, node n -> position in the 2k+1 lattice
   extern __shared__ __align__(16) unsigned char smem[];
   CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem);
   T* cb = reinterpret_cast<T*>(smem + (size_t)A.tc * sizeof(CellMeta));
@@ -218,6 +220,16 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
     for (int i = threadIdx.x; i < nc * 4; i += blockDim.x) s[i] = g[i];
   }
   for (int i = threadIdx.x; i < ti.n_owned + ti.n_foreign; i += blockDim.x) ys[i] = T(0);
+  for (int i = threadIdx.x; i < 8 * N3; i += blockDim.x) {
+    const int q = i / N3, n = i - q * N3;
+    const int a = n % N, b = (n / N) % N, c = n / (N * N);
+    if (q == 0) {
+      int slot, off;
+      node_slot<K>(a, b, c, slot, off);
+      s_so[n] = (uint16_t)(slot | (off << 5));
+    }
+    s_e3[i] = (uint16_t)(((q & 1) * K + a) + M * ((((q >> 1) & 1) * K + b) + M * ((q >> 2) * K + c)));
+  }
   for (int c0 = 0; c0 < nc; c0 += TP) {
     const int np = min(TP, nc - c0);
     __syncthreads();
@@ -252,19 +264,14 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
         const int t = t0 + u * BLOCK;
         dst[u] = -1;
         if (t < ntot) {
-          const int j = t / (8 * N3), r = t - j * 8 * N3;
+          const int j = t / (8 * N3), r = t - j * 8 * N3;  // r = q N3 + n
           const int q = r / N3, n = r - q * N3;
-          const int a = n % N, b = (n / N) % N, c = n / (N * N);
-          int slot, off;
-          node_slot<K>(a, b, c, slot, off);
+          const int so = s_so[n], slot = so & 31;
           if ((sm_own[j * 8 + q] >> slot) & 1u) {
-            val[u] = A.src[sm_gs[(j * 8 + q) * NSLOT + slot] + off];
-            if (sm_ref[j]) {
-              const int gi = (q & 1) * K + a, gj = ((q >> 1) & 1) * K + b, gk = (q >> 2) * K + c;
-              dst[u] = j * M3 + gi + M * (gj + M * gk);
-            } else {
-              dst[u] = TP * M3 + j * N3 + n;  // marks the identity category: into cb
-            }
+            val[u] = A.src[sm_gs[(j * 8 + q) * NSLOT + slot] + (so >> 5)];
+            // refined: position in the children's 2k+1 lattice; else the
+            // identity category (marked by the offset TP M3): into cb
+            dst[u] = sm_ref[j] ? j * M3 + s_e3[r] : TP * M3 + j * N3 + n;
           }
         }
       }

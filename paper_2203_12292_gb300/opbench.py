@@ -1,11 +1,14 @@
-"""Operator microbenchmark: time the matrix-free operator of one level.
+"""Kernel microbenchmark: time one operation of one level.
 
     python -m paper_2203_12292_gb300.opbench [--workload q4octant] [--level -1]
-        [--dtype f32|f64] [--reps 20] [--tile-cells 0] [--cell-kernel 0|1|2]
+        [--op vmult|restrict|prolong|mlp] [--dtype f32|f64] [--reps 20]
+        [--tile-cells 0] [--cell-kernel 0|1|2] [--cell-threads 0]
 
-The timed applications run inside an NVTX range named "opbench", so a
-profiler can select exactly them.  Prints one JSON line (ms per application,
-GDoF/s).
+vmult: the level's operator; restrict/prolong: the transfer between the
+level and the next coarser one; mlp: the learned-smoother correction (Q4,
+random initial network).  The timed calls run inside an NVTX range named
+"opbench", so a profiler can select exactly them.  Prints one JSON line
+(ms per call, GDoF/s of the level's free DoFs).
 """
 from __future__ import annotations
 
@@ -30,6 +33,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="q4octant", choices=sorted(WORKLOADS))
     ap.add_argument("--level", type=int, default=-1)
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--op", default="vmult", choices=["vmult", "restrict", "prolong", "mlp"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--tile-cells", type=int, default=0)
     ap.add_argument("--cell-kernel", type=int, default=0, choices=[0, 1, 2])
@@ -37,7 +41,9 @@ def main(argv=None):
     a = ap.parse_args(argv)
     import torch
 
-    from . import Mesh, Multigrid, build as b
+    import synth as sy
+
+    from . import MLP, Mesh, Multigrid, build as b
 
     b.build()
     w = WORKLOADS[a.workload]
@@ -49,20 +55,36 @@ def main(argv=None):
     dt = torch.float32 if a.dtype == "f32" else torch.float64
     x = torch.rand(n, dtype=dt, device="cuda")
     y = torch.empty_like(x)
+    xc = torch.rand(mg.n_free(max(lev - 1, 0)), dtype=dt, device="cuda")
+    if a.op == "mlp":
+        net = MLP(*sy.mlp_shape(w.degree))
+        net.set_params(torch.tensor(sy.mlp_init(*sy.mlp_shape(w.degree), 1), dtype=torch.float32, device="cuda"))
+
+    def call():
+        if a.op == "vmult":
+            mg.vmult(lev, x, y)
+        elif a.op == "restrict":
+            mg.restrict_add(lev, x, xc)
+        elif a.op == "prolong":
+            mg.prolongate_add(lev, xc, y)
+        else:
+            mg.mlp_correct(lev, net, x, y)
+
     for _ in range(3):
-        mg.vmult(lev, x, y)
+        call()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("opbench")
     e0.record()
     for _ in range(a.reps):
-        mg.vmult(lev, x, y)
+        call()
     e1.record()
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / a.reps
     info = mg.level_info(lev)
-    print(json.dumps({"workload": w.name, "level": lev, "dtype": a.dtype, "n_free": n, "cells": info.n_cells,
+    print(json.dumps({"workload": w.name, "op": a.op, "level": lev, "dtype": a.dtype, "n_free": n,
+                      "cells": info.n_cells,
                       "tiles": info.n_tiles, "halo_dofs": info.n_halo, "tile_cells": info.tile_cells,
                       "cell_kernel": a.cell_kernel, "cell_threads": a.cell_threads,
                       "ms": ms, "gdofs": n / ms / 1e6}))
