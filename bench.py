@@ -193,7 +193,9 @@ def run_batch(g, seed: int = 12292, n: int = 256):
     for k, d, e, _ in rec:
         if (d, e) not in meshes:
             meshes[(d, e)] = g.Mesh.from_recipe(synth.cube_octant(d, e))
-    probe = g.Mesh.from_recipe(synth.cube_octant(4, 1))
+    # probe large enough that every candidate tile size is kept on its finest
+    # level (61,440 cells; smaller levels halve their tiles)
+    probe = g.Mesh.from_recipe(synth.cube_octant(5, 1))
     tuning = {}
     for k in sorted({r[0] for r in rec}):
         best, _ = g.autotune(probe, k, True, 10)
