@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
   uint16_t* sm_cell = reinterpret_cast<uint16_t*>(smem + SL.cell);
   T* cb = reinterpret_cast<T*>(smem + SL.cb);
   T* xs = reinterpret_cast<T*>(smem + SL.xs);
-  T* ys = reinterpret_cast<T*>(smem + SL.ys);
+  T* ys = xs;  // the accumulator reuses the input buffer once the gather is done
   __shared__ uint8_t sm_sub[CHUNK];
   __shared__ T s_lab[N2];
   __shared__ uint16_t s_so[N3];  // per local node: entity slot | offset << 5
@@ -273,7 +273,6 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
   const int nloc = ti.n_owned + ti.n_foreign;
   load_meta(sm_meta, A.meta, ti.cell_begin, nc);
   load_tile_dofs(xs, A.src, A.foreign, ti);
-  for (int i = threadIdx.x; i < nloc; i += BLOCK) ys[i] = T(0);
   constexpr bool EO = sizeof(T) == 8;  // fp64: even-odd sweeps (FP64 pipe bound), modes in mode order
   for (int r = threadIdx.x; r < N2; r += BLOCK)
     s_lab[r] = EO ? tb.lame[r % N] + tb.lame[r / N] : tb.lam[r % N] + tb.lam[r / N];
@@ -304,6 +303,7 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
     }
   }
   __syncthreads();
+  for (int i = threadIdx.x; i < nloc; i += BLOCK) ys[i] = T(0);  // ordered before the scatter by the sweeps' barriers
   hanging_all<K, false>(cb, sm_mask, hang ? nc : 0);  // C_e (no work without hanging cells)
 
   // S^T Q S: x, y forward, z forward/scale/backward, y, x backward
@@ -928,8 +928,10 @@ template <int K, typename T, int MODE>
 void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
   const size_t sm = smem_layout<T>((K + 1) * (K + 1) * (K + 1), L.tc, L.max_local).total;
   if (MODE == MODE_VMULT && L.tc <= CHUNK && (sizeof(T) == 8 || L.threads == BLOCK)) {
-    ensure_smem(vmult_lines<K, T>, sm);
-    vmult_lines<K, T><<<L.n_tiles, BLOCK, sm, s>>>(A);
+    // vmult_lines keeps one tile-DoF buffer (input, then accumulator)
+    const size_t sm1 = sm - (size_t)L.max_local * sizeof(T);
+    ensure_smem(vmult_lines<K, T>, sm1);
+    vmult_lines<K, T><<<L.n_tiles, BLOCK, sm1, s>>>(A);
     note_launches(1);
     run_halo<T>(L, A.dst, s);
     return;
