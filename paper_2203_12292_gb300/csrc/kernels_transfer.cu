@@ -104,9 +104,15 @@ template <int K, typename T>
 __global__ void __launch_bounds__(BLOCK) prolong_h(TArgs<T> A) {
   constexpr int N = K + 1, N3 = N * N * N, M = 2 * K + 1, M3 = M * M * M;
   constexpr int S1 = M * N * N, S2 = M * M * N;
+  constexpr int RG = 8;  // loads in flight per thread
   __shared__ uint16_t sm_mask[TP];
   __shared__ uint8_t sm_ref[TP];
   __shared__ int32_t sm_fine[TP];
+  __shared__ int32_t sm_gsc[TP * NSLOT];       // coarse cells' global slot starts
+  __shared__ uint32_t sm_own[TP * 8];          // ownership masks of the fine cells
+  __shared__ int32_t sm_gs[TP * 8 * NSLOT];    // their global slot starts (-1: none)
+  __shared__ uint16_t s_so[N3];                // per local node: entity slot | offset << 5
+  __shared__ uint16_t s_e3[8 * N3];            // child q, node n -> position in the 2k+1 lattice
   extern __shared__ __align__(16) unsigned char smem[];
   T* cb = reinterpret_cast<T*>(smem);
   T* e1 = cb + TP * N3;
@@ -119,12 +125,42 @@ __global__ void __launch_bounds__(BLOCK) prolong_h(TArgs<T> A) {
     sm_ref[c] = A.refined[c0 + c];
     sm_fine[c] = A.fine_of[c0 + c];
   }
-  for (int t = threadIdx.x; t < nc * N3; t += blockDim.x) {
-    const int cell = t / N3, n = t - cell * N3;
-    int slot, off;
-    node_slot<K>(n % N, (n / N) % N, n / (N * N), slot, off);
-    const int32_t g = A.gstart_c[(size_t)(c0 + cell) * NSLOT + slot];
-    cb[t] = g < 0 ? T(0) : A.src[g + off];
+  for (int i = threadIdx.x; i < 8 * N3; i += blockDim.x) {
+    const int q = i / N3, n = i - q * N3;
+    const int a = n % N, b = (n / N) % N, c = n / (N * N);
+    if (q == 0) {
+      int slot, off;
+      node_slot<K>(a, b, c, slot, off);
+      s_so[n] = (uint16_t)(slot | (off << 5));
+    }
+    s_e3[i] = (uint16_t)(((q & 1) * K + a) + M * ((((q >> 1) & 1) * K + b) + M * ((q >> 2) * K + c)));
+  }
+  for (int t = threadIdx.x; t < nc * NSLOT; t += blockDim.x) sm_gsc[t] = A.gstart_c[(size_t)c0 * NSLOT + t];
+  __syncthreads();
+  // the fine cells' slot starts and ownership (children of a refined cell are consecutive)
+  for (int t = threadIdx.x; t < nc * 8 * NSLOT; t += blockDim.x) {
+    const int jq = t / NSLOT, slot = t - jq * NSLOT, j = jq >> 3, q = jq & 7;
+    const bool use = sm_ref[j] || q == 0;
+    const int f = sm_fine[j] + q;
+    sm_gs[t] = use ? A.gstart_f[(size_t)f * NSLOT + slot] : -1;
+    if (slot == 0) sm_own[jq] = use ? A.own_f[f] : 0u;
+  }
+  // G^(c): the coarse values (RG loads in flight per thread)
+  for (int t0 = threadIdx.x; t0 < nc * N3; t0 += RG * BLOCK) {
+    T v[RG];
+#pragma unroll
+    for (int u = 0; u < RG; ++u) {
+      const int t = t0 + u * BLOCK;
+      v[u] = T(0);
+      if (t < nc * N3) {
+        const int cell = t / N3, n = t - cell * N3, so = s_so[n];
+        const int32_t g = sm_gsc[cell * NSLOT + (so & 31)];
+        if (g >= 0) v[u] = A.src[g + (so >> 5)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RG; ++u)
+      if (t0 + u * BLOCK < nc * N3) cb[t0 + u * BLOCK] = v[u];
   }
   __syncthreads();
   hanging_all<K, false>(cb, sm_mask, nc);
@@ -134,27 +170,29 @@ __global__ void __launch_bounds__(BLOCK) prolong_h(TArgs<T> A) {
   __syncthreads();
   tsweep<K, 0, N, M, 2, false>(e2, e3, M, M, N, nc, S2, M3, sm_ref);
   __syncthreads();
-  for (int t = threadIdx.x; t < nc * 8 * N3; t += blockDim.x) {
-    const int cell = t / (8 * N3), r = t - cell * 8 * N3;
-    const int q = r / N3, n = r - q * N3;
-    const int a = n % N, b = (n / N) % N, c = n / (N * N);
-    T val;
-    int f;
-    if (sm_ref[cell]) {
-      f = sm_fine[cell] + q;
-      const int gi = (q & 1) * K + a, gj = ((q >> 1) & 1) * K + b, gk = (q >> 2) * K + c;
-      val = e3[cell * M3 + gi + M * (gj + M * gk)];
-    } else {
-      if (q) continue;
-      f = sm_fine[cell];
-      val = cb[cell * N3 + n];
+  // owner-selected additions to the fine vector (RG read-modify-writes in flight)
+  const int ntot = nc * 8 * N3;
+  for (int t0 = threadIdx.x; t0 < ntot; t0 += RG * BLOCK) {
+    int idx[RG];
+    T val[RG], old[RG];
+#pragma unroll
+    for (int u = 0; u < RG; ++u) {
+      const int t = t0 + u * BLOCK;
+      idx[u] = -1;
+      if (t < ntot) {
+        const int j = t / (8 * N3), r = t - j * 8 * N3;  // r = q N3 + n
+        const int q = r / N3, n = r - q * N3;
+        const int so = s_so[n], slot = so & 31;
+        if ((sm_own[j * 8 + q] >> slot) & 1u) {
+          idx[u] = sm_gs[(j * 8 + q) * NSLOT + slot] + (so >> 5);
+          val[u] = sm_ref[j] ? e3[j * M3 + s_e3[r]] : cb[j * N3 + n];
+        }
+      }
+      if (idx[u] >= 0) old[u] = A.dst[idx[u]];
     }
-    int slot, off;
-    node_slot<K>(a, b, c, slot, off);
-    if ((A.own_f[f] >> slot) & 1u) {
-      const int32_t g = A.gstart_f[(size_t)f * NSLOT + slot];
-      A.dst[g + off] += val;
-    }
+#pragma unroll
+    for (int u = 0; u < RG; ++u)
+      if (idx[u] >= 0) A.dst[idx[u]] = old[u] + val[u];
   }
 }
 

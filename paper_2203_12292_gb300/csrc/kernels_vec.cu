@@ -96,16 +96,36 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return sh[0];
 }
 
-// each block sums a fixed contiguous chunk: the result does not depend on
-// scheduling
-__global__ void __launch_bounds__(BLOCK) dot_partial(const double* x, const double* y, int64_t n, double* part) {
-  __shared__ double sh[BLOCK];
+// reductions of the CG vectors: DOT_BLOCKS blocks of RB threads (two per SM,
+// full occupancy), every thread keeps RU partial sums so that RU loads per
+// array are in flight
+constexpr int RB = 1024, RU = 4;
+
+__device__ __forceinline__ double block_sum_rb(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = RB / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// each block sums a fixed contiguous chunk in a fixed order: the result does
+// not depend on scheduling
+__global__ void __launch_bounds__(RB, 2) dot_partial(const double* x, const double* y, int64_t n, double* part) {
+  __shared__ double sh[RB];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
-  double s = 0.0;
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += BLOCK) s += x[i] * y[i];
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  double s[RU] = {};
+  int64_t i = i0 + threadIdx.x;
+  for (; i + (RU - 1) * RB < i1; i += RU * RB) {
+#pragma unroll
+    for (int u = 0; u < RU; ++u) s[u] += x[i + u * RB] * y[i + u * RB];
+  }
+  for (; i < i1; i += RB) s[0] += x[i] * y[i];
+  const double v = block_sum_rb((s[0] + s[1]) + (s[2] + s[3]), sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
 }
 
 __global__ void __launch_bounds__(BLOCK) dot_final(const double* part, int np, double* scal, int slot, int op) {
@@ -131,22 +151,48 @@ __global__ void __launch_bounds__(BLOCK) dot_final(const double* part, int np, d
   }
 }
 
-// x += alpha p, r -= alpha q, partial sums of r.r
-__global__ void __launch_bounds__(BLOCK) cg_xr_kernel(double* x, double* r, const double* p, const double* q,
+// x += alpha p, r -= alpha q, partial sums of r.r: DOT_BLOCKS blocks of XB
+// threads, XU elements per thread in flight
+constexpr int XB = 512, XU = 4;
+
+__global__ void __launch_bounds__(XB, 2) cg_xr_kernel(double* x, double* r, const double* p, const double* q,
                                                       const double* scal, int64_t n, double* part) {
-  __shared__ double sh[BLOCK];
+  __shared__ double sh[XB];
   const double alpha = scal[3];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
-  double s = 0.0;
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += BLOCK) {
+  double s[XU] = {};
+  int64_t i = i0 + threadIdx.x;
+  for (; i + (XU - 1) * XB < i1; i += XU * XB) {
+    double xv[XU], rv[XU], pv[XU], qv[XU];
+#pragma unroll
+    for (int u = 0; u < XU; ++u) {
+      xv[u] = x[i + u * XB];
+      rv[u] = r[i + u * XB];
+      pv[u] = p[i + u * XB];
+      qv[u] = q[i + u * XB];
+    }
+#pragma unroll
+    for (int u = 0; u < XU; ++u) {
+      x[i + u * XB] = xv[u] + alpha * pv[u];
+      const double ri = rv[u] - alpha * qv[u];
+      r[i + u * XB] = ri;
+      s[u] += ri * ri;
+    }
+  }
+  for (; i < i1; i += XB) {
     x[i] += alpha * p[i];
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
-    s += ri * ri;
+    s[0] += ri * ri;
   }
-  s = block_sum(s, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  sh[threadIdx.x] = (s[0] + s[1]) + (s[2] + s[3]);
+  __syncthreads();
+  for (int h = XB / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
 __global__ void cg_p_kernel(double* p, const double* z, const double* scal, int64_t n) {
@@ -297,13 +343,13 @@ void launch_coarse_solve(bool fp64, const double* Ainv, int n, const void* b, vo
 
 void launch_dot(const double* x, const double* y, int64_t n, double* scratch, double* scal, int slot, int op,
                 cudaStream_t s) {
-  { dot_partial<<<DOT_BLOCKS, BLOCK, 0, s>>>(x, y, n, scratch); note_launches(1); }
+  { dot_partial<<<DOT_BLOCKS, RB, 0, s>>>(x, y, n, scratch); note_launches(1); }
   { dot_final<<<1, BLOCK, 0, s>>>(scratch, DOT_BLOCKS, scal, slot, op); note_launches(1); }
 }
 
 void launch_cg_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, int64_t n,
                          double* scratch, double* scal_out, cudaStream_t s) {
-  { cg_xr_kernel<<<DOT_BLOCKS, BLOCK, 0, s>>>(x, r, p, q, scal, n, scratch); note_launches(1); }
+  { cg_xr_kernel<<<DOT_BLOCKS, XB, 0, s>>>(x, r, p, q, scal, n, scratch); note_launches(1); }
   { dot_final<<<1, BLOCK, 0, s>>>(scratch, DOT_BLOCKS, scal_out, 2, DOT_STORE); note_launches(1); }
 }
 
