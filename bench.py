@@ -55,10 +55,11 @@ METRIC = "fine-level vmult GDoF/s; solve time to 1e-8 rel. res., mixed/learned v
 # destination vector plus the per-cell metadata (roofline model of the
 # workload, per free DoF)
 BYTES_PER_DOF = {"fp32": 9.8, "fp64": 17.8}
-# DRAM bytes (read + write) of one launch of the fine-level tile kernel on
-# this workload from an ncu capture (profiles/); 0 = not captured for the
-# current kernel
-VMULT_TRAFFIC_BYTES = 0.0
+# DRAM bytes (read + write) of one launch of the fine-level tile kernel
+# vmult_lines<4,float> on this workload, from the ncu capture summarised in
+# profiles/vmult_lines_q4_octant_fp32.md (114.8 MB read + 53.9 MB written);
+# set to 0 (reported as null) when the kernel changes until it is re-captured
+VMULT_TRAFFIC_BYTES = 168.6e6
 SAMPLE = synth.cube_octant(4, 2)  # 1/8 of the workload's cells, same recipe family
 
 
