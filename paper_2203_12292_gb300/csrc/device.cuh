@@ -34,6 +34,9 @@ struct DevTables {
 // device code); each one is filled by that unit's upload function
 static __constant__ DevTables<double> c_td[KMAX + 1];
 static __constant__ DevTables<float> c_tf[KMAX + 1];
+// low parts of the fp64 tables: c_tf + c_tflo represents every entry to
+// about 2^-48 (double-float constants)
+static __constant__ DevTables<float> c_tflo[KMAX + 1];
 
 template <typename T>
 __device__ __forceinline__ const DevTables<T>& tab(int k);
@@ -107,13 +110,26 @@ static inline void fill_tables(DevTables<double>* td, DevTables<float>* tf) {
   }
 }
 
+// host: low parts tflo = fp32(td - tf) of the fp64 tables
+static inline void fill_tables_lo(const DevTables<double>* td, const DevTables<float>* tf, DevTables<float>* lo) {
+  for (int k = 0; k <= KMAX; ++k) {
+    const double* d = reinterpret_cast<const double*>(&td[k]);
+    const float* f = reinterpret_cast<const float*>(&tf[k]);
+    float* l = reinterpret_cast<float*>(&lo[k]);
+    for (size_t i = 0; i < sizeof(DevTables<double>) / sizeof(double); ++i) l[i] = (float)(d[i] - (double)f[i]);
+  }
+}
+
 #define GCMG_DEFINE_UPLOAD(name)                                             \
   void name() {                                                              \
     static DevTables<double> td[KMAX + 1];                                   \
     static DevTables<float> tf[KMAX + 1];                                    \
+    static DevTables<float> tl[KMAX + 1];                                    \
     fill_tables(td, tf);                                                     \
+    fill_tables_lo(td, tf, tl);                                              \
     cudaMemcpyToSymbol(c_td, td, sizeof(td));                                \
     cudaMemcpyToSymbol(c_tf, tf, sizeof(tf));                                \
+    cudaMemcpyToSymbol(c_tflo, tl, sizeof(tl));                              \
   }
 
 // entity slot and offset of local node (a,b,c) of a degree-K cell: the slot
@@ -446,6 +462,166 @@ __device__ __forceinline__ void cell_laplace(T* cb, const T* sm_h, int ncells) {
     sweep_B<K, 1, true>(cb, ncells);
     __syncthreads();
     sweep_B<K, 0, true>(cb, ncells);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// double-float arithmetic (a value = hi + lo, two floats, about 48 bits):
+// the fp64 operator runs on the FP32 pipe, several times wider than the FP64
+// pipe of GB300.  Error-free transformations (Dekker, Knuth two-sum, and the
+// fused multiply-add product error); explicit _rn intrinsics keep the
+// compiler from contracting the roundings they rely on.
+// ---------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_from(double x) {
+  const float h = __double2float_rn(x);
+  return df{h, __double2float_rn(x - (double)h)};
+}
+
+__device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df df_norm(float hi, float lo) {  // |lo| small against |hi|
+  const float s = __fadd_rn(hi, lo);
+  return df{s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float z = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, z)), __fsub_rn(b.hi, z));
+  return df_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+
+// a * (ch + cl)
+__device__ __forceinline__ df df_mulc(df a, float ch, float cl) {
+  const float p = __fmul_rn(a.hi, ch);
+  float e = __fmaf_rn(a.hi, ch, -p);
+  e = __fmaf_rn(a.hi, cl, e);
+  e = __fmaf_rn(a.lo, ch, e);
+  return df_norm(p, e);
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) { return df_mulc(a, b.hi, b.lo); }
+
+// s + a * (ch + cl)
+__device__ __forceinline__ df df_fma(df s, df a, float ch, float cl) { return df_add(s, df_mulc(a, ch, cl)); }
+
+// 1D transforms on df lines (BASE + i STRIDE) with the fp64 tables of degree K
+template <int K, int STRIDE, bool TRANS>
+__device__ __forceinline__ void df_line_apply(df* p, const float (&Mh)[NMAX][NMAX], const float (&Ml)[NMAX][NMAX]) {
+  constexpr int N = K + 1;
+  df v[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) v[a] = p[a * STRIDE];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    df s{0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < N; ++a) s = TRANS ? df_fma(s, v[a], Mh[a][i], Ml[a][i]) : df_fma(s, v[a], Mh[i][a], Ml[i][a]);
+    p[i * STRIDE] = s;
+  }
+}
+
+// even-odd forward (B, nodal -> modes in mode order) and backward (B^T)
+template <int K, int STRIDE>
+__device__ __forceinline__ void df_eo_forward(df* u) {
+  constexpr int N = K + 1, NH = N / 2, NE = (N + 1) / 2;
+  const float(&Bh)[NMAX][NMAX] = c_tf[K].Be;
+  const float(&Bl)[NMAX][NMAX] = c_tflo[K].Be;
+  df e[NE], o[NH > 0 ? NH : 1];
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    e[j] = df_add(u[j * STRIDE], u[(N - 1 - j) * STRIDE]);
+    o[j] = df_sub(u[j * STRIDE], u[(N - 1 - j) * STRIDE]);
+  }
+  if (N % 2) e[NH] = u[NH * STRIDE];
+#pragma unroll
+  for (int r = 0; r < NE; ++r) {
+    df s = (N % 2) ? df_mulc(e[NH], Bh[r][NH], Bl[r][NH]) : df{0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < NH; ++j) s = df_fma(s, e[j], Bh[r][j], Bl[r][j]);
+    u[r * STRIDE] = s;
+  }
+#pragma unroll
+  for (int r = 0; r < NH; ++r) {
+    df s{0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < NH; ++j) s = df_fma(s, o[j], Bh[NE + r][j], Bl[NE + r][j]);
+    u[(NE + r) * STRIDE] = s;
+  }
+}
+
+template <int K, int STRIDE>
+__device__ __forceinline__ void df_eo_backward(df* u) {
+  constexpr int N = K + 1, NH = N / 2, NE = (N + 1) / 2;
+  const float(&Bh)[NMAX][NMAX] = c_tf[K].Be;
+  const float(&Bl)[NMAX][NMAX] = c_tflo[K].Be;
+  df E[NE], O[NH > 0 ? NH : 1];
+#pragma unroll
+  for (int j = 0; j < NE; ++j) {
+    df s{0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < NE; ++r) s = df_fma(s, u[r * STRIDE], Bh[r][j], Bl[r][j]);
+    E[j] = s;
+  }
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    df s{0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < NH; ++r) s = df_fma(s, u[(NE + r) * STRIDE], Bh[NE + r][j], Bl[NE + r][j]);
+    O[j] = s;
+  }
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    u[j * STRIDE] = df_add(E[j], O[j]);
+    u[(N - 1 - j) * STRIDE] = df_sub(E[j], O[j]);
+  }
+  if (N % 2) u[NH * STRIDE] = E[NH];
+}
+
+// hanging-node interpolation C_e (TRANS: C_e^T) on df cell buffers, one
+// direction for all cells of the block
+template <int K, int D, bool TRANS>
+__device__ __forceinline__ void df_hanging_dir(df* cb, const uint16_t* sm_mask, int ncells) {
+  constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
+  for (int t = threadIdx.x; t < ncells * N2; t += blockDim.x) {
+    const int cell = t / N2, r = t - cell * N2;
+    const uint16_t m = sm_mask[cell];
+    if (!(m & MASK_HANG)) continue;
+    int base, u, v;
+    line_geom<N, D>(r, base, u, v);
+    if (!line_hangs<K, D>(m, u, v)) continue;
+    df* p = cb + cell * N3 + base;
+    if ((m >> D) & 1)
+      df_line_apply<K, line_stride<N, D>(), TRANS>(p, c_tf[K].I[1], c_tflo[K].I[1]);
+    else
+      df_line_apply<K, line_stride<N, D>(), TRANS>(p, c_tf[K].I[0], c_tflo[K].I[0]);
+  }
+}
+
+template <int K, bool TRANS>
+__device__ __forceinline__ void df_hanging_all(df* cb, const uint16_t* sm_mask, int ncells) {
+  if (!TRANS) {
+    df_hanging_dir<K, 0, false>(cb, sm_mask, ncells);
+    __syncthreads();
+    df_hanging_dir<K, 1, false>(cb, sm_mask, ncells);
+    __syncthreads();
+    df_hanging_dir<K, 2, false>(cb, sm_mask, ncells);
+    __syncthreads();
+  } else {
+    df_hanging_dir<K, 2, true>(cb, sm_mask, ncells);
+    __syncthreads();
+    df_hanging_dir<K, 1, true>(cb, sm_mask, ncells);
+    __syncthreads();
+    df_hanging_dir<K, 0, true>(cb, sm_mask, ncells);
     __syncthreads();
   }
 }

@@ -403,6 +403,140 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
 }
 
 // ---------------------------------------------------------------------------
+// fp64 operator in double-float arithmetic (fp64 vectors, all arithmetic of
+// the cell pipeline on the FP32 pipe in hi + lo pairs, about 48 bits): the
+// structure of vmult_lines with the tile buffer and the cell buffers in df;
+// values are converted once on entry to and once on exit from the tile.
+// ---------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(BLOCK) vmult_lines_df(CellArgs<double> A) {
+  constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
+  static_assert(sizeof(df) == sizeof(double), "df buffers reuse the fp64 layout");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SmemLayout SL = smem_layout<double>(N3, A.tc, A.max_local);
+  CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem + SL.meta);
+  df* sm_h = reinterpret_cast<df*>(smem + SL.h);
+  uint16_t* sm_mask = reinterpret_cast<uint16_t*>(smem + SL.mask);
+  uint16_t* sm_cell = reinterpret_cast<uint16_t*>(smem + SL.cell);
+  df* cb = reinterpret_cast<df*>(smem + SL.cb);
+  df* xs = reinterpret_cast<df*>(smem + SL.xs);
+  df* ys = xs;  // the accumulator reuses the input buffer once the gather is done
+  __shared__ uint8_t sm_sub[CHUNK];
+  __shared__ df s_lam3[N3];      // lam_a + lam_b + lam_c in mode order
+  __shared__ uint16_t s_so[N3];  // per local node: entity slot | offset << 5
+
+  const TileInfo ti = A.tiles[blockIdx.x];
+  const int nc = ti.n_cells;  // <= CHUNK
+  const int nl = nc * N2;
+  const int nloc = ti.n_owned + ti.n_foreign;
+  for (int n = threadIdx.x; n < N3; n += BLOCK) {
+    int slot, off;
+    node_slot<K>(n % N, (n / N) % N, n / N2, slot, off);
+    s_so[n] = (uint16_t)(slot | (off << 5));
+    s_lam3[n] = df_from(c_td[K].lam3[n]);
+  }
+  load_meta(sm_meta, A.meta, ti.cell_begin, nc);
+  {
+    const double* src = A.src + ti.dof_begin;
+    for (int i = threadIdx.x; i < ti.n_owned; i += BLOCK) xs[i] = df_from(src[i]);
+    const int32_t* fl = A.foreign + ti.foreign_begin;
+    for (int i = threadIdx.x; i < ti.n_foreign; i += BLOCK) xs[ti.n_owned + i] = df_from(A.src[fl[i]]);
+  }
+  __syncthreads();
+  int hang = 0;
+  if (threadIdx.x < nc) {
+    const int cell = A.perm[ti.cell_begin + threadIdx.x];
+    const CellMeta& m = sm_meta[cell];
+    sm_cell[threadIdx.x] = (uint16_t)cell;
+    sm_mask[threadIdx.x] = m.mask;
+    sm_sub[threadIdx.x] = m.sub;
+    sm_h[threadIdx.x] = df_from(ldexp(A.dom, -(int)m.level));
+    hang = (m.mask & MASK_HANG) != 0;
+  }
+  hang = __syncthreads_or(hang);
+
+  // G_e
+#pragma unroll 1
+  for (int t = threadIdx.x; t < nl; t += BLOCK) {
+    const int j = t / N2, r = t - j * N2;
+    const uint16_t* ls = sm_meta[sm_cell[j]].ls;
+    df* out = cb + j * N3 + N * r;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      const int so = s_so[N * r + a];
+      const uint16_t l = ls[so & 31];
+      out[a] = (l == LS_NONE) ? df{0.f, 0.f} : xs[l + (so >> 5)];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nloc; i += BLOCK) ys[i] = df{0.f, 0.f};
+  df_hanging_all<K, false>(cb, sm_mask, hang ? nc : 0);  // C_e
+
+  // S^T Q S with even-odd sweeps
+#pragma unroll 1
+  for (int t = threadIdx.x; t < nl; t += BLOCK) df_eo_forward<K, 1>(cb + (t / N2) * N3 + N * (t % N2));
+  __syncthreads();
+#pragma unroll 1
+  for (int t = threadIdx.x; t < nl; t += BLOCK) {
+    const int j = t / N2, r = t - j * N2;
+    df_eo_forward<K, N>(cb + j * N3 + r % N + N2 * (r / N));
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int t = threadIdx.x; t < nl; t += BLOCK) {
+    const int j = t / N2, r = t - j * N2;
+    df* p = cb + j * N3 + r;
+    df v[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] = p[c * N2];
+    df_eo_forward<K, 1>(v);
+    const df h = sm_h[j];
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] = df_mul(df_mul(v[c], s_lam3[r + N2 * c]), h);
+    df_eo_backward<K, 1>(v);
+#pragma unroll
+    for (int c = 0; c < N; ++c) p[c * N2] = v[c];
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int t = threadIdx.x; t < nl; t += BLOCK) {
+    const int j = t / N2, r = t - j * N2;
+    df_eo_backward<K, N>(cb + j * N3 + r % N + N2 * (r / N));
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int t = threadIdx.x; t < nl; t += BLOCK) df_eo_backward<K, 1>(cb + (t / N2) * N3 + N * (t % N2));
+  __syncthreads();
+  df_hanging_all<K, true>(cb, sm_mask, hang ? nc : 0);  // C_e^T
+
+  // G_e^T, sub-colour by sub-colour
+  for (int sc = 0; sc < ti.n_sub; ++sc) {
+#pragma unroll 1
+    for (int t = threadIdx.x; t < nl; t += BLOCK) {
+      const int j = t / N2;
+      if (sm_sub[j] != sc) continue;
+      const int r = t - j * N2;
+      const uint16_t* ls = sm_meta[sm_cell[j]].ls;
+      const df* in = cb + j * N3 + N * r;
+#pragma unroll
+      for (int a = 0; a < N; ++a) {
+        const int so = s_so[N * r + a];
+        const uint16_t l = ls[so & 31];
+        if (l != LS_NONE) ys[l + (so >> 5)] = df_add(ys[l + (so >> 5)], in[a]);
+      }
+    }
+    __syncthreads();
+  }
+  double* d = A.dst + ti.dof_begin;
+  if (A.add)
+    for (int i = threadIdx.x; i < ti.n_owned; i += BLOCK) d[i] += df_to(ys[i]);
+  else
+    for (int i = threadIdx.x; i < ti.n_owned; i += BLOCK) d[i] = df_to(ys[i]);
+  double* hl = A.halo + ti.foreign_begin;
+  for (int i = threadIdx.x; i < ti.n_foreign; i += BLOCK) hl[i] = df_to(ys[ti.n_owned + i]);
+}
+
+// ---------------------------------------------------------------------------
 // fp32 operator, one cell per thread, values in registers
 // ---------------------------------------------------------------------------
 
@@ -927,6 +1061,16 @@ void launch_cells_nt(const CellLaunch& L, CellArgs<T> A, size_t sm, cudaStream_t
 template <int K, typename T, int MODE>
 void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
   const size_t sm = smem_layout<T>((K + 1) * (K + 1) * (K + 1), L.tc, L.max_local).total;
+  if constexpr (MODE == MODE_VMULT && sizeof(T) == 8) {
+    if (L.tc <= CHUNK) {  // fp64 operator: double-float arithmetic on the FP32 pipe
+      const size_t sm1 = sm - (size_t)L.max_local * sizeof(T);
+      ensure_smem(vmult_lines_df<K>, sm1);
+      vmult_lines_df<K><<<L.n_tiles, BLOCK, sm1, s>>>(A);
+      note_launches(1);
+      run_halo<T>(L, A.dst, s);
+      return;
+    }
+  }
   if (MODE == MODE_VMULT && L.tc <= CHUNK && (sizeof(T) == 8 || L.threads == BLOCK)) {
     // vmult_lines keeps one tile-DoF buffer (input, then accumulator)
     const size_t sm1 = sm - (size_t)L.max_local * sizeof(T);
