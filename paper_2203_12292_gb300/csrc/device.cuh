@@ -16,6 +16,33 @@ namespace gcmg {
 
 constexpr int BLOCK = 256;
 
+// Programmatic dependent launch.  Every kernel of the multigrid cycle is
+// launched with launch_pdl and starts with pdl_begin(): it waits until the
+// preceding kernel of the stream has completed and its writes are visible,
+// then lets the next kernel be scheduled.  Stream order and results are
+// unchanged; the launch of a kernel overlaps the tail of its predecessor
+// (the many small kernels of the coarse levels are bound by launch latency).
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <typename T>
 struct DevTables {
   T B[NMAX][NMAX];          // fast-diagonalisation transform, rows = modes

@@ -118,6 +118,7 @@ __device__ __forceinline__ void write_tile_dofs(T* dst, T* halo, const T* ys, co
 
 template <int K, typename T, int MODE, int NT = BLOCK>
 __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
+  pdl_begin();
   constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout SL = smem_layout<T>(N3, A.tc, A.max_local);
@@ -247,6 +248,7 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
 // ---------------------------------------------------------------------------
 template <int K, typename T>
 __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
+  pdl_begin();
   constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout SL = smem_layout<T>(N3, A.tc, A.max_local);
@@ -410,6 +412,7 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
 // ---------------------------------------------------------------------------
 template <int K>
 __global__ void __launch_bounds__(BLOCK) vmult_lines_df(CellArgs<double> A) {
+  pdl_begin();
   constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
   static_assert(sizeof(df) == sizeof(double), "df buffers reuse the fp64 layout");
   extern __shared__ __align__(16) unsigned char smem[];
@@ -879,6 +882,7 @@ __device__ __forceinline__ void z_lines(float* zv, const float (&Be)[NMAX][NMAX]
 
 template <int K>
 __global__ void __launch_bounds__(11 * 32, 2) vmult_slab(CellArgs<float> A) {
+  pdl_begin();
   using G = SlabGeom<K>;
   constexpr int N = G::N, N2 = G::N2, N3 = G::N3, CPW = G::CPW;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -997,6 +1001,7 @@ __global__ void __launch_bounds__(11 * 32, 2) vmult_slab(CellArgs<float> A) {
 template <typename T>
 __global__ void halo_add_kernel(T* dst, const T* halo, const int32_t* dofs, const int32_t* ptr,
                                 const int32_t* src, int nh) {
+  pdl_begin();
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nh; u += gridDim.x * blockDim.x) {
     const int32_t g = dofs[u];
     T s = dst[g];
@@ -1010,6 +1015,7 @@ __global__ void halo_add_kernel(T* dst, const T* halo, const int32_t* dofs, cons
 // Eq. 4 with the constraints applied on both sides)
 template <int K>
 __global__ void __launch_bounds__(BLOCK) diag_table_kernel(double* out, int tc) {
+  pdl_begin();
   constexpr int N = K + 1, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem[];
   double* sm_h = reinterpret_cast<double*>(smem);
@@ -1045,7 +1051,7 @@ void run_halo(const CellLaunch& L, T* dst, cudaStream_t s) {
   if (L.n_halo == 0) return;
   const int nb = std::min((L.n_halo + BLOCK - 1) / BLOCK, 152 * 8);
   {
-    halo_add_kernel<T><<<nb, BLOCK, 0, s>>>(dst, static_cast<const T*>(L.halo), L.halo_dofs, L.halo_ptr,
+    launch_pdl(halo_add_kernel<T>, nb, BLOCK, 0, s, dst, static_cast<const T*>(L.halo), L.halo_dofs, L.halo_ptr,
                                            L.halo_src, L.n_halo);
     note_launches(1);
   }
@@ -1054,7 +1060,7 @@ void run_halo(const CellLaunch& L, T* dst, cudaStream_t s) {
 template <int K, typename T, int MODE, int NT>
 void launch_cells_nt(const CellLaunch& L, CellArgs<T> A, size_t sm, cudaStream_t s) {
   ensure_smem(cell_kernel<K, T, MODE, NT>, sm);
-  cell_kernel<K, T, MODE, NT><<<L.n_tiles, NT, sm, s>>>(A);
+  launch_pdl(cell_kernel<K, T, MODE, NT>, L.n_tiles, NT, sm, s, A);
   note_launches(1);
 }
 
@@ -1065,7 +1071,7 @@ void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
     if (L.tc <= CHUNK) {  // fp64 operator: double-float arithmetic on the FP32 pipe
       const size_t sm1 = sm - (size_t)L.max_local * sizeof(T);
       ensure_smem(vmult_lines_df<K>, sm1);
-      vmult_lines_df<K><<<L.n_tiles, BLOCK, sm1, s>>>(A);
+      launch_pdl(vmult_lines_df<K>, L.n_tiles, BLOCK, sm1, s, A);
       note_launches(1);
       run_halo<T>(L, A.dst, s);
       return;
@@ -1075,7 +1081,7 @@ void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
     // vmult_lines keeps one tile-DoF buffer (input, then accumulator)
     const size_t sm1 = sm - (size_t)L.max_local * sizeof(T);
     ensure_smem(vmult_lines<K, T>, sm1);
-    vmult_lines<K, T><<<L.n_tiles, BLOCK, sm1, s>>>(A);
+    launch_pdl(vmult_lines<K, T>, L.n_tiles, BLOCK, sm1, s, A);
     note_launches(1);
     run_halo<T>(L, A.dst, s);
     return;
@@ -1098,7 +1104,7 @@ void run_regs(const CellLaunch& L, CellArgs<float> A, cudaStream_t s) {
   const size_t sm = slab_smem<K>(L.tc, L.max_local);
   ensure_smem(vmult_slab<K>, sm);
   {
-    vmult_slab<K><<<L.n_tiles, slab_warps<K>(L.tc) * 32, sm, s>>>(A);
+    launch_pdl(vmult_slab<K>, L.n_tiles, slab_warps<K>(L.tc) * 32, sm, s, A);
     note_launches(1);
   }
   run_halo<float>(L, A.dst, s);
@@ -1197,10 +1203,10 @@ void launch_diag_table(int k, double* tab_out, cudaStream_t s) {
   const size_t sm = (((size_t)tc * 10 + 15) & ~(size_t)15) + (size_t)tc * n3 * sizeof(double);
   const int nb = (512 * n3 + tc - 1) / tc;
   switch (k) {
-    case 1: { diag_table_kernel<1><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
-    case 2: { diag_table_kernel<2><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
-    case 3: { diag_table_kernel<3><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
-    case 4: { diag_table_kernel<4><<<nb, BLOCK, sm, s>>>(tab_out, tc); note_launches(1); } break;
+    case 1: { launch_pdl(diag_table_kernel<1>, nb, BLOCK, sm, s, tab_out, tc); note_launches(1); } break;
+    case 2: { launch_pdl(diag_table_kernel<2>, nb, BLOCK, sm, s, tab_out, tc); note_launches(1); } break;
+    case 3: { launch_pdl(diag_table_kernel<3>, nb, BLOCK, sm, s, tab_out, tc); note_launches(1); } break;
+    case 4: { launch_pdl(diag_table_kernel<4>, nb, BLOCK, sm, s, tab_out, tc); note_launches(1); } break;
     default: break;
   }
 }

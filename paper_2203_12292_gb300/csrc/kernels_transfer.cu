@@ -102,6 +102,7 @@ struct TArgs {
 // ---------------------------------------------------------------------------
 template <int K, typename T>
 __global__ void __launch_bounds__(BLOCK) prolong_h(TArgs<T> A) {
+  pdl_begin();
   constexpr int N = K + 1, N3 = N * N * N, M = 2 * K + 1, M3 = M * M * M;
   constexpr int S1 = M * N * N, S2 = M * M * N;
   constexpr int RG = 8;  // loads in flight per thread
@@ -233,6 +234,7 @@ __device__ __forceinline__ void restrict_write(const TArgs<T>& A, const TileInfo
 
 template <int K, typename T>
 __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
+  pdl_begin();
   constexpr int N = K + 1, N3 = N * N * N, M = 2 * K + 1, M3 = M * M * M;
   constexpr int S1 = M * N * N, S2 = M * M * N;
   __shared__ uint8_t sm_ref[TP];
@@ -341,6 +343,7 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
 // ---------------------------------------------------------------------------
 template <int KF, typename T>
 __global__ void __launch_bounds__(BLOCK) prolong_p(TArgs<T> A) {
+  pdl_begin();
   constexpr int KC = KF / 2, NF = KF + 1, NC = KC + 1;
   constexpr int NC3 = NC * NC * NC, NF3 = NF * NF * NF, S1 = NF * NC * NC, S2 = NF * NF * NC;
   __shared__ uint16_t sm_mask[TP];
@@ -378,6 +381,7 @@ __global__ void __launch_bounds__(BLOCK) prolong_p(TArgs<T> A) {
 
 template <int KF, typename T>
 __global__ void __launch_bounds__(BLOCK) restrict_p(TArgs<T> A) {
+  pdl_begin();
   constexpr int KC = KF / 2, NF = KF + 1, NC = KC + 1;
   constexpr int NC3 = NC * NC * NC, NF3 = NF * NF * NF, S1 = NF * NC * NC, S2 = NF * NF * NC;
   __shared__ uint16_t sm_mask[TP];
@@ -462,7 +466,7 @@ void prolong_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s
   A.src = src;
   A.dst = dst;
   const int nb = (L.n_coarse + TP - 1) / TP;
-  { prolong_h<K, T><<<nb, BLOCK, sm, s>>>(A); note_launches(1); }
+  { launch_pdl(prolong_h<K, T>, nb, BLOCK, sm, s, A); note_launches(1); }
 }
 
 template <int K, typename T>
@@ -474,7 +478,7 @@ void restrict_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t 
   TArgs<T> A = targs<T>(L);
   A.src = src;
   A.dst = dst;
-  { restrict_h<K, T><<<L.coarse.n_tiles, BLOCK, sm, s>>>(A); note_launches(1); }
+  { launch_pdl(restrict_h<K, T>, L.coarse.n_tiles, BLOCK, sm, s, A); note_launches(1); }
   launch_halo_add(L.coarse, sizeof(T) == 8, dst, s);
 }
 
@@ -487,7 +491,7 @@ void prolong_p_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s
   A.src = src;
   A.dst = dst;
   const int nb = (L.n_coarse + TP - 1) / TP;
-  { prolong_p<KF, T><<<nb, BLOCK, sm, s>>>(A); note_launches(1); }
+  { launch_pdl(prolong_p<KF, T>, nb, BLOCK, sm, s, A); note_launches(1); }
 }
 
 template <int KF, typename T>
@@ -500,7 +504,7 @@ void restrict_p_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t 
   TArgs<T> A = targs<T>(L);
   A.src = src;
   A.dst = dst;
-  { restrict_p<KF, T><<<L.coarse.n_tiles, BLOCK, sm, s>>>(A); note_launches(1); }
+  { launch_pdl(restrict_p<KF, T>, L.coarse.n_tiles, BLOCK, sm, s, A); note_launches(1); }
   launch_halo_add(L.coarse, sizeof(T) == 8, dst, s);
 }
 

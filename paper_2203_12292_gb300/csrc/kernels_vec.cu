@@ -27,17 +27,20 @@ inline int grid_for(int64_t n) {
 
 template <typename A, typename B>
 __global__ void cast_kernel(const A* src, B* dst, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = (B)src[i];
 }
 
 template <typename T>
 __global__ void zero_kernel(T* x, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = T(0);
 }
 
 __global__ void invert_kernel(const double* d, double* i64, float* i32, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = 1.0 / d[i];
     if (i64) i64[i] = v;
@@ -47,6 +50,7 @@ __global__ void invert_kernel(const double* d, double* i64, float* i32, int64_t 
 
 template <typename T>
 __global__ void cheb_init_kernel(T* x, T* d, const T* b, const T* dinv, T c2, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const T v = c2 * dinv[i] * b[i];
     d[i] = v;
@@ -56,6 +60,7 @@ __global__ void cheb_init_kernel(T* x, T* d, const T* b, const T* dinv, T c2, in
 
 template <typename T, bool FIRST>
 __global__ void cheb_step_kernel(T* x, T* d, const T* b, const T* Ax, const T* dinv, T c1, T c2, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const T r = b[i] - Ax[i];
     const T v = FIRST ? c2 * dinv[i] * r : c1 * d[i] + c2 * dinv[i] * r;
@@ -66,18 +71,21 @@ __global__ void cheb_step_kernel(T* x, T* d, const T* b, const T* Ax, const T* d
 
 template <typename T>
 __global__ void residual_kernel(T* r, const T* b, const T* Ax, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     r[i] = b[i] - Ax[i];
 }
 
 template <typename T>
 __global__ void axpy_kernel(T* y, const T* x, T a, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] += a * x[i];
 }
 
 template <typename T>
 __global__ void coarse_kernel(const double* Ainv, int n, const T* b, T* x) {
+  pdl_begin();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double s = 0.0;
     for (int j = 0; j < n; ++j) s += Ainv[(size_t)i * n + j] * (double)b[j];
@@ -114,6 +122,7 @@ __device__ __forceinline__ double block_sum_rb(double v, double* sh) {
 // each block sums a fixed contiguous chunk in a fixed order: the result does
 // not depend on scheduling
 __global__ void __launch_bounds__(RB, 2) dot_partial(const double* x, const double* y, int64_t n, double* part) {
+  pdl_begin();
   __shared__ double sh[RB];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
@@ -129,6 +138,7 @@ __global__ void __launch_bounds__(RB, 2) dot_partial(const double* x, const doub
 }
 
 __global__ void __launch_bounds__(BLOCK) dot_final(const double* part, int np, double* scal, int slot, int op) {
+  pdl_begin();
   __shared__ double sh[BLOCK];
   double s = 0.0;
   for (int i = threadIdx.x; i < np; i += BLOCK) s += part[i];
@@ -157,6 +167,7 @@ constexpr int XB = 512, XU = 4;
 
 __global__ void __launch_bounds__(XB, 2) cg_xr_kernel(double* x, double* r, const double* p, const double* q,
                                                       const double* scal, int64_t n, double* part) {
+  pdl_begin();
   __shared__ double sh[XB];
   const double alpha = scal[3];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -196,22 +207,26 @@ __global__ void __launch_bounds__(XB, 2) cg_xr_kernel(double* x, double* r, cons
 }
 
 __global__ void cg_p_kernel(double* p, const double* z, const double* scal, int64_t n) {
+  pdl_begin();
   const double beta = scal[4];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = z[i] + beta * p[i];
 }
 
 __global__ void fill_kernel(double* x, double v, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = v;
 }
 
 __global__ void pmul_kernel(double* z, const double* a, const double* b, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     z[i] = a[i] * b[i];
 }
 
 __global__ void xpby_kernel(double* p, const double* z, double beta, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = z[i] + beta * p[i];
 }
@@ -221,6 +236,7 @@ __global__ void xpby_kernel(double* p, const double* z, double beta, int64_t n) 
 // lives in scal[8]; the loop continues while it < maxit, the residual is above
 // the tolerance and (p, Ap) > 0 (a NaN residual stops it as well)
 __global__ void cg_check_kernel(cudaGraphConditionalHandle h, double* scal, int maxit, double rtol2) {
+  pdl_begin();
   const double it = scal[8] + 1.0;
   scal[8] = it;
   const double rr = scal[2], nb2 = scal[7], pq = scal[1];
@@ -229,6 +245,7 @@ __global__ void cg_check_kernel(cudaGraphConditionalHandle h, double* scal, int 
 }
 
 __global__ void cg_stats_kernel(const double* scal, double rtol2, double* out) {
+  pdl_begin();
   const double it = scal[8], rr = scal[2], nb2 = scal[7], pq = scal[1];
   double status = GCMG_ERR_NOT_CONVERGED;
   if (nb2 == 0.0 || rr <= rtol2 * nb2)
@@ -241,9 +258,11 @@ __global__ void cg_stats_kernel(const double* scal, double rtol2, double* out) {
   out[3] = status;
 }
 
-__global__ void scalar_set_kernel(double* scal, int slot, double v) { scal[slot] = v; }
+__global__ void scalar_set_kernel(double* scal, int slot, double v) {
+  pdl_begin(); scal[slot] = v; }
 
 __global__ void copy_kernel(const double* src, double* dst, int64_t n) {
+  pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = src[i];
 }
@@ -251,46 +270,46 @@ __global__ void copy_kernel(const double* src, double* dst, int64_t n) {
 }  // namespace
 
 void launch_fill(double* x, double v, int64_t n, cudaStream_t s) {
-  if (n > 0) { fill_kernel<<<grid_for(n), BLOCK, 0, s>>>(x, v, n); note_launches(1); }
+  if (n > 0) { launch_pdl(fill_kernel, grid_for(n), BLOCK, 0, s, x, v, n); note_launches(1); }
 }
 
 void launch_pmul(double* z, const double* a, const double* b, int64_t n, cudaStream_t s) {
-  if (n > 0) { pmul_kernel<<<grid_for(n), BLOCK, 0, s>>>(z, a, b, n); note_launches(1); }
+  if (n > 0) { launch_pdl(pmul_kernel, grid_for(n), BLOCK, 0, s, z, a, b, n); note_launches(1); }
 }
 
 void launch_xpby(double* p, const double* z, double beta, int64_t n, cudaStream_t s) {
-  if (n > 0) { xpby_kernel<<<grid_for(n), BLOCK, 0, s>>>(p, z, beta, n); note_launches(1); }
+  if (n > 0) { launch_pdl(xpby_kernel, grid_for(n), BLOCK, 0, s, p, z, beta, n); note_launches(1); }
 }
 
 void launch_cast(bool to64, const void* src, void* dst, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   if (to64)
-    { cast_kernel<float, double><<<grid_for(n), BLOCK, 0, s>>>(static_cast<const float*>(src), static_cast<double*>(dst), n); note_launches(1); }
+    { launch_pdl(cast_kernel<float, double>, grid_for(n), BLOCK, 0, s, static_cast<const float*>(src), static_cast<double*>(dst), n); note_launches(1); }
   else
-    { cast_kernel<double, float><<<grid_for(n), BLOCK, 0, s>>>(static_cast<const double*>(src), static_cast<float*>(dst), n); note_launches(1); }
+    { launch_pdl(cast_kernel<double, float>, grid_for(n), BLOCK, 0, s, static_cast<const double*>(src), static_cast<float*>(dst), n); note_launches(1); }
 }
 
 void launch_zero(bool fp64, void* x, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   if (fp64)
-    { zero_kernel<double><<<grid_for(n), BLOCK, 0, s>>>(static_cast<double*>(x), n); note_launches(1); }
+    { launch_pdl(zero_kernel<double>, grid_for(n), BLOCK, 0, s, static_cast<double*>(x), n); note_launches(1); }
   else
-    { zero_kernel<float><<<grid_for(n), BLOCK, 0, s>>>(static_cast<float*>(x), n); note_launches(1); }
+    { launch_pdl(zero_kernel<float>, grid_for(n), BLOCK, 0, s, static_cast<float*>(x), n); note_launches(1); }
 }
 
 void launch_invert(const double* d, double* inv64, float* inv32, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
-  { invert_kernel<<<grid_for(n), BLOCK, 0, s>>>(d, inv64, inv32, n); note_launches(1); }
+  { launch_pdl(invert_kernel, grid_for(n), BLOCK, 0, s, d, inv64, inv32, n); note_launches(1); }
 }
 
 void launch_cheb_init(bool fp64, void* x, void* d, const void* b, const void* dinv, double c2, int64_t n,
                       cudaStream_t s) {
   if (n <= 0) return;
   if (fp64)
-    { cheb_init_kernel<double><<<grid_for(n), BLOCK, 0, s>>>((double*)x, (double*)d, (const double*)b,
+    { launch_pdl(cheb_init_kernel<double>, grid_for(n), BLOCK, 0, s, (double*)x, (double*)d, (const double*)b,
                                                             (const double*)dinv, c2, n); note_launches(1); }
   else
-    { cheb_init_kernel<float><<<grid_for(n), BLOCK, 0, s>>>((float*)x, (float*)d, (const float*)b, (const float*)dinv,
+    { launch_pdl(cheb_init_kernel<float>, grid_for(n), BLOCK, 0, s, (float*)x, (float*)d, (const float*)b, (const float*)dinv,
                                                            (float)c2, n); note_launches(1); }
 }
 
@@ -300,18 +319,18 @@ void launch_cheb_step(bool fp64, void* x, void* d, const void* b, const void* Ax
   const bool first = (c1 == 0.0);
   if (fp64) {
     if (first)
-      { cheb_step_kernel<double, true><<<grid_for(n), BLOCK, 0, s>>>((double*)x, (double*)d, (const double*)b,
+      { launch_pdl(cheb_step_kernel<double, true>, grid_for(n), BLOCK, 0, s, (double*)x, (double*)d, (const double*)b,
                                                                    (const double*)Ax, (const double*)dinv, c1, c2, n); note_launches(1); }
     else
-      { cheb_step_kernel<double, false><<<grid_for(n), BLOCK, 0, s>>>((double*)x, (double*)d, (const double*)b,
+      { launch_pdl(cheb_step_kernel<double, false>, grid_for(n), BLOCK, 0, s, (double*)x, (double*)d, (const double*)b,
                                                                     (const double*)Ax, (const double*)dinv, c1, c2, n); note_launches(1); }
   } else {
     if (first)
-      { cheb_step_kernel<float, true><<<grid_for(n), BLOCK, 0, s>>>((float*)x, (float*)d, (const float*)b,
+      { launch_pdl(cheb_step_kernel<float, true>, grid_for(n), BLOCK, 0, s, (float*)x, (float*)d, (const float*)b,
                                                                   (const float*)Ax, (const float*)dinv, (float)c1,
                                                                   (float)c2, n); note_launches(1); }
     else
-      { cheb_step_kernel<float, false><<<grid_for(n), BLOCK, 0, s>>>((float*)x, (float*)d, (const float*)b,
+      { launch_pdl(cheb_step_kernel<float, false>, grid_for(n), BLOCK, 0, s, (float*)x, (float*)d, (const float*)b,
                                                                    (const float*)Ax, (const float*)dinv, (float)c1,
                                                                    (float)c2, n); note_launches(1); }
   }
@@ -320,37 +339,37 @@ void launch_cheb_step(bool fp64, void* x, void* d, const void* b, const void* Ax
 void launch_residual(bool fp64, void* r, const void* b, const void* Ax, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   if (fp64)
-    { residual_kernel<double><<<grid_for(n), BLOCK, 0, s>>>((double*)r, (const double*)b, (const double*)Ax, n); note_launches(1); }
+    { launch_pdl(residual_kernel<double>, grid_for(n), BLOCK, 0, s, (double*)r, (const double*)b, (const double*)Ax, n); note_launches(1); }
   else
-    { residual_kernel<float><<<grid_for(n), BLOCK, 0, s>>>((float*)r, (const float*)b, (const float*)Ax, n); note_launches(1); }
+    { launch_pdl(residual_kernel<float>, grid_for(n), BLOCK, 0, s, (float*)r, (const float*)b, (const float*)Ax, n); note_launches(1); }
 }
 
 void launch_axpy(bool fp64, void* y, const void* x, double a, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   if (fp64)
-    { axpy_kernel<double><<<grid_for(n), BLOCK, 0, s>>>((double*)y, (const double*)x, a, n); note_launches(1); }
+    { launch_pdl(axpy_kernel<double>, grid_for(n), BLOCK, 0, s, (double*)y, (const double*)x, a, n); note_launches(1); }
   else
-    { axpy_kernel<float><<<grid_for(n), BLOCK, 0, s>>>((float*)y, (const float*)x, (float)a, n); note_launches(1); }
+    { launch_pdl(axpy_kernel<float>, grid_for(n), BLOCK, 0, s, (float*)y, (const float*)x, (float)a, n); note_launches(1); }
 }
 
 void launch_coarse_solve(bool fp64, const double* Ainv, int n, const void* b, void* x, cudaStream_t s) {
   if (n <= 0) return;
   if (fp64)
-    { coarse_kernel<double><<<1, BLOCK, 0, s>>>(Ainv, n, (const double*)b, (double*)x); note_launches(1); }
+    { launch_pdl(coarse_kernel<double>, 1, BLOCK, 0, s, Ainv, n, (const double*)b, (double*)x); note_launches(1); }
   else
-    { coarse_kernel<float><<<1, BLOCK, 0, s>>>(Ainv, n, (const float*)b, (float*)x); note_launches(1); }
+    { launch_pdl(coarse_kernel<float>, 1, BLOCK, 0, s, Ainv, n, (const float*)b, (float*)x); note_launches(1); }
 }
 
 void launch_dot(const double* x, const double* y, int64_t n, double* scratch, double* scal, int slot, int op,
                 cudaStream_t s) {
-  { dot_partial<<<DOT_BLOCKS, RB, 0, s>>>(x, y, n, scratch); note_launches(1); }
-  { dot_final<<<1, BLOCK, 0, s>>>(scratch, DOT_BLOCKS, scal, slot, op); note_launches(1); }
+  { launch_pdl(dot_partial, DOT_BLOCKS, RB, 0, s, x, y, n, scratch); note_launches(1); }
+  { launch_pdl(dot_final, 1, BLOCK, 0, s, scratch, DOT_BLOCKS, scal, slot, op); note_launches(1); }
 }
 
 void launch_cg_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, int64_t n,
                          double* scratch, double* scal_out, cudaStream_t s) {
-  { cg_xr_kernel<<<DOT_BLOCKS, XB, 0, s>>>(x, r, p, q, scal, n, scratch); note_launches(1); }
-  { dot_final<<<1, BLOCK, 0, s>>>(scratch, DOT_BLOCKS, scal_out, 2, DOT_STORE); note_launches(1); }
+  { launch_pdl(cg_xr_kernel, DOT_BLOCKS, XB, 0, s, x, r, p, q, scal, n, scratch); note_launches(1); }
+  { launch_pdl(dot_final, 1, BLOCK, 0, s, scratch, DOT_BLOCKS, scal_out, 2, DOT_STORE); note_launches(1); }
 }
 
 // ---------------------------------------------------------------------------
@@ -368,6 +387,7 @@ constexpr int MAX_DEVICES = 64;
 static __device__ __align__(256) double g_noalloc_partials[NOALLOC_MAX_PARTIALS];
 
 __global__ void __launch_bounds__(BLOCK) dot_chunk_partial(const double* x, const double* y, int64_t n, double* part) {
+  pdl_begin();
   __shared__ double sh[BLOCK];
   const int64_t i0 = (int64_t)blockIdx.x * NOALLOC_CHUNK;
   const int64_t i1 = min(n, i0 + NOALLOC_CHUNK);
@@ -378,6 +398,7 @@ __global__ void __launch_bounds__(BLOCK) dot_chunk_partial(const double* x, cons
 }
 
 __global__ void __launch_bounds__(BLOCK) dot_chunk_final(const double* part, int np, double* result) {
+  pdl_begin();
   __shared__ double sh[BLOCK];
   double s = 0.0;
   for (int i = threadIdx.x; i < np; i += BLOCK) s += part[i];
@@ -417,34 +438,34 @@ cudaError_t launch_dot_noalloc(const double* x, const double* y, int64_t n, doub
   if (e != cudaSuccess) return e;
   if (n == 0) return cudaMemsetAsync(result, 0, sizeof(double), s);
   const int np = (int)((n + NOALLOC_CHUNK - 1) / NOALLOC_CHUNK);
-  { dot_chunk_partial<<<np, BLOCK, 0, s>>>(x, y, n, part); note_launches(1); }
-  { dot_chunk_final<<<1, BLOCK, 0, s>>>(part, np, result); note_launches(1); }
+  { launch_pdl(dot_chunk_partial, np, BLOCK, 0, s, x, y, n, part); note_launches(1); }
+  { launch_pdl(dot_chunk_final, 1, BLOCK, 0, s, part, np, result); note_launches(1); }
   return cudaGetLastError();
 }
 
 void launch_cg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
-  { cg_p_kernel<<<grid_for(n), BLOCK, 0, s>>>(p, z, scal, n); note_launches(1); }
+  { launch_pdl(cg_p_kernel, grid_for(n), BLOCK, 0, s, p, z, scal, n); note_launches(1); }
 }
 
 void launch_cg_check(cudaGraphConditionalHandle h, double* scal, int maxit, double rtol2, cudaStream_t s) {
-  cg_check_kernel<<<1, 1, 0, s>>>(h, scal, maxit, rtol2);
+  launch_pdl(cg_check_kernel, 1, 1, 0, s, h, scal, maxit, rtol2);
   note_launches(1);
 }
 
 void launch_cg_stats(const double* scal, double rtol2, double* out, cudaStream_t s) {
-  cg_stats_kernel<<<1, 1, 0, s>>>(scal, rtol2, out);
+  launch_pdl(cg_stats_kernel, 1, 1, 0, s, scal, rtol2, out);
   note_launches(1);
 }
 
 void launch_scalar_set(double* scal, int slot, double v, cudaStream_t s) {
-  scalar_set_kernel<<<1, 1, 0, s>>>(scal, slot, v);
+  launch_pdl(scalar_set_kernel, 1, 1, 0, s, scal, slot, v);
   note_launches(1);
 }
 
 void launch_copy(const double* src, double* dst, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
-  copy_kernel<<<grid_for(n), BLOCK, 0, s>>>(src, dst, n);
+  launch_pdl(copy_kernel, grid_for(n), BLOCK, 0, s, src, dst, n);
   note_launches(1);
 }
 
