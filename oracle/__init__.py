@@ -21,6 +21,10 @@ What it computes, each part a plain definition written out in fp64:
                 fine one and restriction as its transpose (Sec. 3.5, Eq. 5).
 * ``mg``        Chebyshev/point-Jacobi smoother (Sec. 3.3), exact coarse
                 solve (Sec. 3.4), V-cycle (Algorithms 1-2), PCG (Sec. 2).
+* ``dirichlet`` inhomogeneous Dirichlet data as constraints with b_i != 0:
+                lifting u_g, right-hand side C^T (F - A_all u_g) (Sec. 3.1);
+                the Gaussian manufactured solution of Table A.1 and
+                polynomial ones.
 * ``mlp``       learned per-cell smoother, an extension outside the paper:
                 network forward/backward, loss, Adam, cell features, owner-
                 selected correction, optional bf16 operand rounding.
