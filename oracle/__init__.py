@@ -25,6 +25,9 @@ What it computes, each part a plain definition written out in fp64:
                 lifting u_g, right-hand side C^T (F - A_all u_g) (Sec. 3.1);
                 the Gaussian manufactured solution of Table A.1 and
                 polynomial ones.
+* ``coefficient`` variable coefficient nu of -div(nu grad u): harmonic
+                cell averages of Gauss-point values on the finest level,
+                transfer to the coarser levels (Sec. 7, Sec. 3.5).
 * ``mlp``       learned per-cell smoother, an extension outside the paper:
                 network forward/backward, loss, Adam, cell features, owner-
                 selected correction, optional bf16 operand rounding.

@@ -91,10 +91,10 @@ def lifting(space, g: Callable) -> np.ndarray:
 
 
 def apply_all(space, u_all: np.ndarray) -> np.ndarray:
-    """A_all u_all = sum_e P_e^T (h_e A_ref) P_e u_all (all support points)."""
+    """A_all u_all = sum_e P_e^T A_e P_e u_all (all support points)."""
     Aref = fe.reference_laplace_matrix(space.k)
     U = u_all[space.cell_nodes]
-    V = (U @ Aref.T) * space.h[:, None]
+    V = (U @ Aref.T) * space.element_matrices_scale()[:, None]
     return np.bincount(space.cell_nodes.ravel(), weights=V.ravel(), minlength=space.n_points)
 
 

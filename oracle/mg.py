@@ -40,6 +40,7 @@ import scipy.sparse as sp
 
 import synth
 
+from . import coefficient as ocoef
 from . import mesh as omesh
 from .space import Space
 from .transfer import prolongation_matrix
@@ -146,10 +147,12 @@ class Level:
 
 
 def build_levels(fine_mesh: omesh.Mesh, k: int, p_coarsening: bool = False,
-                 assembled: bool = True, lam_max: Optional[List[float]] = None) -> List[Level]:
+                 assembled: bool = True, lam_max: Optional[List[float]] = None,
+                 coefficient: Optional[Callable] = None) -> List[Level]:
     """Global-coarsening levels (coarsest first). With p_coarsening the
     finest mesh is first coarsened in degree k -> floor(k/2) -> ... -> 1
-    (Sec. 2.3), then geometrically with degree 1."""
+    (Sec. 2.3), then geometrically with degree 1.  ``coefficient``: nu(x) of
+    -div(nu grad u), set on all levels as in oracle.coefficient."""
     meshes = omesh.gc_hierarchy(fine_mesh)
     specs = []
     if p_coarsening:
@@ -159,9 +162,11 @@ def build_levels(fine_mesh: omesh.Mesh, k: int, p_coarsening: bool = False,
         specs = [(m, 1) for m in meshes[:-1]] + [(meshes[-1], d) for d in degs[::-1]]
     else:
         specs = [(m, k) for m in meshes]
+    spaces = [Space(m, kk) for m, kk in specs]
+    if coefficient is not None:
+        ocoef.set_level_coefficients(spaces, coefficient)
     levels: List[Level] = []
-    for idx, (m, kk) in enumerate(specs):
-        s = Space(m, kk)
+    for idx, s in enumerate(spaces):
         A = s.assemble() if assembled else None
         lev = Level(s, A, s.diagonal())
         if idx > 0:

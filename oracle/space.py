@@ -57,6 +57,8 @@ class Space:
         self.level = cells[:, 0]
         self.h = (mesh.hi - mesh.lo) / (2.0 ** self.level)
         self.origin = mesh.lo + self.h[:, None] * cells[:, 1:4]
+        # per-cell coefficient nu_e of -div(nu grad u) (1 unless set)
+        self.nu = np.ones(self.nc)
         self.codes = cell_code(cells[:, 0], cells[:, 1], cells[:, 2], cells[:, 3])
         self.code_order = np.argsort(self.codes)
         self.sorted_codes = self.codes[self.code_order]
@@ -164,17 +166,19 @@ class Space:
         return self.points[self.free_points]
 
     def element_matrices_scale(self) -> np.ndarray:
-        return self.h
+        """A_e = nu_e h_e A_ref: the Laplace matrix of a cube of edge h times
+        the cell's coefficient."""
+        return self.h * self.nu
 
     def apply(self, x: np.ndarray) -> np.ndarray:
-        """y = C^T sum_e P_e^T (h_e A_ref) P_e C x, cell by cell, in the
+        """y = C^T sum_e P_e^T (nu_e h_e A_ref) P_e C x, cell by cell, in the
         precision of x (fp64, or fp32 with fp32 element products)."""
         dt = x.dtype
         Aref = fe.reference_laplace_matrix(self.k).astype(dt)
         C = self.C.astype(dt) if dt != np.float64 else self.C
         u = C @ x
         U = u[self.cell_nodes]
-        V = (U @ Aref.T) * self.h.astype(dt)[:, None]
+        V = (U @ Aref.T) * self.element_matrices_scale().astype(dt)[:, None]
         v = np.bincount(self.cell_nodes.ravel(), weights=V.ravel(), minlength=self.n_points).astype(dt)
         return C.T @ v
 
@@ -184,7 +188,7 @@ class Space:
         n3 = self.n3
         r = np.repeat(self.cell_nodes, n3, axis=1).ravel()
         c = np.tile(self.cell_nodes, (1, n3)).ravel()
-        v = (self.h[:, None, None] * Aref[None, :, :]).ravel()
+        v = (self.element_matrices_scale()[:, None, None] * Aref[None, :, :]).ravel()
         Aall = sp.csr_matrix((v, (r, c)), shape=(self.n_points, self.n_points))
         return (self.C.T @ Aall @ self.C).tocsr()
 
@@ -196,7 +200,7 @@ class Space:
         # cells without constrained values: d_e(i) = A_e(i, i)
         nodes = self.cell_nodes[plain]
         fi = self.free_index[nodes]
-        contrib = self.h[plain][:, None] * np.diag(Aref)[None, :]
+        contrib = self.element_matrices_scale()[plain][:, None] * np.diag(Aref)[None, :]
         m = fi >= 0
         np.add.at(d, fi[m], contrib[m])
         C = self.C.tocsr()
@@ -206,7 +210,7 @@ class Space:
             if len(cols) == 0:
                 continue
             Ced = Ce[:, cols].toarray()
-            d[cols] += np.einsum("mi,mn,ni->i", Ced, self.h[e] * Aref, Ced)
+            d[cols] += np.einsum("mi,mn,ni->i", Ced, self.element_matrices_scale()[e] * Aref, Ced)
         return d
 
     def rhs(self, f: Optional[Callable[[np.ndarray], np.ndarray]] = None) -> np.ndarray:

@@ -233,6 +233,46 @@ def point_values(xyz: np.ndarray, seed: int, resolution_bits: int = 20) -> np.nd
 
 
 # --------------------------------------------------------------------------
+# coefficient fields nu(x) of -div(nu grad u)
+# --------------------------------------------------------------------------
+
+@dataclass
+class Inclusions:
+    """nu(x) = 1 + (contrast - 1) * max_i exp(-|x - c_i|^2 / width^2): smooth
+    high-viscosity inclusions at seeded centres c_i in [lo, hi]^3 in a unit
+    background (a stand-in for the sinker viscosity of a Stokes benchmark)."""
+    centres: np.ndarray  # (n, 3)
+    width: float
+    contrast: float
+
+    def __call__(self, xyz: np.ndarray) -> np.ndarray:
+        x = np.asarray(xyz, dtype=np.float64)
+        d2 = ((x[:, None, :] - self.centres[None, :, :]) ** 2).sum(axis=2)
+        return 1.0 + (self.contrast - 1.0) * np.exp(-d2 / (self.width * self.width)).max(axis=1)
+
+
+def inclusions(seed: int, lo: float, hi: float, n: int = 7, width: float = 0.1,
+               contrast: float = 1e3) -> Inclusions:
+    u = (splitmix64_array(seed, 3 * n) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+    return Inclusions(lo + (hi - lo) * u.reshape(n, 3), width * (hi - lo), contrast)
+
+
+def random_cells(seed: int, contrast: float = 1e2):
+    """nu(x) = contrast^(v(x)) with v the position-keyed values in [-1, 1):
+    unrelated values at every point (rough coefficient, parity tests)."""
+    def nu(xyz):
+        return contrast ** point_values(xyz, seed)
+    return nu
+
+
+def step(x_c: float, nu_lo: float, nu_hi: float):
+    """nu = nu_lo for x < x_c, nu_hi otherwise (a jump across a plane)."""
+    def nu(xyz):
+        return np.where(np.asarray(xyz)[:, 0] < x_c, nu_lo, nu_hi)
+    return nu
+
+
+# --------------------------------------------------------------------------
 # learned smoother: network size, initial parameters, sample orders
 # --------------------------------------------------------------------------
 
