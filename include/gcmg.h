@@ -150,6 +150,51 @@ int gcmg_diagonal(gcmg_handle* h, int level, double* dst);
  * host array kappa_x, kappa_y, kappa_z, phi per mode) or f = 1 (n_modes = 0).
  */
 int gcmg_rhs(gcmg_handle* h, int n_modes, const double* modes, double amp, double* b);
+
+/*
+ * Inhomogeneous Dirichlet data (Sec. 3.1: constraints x_i = sum_j c_ij x_j
+ * + b_i with b_i != 0) for a manufactured solution u: Dirichlet data g = u
+ * on the domain boundary and f = -Lap u.  The known values are moved to the
+ * right-hand side,
+ *     b = C^T (F - A_all u_g),
+ * u_g the lifting (u at boundary support points, the interpolated boundary
+ * values at hanging support points, zero at free ones); the solution at the
+ * free DoFs then approximates u there.  b: device, n_free(finest), fp64.
+ *   kind GCMG_FUNC_GAUSSIAN:   n = 1, params = {alpha, x0, y0, z0}:
+ *       u = (alpha sqrt(2 pi))^-3 exp(-|x - x0|^2 / alpha^2)   (Table A.1,
+ *       with the squared distance of a Gaussian)
+ *   kind GCMG_FUNC_POLYNOMIAL: n = 1..64 terms, params = n x {c, a, b, e}:
+ *       u = sum c x^a y^b z^e, integer exponents 0..16
+ * params is a host array.  Two cell loops: the quadrature of f, then the
+ * lifting term (u_g built per cell from geometry, C_e applied in place, the
+ * cell operator, C_e^T).  GCMG_ERR_ARG for an unknown kind or bad params.
+ */
+#define GCMG_FUNC_GAUSSIAN 2
+#define GCMG_FUNC_POLYNOMIAL 3
+int gcmg_rhs_dirichlet(gcmg_handle* h, int kind, int n, const double* params, double* b);
+
+/*
+ * Variable coefficient: the operator becomes -div(nu grad u) with nu
+ * constant on every cell, element matrix nu_e h_e A_ref (the set-up of the
+ * Stokes application, Sec. 7: nu at the quadrature points of the finest
+ * level, harmonically averaged per cell, carried to the coarser levels by
+ * the transfer, `interpolate_to_mg` of Sec. 3.5).
+ *   values_per_cell = (k+1)^3: nu holds n_cells(finest) x (k+1)^3 values at
+ *     the Gauss points of gcmg_quadrature_points (cell order of
+ *     gcmg_level_cells, x fastest); nu_e = (sum_q w_q) / (sum_q w_q / nu_q);
+ *   values_per_cell = 1: nu holds nu_e per finest cell.
+ * Coarser levels: an unrefined cell keeps its value, a refined one takes the
+ * mean of its eight children; levels of one mesh share them.  Then the
+ * Jacobi diagonals, the coarse inverse and the Chebyshev eigenvalue
+ * estimates are recomputed (synchronous; graphs are re-captured).  nu:
+ * device, fp64; values must be positive and finite (GCMG_ERR_ARG otherwise,
+ * the handle unchanged).  Not combinable with the learned smoother.
+ */
+int gcmg_set_coefficient(gcmg_handle* h, int values_per_cell, const double* nu);
+/* nu_e of every cell of a level into device memory (1 where none was set) */
+int gcmg_get_coefficient(gcmg_handle* h, int level, double* nu);
+/* Gauss points of every finest cell: device array n_cells x (k+1)^3 x 3 */
+int gcmg_quadrature_points(gcmg_handle* h, double* xyz);
 /* lambda_max used by the Chebyshev smoother of a level (after the safety factor) */
 int gcmg_get_lambda(const gcmg_handle* h, int level, double* lam);
 int gcmg_set_lambda(gcmg_handle* h, int level, double lam);

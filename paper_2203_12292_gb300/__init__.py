@@ -24,6 +24,7 @@ STAGES = ["vmult", "presmooth", "residual", "restrict", "coarse", "prolongate", 
           "cg_vector", "learned"]
 
 SMOOTHER_CHEBYSHEV, SMOOTHER_MLP_AUGMENT, SMOOTHER_MLP_REPLACE = 0, 1, 2
+FUNC_GAUSSIAN, FUNC_POLYNOMIAL = 2, 3  # manufactured solutions of rhs_dirichlet
 
 ERRORS = {1: "GCMG_ERR_ARG", 2: "GCMG_ERR_CUDA", 3: "GCMG_ERR_OOM", 4: "GCMG_ERR_NOT_CONVERGED",
           5: "GCMG_ERR_BREAKDOWN", 6: "GCMG_ERR_INTERNAL"}
@@ -84,6 +85,10 @@ _SIGS = {
     "gcmg_get_profile": (_c_int, [_c_void_p, _c_int, _c_int, ctypes.POINTER(_c_int64), ctypes.POINTER(_c_double)]),
     "gcmg_diagonal": (_c_int, [_c_void_p, _c_int, _c_void_p]),
     "gcmg_rhs": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_double, _c_void_p]),
+    "gcmg_rhs_dirichlet": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
+    "gcmg_set_coefficient": (_c_int, [_c_void_p, _c_int, _c_void_p]),
+    "gcmg_get_coefficient": (_c_int, [_c_void_p, _c_int, _c_void_p]),
+    "gcmg_quadrature_points": (_c_int, [_c_void_p, _c_void_p]),
     "gcmg_get_lambda": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_double)]),
     "gcmg_set_lambda": (_c_int, [_c_void_p, _c_int, _c_double]),
     "gcmg_smooth": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p, _c_int]),
@@ -345,6 +350,40 @@ class Multigrid:
                                                          np.asarray(phi, np.float64)[:, None]], axis=1))
             _check(lib().gcmg_rhs(self._h, len(phi), modes.ctypes.data_as(_c_void_p), float(amp), _ptr(b)))
         return b
+
+    def rhs_dirichlet(self, kind: int, params):
+        """b = C^T (F - A_all u_g) for the manufactured solution u (Dirichlet
+        data u, f = -Lap u): kind FUNC_GAUSSIAN with params (alpha, x0, y0, z0),
+        or FUNC_POLYNOMIAL with params = terms (c, a, b, e)."""
+        import torch
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(-1, 4))
+        b = torch.empty(self.n_free(self.finest), dtype=torch.float64, device="cuda")
+        _check(lib().gcmg_rhs_dirichlet(self._h, int(kind), len(p), p.ctypes.data_as(_c_void_p), _ptr(b)))
+        return b
+
+    def quadrature_points(self):
+        """Gauss points of every finest cell, (n_cells, (k+1)^3, 3) on the device."""
+        import torch
+        n3 = (self.info[self.finest].degree + 1) ** 3
+        xyz = torch.empty((self.n_cells(self.finest), n3, 3), dtype=torch.float64, device="cuda")
+        _check(lib().gcmg_quadrature_points(self._h, _ptr(xyz)))
+        return xyz
+
+    def set_coefficient(self, nu) -> None:
+        """nu: device fp64, per finest cell (n_cells,) or per Gauss point
+        (n_cells, (k+1)^3); see gcmg_set_coefficient."""
+        import torch
+        nc = self.n_cells(self.finest)
+        assert nu.dtype == torch.float64 and nu.is_cuda and nu.is_contiguous()
+        assert nu.numel() % max(nc, 1) == 0
+        per = nu.numel() // nc if nc else 1
+        _check(lib().gcmg_set_coefficient(self._h, per, _ptr(nu)))
+
+    def get_coefficient(self, level: int):
+        import torch
+        nu = torch.empty(self.n_cells(level), dtype=torch.float64, device="cuda")
+        _check(lib().gcmg_get_coefficient(self._h, level, _ptr(nu)))
+        return nu
 
     def get_lambda(self, level: int) -> float:
         v = _c_double()

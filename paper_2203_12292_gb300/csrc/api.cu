@@ -470,6 +470,28 @@ void upload_all_tables() {
   done[dev] = 1;
 }
 
+void setup_numerics(Handle& H) {
+  const int nl = (int)H.lev.size();
+  // Jacobi diagonals (Eqs. 3-4)
+  for (int l = 0; l < nl; ++l) {
+    const int k = H.lev[l]->cl.k;
+    if (!H.diag_tab[k].p) {
+      const int n3 = (k + 1) * (k + 1) * (k + 1);
+      H.diag_tab[k].alloc((size_t)512 * n3 * sizeof(double));
+      launch_diag_table(k, H.diag_tab[k].as<double>(), H.stream);
+    }
+    LevelDev& L = *H.lev[l];
+    if (L.n() == 0) continue;
+    launch_diag(L.cl, H.diag_tab[k].as<double>(), L.diag64.as<double>(), H.stream);
+    launch_invert(L.diag64.as<double>(), L.dinv64.as<double>(), L.dinv32.as<float>(), L.n(), H.stream);
+  }
+  ck(cudaGetLastError(), "diagonal");
+  setup_coarse(H);
+  for (int l = 1; l < nl; ++l) H.lev[l]->lam = H.cfg.eig_safety * estimate_lambda(H, l);
+  H.g_core.reset();
+  H.g_a.reset();
+}
+
 void setup_handle(Handle& H, const std::vector<Octree>& meshes, int lmax, const gcmg_config& cfg) {
   H.cfg = cfg;
   // level list: (mesh index, degree), coarsest first
@@ -574,22 +596,7 @@ void setup_handle(Handle& H, const std::vector<Octree>& meshes, int lmax, const 
   H.scratch.alloc(DOT_BLOCKS * sizeof(double));
   H.scal.alloc(16 * sizeof(double));
   ck(cudaMemsetAsync(H.scal.p, 0, 16 * sizeof(double), H.stream), "memset");
-  // Jacobi diagonals (Eqs. 3-4)
-  for (int l = 0; l < nl; ++l) {
-    const int k = spec[l].second;
-    if (!H.diag_tab[k].p) {
-      const int n3 = (k + 1) * (k + 1) * (k + 1);
-      H.diag_tab[k].alloc((size_t)512 * n3 * sizeof(double));
-      launch_diag_table(k, H.diag_tab[k].as<double>(), H.stream);
-    }
-    LevelDev& L = *H.lev[l];
-    if (L.n() == 0) continue;
-    launch_diag(L.cl, H.diag_tab[k].as<double>(), L.diag64.as<double>(), H.stream);
-    launch_invert(L.diag64.as<double>(), L.dinv64.as<double>(), L.dinv32.as<float>(), L.n(), H.stream);
-  }
-  ck(cudaGetLastError(), "diagonal");
-  setup_coarse(H);
-  for (int l = 1; l < nl; ++l) H.lev[l]->lam = cfg.eig_safety * estimate_lambda(H, l);
+  setup_numerics(H);
   const int64_t nf = H.lev.back()->n();
   H.cg_r.alloc(nf * sizeof(double));
   H.cg_p.alloc(nf * sizeof(double));
@@ -890,8 +897,39 @@ int gcmg_rhs(gcmg_handle* h, int n_modes, const double* modes, double amp, doubl
       std::vector<double> v(modes, modes + 4 * n_modes);
       H.modes.upload(v, H.stream);
     }
-    RhsDesc f{n_modes ? H.modes.as<double>() : nullptr, n_modes, amp};
+    RhsDesc f{n_modes ? FUNC_FOURIER : FUNC_ONE, n_modes ? H.modes.as<double>() : nullptr, n_modes, amp};
     if (L.n()) launch_rhs(L.cl, f, b, H.stream);
+    ck(cudaStreamSynchronize(H.stream), "rhs");
+  });
+}
+
+int gcmg_rhs_dirichlet(gcmg_handle* h, int kind, int n, const double* params, double* b) {
+  return guarded([&] {
+    if (!h || !params) throw Error(GCMG_ERR_ARG, "bad arguments");
+    std::vector<double> v;
+    if (kind == GCMG_FUNC_GAUSSIAN) {
+      if (n != 1 || !(params[0] > 0.0) || !std::isfinite(params[0])) throw Error(GCMG_ERR_ARG, "gaussian: n = 1, alpha > 0");
+      v.assign(params, params + 4);
+    } else if (kind == GCMG_FUNC_POLYNOMIAL) {
+      if (n < 1 || n > 64) throw Error(GCMG_ERR_ARG, "polynomial: 1..64 terms");
+      v.assign(params, params + 4 * n);
+      for (int m = 0; m < n; ++m)
+        for (int d = 1; d <= 3; ++d) {
+          const double e = v[4 * m + d];
+          if (!(e >= 0.0 && e <= 16.0 && e == std::floor(e))) throw Error(GCMG_ERR_ARG, "polynomial: exponents 0..16");
+        }
+    } else {
+      throw Error(GCMG_ERR_ARG, "unknown function kind");
+    }
+    Handle& H = h->h;
+    LevelDev& L = *H.lev.back();
+    if (L.n() && !b) throw Error(GCMG_ERR_ARG, "bad vector");
+    H.modes.upload(v, H.stream);
+    RhsDesc u{kind, H.modes.as<double>(), n, 1.0};
+    if (L.n()) {
+      launch_rhs(L.cl, u, b, H.stream);       // C^T F, f = -Lap u
+      launch_rhs_lift(L.cl, u, b, H.stream);  // - C^T A_all u_g
+    }
     ck(cudaStreamSynchronize(H.stream), "rhs");
   });
 }
@@ -1163,6 +1201,7 @@ int gcmg_set_smoother(gcmg_handle* h, int level, int kind, const gcmg_mlp* net) 
     Handle& H = h->h;
     LevelDev& L = *H.lev[level];
     if (kind != GCMG_SMOOTHER_CHEBYSHEV) {
+      if (L.cl.coef) throw Error(GCMG_ERR_ARG, "the learned smoother assumes a unit coefficient");
       check_q4_net(L, net);
       ensure_dfeat(H, level);
       if (!L.mlp_image.p) L.mlp_image.alloc(mlp_image_bytes());
@@ -1170,6 +1209,80 @@ int gcmg_set_smoother(gcmg_handle* h, int level, int kind, const gcmg_mlp* net) 
     }
     L.smoother = kind;
     H.g_core.reset();
+  });
+}
+
+int gcmg_set_coefficient(gcmg_handle* h, int values_per_cell, const double* nu) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    Handle& H = h->h;
+    LevelDev& F = *H.lev.back();
+    const int k = F.cl.k;
+    const int n3 = (k + 1) * (k + 1) * (k + 1);
+    const int64_t ncf = (int64_t)F.host.cells.size();
+    if (values_per_cell != 1 && values_per_cell != n3) throw Error(GCMG_ERR_ARG, "values_per_cell must be 1 or (k+1)^3");
+    if (ncf > 0 && !nu) throw Error(GCMG_ERR_ARG, "null coefficient");
+    if (any_learned(H)) throw Error(GCMG_ERR_ARG, "the learned smoother assumes a unit coefficient");
+    // validate the input before touching the level data
+    {
+      const int64_t n = ncf * values_per_cell;
+      int* bad = H.scratch.as<int>();
+      ck(cudaMemsetAsync(bad, 0, sizeof(int), H.stream), "memset");
+      launch_check_positive(nu, n, bad, H.stream);
+      int hb = 0;
+      ck(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, H.stream), "copy");
+      ck(cudaStreamSynchronize(H.stream), "sync");
+      if (hb) throw Error(GCMG_ERR_ARG, "coefficient values must be positive and finite");
+    }
+    const int nl = (int)H.lev.size();
+    for (int l = 0; l < nl; ++l) {
+      LevelDev& L = *H.lev[l];
+      if (!L.coef.p) L.coef.alloc(std::max<size_t>(1, L.host.cells.size()) * sizeof(double));
+      L.cl.coef = L.coef.as<double>();
+    }
+    for (int l = 1; l < nl; ++l) H.tr[l]->tl.coarse = H.lev[l - 1]->cl;
+    if (values_per_cell == 1)
+      ck(cudaMemcpyAsync(F.coef.p, nu, ncf * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
+    else
+      launch_coef_harmonic(k, ncf, nu, F.coef.as<double>(), H.stream);
+    for (int l = nl - 2; l >= 0; --l) {
+      const TransferDev& T = *H.tr[l + 1];
+      launch_coef_coarsen((int)H.lev[l]->host.cells.size(), T.fine_of.as<int32_t>(), T.refined.as<uint8_t>(),
+                          H.lev[l + 1]->coef.as<double>(), H.lev[l]->coef.as<double>(), H.stream);
+    }
+    ck(cudaGetLastError(), "coefficient");
+    setup_numerics(H);
+    ck(cudaStreamSynchronize(H.stream), "coefficient");
+  });
+}
+
+int gcmg_get_coefficient(gcmg_handle* h, int level, double* nu) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    check_level(h->h, level);
+    Handle& H = h->h;
+    LevelDev& L = *H.lev[level];
+    const size_t nc = L.host.cells.size();
+    if (nc && !nu) throw Error(GCMG_ERR_ARG, "bad vector");
+    if (L.cl.coef) {
+      ck(cudaMemcpyAsync(nu, L.coef.p, nc * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
+    } else {
+      std::vector<double> one(nc, 1.0);
+      ck(cudaMemcpyAsync(nu, one.data(), nc * sizeof(double), cudaMemcpyHostToDevice, H.stream), "copy");
+    }
+    ck(cudaStreamSynchronize(H.stream), "copy");
+  });
+}
+
+int gcmg_quadrature_points(gcmg_handle* h, double* xyz) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    Handle& H = h->h;
+    LevelDev& F = *H.lev.back();
+    const int64_t nc = (int64_t)F.host.cells.size();
+    if (nc && !xyz) throw Error(GCMG_ERR_ARG, "bad vector");
+    launch_quadrature_points(F.cl, nc, xyz, H.stream);
+    ck(cudaStreamSynchronize(H.stream), "quadrature points");
   });
 }
 

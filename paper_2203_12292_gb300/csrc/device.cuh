@@ -55,6 +55,7 @@ struct DevTables {
   T Be[NMAX][NMAX];         // rows of B reordered: symmetric modes first, then antisymmetric
   T lame[NMAX];             // eigenvalues in the same order
   T lam3[(KMAX + 1) * (KMAX + 1) * (KMAX + 1)];  // lame[a] + lame[b] + lame[c], a fastest
+  T xi[NMAX];               // Gauss-Lobatto support points on [0,1]
 };
 
 // every translation unit holds its own copy of the tables (no relocatable
@@ -90,6 +91,7 @@ static inline void fill_tables(DevTables<double>* td, DevTables<float>* tf) {
       d.lam[i] = b.lam[i];
       d.gq[i] = b.gq[i];
       d.gw[i] = b.gw[i];
+      d.xi[i] = b.xi[i];
       for (int j = 0; j < NMAX; ++j) {
         d.B[i][j] = b.B[i][j];
         d.I[0][i][j] = b.I[0][i][j];

@@ -27,6 +27,7 @@ struct LevelDev {
   // learned smoother: kind, parameter copy, bf16 diagonal features per cell
   int smoother = GCMG_SMOOTHER_CHEBYSHEV;
   DevBuf mlp_image, dfeat;  // packed bf16 weights of the fused kernel
+  DevBuf coef;              // per cell coefficient nu_e (allocated once one is set)
   int64_t n() const { return host.n_free; }
 };
 
@@ -107,6 +108,9 @@ struct Handle {
 // set-up of all levels, transfers, diagonals, coarse factor and eigenvalue
 // estimates of one problem (Sec. 5 set-up); throws Error
 void setup_handle(Handle& H, const std::vector<Octree>& meshes, int lmax, const gcmg_config& cfg);
+// the operator-dependent parts of the set-up: Jacobi diagonals, coarse
+// inverse, Chebyshev eigenvalue estimates (after a change of coefficient)
+void setup_numerics(Handle& H);
 void upload_all_tables();
 void check_config(const gcmg_config* cfg);
 void check_level(const Handle& h, int level);

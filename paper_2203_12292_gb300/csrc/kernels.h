@@ -12,7 +12,7 @@ namespace gcmg {
 // count of kernel launches issued by the library (all host threads)
 void note_launches(int n);
 
-enum CellMode { MODE_VMULT = 0, MODE_RHS = 1, MODE_DIAG = 2 };
+enum CellMode { MODE_VMULT = 0, MODE_RHS = 1, MODE_DIAG = 2, MODE_LIFT = 3 };
 
 // arguments of the tile kernels (operator, right-hand side, diagonal)
 struct CellLaunch {
@@ -35,17 +35,38 @@ struct CellLaunch {
   int use_lines;  // 1: fp32 operator with the line-parallel kernel
   int threads;    // threads per CTA of the line-parallel operator kernel (128, 256, 384 or 512)
   double lo, dom;
+  const double* coef;  // per cell coefficient nu_e (element matrix nu_e h A_ref); null: 1
 };
 
+// analytic function of a right-hand side or of Dirichlet data
+enum FuncKind { FUNC_ONE = 0, FUNC_FOURIER = 1, FUNC_GAUSSIAN = 2, FUNC_POLYNOMIAL = 3 };
 struct RhsDesc {
-  const double* modes;  // per mode: kappa_x, kappa_y, kappa_z, phi
-  int n_modes;          // 0: f = 1
-  double amp;
+  int kind;               // FuncKind
+  const double* params;   // FOURIER: per mode kx, ky, kz, phi; GAUSSIAN: alpha, x0, y0, z0;
+                          // POLYNOMIAL: per term c, a, b, e (u = sum c x^a y^b z^e)
+  int n;                  // modes or terms
+  double amp;             // FOURIER: amplitude
 };
 
 // dst = A src (add = 0) or dst += A src (add = 1), precision by `fp64`
 void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, int add, cudaStream_t s);
+// dst = C^T F: Gauss quadrature of f against the basis (FOURIER, ONE: f
+// itself; GAUSSIAN, POLYNOMIAL: f = -Lap u of the manufactured solution u)
 void launch_rhs(const CellLaunch& L, const RhsDesc& f, double* dst, cudaStream_t s);
+// dst -= C^T A_all u_g: the lifting u_g of the Dirichlet data g = u (u at
+// boundary support points, interpolated at hanging points, zero elsewhere)
+void launch_rhs_lift(const CellLaunch& L, const RhsDesc& u, double* dst, cudaStream_t s);
+
+// variable coefficient: nu_e = (sum_q w_q) / (sum_q w_q / nu_q) from the
+// (k+1)^3 Gauss-point values of every cell; coarse cells from the fine level
+// (the fine cell's value, or the mean of the eight children of a refined
+// cell); Gauss points of every cell (n_cells x (k+1)^3 x 3, x fastest)
+void launch_coef_harmonic(int k, int64_t n_cells, const double* nu_q, double* nu, cudaStream_t s);
+void launch_coef_coarsen(int n_coarse, const int32_t* fine_of, const uint8_t* refined, const double* nu_f,
+                         double* nu_c, cudaStream_t s);
+void launch_quadrature_points(const CellLaunch& L, int64_t n_cells, double* xyz, cudaStream_t s);
+// *bad = 1 if any of v[0..n) is not positive and finite (*bad unchanged otherwise)
+void launch_check_positive(const double* v, int64_t n, int* bad, cudaStream_t s);
 void launch_diag(const CellLaunch& L, const double* diag_tab, double* dst, cudaStream_t s);
 // diag_tab[m * (k+1)^3 + j] = (C_m^T A_ref C_m)_{jj} for all 512 masks m
 void launch_diag_table(int k, double* diag_tab, cudaStream_t s);

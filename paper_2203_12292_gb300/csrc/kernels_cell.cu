@@ -56,11 +56,89 @@ struct CellArgs {
   int tc;
   int max_local;
   int add;
-  const double* modes;
-  int n_modes;
-  double amp;
+  RhsDesc fn;
   const double* diag_tab;
+  const double* coef;  // per cell nu_e, null: 1
 };
+
+// scale of the element matrix of cell ci: nu_e h (h = dom 2^-level)
+template <typename T>
+__device__ __forceinline__ double cell_scale(const CellArgs<T>& A, double dom, int level, int ci) {
+  const double h = ldexp(dom, -level);
+  return A.coef ? h * A.coef[ci] : h;
+}
+
+// the analytic functions of RhsDesc: f (right-hand side) and u (manufactured
+// solution, whose boundary values are the Dirichlet data)
+__device__ inline double int_pow(double x, int e) {
+  double r = 1.0;
+  for (int i = 0; i < e; ++i) r *= x;
+  return r;
+}
+
+__device__ inline double func_u(const RhsDesc& F, double x, double y, double z) {
+  if (F.kind == FUNC_GAUSSIAN) {
+    // (alpha sqrt(2 pi))^-3 exp(-|x - x0|^2 / alpha^2)
+    const double al = F.params[0];
+    const double dx = x - F.params[1], dy = y - F.params[2], dz = z - F.params[3];
+    const double c = 1.0 / (al * sqrt(2.0 * M_PI));
+    return c * c * c * exp(-(dx * dx + dy * dy + dz * dz) / (al * al));
+  }
+  if (F.kind == FUNC_POLYNOMIAL) {
+    double u = 0.0;
+    for (int m = 0; m < F.n; ++m) {
+      const double* t = F.params + 4 * m;
+      u += t[0] * int_pow(x, (int)t[1]) * int_pow(y, (int)t[2]) * int_pow(z, (int)t[3]);
+    }
+    return u;
+  }
+  return 0.0;
+}
+
+__device__ inline double func_f(const RhsDesc& F, double x, double y, double z) {
+  switch (F.kind) {
+    case FUNC_FOURIER: {
+      double f = 0.0;
+      for (int m = 0; m < F.n; ++m) {
+        const double* md = F.params + 4 * m;
+        f += cos(2.0 * M_PI * (md[0] * x + md[1] * y + md[2] * z) + md[3]);
+      }
+      return f * F.amp;
+    }
+    case FUNC_GAUSSIAN: {
+      // -Lap u = u (6 / alpha^2 - 4 |x - x0|^2 / alpha^4)
+      const double a = F.params[0] * F.params[0];
+      const double dx = x - F.params[1], dy = y - F.params[2], dz = z - F.params[3];
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      return func_u(F, x, y, z) * (6.0 / a - 4.0 * r2 / (a * a));
+    }
+    case FUNC_POLYNOMIAL: {
+      double f = 0.0;
+      for (int m = 0; m < F.n; ++m) {
+        const double* t = F.params + 4 * m;
+        const int a = (int)t[1], b = (int)t[2], e = (int)t[3];
+        if (a >= 2) f -= t[0] * a * (a - 1) * int_pow(x, a - 2) * int_pow(y, b) * int_pow(z, e);
+        if (b >= 2) f -= t[0] * b * (b - 1) * int_pow(x, a) * int_pow(y, b - 2) * int_pow(z, e);
+        if (e >= 2) f -= t[0] * e * (e - 1) * int_pow(x, a) * int_pow(y, b) * int_pow(z, e - 2);
+      }
+      return f;
+    }
+    default:
+      return 1.0;
+  }
+}
+
+// Is local node (a,b,c) of a cell with hanging mask m on one of its hanging
+// faces or edges?  (Such a node takes, before C_e, the value of the parent
+// cell's node with the same local index.)
+template <int K>
+__device__ __forceinline__ bool node_hangs(uint16_t m, int a, int b, int c) {
+  if (!(m & MASK_HANG)) return false;
+  const bool o0 = a == (m & 1) * K, o1 = b == ((m >> 1) & 1) * K, o2 = c == ((m >> 2) & 1) * K;
+  const bool f0 = (m >> 3) & 1, f1 = (m >> 4) & 1, f2 = (m >> 5) & 1;
+  const bool e0 = (m >> 6) & 1, e1 = (m >> 7) & 1, e2 = (m >> 8) & 1;
+  return (f0 && o0) || (f1 && o1) || (f2 && o2) || (e0 && o1 && o2) || (e1 && o0 && o2) || (e2 && o0 && o1);
+}
 
 struct SmemLayout {
   size_t meta, h, mask, cell, cb, xs, ys, total;
@@ -144,7 +222,8 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
       const int cell = A.perm[ti.cell_begin + c0 + j];
       sm_cell[j] = (uint16_t)cell;
       sm_mask[j] = sm_meta[cell].mask;
-      sm_h[j] = (T)ldexp(A.dom, -(int)sm_meta[cell].level);
+      // MODE_LIFT applies -A_e: the cell operator is linear in h
+      sm_h[j] = (T)cell_scale(A, MODE == MODE_LIFT ? -A.dom : A.dom, sm_meta[cell].level, ti.cell_begin + cell);
     }
     __syncthreads();
     if (MODE == MODE_VMULT) {
@@ -167,6 +246,28 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
         const int j = t / N3, n = t - j * N3;
         cb[t] = (T)(A.diag_tab[(sm_mask[j] & 0x1FF) * N3 + n]) * sm_h[j];
       }
+    } else if (MODE == MODE_LIFT) {
+      // u_g before C_e: at a node of a hanging face or edge the value at the
+      // parent's node with the same local index, elsewhere the value at the
+      // node; u there if the position is on the domain boundary, else zero
+      for (int t = threadIdx.x; t < nch * N3; t += blockDim.x) {
+        const int j = t / N3, n = t - j * N3;
+        const int nd[3] = {n % N, (n / N) % N, n / N2};
+        const int ci = ti.cell_begin + sm_cell[j];
+        const int lev = sm_meta[sm_cell[j]].level;
+        const bool hang = node_hangs<K>(sm_mask[j], nd[0], nd[1], nd[2]);
+        const int l = hang ? lev - 1 : lev;
+        const double h = ldexp(A.dom, -l);
+        const int last = (1 << l) - 1;
+        double p[3];
+        bool bnd = false;
+        for (int d = 0; d < 3; ++d) {
+          const int I = hang ? (A.cell_ijk[3 * ci + d] >> 1) : A.cell_ijk[3 * ci + d];
+          bnd |= (nd[d] == 0 && I == 0) || (nd[d] == K && I == last);
+          p[d] = A.lo + h * ((double)I + tab<double>(K).xi[nd[d]]);
+        }
+        cb[t] = bnd ? (T)func_u(A.fn, p[0], p[1], p[2]) : T(0);
+      }
     } else {  // MODE_RHS: h^3 w_q f(x_q) at the Gauss points, then S^T
       for (int t = threadIdx.x; t < nch * N3; t += blockDim.x) {
         const int j = t / N3, n = t - j * N3;
@@ -176,15 +277,7 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
         const double x = A.lo + h * (A.cell_ijk[3 * ci + 0] + (double)tab<double>(K).gq[qa]);
         const double y = A.lo + h * (A.cell_ijk[3 * ci + 1] + (double)tab<double>(K).gq[qb]);
         const double z = A.lo + h * (A.cell_ijk[3 * ci + 2] + (double)tab<double>(K).gq[qc]);
-        double f = 1.0;
-        if (A.n_modes > 0) {
-          f = 0.0;
-          for (int m = 0; m < A.n_modes; ++m) {
-            const double* md = A.modes + 4 * m;
-            f += cos(2.0 * M_PI * (md[0] * x + md[1] * y + md[2] * z) + md[3]);
-          }
-          f *= A.amp;
-        }
+        const double f = func_f(A.fn, x, y, z);
         const double w = tab<double>(K).gw[qa] * tab<double>(K).gw[qb] * tab<double>(K).gw[qc];
         cb[t] = (T)(w * h * h * h * f);
       }
@@ -211,6 +304,28 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
     if (MODE == MODE_VMULT) {
       hanging_all<K, false>(cb, sm_mask, nch);  // C_e
       cell_laplace<K>(cb, sm_h, nch);           // S^T Q S
+    }
+    if (MODE == MODE_LIFT) {
+      hanging_all<K, false>(cb, sm_mask, nch);  // C_e: interpolated boundary values at hanging nodes
+      // support points on the boundary carry u itself, hanging or not
+      for (int t = threadIdx.x; t < nch * N3; t += blockDim.x) {
+        const int j = t / N3, n = t - j * N3;
+        const int nd[3] = {n % N, (n / N) % N, n / N2};
+        const int ci = ti.cell_begin + sm_cell[j];
+        const int lev = sm_meta[sm_cell[j]].level;
+        const double h = ldexp(A.dom, -lev);
+        const int last = (1 << lev) - 1;
+        double p[3];
+        bool bnd = false;
+        for (int d = 0; d < 3; ++d) {
+          const int I = A.cell_ijk[3 * ci + d];
+          bnd |= (nd[d] == 0 && I == 0) || (nd[d] == K && I == last);
+          p[d] = A.lo + h * ((double)I + tab<double>(K).xi[nd[d]]);
+        }
+        if (bnd && node_hangs<K>(sm_mask[j], nd[0], nd[1], nd[2])) cb[t] = (T)func_u(A.fn, p[0], p[1], p[2]);
+      }
+      __syncthreads();
+      cell_laplace<K>(cb, sm_h, nch);  // -A_e u_g
     }
     if (MODE != MODE_DIAG) hanging_all<K, true>(cb, sm_mask, nch);  // C_e^T
     // G_e^T into the shared accumulator, sub-colour by sub-colour
@@ -286,7 +401,7 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
     sm_cell[threadIdx.x] = (uint16_t)cell;
     sm_mask[threadIdx.x] = m.mask;
     sm_sub[threadIdx.x] = m.sub;
-    sm_h[threadIdx.x] = (T)ldexp(A.dom, -(int)m.level);
+    sm_h[threadIdx.x] = (T)cell_scale(A, A.dom, m.level, ti.cell_begin + cell);
     hang = (m.mask & MASK_HANG) != 0;
   }
   hang = __syncthreads_or(hang);
@@ -453,7 +568,7 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines_df(CellArgs<double> A) {
     sm_cell[threadIdx.x] = (uint16_t)cell;
     sm_mask[threadIdx.x] = m.mask;
     sm_sub[threadIdx.x] = m.sub;
-    sm_h[threadIdx.x] = df_from(ldexp(A.dom, -(int)m.level));
+    sm_h[threadIdx.x] = df_from(cell_scale(A, A.dom, m.level, ti.cell_begin + cell));
     hang = (m.mask & MASK_HANG) != 0;
   }
   hang = __syncthreads_or(hang);
@@ -946,7 +1061,8 @@ __global__ void __launch_bounds__(11 * 32, 2) vmult_slab(CellArgs<float> A) {
   slab_sweeps_xy<N>(sv, tb.Be, true);   // B along x
   slab_sweeps_yx<N>(sv, tb.Be, true);   // B along y
   to_z<K>(sv, zv, reg, c);
-  const float h = active ? ldexpf((float)A.dom, -(int)sm_lev[qq]) : 0.f;
+  float h = active ? ldexpf((float)A.dom, -(int)sm_lev[qq]) : 0.f;
+  if (A.coef && active) h = (float)cell_scale(A, A.dom, sm_lev[qq], ti.cell_begin + qq);
   z_lines<N>(zv, tb.Be, lam3, c, h);    // B, h (lam_a + lam_b + lam_c), B^T along z
   to_slab<K>(zv, sv, reg, c);
   slab_sweeps_yx<N>(sv, tb.Be, false);  // B^T along y
@@ -1122,6 +1238,7 @@ CellArgs<T> make_args(const CellLaunch& L) {
   A.halo = static_cast<T*>(L.halo);
   A.lo = L.lo;
   A.dom = L.dom;
+  A.coef = L.coef;
   A.tc = L.tc;
   A.max_local = L.max_local;
   return A;
@@ -1176,10 +1293,17 @@ void launch_rhs(const CellLaunch& L, const RhsDesc& f, double* dst, cudaStream_t
   if (L.n_tiles == 0) return;
   CellArgs<double> A = make_args<double>(L);
   A.dst = dst;
-  A.modes = f.modes;
-  A.n_modes = f.n_modes;
-  A.amp = f.amp;
+  A.fn = f;
   dispatch<double, MODE_RHS>(L, A, s);
+}
+
+void launch_rhs_lift(const CellLaunch& L, const RhsDesc& u, double* dst, cudaStream_t s) {
+  if (L.n_tiles == 0) return;
+  CellArgs<double> A = make_args<double>(L);
+  A.dst = dst;
+  A.add = 1;
+  A.fn = u;
+  dispatch<double, MODE_LIFT>(L, A, s);
 }
 
 void launch_diag(const CellLaunch& L, const double* diag_tab, double* dst, cudaStream_t s) {
@@ -1209,6 +1333,102 @@ void launch_diag_table(int k, double* tab_out, cudaStream_t s) {
     case 4: { launch_pdl(diag_table_kernel<4>, nb, BLOCK, sm, s, tab_out, tc); note_launches(1); } break;
     default: break;
   }
+}
+
+namespace {
+
+template <int K>
+__global__ void coef_harmonic_kernel(int64_t n_cells, const double* __restrict__ nu_q, double* __restrict__ nu) {
+  constexpr int N = K + 1, N3 = N * N * N;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const DevTables<double>& tb = tab<double>(K);
+  double sw = 0.0, s = 0.0;
+  for (int q = 0; q < N3; ++q) {
+    const double w = tb.gw[q % N] * tb.gw[(q / N) % N] * tb.gw[q / (N * N)];
+    sw += w;
+    s += w / nu_q[c * N3 + q];
+  }
+  nu[c] = sw / s;
+}
+
+__global__ void check_positive_kernel(const double* __restrict__ v, int64_t n, int* bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = v[i];
+    if (!(x > 0.0 && x <= 1.7976931348623157e308)) *bad = 1;
+  }
+}
+
+__global__ void coef_coarsen_kernel(int n_coarse, const int32_t* __restrict__ fine_of, const uint8_t* __restrict__ refined,
+                                    const double* __restrict__ nu_f, double* __restrict__ nu_c) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_coarse) return;
+  const int32_t f = fine_of[c];
+  if (!refined[c]) {
+    nu_c[c] = nu_f[f];
+    return;
+  }
+  double s = 0.0;
+  for (int q = 0; q < 8; ++q) s += nu_f[f + q];
+  nu_c[c] = s / 8.0;
+}
+
+template <int K>
+__global__ void quadrature_points_kernel(int64_t n_cells, const CellMeta* __restrict__ meta,
+                                         const int32_t* __restrict__ ijk, double lo, double dom,
+                                         double* __restrict__ xyz) {
+  constexpr int N = K + 1, N3 = N * N * N;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_cells * N3) return;
+  const int64_t c = t / N3;
+  const int q = (int)(t - c * N3);
+  const int qi[3] = {q % N, (q / N) % N, q / (N * N)};
+  const double h = ldexp(dom, -(int)meta[c].level);
+  for (int d = 0; d < 3; ++d) xyz[3 * t + d] = lo + h * ((double)ijk[3 * c + d] + tab<double>(K).gq[qi[d]]);
+}
+
+}  // namespace
+
+void launch_coef_harmonic(int k, int64_t n_cells, const double* nu_q, double* nu, cudaStream_t s) {
+  if (n_cells == 0) return;
+  const int grid = (int)((n_cells + 255) / 256);
+  switch (k) {
+    case 1: coef_harmonic_kernel<1><<<grid, 256, 0, s>>>(n_cells, nu_q, nu); break;
+    case 2: coef_harmonic_kernel<2><<<grid, 256, 0, s>>>(n_cells, nu_q, nu); break;
+    case 3: coef_harmonic_kernel<3><<<grid, 256, 0, s>>>(n_cells, nu_q, nu); break;
+    case 4: coef_harmonic_kernel<4><<<grid, 256, 0, s>>>(n_cells, nu_q, nu); break;
+    default: return;
+  }
+  note_launches(1);
+}
+
+void launch_check_positive(const double* v, int64_t n, int* bad, cudaStream_t s) {
+  if (n == 0) return;
+  const int64_t g = std::min<int64_t>((n + 255) / 256, 152 * 8);
+  check_positive_kernel<<<(int)g, 256, 0, s>>>(v, n, bad);
+  note_launches(1);
+}
+
+void launch_coef_coarsen(int n_coarse, const int32_t* fine_of, const uint8_t* refined, const double* nu_f,
+                         double* nu_c, cudaStream_t s) {
+  if (n_coarse == 0) return;
+  coef_coarsen_kernel<<<(n_coarse + 255) / 256, 256, 0, s>>>(n_coarse, fine_of, refined, nu_f, nu_c);
+  note_launches(1);
+}
+
+void launch_quadrature_points(const CellLaunch& L, int64_t n_cells, double* xyz, cudaStream_t s) {
+  const int n3 = (L.k + 1) * (L.k + 1) * (L.k + 1);
+  const int64_t n = n_cells * n3;
+  if (n == 0) return;
+  const int grid = (int)((n + 255) / 256);
+  switch (L.k) {
+    case 1: quadrature_points_kernel<1><<<grid, 256, 0, s>>>(n_cells, L.meta, L.cell_ijk, L.lo, L.dom, xyz); break;
+    case 2: quadrature_points_kernel<2><<<grid, 256, 0, s>>>(n_cells, L.meta, L.cell_ijk, L.lo, L.dom, xyz); break;
+    case 3: quadrature_points_kernel<3><<<grid, 256, 0, s>>>(n_cells, L.meta, L.cell_ijk, L.lo, L.dom, xyz); break;
+    case 4: quadrature_points_kernel<4><<<grid, 256, 0, s>>>(n_cells, L.meta, L.cell_ijk, L.lo, L.dom, xyz); break;
+    default: return;
+  }
+  note_launches(1);
 }
 
 }  // namespace gcmg
