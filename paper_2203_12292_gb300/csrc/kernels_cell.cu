@@ -354,17 +354,20 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
 }
 
 // ---------------------------------------------------------------------------
-// operator for tiles of at most CHUNK cells (the default configuration):
-// every thread owns the same lines of the tile in every phase (line l of the
-// tile = cell l / (k+1)^2, position l % (k+1)^2), so their cell and offsets
-// are computed once per tile; the hanging-node passes are skipped for tiles
-// without hanging cells; the accumulation runs sub-colour by sub-colour from
-// the cells' sub-colour numbers.
+// fp32 operator for tiles of at most CHUNK cells (the default configuration):
+// every thread owns the same lines of the tile in every phase, so their cell,
+// position and gather/scatter starts are computed once per tile and kept in
+// registers; the tile's metadata and DoFs arrive by asynchronous copies that
+// are all in flight together; the hanging-node passes do no work for tiles
+// without hanging cells; the accumulation runs sub-colour by sub-colour, each
+// sub-colour a contiguous range of the permuted cell list.
 // ---------------------------------------------------------------------------
 template <int K, typename T>
 __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
+  static_assert(sizeof(T) == 4, "the fp64 operator is vmult_lines_df");
   pdl_begin();
   constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
+  constexpr int LPT = (CHUNK * N2 + BLOCK - 1) / BLOCK;  // lines per thread
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout SL = smem_layout<T>(N3, A.tc, A.max_local);
   CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem + SL.meta);
@@ -374,25 +377,42 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
   T* cb = reinterpret_cast<T*>(smem + SL.cb);
   T* xs = reinterpret_cast<T*>(smem + SL.xs);
   T* ys = xs;  // the accumulator reuses the input buffer once the gather is done
-  __shared__ uint8_t sm_sub[CHUNK];
   __shared__ T s_lab[N2];
-  __shared__ uint16_t s_so[N3];  // per local node: entity slot | offset << 5
+  __shared__ uint16_t s_so[N3];          // per local node: entity slot | offset << 5
+  __shared__ uint16_t s_sub[CHUNK + 1];  // sub-colour starts (positions in the permuted cell list)
   const DevTables<T>& tb = tab<T>(K);
 
   const TileInfo ti = A.tiles[blockIdx.x];
-  const int nc = ti.n_cells;  // <= CHUNK
-  const int nl = nc * N2;     // x-lines of the tile
+  const int nc = ti.n_cells;
+  const int nl = nc * N2;
+  const int nloc = ti.n_owned + ti.n_foreign;
+  {  // asynchronous copies of the tile's metadata and DoFs, all in flight at once
+    const uint4* gm = reinterpret_cast<const uint4*>(A.meta + ti.cell_begin);
+    uint4* smm = reinterpret_cast<uint4*>(sm_meta);
+    for (int i = threadIdx.x; i < nc * 4; i += BLOCK) cp_async16(smm + i, gm + i);
+    const T* so_ = A.src + ti.dof_begin;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < ti.n_owned; i += BLOCK) cp_async(xs + i, so_ + i);
+    const int32_t* fl = A.foreign + ti.foreign_begin;
+    T* xf = xs + ti.n_owned;
+    for (int i0 = threadIdx.x; i0 < ti.n_foreign; i0 += 4 * BLOCK) {
+      int idx[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) idx[u] = (i0 + u * BLOCK < ti.n_foreign) ? fl[i0 + u * BLOCK] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (idx[u] >= 0) cp_async(xf + i0 + u * BLOCK, A.src + idx[u]);
+    }
+  }
   for (int n = threadIdx.x; n < N3; n += BLOCK) {
     int slot, off;
     node_slot<K>(n % N, (n / N) % N, n / N2, slot, off);
     s_so[n] = (uint16_t)(slot | (off << 5));
   }
-  const int nloc = ti.n_owned + ti.n_foreign;
-  load_meta(sm_meta, A.meta, ti.cell_begin, nc);
-  load_tile_dofs(xs, A.src, A.foreign, ti);
-  constexpr bool EO = sizeof(T) == 8;  // fp64: even-odd sweeps (FP64 pipe bound), modes in mode order
-  for (int r = threadIdx.x; r < N2; r += BLOCK)
-    s_lab[r] = EO ? tb.lame[r % N] + tb.lame[r / N] : tb.lam[r % N] + tb.lam[r / N];
+  if (threadIdx.x == 0) xs[nloc] = T(0);  // zero slot: absent DoFs gather 0
+  for (int r = threadIdx.x; r < N2; r += BLOCK) s_lab[r] = tb.lam[r % N] + tb.lam[r / N];
+  for (int s = threadIdx.x; s <= ti.n_sub; s += BLOCK) s_sub[s] = A.subptr[ti.sub_begin + s];
+  cp_async_wait_all();
   __syncthreads();
   int hang = 0;
   if (threadIdx.x < nc) {
@@ -400,63 +420,70 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
     const CellMeta& m = sm_meta[cell];
     sm_cell[threadIdx.x] = (uint16_t)cell;
     sm_mask[threadIdx.x] = m.mask;
-    sm_sub[threadIdx.x] = m.sub;
     sm_h[threadIdx.x] = (T)cell_scale(A, A.dom, m.level, ti.cell_begin + cell);
     hang = (m.mask & MASK_HANG) != 0;
   }
   hang = __syncthreads_or(hang);
 
-  // G_e: gather the x-lines (line t of the tile = cell t / N2, position r = b + N c)
-#pragma unroll 1
-  for (int t = threadIdx.x; t < nl; t += BLOCK) {
-    const int j = t / N2, r = t - j * N2;
-    const uint16_t* ls = sm_meta[sm_cell[j]].ls;
-    T* out = cb + j * N3 + N * r;
+  // the thread's lines t = tid + BLOCK i (cell position j = t / N2, r = t % N2 = b + N c) and the
+  // tile-local starts of their three x-classes (node a = 0, interior 1..K-1, a = K); absent DoFs
+  // point to the zero slot xs[nloc], so gather and scatter need no branch per node (the slot
+  // reads 0 in the gather and absorbs the dropped contributions in the scatter; it is never
+  // written out)
+  int lj[LPT], lr[LPT], g0[LPT], g1[LPT], g2[LPT];
 #pragma unroll
-    for (int a = 0; a < N; ++a) {
-      const int so = s_so[N * r + a];
-      const uint16_t l = ls[so & 31];
-      out[a] = (l == LS_NONE) ? T(0) : xs[l + (so >> 5)];
+  for (int i = 0; i < LPT; ++i) {
+    const int t = threadIdx.x + BLOCK * i;
+    lj[i] = t / N2;
+    lr[i] = t - lj[i] * N2;
+    g0[i] = g1[i] = g2[i] = nloc;
+    if (t < nl) {
+      const uint16_t* ls = sm_meta[sm_cell[lj[i]]].ls;
+      const int so0 = s_so[N * lr[i]], so1 = s_so[N * lr[i] + 1], so2 = s_so[N * lr[i] + K];
+      const uint16_t l0 = ls[so0 & 31], l1 = ls[so1 & 31], l2 = ls[so2 & 31];
+      if (l0 != LS_NONE) g0[i] = l0 + (so0 >> 5);
+      if (l1 != LS_NONE) g1[i] = l1 + (so1 >> 5);
+      if (l2 != LS_NONE) g2[i] = l2 + (so2 >> 5);
+    }
+  }
+  // G_e: gather the x-lines
+#pragma unroll
+  for (int i = 0; i < LPT; ++i) {
+    const int t = threadIdx.x + BLOCK * i;
+    if (t < nl) {
+      T* out = cb + N * t;
+      out[0] = xs[g0[i]];
+#pragma unroll
+      for (int a = 1; a < K; ++a) out[a] = xs[g1[i] == nloc ? nloc : g1[i] + a - 1];
+      out[K] = xs[g2[i]];
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < nloc; i += BLOCK) ys[i] = T(0);  // ordered before the scatter by the sweeps' barriers
+  for (int i = threadIdx.x; i < nloc; i += BLOCK) ys[i] = T(0);
   hanging_all<K, false>(cb, sm_mask, hang ? nc : 0);  // C_e (no work without hanging cells)
 
   // S^T Q S: x, y forward, z forward/scale/backward, y, x backward
-#pragma unroll 1
-  for (int t = threadIdx.x; t < nl; t += BLOCK) {
-    T* p = cb + (t / N2) * N3 + N * (t % N2);
-    if (EO)
-      eo_forward<N, 0, 1>(p, tb.Be);
-    else
-      line_apply<N, 1, false>(p, tb.B);
+#pragma unroll
+  for (int i = 0; i < LPT; ++i) {
+    const int t = threadIdx.x + BLOCK * i;
+    if (t < nl) line_apply<N, 1, false>(cb + N * t, tb.B);
   }
   __syncthreads();
-#pragma unroll 1
-  for (int t = threadIdx.x; t < nl; t += BLOCK) {
-    const int j = t / N2, r = t - j * N2;
-    T* p = cb + j * N3 + r % N + N2 * (r / N);
-    if (EO)
-      eo_forward<N, 0, N>(p, tb.Be);
-    else
-      line_apply<N, N, false>(p, tb.B);
+#pragma unroll
+  for (int i = 0; i < LPT; ++i) {
+    const int t = threadIdx.x + BLOCK * i;
+    if (t < nl) line_apply<N, N, false>(cb + lj[i] * N3 + lr[i] % N + N2 * (lr[i] / N), tb.B);
   }
   __syncthreads();
-#pragma unroll 1
-  for (int t = threadIdx.x; t < nl; t += BLOCK) {
-    const int j = t / N2, r = t - j * N2;
-    T* p = cb + j * N3 + r;
-    T v[N];
 #pragma unroll
-    for (int c = 0; c < N; ++c) v[c] = p[c * N2];
-    const T hab = sm_h[j], lab = s_lab[r];
-    if (EO) {
-      eo_forward<N, 0, 1>(v, tb.Be);
+  for (int i = 0; i < LPT; ++i) {
+    const int t = threadIdx.x + BLOCK * i;
+    if (t < nl) {
+      T* p = cb + lj[i] * N3 + lr[i];
+      T v[N];
 #pragma unroll
-      for (int c = 0; c < N; ++c) v[c] *= hab * (tb.lame[c] + lab);
-      eo_backward<N, 0, 1>(v, tb.Be);
-    } else {
+      for (int c = 0; c < N; ++c) v[c] = p[c * N2];
+      const T hab = sm_h[lj[i]], lab = s_lab[lr[i]];
       T w[N];
 #pragma unroll
       for (int q = 0; q < N; ++q) {
@@ -470,48 +497,39 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
         T sum = 0;
 #pragma unroll
         for (int c = 0; c < N; ++c) sum += tb.B[c][q] * w[c];
-        v[q] = sum;
+        p[q * N2] = sum;
       }
     }
+  }
+  __syncthreads();
 #pragma unroll
-    for (int c = 0; c < N; ++c) p[c * N2] = v[c];
+  for (int i = 0; i < LPT; ++i) {
+    const int t = threadIdx.x + BLOCK * i;
+    if (t < nl) line_apply<N, N, true>(cb + lj[i] * N3 + lr[i] % N + N2 * (lr[i] / N), tb.B);
   }
   __syncthreads();
-#pragma unroll 1
-  for (int t = threadIdx.x; t < nl; t += BLOCK) {
-    const int j = t / N2, r = t - j * N2;
-    T* p = cb + j * N3 + r % N + N2 * (r / N);
-    if (EO)
-      eo_backward<N, 0, N>(p, tb.Be);
-    else
-      line_apply<N, N, true>(p, tb.B);
-  }
-  __syncthreads();
-#pragma unroll 1
-  for (int t = threadIdx.x; t < nl; t += BLOCK) {
-    T* p = cb + (t / N2) * N3 + N * (t % N2);
-    if (EO)
-      eo_backward<N, 0, 1>(p, tb.Be);
-    else
-      line_apply<N, 1, true>(p, tb.B);
+#pragma unroll
+  for (int i = 0; i < LPT; ++i) {
+    const int t = threadIdx.x + BLOCK * i;
+    if (t < nl) line_apply<N, 1, true>(cb + N * t, tb.B);
   }
   __syncthreads();
   hanging_all<K, true>(cb, sm_mask, hang ? nc : 0);  // C_e^T
 
-  // G_e^T into the tile accumulator, sub-colour by sub-colour
+  // G_e^T, sub-colour by sub-colour (cells of sub-colour s: positions s_sub[s] .. s_sub[s+1])
   for (int sc = 0; sc < ti.n_sub; ++sc) {
-#pragma unroll 1
-    for (int t = threadIdx.x; t < nl; t += BLOCK) {
-      const int j = t / N2;
-      if (sm_sub[j] != sc) continue;
-      const int r = t - j * N2;
-      const uint16_t* ls = sm_meta[sm_cell[j]].ls;
-      const T* in = cb + j * N3 + N * r;
+    const int t0 = s_sub[sc] * N2, t1 = s_sub[sc + 1] * N2;
 #pragma unroll
-      for (int a = 0; a < N; ++a) {
-        const int so = s_so[N * r + a];
-        const uint16_t l = ls[so & 31];
-        if (l != LS_NONE) ys[l + (so >> 5)] += in[a];
+    for (int i = 0; i < LPT; ++i) {
+      const int t = threadIdx.x + BLOCK * i;
+      if (t >= t0 && t < t1) {
+        const T* in = cb + N * t;
+        ys[g0[i]] += in[0];
+        if (g1[i] != nloc) {
+#pragma unroll
+          for (int a = 1; a < K; ++a) ys[g1[i] + a - 1] += in[a];
+        }
+        ys[g2[i]] += in[K];
       }
     }
     __syncthreads();
@@ -547,19 +565,35 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines_df(CellArgs<double> A) {
   const int nc = ti.n_cells;  // <= CHUNK
   const int nl = nc * N2;
   const int nloc = ti.n_owned + ti.n_foreign;
+  double* xd = reinterpret_cast<double*>(xs);
+  {  // asynchronous copies of the metadata and the fp64 DoFs, all in flight at once
+    const uint4* gm = reinterpret_cast<const uint4*>(A.meta + ti.cell_begin);
+    uint4* smm = reinterpret_cast<uint4*>(sm_meta);
+    for (int i = threadIdx.x; i < nc * 4; i += BLOCK) cp_async16(smm + i, gm + i);
+    const double* src = A.src + ti.dof_begin;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < ti.n_owned; i += BLOCK) cp_async(xd + i, src + i);
+    const int32_t* fl = A.foreign + ti.foreign_begin;
+    double* xf = xd + ti.n_owned;
+    for (int i0 = threadIdx.x; i0 < ti.n_foreign; i0 += 4 * BLOCK) {
+      int idx[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) idx[u] = (i0 + u * BLOCK < ti.n_foreign) ? fl[i0 + u * BLOCK] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (idx[u] >= 0) cp_async(xf + i0 + u * BLOCK, A.src + idx[u]);
+    }
+  }
   for (int n = threadIdx.x; n < N3; n += BLOCK) {
     int slot, off;
     node_slot<K>(n % N, (n / N) % N, n / N2, slot, off);
     s_so[n] = (uint16_t)(slot | (off << 5));
     s_lam3[n] = df_from(c_td[K].lam3[n]);
   }
-  load_meta(sm_meta, A.meta, ti.cell_begin, nc);
-  {
-    const double* src = A.src + ti.dof_begin;
-    for (int i = threadIdx.x; i < ti.n_owned; i += BLOCK) xs[i] = df_from(src[i]);
-    const int32_t* fl = A.foreign + ti.foreign_begin;
-    for (int i = threadIdx.x; i < ti.n_foreign; i += BLOCK) xs[ti.n_owned + i] = df_from(A.src[fl[i]]);
-  }
+  cp_async_wait_all();
+  // every thread converts the values it copied itself, in place (a df has the size of a double)
+  for (int i = threadIdx.x; i < ti.n_owned; i += BLOCK) xs[i] = df_from(xd[i]);
+  for (int i = threadIdx.x; i < ti.n_foreign; i += BLOCK) xs[ti.n_owned + i] = df_from(xd[ti.n_owned + i]);
   __syncthreads();
   int hang = 0;
   if (threadIdx.x < nc) {
@@ -1193,14 +1227,16 @@ void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
       return;
     }
   }
-  if (MODE == MODE_VMULT && L.tc <= CHUNK && (sizeof(T) == 8 || L.threads == BLOCK)) {
-    // vmult_lines keeps one tile-DoF buffer (input, then accumulator)
-    const size_t sm1 = sm - (size_t)L.max_local * sizeof(T);
-    ensure_smem(vmult_lines<K, T>, sm1);
-    launch_pdl(vmult_lines<K, T>, L.n_tiles, BLOCK, sm1, s, A);
-    note_launches(1);
-    run_halo<T>(L, A.dst, s);
-    return;
+  if constexpr (MODE == MODE_VMULT && sizeof(T) == 4) {
+    if (L.tc <= CHUNK && L.threads == BLOCK) {
+      // vmult_lines keeps one tile-DoF buffer (input, then accumulator) plus the zero slot
+      const size_t sm1 = sm - (size_t)L.max_local * sizeof(T) + 16;
+      ensure_smem(vmult_lines<K, T>, sm1);
+      launch_pdl(vmult_lines<K, T>, L.n_tiles, BLOCK, sm1, s, A);
+      note_launches(1);
+      run_halo<T>(L, A.dst, s);
+      return;
+    }
   }
   // the thread count is a tuning parameter of the fp32 operator only
   const int nt = (MODE == MODE_VMULT && sizeof(T) == 4) ? L.threads : BLOCK;
