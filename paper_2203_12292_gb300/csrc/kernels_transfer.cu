@@ -136,16 +136,27 @@ __global__ void __launch_bounds__(BLOCK) prolong_h(TArgs<T> A) {
     }
     s_e3[i] = (uint16_t)(((q & 1) * K + a) + M * ((((q >> 1) & 1) * K + b) + M * ((q >> 2) * K + c)));
   }
-  for (int t = threadIdx.x; t < nc * NSLOT; t += blockDim.x) sm_gsc[t] = A.gstart_c[(size_t)c0 * NSLOT + t];
+  for (int t = threadIdx.x; t < nc * NSLOT; t += blockDim.x) cp_async(sm_gsc + t, A.gstart_c + (size_t)c0 * NSLOT + t);
   __syncthreads();
-  // the fine cells' slot starts and ownership (children of a refined cell are consecutive)
+  // the fine cells' slot starts and ownership (children of a refined cell are consecutive),
+  // asynchronous copies all in flight at once
   for (int t = threadIdx.x; t < nc * 8 * NSLOT; t += blockDim.x) {
     const int jq = t / NSLOT, slot = t - jq * NSLOT, j = jq >> 3, q = jq & 7;
     const bool use = sm_ref[j] || q == 0;
     const int f = sm_fine[j] + q;
-    sm_gs[t] = use ? A.gstart_f[(size_t)f * NSLOT + slot] : -1;
-    if (slot == 0) sm_own[jq] = use ? A.own_f[f] : 0u;
+    if (use)
+      cp_async(sm_gs + t, A.gstart_f + (size_t)f * NSLOT + slot);
+    else
+      sm_gs[t] = -1;
+    if (slot == 0) {
+      if (use)
+        cp_async(sm_own + jq, A.own_f + f);
+      else
+        sm_own[jq] = 0u;
+    }
   }
+  cp_async_wait_all();
+  __syncthreads();
   // G^(c): the coarse values (RG loads in flight per thread)
   for (int t0 = threadIdx.x; t0 < nc * N3; t0 += RG * BLOCK) {
     T v[RG];
@@ -289,9 +300,18 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
       const int jq = t / NSLOT, slot = t - jq * NSLOT, j = jq >> 3, q = jq & 7;
       const bool use = sm_ref[j] || q == 0;
       const int f = sm_fine[j] + q;
-      sm_gs[t] = use ? A.gstart_f[(size_t)f * NSLOT + slot] : -1;
-      if (slot == 0) sm_own[jq] = use ? A.own_f[f] : 0u;
+      if (use)
+        cp_async(sm_gs + t, A.gstart_f + (size_t)f * NSLOT + slot);
+      else
+        sm_gs[t] = -1;
+      if (slot == 0) {
+        if (use)
+          cp_async(sm_own + jq, A.own_f + f);
+        else
+          sm_own[jq] = 0u;
+      }
     }
+    cp_async_wait_all();
     __syncthreads();
     // gather the owned fine values (RG loads in flight per thread)
     constexpr int RG = 8;
