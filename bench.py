@@ -57,11 +57,12 @@ METRIC = "fine-level vmult GDoF/s; solve time to 1e-8 rel. res., mixed/learned v
 # destination vector plus the per-cell metadata (roofline model of the
 # workload, per free DoF)
 BYTES_PER_DOF = {"fp32": 9.8, "fp64": 17.8}
-# DRAM bytes (read + write) of one launch of the fine-level tile kernel
-# vmult_lines<4,float> on this workload, from the ncu capture summarised in
-# profiles/vmult_lines_q4_octant_fp32.md (114.8 MB read + 53.9 MB written);
-# set to 0 (reported as null) when the kernel changes until it is re-captured
-VMULT_TRAFFIC_BYTES = 168.6e6
+# DRAM bytes (read + write) of one fine-level fp32 operator application on
+# this workload, both of its launches (tile kernel vmult_lines<4,float>:
+# 115.0 MB read + 54.8 MB written; halo pass: 110.2 MB + 6.9 MB), from the
+# ncu capture summarised in profiles/vmult_lines_q4_octant_fp32.md; set to 0
+# (reported as null) when the kernel changes until it is re-captured
+VMULT_TRAFFIC_BYTES = 286.9e6
 SAMPLE = synth.cube_octant(4, 2)  # 1/8 of the workload's cells, same recipe family
 
 
@@ -406,8 +407,8 @@ def main():
                          "kernel": "vmult_lines<4,float> line-parallel tile kernel + halo pass "
                                    "(fine-level fp32 operator, 32-cell tiles)",
                          "peak_kind": peak_kind, "bytes_per_dof": BYTES_PER_DOF["fp32"],
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the tile kernel, "
-                                           "one launch on this workload"},
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the tile kernel "
+                                           "and the halo pass, one application on this workload"},
             "cpu_baseline": cpu,
             "e2e": {"value": n / e2e_s / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 4 * n,
                     "d2h_bytes_per_step": 4 * n, "call": "gcmg_vmult_host, pinned host buffers, fp32"},
