@@ -486,8 +486,13 @@ void setup_numerics(Handle& H) {
     launch_invert(L.diag64.as<double>(), L.dinv64.as<double>(), L.dinv32.as<float>(), L.n(), H.stream);
   }
   ck(cudaGetLastError(), "diagonal");
+  ck(cudaStreamSynchronize(H.stream), "diagonal");
   setup_coarse(H);
-  for (int l = 1; l < nl; ++l) H.lev[l]->lam = H.cfg.eig_safety * estimate_lambda(H, l);
+  ck(cudaGetLastError(), "coarse matrix");
+  for (int l = 1; l < nl; ++l) {
+    H.lev[l]->lam = H.cfg.eig_safety * estimate_lambda(H, l);
+    ck(cudaGetLastError(), "eigenvalue estimate");
+  }
   H.g_core.reset();
   H.g_a.reset();
 }

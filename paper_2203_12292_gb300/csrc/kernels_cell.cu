@@ -1193,7 +1193,9 @@ __global__ void __launch_bounds__(BLOCK) diag_table_kernel(double* out, int tc) 
 
 template <typename KERN>
 void ensure_smem(KERN kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // the 48 KB default limit covers static plus dynamic shared memory; the
+  // kernels here hold at most 8 KB of static shared memory
+  if (bytes > 40 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <typename T>

@@ -325,3 +325,22 @@ def test_vmult_fp32_slab_kernel(gcmg, rec, k, tc):
         torch.cuda.synchronize()
         ref = c.levels[l].apply64(c.ovec(l, 700 + l).astype(np.float32).astype(np.float64))
         assert c.cmp(l, y, ref) < 2e-6, l
+
+
+@pytest.mark.parametrize("tc", [20, 24, 12])
+def test_tile_sizes_compute_the_same_operator(gcmg, tc):
+    """Tiles of 20 cells put the fp64 kernel's dynamic shared memory just
+    under 48 KB, where the static shared memory pushes the total over the
+    default limit (a launch error before the opt-in threshold was lowered)."""
+    mesh = gcmg.Mesh.from_recipe(synth.cube_octant(4, 1))
+    a = gcmg.Multigrid(mesh, 4, tile_cells=tc)
+    b = gcmg.Multigrid(mesh, 4)
+    assert a.info[a.finest].tile_cells == tc
+    perm = match(a.dof_coords(a.finest), b.dof_coords(b.finest))
+    for dt, tol in ((torch.float64, 1e-13), (torch.float32, 2e-6)):
+        xa = torch.tensor(synth.point_values(a.dof_coords(a.finest), 9), dtype=dt, device="cuda")
+        xb = torch.tensor(synth.point_values(b.dof_coords(b.finest), 9), dtype=dt, device="cuda")
+        ya, yb = torch.empty_like(xa), torch.empty_like(xb)
+        a.vmult(a.finest, xa, ya)
+        b.vmult(b.finest, xb, yb)
+        assert rel_err(ya.double().cpu().numpy(), yb.double().cpu().numpy()[perm]) < tol
