@@ -28,6 +28,10 @@ What it computes, each part a plain definition written out in fp64:
 * ``coefficient`` variable coefficient nu of -div(nu grad u): harmonic
                 cell averages of Gauss-point values on the finest level,
                 transfer to the coarser levels (Sec. 7, Sec. 3.5).
+* ``ls``        geometric local smoothing, the paper's comparison variant:
+                refinement levels, refinement-edge DoFs, the V-cycle with
+                edge treatment and the copy to/from all active levels
+                (Sec. 2.1, Algorithms 1-2).
 * ``mlp``       learned per-cell smoother, an extension outside the paper:
                 network forward/backward, loss, Adam, cell features, owner-
                 selected correction, optional bf16 operand rounding.
