@@ -105,6 +105,17 @@ typedef struct {
                               cell, z-slabs in registers; tiles <= 64 cells) */
   int cell_threads;        /* threads per CTA of the line-parallel fp32 operator:
                               0 = default (256), 128, 256, 384 or 512 */
+  int local_smoothing;     /* 1: geometric local smoothing instead of global
+                              coarsening (Sec. 2.1, the paper's comparison
+                              variant): levels 0..L are the refinement levels
+                              (every cell of level l), smoothing on the
+                              interior DoFs with the refinement-edge terms of
+                              Algorithm 2, copy to/from every active level
+                              (Algorithm 1); the handle's last level is then
+                              the active mesh (CG operator, right-hand side),
+                              not a multigrid level.  Requires
+                              p_coarsening = 0; not combinable with the learned
+                              smoother, a coefficient or the batch. */
 } gcmg_config;
 
 int gcmg_config_default(gcmg_config* cfg);
@@ -135,6 +146,12 @@ int gcmg_get_level_info(const gcmg_handle* h, int level, gcmg_level_info* info);
 /* support point (x, y, z) of every free DoF of a level into a host array of
  * 3 * n_free doubles (synchronous) */
 int gcmg_level_dof_coords(const gcmg_handle* h, int level, double* xyz);
+/* local smoothing: the DoFs of a refinement level on its refinement edges
+ * (Sec. 2.1: support points on the boundary of the region the level's cells
+ * cover, inside the domain; the smoother keeps them fixed).  *n receives
+ * their number (0 for global coarsening); if idx is not NULL it receives
+ * the increasing DoF indices (host array of *n entries, synchronous). */
+int gcmg_level_edge_dofs(const gcmg_handle* h, int level, int64_t* n, int32_t* idx);
 
 /*
  * dst = A_level src, the matrix-free operator of Eq. 2 (Laplace, constraints

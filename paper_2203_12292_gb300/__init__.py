@@ -43,7 +43,8 @@ class RefineStep(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("degree", _c_int), ("p_coarsening", _c_int), ("mg_fp32", _c_int), ("cheb_degree", _c_int),
                 ("smoothing_range", _c_double), ("eig_steps", _c_int), ("eig_safety", _c_double),
-                ("tile_cells", _c_int), ("cell_kernel", _c_int), ("cell_threads", _c_int)]
+                ("tile_cells", _c_int), ("cell_kernel", _c_int), ("cell_threads", _c_int),
+                ("local_smoothing", _c_int)]
 
 
 class LevelInfo(ctypes.Structure):
@@ -76,6 +77,7 @@ _SIGS = {
     "gcmg_num_levels": (_c_int, [_c_void_p, ctypes.POINTER(_c_int)]),
     "gcmg_get_level_info": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(LevelInfo)]),
     "gcmg_level_dof_coords": (_c_int, [_c_void_p, _c_int, _c_void_p]),
+    "gcmg_level_edge_dofs": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p]),
     "gcmg_vmult": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
     "gcmg_vmult_host": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
     "gcmg_dot": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int64, _c_void_p]),
@@ -233,13 +235,14 @@ def _is64(t) -> int:
 
 def make_config(degree: int, p_coarsening: bool = False, mg_fp32: bool = True, tile_cells: int = 0,
                 cheb_degree: int = 3, smoothing_range: float = 20.0, eig_steps: int = 12, eig_safety: float = 1.2,
-                cell_kernel: int = 0, cell_threads: int = 0) -> Config:
+                cell_kernel: int = 0, cell_threads: int = 0, local_smoothing: bool = False) -> Config:
     cfg = Config()
     _check(lib().gcmg_config_default(ctypes.byref(cfg)))
     cfg.degree, cfg.p_coarsening, cfg.mg_fp32 = degree, int(p_coarsening), int(mg_fp32)
     cfg.tile_cells, cfg.cheb_degree, cfg.smoothing_range = tile_cells, cheb_degree, smoothing_range
     cfg.eig_steps, cfg.eig_safety, cfg.cell_kernel = eig_steps, eig_safety, cell_kernel
     cfg.cell_threads = cell_threads
+    cfg.local_smoothing = int(local_smoothing)
     return cfg
 
 
@@ -250,7 +253,7 @@ class Multigrid:
     def __init__(self, mesh: Mesh, degree: int, p_coarsening: bool = False, mg_fp32: bool = True,
                  tile_cells: int = 0, cheb_degree: int = 3, smoothing_range: float = 20.0,
                  eig_steps: int = 12, eig_safety: float = 1.2, cell_kernel: int = 0, cell_threads: int = 0,
-                 _handle=None, _owner=None):
+                 local_smoothing: bool = False, _handle=None, _owner=None):
         import torch
         self.mesh = mesh
         self.stream = torch.cuda.current_stream()
@@ -258,12 +261,14 @@ class Multigrid:
             self._h, self._owned, self._owner = _handle, False, _owner
         else:
             cfg = make_config(degree, p_coarsening, mg_fp32, tile_cells, cheb_degree, smoothing_range, eig_steps,
-                              eig_safety, cell_kernel, cell_threads)
+                              eig_safety, cell_kernel, cell_threads, local_smoothing)
             h = _c_void_p()
             _check(lib().gcmg_setup(mesh._p, ctypes.byref(cfg), _c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
             self._h, self._owned = h, True
         self.num_levels = self._num_levels()
         self.info = [self.level_info(l) for l in range(self.num_levels)]
+        # local smoothing: levels 0 .. num_levels - 2 are the refinement levels, the last one the active mesh
+        self.local_smoothing = bool(local_smoothing) and _handle is None
 
     def __del__(self):
         if getattr(self, "_h", None) and getattr(self, "_owned", False) and _lib is not None:
@@ -286,6 +291,15 @@ class Multigrid:
     @property
     def finest(self) -> int:
         return self.num_levels - 1
+
+    def edge_dofs(self, level: int) -> np.ndarray:
+        """local smoothing: indices of the refinement-edge DoFs of a level"""
+        n = _c_int64()
+        _check(lib().gcmg_level_edge_dofs(self._h, level, ctypes.byref(n), None))
+        out = np.empty(n.value, dtype=np.int32)
+        if n.value:
+            _check(lib().gcmg_level_edge_dofs(self._h, level, ctypes.byref(n), out.ctypes.data_as(_c_void_p)))
+        return out
 
     def dof_coords(self, level: int) -> np.ndarray:
         xyz = np.empty((self.n_free(level), 3), dtype=np.float64)

@@ -361,7 +361,9 @@ void vcycle_level(Handle& H, int l) {
   prof_end(H, r);
   LevelDev& C = *H.lev[l - 1];
   r = prof_begin(H, l, GCMG_STAGE_RESTRICT);
-  launch_zero(!C.fp32, C.b.p, C.n(), H.stream);
+  // global coarsening: b^(l-1) = R r; local smoothing: b^(l-1) += R (r_S, r_E) on top of the
+  // values Algorithm 1 copied to level l-1 (r_E = -A_ES x_S: b_E is zero on level l)
+  if (!H.ls) launch_zero(!C.fp32, C.b.p, C.n(), H.stream);
   if (C.n()) launch_restrict_add(H.tr[l]->tl, f64, L.t.p, C.b.p, H.stream);  // restriction
   prof_end(H, r);
   vcycle_level(H, l - 1);
@@ -412,20 +414,53 @@ void capture(Handle& H, GraphRec& g, F&& body) {
   ck(e, "graph instantiate");
 }
 
+// local smoothing, Algorithm 1: the fp64 active vector A.w64a to every level
+// (each active DoF to the coarsest level among its active cells, edge entries
+// zero), the V-cycle from the finest refinement level, the levels' solutions
+// back to A.w64b
+void vcycle_ls_body(Handle& H) {
+  LevelDev& A = *H.lev.back();
+  for (int l = 0; l <= H.top_mg; ++l) {
+    LevelDev& L = *H.lev[l];
+    launch_zero(!L.fp32, L.b.p, L.n(), H.stream);
+    launch_copy_to_level(!L.fp32, A.w64a.as<double>(), L.cp_g.as<int32_t>(), L.cp_idx.as<int32_t>(), L.n_cp, L.b.p,
+                         H.stream);
+  }
+  vcycle_level(H, H.top_mg);
+  for (int l = 0; l <= H.top_mg; ++l) {
+    LevelDev& L = *H.lev[l];
+    launch_copy_from_level(!L.fp32, L.x.p, L.cp_g.as<int32_t>(), L.cp_idx.as<int32_t>(), L.n_cp, A.w64b.as<double>(),
+                           H.stream);
+  }
+}
+
 // the V-cycle on the level vectors (b -> x of the finest level)
 void vcycle_core(Handle& H) {
-  const int top = (int)H.lev.size() - 1;
+  const int top = H.top_mg;
+  auto body = [&] {
+    if (H.ls)
+      vcycle_ls_body(H);
+    else
+      vcycle_level(H, top);
+  };
   if (!H.use_graphs) {
-    vcycle_level(H, top);
+    body();
     return;
   }
-  if (!H.g_core.exec) capture(H, H.g_core, [&] { vcycle_level(H, top); });
+  if (!H.g_core.exec) capture(H, H.g_core, body);
   ck(cudaGraphLaunch(H.g_core.exec, H.stream), "graph launch");
   note_launches((int)H.g_core.kernels);
 }
 
 void vcycle(Handle& H, const double* b, double* x) {
   const int top = (int)H.lev.size() - 1;
+  if (H.ls) {
+    LevelDev& A = *H.lev[top];
+    ck(cudaMemcpyAsync(A.w64a.p, b, A.n() * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
+    vcycle_core(H);
+    ck(cudaMemcpyAsync(x, A.w64b.p, A.n() * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
+    return;
+  }
   LevelDev& F = *H.lev[top];
   int r = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);
   if (F.fp32)
@@ -452,6 +487,9 @@ void check_config(const gcmg_config* cfg) {
   if (cfg->cell_threads != 0 && cfg->cell_threads != 128 && cfg->cell_threads != 256 && cfg->cell_threads != 384 &&
       cfg->cell_threads != 512)
     throw Error(GCMG_ERR_ARG, "cell_threads must be 0, 128, 256, 384 or 512");
+  if (cfg->local_smoothing != 0 && cfg->local_smoothing != 1) throw Error(GCMG_ERR_ARG, "local_smoothing must be 0 or 1");
+  if (cfg->local_smoothing && cfg->p_coarsening)
+    throw Error(GCMG_ERR_ARG, "local smoothing uses the refinement levels (no polynomial coarsening)");
 }
 
 // the per-degree constant tables of every translation unit, once per device
@@ -484,12 +522,14 @@ void setup_numerics(Handle& H) {
     if (L.n() == 0) continue;
     launch_diag(L.cl, H.diag_tab[k].as<double>(), L.diag64.as<double>(), H.stream);
     launch_invert(L.diag64.as<double>(), L.dinv64.as<double>(), L.dinv32.as<float>(), L.n(), H.stream);
+    // local smoothing: the smoother sees A_SS only, edge values stay as they are
+    if (L.n_edge) launch_zero_at(L.edge_idx.as<int32_t>(), L.n_edge, L.dinv64.as<double>(), L.dinv32.as<float>(), H.stream);
   }
   ck(cudaGetLastError(), "diagonal");
   ck(cudaStreamSynchronize(H.stream), "diagonal");
   setup_coarse(H);
   ck(cudaGetLastError(), "coarse matrix");
-  for (int l = 1; l < nl; ++l) {
+  for (int l = 1; l <= H.top_mg; ++l) {
     H.lev[l]->lam = H.cfg.eig_safety * estimate_lambda(H, l);
     ck(cudaGetLastError(), "eigenvalue estimate");
   }
@@ -497,8 +537,18 @@ void setup_numerics(Handle& H) {
   H.g_a.reset();
 }
 
-void setup_handle(Handle& H, const std::vector<Octree>& meshes, int lmax, const gcmg_config& cfg) {
+void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, const gcmg_config& cfg) {
   H.cfg = cfg;
+  H.ls = cfg.local_smoothing != 0;
+  // local smoothing: the refinement levels 0..L of the finest mesh, then the active mesh itself
+  std::vector<Octree> ls_meshes;
+  if (H.ls) {
+    const Octree& fine = gc_meshes.back();
+    const int L = fine.max_level();
+    for (int l = 0; l <= L; ++l) ls_meshes.push_back(refinement_level(fine, l));
+    ls_meshes.push_back(fine);
+  }
+  const std::vector<Octree>& meshes = H.ls ? ls_meshes : gc_meshes;
   // level list: (mesh index, degree), coarsest first
   std::vector<std::pair<int, int>> spec;
   const int nm = (int)meshes.size();
@@ -573,15 +623,16 @@ void setup_handle(Handle& H, const std::vector<Octree>& meshes, int lmax, const 
     L->dinv32.alloc(n * sizeof(float));
     H.lev.push_back(std::move(L));
   }
+  H.top_mg = H.ls ? nl - 2 : nl - 1;
   H.tr.resize(nl);
-  for (int l = 1; l < nl; ++l) {
+  for (int l = 1; l <= H.top_mg; ++l) {
     auto T = std::make_unique<TransferDev>();
     LevelHost& fh = H.lev[l]->host;
     LevelHost& ch = H.lev[l - 1]->host;
     if (spec[l].first == spec[l - 1].first)
       build_transfer_p(fh, ch, T->host);
     else
-      build_transfer_h(fh, ch, T->host);
+      build_transfer_h(fh, ch, T->host, H.ls);
     T->fine_of.upload(T->host.fine_of, H.stream);
     T->refined.upload(T->host.refined, H.stream);
     TransferLaunch& t = T->tl;
@@ -597,6 +648,29 @@ void setup_handle(Handle& H, const std::vector<Octree>& meshes, int lmax, const 
     t.mask_c = H.lev[l - 1]->mask.as<uint16_t>();
     t.coarse = H.lev[l - 1]->cl;
     H.tr[l] = std::move(T);
+  }
+  if (H.ls) {
+    // refinement edges of every level, Algorithm 1's copy pairs
+    std::vector<const LevelHost*> hosts;
+    for (int l = 0; l <= H.top_mg; ++l) {
+      LevelDev& L = *H.lev[l];
+      const std::vector<int32_t> e = refinement_edge_dofs(L.host, meshes[l]);
+      if (l == 0 && !e.empty()) throw Error(GCMG_ERR_INTERNAL, "level 0 does not cover the domain");
+      L.n_edge = (int64_t)e.size();
+      if (L.n_edge) L.edge_idx.upload(e, H.stream);
+      hosts.push_back(&L.host);
+    }
+    std::vector<std::vector<int32_t>> cg, ci;
+    local_copy_map(H.lev.back()->host, hosts, cg, ci);
+    for (int l = 0; l <= H.top_mg; ++l) {
+      LevelDev& L = *H.lev[l];
+      L.n_cp = (int64_t)cg[l].size();
+      if (L.n_cp) {
+        L.cp_g.upload(cg[l], H.stream);
+        L.cp_idx.upload(ci[l], H.stream);
+      }
+    }
+    ck(cudaStreamSynchronize(H.stream), "upload");  // the host vectors are freed on return
   }
   H.scratch.alloc(DOT_BLOCKS * sizeof(double));
   H.scal.alloc(16 * sizeof(double));
@@ -702,6 +776,7 @@ int gcmg_config_default(gcmg_config* cfg) {
     cfg->tile_cells = 0;
     cfg->cell_kernel = 0;
     cfg->cell_threads = 0;
+    cfg->local_smoothing = 0;
   });
 }
 
@@ -755,6 +830,17 @@ int gcmg_level_dof_coords(const gcmg_handle* h, int level, double* xyz) {
     check_level(h->h, level);
     const auto& v = h->h.lev[level]->host.dof_xyz_cache;
     std::memcpy(xyz, v.data(), v.size() * sizeof(double));
+  });
+}
+
+int gcmg_level_edge_dofs(const gcmg_handle* h, int level, int64_t* n, int32_t* idx) {
+  return guarded([&] {
+    if (!h || !n) throw Error(GCMG_ERR_ARG, "null argument");
+    check_level(h->h, level);
+    const LevelDev& L = *h->h.lev[level];
+    *n = L.n_edge;
+    if (idx && L.n_edge)
+      ck(cudaMemcpy(idx, L.edge_idx.p, L.n_edge * sizeof(int32_t), cudaMemcpyDeviceToHost), "copy");
   });
 }
 
@@ -857,6 +943,7 @@ int gcmg_vcycle_cgc(gcmg_handle* h, const double* b, double* x) {
   return guarded([&] {
     if (!h) throw Error(GCMG_ERR_ARG, "null handle");
     Handle& H = h->h;
+    if (H.ls) throw Error(GCMG_ERR_ARG, "not available with local smoothing");
     const int top = (int)H.lev.size() - 1;
     LevelDev& F = *H.lev[top];
     if (F.n() == 0) return;
@@ -976,6 +1063,7 @@ int gcmg_prolongate_add(gcmg_handle* h, int fine_level, int fp64, const void* co
     if (!h) throw Error(GCMG_ERR_ARG, "null handle");
     if (fine_level < 1) throw Error(GCMG_ERR_ARG, "fine_level must be >= 1");
     check_level(h->h, fine_level);
+    if (!h->h.tr[fine_level]) throw Error(GCMG_ERR_ARG, "no transfer into this level (the active mesh of local smoothing)");
     if (h->h.lev[fine_level - 1]->n() == 0 || h->h.lev[fine_level]->n() == 0) return;
     if (!coarse || !fine) throw Error(GCMG_ERR_ARG, "bad vectors");
     if (h->h.lev[fine_level - 1]->n())
@@ -989,6 +1077,7 @@ int gcmg_restrict_add(gcmg_handle* h, int fine_level, int fp64, const void* fine
     if (!h) throw Error(GCMG_ERR_ARG, "null handle");
     if (fine_level < 1) throw Error(GCMG_ERR_ARG, "fine_level must be >= 1");
     check_level(h->h, fine_level);
+    if (!h->h.tr[fine_level]) throw Error(GCMG_ERR_ARG, "no transfer into this level (the active mesh of local smoothing)");
     if (h->h.lev[fine_level - 1]->n() == 0 || h->h.lev[fine_level]->n() == 0) return;
     if (!coarse || !fine) throw Error(GCMG_ERR_ARG, "bad vectors");
     if (h->h.lev[fine_level - 1]->n())
@@ -1203,6 +1292,7 @@ int gcmg_set_smoother(gcmg_handle* h, int level, int kind, const gcmg_mlp* net) 
     check_level(h->h, level);
     if (level < 1) throw Error(GCMG_ERR_ARG, "level 0 is solved exactly");
     if (kind < GCMG_SMOOTHER_CHEBYSHEV || kind > GCMG_SMOOTHER_MLP_REPLACE) throw Error(GCMG_ERR_ARG, "unknown smoother");
+    if (h->h.ls) throw Error(GCMG_ERR_ARG, "the learned smoother is not available with local smoothing");
     Handle& H = h->h;
     LevelDev& L = *H.lev[level];
     if (kind != GCMG_SMOOTHER_CHEBYSHEV) {
@@ -1228,6 +1318,7 @@ int gcmg_set_coefficient(gcmg_handle* h, int values_per_cell, const double* nu) 
     if (values_per_cell != 1 && values_per_cell != n3) throw Error(GCMG_ERR_ARG, "values_per_cell must be 1 or (k+1)^3");
     if (ncf > 0 && !nu) throw Error(GCMG_ERR_ARG, "null coefficient");
     if (any_learned(H)) throw Error(GCMG_ERR_ARG, "the learned smoother assumes a unit coefficient");
+    if (H.ls) throw Error(GCMG_ERR_ARG, "a coefficient is not available with local smoothing");
     // validate the input before touching the level data
     {
       const int64_t n = ncf * values_per_cell;

@@ -261,6 +261,7 @@ int gcmg_batch_create(int n, const gcmg_mesh* const* meshes, const gcmg_config* 
     for (int i = 0; i < n; ++i) {
       if (!meshes[i]) throw Error(GCMG_ERR_ARG, "null mesh");
       check_config(&cfgs[i]);
+      if (cfgs[i].local_smoothing) throw Error(GCMG_ERR_ARG, "the batch runs global coarsening only");
     }
     upload_all_tables();
     int dev = 0;

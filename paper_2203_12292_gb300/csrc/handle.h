@@ -28,6 +28,9 @@ struct LevelDev {
   int smoother = GCMG_SMOOTHER_CHEBYSHEV;
   DevBuf mlp_image, dfeat;  // packed bf16 weights of the fused kernel
   DevBuf coef;              // per cell coefficient nu_e (allocated once one is set)
+  // local smoothing: refinement-edge DoFs; Algorithm 1's copy pairs (active DoF, level DoF)
+  DevBuf edge_idx, cp_g, cp_idx;
+  int64_t n_edge = 0, n_cp = 0;
   int64_t n() const { return host.n_free; }
 };
 
@@ -84,6 +87,8 @@ struct GraphRec {
 struct Handle {
   cudaStream_t stream = nullptr;
   bool stop_after_cgc = false;  // finest level: return after the prolongation
+  bool ls = false;              // local smoothing: lev[0..top_mg] refinement levels, lev.back() the active mesh
+  int top_mg = 0;               // finest multigrid level (lev.size() - 1 for global coarsening)
   cudaStream_t cap_stream = nullptr;
   bool use_graphs = true;
   GraphRec* capturing = nullptr;

@@ -134,10 +134,27 @@ void validate_level(const LevelHost& L);
 // transfer between a fine level and the next coarser one
 struct TransferHost {
   int kind = 0;                      // 0 = h (geometric), 1 = p (polynomial)
-  std::vector<int32_t> fine_of;      // per coarse cell: fine cell (identity) or first child
+  std::vector<int32_t> fine_of;      // per coarse cell: fine cell (identity) or first child; -1: none
   std::vector<uint8_t> refined;      // per coarse cell: 1 if refined (8 children)
 };
-void build_transfer_h(const LevelHost& fine, const LevelHost& coarse, TransferHost& T);
+// allow_missing: coarse cells without a counterpart on the fine level take no
+// part (the refinement levels of local smoothing)
+void build_transfer_h(const LevelHost& fine, const LevelHost& coarse, TransferHost& T, bool allow_missing = false);
 void build_transfer_p(const LevelHost& fine, const LevelHost& coarse, TransferHost& T);
+
+// ---------------------------------------------------------------------------
+// local smoothing (Sec. 2.1): refinement levels, refinement edges, the copy of
+// Algorithm 1
+// ---------------------------------------------------------------------------
+// every cell of refinement level l of `fine` (active or refined) as a leaf
+Octree refinement_level(const Octree& fine, int l);
+// DoFs of a refinement level on its refinement edges: support points on the
+// boundary of the region its cells cover, inside the domain (increasing)
+std::vector<int32_t> refinement_edge_dofs(const LevelHost& L, const Octree& level_mesh);
+// Algorithm 1: every free DoF g of the active level goes to the coarsest
+// refinement level among its active cells; per level l the pairs
+// (g[l][i], idx[l][i]) of active DoF and level DoF
+void local_copy_map(const LevelHost& active, const std::vector<const LevelHost*>& levels,
+                    std::vector<std::vector<int32_t>>& g, std::vector<std::vector<int32_t>>& idx);
 
 }  // namespace gcmg

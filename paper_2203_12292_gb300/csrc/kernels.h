@@ -94,6 +94,14 @@ void launch_restrict_add(const TransferLaunch& T, bool fp64, const void* fine, v
 void upload_tables();
 void launch_cast(bool to64, const void* src, void* dst, int64_t n, cudaStream_t s);
 void launch_zero(bool fp64, void* x, int64_t n, cudaStream_t s);
+// local smoothing, Algorithm 1: dst[idx[i]] = src[g[i]] (to a level, in its
+// precision) and dst[g[i]] = src[idx[i]] (back to the fp64 active vector)
+void launch_copy_to_level(bool fp64, const double* src, const int32_t* g, const int32_t* idx, int64_t n, void* dst,
+                          cudaStream_t s);
+void launch_copy_from_level(bool fp64, const void* src, const int32_t* g, const int32_t* idx, int64_t n, double* dst,
+                            cudaStream_t s);
+// a[idx[i]] = b[idx[i]] = 0 (Jacobi inverse on refinement-edge DoFs)
+void launch_zero_at(const int32_t* idx, int64_t n, double* a, float* b, cudaStream_t s);
 void launch_invert(const double* d, double* inv64, float* inv32, int64_t n, cudaStream_t s);
 void launch_cheb_init(bool fp64, void* x, void* d, const void* b, const void* dinv, double c2, int64_t n, cudaStream_t s);
 void launch_cheb_step(bool fp64, void* x, void* d, const void* b, const void* Ax, const void* dinv, double c1,

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(BLOCK) prolong_h(TArgs<T> A) {
   // asynchronous copies all in flight at once
   for (int t = threadIdx.x; t < nc * 8 * NSLOT; t += blockDim.x) {
     const int jq = t / NSLOT, slot = t - jq * NSLOT, j = jq >> 3, q = jq & 7;
-    const bool use = sm_ref[j] || q == 0;
+    const bool use = sm_fine[j] >= 0 && (sm_ref[j] || q == 0);  // fine_of < 0: no fine cells
     const int f = sm_fine[j] + q;
     if (use)
       cp_async(sm_gs + t, A.gstart_f + (size_t)f * NSLOT + slot);
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
     // refined coarse cell are consecutive fine cells)
     for (int t = threadIdx.x; t < np * 8 * NSLOT; t += blockDim.x) {
       const int jq = t / NSLOT, slot = t - jq * NSLOT, j = jq >> 3, q = jq & 7;
-      const bool use = sm_ref[j] || q == 0;
+      const bool use = sm_fine[j] >= 0 && (sm_ref[j] || q == 0);  // fine_of < 0: no fine cells
       const int f = sm_fine[j] + q;
       if (use)
         cp_async(sm_gs + t, A.gstart_f + (size_t)f * NSLOT + slot);

@@ -33,6 +33,30 @@ __global__ void cast_kernel(const A* src, B* dst, int64_t n) {
 }
 
 template <typename T>
+__global__ void copy_to_level_kernel(const double* __restrict__ src, const int32_t* __restrict__ g,
+                                     const int32_t* __restrict__ idx, int64_t n, T* __restrict__ dst) {
+  pdl_begin();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[idx[i]] = (T)src[g[i]];
+}
+
+template <typename T>
+__global__ void copy_from_level_kernel(const T* __restrict__ src, const int32_t* __restrict__ g,
+                                       const int32_t* __restrict__ idx, int64_t n, double* __restrict__ dst) {
+  pdl_begin();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[g[i]] = (double)src[idx[i]];
+}
+
+__global__ void zero_at_kernel(const int32_t* __restrict__ idx, int64_t n, double* a, float* b) {
+  pdl_begin();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    a[idx[i]] = 0.0;
+    b[idx[i]] = 0.f;
+  }
+}
+
+template <typename T>
 __global__ void zero_kernel(T* x, int64_t n) {
   pdl_begin();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -287,6 +311,32 @@ void launch_cast(bool to64, const void* src, void* dst, int64_t n, cudaStream_t 
     { launch_pdl(cast_kernel<float, double>, grid_for(n), BLOCK, 0, s, static_cast<const float*>(src), static_cast<double*>(dst), n); note_launches(1); }
   else
     { launch_pdl(cast_kernel<double, float>, grid_for(n), BLOCK, 0, s, static_cast<const double*>(src), static_cast<float*>(dst), n); note_launches(1); }
+}
+
+void launch_copy_to_level(bool fp64, const double* src, const int32_t* g, const int32_t* idx, int64_t n, void* dst,
+                          cudaStream_t s) {
+  if (n <= 0) return;
+  if (fp64)
+    launch_pdl(copy_to_level_kernel<double>, grid_for(n), BLOCK, 0, s, src, g, idx, n, static_cast<double*>(dst));
+  else
+    launch_pdl(copy_to_level_kernel<float>, grid_for(n), BLOCK, 0, s, src, g, idx, n, static_cast<float*>(dst));
+  note_launches(1);
+}
+
+void launch_copy_from_level(bool fp64, const void* src, const int32_t* g, const int32_t* idx, int64_t n, double* dst,
+                            cudaStream_t s) {
+  if (n <= 0) return;
+  if (fp64)
+    launch_pdl(copy_from_level_kernel<double>, grid_for(n), BLOCK, 0, s, static_cast<const double*>(src), g, idx, n, dst);
+  else
+    launch_pdl(copy_from_level_kernel<float>, grid_for(n), BLOCK, 0, s, static_cast<const float*>(src), g, idx, n, dst);
+  note_launches(1);
+}
+
+void launch_zero_at(const int32_t* idx, int64_t n, double* a, float* b, cudaStream_t s) {
+  if (n <= 0) return;
+  launch_pdl(zero_at_kernel, grid_for(n), BLOCK, 0, s, idx, n, a, b);
+  note_launches(1);
 }
 
 void launch_zero(bool fp64, void* x, int64_t n, cudaStream_t s) {

@@ -22,6 +22,7 @@
 //   shared-memory accumulation runs sub-colour by sub-colour, and the cells
 //   are permuted so that each sub-colour is contiguous.
 #include <algorithm>
+#include <cmath>
 #include <stdexcept>
 
 #include "internal.h"
@@ -439,7 +440,7 @@ void validate_level(const LevelHost& L) {
     if (!owned[g]) fail("DoF without a transfer owner");
 }
 
-void build_transfer_h(const LevelHost& fine, const LevelHost& coarse, TransferHost& T) {
+void build_transfer_h(const LevelHost& fine, const LevelHost& coarse, TransferHost& T, bool allow_missing) {
   T.kind = 0;
   std::unordered_map<uint64_t, int32_t> fidx;
   fidx.reserve(fine.cells.size() * 2);
@@ -458,7 +459,10 @@ void build_transfer_h(const LevelHost& fine, const LevelHost& coarse, TransferHo
       continue;
     }
     auto ch = fidx.find(cell_key(c.l + 1, 2 * c.i, 2 * c.j, 2 * c.k));
-    if (ch == fidx.end()) throw std::runtime_error("levels are not nested");
+    if (ch == fidx.end()) {
+      if (allow_missing) continue;  // fine_of stays -1
+      throw std::runtime_error("levels are not nested");
+    }
     // the eight children are consecutive in Morton order
     for (int q = 0; q < 8; ++q) {
       const Cell& f = fine.cells[ch->second + q];
@@ -477,6 +481,102 @@ void build_transfer_p(const LevelHost& fine, const LevelHost& coarse, TransferHo
   T.fine_of.resize(coarse.cells.size());
   T.refined.assign(coarse.cells.size(), 0);
   for (size_t i = 0; i < coarse.cells.size(); ++i) T.fine_of[i] = (int32_t)i;
+}
+
+// ---------------------------------------------------------------------------
+// local smoothing
+// ---------------------------------------------------------------------------
+Octree refinement_level(const Octree& fine, int l) {
+  Octree m;
+  m.lo = fine.lo;
+  m.hi = fine.hi;
+  for (const auto* set : {&fine.leaves, &fine.internal})
+    for (uint64_t key : *set)
+      if ((int)(key >> 57) == l) m.leaves.insert(key);
+  return m;
+}
+
+std::vector<int32_t> refinement_edge_dofs(const LevelHost& L, const Octree& level_mesh) {
+  std::vector<int32_t> out;
+  if (L.cells.empty()) return out;
+  const int l = L.cells[0].l;
+  const int n = 1 << l;
+  const double h = (L.hi - L.lo) / n;
+  std::vector<double> xyz;
+  L.dof_coordinates(xyz);
+  for (int64_t g = 0; g < L.n_free; ++g) {
+    // the grid cells of level l whose closure holds the point: one or two per axis
+    int lo_idx[3], hi_idx[3];
+    for (int d = 0; d < 3; ++d) {
+      const double t = (xyz[3 * g + d] - L.lo) / h;
+      const double r = std::nearbyint(t);
+      if (std::fabs(t - r) < 1e-9) {
+        lo_idx[d] = (int)r - 1;
+        hi_idx[d] = (int)r;
+      } else {
+        lo_idx[d] = hi_idx[d] = (int)std::floor(t);
+      }
+    }
+    bool edge = false;
+    for (int i = lo_idx[0]; i <= hi_idx[0] && !edge; ++i)
+      for (int j = lo_idx[1]; j <= hi_idx[1] && !edge; ++j)
+        for (int k = lo_idx[2]; k <= hi_idx[2] && !edge; ++k)
+          if (i >= 0 && i < n && j >= 0 && j < n && k >= 0 && k < n &&
+              !level_mesh.leaves.count(cell_key(l, i, j, k)))
+            edge = true;
+    if (edge) out.push_back((int32_t)g);
+  }
+  return out;
+}
+
+void local_copy_map(const LevelHost& active, const std::vector<const LevelHost*>& levels,
+                    std::vector<std::vector<int32_t>>& g, std::vector<std::vector<int32_t>>& idx) {
+  const int nl = (int)levels.size();
+  const int k = active.k;
+  std::vector<std::unordered_map<uint64_t, int32_t>> cidx(nl);
+  for (int l = 0; l < nl; ++l)
+    for (size_t c = 0; c < levels[l]->cells.size(); ++c) {
+      const Cell& cc = levels[l]->cells[c];
+      cidx[l].emplace(cell_key(cc.l, cc.i, cc.j, cc.k), (int32_t)c);
+    }
+  // active cells by increasing level: the first level to reach a DoF keeps it
+  std::vector<int32_t> order(active.cells.size());
+  for (size_t c = 0; c < order.size(); ++c) order[c] = (int32_t)c;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return active.cells[a].l < active.cells[b].l; });
+  std::vector<int32_t> lvl(active.n_free, -1), at(active.n_free, -1);
+  for (int32_t c : order) {
+    const Cell& cc = active.cells[c];
+    if (cc.l >= nl) throw std::runtime_error("active cell finer than the refinement levels");
+    auto it = cidx[cc.l].find(cell_key(cc.l, cc.i, cc.j, cc.k));
+    if (it == cidx[cc.l].end()) throw std::runtime_error("active cell missing on its refinement level");
+    const LevelHost& Lv = *levels[cc.l];
+    const int lc = it->second;
+    const uint16_t m = active.mask[c];
+    for (int s = 0; s < NSLOT; ++s) {
+      const int cl[3] = {s % 3, (s / 3) % 3, s / 9};
+      if (slot_hanging(m, cl)) continue;  // constrained values: no active DoF here
+      const int32_t ga = active.gstart[(size_t)c * NSLOT + s];
+      const int32_t gl = Lv.gstart[(size_t)lc * NSLOT + s];
+      if (ga < 0) continue;
+      if (gl < 0) throw std::runtime_error("refinement level lacks a DoF of an active cell");
+      int nd = 0;
+      for (int d = 0; d < 3; ++d) nd += cl[d] == 1;
+      const int cnt = ipow(k - 1, nd);
+      for (int q = 0; q < cnt; ++q)
+        if (lvl[ga + q] < 0) {
+          lvl[ga + q] = cc.l;
+          at[ga + q] = gl + q;
+        }
+    }
+  }
+  g.assign(nl, {});
+  idx.assign(nl, {});
+  for (int64_t d = 0; d < active.n_free; ++d) {
+    if (lvl[d] < 0) throw std::runtime_error("an active DoF without a refinement level");
+    g[lvl[d]].push_back((int32_t)d);
+    idx[lvl[d]].push_back(at[d]);
+  }
 }
 
 }  // namespace gcmg
