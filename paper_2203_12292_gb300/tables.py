@@ -1,6 +1,6 @@
 """Time to solution of the paper's own test cases on one GPU.
 
-    python -m paper_2203_12292_gb300.tables [--case octant|gaussian|ls|all] [--reps 3]
+    python -m paper_2203_12292_gb300.tables [--case octant|gaussian|ls|shell|shell_ls|all] [--reps 3]
 
 octant: -Delta u = 1, homogeneous Dirichlet data, the octant mesh of Sec. 4
 ("Examples") on [-1,1]^3, L = 3..8 for p = 1 and L = 3..7 for p = 4 (the
@@ -10,6 +10,8 @@ gaussian: the same meshes with the Gaussian manufactured solution of
 Table A.1 (inhomogeneous Dirichlet data).
 ls: the octant case with geometric local smoothing instead of global
 coarsening (Sec. 2.1; the LS columns of Table 4).
+shell, shell_ls: the shell mesh of Sec. 4 (three radius bands), global
+coarsening and local smoothing (Table 5), L = 5..9 for p = 1, 5..8 for p = 4.
 
 Prints one JSON line per case: iterations, DoFs, and the time of one solve
 (CUDA events on the solve's stream, the best of ``reps`` solves after one
@@ -33,8 +35,8 @@ GAUSSIAN = [0.1, -0.5, -0.5, -0.5]  # alpha, x0 (Table A.1)
 
 def run_case(g, case: str, L: int, k: int, reps: int) -> dict:
     import torch
-    mesh = g.Mesh.from_recipe(synth.octant(L))
-    mg = g.Multigrid(mesh, k, mg_fp32=True, local_smoothing=(case == "ls"))
+    mesh = g.Mesh.from_recipe(synth.shell(L) if case.startswith("shell") else synth.octant(L))
+    mg = g.Multigrid(mesh, k, mg_fp32=True, local_smoothing=case.endswith("ls"))
     b = mg.rhs_dirichlet(g.FUNC_GAUSSIAN, GAUSSIAN) if case == "gaussian" else mg.rhs()
     x = torch.zeros_like(b)
     st = mg.cg_solve(b, x, 1e-4, maxit=50)  # warm-up: graphs captured here
@@ -54,15 +56,16 @@ def run_case(g, case: str, L: int, k: int, reps: int) -> dict:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="all", choices=["octant", "gaussian", "ls", "all"])
+    ap.add_argument("--case", default="all", choices=["octant", "gaussian", "ls", "shell", "shell_ls", "all"])
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
     from . import build as b
     b.build()
     import paper_2203_12292_gb300 as g
-    cases = ["octant", "gaussian", "ls"] if a.case == "all" else [a.case]
+    cases = ["octant", "gaussian", "ls", "shell", "shell_ls"] if a.case == "all" else [a.case]
     for case in cases:
-        for k, levels in ((1, range(3, 9)), (4, range(3, 8))):
+        ranges = ((1, range(5, 10)), (4, range(5, 9))) if case.startswith("shell") else ((1, range(3, 9)), (4, range(3, 8)))
+        for k, levels in ranges:
             for L in levels:
                 print(json.dumps(run_case(g, case, L, k, a.reps)), flush=True)
 

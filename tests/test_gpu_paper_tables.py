@@ -69,3 +69,18 @@ def test_octant_level_cells_workload_figure(gcmg):
     # the Q1 solve of the L = 8 octant mesh end to end (2.1 M cells)
     st = _solve(gcmg, synth.octant(8), 1, 1e-8, True)
     assert st.status == 0 and st.iterations <= 8
+
+
+@pytest.mark.parametrize("ls", [False, True], ids=["GC", "LS"])
+@pytest.mark.parametrize("k,L", [(1, 5), (1, 6), (1, 7), (1, 8), (4, 5), (4, 6), (4, 7)])
+def test_shell_iterations_table_5(gcmg, k, L, ls):
+    """Table 5: the shell case (three radius bands), global coarsening and
+    local smoothing, fp32 V-cycle, 1e-4."""
+    row = [r for r in table("shell_t5") if int(r[0]) == L][0]
+    ref = row[(1 if ls else 2) if k == 1 else (3 if ls else 4)]
+    mg = gcmg.Multigrid(gcmg.Mesh.from_recipe(synth.shell(L)), k, local_smoothing=ls)
+    b = mg.rhs()
+    x = torch.zeros_like(b)
+    st = mg.cg_solve(b, x, 1e-4, maxit=50)
+    assert st.status == 0 and st.rel_residual <= 1e-4
+    assert ref - 1 <= st.iterations <= ref, (k, L, ls, st.iterations, ref)
