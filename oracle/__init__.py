@@ -32,6 +32,9 @@ What it computes, each part a plain definition written out in fp64:
                 refinement levels, refinement-edge DoFs, the V-cycle with
                 edge treatment and the copy to/from all active levels
                 (Sec. 2.1, Algorithms 1-2).
+* ``mapped``    non-Cartesian geometry: the cells mapped by a global
+                non-affine map, element matrices with the Jacobian at every
+                quadrature point (Sec. 3.2, Eq. 2 in its general form).
 * ``mlp``       learned per-cell smoother, an extension outside the paper:
                 network forward/backward, loss, Adam, cell features, owner-
                 selected correction, optional bf16 operand rounding.

@@ -148,11 +148,12 @@ class Level:
 
 def build_levels(fine_mesh: omesh.Mesh, k: int, p_coarsening: bool = False,
                  assembled: bool = True, lam_max: Optional[List[float]] = None,
-                 coefficient: Optional[Callable] = None) -> List[Level]:
+                 coefficient: Optional[Callable] = None, warp_eps: Optional[float] = None) -> List[Level]:
     """Global-coarsening levels (coarsest first). With p_coarsening the
     finest mesh is first coarsened in degree k -> floor(k/2) -> ... -> 1
     (Sec. 2.3), then geometrically with degree 1.  ``coefficient``: nu(x) of
-    -div(nu grad u), set on all levels as in oracle.coefficient."""
+    -div(nu grad u), set on all levels as in oracle.coefficient.  ``warp_eps``:
+    the cells mapped by oracle.mapped.warp on every level."""
     meshes = omesh.gc_hierarchy(fine_mesh)
     specs = []
     if p_coarsening:
@@ -162,9 +163,16 @@ def build_levels(fine_mesh: omesh.Mesh, k: int, p_coarsening: bool = False,
         specs = [(m, 1) for m in meshes[:-1]] + [(meshes[-1], d) for d in degs[::-1]]
     else:
         specs = [(m, k) for m in meshes]
-    spaces = [Space(m, kk) for m, kk in specs]
+    if warp_eps is None:
+        spaces = [Space(m, kk) for m, kk in specs]
+    else:
+        from .mapped import MappedSpace
+        spaces = [MappedSpace(m, kk, warp_eps) for m, kk in specs]
     if coefficient is not None:
         ocoef.set_level_coefficients(spaces, coefficient)
+        if warp_eps is not None:
+            for s in spaces:
+                s.set_coefficient(s.nu)
     levels: List[Level] = []
     for idx, s in enumerate(spaces):
         A = s.assemble() if assembled else None
