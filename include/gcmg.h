@@ -208,6 +208,24 @@ int gcmg_rhs_dirichlet(gcmg_handle* h, int kind, int n, const double* params, do
  * the handle unchanged).  Not combinable with the learned smoother.
  */
 int gcmg_set_coefficient(gcmg_handle* h, int values_per_cell, const double* nu);
+/*
+ * Non-Cartesian geometry (the general form of Eq. 2: Q_e holds the Jacobian
+ * of the cell's map at every quadrature point).  The octree lives in
+ * parameter space [lo, hi]^3; the physical domain is Phi([lo, hi]^3) with
+ *   kind GCMG_GEOM_WARP: Phi(x) = x + eps (x1 x2, 2 x2 x0, x0 x1 / 2),
+ * so every cell is a general trilinear hexahedron; kind 0 restores
+ * Cartesian cells.  All levels switch to the quadrature-point operator
+ * (values and collocation derivatives at the (k+1)^3 Gauss points, the 3x3
+ * factor w det(J) J^-1 J^-T per point, transposed sweeps), the diagonal is
+ * recomputed cell by cell, then the coarse inverse and the eigenvalue
+ * estimates (synchronous).  Right-hand sides evaluate f and the Dirichlet
+ * data at Phi(x) and weight with det(J); DoF coordinates stay in parameter
+ * space (physical point = Phi(point)).  GCMG_ERR_ARG for an unknown kind,
+ * a map with det(J_Phi) <= 0.05 somewhere in the domain, the learned
+ * smoother or a batch's problem.
+ */
+#define GCMG_GEOM_WARP 1
+int gcmg_set_geometry(gcmg_handle* h, int kind, double eps);
 /* nu_e of every cell of a level into device memory (1 where none was set) */
 int gcmg_get_coefficient(gcmg_handle* h, int level, double* nu);
 /* Gauss points of every finest cell: device array n_cells x (k+1)^3 x 3 */

@@ -25,6 +25,7 @@ STAGES = ["vmult", "presmooth", "residual", "restrict", "coarse", "prolongate", 
 
 SMOOTHER_CHEBYSHEV, SMOOTHER_MLP_AUGMENT, SMOOTHER_MLP_REPLACE = 0, 1, 2
 FUNC_GAUSSIAN, FUNC_POLYNOMIAL = 2, 3  # manufactured solutions of rhs_dirichlet
+GEOM_CARTESIAN, GEOM_WARP = 0, 1  # cell geometry of set_geometry
 
 ERRORS = {1: "GCMG_ERR_ARG", 2: "GCMG_ERR_CUDA", 3: "GCMG_ERR_OOM", 4: "GCMG_ERR_NOT_CONVERGED",
           5: "GCMG_ERR_BREAKDOWN", 6: "GCMG_ERR_INTERNAL"}
@@ -89,6 +90,7 @@ _SIGS = {
     "gcmg_rhs": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_double, _c_void_p]),
     "gcmg_rhs_dirichlet": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
     "gcmg_set_coefficient": (_c_int, [_c_void_p, _c_int, _c_void_p]),
+    "gcmg_set_geometry": (_c_int, [_c_void_p, _c_int, _c_double]),
     "gcmg_get_coefficient": (_c_int, [_c_void_p, _c_int, _c_void_p]),
     "gcmg_quadrature_points": (_c_int, [_c_void_p, _c_void_p]),
     "gcmg_get_lambda": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_double)]),
@@ -392,6 +394,11 @@ class Multigrid:
         assert nu.numel() % max(nc, 1) == 0
         per = nu.numel() // nc if nc else 1
         _check(lib().gcmg_set_coefficient(self._h, per, _ptr(nu)))
+
+    def set_geometry(self, kind: int, eps: float = 0.0) -> None:
+        """GEOM_WARP: the cells mapped by Phi(x) = x + eps (x1 x2, 2 x2 x0, x0 x1 / 2);
+        GEOM_CARTESIAN: back to Cartesian cells (see gcmg_set_geometry)."""
+        _check(lib().gcmg_set_geometry(self._h, int(kind), float(eps)))
 
     def get_coefficient(self, level: int):
         import torch

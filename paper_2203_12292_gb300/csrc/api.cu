@@ -1297,6 +1297,7 @@ int gcmg_set_smoother(gcmg_handle* h, int level, int kind, const gcmg_mlp* net) 
     LevelDev& L = *H.lev[level];
     if (kind != GCMG_SMOOTHER_CHEBYSHEV) {
       if (L.cl.coef) throw Error(GCMG_ERR_ARG, "the learned smoother assumes a unit coefficient");
+      if (L.cl.geom) throw Error(GCMG_ERR_ARG, "the learned smoother assumes Cartesian cells");
       check_q4_net(L, net);
       ensure_dfeat(H, level);
       if (!L.mlp_image.p) L.mlp_image.alloc(mlp_image_bytes());
@@ -1319,6 +1320,7 @@ int gcmg_set_coefficient(gcmg_handle* h, int values_per_cell, const double* nu) 
     if (ncf > 0 && !nu) throw Error(GCMG_ERR_ARG, "null coefficient");
     if (any_learned(H)) throw Error(GCMG_ERR_ARG, "the learned smoother assumes a unit coefficient");
     if (H.ls) throw Error(GCMG_ERR_ARG, "a coefficient is not available with local smoothing");
+    if (H.in_batch) throw Error(GCMG_ERR_ARG, "the problems of a batch keep their set-up");
     // validate the input before touching the level data
     {
       const int64_t n = ncf * values_per_cell;
@@ -1336,7 +1338,8 @@ int gcmg_set_coefficient(gcmg_handle* h, int values_per_cell, const double* nu) 
       if (!L.coef.p) L.coef.alloc(std::max<size_t>(1, L.host.cells.size()) * sizeof(double));
       L.cl.coef = L.coef.as<double>();
     }
-    for (int l = 1; l < nl; ++l) H.tr[l]->tl.coarse = H.lev[l - 1]->cl;
+    for (int l = 1; l < nl; ++l)
+      if (H.tr[l]) H.tr[l]->tl.coarse = H.lev[l - 1]->cl;
     if (values_per_cell == 1)
       ck(cudaMemcpyAsync(F.coef.p, nu, ncf * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
     else
@@ -1349,6 +1352,45 @@ int gcmg_set_coefficient(gcmg_handle* h, int values_per_cell, const double* nu) 
     ck(cudaGetLastError(), "coefficient");
     setup_numerics(H);
     ck(cudaStreamSynchronize(H.stream), "coefficient");
+  });
+}
+
+int gcmg_set_geometry(gcmg_handle* h, int kind, double eps) {
+  return guarded([&] {
+    if (!h) throw Error(GCMG_ERR_ARG, "null handle");
+    Handle& H = h->h;
+    if (kind != 0 && kind != GCMG_GEOM_WARP) throw Error(GCMG_ERR_ARG, "unknown geometry");
+    if (!std::isfinite(eps)) throw Error(GCMG_ERR_ARG, "eps must be finite");
+    if (any_learned(H)) throw Error(GCMG_ERR_ARG, "the learned smoother assumes Cartesian cells");
+    if (H.in_batch) throw Error(GCMG_ERR_ARG, "the problems of a batch keep their set-up");
+    if (kind == GCMG_GEOM_WARP) {
+      // the map must be invertible on the domain: det J_Phi > 0 on a 33^3 lattice
+      const double lo = H.lev.back()->host.lo, hi = H.lev.back()->host.hi;
+      double dmin = 1e300;
+      for (int a = 0; a <= 32; ++a)
+        for (int b = 0; b <= 32; ++b)
+          for (int c = 0; c <= 32; ++c) {
+            const double x = lo + (hi - lo) * a / 32, y = lo + (hi - lo) * b / 32, z = lo + (hi - lo) * c / 32;
+            const double det = 1.0 - eps * eps * (x * x + 0.5 * y * y + 2.0 * z * z) + 2.0 * eps * eps * eps * x * y * z;
+            dmin = std::min(dmin, det);
+          }
+      if (!(dmin > 0.05)) throw Error(GCMG_ERR_ARG, "the warp folds the domain (det J <= 0.05): reduce eps");
+    }
+    const int nl = (int)H.lev.size();
+    if (kind)
+      for (int l = 0; l < nl; ++l) {
+        const CellLaunch& c = H.lev[l]->cl;
+        if (cell_smem_bytes(c.k, true, c.tc, c.max_local, true) > 227 * 1024)
+          throw Error(GCMG_ERR_ARG, "tiles too large for the mapped operator's shared memory (use tile_cells <= 32)");
+      }
+    for (int l = 0; l < nl; ++l) {
+      H.lev[l]->cl.geom = kind;
+      H.lev[l]->cl.geps = kind ? eps : 0.0;
+    }
+    for (int l = 1; l < nl; ++l)
+      if (H.tr[l]) H.tr[l]->tl.coarse = H.lev[l - 1]->cl;
+    setup_numerics(H);
+    ck(cudaStreamSynchronize(H.stream), "geometry");
   });
 }
 

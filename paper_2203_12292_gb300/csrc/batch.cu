@@ -283,6 +283,7 @@ int gcmg_batch_create(int n, const gcmg_mesh* const* meshes, const gcmg_config* 
         for (int i; (i = next.fetch_add(1)) < n;) {
           auto h = std::make_unique<gcmg_handle>();
           h->h.stream = s;
+          h->h.in_batch = true;
           setup_handle(h->h, meshes[i]->levels, meshes[i]->lmax, cfgs[i]);
           B->probs[i] = std::move(h);
         }

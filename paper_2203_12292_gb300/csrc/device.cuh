@@ -75,6 +75,7 @@ struct DevTables {
   T lame[NMAX];             // eigenvalues in the same order
   T lam3[(KMAX + 1) * (KMAX + 1) * (KMAX + 1)];  // lame[a] + lame[b] + lame[c], a fastest
   T xi[NMAX];               // Gauss-Lobatto support points on [0,1]
+  T Dq[NMAX][NMAX];         // collocation derivative on the Gauss points: Dq[i][j] = L'_j(gq_i)
 };
 
 // every translation unit holds its own copy of the tables (no relocatable
@@ -111,6 +112,19 @@ static inline void fill_tables(DevTables<double>* td, DevTables<float>* tf) {
       d.gq[i] = b.gq[i];
       d.gw[i] = b.gw[i];
       d.xi[i] = b.xi[i];
+      // derivative of the Lagrange polynomial L_j on the k+1 Gauss points at gq_i
+      for (int j = 0; j <= k; ++j) {
+        double dsum = 0.0;
+        if (i <= k)
+          for (int c = 0; c <= k; ++c) {
+            if (c == j) continue;
+            double term = 1.0 / (b.gq[j] - b.gq[c]);
+            for (int m = 0; m <= k; ++m)
+              if (m != j && m != c) term *= (b.gq[i] - b.gq[m]) / (b.gq[j] - b.gq[m]);
+            dsum += term;
+          }
+        d.Dq[i][j] = dsum;
+      }
       for (int j = 0; j < NMAX; ++j) {
         d.B[i][j] = b.B[i][j];
         d.I[0][i][j] = b.I[0][i][j];

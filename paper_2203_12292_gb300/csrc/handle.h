@@ -89,6 +89,7 @@ struct Handle {
   bool stop_after_cgc = false;  // finest level: return after the prolongation
   bool ls = false;              // local smoothing: lev[0..top_mg] refinement levels, lev.back() the active mesh
   int top_mg = 0;               // finest multigrid level (lev.size() - 1 for global coarsening)
+  bool in_batch = false;        // owned by a batch, whose graph holds the kernels' arguments
   cudaStream_t cap_stream = nullptr;
   bool use_graphs = true;
   GraphRec* capturing = nullptr;

@@ -36,7 +36,14 @@ struct CellLaunch {
   int threads;    // threads per CTA of the line-parallel operator kernel (128, 256, 384 or 512)
   double lo, dom;
   const double* coef;  // per cell coefficient nu_e (element matrix nu_e h A_ref); null: 1
+  int geom;            // 0: Cartesian cells; GEOM_WARP: the cells mapped by the warp below
+  double geps;         // its eps
 };
+
+// non-Cartesian geometry: the octree cells (parameter space) mapped by
+// Phi(x) = x + eps (x1 x2, 2 x2 x0, x0 x1 / 2), the Jacobian evaluated at every
+// Gauss point
+constexpr int GEOM_WARP = 1;
 
 // analytic function of a right-hand side or of Dirichlet data
 enum FuncKind { FUNC_ONE = 0, FUNC_FOURIER = 1, FUNC_GAUSSIAN = 2, FUNC_POLYNOMIAL = 3 };
@@ -72,7 +79,7 @@ void launch_diag(const CellLaunch& L, const double* diag_tab, double* dst, cudaS
 void launch_diag_table(int k, double* diag_tab, cudaStream_t s);
 // second pass of every tile loop: dst[g] += halo slots of g, fixed order
 void launch_halo_add(const CellLaunch& L, bool fp64, void* dst, cudaStream_t s);
-size_t cell_smem_bytes(int k, bool fp64, int tc, int max_local);
+size_t cell_smem_bytes(int k, bool fp64, int tc, int max_local, bool mapped = false);
 
 // transfer between levels; fine_of/refined per coarse cell
 struct TransferLaunch {

@@ -59,6 +59,8 @@ struct CellArgs {
   RhsDesc fn;
   const double* diag_tab;
   const double* coef;  // per cell nu_e, null: 1
+  int geom;            // 0: Cartesian cells; GEOM_WARP: cells mapped by the warp of eps
+  double geps;
 };
 
 // scale of the element matrix of cell ci: nu_e h (h = dom 2^-level)
@@ -141,11 +143,13 @@ __device__ __forceinline__ bool node_hangs(uint16_t m, int a, int b, int c) {
 }
 
 struct SmemLayout {
-  size_t meta, h, mask, cell, cb, xs, ys, total;
+  size_t meta, h, mask, cell, cb, xs, ys, gx, gy, gr, total;
 };
 
+// mapped: three more chunk buffers (two reference-gradient components and,
+// for the diagonal, the collected entries) for the non-Cartesian operator
 template <typename T>
-__host__ __device__ inline SmemLayout smem_layout(int n3, int tc, int max_local) {
+__host__ __device__ inline SmemLayout smem_layout(int n3, int tc, int max_local, bool mapped = false) {
   SmemLayout L;
   size_t o = 0;
   L.meta = o;
@@ -163,6 +167,16 @@ __host__ __device__ inline SmemLayout smem_layout(int n3, int tc, int max_local)
   o += (size_t)max_local * sizeof(T);
   L.ys = o;
   o += (size_t)max_local * sizeof(T);
+  o = (o + 15) & ~(size_t)15;
+  L.gx = L.gy = L.gr = o;
+  if (mapped) {
+    L.gx = o;
+    o += (size_t)CHUNK * n3 * sizeof(T);
+    L.gy = o;
+    o += (size_t)CHUNK * n3 * sizeof(T);
+    L.gr = o;
+    o += (size_t)CHUNK * n3 * sizeof(T);
+  }
   L.total = (o + 15) & ~(size_t)15;
   return L;
 }
@@ -194,12 +208,164 @@ __device__ __forceinline__ void write_tile_dofs(T* dst, T* halo, const T* ys, co
   for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) h[i] = ys[ti.n_owned + i];
 }
 
+// ---------------------------------------------------------------------------
+// non-Cartesian cells (Eq. 2 with the geometry at the quadrature points)
+// ---------------------------------------------------------------------------
+// the warp Phi(x) = x + eps (x1 x2, 2 x2 x0, x0 x1 / 2) and its Jacobian
+template <typename T>
+__device__ __forceinline__ void warp_point(T eps, T& x, T& y, T& z) {
+  const T px = x + eps * y * z, py = y + T(2) * eps * z * x, pz = z + T(0.5) * eps * x * y;
+  x = px;
+  y = py;
+  z = pz;
+}
+
+// G = sw adj(J) adj(J)^T / det(J) for J = J_Phi(x, y, z): with sw = w h nu
+// this is w det(J_cell) J_cell^-1 J_cell^-T of the cell map h J_Phi; G[6] =
+// (00, 01, 02, 11, 12, 22); returns det(J_Phi)
+template <typename T>
+__device__ __forceinline__ T warp_metric(T eps, T x, T y, T z, T sw, T* G) {
+  const T j00 = 1, j01 = eps * z, j02 = eps * y;
+  const T j10 = T(2) * eps * z, j11 = 1, j12 = T(2) * eps * x;
+  const T j20 = T(0.5) * eps * y, j21 = T(0.5) * eps * x, j22 = 1;
+  const T a00 = j11 * j22 - j12 * j21, a01 = j02 * j21 - j01 * j22, a02 = j01 * j12 - j02 * j11;
+  const T a10 = j12 * j20 - j10 * j22, a11 = j00 * j22 - j02 * j20, a12 = j02 * j10 - j00 * j12;
+  const T a20 = j10 * j21 - j11 * j20, a21 = j01 * j20 - j00 * j21, a22 = j00 * j11 - j01 * j10;
+  const T det = j00 * a00 + j01 * a10 + j02 * a20;
+  const T f = sw / det;
+  G[0] = f * (a00 * a00 + a01 * a01 + a02 * a02);
+  G[1] = f * (a00 * a10 + a01 * a11 + a02 * a12);
+  G[2] = f * (a00 * a20 + a01 * a21 + a02 * a22);
+  G[3] = f * (a10 * a10 + a11 * a11 + a12 * a12);
+  G[4] = f * (a10 * a20 + a11 * a21 + a12 * a22);
+  G[5] = f * (a20 * a20 + a21 * a21 + a22 * a22);
+  return det;
+}
+
+// one 1D matrix along a line from src into dst (ADD: dst += ...)
+template <int N, int STRIDE, bool TRANS, bool ADD, typename T>
+__device__ __forceinline__ void line_apply2(const T* src, T* dst, const T (&M)[NMAX][NMAX]) {
+  T v[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) v[a] = src[a * STRIDE];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T sum = 0;
+#pragma unroll
+    for (int a = 0; a < N; ++a) sum += (TRANS ? M[a][i] : M[i][a]) * v[a];
+    dst[i * STRIDE] = ADD ? dst[i * STRIDE] + sum : sum;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void line_bases(int t, int& j, int& bx, int& by, int& bz) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  j = t / N2;
+  const int r = t - j * N2;
+  bx = j * N3 + N * r;
+  by = j * N3 + r % N + N2 * (r / N);
+  bz = j * N3 + r;
+}
+
+// the cell operator of mapped cells, in place on the chunk buffer cb (values
+// at the support points in, A_e u out): values at the Gauss points (three
+// sweeps with the values of the basis), reference gradients by collocation
+// derivatives (into gx, gy and, in place, cb), the 3x3 geometry factor of
+// every Gauss point, the transposed derivatives summed back into cb, the
+// transposed value sweeps.  sm_h[j] = h nu of cell j (negative: -A_e).
+template <int K, typename T>
+__device__ void cell_laplace_mapped(T* cb, T* gx, T* gy, const T* sm_h, const uint16_t* sm_cell,
+                                    const CellMeta* sm_meta, const int32_t* cell_ijk, int cell_begin, double lo,
+                                    double dom, T eps, int nch) {
+  constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
+  const DevTables<T>& tb = tab<T>(K);
+  const int nl = nch * N2;
+  int j, bx, by, bz;
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    line_bases<N>(t, j, bx, by, bz);
+    line_apply<N, 1, false>(cb + bx, tb.Pq);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    line_bases<N>(t, j, bx, by, bz);
+    line_apply<N, N, false>(cb + by, tb.Pq);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    line_bases<N>(t, j, bx, by, bz);
+    line_apply<N, N2, false>(cb + bz, tb.Pq);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    line_bases<N>(t, j, bx, by, bz);
+    line_apply2<N, 1, false, false>(cb + bx, gx + bx, tb.Dq);
+    line_apply2<N, N, false, false>(cb + by, gy + by, tb.Dq);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    line_bases<N>(t, j, bx, by, bz);
+    line_apply<N, N2, false>(cb + bz, tb.Dq);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nch * N3; t += blockDim.x) {
+    const int jj = t / N3, q = t - jj * N3;
+    const int qa = q % N, qb = (q / N) % N, qc = q / N2;
+    const int ci = cell_begin + sm_cell[jj];
+    const double h = ldexp(dom, -(int)sm_meta[sm_cell[jj]].level);
+    const T x = (T)(lo + h * ((double)cell_ijk[3 * ci + 0] + (double)tab<double>(K).gq[qa]));
+    const T y = (T)(lo + h * ((double)cell_ijk[3 * ci + 1] + (double)tab<double>(K).gq[qb]));
+    const T z = (T)(lo + h * ((double)cell_ijk[3 * ci + 2] + (double)tab<double>(K).gq[qc]));
+    T G[6];
+    warp_metric<T>(eps, x, y, z, tb.gw[qa] * tb.gw[qb] * tb.gw[qc] * sm_h[jj], G);
+    const T g0 = gx[t], g1 = gy[t], g2 = cb[t];
+    gx[t] = G[0] * g0 + G[1] * g1 + G[2] * g2;
+    gy[t] = G[1] * g0 + G[3] * g1 + G[4] * g2;
+    cb[t] = G[2] * g0 + G[4] * g1 + G[5] * g2;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    line_bases<N>(t, j, bx, by, bz);
+    line_apply<N, N2, true>(cb + bz, tb.Dq);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    line_bases<N>(t, j, bx, by, bz);
+    line_apply2<N, N, true, true>(gy + by, cb + by, tb.Dq);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    line_bases<N>(t, j, bx, by, bz);
+    line_apply2<N, 1, true, true>(gx + bx, cb + bx, tb.Dq);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    line_bases<N>(t, j, bx, by, bz);
+    line_apply<N, N2, true>(cb + bz, tb.Pq);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    line_bases<N>(t, j, bx, by, bz);
+    line_apply<N, N, true>(cb + by, tb.Pq);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    line_bases<N>(t, j, bx, by, bz);
+    line_apply<N, 1, true>(cb + bx, tb.Pq);
+  }
+  __syncthreads();
+}
+
 template <int K, typename T, int MODE, int NT = BLOCK>
 __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
   pdl_begin();
   constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmemLayout SL = smem_layout<T>(N3, A.tc, A.max_local);
+  const bool mapped = A.geom != 0;
+  const SmemLayout SL = smem_layout<T>(N3, A.tc, A.max_local, mapped);
+  T* gx = reinterpret_cast<T*>(smem + SL.gx);
+  T* gy = reinterpret_cast<T*>(smem + SL.gy);
+  T* gr = reinterpret_cast<T*>(smem + SL.gr);
+  const T eps = (T)A.geps;
   CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem + SL.meta);
   T* sm_h = reinterpret_cast<T*>(smem + SL.h);
   uint16_t* sm_mask = reinterpret_cast<uint16_t*>(smem + SL.mask);
@@ -242,10 +408,11 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
         }
       }
     } else if (MODE == MODE_DIAG) {
-      for (int t = threadIdx.x; t < nch * N3; t += blockDim.x) {
-        const int j = t / N3, n = t - j * N3;
-        cb[t] = (T)(A.diag_tab[(sm_mask[j] & 0x1FF) * N3 + n]) * sm_h[j];
-      }
+      if (!mapped)
+        for (int t = threadIdx.x; t < nch * N3; t += blockDim.x) {
+          const int j = t / N3, n = t - j * N3;
+          cb[t] = (T)(A.diag_tab[(sm_mask[j] & 0x1FF) * N3 + n]) * sm_h[j];
+        }
     } else if (MODE == MODE_LIFT) {
       // u_g before C_e: at a node of a hanging face or edge the value at the
       // parent's node with the same local index, elsewhere the value at the
@@ -266,6 +433,7 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
           bnd |= (nd[d] == 0 && I == 0) || (nd[d] == K && I == last);
           p[d] = A.lo + h * ((double)I + tab<double>(K).xi[nd[d]]);
         }
+        if (mapped) warp_point<double>(A.geps, p[0], p[1], p[2]);
         cb[t] = bnd ? (T)func_u(A.fn, p[0], p[1], p[2]) : T(0);
       }
     } else {  // MODE_RHS: h^3 w_q f(x_q) at the Gauss points, then S^T
@@ -277,9 +445,16 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
         const double x = A.lo + h * (A.cell_ijk[3 * ci + 0] + (double)tab<double>(K).gq[qa]);
         const double y = A.lo + h * (A.cell_ijk[3 * ci + 1] + (double)tab<double>(K).gq[qb]);
         const double z = A.lo + h * (A.cell_ijk[3 * ci + 2] + (double)tab<double>(K).gq[qc]);
-        const double f = func_f(A.fn, x, y, z);
         const double w = tab<double>(K).gw[qa] * tab<double>(K).gw[qb] * tab<double>(K).gw[qc];
-        cb[t] = (T)(w * h * h * h * f);
+        if (mapped) {  // w det(J) f(Phi(x)), det(J) = h^3 det(J_Phi)
+          double G[6];
+          const double dj = warp_metric<double>(A.geps, x, y, z, 1.0, G);
+          double px = x, py = y, pz = z;
+          warp_point<double>(A.geps, px, py, pz);
+          cb[t] = (T)(w * h * h * h * dj * func_f(A.fn, px, py, pz));
+        } else {
+          cb[t] = (T)(w * h * h * h * func_f(A.fn, x, y, z));
+        }
       }
       __syncthreads();
       const DevTables<T>& tb = tab<T>(K);
@@ -303,7 +478,25 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
     __syncthreads();
     if (MODE == MODE_VMULT) {
       hanging_all<K, false>(cb, sm_mask, nch);  // C_e
-      cell_laplace<K>(cb, sm_h, nch);           // S^T Q S
+      if (mapped)                               // S^T Q S
+        cell_laplace_mapped<K, T>(cb, gx, gy, sm_h, sm_cell, sm_meta, A.cell_ijk, ti.cell_begin, A.lo, A.dom, eps, nch);
+      else
+        cell_laplace<K>(cb, sm_h, nch);
+    }
+    if (MODE == MODE_DIAG && mapped) {
+      // (C_e^T A_e C_e)_nn of every cell, column by column (Eqs. 3-4): no
+      // per-mask table for cells with their own geometry
+      for (int n = 0; n < N3; ++n) {
+        for (int t = threadIdx.x; t < nch * N3; t += blockDim.x) cb[t] = (t % N3 == n) ? T(1) : T(0);
+        __syncthreads();
+        hanging_all<K, false>(cb, sm_mask, nch);
+        cell_laplace_mapped<K, T>(cb, gx, gy, sm_h, sm_cell, sm_meta, A.cell_ijk, ti.cell_begin, A.lo, A.dom, eps, nch);
+        hanging_all<K, true>(cb, sm_mask, nch);
+        for (int j = threadIdx.x; j < nch; j += blockDim.x) gr[j * N3 + n] = cb[j * N3 + n];
+        __syncthreads();
+      }
+      for (int t = threadIdx.x; t < nch * N3; t += blockDim.x) cb[t] = gr[t];
+      __syncthreads();
     }
     if (MODE == MODE_LIFT) {
       hanging_all<K, false>(cb, sm_mask, nch);  // C_e: interpolated boundary values at hanging nodes
@@ -322,10 +515,14 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
           bnd |= (nd[d] == 0 && I == 0) || (nd[d] == K && I == last);
           p[d] = A.lo + h * ((double)I + tab<double>(K).xi[nd[d]]);
         }
+        if (mapped) warp_point<double>(A.geps, p[0], p[1], p[2]);
         if (bnd && node_hangs<K>(sm_mask[j], nd[0], nd[1], nd[2])) cb[t] = (T)func_u(A.fn, p[0], p[1], p[2]);
       }
       __syncthreads();
-      cell_laplace<K>(cb, sm_h, nch);  // -A_e u_g
+      if (mapped)  // -A_e u_g
+        cell_laplace_mapped<K, T>(cb, gx, gy, sm_h, sm_cell, sm_meta, A.cell_ijk, ti.cell_begin, A.lo, A.dom, eps, nch);
+      else
+        cell_laplace<K>(cb, sm_h, nch);
     }
     if (MODE != MODE_DIAG) hanging_all<K, true>(cb, sm_mask, nch);  // C_e^T
     // G_e^T into the shared accumulator, sub-colour by sub-colour
@@ -1218,6 +1415,12 @@ void launch_cells_nt(const CellLaunch& L, CellArgs<T> A, size_t sm, cudaStream_t
 
 template <int K, typename T, int MODE>
 void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
+  if (A.geom) {  // mapped cells: the chunked kernel with the quadrature-point geometry, every mode
+    const size_t smm = smem_layout<T>((K + 1) * (K + 1) * (K + 1), L.tc, L.max_local, true).total;
+    launch_cells_nt<K, T, MODE, BLOCK>(L, A, smm, s);
+    run_halo<T>(L, A.dst, s);
+    return;
+  }
   const size_t sm = smem_layout<T>((K + 1) * (K + 1) * (K + 1), L.tc, L.max_local).total;
   if constexpr (MODE == MODE_VMULT && sizeof(T) == 8) {
     if (L.tc <= CHUNK) {  // fp64 operator: double-float arithmetic on the FP32 pipe
@@ -1277,6 +1480,8 @@ CellArgs<T> make_args(const CellLaunch& L) {
   A.lo = L.lo;
   A.dom = L.dom;
   A.coef = L.coef;
+  A.geom = L.geom;
+  A.geps = L.geps;
   A.tc = L.tc;
   A.max_local = L.max_local;
   return A;
@@ -1295,9 +1500,10 @@ void dispatch(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
 
 }  // namespace
 
-size_t cell_smem_bytes(int k, bool fp64, int tc, int max_local) {
+size_t cell_smem_bytes(int k, bool fp64, int tc, int max_local, bool mapped) {
   const int n3 = (k + 1) * (k + 1) * (k + 1);
-  return fp64 ? smem_layout<double>(n3, tc, max_local).total : smem_layout<float>(n3, tc, max_local).total;
+  return fp64 ? smem_layout<double>(n3, tc, max_local, mapped).total
+              : smem_layout<float>(n3, tc, max_local, mapped).total;
 }
 
 void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, int add, cudaStream_t s) {
@@ -1313,7 +1519,7 @@ void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, in
     A.src = static_cast<const float*>(src);
     A.dst = static_cast<float*>(dst);
     A.add = add;
-    if (L.tc > 64 || L.use_lines) {
+    if (L.tc > 64 || L.use_lines || L.geom) {
       dispatch<float, MODE_VMULT>(L, A, s);
       return;
     }

@@ -2,7 +2,7 @@
 
     python -m paper_2203_12292_gb300.opbench [--workload q4octant] [--level -1]
         [--op vmult|restrict|prolong|mlp] [--dtype f32|f64] [--reps 20]
-        [--tile-cells 0] [--cell-kernel 0|1|2] [--cell-threads 0]
+        [--tile-cells 0] [--cell-kernel 0|1|2] [--cell-threads 0] [--warp EPS]
 
 vmult: the level's operator; restrict/prolong: the transfer between the
 level and the next coarser one; mlp: the learned-smoother correction (Q4,
@@ -38,6 +38,7 @@ def main(argv=None):
     ap.add_argument("--tile-cells", type=int, default=0)
     ap.add_argument("--cell-kernel", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--cell-threads", type=int, default=0, choices=[0, 128, 256, 384, 512])
+    ap.add_argument("--warp", type=float, default=None, help="cells mapped by the warp of this eps")
     a = ap.parse_args(argv)
     import torch
 
@@ -50,6 +51,9 @@ def main(argv=None):
     mesh = Mesh.from_recipe(w.recipe)
     mg = Multigrid(mesh, w.degree, p_coarsening=w.p_coarsening, mg_fp32=True, tile_cells=a.tile_cells,
                    cell_kernel=a.cell_kernel, cell_threads=a.cell_threads)
+    if a.warp is not None:
+        from . import GEOM_WARP
+        mg.set_geometry(GEOM_WARP, a.warp)
     lev = a.level if a.level >= 0 else mg.num_levels + a.level
     n = mg.n_free(lev)
     dt = torch.float32 if a.dtype == "f32" else torch.float64
@@ -86,7 +90,7 @@ def main(argv=None):
     print(json.dumps({"workload": w.name, "op": a.op, "level": lev, "dtype": a.dtype, "n_free": n,
                       "cells": info.n_cells,
                       "tiles": info.n_tiles, "halo_dofs": info.n_halo, "tile_cells": info.tile_cells,
-                      "cell_kernel": a.cell_kernel, "cell_threads": a.cell_threads,
+                      "cell_kernel": a.cell_kernel, "cell_threads": a.cell_threads, "warp": a.warp,
                       "ms": ms, "gdofs": n / ms / 1e6}))
 
 
