@@ -149,7 +149,8 @@ struct SmemLayout {
 // mapped: three more chunk buffers (two reference-gradient components and,
 // for the diagonal, the collected entries) for the non-Cartesian operator
 template <typename T>
-__host__ __device__ inline SmemLayout smem_layout(int n3, int tc, int max_local, bool mapped = false) {
+__host__ __device__ inline SmemLayout smem_layout(int n3, int tc, int max_local, bool mapped = false,
+                                                  bool diag = false) {
   SmemLayout L;
   size_t o = 0;
   L.meta = o;
@@ -175,7 +176,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n3, int tc, int max_local,
     L.gy = o;
     o += (size_t)CHUNK * n3 * sizeof(T);
     L.gr = o;
-    o += (size_t)CHUNK * n3 * sizeof(T);
+    if (diag) o += (size_t)CHUNK * n3 * sizeof(T);
   }
   L.total = (o + 15) & ~(size_t)15;
   return L;
@@ -311,10 +312,11 @@ __device__ void cell_laplace_mapped(T* cb, T* gx, T* gy, const T* sm_h, const ui
     const int jj = t / N3, q = t - jj * N3;
     const int qa = q % N, qb = (q / N) % N, qc = q / N2;
     const int ci = cell_begin + sm_cell[jj];
-    const double h = ldexp(dom, -(int)sm_meta[sm_cell[jj]].level);
-    const T x = (T)(lo + h * ((double)cell_ijk[3 * ci + 0] + (double)tab<double>(K).gq[qa]));
-    const T y = (T)(lo + h * ((double)cell_ijk[3 * ci + 1] + (double)tab<double>(K).gq[qb]));
-    const T z = (T)(lo + h * ((double)cell_ijk[3 * ci + 2] + (double)tab<double>(K).gq[qc]));
+    // the Gauss point in the arithmetic of T (fp32 positions for the fp32 operator)
+    const T h = (T)dom / (T)(1 << sm_meta[sm_cell[jj]].level);
+    const T x = (T)lo + h * ((T)cell_ijk[3 * ci + 0] + tb.gq[qa]);
+    const T y = (T)lo + h * ((T)cell_ijk[3 * ci + 1] + tb.gq[qb]);
+    const T z = (T)lo + h * ((T)cell_ijk[3 * ci + 2] + tb.gq[qc]);
     T G[6];
     warp_metric<T>(eps, x, y, z, tb.gw[qa] * tb.gw[qb] * tb.gw[qc] * sm_h[jj], G);
     const T g0 = gx[t], g1 = gy[t], g2 = cb[t];
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
   constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
   extern __shared__ __align__(16) unsigned char smem[];
   const bool mapped = A.geom != 0;
-  const SmemLayout SL = smem_layout<T>(N3, A.tc, A.max_local, mapped);
+  const SmemLayout SL = smem_layout<T>(N3, A.tc, A.max_local, mapped, MODE == MODE_DIAG);
   T* gx = reinterpret_cast<T*>(smem + SL.gx);
   T* gy = reinterpret_cast<T*>(smem + SL.gy);
   T* gr = reinterpret_cast<T*>(smem + SL.gr);
@@ -1416,7 +1418,7 @@ void launch_cells_nt(const CellLaunch& L, CellArgs<T> A, size_t sm, cudaStream_t
 template <int K, typename T, int MODE>
 void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
   if (A.geom) {  // mapped cells: the chunked kernel with the quadrature-point geometry, every mode
-    const size_t smm = smem_layout<T>((K + 1) * (K + 1) * (K + 1), L.tc, L.max_local, true).total;
+    const size_t smm = smem_layout<T>((K + 1) * (K + 1) * (K + 1), L.tc, L.max_local, true, MODE == MODE_DIAG).total;
     launch_cells_nt<K, T, MODE, BLOCK>(L, A, smm, s);
     run_halo<T>(L, A.dst, s);
     return;
@@ -1502,8 +1504,8 @@ void dispatch(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
 
 size_t cell_smem_bytes(int k, bool fp64, int tc, int max_local, bool mapped) {
   const int n3 = (k + 1) * (k + 1) * (k + 1);
-  return fp64 ? smem_layout<double>(n3, tc, max_local, mapped).total
-              : smem_layout<float>(n3, tc, max_local, mapped).total;
+  return fp64 ? smem_layout<double>(n3, tc, max_local, mapped, mapped).total
+              : smem_layout<float>(n3, tc, max_local, mapped, mapped).total;
 }
 
 void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, int add, cudaStream_t s) {
