@@ -575,6 +575,7 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
     L->halo_dofs.upload(lh.halo_dofs, H.stream);
     L->halo_ptr.upload(lh.halo_ptr, H.stream);
     L->halo_src.upload(lh.halo_src, H.stream);
+    L->halo_pos.upload(lh.halo_pos, H.stream);
     L->meta.upload(lh.meta, H.stream);
     L->foreign.upload(lh.foreign, H.stream);
     L->subptr.upload(lh.subptr, H.stream);
@@ -596,6 +597,7 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
     c.halo_dofs = L->halo_dofs.as<int32_t>();
     c.halo_ptr = L->halo_ptr.as<int32_t>();
     c.halo_src = L->halo_src.as<int32_t>();
+    c.halo_pos = L->halo_pos.as<int32_t>();
     c.n_halo = (int)lh.halo_dofs.size();
     c.meta = L->meta.as<CellMeta>();
     c.foreign = L->foreign.as<int32_t>();

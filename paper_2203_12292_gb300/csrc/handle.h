@@ -17,7 +17,7 @@ struct LevelDev {
   LevelHost host;
   bool fp32 = true;
   DevBuf tiles, meta, foreign, subptr, perm, cell_ijk, gstart, own, mask;
-  DevBuf halo, halo_dofs, halo_ptr, halo_src;
+  DevBuf halo, halo_dofs, halo_ptr, halo_src, halo_pos;
   DevBuf diag64, dinv64, dinv32;
   DevBuf x, b, d, t;        // V-cycle vectors in level precision
   DevBuf w64a, w64b, w64c;  // fp64 work vectors (set-up, fp64 smoothing through the API)

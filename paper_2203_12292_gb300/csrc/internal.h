@@ -121,6 +121,7 @@ struct LevelHost {
   std::vector<int32_t> halo_dofs;  // DoFs that receive contributions from other tiles (increasing)
   std::vector<int32_t> halo_ptr;   // per halo DoF: range into halo_src
   std::vector<int32_t> halo_src;   // foreign-slot indices (positions in `foreign`)
+  std::vector<int32_t> halo_pos;   // per foreign slot: its position in the DoF-ordered halo buffer
   int max_local = 0;               // max tile-local DoF count
   int max_sub = 0;
   // dof coordinates (host) for checks

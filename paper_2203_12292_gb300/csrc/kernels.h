@@ -28,6 +28,7 @@ struct CellLaunch {
   const int32_t* halo_dofs;
   const int32_t* halo_ptr;
   const int32_t* halo_src;
+  const int32_t* halo_pos;  // per foreign slot: position in the DoF-ordered halo buffer
   int n_halo;
   int k;
   int tc;

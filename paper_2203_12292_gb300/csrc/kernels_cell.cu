@@ -46,6 +46,7 @@ struct CellArgs {
   const TileInfo* tiles;
   const CellMeta* meta;
   const int32_t* foreign;
+  const int32_t* halo_pos;
   const uint16_t* subptr;
   const uint8_t* perm;
   const int32_t* cell_ijk;
@@ -199,14 +200,15 @@ __device__ __forceinline__ void load_tile_dofs(T* xs, const T* src, const int32_
 
 // owned DoFs: plain stores (or additions); foreign DoFs: into the halo slots
 template <typename T>
-__device__ __forceinline__ void write_tile_dofs(T* dst, T* halo, const T* ys, const TileInfo& ti, int add) {
+__device__ __forceinline__ void write_tile_dofs(T* dst, T* halo, const int32_t* halo_pos, const T* ys,
+                                                const TileInfo& ti, int add) {
   T* d = dst + ti.dof_begin;
   if (add)
     for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) d[i] += ys[i];
   else
     for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) d[i] = ys[i];
-  T* h = halo + ti.foreign_begin;
-  for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) h[i] = ys[ti.n_owned + i];
+  const int32_t* hp = halo_pos + ti.foreign_begin;
+  for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) halo[hp[i]] = ys[ti.n_owned + i];
 }
 
 // ---------------------------------------------------------------------------
@@ -549,7 +551,7 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
     }
   }
   __syncthreads();
-  write_tile_dofs(A.dst, A.halo, ys, ti, A.add);
+  write_tile_dofs(A.dst, A.halo, A.halo_pos, ys, ti, A.add);
 }
 
 // ---------------------------------------------------------------------------
@@ -733,7 +735,7 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
     }
     __syncthreads();
   }
-  write_tile_dofs(A.dst, A.halo, ys, ti, A.add);
+  write_tile_dofs(A.dst, A.halo, A.halo_pos, ys, ti, A.add);
 }
 
 // ---------------------------------------------------------------------------
@@ -883,8 +885,8 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines_df(CellArgs<double> A) {
     for (int i = threadIdx.x; i < ti.n_owned; i += BLOCK) d[i] += df_to(ys[i]);
   else
     for (int i = threadIdx.x; i < ti.n_owned; i += BLOCK) d[i] = df_to(ys[i]);
-  double* hl = A.halo + ti.foreign_begin;
-  for (int i = threadIdx.x; i < ti.n_foreign; i += BLOCK) hl[i] = df_to(ys[ti.n_owned + i]);
+  const int32_t* hp = A.halo_pos + ti.foreign_begin;
+  for (int i = threadIdx.x; i < ti.n_foreign; i += BLOCK) A.halo[hp[i]] = df_to(ys[ti.n_owned + i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1340,21 +1342,20 @@ __global__ void __launch_bounds__(11 * 32, 2) vmult_slab(CellArgs<float> A) {
       for (int i = threadIdx.x; i < ti.n_owned; i += nthr) d[i] += buf[swz(i)];
     else
       for (int i = threadIdx.x; i < ti.n_owned; i += nthr) d[i] = buf[swz(i)];
-    float* hl = A.halo + ti.foreign_begin;
-    for (int i = threadIdx.x; i < ti.n_foreign; i += nthr) hl[i] = buf[swz(ti.n_owned + i)];
+    const int32_t* hp = A.halo_pos + ti.foreign_begin;
+    for (int i = threadIdx.x; i < ti.n_foreign; i += nthr) A.halo[hp[i]] = buf[swz(ti.n_owned + i)];
   }
 }
 
 // second pass: every DoF that other tiles contributed to adds its halo slots
 // in a fixed order
 template <typename T>
-__global__ void halo_add_kernel(T* dst, const T* halo, const int32_t* dofs, const int32_t* ptr,
-                                const int32_t* src, int nh) {
+__global__ void halo_add_kernel(T* dst, const T* halo, const int32_t* dofs, const int32_t* ptr, int nh) {
   pdl_begin();
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nh; u += gridDim.x * blockDim.x) {
     const int32_t g = dofs[u];
     T s = dst[g];
-    for (int e = ptr[u]; e < ptr[u + 1]; ++e) s += halo[src[e]];
+    for (int e = ptr[u]; e < ptr[u + 1]; ++e) s += halo[e];  // the DoF's slots are contiguous
     dst[g] = s;
   }
 }
@@ -1403,7 +1404,7 @@ void run_halo(const CellLaunch& L, T* dst, cudaStream_t s) {
   const int nb = std::min((L.n_halo + BLOCK - 1) / BLOCK, 152 * 8);
   {
     launch_pdl(halo_add_kernel<T>, nb, BLOCK, 0, s, dst, static_cast<const T*>(L.halo), L.halo_dofs, L.halo_ptr,
-                                           L.halo_src, L.n_halo);
+               L.n_halo);
     note_launches(1);
   }
 }
@@ -1479,6 +1480,7 @@ CellArgs<T> make_args(const CellLaunch& L) {
   A.perm = L.perm;
   A.cell_ijk = L.cell_ijk;
   A.halo = static_cast<T*>(L.halo);
+  A.halo_pos = L.halo_pos;
   A.lo = L.lo;
   A.dom = L.dom;
   A.coef = L.coef;

@@ -89,6 +89,7 @@ struct TArgs {
   // restriction: coarse tiles
   const TileInfo* tiles;
   T* halo;
+  const int32_t* halo_pos;
   const CellMeta* meta;
   const int32_t* foreign;
   const uint16_t* subptr;
@@ -239,8 +240,8 @@ template <typename T>
 __device__ __forceinline__ void restrict_write(const TArgs<T>& A, const TileInfo& ti, const T* ys) {
   T* dst = A.dst + ti.dof_begin;
   for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) dst[i] += ys[i];
-  T* h = A.halo + ti.foreign_begin;
-  for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) h[i] = ys[ti.n_owned + i];
+  const int32_t* hp = A.halo_pos + ti.foreign_begin;
+  for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) A.halo[hp[i]] = ys[ti.n_owned + i];
 }
 
 template <int K, typename T>
@@ -463,6 +464,7 @@ TArgs<T> targs(const TransferLaunch& L) {
   A.mask_c = L.mask_c;
   A.tiles = L.coarse.tiles;
   A.halo = static_cast<T*>(L.coarse.halo);
+  A.halo_pos = L.coarse.halo_pos;
   A.meta = L.coarse.meta;
   A.foreign = L.coarse.foreign;
   A.subptr = L.coarse.subptr;

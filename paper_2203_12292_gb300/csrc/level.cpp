@@ -306,6 +306,10 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
     }
     L.halo_ptr.push_back((int32_t)nf);
     if (L.halo_dofs.empty()) L.halo_ptr.assign(1, 0);
+    // tiles write each foreign contribution straight to its DoF-ordered position, so that
+    // the halo pass reads every DoF's slots contiguously
+    L.halo_pos.assign(nf, 0);
+    for (int64_t e = 0; e < nf; ++e) L.halo_pos[L.halo_src[e]] = (int32_t)e;
   }
   // global starts and transfer ownership (first non-hanging reference wins)
   L.gstart.assign((size_t)nc * NSLOT, -1);
