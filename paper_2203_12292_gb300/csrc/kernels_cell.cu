@@ -610,7 +610,7 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
     node_slot<K>(n % N, (n / N) % N, n / N2, slot, off);
     s_so[n] = (uint16_t)(slot | (off << 5));
   }
-  if (threadIdx.x == 0) xs[nloc] = T(0);  // zero slot: absent DoFs gather 0
+  if (threadIdx.x < (K > 1 ? K - 1 : 1)) xs[nloc + threadIdx.x] = T(0);  // zero slots: absent DoFs gather 0
   for (int r = threadIdx.x; r < N2; r += BLOCK) s_lab[r] = tb.lam[r % N] + tb.lam[r / N];
   for (int s = threadIdx.x; s <= ti.n_sub; s += BLOCK) s_sub[s] = A.subptr[ti.sub_begin + s];
   cp_async_wait_all();
@@ -628,9 +628,9 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
 
   // the thread's lines t = tid + BLOCK i (cell position j = t / N2, r = t % N2 = b + N c) and the
   // tile-local starts of their three x-classes (node a = 0, interior 1..K-1, a = K); absent DoFs
-  // point to the zero slot xs[nloc], so gather and scatter need no branch per node (the slot
-  // reads 0 in the gather and absorbs the dropped contributions in the scatter; it is never
-  // written out)
+  // point to the zero slots xs[nloc .. nloc+K-2], so gather and scatter need no branch per node
+  // (the slots read 0 in the gather and absorb the dropped contributions in the scatter; they are
+  // never written out)
   int lj[LPT], lr[LPT], g0[LPT], g1[LPT], g2[LPT];
 #pragma unroll
   for (int i = 0; i < LPT; ++i) {
@@ -655,7 +655,7 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
       T* out = cb + N * t;
       out[0] = xs[g0[i]];
 #pragma unroll
-      for (int a = 1; a < K; ++a) out[a] = xs[g1[i] == nloc ? nloc : g1[i] + a - 1];
+      for (int a = 1; a < K; ++a) out[a] = xs[g1[i] + a - 1];  // absent: the K-1 zero slots
       out[K] = xs[g2[i]];
     }
   }
@@ -726,10 +726,8 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
       if (t >= t0 && t < t1) {
         const T* in = cb + N * t;
         ys[g0[i]] += in[0];
-        if (g1[i] != nloc) {
 #pragma unroll
-          for (int a = 1; a < K; ++a) ys[g1[i] + a - 1] += in[a];
-        }
+        for (int a = 1; a < K; ++a) ys[g1[i] + a - 1] += in[a];
         ys[g2[i]] += in[K];
       }
     }
@@ -1437,7 +1435,7 @@ void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
   }
   if constexpr (MODE == MODE_VMULT && sizeof(T) == 4) {
     if (L.tc <= CHUNK && L.threads == BLOCK) {
-      // vmult_lines keeps one tile-DoF buffer (input, then accumulator) plus the zero slot
+      // vmult_lines keeps one tile-DoF buffer (input, then accumulator) plus K-1 <= 4 zero slots
       const size_t sm1 = sm - (size_t)L.max_local * sizeof(T) + 16;
       ensure_smem(vmult_lines<K, T>, sm1);
       launch_pdl(vmult_lines<K, T>, L.n_tiles, BLOCK, sm1, s, A);
