@@ -62,6 +62,15 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// a double-float value hi + lo (arithmetic further below)
+struct df {
+  float hi, lo;
+  df() = default;
+  __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr df(int v) : hi((float)v), lo(0.f) {}
+  __host__ __device__ df(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+};
+
 template <typename T>
 struct DevTables {
   T B[NMAX][NMAX];          // fast-diagonalisation transform, rows = modes
@@ -85,6 +94,8 @@ static __constant__ DevTables<float> c_tf[KMAX + 1];
 // low parts of the fp64 tables: c_tf + c_tflo represents every entry to
 // about 2^-48 (double-float constants)
 static __constant__ DevTables<float> c_tflo[KMAX + 1];
+// the fp64 tables as double-float pairs (the mapped fp64 operator)
+static __constant__ DevTables<df> c_tdf[KMAX + 1];
 
 template <typename T>
 __device__ __forceinline__ const DevTables<T>& tab(int k);
@@ -95,6 +106,10 @@ __device__ __forceinline__ const DevTables<double>& tab<double>(int k) {
 template <>
 __device__ __forceinline__ const DevTables<float>& tab<float>(int k) {
   return c_tf[k];
+}
+template <>
+__device__ __forceinline__ const DevTables<df>& tab<df>(int k) {
+  return c_tdf[k];
 }
 
 // host: fill the tables of all degrees from the fp64 1D basis
@@ -172,6 +187,20 @@ static inline void fill_tables(DevTables<double>* td, DevTables<float>* tf) {
   }
 }
 
+// host: the fp64 tables split into double-float pairs
+static inline void fill_tables_df(const DevTables<double>* td, DevTables<df>* out) {
+  static_assert(sizeof(DevTables<df>) == sizeof(DevTables<double>), "table layout");
+  for (int k = 0; k <= KMAX; ++k) {
+    const double* d = reinterpret_cast<const double*>(&td[k]);
+    float* o = reinterpret_cast<float*>(&out[k]);
+    for (size_t i = 0; i < sizeof(DevTables<double>) / sizeof(double); ++i) {
+      const float h = (float)d[i];
+      o[2 * i] = h;
+      o[2 * i + 1] = (float)(d[i] - (double)h);
+    }
+  }
+}
+
 // host: low parts tflo = fp32(td - tf) of the fp64 tables
 static inline void fill_tables_lo(const DevTables<double>* td, const DevTables<float>* tf, DevTables<float>* lo) {
   for (int k = 0; k <= KMAX; ++k) {
@@ -187,11 +216,14 @@ static inline void fill_tables_lo(const DevTables<double>* td, const DevTables<f
     static DevTables<double> td[KMAX + 1];                                   \
     static DevTables<float> tf[KMAX + 1];                                    \
     static DevTables<float> tl[KMAX + 1];                                    \
+    static DevTables<df> tdf[KMAX + 1];                                      \
     fill_tables(td, tf);                                                     \
     fill_tables_lo(td, tf, tl);                                              \
+    fill_tables_df(td, tdf);                                                 \
     cudaMemcpyToSymbol(c_td, td, sizeof(td));                                \
     cudaMemcpyToSymbol(c_tf, tf, sizeof(tf));                                \
     cudaMemcpyToSymbol(c_tflo, tl, sizeof(tl));                              \
+    cudaMemcpyToSymbol(c_tdf, tdf, sizeof(tdf));                             \
   }
 
 // entity slot and offset of local node (a,b,c) of a degree-K cell: the slot
@@ -535,9 +567,6 @@ __device__ __forceinline__ void cell_laplace(T* cb, const T* sm_h, int ncells) {
 // fused multiply-add product error); explicit _rn intrinsics keep the
 // compiler from contracting the roundings they rely on.
 // ---------------------------------------------------------------------------
-struct df {
-  float hi, lo;
-};
 
 __device__ __forceinline__ df df_from(double x) {
   const float h = __double2float_rn(x);
@@ -575,6 +604,21 @@ __device__ __forceinline__ df df_mul(df a, df b) { return df_mulc(a, b.hi, b.lo)
 
 // s + a * (ch + cl)
 __device__ __forceinline__ df df_fma(df s, df a, float ch, float cl) { return df_add(s, df_mulc(a, ch, cl)); }
+
+// a / b: quotient of the high parts, corrected once by the remainder
+__device__ __forceinline__ df df_div(df a, df b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const df r = df_sub(a, df_mulc(b, q1, 0.f));
+  return df_norm(q1, __fdiv_rn(r.hi, b.hi));
+}
+
+// operators, so that the templated cell pipeline runs in double-float unchanged
+__device__ __forceinline__ df operator+(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ df operator-(df a, df b) { return df_sub(a, b); }
+__device__ __forceinline__ df operator-(df a) { return df_neg(a); }
+__device__ __forceinline__ df operator*(df a, df b) { return df_mul(a, b); }
+__device__ __forceinline__ df operator/(df a, df b) { return df_div(a, b); }
+__device__ __forceinline__ df& operator+=(df& a, df b) { return a = df_add(a, b); }
 
 // 1D transforms on df lines (BASE + i STRIDE) with the fp64 tables of degree K
 template <int K, int STRIDE, bool TRANS>

@@ -742,7 +742,18 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
 // structure of vmult_lines with the tile buffer and the cell buffers in df;
 // values are converted once on entry to and once on exit from the tile.
 // ---------------------------------------------------------------------------
-template <int K>
+// shared memory of the mapped variant: the layout of the operator kernel up
+// to the tile buffer, then two gradient buffers of MAPPED_SUB cells
+constexpr int MAPPED_SUB = 16;
+__host__ __device__ inline size_t mapped_df_gx(int n3, int tc, int max_local) {
+  const SmemLayout SL = smem_layout<double>(n3, tc, max_local);
+  return (SL.xs + (size_t)max_local * sizeof(double) + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t mapped_df_smem(int n3, int tc, int max_local) {
+  return mapped_df_gx(n3, tc, max_local) + 2 * (size_t)MAPPED_SUB * n3 * sizeof(double);
+}
+
+template <int K, bool MAPPED = false>
 __global__ void __launch_bounds__(BLOCK) vmult_lines_df(CellArgs<double> A) {
   pdl_begin();
   constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
@@ -823,41 +834,50 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines_df(CellArgs<double> A) {
   for (int i = threadIdx.x; i < nloc; i += BLOCK) ys[i] = df{0.f, 0.f};
   df_hanging_all<K, false>(cb, sm_mask, hang ? nc : 0);  // C_e
 
-  // S^T Q S with even-odd sweeps
-#pragma unroll 1
-  for (int t = threadIdx.x; t < nl; t += BLOCK) df_eo_forward<K, 1>(cb + (t / N2) * N3 + N * (t % N2));
-  __syncthreads();
-#pragma unroll 1
-  for (int t = threadIdx.x; t < nl; t += BLOCK) {
-    const int j = t / N2, r = t - j * N2;
-    df_eo_forward<K, N>(cb + j * N3 + r % N + N2 * (r / N));
+  if constexpr (MAPPED) {
+    // non-Cartesian cells: the quadrature-point operator in double-float, MAPPED_SUB cells at a time
+    df* gx = reinterpret_cast<df*>(smem + mapped_df_gx(N3, A.tc, A.max_local));
+    df* gy = gx + MAPPED_SUB * N3;
+    for (int s0 = 0; s0 < nc; s0 += MAPPED_SUB)
+      cell_laplace_mapped<K, df>(cb + s0 * N3, gx, gy, sm_h + s0, sm_cell + s0, sm_meta, A.cell_ijk, ti.cell_begin,
+                                 A.lo, A.dom, df(A.geps), min(MAPPED_SUB, nc - s0));
+  } else {
+    // S^T Q S with even-odd sweeps
+  #pragma unroll 1
+    for (int t = threadIdx.x; t < nl; t += BLOCK) df_eo_forward<K, 1>(cb + (t / N2) * N3 + N * (t % N2));
+    __syncthreads();
+  #pragma unroll 1
+    for (int t = threadIdx.x; t < nl; t += BLOCK) {
+      const int j = t / N2, r = t - j * N2;
+      df_eo_forward<K, N>(cb + j * N3 + r % N + N2 * (r / N));
+    }
+    __syncthreads();
+  #pragma unroll 1
+    for (int t = threadIdx.x; t < nl; t += BLOCK) {
+      const int j = t / N2, r = t - j * N2;
+      df* p = cb + j * N3 + r;
+      df v[N];
+  #pragma unroll
+      for (int c = 0; c < N; ++c) v[c] = p[c * N2];
+      df_eo_forward<K, 1>(v);
+      const df h = sm_h[j];
+  #pragma unroll
+      for (int c = 0; c < N; ++c) v[c] = df_mul(df_mul(v[c], s_lam3[r + N2 * c]), h);
+      df_eo_backward<K, 1>(v);
+  #pragma unroll
+      for (int c = 0; c < N; ++c) p[c * N2] = v[c];
+    }
+    __syncthreads();
+  #pragma unroll 1
+    for (int t = threadIdx.x; t < nl; t += BLOCK) {
+      const int j = t / N2, r = t - j * N2;
+      df_eo_backward<K, N>(cb + j * N3 + r % N + N2 * (r / N));
+    }
+    __syncthreads();
+  #pragma unroll 1
+    for (int t = threadIdx.x; t < nl; t += BLOCK) df_eo_backward<K, 1>(cb + (t / N2) * N3 + N * (t % N2));
+    __syncthreads();
   }
-  __syncthreads();
-#pragma unroll 1
-  for (int t = threadIdx.x; t < nl; t += BLOCK) {
-    const int j = t / N2, r = t - j * N2;
-    df* p = cb + j * N3 + r;
-    df v[N];
-#pragma unroll
-    for (int c = 0; c < N; ++c) v[c] = p[c * N2];
-    df_eo_forward<K, 1>(v);
-    const df h = sm_h[j];
-#pragma unroll
-    for (int c = 0; c < N; ++c) v[c] = df_mul(df_mul(v[c], s_lam3[r + N2 * c]), h);
-    df_eo_backward<K, 1>(v);
-#pragma unroll
-    for (int c = 0; c < N; ++c) p[c * N2] = v[c];
-  }
-  __syncthreads();
-#pragma unroll 1
-  for (int t = threadIdx.x; t < nl; t += BLOCK) {
-    const int j = t / N2, r = t - j * N2;
-    df_eo_backward<K, N>(cb + j * N3 + r % N + N2 * (r / N));
-  }
-  __syncthreads();
-#pragma unroll 1
-  for (int t = threadIdx.x; t < nl; t += BLOCK) df_eo_backward<K, 1>(cb + (t / N2) * N3 + N * (t % N2));
-  __syncthreads();
   df_hanging_all<K, true>(cb, sm_mask, hang ? nc : 0);  // C_e^T
 
   // G_e^T, sub-colour by sub-colour
@@ -1416,6 +1436,16 @@ void launch_cells_nt(const CellLaunch& L, CellArgs<T> A, size_t sm, cudaStream_t
 
 template <int K, typename T, int MODE>
 void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
+  if constexpr (MODE == MODE_VMULT && sizeof(T) == 8) {
+    if (A.geom && L.tc <= CHUNK) {  // mapped cells, fp64 operator: double-float arithmetic on the FP32 pipe
+      const size_t smm = mapped_df_smem((K + 1) * (K + 1) * (K + 1), L.tc, L.max_local);
+      ensure_smem(vmult_lines_df<K, true>, smm);
+      launch_pdl(vmult_lines_df<K, true>, L.n_tiles, BLOCK, smm, s, A);
+      note_launches(1);
+      run_halo<T>(L, A.dst, s);
+      return;
+    }
+  }
   if (A.geom) {  // mapped cells: the chunked kernel with the quadrature-point geometry, every mode
     const size_t smm = smem_layout<T>((K + 1) * (K + 1) * (K + 1), L.tc, L.max_local, true, MODE == MODE_DIAG).total;
     launch_cells_nt<K, T, MODE, BLOCK>(L, A, smm, s);
