@@ -59,10 +59,10 @@ METRIC = "fine-level vmult GDoF/s; solve time to 1e-8 rel. res., mixed/learned v
 BYTES_PER_DOF = {"fp32": 9.8, "fp64": 17.8}
 # DRAM bytes (read + write) of one fine-level fp32 operator application on
 # this workload, both of its launches (tile kernel vmult_lines<4,float>:
-# 115.0 MB read + 54.8 MB written; halo pass: 110.2 MB + 6.9 MB), from the
+# 135.1 MB read + 58.7 MB written; halo pass: 90.4 MB + 3.3 MB), from the
 # ncu capture summarised in profiles/vmult_lines_q4_octant_fp32.md; set to 0
 # (reported as null) when the kernel changes until it is re-captured
-VMULT_TRAFFIC_BYTES = 286.9e6
+VMULT_TRAFFIC_BYTES = 287.5e6
 SAMPLE = synth.cube_octant(4, 2)  # 1/8 of the workload's cells, same recipe family
 
 
@@ -169,7 +169,7 @@ def run_reference(args, rank):
                              "sample": f"one fp64 operator application per step on {SAMPLE.name}"},
             "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "setup_s": time.perf_counter() - t0}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(finite(line), allow_nan=False), flush=True)
 
 
 def run_learned(g, mg, mg64):
@@ -237,6 +237,17 @@ def run_batch(g, seed: int = 12292, n: int = 256):
            "tune_s": t1 - t0, "setup_s": t2 - t1}
     del B
     return out
+
+
+def finite(v):
+    """The JSON line with non-finite numbers (a diverged variant) as null."""
+    if isinstance(v, float):
+        return v if np.isfinite(v) else None
+    if isinstance(v, dict):
+        return {k: finite(x) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [finite(x) for x in v]
+    return v
 
 
 def main():
@@ -426,7 +437,7 @@ def main():
             "learned": learned,
             "batch": batch,
         }
-        print(json.dumps(res), flush=True)
+        print(json.dumps(finite(res), allow_nan=False), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
