@@ -215,11 +215,26 @@ def vcycle(levels: List[Level], l: int, b: np.ndarray) -> np.ndarray:
     xc = vcycle(levels, l - 1, bc)                                 # recursion
     x = x + P @ xc                                                 # prolongation
     if lev.learned is not None and lev.learned_mode == "replace":
-        return x + lev.learned(b - lev.apply(x)).astype(dt)        # learned step only
+        return learned_step(lev, b, x)                             # learned step only
     x = chebyshev(lev.apply, dinv, b, x, lev.lam_max)             # postsmoothing
     if lev.learned is not None:
-        x = x + lev.learned(b - lev.apply(x)).astype(dt)           # learned step after it
+        x = learned_step(lev, b, x)                                # learned step after it
     return x
+
+
+def learned_step(lev: Level, b: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """x + omega c with c the learned correction of the residual and omega
+    the Galerkin step length (r.c) / (c.A c): the A-norm of the error cannot
+    grow whatever the network returns (omega = 0 when c.A c <= 0).  Inner
+    products in fp64."""
+    dt = x.dtype
+    r = b - lev.apply(x)
+    c = lev.learned(r).astype(dt)
+    w = lev.apply(c)
+    num = float(np.dot(r.astype(np.float64), c.astype(np.float64)))
+    den = float(np.dot(c.astype(np.float64), w.astype(np.float64)))
+    om = num / den if den > 0 else 0.0
+    return x + dt.type(om) * c
 
 
 def set_precision(levels: List[Level], dtype) -> None:

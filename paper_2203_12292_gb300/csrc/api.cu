@@ -325,14 +325,21 @@ void mlp_correct(Handle& H, int l, const void* image, bool fp64, const void* r, 
   ck(launch_mlp_correct(P, fp64, r, x, H.stream), "learned correction");
 }
 
-// residual of level l into t, then x += learned correction
+// residual r of level l into t, the learned correction c into d, then
+// x += om c with the Galerkin step length om = (r.c) / (c.A c): the energy
+// norm of the error cannot grow, whatever the network returns
 void learned_step(Handle& H, int l) {
   LevelDev& L = *H.lev[l];
   const bool f64 = !L.fp32;
   const int r = prof_begin(H, l, GCMG_STAGE_LEARNED);
   vmult(H, l, f64, L.x.p, L.t.p);
   launch_residual(f64, L.t.p, L.b.p, L.t.p, L.n(), H.stream);
-  mlp_correct(H, l, L.mlp_image.p, f64, L.t.p, L.x.p);
+  launch_zero(f64, L.d.p, L.n(), H.stream);
+  mlp_correct(H, l, L.mlp_image.p, f64, L.t.p, L.d.p);
+  void* w = f64 ? L.w64a.p : L.w32a.p;
+  vmult(H, l, f64, L.d.p, w);
+  if (!H.lscratch.p) throw Error(GCMG_ERR_INTERNAL, "learned step without its scratch");
+  launch_galerkin_step(f64, L.t.p, L.d.p, w, L.x.p, L.n(), H.lscratch.as<double>(), H.stream);
   prof_end(H, r);
 }
 
@@ -1304,6 +1311,7 @@ int gcmg_set_smoother(gcmg_handle* h, int level, int kind, const gcmg_mlp* net) 
       ensure_dfeat(H, level);
       if (!L.mlp_image.p) L.mlp_image.alloc(mlp_image_bytes());
       launch_mlp_pack(net->net.params.as<float>(), L.mlp_image.p, H.stream);
+      if (!H.lscratch.p) H.lscratch.alloc((2 * DOT_BLOCKS + 2) * sizeof(double));
     }
     L.smoother = kind;
     H.g_core.reset();

@@ -104,6 +104,7 @@ struct Handle {
   DevBuf scratch, scal, modes;
   DevBuf cg_r, cg_p, cg_q, cg_z, cg_x;
   DevBuf mlp_scratch;  // weight image of gcmg_mlp_correct calls
+  DevBuf lscratch;     // inner products of the learned step's Galerkin step length
   ~Handle() {
     g_core.reset();
     g_a.reset();

@@ -102,6 +102,10 @@ void launch_restrict_add(const TransferLaunch& T, bool fp64, const void* fine, v
 void upload_tables();
 void launch_cast(bool to64, const void* src, void* dst, int64_t n, cudaStream_t s);
 void launch_zero(bool fp64, void* x, int64_t n, cudaStream_t s);
+// x += om c with om = (r.c) / (c.w) (0 when c.w <= 0), w = A c; the two inner
+// products in fp64, deterministic; scratch: 2 DOT_BLOCKS + 2 doubles
+void launch_galerkin_step(bool fp64, const void* r, const void* c, const void* w, void* x, int64_t n,
+                          double* scratch, cudaStream_t s);
 // local smoothing, Algorithm 1: dst[idx[i]] = src[g[i]] (to a level, in its
 // precision) and dst[g[i]] = src[idx[i]] (back to the fp64 active vector)
 void launch_copy_to_level(bool fp64, const double* src, const int32_t* g, const int32_t* idx, int64_t n, void* dst,

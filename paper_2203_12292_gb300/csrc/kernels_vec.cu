@@ -56,6 +56,57 @@ __global__ void zero_at_kernel(const int32_t* __restrict__ idx, int64_t n, doubl
   }
 }
 
+// Galerkin step length of the learned correction: (r.c, c.w) in fp64 with a
+// fixed grid and a fixed summation order (bit-reproducible), then x += om c
+template <typename T>
+__global__ void __launch_bounds__(BLOCK) dot_pair_partial(const T* __restrict__ r, const T* __restrict__ c,
+                                                           const T* __restrict__ w, int64_t n, double* part) {
+  pdl_begin();
+  __shared__ double s0[BLOCK], s1[BLOCK];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)BLOCK + threadIdx.x; i < n; i += (int64_t)gridDim.x * BLOCK) {
+    const double ci = (double)c[i];
+    a += (double)r[i] * ci;
+    b += ci * (double)w[i];
+  }
+  s0[threadIdx.x] = a;
+  s1[threadIdx.x] = b;
+  __syncthreads();
+  for (int h = BLOCK / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      s0[threadIdx.x] += s0[threadIdx.x + h];
+      s1[threadIdx.x] += s1[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = s0[0];
+    part[2 * blockIdx.x + 1] = s1[0];
+  }
+}
+
+__global__ void dot_pair_final(const double* part, int nb, double* out) {
+  pdl_begin();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nb; ++i) {
+      a += part[2 * i];
+      b += part[2 * i + 1];
+    }
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+template <typename T>
+__global__ void axpy_ratio_kernel(T* x, const T* c, const double* nd, int64_t n) {
+  pdl_begin();
+  const double den = nd[1];
+  const T om = den > 0.0 ? (T)(nd[0] / den) : T(0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += om * c[i];
+}
+
 template <typename T>
 __global__ void zero_kernel(T* x, int64_t n) {
   pdl_begin();
@@ -337,6 +388,26 @@ void launch_zero_at(const int32_t* idx, int64_t n, double* a, float* b, cudaStre
   if (n <= 0) return;
   launch_pdl(zero_at_kernel, grid_for(n), BLOCK, 0, s, idx, n, a, b);
   note_launches(1);
+}
+
+void launch_galerkin_step(bool fp64, const void* r, const void* c, const void* w, void* x, int64_t n,
+                          double* scratch, cudaStream_t s) {
+  if (n <= 0) return;
+  double* nd = scratch + 2 * DOT_BLOCKS;
+  if (fp64) {
+    launch_pdl(dot_pair_partial<double>, DOT_BLOCKS, BLOCK, 0, s, static_cast<const double*>(r),
+               static_cast<const double*>(c), static_cast<const double*>(w), n, scratch);
+    launch_pdl(dot_pair_final, 1, 32, 0, s, (const double*)scratch, DOT_BLOCKS, nd);
+    launch_pdl(axpy_ratio_kernel<double>, grid_for(n), BLOCK, 0, s, static_cast<double*>(x),
+               static_cast<const double*>(c), (const double*)nd, n);
+  } else {
+    launch_pdl(dot_pair_partial<float>, DOT_BLOCKS, BLOCK, 0, s, static_cast<const float*>(r),
+               static_cast<const float*>(c), static_cast<const float*>(w), n, scratch);
+    launch_pdl(dot_pair_final, 1, 32, 0, s, (const double*)scratch, DOT_BLOCKS, nd);
+    launch_pdl(axpy_ratio_kernel<float>, grid_for(n), BLOCK, 0, s, static_cast<float*>(x),
+               static_cast<const float*>(c), (const double*)nd, n);
+  }
+  note_launches(3);
 }
 
 void launch_zero(bool fp64, void* x, int64_t n, cudaStream_t s) {

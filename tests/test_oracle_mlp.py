@@ -6,6 +6,7 @@ import math
 import numpy as np
 import pytest
 import scipy.sparse as sp
+import scipy.sparse.linalg as sla
 
 import synth
 from oracle import fe, mesh as omesh, mg, mlp
@@ -328,3 +329,25 @@ def test_learned_hook_zero_map_is_the_plain_vcycle():
     top = levels[-1]
     post = mg.chebyshev(top.apply, 1.0 / top.diag, b, xr, top.lam_max)
     assert np.abs(post - x0).max() < 1e-14 * np.abs(x0).max()
+
+
+def test_learned_step_is_the_energy_minimising_step_length():
+    """Galerkin step length: along the learned direction c the A-norm of the
+    error is smallest at omega = (r.c)/(c.A c) (pinned against a scan of
+    omega), and never larger than before the step, for an arbitrary map."""
+    m = omesh.build_mesh(synth.octant(2))
+    levels = mg.build_levels(m, 2)
+    top = levels[-1]
+    A = top.space.assemble()
+    b = top.space.rhs()
+    xs = sla.spsolve(A.tocsc(), b)
+    rng = np.random.default_rng(4)
+    M = rng.standard_normal((len(b), len(b)))
+    top.learned = lambda r: M @ r  # any map, e.g. an untrained network
+    x = synth.uniform_vector(len(b), 8)
+    xn = mg.learned_step(top, b, x)
+    energy = lambda y: float((xs - y) @ (A @ (xs - y)))
+    assert energy(xn) <= energy(x) * (1 + 1e-14)
+    c = M @ (b - A @ x)
+    for om in np.linspace(-2, 2, 41):
+        assert energy(xn) <= energy(x + om * c) * (1 + 1e-12) + 1e-14
