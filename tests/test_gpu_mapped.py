@@ -137,3 +137,45 @@ def test_geometry_arguments(gcmg):
         mg.set_geometry(7, 0.1)
     with pytest.raises(gcmg.GcmgError):  # folds [-1, 1]^3
         mg.set_geometry(gcmg.GEOM_WARP, 2.0)
+
+
+def test_mapped_with_coefficient(gcmg):
+    """geometry and a cell-wise coefficient together (either order) against
+    the oracle's mapped levels with the same coefficient"""
+    rec, k = synth.octant(3), 2
+    nu_f = synth.random_cells(11)
+    levels = omg.build_levels(omesh.build_mesh(rec), k, assembled=False, coefficient=nu_f, warp_eps=EPS)
+    for order in ("geometry first", "coefficient first"):
+        mg = gcmg.Multigrid(gcmg.Mesh.from_recipe(rec), k)
+        xq = mg.quadrature_points().cpu().numpy()
+        nu = torch.tensor(nu_f(xq.reshape(-1, 3)).reshape(xq.shape[:2]), dtype=torch.float64, device="cuda")
+        if order == "geometry first":
+            mg.set_geometry(gcmg.GEOM_WARP, EPS)
+            mg.set_coefficient(nu)
+        else:
+            mg.set_coefficient(nu)
+            mg.set_geometry(gcmg.GEOM_WARP, EPS)
+        for l in range(mg.num_levels):
+            if mg.n_free(l) == 0:
+                continue
+            s = levels[l].space
+            perm = match(mg.dof_coords(l), s.free_coordinates())
+            x = torch.tensor(synth.point_values(mg.dof_coords(l), 3 + l), dtype=torch.float64, device="cuda")
+            y = torch.empty_like(x)
+            mg.vmult(l, x, y)
+            ref = s.apply(synth.point_values(s.free_coordinates(), 3 + l))
+            assert rel_err(y.cpu().numpy(), ref[perm]) < 1e-12, (order, l)
+            assert rel_err(mg.diagonal(l).cpu().numpy(), s.diagonal()[perm]) < 1e-12, (order, l)
+
+
+def test_mapped_with_local_smoothing(gcmg):
+    """the patch test through local smoothing on mapped cells"""
+    mg = gcmg.Multigrid(gcmg.Mesh.from_recipe(synth.octant(3)), 2, local_smoothing=True)
+    mg.set_geometry(gcmg.GEOM_WARP, EPS)
+    terms = [(0.7, 1, 0, 0), (-0.4, 0, 1, 0), (1.3, 0, 0, 1), (0.25, 0, 0, 0)]
+    b = mg.rhs_dirichlet(gcmg.FUNC_POLYNOMIAL, terms)
+    x = torch.zeros_like(b)
+    assert mg.cg_solve(b, x, 1e-13, maxit=80).status == 0
+    y = om.warp(mg.dof_coords(mg.finest), EPS)
+    ref = y @ np.array([0.7, -0.4, 1.3]) + 0.25
+    assert np.abs(x.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
