@@ -914,11 +914,43 @@ int gcmg_vmult_host(gcmg_handle* h, int level, int fp64, const void* src, void* 
     LevelDev& L = *H.lev[level];
     if (L.n() == 0) return;
     if (!src || !dst) throw Error(GCMG_ERR_ARG, "bad vectors");
-    const size_t bytes = L.n() * (fp64 ? sizeof(double) : sizeof(float));
-    void* a = fp64 ? L.w64a.p : L.w32a.p;
-    void* b = fp64 ? L.w64b.p : L.w32b.p;
-    ck(cudaMemcpyAsync(a, src, bytes, cudaMemcpyHostToDevice, H.stream), "copy in");
-    vmult(H, level, fp64 != 0, a, b);
+    const bool f64 = fp64 != 0;
+    const size_t es = f64 ? sizeof(double) : sizeof(float);
+    const size_t bytes = L.n() * es;
+    char* a = static_cast<char*>(f64 ? L.w64a.p : L.w32a.p);
+    void* b = f64 ? L.w64b.p : L.w32b.p;
+    const int nt = L.cl.n_tiles;
+    constexpr int K = 8;  // tile groups
+    if (vmult_tiles_ok(L.cl, f64) && nt >= K) {
+      // the input arrives in DoF order on a second stream; tile group g starts once the DoFs
+      // below the end of its owned range are in (a tile reads no DoF above that)
+      if (!H.copy_stream) ck(cudaStreamCreateWithFlags(&H.copy_stream, cudaStreamNonBlocking), "stream");
+      while (H.pipe_ev.size() < K + 1) {
+        cudaEvent_t e;
+        ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+        H.pipe_ev.push_back(e);
+      }
+      ck(cudaEventRecord(H.pipe_ev[K], H.stream), "event");
+      ck(cudaStreamWaitEvent(H.copy_stream, H.pipe_ev[K], 0), "wait");
+      const char* sp = static_cast<const char*>(src);
+      int64_t done = 0;
+      for (int g = 0; g < K; ++g) {
+        const int t0 = (int)((int64_t)g * nt / K), t1 = (int)((int64_t)(g + 1) * nt / K);
+        const TileInfo& last = L.host.tiles[t1 - 1];
+        const int64_t end = (g == K - 1) ? L.n() : (int64_t)last.dof_begin + last.n_owned;
+        if (end > done)
+          ck(cudaMemcpyAsync(a + done * es, sp + done * es, (end - done) * es, cudaMemcpyHostToDevice, H.copy_stream),
+             "copy in");
+        done = std::max(done, end);
+        ck(cudaEventRecord(H.pipe_ev[g], H.copy_stream), "event");
+        ck(cudaStreamWaitEvent(H.stream, H.pipe_ev[g], 0), "wait");
+        launch_vmult_tiles(L.cl, f64, a, b, t0, t1, H.stream);
+      }
+      launch_halo_add(L.cl, f64, b, H.stream);
+    } else {
+      ck(cudaMemcpyAsync(a, src, bytes, cudaMemcpyHostToDevice, H.stream), "copy in");
+      vmult(H, level, f64, a, b);
+    }
     ck(cudaMemcpyAsync(dst, b, bytes, cudaMemcpyDeviceToHost, H.stream), "copy out");
     ck(cudaStreamSynchronize(H.stream), "vmult_host");
   });

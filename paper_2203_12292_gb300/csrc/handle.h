@@ -105,10 +105,15 @@ struct Handle {
   DevBuf cg_r, cg_p, cg_q, cg_z, cg_x;
   DevBuf mlp_scratch;  // weight image of gcmg_mlp_correct calls
   DevBuf lscratch;     // inner products of the learned step's Galerkin step length
+  // host-buffer operator: the input copy in DoF order on its own stream, overlapped with the tiles
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> pipe_ev;
   ~Handle() {
     g_core.reset();
     g_a.reset();
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (cudaEvent_t e : pipe_ev) cudaEventDestroy(e);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
   }
 };
 

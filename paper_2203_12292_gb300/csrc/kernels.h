@@ -58,6 +58,12 @@ struct RhsDesc {
 
 // dst = A src (add = 0) or dst += A src (add = 1), precision by `fp64`
 void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, int add, cudaStream_t s);
+// the tile kernel of the operator for tiles [t0, t1) only (the halo pass is
+// launch_halo_add, after all tiles); a tile reads x only below the end of its
+// owned range (first-touch ownership), so tile groups can start as the input
+// arrives in DoF order.  vmult_tiles_ok: the level's kernels allow it.
+bool vmult_tiles_ok(const CellLaunch& L, bool fp64);
+void launch_vmult_tiles(const CellLaunch& L, bool fp64, const void* src, void* dst, int t0, int t1, cudaStream_t s);
 // dst = C^T F: Gauss quadrature of f against the basis (FOURIER, ONE: f
 // itself; GAUSSIAN, POLYNOMIAL: f = -Lap u of the manufactured solution u)
 void launch_rhs(const CellLaunch& L, const RhsDesc& f, double* dst, cudaStream_t s);

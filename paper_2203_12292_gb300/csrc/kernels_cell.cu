@@ -62,6 +62,7 @@ struct CellArgs {
   const double* coef;  // per cell nu_e, null: 1
   int geom;            // 0: Cartesian cells; GEOM_WARP: cells mapped by the warp of eps
   double geps;
+  int tile0;           // first tile of the launch (the launch covers gridDim.x tiles)
 };
 
 // scale of the element matrix of cell ci: nu_e h (h = dom 2^-level)
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
   T* xs = reinterpret_cast<T*>(smem + SL.xs);
   T* ys = reinterpret_cast<T*>(smem + SL.ys);
 
-  const TileInfo ti = A.tiles[blockIdx.x];
+  const TileInfo ti = A.tiles[A.tile0 + blockIdx.x];
   const int nc = ti.n_cells;
   const int nloc = ti.n_owned + ti.n_foreign;
   load_meta(sm_meta, A.meta, ti.cell_begin, nc);
@@ -583,7 +584,7 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
   __shared__ uint16_t s_sub[CHUNK + 1];  // sub-colour starts (positions in the permuted cell list)
   const DevTables<T>& tb = tab<T>(K);
 
-  const TileInfo ti = A.tiles[blockIdx.x];
+  const TileInfo ti = A.tiles[A.tile0 + blockIdx.x];
   const int nc = ti.n_cells;
   const int nl = nc * N2;
   const int nloc = ti.n_owned + ti.n_foreign;
@@ -771,7 +772,7 @@ __global__ void __launch_bounds__(BLOCK) vmult_lines_df(CellArgs<double> A) {
   __shared__ df s_lam3[N3];      // lam_a + lam_b + lam_c in mode order
   __shared__ uint16_t s_so[N3];  // per local node: entity slot | offset << 5
 
-  const TileInfo ti = A.tiles[blockIdx.x];
+  const TileInfo ti = A.tiles[A.tile0 + blockIdx.x];
   const int nc = ti.n_cells;  // <= CHUNK
   const int nl = nc * N2;
   const int nloc = ti.n_owned + ti.n_foreign;
@@ -1263,7 +1264,7 @@ __global__ void __launch_bounds__(11 * 32, 2) vmult_slab(CellArgs<float> A) {
   float* creg = lam3 + N3;           // per-cell transposition regions, (tc + 1) x N3
   float* buf = creg + (tc + 1) * N3;  // tile DoFs (padded): input, then the accumulator
   __shared__ int any_hanging;
-  const TileInfo ti = A.tiles[blockIdx.x];
+  const TileInfo ti = A.tiles[A.tile0 + blockIdx.x];
   const int nc = ti.n_cells;
   const int nloc = ti.n_owned + ti.n_foreign;
   const int nthr = blockDim.x;
@@ -1563,6 +1564,43 @@ void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, in
       default: break;
     }
   }
+}
+
+bool vmult_tiles_ok(const CellLaunch& L, bool fp64) {
+  return L.tc <= CHUNK && !L.geom && (fp64 || (L.use_lines && L.threads == BLOCK));
+}
+
+void launch_vmult_tiles(const CellLaunch& L, bool fp64, const void* src, void* dst, int t0, int t1, cudaStream_t s) {
+  if (t1 <= t0 || !vmult_tiles_ok(L, fp64)) return;
+  const int n3 = (L.k + 1) * (L.k + 1) * (L.k + 1);
+  if (fp64) {
+    CellArgs<double> A = make_args<double>(L);
+    A.src = static_cast<const double*>(src);
+    A.dst = static_cast<double*>(dst);
+    A.tile0 = t0;
+    const size_t sm = smem_layout<double>(n3, L.tc, L.max_local).total - (size_t)L.max_local * sizeof(double);
+    switch (L.k) {
+      case 1: ensure_smem(vmult_lines_df<1>, sm); launch_pdl(vmult_lines_df<1>, t1 - t0, BLOCK, sm, s, A); break;
+      case 2: ensure_smem(vmult_lines_df<2>, sm); launch_pdl(vmult_lines_df<2>, t1 - t0, BLOCK, sm, s, A); break;
+      case 3: ensure_smem(vmult_lines_df<3>, sm); launch_pdl(vmult_lines_df<3>, t1 - t0, BLOCK, sm, s, A); break;
+      case 4: ensure_smem(vmult_lines_df<4>, sm); launch_pdl(vmult_lines_df<4>, t1 - t0, BLOCK, sm, s, A); break;
+      default: return;
+    }
+  } else {
+    CellArgs<float> A = make_args<float>(L);
+    A.src = static_cast<const float*>(src);
+    A.dst = static_cast<float*>(dst);
+    A.tile0 = t0;
+    const size_t sm = smem_layout<float>(n3, L.tc, L.max_local).total - (size_t)L.max_local * sizeof(float) + 16;
+    switch (L.k) {
+      case 1: ensure_smem(vmult_lines<1, float>, sm); launch_pdl(vmult_lines<1, float>, t1 - t0, BLOCK, sm, s, A); break;
+      case 2: ensure_smem(vmult_lines<2, float>, sm); launch_pdl(vmult_lines<2, float>, t1 - t0, BLOCK, sm, s, A); break;
+      case 3: ensure_smem(vmult_lines<3, float>, sm); launch_pdl(vmult_lines<3, float>, t1 - t0, BLOCK, sm, s, A); break;
+      case 4: ensure_smem(vmult_lines<4, float>, sm); launch_pdl(vmult_lines<4, float>, t1 - t0, BLOCK, sm, s, A); break;
+      default: return;
+    }
+  }
+  note_launches(1);
 }
 
 void launch_rhs(const CellLaunch& L, const RhsDesc& f, double* dst, cudaStream_t s) {

@@ -344,3 +344,21 @@ def test_tile_sizes_compute_the_same_operator(gcmg, tc):
         a.vmult(a.finest, xa, ya)
         b.vmult(b.finest, xb, yb)
         assert rel_err(ya.double().cpu().numpy(), yb.double().cpu().numpy()[perm]) < tol
+
+
+@pytest.mark.parametrize("fp64", [False, True], ids=["f32", "f64"])
+def test_vmult_host_pipeline_equals_device_vmult(gcmg, fp64):
+    """gcmg_vmult_host overlaps the input copy (in DoF order, on a second
+    stream) with groups of tiles; the result is the device operator's, bit
+    for bit"""
+    mg = gcmg.Multigrid(gcmg.Mesh.from_recipe(synth.cube_octant(3, 1)), 4)
+    l = mg.finest
+    assert mg.level_info(l).n_tiles >= 8
+    dt = torch.float64 if fp64 else torch.float32
+    x = torch.tensor(synth.point_values(mg.dof_coords(l), 12), dtype=dt, device="cuda")
+    y = torch.empty_like(x)
+    mg.vmult(l, x, y)
+    xh = x.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    mg.vmult_host(l, xh.numpy(), yh.numpy())
+    assert torch.equal(yh, y.cpu())
