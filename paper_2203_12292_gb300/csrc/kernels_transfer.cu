@@ -24,7 +24,8 @@ GCMG_DEFINE_UPLOAD(upload_tables_transfer)
 
 namespace {
 
-constexpr int TP = 8;  // coarse cells expanded at a time
+constexpr int TP = 8;   // coarse cells expanded at a time (prolongation, p-transfer)
+constexpr int TPR = 4;  // the same for the h-restriction: 5 instead of 3 CTAs per SM at k = 4
 
 template <int KT, int WHICH, typename T>
 __device__ __forceinline__ T pm(int i, int a) {
@@ -117,9 +118,9 @@ __global__ void __launch_bounds__(BLOCK) prolong_h(TArgs<T> A) {
   __shared__ uint16_t s_e3[8 * N3];            // child q, node n -> position in the 2k+1 lattice
   extern __shared__ __align__(16) unsigned char smem[];
   T* cb = reinterpret_cast<T*>(smem);
-  T* e1 = cb + TP * N3;
-  T* e2 = e1 + TP * S1;
+  T* e2 = cb + TP * N3;
   T* e3 = e2 + TP * S2;
+  T* e1 = e3;  // e1 is dead before the z sweep writes e3
   const int c0 = blockIdx.x * TP;
   const int nc = min(TP, A.n_coarse - c0);
   for (int c = threadIdx.x; c < nc; c += blockDim.x) {
@@ -249,21 +250,21 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
   pdl_begin();
   constexpr int N = K + 1, N3 = N * N * N, M = 2 * K + 1, M3 = M * M * M;
   constexpr int S1 = M * N * N, S2 = M * M * N;
-  __shared__ uint8_t sm_ref[TP];
-  __shared__ int32_t sm_fine[TP];
-  __shared__ uint16_t sm_mask[TP];
-  __shared__ uint16_t sm_cell[TP];
-  __shared__ uint32_t sm_own[TP * 8];          // ownership masks of the fine cells
-  __shared__ int32_t sm_gs[TP * 8 * NSLOT];    // their global slot starts (-1: none)
+  __shared__ uint8_t sm_ref[TPR];
+  __shared__ int32_t sm_fine[TPR];
+  __shared__ uint16_t sm_mask[TPR];
+  __shared__ uint16_t sm_cell[TPR];
+  __shared__ uint32_t sm_own[TPR * 8];          // ownership masks of the fine cells
+  __shared__ int32_t sm_gs[TPR * 8 * NSLOT];    // their global slot starts (-1: none)
   __shared__ uint16_t s_so[N3];                // per local node: entity slot | offset << 5
   __shared__ uint16_t s_e3[8 * N3];            // child q, node n -> position in the 2k+1 lattice
   extern __shared__ __align__(16) unsigned char smem[];
   CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem);
   T* cb = reinterpret_cast<T*>(smem + (size_t)A.tc * sizeof(CellMeta));
-  T* e1 = cb + TP * N3;
-  T* e2 = e1 + TP * S1;
-  T* e3 = e2 + TP * S2;
-  T* ys = e3 + TP * M3;
+  T* e2 = cb + TPR * N3;
+  T* e3 = e2 + TPR * S2;
+  T* e1 = e3;  // e3 is dead once the z sweep has read it
+  T* ys = e3 + TPR * M3;
   const TileInfo ti = A.tiles[blockIdx.x];
   const int nc = ti.n_cells;
   {
@@ -282,8 +283,8 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
     }
     s_e3[i] = (uint16_t)(((q & 1) * K + a) + M * ((((q >> 1) & 1) * K + b) + M * ((q >> 2) * K + c)));
   }
-  for (int c0 = 0; c0 < nc; c0 += TP) {
-    const int np = min(TP, nc - c0);
+  for (int c0 = 0; c0 < nc; c0 += TPR) {
+    const int np = min(TPR, nc - c0);
     __syncthreads();
     for (int j = threadIdx.x; j < np; j += blockDim.x) {
       const int cell = A.perm[ti.cell_begin + c0 + j];
@@ -331,16 +332,16 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
           if ((sm_own[j * 8 + q] >> slot) & 1u) {
             val[u] = A.src[sm_gs[(j * 8 + q) * NSLOT + slot] + (so >> 5)];
             // refined: position in the children's 2k+1 lattice; else the
-            // identity category (marked by the offset TP M3): into cb
-            dst[u] = sm_ref[j] ? j * M3 + s_e3[r] : TP * M3 + j * N3 + n;
+            // identity category (marked by the offset TPR M3): into cb
+            dst[u] = sm_ref[j] ? j * M3 + s_e3[r] : TPR * M3 + j * N3 + n;
           }
         }
       }
 #pragma unroll
       for (int u = 0; u < RG; ++u) {
         if (dst[u] < 0) continue;
-        if (dst[u] >= TP * M3)
-          cb[dst[u] - TP * M3] = val[u];
+        if (dst[u] >= TPR * M3)
+          cb[dst[u] - TPR * M3] = val[u];
         else
           e3[dst[u]] = val[u];
       }
@@ -482,7 +483,7 @@ void set_smem(K_ kernel, size_t bytes) {
 template <int K, typename T>
 void prolong_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
   constexpr int N = K + 1, M = 2 * K + 1;
-  const size_t sm = (size_t)TP * (N * N * N + M * N * N + M * M * N + M * M * M) * sizeof(T);
+  const size_t sm = (size_t)TP * (N * N * N + M * M * N + M * M * M) * sizeof(T);  // cb, e2, e3 (= e1)
   set_smem(prolong_h<K, T>, sm);
   TArgs<T> A = targs<T>(L);
   A.src = src;
@@ -495,7 +496,7 @@ template <int K, typename T>
 void restrict_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
   constexpr int N = K + 1, M = 2 * K + 1;
   const size_t sm = (size_t)L.coarse.tc * sizeof(CellMeta) +
-                    ((size_t)TP * (N * N * N + M * N * N + M * M * N + M * M * M) + L.coarse.max_local) * sizeof(T);
+                    ((size_t)TPR * (N * N * N + M * M * N + M * M * M) + L.coarse.max_local) * sizeof(T);
   set_smem(restrict_h<K, T>, sm);
   TArgs<T> A = targs<T>(L);
   A.src = src;
