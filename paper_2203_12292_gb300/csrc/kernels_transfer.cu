@@ -24,8 +24,7 @@ GCMG_DEFINE_UPLOAD(upload_tables_transfer)
 
 namespace {
 
-constexpr int TP = 8;   // coarse cells expanded at a time (prolongation, p-transfer)
-constexpr int TPR = 4;  // the same for the h-restriction: 5 instead of 3 CTAs per SM at k = 4
+constexpr int TP = 8;  // coarse cells expanded at a time
 
 template <int KT, int WHICH, typename T>
 __device__ __forceinline__ T pm(int i, int a) {
@@ -245,26 +244,29 @@ __device__ __forceinline__ void restrict_write(const TArgs<T>& A, const TileInfo
   for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) A.halo[hp[i]] = ys[ti.n_owned + i];
 }
 
-template <int K, typename T>
+// TPC coarse cells are expanded at a time: 8, or 4 on levels with many tiles
+// (at k = 4, 5 instead of 3 CTAs per SM; on levels of one or two waves the
+// longer chain of chunks per tile costs more than the occupancy gains)
+template <int K, typename T, int TPC>
 __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
   pdl_begin();
   constexpr int N = K + 1, N3 = N * N * N, M = 2 * K + 1, M3 = M * M * M;
   constexpr int S1 = M * N * N, S2 = M * M * N;
-  __shared__ uint8_t sm_ref[TPR];
-  __shared__ int32_t sm_fine[TPR];
-  __shared__ uint16_t sm_mask[TPR];
-  __shared__ uint16_t sm_cell[TPR];
-  __shared__ uint32_t sm_own[TPR * 8];          // ownership masks of the fine cells
-  __shared__ int32_t sm_gs[TPR * 8 * NSLOT];    // their global slot starts (-1: none)
+  __shared__ uint8_t sm_ref[TPC];
+  __shared__ int32_t sm_fine[TPC];
+  __shared__ uint16_t sm_mask[TPC];
+  __shared__ uint16_t sm_cell[TPC];
+  __shared__ uint32_t sm_own[TPC * 8];          // ownership masks of the fine cells
+  __shared__ int32_t sm_gs[TPC * 8 * NSLOT];    // their global slot starts (-1: none)
   __shared__ uint16_t s_so[N3];                // per local node: entity slot | offset << 5
   __shared__ uint16_t s_e3[8 * N3];            // child q, node n -> position in the 2k+1 lattice
   extern __shared__ __align__(16) unsigned char smem[];
   CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem);
   T* cb = reinterpret_cast<T*>(smem + (size_t)A.tc * sizeof(CellMeta));
-  T* e2 = cb + TPR * N3;
-  T* e3 = e2 + TPR * S2;
+  T* e2 = cb + TPC * N3;
+  T* e3 = e2 + TPC * S2;
   T* e1 = e3;  // e3 is dead once the z sweep has read it
-  T* ys = e3 + TPR * M3;
+  T* ys = e3 + TPC * M3;
   const TileInfo ti = A.tiles[blockIdx.x];
   const int nc = ti.n_cells;
   {
@@ -283,8 +285,8 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
     }
     s_e3[i] = (uint16_t)(((q & 1) * K + a) + M * ((((q >> 1) & 1) * K + b) + M * ((q >> 2) * K + c)));
   }
-  for (int c0 = 0; c0 < nc; c0 += TPR) {
-    const int np = min(TPR, nc - c0);
+  for (int c0 = 0; c0 < nc; c0 += TPC) {
+    const int np = min(TPC, nc - c0);
     __syncthreads();
     for (int j = threadIdx.x; j < np; j += blockDim.x) {
       const int cell = A.perm[ti.cell_begin + c0 + j];
@@ -332,16 +334,16 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
           if ((sm_own[j * 8 + q] >> slot) & 1u) {
             val[u] = A.src[sm_gs[(j * 8 + q) * NSLOT + slot] + (so >> 5)];
             // refined: position in the children's 2k+1 lattice; else the
-            // identity category (marked by the offset TPR M3): into cb
-            dst[u] = sm_ref[j] ? j * M3 + s_e3[r] : TPR * M3 + j * N3 + n;
+            // identity category (marked by the offset TPC M3): into cb
+            dst[u] = sm_ref[j] ? j * M3 + s_e3[r] : TPC * M3 + j * N3 + n;
           }
         }
       }
 #pragma unroll
       for (int u = 0; u < RG; ++u) {
         if (dst[u] < 0) continue;
-        if (dst[u] >= TPR * M3)
-          cb[dst[u] - TPR * M3] = val[u];
+        if (dst[u] >= TPC * M3)
+          cb[dst[u] - TPC * M3] = val[u];
         else
           e3[dst[u]] = val[u];
       }
@@ -492,16 +494,35 @@ void prolong_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s
   { launch_pdl(prolong_h<K, T>, nb, BLOCK, sm, s, A); note_launches(1); }
 }
 
-template <int K, typename T>
-void restrict_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
+template <int K, typename T, int TPC>
+void restrict_h_launch(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
   constexpr int N = K + 1, M = 2 * K + 1;
   const size_t sm = (size_t)L.coarse.tc * sizeof(CellMeta) +
-                    ((size_t)TPR * (N * N * N + M * M * N + M * M * M) + L.coarse.max_local) * sizeof(T);
-  set_smem(restrict_h<K, T>, sm);
+                    ((size_t)TPC * (N * N * N + M * M * N + M * M * M) + L.coarse.max_local) * sizeof(T);
+  set_smem(restrict_h<K, T, TPC>, sm);
   TArgs<T> A = targs<T>(L);
   A.src = src;
   A.dst = dst;
-  { launch_pdl(restrict_h<K, T>, L.coarse.n_tiles, BLOCK, sm, s, A); note_launches(1); }
+  launch_pdl(restrict_h<K, T, TPC>, L.coarse.n_tiles, BLOCK, sm, s, A);
+  note_launches(1);
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int d = 0;
+    cudaGetDevice(&d);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+  }
+  return n;
+}
+
+template <int K, typename T>
+void restrict_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
+  if (L.coarse.n_tiles > 4 * sm_count())
+    restrict_h_launch<K, T, 4>(L, src, dst, s);
+  else
+    restrict_h_launch<K, T, TP>(L, src, dst, s);
   launch_halo_add(L.coarse, sizeof(T) == 8, dst, s);
 }
 
