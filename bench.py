@@ -99,7 +99,7 @@ class ClockSampler:
     """nvidia-smi samples of the SM clock and throttle reasons during the
     timed region (read only)."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -111,11 +111,14 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.5)  # nvidia-smi is up and sampling before the timed region starts
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0: float, t1: float):
+        """Samples stamped within [t0, t1] (host epoch seconds, the timed
+        region) widened by one sampling interval; without any, the nearest."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -124,22 +127,34 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], None, set()
+        return self.parse(out, t0, t1)
+
+    @staticmethod
+    def parse(out: str, t0: float, t1: float, interval: float = 0.05):
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx = float(parts[1])
+                day, frac = parts[0].rsplit(".", 1) if "." in parts[0] else (parts[0], "0")
+                ts = time.mktime(time.strptime(day, "%Y/%m/%d %H:%M:%S")) + float("0." + frac)
+            except ValueError:
+                ts = None  # an unknown stamp format: the sample counts as inside
+            try:
+                rows.append((ts, float(parts[1]), float(parts[2]),
+                             [nm for nm, v in zip(names, parts[5:9]) if v.lower() == "active"]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        inside = [r for r in rows if r[0] is None or t0 - interval <= r[0] <= t1 + interval]
+        if not inside and rows:
+            mid = 0.5 * (t0 + t1)
+            inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+        sm = [r[1] for r in inside]
+        reasons = sorted({nm for r in inside for nm in r[3]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": inside[-1][2] if inside else None,
+                "reasons": reasons, "samples": len(inside), "samples_total": len(rows)}
 
 
 def run_reference(args, rank):
@@ -321,6 +336,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_region0 = time.time()
     e0.record(stream)
     iters = []
     for _ in range(args.steps):
@@ -328,8 +344,9 @@ def main():
         iters.append(st.iterations)
     e1.record(stream)
     torch.cuda.synchronize()
+    t_region1 = time.time()
     barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_region0, t_region1)
     launches = g.launch_count() - launches0
     ms_total = e0.elapsed_time(e1)
     if dist is not None:
