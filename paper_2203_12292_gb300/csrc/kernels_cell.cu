@@ -562,14 +562,16 @@ __global__ void __launch_bounds__(NT) cell_kernel(CellArgs<T> A) {
 // registers; the tile's metadata and DoFs arrive by asynchronous copies that
 // are all in flight together; the hanging-node passes do no work for tiles
 // without hanging cells; the accumulation runs sub-colour by sub-colour, each
-// sub-colour a contiguous range of the permuted cell list.
+// sub-colour a contiguous range of the permuted cell list.  LPT, the lines
+// per thread, covers the level's largest tile (the small tiles of the coarse
+// levels run with LPT = 1: a shorter kernel for a launch that is one chain of
+// latencies).
 // ---------------------------------------------------------------------------
-template <int K, typename T>
+template <int K, typename T, int LPT>
 __global__ void __launch_bounds__(BLOCK) vmult_lines(CellArgs<T> A) {
   static_assert(sizeof(T) == 4, "the fp64 operator is vmult_lines_df");
   pdl_begin();
   constexpr int N = K + 1, N2 = N * N, N3 = N2 * N;
-  constexpr int LPT = (CHUNK * N2 + BLOCK - 1) / BLOCK;  // lines per thread
   extern __shared__ __align__(16) unsigned char smem[];
   const SmemLayout SL = smem_layout<T>(N3, A.tc, A.max_local);
   CellMeta* sm_meta = reinterpret_cast<CellMeta*>(smem + SL.meta);
@@ -1417,6 +1419,25 @@ void ensure_smem(KERN kernel, size_t bytes) {
   if (bytes > 40 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// the fp32 line kernel with enough lines per thread for the level's tiles of
+// at most L.tc cells
+template <int K>
+void launch_lines_f32(const CellLaunch& L, int n_tiles, size_t sm, cudaStream_t s, const CellArgs<float>& A) {
+  constexpr int N2 = (K + 1) * (K + 1);
+  constexpr int LMAX = (CHUNK * N2 + BLOCK - 1) / BLOCK;
+  const int lpt = (L.tc * N2 + BLOCK - 1) / BLOCK;
+  if (lpt <= 1) {
+    ensure_smem(vmult_lines<K, float, 1>, sm);
+    launch_pdl(vmult_lines<K, float, 1>, n_tiles, BLOCK, sm, s, A);
+  } else if (lpt <= 2 && LMAX > 2) {
+    ensure_smem(vmult_lines<K, float, (LMAX > 2 ? 2 : LMAX)>, sm);
+    launch_pdl(vmult_lines<K, float, (LMAX > 2 ? 2 : LMAX)>, n_tiles, BLOCK, sm, s, A);
+  } else {
+    ensure_smem(vmult_lines<K, float, LMAX>, sm);
+    launch_pdl(vmult_lines<K, float, LMAX>, n_tiles, BLOCK, sm, s, A);
+  }
+}
+
 template <typename T>
 void run_halo(const CellLaunch& L, T* dst, cudaStream_t s) {
   if (L.n_halo == 0) return;
@@ -1468,8 +1489,7 @@ void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
     if (L.tc <= CHUNK && L.threads == BLOCK) {
       // vmult_lines keeps one tile-DoF buffer (input, then accumulator) plus K-1 <= 4 zero slots
       const size_t sm1 = sm - (size_t)L.max_local * sizeof(T) + 16;
-      ensure_smem(vmult_lines<K, T>, sm1);
-      launch_pdl(vmult_lines<K, T>, L.n_tiles, BLOCK, sm1, s, A);
+      launch_lines_f32<K>(L, L.n_tiles, sm1, s, A);
       note_launches(1);
       run_halo<T>(L, A.dst, s);
       return;
@@ -1593,10 +1613,10 @@ void launch_vmult_tiles(const CellLaunch& L, bool fp64, const void* src, void* d
     A.tile0 = t0;
     const size_t sm = smem_layout<float>(n3, L.tc, L.max_local).total - (size_t)L.max_local * sizeof(float) + 16;
     switch (L.k) {
-      case 1: ensure_smem(vmult_lines<1, float>, sm); launch_pdl(vmult_lines<1, float>, t1 - t0, BLOCK, sm, s, A); break;
-      case 2: ensure_smem(vmult_lines<2, float>, sm); launch_pdl(vmult_lines<2, float>, t1 - t0, BLOCK, sm, s, A); break;
-      case 3: ensure_smem(vmult_lines<3, float>, sm); launch_pdl(vmult_lines<3, float>, t1 - t0, BLOCK, sm, s, A); break;
-      case 4: ensure_smem(vmult_lines<4, float>, sm); launch_pdl(vmult_lines<4, float>, t1 - t0, BLOCK, sm, s, A); break;
+      case 1: launch_lines_f32<1>(L, t1 - t0, sm, s, A); break;
+      case 2: launch_lines_f32<2>(L, t1 - t0, sm, s, A); break;
+      case 3: launch_lines_f32<3>(L, t1 - t0, sm, s, A); break;
+      case 4: launch_lines_f32<4>(L, t1 - t0, sm, s, A); break;
       default: return;
     }
   }
