@@ -1176,15 +1176,22 @@ int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int m
       if (stats) *stats = st;
       return;
     }
+    // with an fp32 V-cycle (global coarsening) the update of r also writes r in
+    // fp32 into the finest level's right-hand side, and the V-cycle's fp32
+    // output z feeds r.z and p = z + beta p directly: the two casts of the
+    // V-cycle's entry and exit drop out, bit for bit the same values
+    LevelDev& F = *H.lev[top];
+    float* r32 = (F.fp32 && !H.ls) ? F.b.as<float>() : nullptr;
     // operator half of an iteration: q = A p, alpha, x += alpha p, r -= alpha q, r.r
     auto op_half = [&] {
       vmult(H, top, true, p, q, GCMG_STAGE_CG_VMULT);
       const int pr = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);
       launch_dot(p, q, n, H.scratch.as<double>(), S, 0, DOT_ALPHA, H.stream);
-      launch_cg_update_xr(xi, r, p, q, S, n, H.scratch.as<double>(), S, H.stream);
+      launch_cg_update_xr(xi, r, p, q, S, n, H.scratch.as<double>(), S, H.stream, r32);
       prof_end(H, pr);
     };
     const bool flexible = any_learned(H);
+    const bool fused = r32 && !flexible;
     vcycle(H, r, z);
     launch_dot(r, z, n, H.scratch.as<double>(), S, 0, DOT_STORE, s);  // rz
     ck(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
@@ -1215,6 +1222,15 @@ int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int m
         const int pc = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);
         launch_dot(r, z, n, H.scratch.as<double>(), S, 6, DOT_STORE, s);
         prof_end(H, pc);
+      }
+      if (fused) {  // F.b holds r in fp32 (written by the update of r)
+        vcycle_core(H);
+        const float* z32 = F.x.as<float>();
+        const int pz = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);
+        launch_dot(r, z32, n, H.scratch.as<double>(), S, 0, DOT_BETA, s);
+        launch_cg_update_p(p, z32, S, n, s);
+        prof_end(H, pz);
+        continue;
       }
       vcycle(H, r, z);
       const int pz = prof_begin(H, top, GCMG_STAGE_CG_VECTOR);

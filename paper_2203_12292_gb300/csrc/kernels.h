@@ -138,15 +138,20 @@ constexpr int DOT_BLOCKS = 304;
 enum DotOp { DOT_STORE = 0, DOT_ALPHA = 1, DOT_BETA = 2, DOT_BETA_FLEX = 3 };
 void launch_dot(const double* x, const double* y, int64_t n, double* scratch, double* scal, int slot, int op,
                 cudaStream_t s);
+// the same with y in fp32 (widened exactly: equal to the sums over an fp64 copy of y)
+void launch_dot(const double* x, const float* y, int64_t n, double* scratch, double* scal, int slot, int op,
+                cudaStream_t s);
 // inner product with the partial sums in a fixed device array (no allocation);
 // n <= dot_noalloc_max_n()
 int64_t dot_noalloc_max_n();
 cudaError_t launch_dot_noalloc(const double* x, const double* y, int64_t n, double* result, cudaStream_t s);
 // CG updates with device scalars: scal[0] = rz, [1] = pq, [2] = rr, [3] = alpha, [4] = beta, [5] = rz_new,
 // [6] = r_{k+1}.z_k of flexible CG
+// r32 != null: r is also written rounded to fp32 (the fp32 V-cycle's right-hand side)
 void launch_cg_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, int64_t n,
-                         double* scratch, double* scal_out, cudaStream_t s);
+                         double* scratch, double* scal_out, cudaStream_t s, float* r32 = nullptr);
 void launch_cg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t s);
+void launch_cg_update_p(double* p, const float* z, const double* scal, int64_t n, cudaStream_t s);
 // CG inside a graph: scal[7] = |b|^2, scal[8] = iterations; the check kernel
 // counts an iteration and sets the while-node condition h; the stats kernel
 // writes (iterations, rr, |b|^2, status) to out

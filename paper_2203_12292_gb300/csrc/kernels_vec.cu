@@ -195,8 +195,10 @@ __device__ __forceinline__ double block_sum_rb(double v, double* sh) {
 }
 
 // each block sums a fixed contiguous chunk in a fixed order: the result does
-// not depend on scheduling
-__global__ void __launch_bounds__(RB, 2) dot_partial(const double* x, const double* y, int64_t n, double* part) {
+// not depend on scheduling (y in fp32: the fp32 V-cycle's output, widened
+// exactly, so the sums equal those over its fp64 copy)
+template <typename TY>
+__global__ void __launch_bounds__(RB, 2) dot_partial(const double* x, const TY* y, int64_t n, double* part) {
   pdl_begin();
   __shared__ double sh[RB];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -205,9 +207,9 @@ __global__ void __launch_bounds__(RB, 2) dot_partial(const double* x, const doub
   int64_t i = i0 + threadIdx.x;
   for (; i + (RU - 1) * RB < i1; i += RU * RB) {
 #pragma unroll
-    for (int u = 0; u < RU; ++u) s[u] += x[i + u * RB] * y[i + u * RB];
+    for (int u = 0; u < RU; ++u) s[u] += x[i + u * RB] * (double)y[i + u * RB];
   }
-  for (; i < i1; i += RB) s[0] += x[i] * y[i];
+  for (; i < i1; i += RB) s[0] += x[i] * (double)y[i];
   const double v = block_sum_rb((s[0] + s[1]) + (s[2] + s[3]), sh);
   if (threadIdx.x == 0) part[blockIdx.x] = v;
 }
@@ -237,11 +239,13 @@ __global__ void __launch_bounds__(BLOCK) dot_final(const double* part, int np, d
 }
 
 // x += alpha p, r -= alpha q, partial sums of r.r: DOT_BLOCKS blocks of XB
-// threads, XU elements per thread in flight
+// threads, XU elements per thread in flight; CAST: r also rounded to fp32
+// into r32 (the fp32 V-cycle's right-hand side)
 constexpr int XB = 512, XU = 4;
 
+template <bool CAST>
 __global__ void __launch_bounds__(XB, 2) cg_xr_kernel(double* x, double* r, const double* p, const double* q,
-                                                      const double* scal, int64_t n, double* part) {
+                                                      const double* scal, int64_t n, double* part, float* r32) {
   pdl_begin();
   __shared__ double sh[XB];
   const double alpha = scal[3];
@@ -263,6 +267,7 @@ __global__ void __launch_bounds__(XB, 2) cg_xr_kernel(double* x, double* r, cons
       x[i + u * XB] = xv[u] + alpha * pv[u];
       const double ri = rv[u] - alpha * qv[u];
       r[i + u * XB] = ri;
+      if (CAST) r32[i + u * XB] = (float)ri;
       s[u] += ri * ri;
     }
   }
@@ -270,6 +275,7 @@ __global__ void __launch_bounds__(XB, 2) cg_xr_kernel(double* x, double* r, cons
     x[i] += alpha * p[i];
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
+    if (CAST) r32[i] = (float)ri;
     s[0] += ri * ri;
   }
   sh[threadIdx.x] = (s[0] + s[1]) + (s[2] + s[3]);
@@ -281,11 +287,12 @@ __global__ void __launch_bounds__(XB, 2) cg_xr_kernel(double* x, double* r, cons
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-__global__ void cg_p_kernel(double* p, const double* z, const double* scal, int64_t n) {
+template <typename TZ>
+__global__ void cg_p_kernel(double* p, const TZ* z, const double* scal, int64_t n) {
   pdl_begin();
   const double beta = scal[4];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+    p[i] = (double)z[i] + beta * p[i];
 }
 
 __global__ void fill_kernel(double* x, double v, int64_t n) {
@@ -483,13 +490,22 @@ void launch_coarse_solve(bool fp64, const double* Ainv, int n, const void* b, vo
 
 void launch_dot(const double* x, const double* y, int64_t n, double* scratch, double* scal, int slot, int op,
                 cudaStream_t s) {
-  { launch_pdl(dot_partial, DOT_BLOCKS, RB, 0, s, x, y, n, scratch); note_launches(1); }
+  { launch_pdl(dot_partial<double>, DOT_BLOCKS, RB, 0, s, x, y, n, scratch); note_launches(1); }
+  { launch_pdl(dot_final, 1, BLOCK, 0, s, scratch, DOT_BLOCKS, scal, slot, op); note_launches(1); }
+}
+
+void launch_dot(const double* x, const float* y, int64_t n, double* scratch, double* scal, int slot, int op,
+                cudaStream_t s) {
+  { launch_pdl(dot_partial<float>, DOT_BLOCKS, RB, 0, s, x, y, n, scratch); note_launches(1); }
   { launch_pdl(dot_final, 1, BLOCK, 0, s, scratch, DOT_BLOCKS, scal, slot, op); note_launches(1); }
 }
 
 void launch_cg_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, int64_t n,
-                         double* scratch, double* scal_out, cudaStream_t s) {
-  { launch_pdl(cg_xr_kernel, DOT_BLOCKS, XB, 0, s, x, r, p, q, scal, n, scratch); note_launches(1); }
+                         double* scratch, double* scal_out, cudaStream_t s, float* r32) {
+  if (r32)
+    { launch_pdl(cg_xr_kernel<true>, DOT_BLOCKS, XB, 0, s, x, r, p, q, scal, n, scratch, r32); note_launches(1); }
+  else
+    { launch_pdl(cg_xr_kernel<false>, DOT_BLOCKS, XB, 0, s, x, r, p, q, scal, n, scratch, r32); note_launches(1); }
   { launch_pdl(dot_final, 1, BLOCK, 0, s, scratch, DOT_BLOCKS, scal_out, 2, DOT_STORE); note_launches(1); }
 }
 
@@ -566,7 +582,12 @@ cudaError_t launch_dot_noalloc(const double* x, const double* y, int64_t n, doub
 
 void launch_cg_update_p(double* p, const double* z, const double* scal, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
-  { launch_pdl(cg_p_kernel, grid_for(n), BLOCK, 0, s, p, z, scal, n); note_launches(1); }
+  { launch_pdl(cg_p_kernel<double>, grid_for(n), BLOCK, 0, s, p, z, scal, n); note_launches(1); }
+}
+
+void launch_cg_update_p(double* p, const float* z, const double* scal, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  { launch_pdl(cg_p_kernel<float>, grid_for(n), BLOCK, 0, s, p, z, scal, n); note_launches(1); }
 }
 
 void launch_cg_check(cudaGraphConditionalHandle h, double* scal, int maxit, double rtol2, cudaStream_t s) {
