@@ -260,6 +260,17 @@ def test_single_cell_q1_has_no_dofs(gcmg):
     assert st.iterations == 0
 
 
+@pytest.mark.parametrize("fp32", [False, True], ids=["mg64", "mg32"])
+def test_zero_right_hand_side(gcmg, fp32):
+    """b = 0: no iteration, x = 0 whatever it held"""
+    mg = gcmg.Multigrid(gcmg.Mesh.from_recipe(synth.octant(3)), 2, mg_fp32=fp32)
+    b = torch.zeros(mg.n_free(mg.finest), dtype=torch.float64, device="cuda")
+    x = torch.full_like(b, 3.0)
+    st = mg.cg_solve(b, x, 1e-8, 10)
+    assert st.status == 0 and st.iterations == 0
+    assert torch.count_nonzero(x) == 0
+
+
 @pytest.mark.parametrize("n", [1, 255, 1000, 304 * 256 + 17, 3_000_001])
 def test_dot_fp64(gcmg, n):
     mg = gcmg.Multigrid(gcmg.Mesh(0.0, 1.0, [(0,)]), 2)
