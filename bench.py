@@ -58,7 +58,7 @@ METRIC = "fine-level vmult GDoF/s; solve time to 1e-8 rel. res., mixed/learned v
 # workload, per free DoF)
 BYTES_PER_DOF = {"fp32": 9.8, "fp64": 17.8}
 # DRAM bytes (read + write) of one fine-level fp32 operator application on
-# this workload, both of its launches (tile kernel vmult_lines<4,float>:
+# this workload, both of its launches (tile kernel vmult_lines<4,float,4>:
 # 135.1 MB read + 58.7 MB written; halo pass: 90.4 MB + 3.3 MB), from the
 # ncu capture summarised in profiles/vmult_lines_q4_octant_fp32.md; set to 0
 # (reported as null) when the kernel changes until it is re-captured
@@ -432,7 +432,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": "vmult_lines<4,float> line-parallel tile kernel + halo pass "
+                         "kernel": "vmult_lines<4,float,4> line-parallel tile kernel + halo pass "
                                    "(fine-level fp32 operator, 32-cell tiles)",
                          "peak_kind": peak_kind, "bytes_per_dof": BYTES_PER_DOF["fp32"],
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the tile kernel "
