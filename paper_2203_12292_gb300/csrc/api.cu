@@ -29,10 +29,23 @@ long long launch_counter() { return g_launches.load(); }
 // autotuner's choice for every degree on GB300), halved while the level would
 // give fewer than two tiles per SM (at least 8 cells per tile): small levels
 // are latency-bound and finish sooner with more, shorter tiles
-int tile_cells_for(int configured, size_t n_cells) {
+int tile_cells_for(int configured, size_t n_cells, int n_sm) {
   int tc = configured ? configured : 32;
-  while (tc > 8 && n_cells < (size_t)2 * 152 * tc) tc /= 2;
+  while (tc > 8 && n_cells < (size_t)2 * n_sm * tc) tc /= 2;
   return tc;
+}
+
+// multiprocessors of the current device, queried on every call (no cached
+// process-wide value: host threads and devices may differ); without a usable
+// device the host-only mesh checks assume a GB300 (152 SMs)
+int device_sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      n <= 0) {
+    cudaGetLastError();
+    return 152;
+  }
+  return n;
 }
 
 void check_level(const Handle& h, int level) {
@@ -490,7 +503,7 @@ void check_config(const gcmg_config* cfg) {
   if (cfg->cheb_degree < 1 || !(cfg->smoothing_range > 1.0) || cfg->eig_steps < 1)
     throw Error(GCMG_ERR_ARG, "bad smoother parameters");
   if (cfg->tile_cells < 0 || cfg->tile_cells > 255) throw Error(GCMG_ERR_ARG, "tile_cells must be 0..255");
-  if (cfg->cell_kernel < 0 || cfg->cell_kernel > 2) throw Error(GCMG_ERR_ARG, "cell_kernel must be 0, 1 or 2");
+  if (cfg->cell_kernel < 0 || cfg->cell_kernel > 3) throw Error(GCMG_ERR_ARG, "cell_kernel must be 0, 1, 2 or 3");
   if (cfg->cell_threads != 0 && cfg->cell_threads != 128 && cfg->cell_threads != 256 && cfg->cell_threads != 384 &&
       cfg->cell_threads != 512)
     throw Error(GCMG_ERR_ARG, "cell_threads must be 0, 128, 256, 384 or 512");
@@ -509,6 +522,7 @@ void upload_all_tables() {
   if ((int)done.size() <= dev) done.resize(dev + 1, 0);
   if (done[dev]) return;
   upload_tables_cell();
+  upload_tables_lanes();
   upload_tables_transfer();
   upload_tables_mlp();
   ck(cudaDeviceSynchronize(), "upload tables");
@@ -532,13 +546,13 @@ void setup_numerics(Handle& H) {
     // local smoothing: the smoother sees A_SS only, edge values stay as they are
     if (L.n_edge) launch_zero_at(L.edge_idx.as<int32_t>(), L.n_edge, L.dinv64.as<double>(), L.dinv32.as<float>(), H.stream);
   }
-  ck(cudaGetLastError(), "diagonal");
+  ck_launches("diagonal");
   ck(cudaStreamSynchronize(H.stream), "diagonal");
   setup_coarse(H);
-  ck(cudaGetLastError(), "coarse matrix");
+  ck_launches("coarse matrix");
   for (int l = 1; l <= H.top_mg; ++l) {
     H.lev[l]->lam = H.cfg.eig_safety * estimate_lambda(H, l);
-    ck(cudaGetLastError(), "eigenvalue estimate");
+    ck_launches("eigenvalue estimate");
   }
   H.g_core.reset();
   H.g_a.reset();
@@ -546,6 +560,7 @@ void setup_numerics(Handle& H) {
 
 void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, const gcmg_config& cfg) {
   H.cfg = cfg;
+  H.n_sm = device_sm_count();
   H.ls = cfg.local_smoothing != 0;
   // local smoothing: the refinement levels 0..L of the finest mesh, then the active mesh itself
   std::vector<Octree> ls_meshes;
@@ -571,10 +586,11 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
   for (int l = 0; l < nl; ++l) {
     auto L = std::make_unique<LevelDev>();
     const int k = spec[l].second;
-    const int tc = tile_cells_for(cfg.tile_cells, meshes[spec[l].first].leaves.size());
+    const int tc = tile_cells_for(cfg.tile_cells, meshes[spec[l].first].leaves.size(), H.n_sm);
     build_level(meshes[spec[l].first], k, tc, lmax, L->host);
     L->fp32 = cfg.mg_fp32 != 0;
     L->cl.use_lines = cfg.cell_kernel != 2;
+    L->cl.use_lanes = cfg.cell_kernel == 0 || cfg.cell_kernel == 3;
     L->cl.threads = cfg.cell_threads ? cfg.cell_threads : 256;
     LevelHost& lh = L->host;
     L->tiles.upload(lh.tiles, H.stream);
@@ -587,6 +603,7 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
     L->foreign.upload(lh.foreign, H.stream);
     L->subptr.upload(lh.subptr, H.stream);
     L->perm.upload(lh.perm, H.stream);
+    L->lane_tiles.upload(lh.lane, H.stream);
     std::vector<int32_t> ijk(lh.cells.size() * 3);
     for (size_t c = 0; c < lh.cells.size(); ++c) {
       ijk[3 * c] = lh.cells[c].i;
@@ -610,9 +627,11 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
     c.foreign = L->foreign.as<int32_t>();
     c.subptr = L->subptr.as<uint16_t>();
     c.perm = L->perm.as<uint8_t>();
+    c.lane_tiles = lh.lane.empty() ? nullptr : L->lane_tiles.p;
     c.cell_ijk = L->cell_ijk.as<int32_t>();
     c.k = k;
     c.tc = tc;
+    c.n_sm = H.n_sm;
     c.max_local = lh.max_local;
     c.lo = lh.lo;
     c.dom = lh.hi - lh.lo;
@@ -692,7 +711,7 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
   H.cg_z.alloc(nf * sizeof(double));
   H.cg_x.alloc(nf * sizeof(double));
   ck(cudaStreamSynchronize(H.stream), "setup");
-  ck(cudaGetLastError(), "setup");
+  ck_launches("setup");
 }
 
 }  // namespace gcmg
@@ -749,7 +768,7 @@ int gcmg_mesh_dof_coords(const gcmg_mesh* mesh, int level, int degree, int tile_
     if (degree < 1 || degree > KMAX) throw Error(GCMG_ERR_ARG, "degree must be 1..4");
     if (tile_cells < 0 || tile_cells > 255) throw Error(GCMG_ERR_ARG, "tile_cells must be 0..255");
     LevelHost L;
-    build_level(mesh->levels[level], degree, tile_cells_for(tile_cells, mesh->levels[level].leaves.size()),
+    build_level(mesh->levels[level], degree, tile_cells_for(tile_cells, mesh->levels[level].leaves.size(), device_sm_count()),
                 mesh->lmax, L);
     *n_free = L.n_free;
     if (xyz) std::memcpy(xyz, L.dof_xyz_cache.data(), L.dof_xyz_cache.size() * sizeof(double));
@@ -762,7 +781,7 @@ int gcmg_mesh_check_level(const gcmg_mesh* mesh, int level, int degree, int tile
     if (degree < 1 || degree > KMAX) throw Error(GCMG_ERR_ARG, "degree must be 1..4");
     if (tile_cells < 0 || tile_cells > 255) throw Error(GCMG_ERR_ARG, "tile_cells must be 0..255");
     LevelHost L;
-    build_level(mesh->levels[level], degree, tile_cells_for(tile_cells, mesh->levels[level].leaves.size()),
+    build_level(mesh->levels[level], degree, tile_cells_for(tile_cells, mesh->levels[level].leaves.size(), device_sm_count()),
                 mesh->lmax, L);
     try {
       validate_level(L);
@@ -892,7 +911,7 @@ int gcmg_dot(gcmg_handle* h, const double* x, const double* y, int64_t n, double
       return;
     }
     launch_dot(x, y, n, H.scratch.as<double>(), result, 0, DOT_STORE, H.stream);
-    ck(cudaGetLastError(), "dot");
+    ck_launches("dot");
   });
 }
 
@@ -963,7 +982,7 @@ int gcmg_vmult(gcmg_handle* h, int level, int fp64, const void* src, void* dst) 
     if (h->h.lev[level]->n() == 0) return;
     if (!src || !dst || src == dst) throw Error(GCMG_ERR_ARG, "bad vectors");
     vmult(h->h, level, fp64 != 0, src, dst);
-    ck(cudaGetLastError(), "vmult");
+    ck_launches("vmult");
   });
 }
 
@@ -976,7 +995,7 @@ int gcmg_residual(gcmg_handle* h, int level, int fp64, const void* b, const void
     if (!b || !x || !r || x == r) throw Error(GCMG_ERR_ARG, "bad vectors");
     vmult(h->h, level, fp64 != 0, x, r);
     launch_residual(fp64 != 0, r, b, r, n, h->h.stream);
-    ck(cudaGetLastError(), "residual");
+    ck_launches("residual");
   });
 }
 
@@ -1005,7 +1024,7 @@ int gcmg_vcycle_cgc(gcmg_handle* h, const double* b, double* x) {
       launch_cast(true, F.x.p, x, F.n(), H.stream);
     else
       ck(cudaMemcpyAsync(x, F.x.p, F.n() * sizeof(double), cudaMemcpyDeviceToDevice, H.stream), "copy");
-    ck(cudaGetLastError(), "vcycle");
+    ck_launches("vcycle");
   });
 }
 
@@ -1095,7 +1114,7 @@ int gcmg_smooth(gcmg_handle* h, int level, int fp64, void* x, const void* b, int
       smooth(h->h, level, true, x, b, L.w64a.p, L.w64b.p, L.dinv64.p, zero_init != 0);
     else
       smooth(h->h, level, false, x, b, L.w32a.p, L.w32b.p, L.dinv32.p, zero_init != 0);
-    ck(cudaGetLastError(), "smooth");
+    ck_launches("smooth");
   });
 }
 
@@ -1109,7 +1128,7 @@ int gcmg_prolongate_add(gcmg_handle* h, int fine_level, int fp64, const void* co
     if (!coarse || !fine) throw Error(GCMG_ERR_ARG, "bad vectors");
     if (h->h.lev[fine_level - 1]->n())
       launch_prolongate_add(h->h.tr[fine_level]->tl, fp64 != 0, coarse, fine, h->h.stream);
-    ck(cudaGetLastError(), "prolongate");
+    ck_launches("prolongate");
   });
 }
 
@@ -1123,7 +1142,7 @@ int gcmg_restrict_add(gcmg_handle* h, int fine_level, int fp64, const void* fine
     if (!coarse || !fine) throw Error(GCMG_ERR_ARG, "bad vectors");
     if (h->h.lev[fine_level - 1]->n())
       launch_restrict_add(h->h.tr[fine_level]->tl, fp64 != 0, fine, coarse, h->h.stream);
-    ck(cudaGetLastError(), "restrict");
+    ck_launches("restrict");
   });
 }
 
@@ -1132,7 +1151,7 @@ int gcmg_coarse_solve(gcmg_handle* h, int fp64, const void* b, void* x) {
     if (!h) throw Error(GCMG_ERR_ARG, "null handle");
     if (h->h.n0 && (!b || !x)) throw Error(GCMG_ERR_ARG, "bad vectors");
     if (h->h.n0) launch_coarse_solve(fp64 != 0, h->h.Ainv.as<double>(), h->h.n0, b, x, h->h.stream);
-    ck(cudaGetLastError(), "coarse solve");
+    ck_launches("coarse solve");
   });
 }
 
@@ -1142,7 +1161,7 @@ int gcmg_vcycle(gcmg_handle* h, const double* b, double* x) {
     if (h->h.lev.back()->n() == 0) return;
     if (!b || !x) throw Error(GCMG_ERR_ARG, "bad vectors");
     vcycle(h->h, b, x);
-    ck(cudaGetLastError(), "vcycle");
+    ck_launches("vcycle");
   });
 }
 
@@ -1247,7 +1266,7 @@ int gcmg_cg_solve(gcmg_handle* h, const double* b, double* x, double rtol, int m
     st.rel_residual = std::sqrt(rr) / nb;
     st.status = status;
     ck(cudaStreamSynchronize(s), "cg");
-    ck(cudaGetLastError(), "cg");
+    ck_launches("cg");
     if (stats) *stats = st;
   });
   if (rc != GCMG_OK) return rc;
@@ -1280,7 +1299,7 @@ int gcmg_cell_gather(gcmg_handle* h, int level, const double* x, int64_t n_cells
     if (!x || !out) throw Error(GCMG_ERR_ARG, "bad vectors");
     launch_cell_gather(L.host.k, x, cells, n_cells, L.gstart.as<int32_t>(), L.meta.as<CellMeta>(), out,
                        h->h.stream);
-    ck(cudaGetLastError(), "cell gather");
+    ck_launches("cell gather");
   });
 }
 
@@ -1407,7 +1426,7 @@ int gcmg_set_coefficient(gcmg_handle* h, int values_per_cell, const double* nu) 
       launch_coef_coarsen((int)H.lev[l]->host.cells.size(), T.fine_of.as<int32_t>(), T.refined.as<uint8_t>(),
                           H.lev[l + 1]->coef.as<double>(), H.lev[l]->coef.as<double>(), H.stream);
     }
-    ck(cudaGetLastError(), "coefficient");
+    ck_launches("coefficient");
     setup_numerics(H);
     ck(cudaStreamSynchronize(H.stream), "coefficient");
   });

@@ -8,8 +8,11 @@
 
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 #include <stdexcept>
+#include <unordered_map>
 
+#include "host.h"
 #include "internal.h"
 
 namespace gcmg {
@@ -46,9 +49,59 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Dynamic shared memory above the 48 KB default needs a per-kernel limit
+// (cudaFuncAttributeMaxDynamicSharedMemorySize).  It is raised once per kernel
+// and device, under a lock, to the device's opt-in maximum, and never lowered:
+// every launch, every replay of a captured launch and launches from several
+// host threads then see the same limit whatever level was launched last.
+// Returns cudaErrorInvalidValue for a request above that maximum; a failure is
+// also recorded for the calling entry point (note_launch_error).
+inline cudaError_t smem_allow_impl(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> limit[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess && (dev < 0 || dev >= 64)) e = cudaErrorInvalidDevice;
+  if (e != cudaSuccess) {
+    note_launch_error(e);
+    return e;
+  }
+  size_t lim = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = limit[dev].find(func);
+    if (it == limit[dev].end()) {
+      int optin = 0;
+      cudaFuncAttributes fa{};
+      e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+      const int dyn = optin - (int)fa.sharedSizeBytes;
+      if (e == cudaSuccess && dyn > 0)
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+      if (e != cudaSuccess) {
+        note_launch_error(e);
+        return e;
+      }
+      it = limit[dev].emplace(func, dyn > 0 ? (size_t)dyn : 0).first;
+    }
+    lim = it->second;
+  }
+  if (bytes > lim) {
+    note_launch_error(cudaErrorInvalidValue);
+    return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+template <typename KERN>
+inline cudaError_t smem_allow(KERN kernel, size_t bytes) {
+  return smem_allow_impl(reinterpret_cast<const void*>(kernel), bytes);
+}
+
+// launch with programmatic stream serialisation (see pdl_begin); a rejected
+// launch is returned and recorded for the calling entry point
 template <typename... KArgs, typename... Args>
-inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                       Args... args) {
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -59,7 +112,9 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+  note_launch_error(e);
+  return e;
 }
 
 // a double-float value hi + lo (arithmetic further below)

@@ -16,7 +16,7 @@ namespace gcmg {
 struct LevelDev {
   LevelHost host;
   bool fp32 = true;
-  DevBuf tiles, meta, foreign, subptr, perm, cell_ijk, gstart, own, mask;
+  DevBuf tiles, meta, foreign, subptr, perm, cell_ijk, gstart, own, mask, lane_tiles;
   DevBuf halo, halo_dofs, halo_ptr, halo_src, halo_pos;
   DevBuf diag64, dinv64, dinv32;
   DevBuf x, b, d, t;        // V-cycle vectors in level precision
@@ -86,6 +86,7 @@ struct GraphRec {
 
 struct Handle {
   cudaStream_t stream = nullptr;
+  int n_sm = 152;               // multiprocessors of the handle's device (set-up)
   bool stop_after_cgc = false;  // finest level: return after the prolongation
   bool ls = false;              // local smoothing: lev[0..top_mg] refinement levels, lev.back() the active mesh
   int top_mg = 0;               // finest multigrid level (lev.size() - 1 for global coarsening)

@@ -29,6 +29,24 @@ inline void ck(cudaError_t e, const char* what) {
   }
 }
 
+// first failed kernel launch (or launch-attribute call) of this host thread
+// that no check has reported yet; the launch helpers record it, every entry
+// point reports it
+inline thread_local cudaError_t g_launch_err = cudaSuccess;
+inline void note_launch_error(cudaError_t e) {
+  if (e != cudaSuccess && g_launch_err == cudaSuccess) g_launch_err = e;
+}
+// throw for a recorded launch failure or a pending CUDA error of this thread
+inline void ck_launches(const char* what) {
+  const cudaError_t e = g_launch_err;
+  g_launch_err = cudaSuccess;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(GCMG_ERR_CUDA, std::string(what) + ": kernel launch failed: " + cudaGetErrorString(e));
+  }
+  ck(cudaGetLastError(), what);
+}
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -58,8 +76,10 @@ struct DevBuf {
 // run f, turn exceptions into GCMG_ERR_* codes and the thread's message
 template <typename F>
 int guarded(F&& f) {
+  g_launch_err = cudaSuccess;
   try {
     f();
+    if (g_launch_err != cudaSuccess) ck_launches("launch");
     return GCMG_OK;
   } catch (const Error& e) {
     g_err = e.what();

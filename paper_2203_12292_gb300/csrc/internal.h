@@ -38,6 +38,21 @@ struct CellMeta {
 };
 static_assert(sizeof(CellMeta) == 64, "CellMeta must be 64 bytes");
 
+// per-tile metadata of the lane-per-cell fp32 operator (one lane per cell of
+// a tile of at most 32 cells, Morton order): the tile-local entity starts
+// transposed (slot s of the cell in lane j at ls[s][j]) so that a warp reads
+// them conflict-free; absent slots (Dirichlet entities, lanes without a
+// cell) point to LANE_ZERO zero values after the tile's DoFs
+constexpr int LANE_ZERO = 32;
+struct LaneTile {
+  uint16_t ls[NSLOT][32];
+  uint16_t mask[32];
+  uint8_t level[32];
+  uint8_t hang;  // 1: a cell of the tile has a hanging face or edge
+  uint8_t pad[31];
+};
+static_assert(sizeof(LaneTile) % 64 == 0, "LaneTile is copied in 16-byte pieces");
+
 struct TileInfo {
   int32_t cell_begin;
   int32_t n_cells;
@@ -123,6 +138,7 @@ struct LevelHost {
   std::vector<int32_t> halo_src;   // foreign-slot indices (positions in `foreign`)
   std::vector<int32_t> halo_pos;   // per foreign slot: its position in the DoF-ordered halo buffer
   int max_local = 0;               // max tile-local DoF count
+  std::vector<LaneTile> lane;      // per tile (tiles of at most 32 cells): lane-per-cell metadata
   int max_sub = 0;
   // dof coordinates (host) for checks
   std::vector<double> dof_xyz_cache;

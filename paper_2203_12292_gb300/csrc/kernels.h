@@ -35,6 +35,9 @@ struct CellLaunch {
   int max_local;
   int use_lines;  // 1: fp32 operator with the line-parallel kernel
   int threads;    // threads per CTA of the line-parallel operator kernel (128, 256, 384 or 512)
+  int n_sm;       // multiprocessors of the device (grid sizes, chunk choices)
+  int use_lanes;  // 1: fp32 operator with the lane-per-cell kernel (tiles of at most 32 cells)
+  const void* lane_tiles;  // per tile LaneTile (null: level without them)
   double lo, dom;
   const double* coef;  // per cell coefficient nu_e (element matrix nu_e h A_ref); null: 1
   int geom;            // 0: Cartesian cells; GEOM_WARP: the cells mapped by the warp below
@@ -64,6 +67,11 @@ void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, in
 // arrives in DoF order.  vmult_tiles_ok: the level's kernels allow it.
 bool vmult_tiles_ok(const CellLaunch& L, bool fp64);
 void launch_vmult_tiles(const CellLaunch& L, bool fp64, const void* src, void* dst, int t0, int t1, cudaStream_t s);
+// the lane-per-cell fp32 operator (tile kernel only, tiles [t0, t1)); lanes_ok:
+// the level has its metadata (tiles of at most 32 cells, Cartesian cells)
+bool lanes_ok(const CellLaunch& L);
+void launch_vmult_lanes(const CellLaunch& L, const void* src, void* dst, int add, int t0, int t1, cudaStream_t s);
+void upload_tables_lanes();
 // dst = C^T F: Gauss quadrature of f against the basis (FOURIER, ONE: f
 // itself; GAUSSIAN, POLYNOMIAL: f = -Lap u of the manufactured solution u)
 void launch_rhs(const CellLaunch& L, const RhsDesc& f, double* dst, cudaStream_t s);

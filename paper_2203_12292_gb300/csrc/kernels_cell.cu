@@ -1414,9 +1414,7 @@ __global__ void __launch_bounds__(BLOCK) diag_table_kernel(double* out, int tc) 
 
 template <typename KERN>
 void ensure_smem(KERN kernel, size_t bytes) {
-  // the 48 KB default limit covers static plus dynamic shared memory; the
-  // kernels here hold at most 8 KB of static shared memory
-  if (bytes > 40 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  smem_allow(kernel, bytes);
 }
 
 // the fp32 line kernel with enough lines per thread for the level's tiles of
@@ -1441,7 +1439,7 @@ void launch_lines_f32(const CellLaunch& L, int n_tiles, size_t sm, cudaStream_t 
 template <typename T>
 void run_halo(const CellLaunch& L, T* dst, cudaStream_t s) {
   if (L.n_halo == 0) return;
-  const int nb = std::min((L.n_halo + BLOCK - 1) / BLOCK, 152 * 8);
+  const int nb = std::min((L.n_halo + BLOCK - 1) / BLOCK, std::max(L.n_sm, 1) * 8);
   {
     launch_pdl(halo_add_kernel<T>, nb, BLOCK, 0, s, dst, static_cast<const T*>(L.halo), L.halo_dofs, L.halo_ptr,
                L.n_halo);
@@ -1486,6 +1484,11 @@ void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
     }
   }
   if constexpr (MODE == MODE_VMULT && sizeof(T) == 4) {
+    if (L.use_lanes && lanes_ok(L)) {  // one lane per cell (default)
+      launch_vmult_lanes(L, A.src, A.dst, A.add, 0, L.n_tiles, s);
+      run_halo<T>(L, A.dst, s);
+      return;
+    }
     if (L.tc <= CHUNK && L.threads == BLOCK) {
       // vmult_lines keeps one tile-DoF buffer (input, then accumulator) plus K-1 <= 4 zero slots
       const size_t sm1 = sm - (size_t)L.max_local * sizeof(T) + 16;
@@ -1587,6 +1590,7 @@ void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, in
 }
 
 bool vmult_tiles_ok(const CellLaunch& L, bool fp64) {
+  if (!fp64 && L.use_lanes && lanes_ok(L)) return true;
   return L.tc <= CHUNK && !L.geom && (fp64 || (L.use_lines && L.threads == BLOCK));
 }
 
@@ -1607,6 +1611,10 @@ void launch_vmult_tiles(const CellLaunch& L, bool fp64, const void* src, void* d
       default: return;
     }
   } else {
+    if (L.use_lanes && lanes_ok(L)) {
+      launch_vmult_lanes(L, src, dst, 0, t0, t1, s);
+      return;
+    }
     CellArgs<float> A = make_args<float>(L);
     A.src = static_cast<const float*>(src);
     A.dst = static_cast<float*>(dst);

@@ -1,0 +1,464 @@
+// fp32 tile kernel of the cell loop of Eq. 2 with one lane per cell:
+//   v = sum_e G_e^T C_e^T S_e^T Q_e S_e C_e G_e x
+//
+// A tile holds at most 32 consecutive (Morton-ordered) cells; lane j of every
+// warp works on cell j, and the k+1 warps of the CTA share the (k+1)^2 1D
+// lines of each direction.  All lanes of a warp therefore touch the same
+// local node of 32 different cells at once, so
+//   * the cell buffer is node-major (node n of cell j at n * 32 + j): every
+//     sweep, in every direction, reads and writes 32 consecutive words
+//     (no bank conflicts), and all indexing except the DoF gather/scatter is
+//     uniform across the warp;
+//   * the entity starts of the tile are stored transposed (slot s of cell j
+//     at s * 32 + j), read conflict-free.
+// The sweeps apply the fast-diagonalisation form of the Cartesian cell matrix
+// h (K x M x M + M x K x M + M x M x K) = h B^T(x3) diag(lam_a+lam_b+lam_c) B(x3)
+// with the even-odd split of B (rows of B are symmetric or antisymmetric
+// under x -> 1 - x).
+//
+// Accumulation without atomics and in a fixed order.  Two local nodes of
+// different cells can be the same DoF only if, along every axis, their
+// coordinates are equal or both lie on the cell boundary (0 or k); the same
+// holds through hanging faces and edges, whose slots point to the coarse
+// entity with the same local offsets.  The x-lines (b, c) are grouped into
+// classes by (b or "boundary", c or "boundary"); each class is given to one
+// warp, so two warps never add to the same DoF, and a warp adds in program
+// order.  Within one instruction two lanes add to the same DoF only through
+// hanging slots (siblings behind one coarse face or edge); tiles with hanging
+// cells add such groups one lane after another in lane order.  The sums are
+// therefore reproducible bit for bit.  Tiles without hanging cells fuse the
+// gather with the first x sweep and the last x sweep with the scatter; tiles
+// with hanging cells apply C_e and C_e^T (Sec. 3.2, direction by direction)
+// between separate passes.
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace gcmg {
+
+GCMG_DEFINE_UPLOAD(upload_tables_lanes_1d)
+
+namespace {
+
+constexpr int LW = 8;  // table entries of x-lines per warp
+
+// x-line r = b + N c of degree K: slot of node (0, b, c) | its entity offset << 8 |
+// entity offset of node (1, b, c) in the slot after it << 16; per warp the
+// x-lines it gathers and scatters (-1: none), class-partitioned
+struct LaneLines {
+  uint32_t line[KMAX + 1][NMAX * NMAX];
+  int8_t xw[KMAX + 1][NMAX][LW];
+  int32_t nx[KMAX + 1][NMAX];  // x-lines of each warp
+};
+__constant__ LaneLines c_ll;
+
+struct LaneArgs {
+  const TileInfo* tiles;
+  const LaneTile* lt;
+  const int32_t* foreign;
+  const int32_t* halo_pos;
+  const float* src;
+  float* dst;
+  float* halo;
+  const double* coef;  // per cell nu_e, null: 1
+  double dom;
+  int add;
+  int tile0;
+};
+
+// one direction D of C_e (TRANS: C_e^T) on the lines of warp w: line
+// q = i + N w has the other coordinates (u, v) = (q % N, q / N) in increasing
+// axis order; lane j interpolates when the line lies on a hanging face or edge
+// of its cell
+template <int K, int D, bool TRANS>
+__device__ __forceinline__ void hang_pass(float* cb, uint16_t m, int w, int lane) {
+  constexpr int N = K + 1, N2 = N * N;
+  constexpr int S = (D == 0 ? 1 : (D == 1 ? N : N2)) * 32;
+  const DevTables<float>& tb = tab<float>(K);
+  const int p = (m >> D) & 1;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int q = i + N * w;
+    const int u = q % N, v = q / N;
+    if (!line_hangs<K, D>(m, u, v)) continue;
+    const int base = D == 0 ? N * u + N2 * v : (D == 1 ? u + N2 * v : u + N * v);
+    float* ptr = cb + base * 32 + lane;
+    float x[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) x[a] = ptr[a * S];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      float s = 0.f;
+#pragma unroll
+      for (int a = 0; a < N; ++a)
+        s += (p ? (TRANS ? tb.I[1][a][r] : tb.I[1][r][a]) : (TRANS ? tb.I[0][a][r] : tb.I[0][r][a])) * x[a];
+      ptr[r * S] = s;
+    }
+  }
+}
+
+// C_x (TRANS: C_x^T) on one x-line in registers
+template <int K, bool TRANS>
+__device__ __forceinline__ void hang_x(float* v, int p) {
+  constexpr int N = K + 1;
+  const DevTables<float>& tb = tab<float>(K);
+  float x[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) x[a] = v[a];
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+      s += (p ? (TRANS ? tb.I[1][a][r] : tb.I[1][r][a]) : (TRANS ? tb.I[0][a][r] : tb.I[0][r][a])) * x[a];
+    v[r] = s;
+  }
+}
+
+// 27-bit set of the slots of a cell (mask m) that lie on a hanging face or edge
+__device__ __forceinline__ uint32_t hanging_slot_set(uint16_t m) {
+  if (!(m & MASK_HANG)) return 0u;
+  const int p0 = m & 1, p1 = (m >> 1) & 1, p2 = (m >> 2) & 1;
+  uint32_t hs = 0;
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) {
+    const int c0 = s % 3, c1 = (s / 3) % 3, c2 = s / 9;
+    const bool on0 = c0 == 2 * p0, on1 = c1 == 2 * p1, on2 = c2 == 2 * p2;
+    const bool h = (((m >> 3) & 1) && on0) || (((m >> 4) & 1) && on1) || (((m >> 5) & 1) && on2) ||
+                   (((m >> 6) & 1) && on1 && on2) || (((m >> 7) & 1) && on0 && on2) || (((m >> 8) & 1) && on0 && on1);
+    if (h) hs |= 1u << s;
+  }
+  return hs;
+}
+
+// xs[g] += v where lanes with the same g (siblings behind one hanging face or
+// edge) add one after another in lane order; g >= nloc (absent DoF) adds
+// nothing.  Only lanes whose slot hangs can share g within one instruction:
+// without such a lane (hang_any = 0) the plain addition is exact.
+__device__ __forceinline__ void add_ordered(float* xs, int g, float v, int nloc, int lane, bool hang_any) {
+  if (!hang_any) {
+    xs[g] += v;
+    return;
+  }
+  const bool real = g < nloc;
+  const unsigned peers = __match_any_sync(0xffffffffu, real ? g : -1 - lane);
+  const int rank = __popc(peers & ((1u << lane) - 1u));
+  const int most = __reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
+  for (int q = 0; q < most; ++q) {
+    if (real && rank == q) xs[g] += v;
+    __syncwarp();
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__((K + 1) * 32) vmult_lanes(LaneArgs A) {
+  pdl_begin();
+  constexpr int N = K + 1, N2 = N * N, N3 = N2 * N, NT = N * 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  LaneTile* st = reinterpret_cast<LaneTile*>(smem);
+  float* cb = reinterpret_cast<float*>(smem + sizeof(LaneTile));
+  float* xs = cb + N3 * 32;  // tile DoFs, then the zero region; later the accumulator
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tile = A.tile0 + blockIdx.x;
+  const TileInfo ti = A.tiles[tile];
+  const int nloc = ti.n_owned + ti.n_foreign;
+  {  // asynchronous copies of the lane metadata and the tile's DoFs, all in flight at once
+    const uint4* g = reinterpret_cast<const uint4*>(A.lt + tile);
+    uint4* s = reinterpret_cast<uint4*>(st);
+    for (int i = threadIdx.x; i < (int)(sizeof(LaneTile) / 16); i += NT) cp_async16(s + i, g + i);
+    const float* so = A.src + ti.dof_begin;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < ti.n_owned; i += NT) cp_async(xs + i, so + i);
+    const int32_t* fl = A.foreign + ti.foreign_begin;
+    float* xf = xs + ti.n_owned;
+    for (int i0 = threadIdx.x; i0 < ti.n_foreign; i0 += 4 * NT) {
+      int idx[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) idx[u] = (i0 + u * NT < ti.n_foreign) ? fl[i0 + u * NT] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (idx[u] >= 0) cp_async(xf + i0 + u * NT, A.src + idx[u]);
+    }
+  }
+  if (threadIdx.x < LANE_ZERO) xs[nloc + threadIdx.x] = 0.f;
+  cp_async_wait_all();
+  __syncthreads();
+
+  const DevTables<float>& tb = tab<float>(K);
+  const uint16_t m = st->mask[lane];
+  const bool hang = st->hang != 0;  // uniform over the CTA
+  float h;
+  {
+    const int c = ti.cell_begin + min(lane, ti.n_cells - 1);
+    const double hd = ldexp(A.dom, -(int)st->level[lane]);
+    h = (float)(A.coef ? hd * A.coef[c] : hd);
+  }
+
+  // G_e (+ C_x on hanging x-lines, or the forward x sweep when the tile has no hanging cells)
+  const int nxl = c_ll.nx[K][w];
+#pragma unroll 1
+  for (int i = 0; i < nxl; ++i) {
+    const int r = c_ll.xw[K][w][i];
+    const uint32_t li = c_ll.line[K][r];
+    const int s0 = li & 0xff, o0 = (li >> 8) & 0xff, o1 = li >> 16;
+    const int g0 = st->ls[s0][lane] + o0, g1 = st->ls[s0 + 1][lane] + o1, g2 = st->ls[s0 + 2][lane] + o0;
+    float v[N];
+    v[0] = xs[g0];
+#pragma unroll
+    for (int a = 1; a < K; ++a) v[a] = xs[g1 + a - 1];
+    v[K] = xs[g2];
+    if (!hang)
+      eo_forward<N, 0, 1>(v, tb.Be);
+    else if (line_hangs<K, 0>(m, r % N, r / N))
+      hang_x<K, false>(v, m & 1);
+    float* p = cb + N * r * 32 + lane;
+#pragma unroll
+    for (int a = 0; a < N; ++a) p[a * 32] = v[a];
+  }
+  __syncthreads();
+  if (hang) {  // C_y, C_z, then the forward x sweep
+    hang_pass<K, 1, false>(cb, m, w, lane);
+    __syncthreads();
+    hang_pass<K, 2, false>(cb, m, w, lane);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float* p = cb + N * (i + N * w) * 32 + lane;
+      float v[N];
+#pragma unroll
+      for (int a = 0; a < N; ++a) v[a] = p[a * 32];
+      eo_forward<N, 0, 1>(v, tb.Be);
+#pragma unroll
+      for (int a = 0; a < N; ++a) p[a * 32] = v[a];
+    }
+    __syncthreads();
+  }
+
+  // forward y sweep (lines (a, c) = (i, w)); the tile DoFs are dead: clear the accumulator
+  {
+    float4* z4 = reinterpret_cast<float4*>(xs);
+    for (int i = threadIdx.x; i < (nloc + 3) / 4; i += NT) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float* p = cb + (i + N2 * w) * 32 + lane;
+    float v[N];
+#pragma unroll
+    for (int b = 0; b < N; ++b) v[b] = p[b * N * 32];
+    eo_forward<N, 0, 1>(v, tb.Be);
+#pragma unroll
+    for (int b = 0; b < N; ++b) p[b * N * 32] = v[b];
+  }
+  __syncthreads();
+  // z: forward sweep, h (lam_a + lam_b + lam_c) in mode order, backward sweep (lines (a, b) = (i, w))
+  {
+    const float hb = h * tb.lame[w];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float* p = cb + (i + N * w) * 32 + lane;
+      float v[N];
+#pragma unroll
+      for (int c = 0; c < N; ++c) v[c] = p[c * N2 * 32];
+      eo_forward<N, 0, 1>(v, tb.Be);
+      const float hab = fmaf(h, tb.lame[i], hb);
+#pragma unroll
+      for (int c = 0; c < N; ++c) v[c] *= fmaf(h, tb.lame[c], hab);
+      eo_backward<N, 0, 1>(v, tb.Be);
+#pragma unroll
+      for (int c = 0; c < N; ++c) p[c * N2 * 32] = v[c];
+    }
+  }
+  __syncthreads();
+  // backward y sweep
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float* p = cb + (i + N2 * w) * 32 + lane;
+    float v[N];
+#pragma unroll
+    for (int b = 0; b < N; ++b) v[b] = p[b * N * 32];
+    eo_backward<N, 0, 1>(v, tb.Be);
+#pragma unroll
+    for (int b = 0; b < N; ++b) p[b * N * 32] = v[b];
+  }
+  __syncthreads();
+
+  if (!hang) {
+    // backward x sweep fused with G_e^T: each warp adds its class of x-lines in program order
+#pragma unroll 1
+    for (int i = 0; i < nxl; ++i) {
+      const int r = c_ll.xw[K][w][i];
+      const float* p = cb + N * r * 32 + lane;
+      float v[N];
+#pragma unroll
+      for (int a = 0; a < N; ++a) v[a] = p[a * 32];
+      eo_backward<N, 0, 1>(v, tb.Be);
+      const uint32_t li = c_ll.line[K][r];
+      const int s0 = li & 0xff, o0 = (li >> 8) & 0xff, o1 = li >> 16;
+      const int g0 = st->ls[s0][lane] + o0, g1 = st->ls[s0 + 1][lane] + o1, g2 = st->ls[s0 + 2][lane] + o0;
+      xs[g0] += v[0];
+#pragma unroll
+      for (int a = 1; a < K; ++a) xs[g1 + a - 1] += v[a];
+      xs[g2] += v[K];
+    }
+  } else {
+    // backward x sweep, C_z^T, C_y^T, then C_x^T and G_e^T on the warp's class of x-lines
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      float* p = cb + N * (i + N * w) * 32 + lane;
+      float v[N];
+#pragma unroll
+      for (int a = 0; a < N; ++a) v[a] = p[a * 32];
+      eo_backward<N, 0, 1>(v, tb.Be);
+#pragma unroll
+      for (int a = 0; a < N; ++a) p[a * 32] = v[a];
+    }
+    __syncthreads();
+    hang_pass<K, 2, true>(cb, m, w, lane);
+    __syncthreads();
+    hang_pass<K, 1, true>(cb, m, w, lane);
+    __syncthreads();
+    const uint32_t hs = hanging_slot_set(m);
+#pragma unroll 1
+    for (int i = 0; i < nxl; ++i) {
+      const int r = c_ll.xw[K][w][i];
+      const float* p = cb + N * r * 32 + lane;
+      float v[N];
+#pragma unroll
+      for (int a = 0; a < N; ++a) v[a] = p[a * 32];
+      if (line_hangs<K, 0>(m, r % N, r / N)) hang_x<K, true>(v, m & 1);
+      const uint32_t li = c_ll.line[K][r];
+      const int s0 = li & 0xff, o0 = (li >> 8) & 0xff, o1 = li >> 16;
+      const int g0 = st->ls[s0][lane] + o0, g1 = st->ls[s0 + 1][lane] + o1, g2 = st->ls[s0 + 2][lane] + o0;
+      const bool h0 = __any_sync(0xffffffffu, (hs >> s0) & 1u), h1 = __any_sync(0xffffffffu, (hs >> (s0 + 1)) & 1u),
+                 h2 = __any_sync(0xffffffffu, (hs >> (s0 + 2)) & 1u);
+      add_ordered(xs, g0, v[0], nloc, lane, h0);
+#pragma unroll
+      for (int a = 1; a < K; ++a) add_ordered(xs, g1 + a - 1, v[a], nloc, lane, h1);
+      add_ordered(xs, g2, v[K], nloc, lane, h2);
+    }
+  }
+  __syncthreads();
+  // owned DoFs: plain stores (or additions); foreign DoFs: into their halo slots
+  float* d = A.dst + ti.dof_begin;
+  if (A.add)
+    for (int i = threadIdx.x; i < ti.n_owned; i += NT) d[i] += xs[i];
+  else
+    for (int i = threadIdx.x; i < ti.n_owned; i += NT) d[i] = xs[i];
+  const int32_t* hp = A.halo_pos + ti.foreign_begin;
+  for (int i = threadIdx.x; i < ti.n_foreign; i += NT) A.halo[hp[i]] = xs[ti.n_owned + i];
+}
+
+// host: entity slot and offset of local node (a, b, c) of a degree-k cell
+// (the numbering of the level set-up: slot cx + 3 cy + 9 cz, DoFs of an
+// entity lexicographic over its interior axes)
+void host_node_slot(int k, int a, int b, int c, int& slot, int& off) {
+  const int ca = a == 0 ? 0 : (a == k ? 2 : 1), cbb = b == 0 ? 0 : (b == k ? 2 : 1),
+            cc = c == 0 ? 0 : (c == k ? 2 : 1);
+  slot = ca + 3 * cbb + 9 * cc;
+  int o = 0, mul = 1;
+  if (ca == 1) {
+    o += a - 1;
+    mul *= k - 1;
+  }
+  if (cbb == 1) {
+    o += (b - 1) * mul;
+    mul *= k - 1;
+  }
+  if (cc == 1) o += (c - 1) * mul;
+  off = o;
+}
+
+// x-line tables: slots and offsets per line; the line classes (lines whose
+// nodes can share DoFs between cells) dealt to the k+1 warps, largest class
+// first to the least loaded warp
+void fill_lane_lines(LaneLines& t) {
+  t = LaneLines{};
+  for (int k = 0; k <= KMAX; ++k)
+    for (int w = 0; w < NMAX; ++w)
+      for (int i = 0; i < LW; ++i) t.xw[k][w][i] = -1;
+  for (int k = 1; k <= KMAX; ++k) {
+    const int n = k + 1;
+    for (int c = 0; c < n; ++c)
+      for (int b = 0; b < n; ++b) {
+        int s0, o0, s1, o1 = 0;
+        host_node_slot(k, 0, b, c, s0, o0);
+        if (k > 1) host_node_slot(k, 1, b, c, s1, o1);
+        t.line[k][b + n * c] = (uint32_t)s0 | ((uint32_t)o0 << 8) | ((uint32_t)o1 << 16);
+      }
+    auto cls = [&](int x) { return (x == 0 || x == k) ? -1 : x; };
+    std::map<std::pair<int, int>, std::vector<int>> classes;
+    for (int c = 0; c < n; ++c)
+      for (int b = 0; b < n; ++b) classes[{cls(b), cls(c)}].push_back(b + n * c);
+    std::vector<std::vector<int>> cl;
+    for (auto& kv : classes) cl.push_back(kv.second);
+    std::stable_sort(cl.begin(), cl.end(), [](const std::vector<int>& x, const std::vector<int>& y) {
+      return x.size() > y.size();
+    });
+    std::vector<int> load(n, 0);
+    for (const auto& c : cl) {
+      int w = 0;
+      for (int u = 1; u < n; ++u)
+        if (load[u] < load[w]) w = u;
+      for (int r : c) {
+        if (load[w] >= LW) throw std::runtime_error("lane line table overflow");
+        t.xw[k][w][load[w]++] = (int8_t)r;
+      }
+    }
+    for (int w = 0; w < n; ++w) t.nx[k][w] = load[w];
+  }
+}
+
+template <int K>
+size_t lanes_smem(int max_local) {
+  constexpr int N3 = (K + 1) * (K + 1) * (K + 1);
+  return sizeof(LaneTile) + ((size_t)N3 * 32 + (size_t)max_local + LANE_ZERO + 3) * sizeof(float);
+}
+
+template <int K>
+cudaError_t run_lanes(const CellLaunch& L, const LaneArgs& A, int n_tiles, cudaStream_t s) {
+  const size_t sm = lanes_smem<K>(L.max_local);
+  cudaError_t e = smem_allow(vmult_lanes<K>, sm);
+  if (e != cudaSuccess) return e;
+  e = launch_pdl(vmult_lanes<K>, n_tiles, (K + 1) * 32, sm, s, A);
+  note_launches(1);
+  return e;
+}
+
+}  // namespace
+
+void upload_tables_lanes() {
+  upload_tables_lanes_1d();
+  static LaneLines t;
+  fill_lane_lines(t);
+  cudaMemcpyToSymbol(c_ll, &t, sizeof(t));
+}
+
+bool lanes_ok(const CellLaunch& L) { return L.lane_tiles && L.tc <= 32 && !L.geom && L.k >= 1 && L.k <= KMAX; }
+
+void launch_vmult_lanes(const CellLaunch& L, const void* src, void* dst, int add, int t0, int t1, cudaStream_t s) {
+  if (t1 <= t0 || !lanes_ok(L)) return;
+  LaneArgs A{};
+  A.tiles = L.tiles;
+  A.lt = static_cast<const LaneTile*>(L.lane_tiles);
+  A.foreign = L.foreign;
+  A.halo_pos = L.halo_pos;
+  A.src = static_cast<const float*>(src);
+  A.dst = static_cast<float*>(dst);
+  A.halo = static_cast<float*>(L.halo);
+  A.coef = L.coef;
+  A.dom = L.dom;
+  A.add = add;
+  A.tile0 = t0;
+  switch (L.k) {
+    case 1: run_lanes<1>(L, A, t1 - t0, s); break;
+    case 2: run_lanes<2>(L, A, t1 - t0, s); break;
+    case 3: run_lanes<3>(L, A, t1 - t0, s); break;
+    case 4: run_lanes<4>(L, A, t1 - t0, s); break;
+    default: break;
+  }
+}
+
+}  // namespace gcmg

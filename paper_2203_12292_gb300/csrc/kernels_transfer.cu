@@ -479,7 +479,7 @@ TArgs<T> targs(const TransferLaunch& L) {
 
 template <typename K_>
 void set_smem(K_ kernel, size_t bytes) {
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  smem_allow(kernel, bytes);
 }
 
 template <int K, typename T>
@@ -507,19 +507,9 @@ void restrict_h_launch(const TransferLaunch& L, const T* src, T* dst, cudaStream
   note_launches(1);
 }
 
-int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int d = 0;
-    cudaGetDevice(&d);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
-  }
-  return n;
-}
-
 template <int K, typename T>
 void restrict_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
-  if (L.coarse.n_tiles > 4 * sm_count())
+  if (L.coarse.n_tiles > 4 * L.coarse.n_sm)
     restrict_h_launch<K, T, 4>(L, src, dst, s);
   else
     restrict_h_launch<K, T, TP>(L, src, dst, s);

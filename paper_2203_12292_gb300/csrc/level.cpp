@@ -171,6 +171,10 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
     }
   }
   const int ne = (int)endofs.size();
+  // entity type: number of interior axes (3 interior, 2 face, 1 edge, 0 vertex)
+  auto etype = [&](int32_t e) {
+    return (egeom[e].cls[0] == 1) + (egeom[e].cls[1] == 1) + (egeom[e].cls[2] == 1);
+  };
 
   // Tiles of consecutive cells.  Every entity is owned by the first tile that
   // touches it (Morton order); the DoFs a tile owns are numbered
@@ -203,33 +207,50 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
     T.cell_begin = c0;
     T.n_cells = c1 - c0;
     T.dof_begin = (int32_t)next;
+    // owned entities in first-touch order, then grouped by type (interiors, faces, edges,
+    // vertices): the same slot of consecutive cells then lies a type's DoF count apart
+    // (27, 9, 3 for Q4) instead of about one cell's DoF count (64 for Q4, a multiple of the
+    // 32 shared-memory banks), which spreads the lanes of a warp that gather one node of 32
+    // cells over the banks
+    std::vector<int32_t> ord;
     for (int ci = c0; ci < c1; ++ci)
       for (int s = 0; s < NSLOT; ++s) {
         int32_t e = eid[(size_t)ci * NSLOT + s];
-        if (e >= 0 && owner[e] == t && estart[e] < 0) {
-          estart[e] = (int32_t)next;
-          next += endofs[e];
+        if (e >= 0 && owner[e] == t && estart[e] == -1) {
+          estart[e] = -2;  // listed
+          ord.push_back(e);
         }
       }
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return etype(x) > etype(y); });
+    for (int32_t e : ord) {
+      estart[e] = (int32_t)next;
+      next += endofs[e];
+    }
     if (next > 0x7FFFFFFF) throw std::runtime_error("too many DoFs for 32-bit indices");
     T.n_owned = (int32_t)(next - T.dof_begin);
     // tile-local numbering: owned entities at their offset, foreign ones after
     T.foreign_begin = (int32_t)L.foreign.size();
     int32_t local_next = T.n_owned;
-    std::vector<int32_t> touched;
+    std::vector<int32_t> touched, fgn;
     for (int ci = c0; ci < c1; ++ci)
       for (int s = 0; s < NSLOT; ++s) {
         int32_t e = eid[(size_t)ci * NSLOT + s];
-        if (e < 0 || lstart_of[e] >= 0) continue;
+        if (e < 0 || lstart_of[e] != -1) continue;
         touched.push_back(e);
         if (owner[e] == t) {
           lstart_of[e] = estart[e] - T.dof_begin;
         } else {
-          lstart_of[e] = local_next;
-          local_next += endofs[e];
-          for (int q = 0; q < endofs[e]; ++q) L.foreign.push_back(estart[e] + q);
+          lstart_of[e] = -2;  // listed
+          fgn.push_back(e);
         }
       }
+    // foreign entities: grouped by type as the owned ones
+    std::stable_sort(fgn.begin(), fgn.end(), [&](int32_t x, int32_t y) { return etype(x) > etype(y); });
+    for (int32_t e : fgn) {
+      lstart_of[e] = local_next;
+      local_next += endofs[e];
+      for (int q = 0; q < endofs[e]; ++q) L.foreign.push_back(estart[e] + q);
+    }
     T.n_foreign = local_next - T.n_owned;
     if (local_next >= (int)LS_NONE) throw std::runtime_error("tile too large for 16-bit local indices");
     L.max_local = std::max(L.max_local, (int)local_next);
@@ -282,6 +303,25 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
       cm.sub = (uint8_t)sub[ci - c0];
     }
     for (int32_t e : touched) lstart_of[e] = -1;
+  }
+  // lane-per-cell metadata of tiles of at most 32 cells
+  L.lane.clear();
+  if (tile_cells <= 32) {
+    L.lane.assign(nt, LaneTile{});
+    for (int t = 0; t < nt; ++t) {
+      const TileInfo& T = L.tiles[t];
+      LaneTile& lt = L.lane[t];
+      const uint16_t zero = (uint16_t)(T.n_owned + T.n_foreign);
+      if ((int)zero + LANE_ZERO >= (int)LS_NONE) throw std::runtime_error("tile too large for 16-bit local indices");
+      for (int j = 0; j < 32; ++j) {
+        const bool cell = j < T.n_cells;
+        const CellMeta* cm = cell ? &L.meta[T.cell_begin + j] : nullptr;
+        for (int s = 0; s < NSLOT; ++s) lt.ls[s][j] = (cell && cm->ls[s] != LS_NONE) ? cm->ls[s] : zero;
+        lt.mask[j] = cell ? cm->mask : 0;
+        lt.level[j] = cell ? cm->level : 0;
+        if (cell && (cm->mask & MASK_HANG)) lt.hang = 1;
+      }
+    }
   }
   L.n_free = next;
   for (int e = 0; e < ne; ++e)

@@ -146,7 +146,7 @@ int gcmg_mlp_forward(gcmg_mlp* net, const float* X, int64_t n, float* Y, void* s
       const int64_t rows = std::min(chunk, n - r0);
       N.forward(X + r0 * N.n_in, rows, Y + r0 * N.n_out, s);
     }
-    ck(cudaGetLastError(), "mlp forward");
+    ck_launches("mlp forward");
   });
 }
 
@@ -159,7 +159,7 @@ int gcmg_mlp_gradient(gcmg_mlp* net, const float* X, const float* T, const float
     N.reserve(n);
     N.gradient(X, T, W, (int)n, loss ? loss : N.loss.as<float>(), s);
     ck(cudaMemcpyAsync(grad, N.grad.p, N.n_params * sizeof(float), cudaMemcpyDeviceToDevice, s), "copy");
-    ck(cudaGetLastError(), "mlp gradient");
+    ck_launches("mlp gradient");
   });
 }
 
@@ -182,7 +182,7 @@ int gcmg_mlp_train(gcmg_mlp* net, const float* X, const float* T, const float* W
                  losses ? losses + st : N.loss.as<float>(), s);
       N.adam(lr, s);
     }
-    ck(cudaGetLastError(), "mlp train");
+    ck_launches("mlp train");
   });
 }
 

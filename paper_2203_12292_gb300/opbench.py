@@ -2,7 +2,7 @@
 
     python -m paper_2203_12292_gb300.opbench [--workload q4octant] [--level -1]
         [--op vmult|restrict|prolong|mlp] [--dtype f32|f64] [--reps 20]
-        [--tile-cells 0] [--cell-kernel 0|1|2] [--cell-threads 0] [--warp EPS]
+        [--tile-cells 0] [--cell-kernel 0|1|2|3] [--cell-threads 0] [--warp EPS]
 
 vmult: the level's operator; restrict/prolong: the transfer between the
 level and the next coarser one; mlp: the learned-smoother correction (Q4,
@@ -36,7 +36,7 @@ def main(argv=None):
     ap.add_argument("--op", default="vmult", choices=["vmult", "restrict", "prolong", "mlp"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--tile-cells", type=int, default=0)
-    ap.add_argument("--cell-kernel", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--cell-kernel", type=int, default=0, choices=[0, 1, 2, 3])
     ap.add_argument("--cell-threads", type=int, default=0, choices=[0, 128, 256, 384, 512])
     ap.add_argument("--warp", type=float, default=None, help="cells mapped by the warp of this eps")
     a = ap.parse_args(argv)
