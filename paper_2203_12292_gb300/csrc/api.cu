@@ -604,6 +604,7 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
     L->subptr.upload(lh.subptr, H.stream);
     L->perm.upload(lh.perm, H.stream);
     L->lane_tiles.upload(lh.lane, H.stream);
+    L->lane_order.upload(lh.lane_order, H.stream);
     std::vector<int32_t> ijk(lh.cells.size() * 3);
     for (size_t c = 0; c < lh.cells.size(); ++c) {
       ijk[3 * c] = lh.cells[c].i;
@@ -628,6 +629,7 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
     c.subptr = L->subptr.as<uint16_t>();
     c.perm = L->perm.as<uint8_t>();
     c.lane_tiles = lh.lane.empty() ? nullptr : L->lane_tiles.p;
+    c.lane_order = lh.lane.empty() ? nullptr : L->lane_order.as<int32_t>();
     c.cell_ijk = L->cell_ijk.as<int32_t>();
     c.k = k;
     c.tc = tc;

@@ -39,10 +39,11 @@ struct CellMeta {
 static_assert(sizeof(CellMeta) == 64, "CellMeta must be 64 bytes");
 
 // per-tile metadata of the lane-per-cell fp32 operator (one lane per cell of
-// a tile of at most 32 cells, Morton order): the tile-local entity starts
-// transposed (slot s of the cell in lane j at ls[s][j]) so that a warp reads
-// them conflict-free; absent slots (Dirichlet entities, lanes without a
-// cell) point to LANE_ZERO zero values after the tile's DoFs
+// a tile of at most 32 cells, Morton order): the tile-local entity starts as
+// byte offsets (4 x tile-local index), transposed (slot s of the cell in lane
+// j at ls[s][j]) so that a warp reads them conflict-free; absent slots
+// (Dirichlet entities, lanes without a cell) point to LANE_ZERO zero values
+// after the tile's DoFs
 constexpr int LANE_ZERO = 32;
 struct LaneTile {
   uint16_t ls[NSLOT][32];
@@ -139,6 +140,7 @@ struct LevelHost {
   std::vector<int32_t> halo_pos;   // per foreign slot: its position in the DoF-ordered halo buffer
   int max_local = 0;               // max tile-local DoF count
   std::vector<LaneTile> lane;      // per tile (tiles of at most 32 cells): lane-per-cell metadata
+  std::vector<int32_t> lane_order; // tiles with hanging cells, then the others (launch order)
   int max_sub = 0;
   // dof coordinates (host) for checks
   std::vector<double> dof_xyz_cache;

@@ -1370,15 +1370,40 @@ __global__ void __launch_bounds__(11 * 32, 2) vmult_slab(CellArgs<float> A) {
 
 // second pass: every DoF that other tiles contributed to adds its halo slots
 // in a fixed order
+// Every halo DoF has at least one slot; a thread takes HU DoFs and issues all
+// their index, destination and first-slot loads before it adds (memory-level
+// parallelism: the pass is a chain of dependent loads per DoF otherwise)
+constexpr int HU = 8;
 template <typename T>
-__global__ void halo_add_kernel(T* dst, const T* halo, const int32_t* dofs, const int32_t* ptr, int nh) {
+__global__ void __launch_bounds__(BLOCK) halo_add_kernel(T* dst, const T* halo, const int32_t* dofs,
+                                                         const int32_t* ptr, int nh) {
   pdl_begin();
-  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nh; u += gridDim.x * blockDim.x) {
-    const int32_t g = dofs[u];
-    T s = dst[g];
-    for (int e = ptr[u]; e < ptr[u + 1]; ++e) s += halo[e];  // the DoF's slots are contiguous
-    dst[g] = s;
+  const int base = blockIdx.x * (BLOCK * HU) + threadIdx.x;
+  int g[HU], e0[HU], e1[HU];
+#pragma unroll
+  for (int k = 0; k < HU; ++k) {
+    const int u = base + k * BLOCK;
+    g[k] = -1;
+    if (u < nh) {
+      g[k] = dofs[u];
+      e0[k] = ptr[u];
+      e1[k] = ptr[u + 1];
+    }
   }
+  T s[HU], f[HU];
+#pragma unroll
+  for (int k = 0; k < HU; ++k)
+    if (g[k] >= 0) {
+      s[k] = dst[g[k]];
+      f[k] = halo[e0[k]];
+    }
+#pragma unroll
+  for (int k = 0; k < HU; ++k)
+    if (g[k] >= 0) {
+      T a = s[k] + f[k];
+      for (int e = e0[k] + 1; e < e1[k]; ++e) a += halo[e];  // the DoF's slots are contiguous, fixed order
+      dst[g[k]] = a;
+    }
 }
 
 // diagonal of C_m^T A_ref C_m for every mask m: virtual cells (m, column j)
@@ -1439,12 +1464,10 @@ void launch_lines_f32(const CellLaunch& L, int n_tiles, size_t sm, cudaStream_t 
 template <typename T>
 void run_halo(const CellLaunch& L, T* dst, cudaStream_t s) {
   if (L.n_halo == 0) return;
-  const int nb = std::min((L.n_halo + BLOCK - 1) / BLOCK, std::max(L.n_sm, 1) * 8);
-  {
-    launch_pdl(halo_add_kernel<T>, nb, BLOCK, 0, s, dst, static_cast<const T*>(L.halo), L.halo_dofs, L.halo_ptr,
-               L.n_halo);
-    note_launches(1);
-  }
+  const int nb = (L.n_halo + BLOCK * HU - 1) / (BLOCK * HU);
+  launch_pdl(halo_add_kernel<T>, nb, BLOCK, 0, s, dst, static_cast<const T*>(L.halo), L.halo_dofs, L.halo_ptr,
+             L.n_halo);
+  note_launches(1);
 }
 
 template <int K, typename T, int MODE, int NT>

@@ -45,9 +45,10 @@ namespace {
 
 constexpr int LW = 8;  // table entries of x-lines per warp
 
-// x-line r = b + N c of degree K: slot of node (0, b, c) | its entity offset << 8 |
-// entity offset of node (1, b, c) in the slot after it << 16; per warp the
-// x-lines it gathers and scatters (-1: none), class-partitioned
+// x-line r = b + N c of degree K: slot of node (0, b, c) | byte offset of the
+// node in its entity << 8 | byte offset of node (1, b, c) in the slot after it
+// << 16; per warp the x-lines it gathers and scatters (-1: none),
+// class-partitioned
 struct LaneLines {
   uint32_t line[KMAX + 1][NMAX * NMAX];
   int8_t xw[KMAX + 1][NMAX][LW];
@@ -58,6 +59,7 @@ __constant__ LaneLines c_ll;
 struct LaneArgs {
   const TileInfo* tiles;
   const LaneTile* lt;
+  const int32_t* order;  // tile of block b: order[b] (null: tile0 + b)
   const int32_t* foreign;
   const int32_t* halo_pos;
   const float* src;
@@ -69,11 +71,43 @@ struct LaneArgs {
   int tile0;
 };
 
+template <int K>
+struct LaneGeom {
+  static constexpr int N = K + 1, N2 = N * N, N3 = N2 * N, NT = N * 32;
+  // x-lines per warp in the class-partitioned table: at most NXW, exactly NXW
+  // on every warp for k >= 3 (balanced); k = 1: one class of 4 lines
+  static constexpr int NXW = K <= 2 ? 4 : N;
+  static constexpr bool BAL = K >= 3;
+};
+
+// child-side interpolation I_p (TRANS: its transpose) on one line in
+// registers.  I_1[a][b] = I_0[k-a][k-b] (Gauss-Lobatto points and Lagrange
+// basis are symmetric under x -> 1 - x), so p = 1 reverses the line, applies
+// I_0 and reverses back: one set of constant-operand multiply-adds
+template <int K, bool TRANS>
+__device__ __forceinline__ void interp_line_reg(float* v, int p) {
+  constexpr int N = K + 1;
+  const DevTables<float>& tb = tab<float>(K);
+  float x[N], y[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) x[a] = p ? v[K - a] : v[a];
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < N; ++a) s += (TRANS ? tb.I[0][a][r] : tb.I[0][r][a]) * x[a];
+    y[r] = s;
+  }
+#pragma unroll
+  for (int a = 0; a < N; ++a) v[a] = p ? y[K - a] : y[a];
+}
+
 // one direction D of C_e (TRANS: C_e^T) on the lines of warp w: line
 // q = i + N w has the other coordinates (u, v) = (q % N, q / N) in increasing
 // axis order; lane j interpolates when the line lies on a hanging face or edge
-// of its cell
-template <int K, int D, bool TRANS>
+// of its cell.  SWEEP (D = 2 only): the z sweep follows (forward after C_z) or
+// precedes (backward before C_z^T) the interpolation on the same lines.
+template <int K, int D, bool TRANS, bool SWEEP = false>
 __device__ __forceinline__ void hang_pass(float* cb, uint16_t m, int w, int lane) {
   constexpr int N = K + 1, N2 = N * N;
   constexpr int S = (D == 0 ? 1 : (D == 1 ? N : N2)) * 32;
@@ -83,38 +117,18 @@ __device__ __forceinline__ void hang_pass(float* cb, uint16_t m, int w, int lane
   for (int i = 0; i < N; ++i) {
     const int q = i + N * w;
     const int u = q % N, v = q / N;
-    if (!line_hangs<K, D>(m, u, v)) continue;
+    const bool hl = line_hangs<K, D>(m, u, v);
+    if (!SWEEP && !hl) continue;
     const int base = D == 0 ? N * u + N2 * v : (D == 1 ? u + N2 * v : u + N * v);
     float* ptr = cb + base * 32 + lane;
     float x[N];
 #pragma unroll
     for (int a = 0; a < N; ++a) x[a] = ptr[a * S];
+    if (SWEEP && TRANS) eo_backward<N, 0, 1>(x, tb.Be);
+    if (hl) interp_line_reg<K, TRANS>(x, p);
+    if (SWEEP && !TRANS) eo_forward<N, 0, 1>(x, tb.Be);
 #pragma unroll
-    for (int r = 0; r < N; ++r) {
-      float s = 0.f;
-#pragma unroll
-      for (int a = 0; a < N; ++a)
-        s += (p ? (TRANS ? tb.I[1][a][r] : tb.I[1][r][a]) : (TRANS ? tb.I[0][a][r] : tb.I[0][r][a])) * x[a];
-      ptr[r * S] = s;
-    }
-  }
-}
-
-// C_x (TRANS: C_x^T) on one x-line in registers
-template <int K, bool TRANS>
-__device__ __forceinline__ void hang_x(float* v, int p) {
-  constexpr int N = K + 1;
-  const DevTables<float>& tb = tab<float>(K);
-  float x[N];
-#pragma unroll
-  for (int a = 0; a < N; ++a) x[a] = v[a];
-#pragma unroll
-  for (int r = 0; r < N; ++r) {
-    float s = 0.f;
-#pragma unroll
-    for (int a = 0; a < N; ++a)
-      s += (p ? (TRANS ? tb.I[1][a][r] : tb.I[1][r][a]) : (TRANS ? tb.I[0][a][r] : tb.I[0][r][a])) * x[a];
-    v[r] = s;
+    for (int a = 0; a < N; ++a) ptr[a * S] = x[a];
   }
 }
 
@@ -134,44 +148,84 @@ __device__ __forceinline__ uint32_t hanging_slot_set(uint16_t m) {
   return hs;
 }
 
-// xs[g] += v where lanes with the same g (siblings behind one hanging face or
-// edge) add one after another in lane order; g >= nloc (absent DoF) adds
-// nothing.  Only lanes whose slot hangs can share g within one instruction:
-// without such a lane (hang_any = 0) the plain addition is exact.
-__device__ __forceinline__ void add_ordered(float* xs, int g, float v, int nloc, int lane, bool hang_any) {
+// *x += v where lanes with the same address (siblings behind one hanging face
+// or edge) add one after another in lane order; absent DoFs (the zero region)
+// add nothing.  Only lanes whose slot hangs can share an address within one
+// instruction: without such a lane (hang_any = 0) the plain addition is exact.
+__device__ __forceinline__ void add_ordered(float* x, float v, bool real, int lane, bool hang_any) {
   if (!hang_any) {
-    xs[g] += v;
+    *x += v;
     return;
   }
-  const bool real = g < nloc;
-  const unsigned peers = __match_any_sync(0xffffffffu, real ? g : -1 - lane);
+  const unsigned key = real ? (unsigned)__cvta_generic_to_shared(x) : ~(unsigned)lane;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int rank = __popc(peers & ((1u << lane) - 1u));
   const int most = __reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
   for (int q = 0; q < most; ++q) {
-    if (real && rank == q) xs[g] += v;
+    if (real && rank == q) *x += v;
     __syncwarp();
   }
 }
 
+// the three gather/scatter addresses of x-line r of the cell in this lane:
+// node (0, b, c), first interior node (1, b, c), node (k, b, c)
 template <int K>
-__global__ void __launch_bounds__((K + 1) * 32) vmult_lanes(LaneArgs A) {
+__device__ __forceinline__ void xline_ptrs(const LaneTile* st, char* xb, int r, int lane, float*& p0, float*& p1,
+                                           float*& p2) {
+  const uint32_t li = c_ll.line[K][r];
+  const int s0 = li & 0xff, o0 = (li >> 8) & 0xff, o1 = li >> 16;
+  p0 = reinterpret_cast<float*>(xb + st->ls[s0][lane] + o0);
+  p1 = reinterpret_cast<float*>(xb + st->ls[s0 + 1][lane] + o1);
+  p2 = reinterpret_cast<float*>(xb + st->ls[s0 + 2][lane] + o0);
+}
+
+// y sweep on the lines (a, c) = (i, w) of warp w
+template <int K, bool FWD>
+__device__ __forceinline__ void sweep_y(float* cb, int w, int lane) {
+  constexpr int N = K + 1, N2 = N * N;
+  const DevTables<float>& tb = tab<float>(K);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float* p = cb + (i + N2 * w) * 32 + lane;
+    float v[N];
+#pragma unroll
+    for (int b = 0; b < N; ++b) v[b] = p[b * N * 32];
+    if (FWD)
+      eo_forward<N, 0, 1>(v, tb.Be);
+    else
+      eo_backward<N, 0, 1>(v, tb.Be);
+#pragma unroll
+    for (int b = 0; b < N; ++b) p[b * N * 32] = v[b];
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(LaneArgs A) {
   pdl_begin();
-  constexpr int N = K + 1, N2 = N * N, N3 = N2 * N, NT = N * 32;
+  using G = LaneGeom<K>;
+  constexpr int N = G::N, N2 = G::N2, N3 = G::N3, NT = G::NT, NXW = G::NXW;
   extern __shared__ __align__(16) unsigned char smem[];
   LaneTile* st = reinterpret_cast<LaneTile*>(smem);
   float* cb = reinterpret_cast<float*>(smem + sizeof(LaneTile));
-  float* xs = cb + N3 * 32;  // tile DoFs, then the zero region; later the accumulator
+  float* xs0 = cb + N3 * 32;  // 16-byte aligned
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int tile = A.tile0 + blockIdx.x;
+  const int tile = A.order ? A.order[blockIdx.x] : A.tile0 + blockIdx.x;
   const TileInfo ti = A.tiles[tile];
   const int nloc = ti.n_owned + ti.n_foreign;
+  // tile DoF i at xs[i] (then the zero region; later the accumulator): xs + i is 16-byte aligned
+  // exactly where src + dof_begin + i is, so the owned range moves in 16-byte pieces
+  const float* so = A.src + ti.dof_begin;
+  const int sh = (int)((reinterpret_cast<uintptr_t>(so) >> 2) & 3);
+  float* xs = xs0 + sh;
+  const int h0 = min((4 - sh) & 3, ti.n_owned), nv = (ti.n_owned - h0) >> 2;
   {  // asynchronous copies of the lane metadata and the tile's DoFs, all in flight at once
     const uint4* g = reinterpret_cast<const uint4*>(A.lt + tile);
     uint4* s = reinterpret_cast<uint4*>(st);
     for (int i = threadIdx.x; i < (int)(sizeof(LaneTile) / 16); i += NT) cp_async16(s + i, g + i);
-    const float* so = A.src + ti.dof_begin;
+    if (threadIdx.x < h0) cp_async(xs + threadIdx.x, so + threadIdx.x);
 #pragma unroll 4
-    for (int i = threadIdx.x; i < ti.n_owned; i += NT) cp_async(xs + i, so + i);
+    for (int j = threadIdx.x; j < nv; j += NT) cp_async16(xs + h0 + 4 * j, so + h0 + 4 * j);
+    for (int i = h0 + 4 * nv + threadIdx.x; i < ti.n_owned; i += NT) cp_async(xs + i, so + i);
     const int32_t* fl = A.foreign + ti.foreign_begin;
     float* xf = xs + ti.n_owned;
     for (int i0 = threadIdx.x; i0 < ti.n_foreign; i0 += 4 * NT) {
@@ -196,131 +250,138 @@ __global__ void __launch_bounds__((K + 1) * 32) vmult_lanes(LaneArgs A) {
     const double hd = ldexp(A.dom, -(int)st->level[lane]);
     h = (float)(A.coef ? hd * A.coef[c] : hd);
   }
-
-  // G_e (+ C_x on hanging x-lines, or the forward x sweep when the tile has no hanging cells)
+  char* xb = reinterpret_cast<char*>(xs);
   const int nxl = c_ll.nx[K][w];
-#pragma unroll 1
-  for (int i = 0; i < nxl; ++i) {
-    const int r = c_ll.xw[K][w][i];
-    const uint32_t li = c_ll.line[K][r];
-    const int s0 = li & 0xff, o0 = (li >> 8) & 0xff, o1 = li >> 16;
-    const int g0 = st->ls[s0][lane] + o0, g1 = st->ls[s0 + 1][lane] + o1, g2 = st->ls[s0 + 2][lane] + o0;
-    float v[N];
-    v[0] = xs[g0];
-#pragma unroll
-    for (int a = 1; a < K; ++a) v[a] = xs[g1 + a - 1];
-    v[K] = xs[g2];
-    if (!hang)
-      eo_forward<N, 0, 1>(v, tb.Be);
-    else if (line_hangs<K, 0>(m, r % N, r / N))
-      hang_x<K, false>(v, m & 1);
-    float* p = cb + N * r * 32 + lane;
-#pragma unroll
-    for (int a = 0; a < N; ++a) p[a * 32] = v[a];
-  }
-  __syncthreads();
-  if (hang) {  // C_y, C_z, then the forward x sweep
-    hang_pass<K, 1, false>(cb, m, w, lane);
-    __syncthreads();
-    hang_pass<K, 2, false>(cb, m, w, lane);
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      float* p = cb + N * (i + N * w) * 32 + lane;
-      float v[N];
-#pragma unroll
-      for (int a = 0; a < N; ++a) v[a] = p[a * 32];
-      eo_forward<N, 0, 1>(v, tb.Be);
-#pragma unroll
-      for (int a = 0; a < N; ++a) p[a * 32] = v[a];
-    }
-    __syncthreads();
-  }
-
-  // forward y sweep (lines (a, c) = (i, w)); the tile DoFs are dead: clear the accumulator
-  {
-    float4* z4 = reinterpret_cast<float4*>(xs);
-    for (int i = threadIdx.x; i < (nloc + 3) / 4; i += NT) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    float* p = cb + (i + N2 * w) * 32 + lane;
-    float v[N];
-#pragma unroll
-    for (int b = 0; b < N; ++b) v[b] = p[b * N * 32];
-    eo_forward<N, 0, 1>(v, tb.Be);
-#pragma unroll
-    for (int b = 0; b < N; ++b) p[b * N * 32] = v[b];
-  }
-  __syncthreads();
-  // z: forward sweep, h (lam_a + lam_b + lam_c) in mode order, backward sweep (lines (a, b) = (i, w))
-  {
-    const float hb = h * tb.lame[w];
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      float* p = cb + (i + N * w) * 32 + lane;
-      float v[N];
-#pragma unroll
-      for (int c = 0; c < N; ++c) v[c] = p[c * N2 * 32];
-      eo_forward<N, 0, 1>(v, tb.Be);
-      const float hab = fmaf(h, tb.lame[i], hb);
-#pragma unroll
-      for (int c = 0; c < N; ++c) v[c] *= fmaf(h, tb.lame[c], hab);
-      eo_backward<N, 0, 1>(v, tb.Be);
-#pragma unroll
-      for (int c = 0; c < N; ++c) p[c * N2 * 32] = v[c];
-    }
-  }
-  __syncthreads();
-  // backward y sweep
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    float* p = cb + (i + N2 * w) * 32 + lane;
-    float v[N];
-#pragma unroll
-    for (int b = 0; b < N; ++b) v[b] = p[b * N * 32];
-    eo_backward<N, 0, 1>(v, tb.Be);
-#pragma unroll
-    for (int b = 0; b < N; ++b) p[b * N * 32] = v[b];
-  }
-  __syncthreads();
 
   if (!hang) {
+    // G_e fused with the forward x sweep: all loads of the warp's x-lines first
+    {
+      float v[NXW][N];
+#pragma unroll
+      for (int i = 0; i < NXW; ++i)
+        if (G::BAL || i < nxl) {
+          float *p0, *p1, *p2;
+          xline_ptrs<K>(st, xb, c_ll.xw[K][w][i], lane, p0, p1, p2);
+          v[i][0] = *p0;
+#pragma unroll
+          for (int a = 1; a < K; ++a) v[i][a] = p1[a - 1];
+          v[i][K] = *p2;
+        }
+#pragma unroll
+      for (int i = 0; i < NXW; ++i)
+        if (G::BAL || i < nxl) {
+          eo_forward<N, 0, 1>(v[i], tb.Be);
+          float* p = cb + N * c_ll.xw[K][w][i] * 32 + lane;
+#pragma unroll
+          for (int a = 0; a < N; ++a) p[a * 32] = v[i][a];
+        }
+    }
+    __syncthreads();
+    {  // the tile DoFs are dead: clear the accumulator
+      float4* z4 = reinterpret_cast<float4*>(xs0);
+      for (int i = threadIdx.x; i < (sh + nloc + 3) / 4; i += NT) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    sweep_y<K, true>(cb, w, lane);
+    __syncthreads();
+    // z: forward sweep, h (lam_a + lam_b + lam_c) in mode order, backward sweep (lines (a, b) = (i, w))
+    {
+      const float hb = h * tb.lame[w];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float* p = cb + (i + N * w) * 32 + lane;
+        float v[N];
+#pragma unroll
+        for (int c = 0; c < N; ++c) v[c] = p[c * N2 * 32];
+        eo_forward<N, 0, 1>(v, tb.Be);
+        const float hab = fmaf(h, tb.lame[i], hb);
+#pragma unroll
+        for (int c = 0; c < N; ++c) v[c] *= fmaf(h, tb.lame[c], hab);
+        eo_backward<N, 0, 1>(v, tb.Be);
+#pragma unroll
+        for (int c = 0; c < N; ++c) p[c * N2 * 32] = v[c];
+      }
+    }
+    __syncthreads();
+    sweep_y<K, false>(cb, w, lane);
+    __syncthreads();
     // backward x sweep fused with G_e^T: each warp adds its class of x-lines in program order
+    {
+      float v[NXW][N];
+#pragma unroll
+      for (int i = 0; i < NXW; ++i)
+        if (G::BAL || i < nxl) {
+          const float* p = cb + N * c_ll.xw[K][w][i] * 32 + lane;
+#pragma unroll
+          for (int a = 0; a < N; ++a) v[i][a] = p[a * 32];
+        }
+#pragma unroll
+      for (int i = 0; i < NXW; ++i)
+        if (G::BAL || i < nxl) {
+          eo_backward<N, 0, 1>(v[i], tb.Be);
+          float *p0, *p1, *p2;
+          xline_ptrs<K>(st, xb, c_ll.xw[K][w][i], lane, p0, p1, p2);
+          *p0 += v[i][0];
+#pragma unroll
+          for (int a = 1; a < K; ++a) p1[a - 1] += v[i][a];
+          *p2 += v[i][K];
+        }
+    }
+  } else {
+    // G_e and C_x on the warp's x-lines
 #pragma unroll 1
     for (int i = 0; i < nxl; ++i) {
       const int r = c_ll.xw[K][w][i];
-      const float* p = cb + N * r * 32 + lane;
+      float *p0, *p1, *p2;
+      xline_ptrs<K>(st, xb, r, lane, p0, p1, p2);
       float v[N];
+      v[0] = *p0;
 #pragma unroll
-      for (int a = 0; a < N; ++a) v[a] = p[a * 32];
-      eo_backward<N, 0, 1>(v, tb.Be);
-      const uint32_t li = c_ll.line[K][r];
-      const int s0 = li & 0xff, o0 = (li >> 8) & 0xff, o1 = li >> 16;
-      const int g0 = st->ls[s0][lane] + o0, g1 = st->ls[s0 + 1][lane] + o1, g2 = st->ls[s0 + 2][lane] + o0;
-      xs[g0] += v[0];
-#pragma unroll
-      for (int a = 1; a < K; ++a) xs[g1 + a - 1] += v[a];
-      xs[g2] += v[K];
-    }
-  } else {
-    // backward x sweep, C_z^T, C_y^T, then C_x^T and G_e^T on the warp's class of x-lines
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      float* p = cb + N * (i + N * w) * 32 + lane;
-      float v[N];
-#pragma unroll
-      for (int a = 0; a < N; ++a) v[a] = p[a * 32];
-      eo_backward<N, 0, 1>(v, tb.Be);
+      for (int a = 1; a < K; ++a) v[a] = p1[a - 1];
+      v[K] = *p2;
+      if (line_hangs<K, 0>(m, r % N, r / N)) interp_line_reg<K, false>(v, m & 1);
+      float* p = cb + N * r * 32 + lane;
 #pragma unroll
       for (int a = 0; a < N; ++a) p[a * 32] = v[a];
     }
     __syncthreads();
-    hang_pass<K, 2, true>(cb, m, w, lane);
+    hang_pass<K, 1, false>(cb, m, w, lane);  // C_y
     __syncthreads();
-    hang_pass<K, 1, true>(cb, m, w, lane);
+    hang_pass<K, 2, false, true>(cb, m, w, lane);  // C_z, forward z sweep
     __syncthreads();
+    {
+      float4* z4 = reinterpret_cast<float4*>(xs0);
+      for (int i = threadIdx.x; i < (sh + nloc + 3) / 4; i += NT) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    sweep_y<K, true>(cb, w, lane);
+    __syncthreads();
+    // x: forward sweep, h (lam_a + lam_b + lam_c) in mode order, backward sweep (lines (b, c) = (i, w))
+    {
+      const float hc = h * tb.lame[w];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        float* p = cb + N * (i + N * w) * 32 + lane;
+        float v[N];
+#pragma unroll
+        for (int a = 0; a < N; ++a) v[a] = p[a * 32];
+        eo_forward<N, 0, 1>(v, tb.Be);
+        const float hbc = fmaf(h, tb.lame[i], hc);
+#pragma unroll
+        for (int a = 0; a < N; ++a) v[a] *= fmaf(h, tb.lame[a], hbc);
+        eo_backward<N, 0, 1>(v, tb.Be);
+#pragma unroll
+        for (int a = 0; a < N; ++a) p[a * 32] = v[a];
+      }
+    }
+    __syncthreads();
+    sweep_y<K, false>(cb, w, lane);
+    __syncthreads();
+    hang_pass<K, 2, true, true>(cb, m, w, lane);  // backward z sweep, C_z^T
+    __syncthreads();
+    hang_pass<K, 1, true>(cb, m, w, lane);  // C_y^T
+    __syncthreads();
+    // C_x^T and G_e^T on the warp's class of x-lines
     const uint32_t hs = hanging_slot_set(m);
+    const int zb = nloc * 4;  // byte offset of the zero region
 #pragma unroll 1
     for (int i = 0; i < nxl; ++i) {
       const int r = c_ll.xw[K][w][i];
@@ -328,25 +389,40 @@ __global__ void __launch_bounds__((K + 1) * 32) vmult_lanes(LaneArgs A) {
       float v[N];
 #pragma unroll
       for (int a = 0; a < N; ++a) v[a] = p[a * 32];
-      if (line_hangs<K, 0>(m, r % N, r / N)) hang_x<K, true>(v, m & 1);
+      if (line_hangs<K, 0>(m, r % N, r / N)) interp_line_reg<K, true>(v, m & 1);
       const uint32_t li = c_ll.line[K][r];
       const int s0 = li & 0xff, o0 = (li >> 8) & 0xff, o1 = li >> 16;
-      const int g0 = st->ls[s0][lane] + o0, g1 = st->ls[s0 + 1][lane] + o1, g2 = st->ls[s0 + 2][lane] + o0;
+      const int b0 = st->ls[s0][lane], b1 = st->ls[s0 + 1][lane], b2 = st->ls[s0 + 2][lane];
+      float* p0 = reinterpret_cast<float*>(xb + b0 + o0);
+      float* p1 = reinterpret_cast<float*>(xb + b1 + o1);
+      float* p2 = reinterpret_cast<float*>(xb + b2 + o0);
       const bool h0 = __any_sync(0xffffffffu, (hs >> s0) & 1u), h1 = __any_sync(0xffffffffu, (hs >> (s0 + 1)) & 1u),
                  h2 = __any_sync(0xffffffffu, (hs >> (s0 + 2)) & 1u);
-      add_ordered(xs, g0, v[0], nloc, lane, h0);
+      add_ordered(p0, v[0], b0 != zb, lane, h0);
 #pragma unroll
-      for (int a = 1; a < K; ++a) add_ordered(xs, g1 + a - 1, v[a], nloc, lane, h1);
-      add_ordered(xs, g2, v[K], nloc, lane, h2);
+      for (int a = 1; a < K; ++a) add_ordered(p1 + a - 1, v[a], b1 != zb, lane, h1);
+      add_ordered(p2, v[K], b2 != zb, lane, h2);
     }
   }
   __syncthreads();
-  // owned DoFs: plain stores (or additions); foreign DoFs: into their halo slots
+  // owned DoFs: plain stores (or additions), 16 bytes at a time where src and dst are aligned
+  // alike; foreign DoFs: into their halo slots
   float* d = A.dst + ti.dof_begin;
-  if (A.add)
-    for (int i = threadIdx.x; i < ti.n_owned; i += NT) d[i] += xs[i];
-  else
-    for (int i = threadIdx.x; i < ti.n_owned; i += NT) d[i] = xs[i];
+  if ((int)((reinterpret_cast<uintptr_t>(d) >> 2) & 3) == sh) {
+    if (threadIdx.x < h0) d[threadIdx.x] = A.add ? d[threadIdx.x] + xs[threadIdx.x] : xs[threadIdx.x];
+    for (int j = threadIdx.x; j < nv; j += NT) {
+      float4 x4 = *reinterpret_cast<const float4*>(xs + h0 + 4 * j);
+      float4* d4 = reinterpret_cast<float4*>(d + h0 + 4 * j);
+      if (A.add) {
+        const float4 o = *d4;
+        x4 = make_float4(o.x + x4.x, o.y + x4.y, o.z + x4.z, o.w + x4.w);
+      }
+      *d4 = x4;
+    }
+    for (int i = h0 + 4 * nv + threadIdx.x; i < ti.n_owned; i += NT) d[i] = A.add ? d[i] + xs[i] : xs[i];
+  } else {
+    for (int i = threadIdx.x; i < ti.n_owned; i += NT) d[i] = A.add ? d[i] + xs[i] : xs[i];
+  }
   const int32_t* hp = A.halo_pos + ti.foreign_begin;
   for (int i = threadIdx.x; i < ti.n_foreign; i += NT) A.halo[hp[i]] = xs[ti.n_owned + i];
 }
@@ -386,7 +462,7 @@ void fill_lane_lines(LaneLines& t) {
         int s0, o0, s1, o1 = 0;
         host_node_slot(k, 0, b, c, s0, o0);
         if (k > 1) host_node_slot(k, 1, b, c, s1, o1);
-        t.line[k][b + n * c] = (uint32_t)s0 | ((uint32_t)o0 << 8) | ((uint32_t)o1 << 16);
+        t.line[k][b + n * c] = (uint32_t)s0 | ((uint32_t)(4 * o0) << 8) | ((uint32_t)(4 * o1) << 16);
       }
     auto cls = [&](int x) { return (x == 0 || x == k) ? -1 : x; };
     std::map<std::pair<int, int>, std::vector<int>> classes;
@@ -414,7 +490,8 @@ void fill_lane_lines(LaneLines& t) {
 template <int K>
 size_t lanes_smem(int max_local) {
   constexpr int N3 = (K + 1) * (K + 1) * (K + 1);
-  return sizeof(LaneTile) + ((size_t)N3 * 32 + (size_t)max_local + LANE_ZERO + 3) * sizeof(float);
+  // tile DoFs shifted by up to 3 for the 16-byte copies, the zero region, and the float4 clearing
+  return sizeof(LaneTile) + ((size_t)N3 * 32 + (size_t)max_local + LANE_ZERO + 8) * sizeof(float);
 }
 
 template <int K>
@@ -443,6 +520,9 @@ void launch_vmult_lanes(const CellLaunch& L, const void* src, void* dst, int add
   LaneArgs A{};
   A.tiles = L.tiles;
   A.lt = static_cast<const LaneTile*>(L.lane_tiles);
+  // a whole level: tiles with hanging cells first (their longer code path then
+  // runs mostly on its own instead of interleaved with the regular tiles')
+  A.order = (t0 == 0 && t1 == L.n_tiles) ? L.lane_order : nullptr;
   A.foreign = L.foreign;
   A.halo_pos = L.halo_pos;
   A.src = static_cast<const float*>(src);

@@ -306,22 +306,28 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
   }
   // lane-per-cell metadata of tiles of at most 32 cells
   L.lane.clear();
+  L.lane_order.clear();
   if (tile_cells <= 32) {
     L.lane.assign(nt, LaneTile{});
     for (int t = 0; t < nt; ++t) {
       const TileInfo& T = L.tiles[t];
       LaneTile& lt = L.lane[t];
-      const uint16_t zero = (uint16_t)(T.n_owned + T.n_foreign);
-      if ((int)zero + LANE_ZERO >= (int)LS_NONE) throw std::runtime_error("tile too large for 16-bit local indices");
+      const int nloc = T.n_owned + T.n_foreign;
+      if (4 * (nloc + LANE_ZERO) >= (int)LS_NONE) throw std::runtime_error("tile too large for 16-bit byte offsets");
       for (int j = 0; j < 32; ++j) {
         const bool cell = j < T.n_cells;
         const CellMeta* cm = cell ? &L.meta[T.cell_begin + j] : nullptr;
-        for (int s = 0; s < NSLOT; ++s) lt.ls[s][j] = (cell && cm->ls[s] != LS_NONE) ? cm->ls[s] : zero;
+        for (int s = 0; s < NSLOT; ++s)
+          lt.ls[s][j] = (uint16_t)(4 * ((cell && cm->ls[s] != LS_NONE) ? cm->ls[s] : nloc));
         lt.mask[j] = cell ? cm->mask : 0;
         lt.level[j] = cell ? cm->level : 0;
         if (cell && (cm->mask & MASK_HANG)) lt.hang = 1;
       }
     }
+    L.lane_order.clear();
+    for (int pass = 1; pass >= 0; --pass)
+      for (int t = 0; t < nt; ++t)
+        if (L.lane[t].hang == pass) L.lane_order.push_back(t);
   }
   L.n_free = next;
   for (int e = 0; e < ne; ++e)
