@@ -99,10 +99,12 @@ typedef struct {
   int tile_cells;          /* cells per tile on large levels, 0 = default (32);
                               levels with fewer than 2 * 152 tiles of that
                               size use halved tiles (down to 8 cells) */
-  int cell_kernel;         /* fp32 operator kernel: 0 = default (line-parallel),
-                              1 = line-parallel (one thread per 1D line of
-                              a cell), 2 = slab threads (k+1 threads per
-                              cell, z-slabs in registers; tiles <= 64 cells) */
+  int cell_kernel;         /* fp32 operator kernel: 0 = default (one lane per
+                              cell on levels with tiles of at most 32 cells,
+                              else line-parallel), 1 = line-parallel (one
+                              thread per 1D line of a cell), 2 = slab threads
+                              (k+1 threads per cell, z-slabs in registers;
+                              tiles <= 64 cells), 3 = one lane per cell */
   int cell_threads;        /* threads per CTA of the line-parallel fp32 operator:
                               0 = default (256), 128, 256, 384 or 512 */
   int local_smoothing;     /* 1: geometric local smoothing instead of global
@@ -116,6 +118,12 @@ typedef struct {
                               not a multigrid level.  Requires
                               p_coarsening = 0; not combinable with the learned
                               smoother, a coefficient or the batch. */
+  int transfer_chunk;      /* coarse cells per chunk of the restriction kernel:
+                              0 = default (4 on levels whose coarse side has
+                              more than 4 tiles per SM, 8 on smaller ones),
+                              4 or 8 = that size on every level (the same
+                              operator; a test knob for the 4-cell variant
+                              on small meshes) */
 } gcmg_config;
 
 int gcmg_config_default(gcmg_config* cfg);

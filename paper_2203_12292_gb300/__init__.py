@@ -45,7 +45,7 @@ class Config(ctypes.Structure):
     _fields_ = [("degree", _c_int), ("p_coarsening", _c_int), ("mg_fp32", _c_int), ("cheb_degree", _c_int),
                 ("smoothing_range", _c_double), ("eig_steps", _c_int), ("eig_safety", _c_double),
                 ("tile_cells", _c_int), ("cell_kernel", _c_int), ("cell_threads", _c_int),
-                ("local_smoothing", _c_int)]
+                ("local_smoothing", _c_int), ("transfer_chunk", _c_int)]
 
 
 class LevelInfo(ctypes.Structure):
@@ -237,7 +237,8 @@ def _is64(t) -> int:
 
 def make_config(degree: int, p_coarsening: bool = False, mg_fp32: bool = True, tile_cells: int = 0,
                 cheb_degree: int = 3, smoothing_range: float = 20.0, eig_steps: int = 12, eig_safety: float = 1.2,
-                cell_kernel: int = 0, cell_threads: int = 0, local_smoothing: bool = False) -> Config:
+                cell_kernel: int = 0, cell_threads: int = 0, local_smoothing: bool = False,
+                transfer_chunk: int = 0) -> Config:
     cfg = Config()
     _check(lib().gcmg_config_default(ctypes.byref(cfg)))
     cfg.degree, cfg.p_coarsening, cfg.mg_fp32 = degree, int(p_coarsening), int(mg_fp32)
@@ -245,6 +246,7 @@ def make_config(degree: int, p_coarsening: bool = False, mg_fp32: bool = True, t
     cfg.eig_steps, cfg.eig_safety, cfg.cell_kernel = eig_steps, eig_safety, cell_kernel
     cfg.cell_threads = cell_threads
     cfg.local_smoothing = int(local_smoothing)
+    cfg.transfer_chunk = transfer_chunk
     return cfg
 
 
@@ -255,7 +257,7 @@ class Multigrid:
     def __init__(self, mesh: Mesh, degree: int, p_coarsening: bool = False, mg_fp32: bool = True,
                  tile_cells: int = 0, cheb_degree: int = 3, smoothing_range: float = 20.0,
                  eig_steps: int = 12, eig_safety: float = 1.2, cell_kernel: int = 0, cell_threads: int = 0,
-                 local_smoothing: bool = False, _handle=None, _owner=None):
+                 local_smoothing: bool = False, transfer_chunk: int = 0, _handle=None, _owner=None):
         import torch
         self.mesh = mesh
         self.stream = torch.cuda.current_stream()
@@ -263,7 +265,7 @@ class Multigrid:
             self._h, self._owned, self._owner = _handle, False, _owner
         else:
             cfg = make_config(degree, p_coarsening, mg_fp32, tile_cells, cheb_degree, smoothing_range, eig_steps,
-                              eig_safety, cell_kernel, cell_threads, local_smoothing)
+                              eig_safety, cell_kernel, cell_threads, local_smoothing, transfer_chunk)
             h = _c_void_p()
             _check(lib().gcmg_setup(mesh._p, ctypes.byref(cfg), _c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
             self._h, self._owned = h, True

@@ -504,6 +504,8 @@ void check_config(const gcmg_config* cfg) {
     throw Error(GCMG_ERR_ARG, "bad smoother parameters");
   if (cfg->tile_cells < 0 || cfg->tile_cells > 255) throw Error(GCMG_ERR_ARG, "tile_cells must be 0..255");
   if (cfg->cell_kernel < 0 || cfg->cell_kernel > 3) throw Error(GCMG_ERR_ARG, "cell_kernel must be 0, 1, 2 or 3");
+  if (cfg->transfer_chunk != 0 && cfg->transfer_chunk != 4 && cfg->transfer_chunk != 8)
+    throw Error(GCMG_ERR_ARG, "transfer_chunk must be 0, 4 or 8");
   if (cfg->cell_threads != 0 && cfg->cell_threads != 128 && cfg->cell_threads != 256 && cfg->cell_threads != 384 &&
       cfg->cell_threads != 512)
     throw Error(GCMG_ERR_ARG, "cell_threads must be 0, 128, 256, 384 or 512");
@@ -634,6 +636,7 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
     c.k = k;
     c.tc = tc;
     c.n_sm = H.n_sm;
+    c.chunk = cfg.transfer_chunk;
     c.max_local = lh.max_local;
     c.lo = lh.lo;
     c.dom = lh.hi - lh.lo;
@@ -807,6 +810,7 @@ int gcmg_config_default(gcmg_config* cfg) {
     cfg->cell_kernel = 0;
     cfg->cell_threads = 0;
     cfg->local_smoothing = 0;
+    cfg->transfer_chunk = 0;
   });
 }
 

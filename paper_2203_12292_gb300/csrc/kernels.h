@@ -36,6 +36,7 @@ struct CellLaunch {
   int use_lines;  // 1: fp32 operator with the line-parallel kernel
   int threads;    // threads per CTA of the line-parallel operator kernel (128, 256, 384 or 512)
   int n_sm;       // multiprocessors of the device (grid sizes, chunk choices)
+  int chunk;      // coarse cells per restriction chunk (0: from the level size)
   int use_lanes;  // 1: fp32 operator with the lane-per-cell kernel (tiles of at most 32 cells)
   const void* lane_tiles;  // per tile LaneTile (null: level without them)
   const int32_t* lane_order;  // launch order of the tiles: those with hanging cells first
