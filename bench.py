@@ -31,8 +31,15 @@ beside it, and two further parts of the method:
 Under torchrun every rank solves its own copy (replicas, weak scaling);
 value sums the ranks.
 
+Beside it: the fp32 and fp64 operators' fractions of the measured HBM
+bandwidth and of the measured CUDA-core peak (an FMA microbenchmark of the
+library), the V-cycle throughput, the same solve on the other two workloads
+of this path (Q2 octant, f = 1, fp64 multigrid; Q4 sphere with p-coarsening
+4 -> 2 -> 1, f = 1), and the oracle's single-threaded timings (operator,
+V-cycle, PCG) on samples of the workload as the CPU baseline.
+
 --impl reference times the oracle (plain CPU implementation, test
-infrastructure) on a bounded sample of the workload on the host cores.
+infrastructure) on a bounded sample of the workload on one host core.
 """
 from __future__ import annotations
 
@@ -42,6 +49,12 @@ import os
 import subprocess
 import sys
 import time
+
+# the oracle's timings (the reference arm and the CPU baseline) run its numpy
+# code on one thread: fix the thread count before numpy loads its BLAS
+if "--oracle-timings" in sys.argv or ("--impl" in sys.argv and "reference" in sys.argv):
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
 
 import numpy as np
 
@@ -58,12 +71,30 @@ METRIC = "fine-level vmult GDoF/s; solve time to 1e-8 rel. res., mixed/learned v
 # workload, per free DoF)
 BYTES_PER_DOF = {"fp32": 9.8, "fp64": 17.8}
 # DRAM bytes (read + write) of one fine-level fp32 operator application on
-# this workload, both of its launches (tile kernel vmult_lines<4,float,4>:
-# 135.1 MB read + 58.7 MB written; halo pass: 90.4 MB + 3.3 MB), from the
-# ncu capture summarised in profiles/vmult_lines_q4_octant_fp32.md; set to 0
-# (reported as null) when the kernel changes until it is re-captured
-VMULT_TRAFFIC_BYTES = 287.5e6
+# this workload, both of its launches, from one ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum with caches flushed before each
+# kernel (ncu's default): tile kernel vmult_lanes<4> 136.2 MB read + 58.9 MB
+# written, halo pass 89.8 MB + 0.8 MB; set to 0 (reported as null) when the
+# kernels change until they are captured again
+VMULT_TRAFFIC_BYTES = 285.7e6
+# V-cycle bytes per finest-level DoF (fp32): six operator applications and
+# five vector updates per level, the transfers, summed over the levels with
+# the 1/(1 - 1/8) factor of the coarser levels
+VCYCLE_BYTES_PER_DOF = 250.0
 SAMPLE = synth.cube_octant(4, 2)  # 1/8 of the workload's cells, same recipe family
+SAMPLE_MG = synth.cube_octant(3, 2)  # 1/64 of the cells: the oracle's V-cycle and PCG
+
+
+def flops_per_cell(k: int) -> int:
+    """Algorithmic flops of one cell of the fast-diagonalisation operator:
+    six 1D even-odd transforms on (k+1)^2 lines each (fold: 2 floor(n/2)
+    adds; symmetric modes: ceil(n/2) rows of 2 ceil(n/2) - 1 flops;
+    antisymmetric: floor(n/2) rows of 2 floor(n/2) - 1), and one scaling per
+    node (a multiply-add counts two; Q4: 3,875)."""
+    n = k + 1
+    nh, ne = n // 2, (n + 1) // 2
+    f1d = 2 * nh + ne * (2 * ne - 1) + nh * (2 * nh - 1)
+    return 6 * n * n * f1d + n ** 3
 
 
 def peaks():
@@ -75,24 +106,61 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def oracle_vmult_sample(seconds: float = 6.0):
-    """Time the oracle's fp64 cell-by-cell operator on the sample mesh."""
-    from oracle import mesh as omesh, space as ospace
+def oracle_timings():
+    """The oracle as it stands, on one thread (set before numpy loads): its
+    fp64 cell-by-cell operator on SAMPLE, and one V-cycle and the PCG solve to
+    1e-8 on SAMPLE_MG (fp64 multigrid, f = the workload's Fourier field).
+    Runs in a child process of bench.py (--oracle-timings)."""
+    from oracle import mesh as omesh, mg as omg, space as ospace
 
+    t0 = time.perf_counter()
     s = ospace.Space(omesh.build_mesh(SAMPLE), WORKLOAD.degree)
     x = synth.point_values(s.free_coordinates(), 1)
     s.apply(x)
-    reps, t0 = 0, time.perf_counter()
+    reps, t = 0, time.perf_counter()
     while True:
         s.apply(x)
         reps += 1
-        el = time.perf_counter() - t0
-        if el > seconds:
+        el = time.perf_counter() - t
+        if el > 5.0:
             break
-    cores = os.cpu_count() or 1
-    return {"value": s.n_free * reps / el / 1e9, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
-            "sample": f"fp64 cell-by-cell operator of the oracle on {SAMPLE.name} (Q4, {s.nc} cells, "
-                      f"{s.n_free} free DoFs, 1/8 of the workload), {reps} applications"}
+    out = {"vmult": {"gdofs": s.n_free * reps / el / 1e9, "ms": 1e3 * el / reps, "n_free": s.n_free,
+                     "cells": s.nc, "reps": reps, "mesh": SAMPLE.name}}
+    levels = omg.build_levels(omesh.build_mesh(SAMPLE_MG), WORKLOAD.degree, assembled=False)
+    sp = levels[-1].space
+    f = synth.fourier_rhs(WORKLOAD.rhs_seed)
+    b = sp.rhs(ospace.fourier_function(f))
+    omg.multigrid_vcycle(levels, b)
+    t = time.perf_counter()
+    for _ in range(3):
+        omg.multigrid_vcycle(levels, b)
+    vc = (time.perf_counter() - t) / 3
+    t = time.perf_counter()
+    r = omg.solve(levels, b, 1e-8)
+    cg = time.perf_counter() - t
+    out["vcycle"] = {"ms": 1e3 * vc, "gdofs": sp.n_free / vc / 1e9, "n_free": sp.n_free, "mesh": SAMPLE_MG.name}
+    out["pcg"] = {"ms": 1e3 * cg, "iterations": r.iterations, "gdofs_solved": sp.n_free / cg / 1e9,
+                  "n_free": sp.n_free, "mesh": SAMPLE_MG.name, "rtol": 1e-8}
+    out["threads"] = 1
+    out["seconds"] = time.perf_counter() - t0
+    return out
+
+
+def cpu_baseline_line():
+    """cpu_baseline of the JSON line: the oracle's timings from a child
+    process pinned to one thread."""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-timings"], capture_output=True,
+                       text=True, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                "sample": "oracle timings failed: " + r.stderr.strip().splitlines()[-1][:200]}
+    o = json.loads(r.stdout.strip().splitlines()[-1])
+    v = o["vmult"]
+    return {"value": v["gdofs"], "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"fp64 cell-by-cell operator of the oracle on {v['mesh']} (Q4, {v['cells']} cells, "
+                      f"{v['n_free']} free DoFs, 1/8 of the workload), {v['reps']} applications, one thread "
+                      f"(OMP/OpenBLAS/MKL threads = 1)",
+            "vcycle": o["vcycle"], "pcg": o["pcg"], "seconds": o["seconds"]}
 
 
 class ClockSampler:
@@ -174,14 +242,14 @@ def run_reference(args, rank):
         times.append(time.perf_counter() - t)
     ms = 1e3 * float(np.mean(times))
     value = s.n_free / (ms * 1e-3) / 1e9
-    cores = os.cpu_count() or 1
+    cores = 1  # OMP/OpenBLAS/MKL threads fixed to 1 before numpy was loaded
     line = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": f"oracle sample: {SAMPLE.name}, Q4, {s.nc} cells, {s.n_free} free DoFs "
                                    f"(1/8 of {WORKLOAD.name})"},
             "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
-                             "sample": f"one fp64 operator application per step on {SAMPLE.name}"},
+                             "sample": f"one fp64 operator application per step on {SAMPLE.name}, one thread"},
             "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "setup_s": time.perf_counter() - t0}
     print(json.dumps(finite(line), allow_nan=False), flush=True)
@@ -254,6 +322,91 @@ def run_batch(g, seed: int = 12292, n: int = 256):
     return out
 
 
+def time_solves(mg, b, reps: int = 5):
+    """median time (ms) of reps CG solves to 1e-8 after warm-up, and the last stats"""
+    import torch
+
+    x = torch.zeros_like(b)
+    for _ in range(3):
+        st = mg.cg_solve(b, x, 1e-8, 100)
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(mg.stream)
+        st = mg.cg_solve(b, x, 1e-8, 100)
+        e1.record(mg.stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return float(np.median(times)), st, x
+
+
+def time_vcycle(mg, b, reps: int = 20):
+    """mean time (ms) of one V-cycle (Algorithms 1-2, captured graph) of the handle"""
+    import torch
+
+    x = torch.zeros_like(b)
+    for _ in range(3):
+        mg.vcycle(b, x)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(mg.stream)
+    for _ in range(reps):
+        mg.vcycle(b, x)
+    e1.record(mg.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def per_level_profile(g, mg, b):
+    """one profiled solve: per level the stage times (ms) and the finest operator's mean time"""
+    import torch
+
+    x = torch.zeros_like(b)
+    mg.set_profiling(True)
+    mg.cg_solve(b, x, 1e-8, 100)
+    torch.cuda.synchronize()
+    rows = []
+    for l in range(mg.num_levels):
+        row = {"level": l, "n_free": mg.n_free(l), "cells": mg.level_info(l).n_cells,
+               "degree": mg.level_info(l).degree}
+        for s_ in ("vmult", "presmooth", "residual", "restrict", "coarse", "prolongate", "postsmooth"):
+            row[s_ + "_ms"] = mg.profile(l, s_)[1]
+        rows.append(row)
+    cnt, vms = mg.profile(mg.finest, "vmult")
+    mg.set_profiling(False)
+    return rows, (vms / cnt if cnt else None)
+
+
+def run_other_config(g, w, hbm):
+    """the same path on another workload of the configuration list: solve to
+    1e-8 with the fp32 V-cycle and with the fp64 V-cycle, finest operator
+    throughput, per-level times"""
+    mesh = g.Mesh.from_recipe(w.recipe)
+    out = {"workload": w.name, "degree": w.degree, "p_coarsening": bool(w.p_coarsening), "rhs": "f = 1"}
+    for fp32 in (True, False):
+        mg = g.Multigrid(mesh, w.degree, p_coarsening=w.p_coarsening, mg_fp32=fp32)
+        b = mg.rhs()
+        ms, st, _ = time_solves(mg, b)
+        key = "mixed" if fp32 else "fp64"
+        out[key + "_ms"] = ms
+        out[key + "_iterations"] = st.iterations
+        out[key + "_rel_residual"] = st.rel_residual
+        rows, t_vm = per_level_profile(g, mg, b)
+        n = mg.n_free(mg.finest)
+        out["n_free"] = n
+        out["cells"] = mg.level_info(mg.finest).n_cells
+        out["levels"] = mg.num_levels
+        out[key + "_vmult_ms"] = t_vm
+        out[key + "_vmult_gdofs"] = n / (t_vm * 1e-3) / 1e9 if t_vm else None
+        if fp32 and t_vm:
+            out["fp32_vmult_hbm_frac"] = BYTES_PER_DOF["fp32"] * n / (t_vm * 1e-3) / 1e9 / hbm
+        out[key + "_per_level"] = rows
+        del mg
+    out["speedup_mixed_vs_fp64"] = out["fp64_ms"] / out["mixed_ms"]
+    out["fp64_arithmetic"] = "fp64 CG and vectors; operators in double-float (two fp32, about 48-bit significand)"
+    return out
+
+
 def finite(v):
     """The JSON line with non-finite numbers (a diverged variant) as null."""
     if isinstance(v, float):
@@ -276,7 +429,12 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-graphs", action="store_true",
                     help="stream launches instead of CUDA graphs (for per-kernel profiler launch lists)")
+    ap.add_argument("--no-configs", action="store_true", help="skip the Q2 octant and Q4 sphere workloads")
+    ap.add_argument("--oracle-timings", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_timings:
+        print(json.dumps(oracle_timings()), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -309,7 +467,10 @@ def main():
     # cpu baseline first (no GPU work in flight), rank 0 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_vmult_sample()
+        cpu = cpu_baseline_line()
+    # measured CUDA-core peaks (fp32, native fp64): denominators of the ALU fractions
+    fma = {"fp32_tflops": g.fma_peak(False, 1 << 20), "fp64_tflops": g.fma_peak(True, 1 << 15),
+           "how": "gcmg_fma_peak: 8 independent multiply-add chains per thread, 2048 threads per SM, CUDA events"}
 
     t0 = time.perf_counter()
     mesh = g.Mesh.from_recipe(WORKLOAD.recipe)
@@ -374,6 +535,7 @@ def main():
                 row["vmult_calls"] = c_
         per_level.append(row)
     mg.set_profiling(False)
+    t_vc = time_vcycle(mg, b)
     t_vmult = vms / cnt  # ms
     value = n / (t_vmult * 1e-3) / 1e9
     value64 = n / (vms64 / cnt64 * 1e-3) / 1e9
@@ -419,7 +581,15 @@ def main():
         batch = run_batch(g)
 
     hbm, peak_kind = peaks()
+    configs = None
+    if not args.no_configs:
+        configs = {"q2_octant": run_other_config(g, synth.WORKLOAD_Q2_OCTANT, hbm),
+                   "q4_sphere_p": run_other_config(g, synth.WORKLOAD_Q4_SPHERE, hbm)}
     achieved = BYTES_PER_DOF["fp32"] * n / (t_vmult * 1e-3) / 1e9
+    cells = mg.level_info(L).n_cells
+    fpc = flops_per_cell(WORKLOAD.degree)
+    tflops32 = fpc * cells / (t_vmult * 1e-3) / 1e12
+    tflops64 = fpc * cells / (vms64 / cnt64 * 1e-3) / 1e12
     traffic = VMULT_TRAFFIC_BYTES if VMULT_TRAFFIC_BYTES > 0 else None
     if rank == 0:
         res = {
@@ -432,11 +602,21 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": "vmult_lines<4,float,4> line-parallel tile kernel + halo pass "
+                         "kernel": "vmult_lanes<4> one-lane-per-cell tile kernel + halo_add_kernel<float> "
                                    "(fine-level fp32 operator, 32-cell tiles)",
                          "peak_kind": peak_kind, "bytes_per_dof": BYTES_PER_DOF["fp32"],
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the tile kernel "
-                                           "and the halo pass, one application on this workload"},
+                                           "and the halo pass, one application on this workload, caches "
+                                           "flushed before each kernel",
+                         "alu_frac": tflops32 / fma["fp32_tflops"], "alu_achieved_tflops": tflops32,
+                         "alu_peak_tflops": fma["fp32_tflops"], "alu_peak_kind": "measured (gcmg_fma_peak, fp32)",
+                         "flop_per_cell": fpc},
+            "alu_peaks": fma,
+            "vcycle": {"ms": t_vc, "gdofs": n / (t_vc * 1e-3) / 1e9, "bytes_per_dof": VCYCLE_BYTES_PER_DOF,
+                       "roofline_gdofs": hbm / VCYCLE_BYTES_PER_DOF,
+                       "frac": n / (t_vc * 1e-3) / 1e9 / (hbm / VCYCLE_BYTES_PER_DOF),
+                       "what": "one fp32 V-cycle of the finest level (Algorithms 1-2, captured graph), "
+                               "including the fp64 <-> fp32 copies"},
             "cpu_baseline": cpu,
             "e2e": {"value": n / e2e_s / 1e9, "unit": "GDoF/s", "h2d_bytes_per_step": 4 * n,
                     "d2h_bytes_per_step": 4 * n, "call": "gcmg_vmult_host, pinned host buffers, fp32"},
@@ -445,9 +625,18 @@ def main():
             "solve": {"mixed_ms": ms_step, "mixed_iterations": iters[-1], "mixed_rel_residual": st.rel_residual,
                       "fp64_ms": fp64_ms, "fp64_iterations": st64.iterations,
                       "fp64_rel_residual": st64.rel_residual, "speedup_mixed_vs_fp64": fp64_ms / ms_step,
-                      "solution_rel_diff_mixed_vs_fp64": sol_diff},
-            "vmult": {"fp32_ms": t_vmult, "fp32_gdofs": value / world, "fp64_ms": vms64 / cnt64,
-                      "fp64_gdofs": value64},
+                      "solution_rel_diff_mixed_vs_fp64": sol_diff,
+                      "fp64_arithmetic": "fp64 CG, fp64 vectors on every level; the operators in double-float "
+                                         "(two fp32 per value, about 48-bit significand)"},
+            "vmult": {"fp32_ms": t_vmult, "fp32_gdofs": value / world, "fp32_tflops": tflops32,
+                      "fp64_ms": vms64 / cnt64, "fp64_gdofs": value64,
+                      "fp64_arithmetic": "double-float (two fp32 per value, about 48-bit significand), fp64 "
+                                         "vectors in and out, on the FP32 pipe",
+                      "fp64_equiv_tflops": tflops64,
+                      "fp64_frac_of_native_fp64_peak": tflops64 / fma["fp64_tflops"],
+                      "fp64_frac_of_fp32_peak": tflops64 / fma["fp32_tflops"],
+                      "fp64_hbm_frac": BYTES_PER_DOF["fp64"] * value64 / hbm},
+            "configs": configs,
             "stage_ms_per_step_finest": stage_ms, "coarser_levels_ms_per_step": coarse_ms,
             "per_level_ms_per_step": per_level,
             "setup_s": setup_s,

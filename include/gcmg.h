@@ -499,6 +499,18 @@ const char* gcmg_last_error(void);
 /* number of CUDA kernel launches issued by this library since it was loaded */
 int64_t gcmg_launch_count(void);
 
+/*
+ * Measurement utility (not part of the method; the paper has none): the
+ * peak arithmetic rate of the CUDA cores of the current device in TFLOP/s
+ * (a fused multiply-add counts two), fp32 (fp64 = 0) or native fp64
+ * (fp64 = 1).  One kernel of `iters` (>= 16) steps of 8 independent
+ * multiply-add chains per thread, 2048 threads per SM, timed with CUDA
+ * events on `stream` after a short warm-up launch; synchronises the
+ * stream.  It is the denominator of the ALU fractions of the operator
+ * kernels.  Allocates one small device buffer for the duration of the call.
+ */
+int gcmg_fma_peak(int fp64, int iters, void* stream, double* tflops);
+
 #ifdef __cplusplus
 }
 #endif

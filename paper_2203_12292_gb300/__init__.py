@@ -65,6 +65,7 @@ class Tuning(ctypes.Structure):
 _SIGS = {
     "gcmg_last_error": (ctypes.c_char_p, []),
     "gcmg_launch_count": (_c_int64, []),
+    "gcmg_fma_peak": (_c_int, [_c_int, _c_int, _c_void_p, ctypes.POINTER(_c_double)]),
     "gcmg_mesh_create": (_c_int, [_c_double, _c_double, _c_int, ctypes.POINTER(RefineStep), ctypes.POINTER(_c_void_p)]),
     "gcmg_mesh_destroy": (None, [_c_void_p]),
     "gcmg_mesh_num_levels": (_c_int, [_c_void_p, ctypes.POINTER(_c_int)]),
@@ -152,6 +153,16 @@ def lib() -> ctypes.CDLL:
 def launch_count() -> int:
     """Kernel launches issued by libgcmg so far."""
     return int(lib().gcmg_launch_count())
+
+
+def fma_peak(fp64: bool, iters: int = 1 << 16) -> float:
+    """Measured peak of the CUDA cores of the current device in TFLOP/s
+    (fp32, or native fp64), on the current torch stream."""
+    import torch
+    out = _c_double()
+    _check(lib().gcmg_fma_peak(int(fp64), iters, _c_void_p(torch.cuda.current_stream().cuda_stream),
+                               ctypes.byref(out)))
+    return out.value
 
 
 def exported_symbols() -> Sequence[str]:

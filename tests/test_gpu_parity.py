@@ -10,8 +10,9 @@ Tolerances (relative 2-norm):
   solve: 1e-12 (sum-factorised vs assembled fp64: rounding differences of a
   few hundred operations, far below 1e-12);
 * fp64 V-cycle: 1e-10 (all levels chained);
-* fp32 operator: 2e-6 (unit roundoff 6e-8 times the depth of the sweep
-  chain, see DESIGN.md);
+* fp32 operator: 2e-6 (unit roundoff 6e-8 times a chain of about 30
+  dependent roundings through the gather, six sweeps, the scaling and the
+  accumulation);
 * CG: same iteration count as the oracle and ||b - A x|| / ||b|| <= rtol,
   evaluated with the oracle's own operator and right-hand side.
 """
