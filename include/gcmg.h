@@ -99,12 +99,13 @@ typedef struct {
   int tile_cells;          /* cells per tile on large levels, 0 = default (32);
                               levels with fewer than 2 * 152 tiles of that
                               size use halved tiles (down to 8 cells) */
-  int cell_kernel;         /* fp32 operator kernel: 0 = default (one lane per
-                              cell on levels with tiles of at most 32 cells,
+  int cell_kernel;         /* operator kernel: 0 = default (one lane per cell
+                              on levels with 32-cell tiles, fp32 and fp64;
                               else line-parallel), 1 = line-parallel (one
                               thread per 1D line of a cell), 2 = slab threads
-                              (k+1 threads per cell, z-slabs in registers;
-                              tiles <= 64 cells), 3 = one lane per cell */
+                              (fp32, k+1 threads per cell, z-slabs in
+                              registers; tiles <= 64 cells), 3 = one lane per
+                              cell on every level with tiles of <= 32 cells */
   int cell_threads;        /* threads per CTA of the line-parallel fp32 operator:
                               0 = default (256), 128, 256, 384 or 512 */
   int local_smoothing;     /* 1: geometric local smoothing instead of global
@@ -460,11 +461,17 @@ typedef struct {
 /*
  * Autotuner of the operator: for one degree, times the finest-level
  * operator (fp32 when mg_fp32, else fp64) on the probe mesh for every
- * candidate tile size (32, 64, 128 cells) and thread mapping (slab threads
- * per cell, line-parallel) over `reps` applications with CUDA events and
- * returns the fastest in *best; all (optional, >= 5 entries) and n_all get
- * every candidate.  Synchronises `stream`.
+ * candidate configuration over `reps` applications with CUDA events and
+ * returns the fastest in *best; all (optional, GCMG_AUTOTUNE_MAX entries)
+ * and n_all get every candidate.  Candidates (tile cells, cell_kernel,
+ * cell_threads): the default; one lane per cell on 8-, 16- and 32-cell
+ * tiles; one thread per line on 8- to 128-cell tiles (256 or 512 threads
+ * for tiles above 32 cells); slab threads on 16- to 64-cell tiles (fp32).
+ * The probe's finest level needs at least 2 x SMs x 128 cells, or the
+ * larger tile sizes are halved like on any small level.  Synchronises
+ * `stream`.
  */
+#define GCMG_AUTOTUNE_MAX 16
 int gcmg_autotune(const gcmg_mesh* probe, int degree, int mg_fp32, int reps, void* stream, gcmg_tuning* best,
                   gcmg_tuning* all, int* n_all);
 /*

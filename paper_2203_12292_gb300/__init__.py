@@ -606,7 +606,7 @@ def autotune(probe: Mesh, degree: int, mg_fp32: bool = True, reps: int = 20):
     """(best, all candidates) of the operator autotuner for one degree."""
     import torch
     best = Tuning()
-    allc = (Tuning * 8)()
+    allc = (Tuning * 16)()  # GCMG_AUTOTUNE_MAX
     n = _c_int()
     _check(lib().gcmg_autotune(probe._p, degree, int(mg_fp32), reps, _c_void_p(torch.cuda.current_stream().cuda_stream),
                                ctypes.byref(best), allc, ctypes.byref(n)))

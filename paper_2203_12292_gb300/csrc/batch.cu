@@ -230,10 +230,18 @@ int gcmg_autotune(const gcmg_mesh* probe, int degree, int mg_fp32, int reps, voi
   return guarded([&] {
     if (!probe || !best || degree < 1 || degree > KMAX || reps < 1) throw Error(GCMG_ERR_ARG, "bad arguments");
     upload_all_tables();
-    // candidates: tile size x thread mapping (the slab mapping needs tiles of <= 64 cells)
-    const int cand[5][2] = {{32, 2}, {64, 2}, {32, 1}, {64, 1}, {128, 1}};
-    const int nc = mg_fp32 ? 5 : 3;  // fp64 always runs the line-parallel kernel
-    const int (*list)[2] = mg_fp32 ? cand : cand + 2;
+    // candidates (tile cells, kernel, threads): the default (one lane per cell on 32-cell tiles), one lane
+    // per cell on 8/16/32-cell tiles, one thread per line on 8..128-cell tiles (lines per thread follow
+    // from the tile size; 256 or 512 threads for the chunked kernel of tiles above 32 cells), slab
+    // threads on 16..64-cell tiles (fp32 only).  The probe's finest level must keep every size
+    // (at least 2 x SMs x 128 cells).
+    static const int c32[][3] = {{32, 0, 0},   {8, 3, 0},   {16, 3, 0},  {32, 3, 0},  {8, 1, 0},
+                                 {16, 1, 0},   {32, 1, 0},  {64, 1, 256}, {64, 1, 512}, {128, 1, 256},
+                                 {128, 1, 512}, {16, 2, 0}, {32, 2, 0},  {64, 2, 0}};
+    static const int c64[][3] = {{32, 0, 0}, {8, 1, 0}, {16, 1, 0}, {32, 1, 0}, {64, 1, 0}, {128, 1, 0}};
+    const int nc = mg_fp32 ? (int)(sizeof(c32) / sizeof(c32[0])) : (int)(sizeof(c64) / sizeof(c64[0]));
+    static_assert(sizeof(c32) / sizeof(c32[0]) <= GCMG_AUTOTUNE_MAX, "candidate list");
+    const int (*list)[3] = mg_fp32 ? c32 : c64;
     gcmg_tuning top{degree, 0, 0, 0, -1.0};
     for (int c = 0; c < nc; ++c) {
       gcmg_config cfg;
@@ -242,6 +250,7 @@ int gcmg_autotune(const gcmg_mesh* probe, int degree, int mg_fp32, int reps, voi
       cfg.mg_fp32 = mg_fp32;
       cfg.tile_cells = list[c][0];
       cfg.cell_kernel = list[c][1];
+      cfg.cell_threads = list[c][2];
       Handle H;
       H.stream = static_cast<cudaStream_t>(stream);
       setup_handle(H, probe->levels, probe->lmax, cfg);

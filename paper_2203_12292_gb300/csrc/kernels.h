@@ -73,6 +73,9 @@ void launch_vmult_tiles(const CellLaunch& L, bool fp64, const void* src, void* d
 // the level has its metadata (tiles of at most 32 cells, Cartesian cells)
 bool lanes_ok(const CellLaunch& L);
 void launch_vmult_lanes(const CellLaunch& L, const void* src, void* dst, int add, int t0, int t1, cudaStream_t s);
+// the fp64 operator (double-float arithmetic) with the same structure
+void launch_vmult_lanes_df(const CellLaunch& L, const double* src, double* dst, int add, int t0, int t1,
+                           cudaStream_t s);
 void upload_tables_lanes();
 // dst = C^T F: Gauss quadrature of f against the basis (FOURIER, ONE: f
 // itself; GAUSSIAN, POLYNOMIAL: f = -Lap u of the manufactured solution u)

@@ -1497,6 +1497,11 @@ void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
   }
   const size_t sm = smem_layout<T>((K + 1) * (K + 1) * (K + 1), L.tc, L.max_local).total;
   if constexpr (MODE == MODE_VMULT && sizeof(T) == 8) {
+    if (L.use_lanes && lanes_ok(L)) {  // one lane per cell, double-float arithmetic (default)
+      launch_vmult_lanes_df(L, A.src, A.dst, A.add, 0, L.n_tiles, s);
+      run_halo<T>(L, A.dst, s);
+      return;
+    }
     if (L.tc <= CHUNK) {  // fp64 operator: double-float arithmetic on the FP32 pipe
       const size_t sm1 = sm - (size_t)L.max_local * sizeof(T);
       ensure_smem(vmult_lines_df<K>, sm1);
@@ -1613,7 +1618,7 @@ void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, in
 }
 
 bool vmult_tiles_ok(const CellLaunch& L, bool fp64) {
-  if (!fp64 && L.use_lanes && lanes_ok(L)) return true;
+  if (L.use_lanes && lanes_ok(L)) return true;
   return L.tc <= CHUNK && !L.geom && (fp64 || (L.use_lines && L.threads == BLOCK));
 }
 
@@ -1621,6 +1626,10 @@ void launch_vmult_tiles(const CellLaunch& L, bool fp64, const void* src, void* d
   if (t1 <= t0 || !vmult_tiles_ok(L, fp64)) return;
   const int n3 = (L.k + 1) * (L.k + 1) * (L.k + 1);
   if (fp64) {
+    if (L.use_lanes && lanes_ok(L)) {
+      launch_vmult_lanes_df(L, static_cast<const double*>(src), static_cast<double*>(dst), 0, t0, t1, s);
+      return;
+    }
     CellArgs<double> A = make_args<double>(L);
     A.src = static_cast<const double*>(src);
     A.dst = static_cast<double*>(dst);

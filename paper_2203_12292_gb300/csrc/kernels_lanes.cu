@@ -56,20 +56,22 @@ struct LaneLines {
 };
 __constant__ LaneLines c_ll;
 
-struct LaneArgs {
+template <typename T>
+struct LaneArgsT {
   const TileInfo* tiles;
   const LaneTile* lt;
   const int32_t* order;  // tile of block b: order[b] (null: tile0 + b)
   const int32_t* foreign;
   const int32_t* halo_pos;
-  const float* src;
-  float* dst;
-  float* halo;
+  const T* src;
+  T* dst;
+  T* halo;
   const double* coef;  // per cell nu_e, null: 1
   double dom;
   int add;
   int tile0;
 };
+using LaneArgs = LaneArgsT<float>;
 
 template <int K>
 struct LaneGeom {
@@ -427,6 +429,338 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
   for (int i = threadIdx.x; i < ti.n_foreign; i += NT) A.halo[hp[i]] = xs[ti.n_owned + i];
 }
 
+// ---------------------------------------------------------------------------
+// fp64 operator (the CG operator of the mixed solve and every level of the
+// fp64 multigrid) with the same lane-per-cell structure: fp64 vectors in and
+// out, all arithmetic in double-float (hi + lo floats, about 48 significand
+// bits: error-free two-sum and fused product error, the fp64 tables split
+// into high and low parts), on the FP32 pipe, which GB300 has many times
+// wider than its FP64 pipe.  Values are converted once on entry to and once
+// on exit from the tile; the cell buffer and the accumulator hold df pairs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ df df_sel(bool p, df a, df b) { return df{p ? a.hi : b.hi, p ? a.lo : b.lo}; }
+
+// sum_j x_j c_j over T double-float values and double-float constants
+// (ch + cl) with one normalisation: the high products p_j = x_j.hi ch_j carry
+// their exact rounding errors (fused multiply-add), the p_j are summed by
+// error-free two-sums, and the low-order terms (product errors, cross terms
+// x.hi cl and x.lo ch, two-sum errors) go into one fp32 sum; 12 T - 5
+// operations instead of 18 T - 11 for a chain of df_fma
+template <int T>
+__device__ __forceinline__ df df_dot(const df* x, const float* ch, const float* cl) {
+  float S = __fmul_rn(x[0].hi, ch[0]);
+  float L = __fmaf_rn(x[0].hi, cl[0], __fmaf_rn(x[0].lo, ch[0], __fmaf_rn(x[0].hi, ch[0], -S)));
+#pragma unroll
+  for (int j = 1; j < T; ++j) {
+    const float p = __fmul_rn(x[j].hi, ch[j]);
+    const float l = __fmaf_rn(x[j].hi, cl[j], __fmaf_rn(x[j].lo, ch[j], __fmaf_rn(x[j].hi, ch[j], -p)));
+    const float s = __fadd_rn(S, p);
+    const float z = __fsub_rn(s, S);
+    const float t = __fadd_rn(__fsub_rn(S, __fsub_rn(s, z)), __fsub_rn(p, z));
+    S = s;
+    L = __fadd_rn(L, __fadd_rn(l, t));
+  }
+  return df_norm(S, L);
+}
+
+// even-odd forward transform with B (nodal -> modes in mode order) and its
+// backward transform, in double-float, rows as df_dot
+template <int K>
+__device__ __forceinline__ void df_eo_fwd_fast(df* u) {
+  constexpr int N = K + 1, NH = N / 2, NE = (N + 1) / 2;
+  const float(&Bh)[NMAX][NMAX] = c_tf[K].Be;
+  const float(&Bl)[NMAX][NMAX] = c_tflo[K].Be;
+  df e[NE], o[NH > 0 ? NH : 1];
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    e[j] = df_add(u[j], u[N - 1 - j]);
+    o[j] = df_sub(u[j], u[N - 1 - j]);
+  }
+  if (N % 2) e[NH] = u[NH];
+#pragma unroll
+  for (int r = 0; r < NE; ++r) u[r] = df_dot<NE>(e, Bh[r], Bl[r]);
+#pragma unroll
+  for (int r = 0; r < NH; ++r) u[NE + r] = df_dot<NH>(o, Bh[NE + r], Bl[NE + r]);
+}
+
+template <int K>
+__device__ __forceinline__ void df_eo_bwd_fast(df* u) {
+  constexpr int N = K + 1, NH = N / 2, NE = (N + 1) / 2;
+  df E[NE], O[NH > 0 ? NH : 1];
+  float ch[NMAX], cl[NMAX];
+#pragma unroll
+  for (int j = 0; j < NE; ++j) {
+#pragma unroll
+    for (int r = 0; r < NE; ++r) {
+      ch[r] = c_tf[K].Be[r][j];
+      cl[r] = c_tflo[K].Be[r][j];
+    }
+    E[j] = df_dot<NE>(u, ch, cl);
+  }
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+#pragma unroll
+    for (int r = 0; r < NH; ++r) {
+      ch[r] = c_tf[K].Be[NE + r][j];
+      cl[r] = c_tflo[K].Be[NE + r][j];
+    }
+    O[j] = df_dot<NH>(u + NE, ch, cl);
+  }
+#pragma unroll
+  for (int j = 0; j < NH; ++j) {
+    u[j] = df_add(E[j], O[j]);
+    u[N - 1 - j] = df_sub(E[j], O[j]);
+  }
+  if (N % 2) u[NH] = E[NH];
+}
+
+// I_p (TRANS: transposed) on one df line, by the mirror identity of interp_line_reg
+template <int K, bool TRANS>
+__device__ __forceinline__ void interp_line_df(df* v, int p) {
+  constexpr int N = K + 1;
+  const float(&Ih)[NMAX][NMAX] = c_tf[K].I[0];
+  const float(&Il)[NMAX][NMAX] = c_tflo[K].I[0];
+  df x[N], y[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) x[a] = df_sel(p, v[K - a], v[a]);
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    df s{0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < N; ++a) s = TRANS ? df_fma(s, x[a], Ih[a][r], Il[a][r]) : df_fma(s, x[a], Ih[r][a], Il[r][a]);
+    y[r] = s;
+  }
+#pragma unroll
+  for (int a = 0; a < N; ++a) v[a] = df_sel(p, y[K - a], y[a]);
+}
+
+template <int K, int D, bool TRANS, bool SWEEP = false>
+__device__ __forceinline__ void hang_pass_df(df* cb, uint16_t m, int w, int lane) {
+  constexpr int N = K + 1, N2 = N * N;
+  constexpr int S = (D == 0 ? 1 : (D == 1 ? N : N2)) * 32;
+  const int p = (m >> D) & 1;
+#pragma unroll 1
+  for (int i = 0; i < N; ++i) {
+    const int q = i + N * w;
+    const int u = q % N, v = q / N;
+    const bool hl = line_hangs<K, D>(m, u, v);
+    if (!SWEEP && !hl) continue;
+    const int base = D == 0 ? N * u + N2 * v : (D == 1 ? u + N2 * v : u + N * v);
+    df* ptr = cb + base * 32 + lane;
+    df x[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) x[a] = ptr[a * S];
+    if (SWEEP && TRANS) df_eo_bwd_fast<K>(x);
+    if (hl) interp_line_df<K, TRANS>(x, p);
+    if (SWEEP && !TRANS) df_eo_fwd_fast<K>(x);
+#pragma unroll
+    for (int a = 0; a < N; ++a) ptr[a * S] = x[a];
+  }
+}
+
+template <int K, bool FWD>
+__device__ __forceinline__ void sweep_y_df(df* cb, int w, int lane) {
+  constexpr int N = K + 1, N2 = N * N;
+#pragma unroll 1
+  for (int i = 0; i < N; ++i) {
+    df* p = cb + (i + N2 * w) * 32 + lane;
+    df v[N];
+#pragma unroll
+    for (int b = 0; b < N; ++b) v[b] = p[b * N * 32];
+    if (FWD)
+      df_eo_fwd_fast<K>(v);
+    else
+      df_eo_bwd_fast<K>(v);
+#pragma unroll
+    for (int b = 0; b < N; ++b) p[b * N * 32] = v[b];
+  }
+}
+
+// forward sweep, h (lam_a + lam_b + lam_c) in mode order, backward sweep on the
+// lines along direction D (2: z-lines (a, b) = (i, w); 0: x-lines (b, c) = (i, w))
+template <int K, int D>
+__device__ __forceinline__ void sweep_scale_df(df* cb, int w, int lane, df h) {
+  constexpr int N = K + 1, N2 = N * N;
+  constexpr int S = (D == 0 ? 1 : N2) * 32;
+#pragma unroll 1
+  for (int i = 0; i < N; ++i) {
+    df* p = cb + (D == 0 ? N * (i + N * w) : i + N * w) * 32 + lane;
+    df v[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] = p[c * S];
+    df_eo_fwd_fast<K>(v);
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      // mode index of the node: along D the line index c, the others (i, w)
+      const int idx = D == 0 ? c + N * i + N2 * w : i + N * w + N2 * c;
+      v[c] = df_mul(v[c], df_mul(df{c_tf[K].lam3[idx], c_tflo[K].lam3[idx]}, h));
+    }
+    df_eo_bwd_fast<K>(v);
+#pragma unroll
+    for (int c = 0; c < N; ++c) p[c * S] = v[c];
+  }
+}
+
+__device__ __forceinline__ void add_ordered_df(df* x, df v, bool real, int lane, bool hang_any) {
+  if (!hang_any) {
+    *x = df_add(*x, v);
+    return;
+  }
+  const unsigned key = real ? (unsigned)__cvta_generic_to_shared(x) : ~(unsigned)lane;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  const int rank = __popc(peers & ((1u << lane) - 1u));
+  const int most = __reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
+  for (int q = 0; q < most; ++q) {
+    if (real && rank == q) *x = df_add(*x, v);
+    __syncwarp();
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__((K + 1) * 32) vmult_lanes_df(LaneArgsT<double> A) {
+  pdl_begin();
+  constexpr int N = K + 1, N3 = N * N * N, NT = N * 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  LaneTile* st = reinterpret_cast<LaneTile*>(smem);
+  df* cb = reinterpret_cast<df*>(smem + sizeof(LaneTile));
+  double* xd0 = reinterpret_cast<double*>(cb + N3 * 32);  // 16-byte aligned
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tile = A.order ? A.order[blockIdx.x] : A.tile0 + blockIdx.x;
+  const TileInfo ti = A.tiles[tile];
+  const int nloc = ti.n_owned + ti.n_foreign;
+  // tile DoF i at xd[i] (fp64 on arrival, then df in place; the zero region after it)
+  const double* so = A.src + ti.dof_begin;
+  const int sh = (int)((reinterpret_cast<uintptr_t>(so) >> 3) & 1);
+  double* xd = xd0 + sh;
+  df* xs = reinterpret_cast<df*>(xd);
+  const int h0 = min(sh, ti.n_owned), nv = (ti.n_owned - h0) >> 1;
+  {
+    const uint4* g = reinterpret_cast<const uint4*>(A.lt + tile);
+    uint4* s = reinterpret_cast<uint4*>(st);
+    for (int i = threadIdx.x; i < (int)(sizeof(LaneTile) / 16); i += NT) cp_async16(s + i, g + i);
+    if (threadIdx.x < h0) cp_async(xd + threadIdx.x, so + threadIdx.x);
+#pragma unroll 4
+    for (int j = threadIdx.x; j < nv; j += NT) cp_async16(xd + h0 + 2 * j, so + h0 + 2 * j);
+    for (int i = h0 + 2 * nv + threadIdx.x; i < ti.n_owned; i += NT) cp_async(xd + i, so + i);
+    const int32_t* fl = A.foreign + ti.foreign_begin;
+    double* xf = xd + ti.n_owned;
+    for (int i0 = threadIdx.x; i0 < ti.n_foreign; i0 += 4 * NT) {
+      int idx[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) idx[u] = (i0 + u * NT < ti.n_foreign) ? fl[i0 + u * NT] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (idx[u] >= 0) cp_async(xf + i0 + u * NT, A.src + idx[u]);
+    }
+  }
+  if (threadIdx.x < LANE_ZERO) xs[nloc + threadIdx.x] = df{0.f, 0.f};
+  cp_async_wait_all();
+  __syncthreads();
+  for (int i = threadIdx.x; i < nloc; i += NT) xs[i] = df_from(xd[i]);  // one thread per element: in place
+  const uint16_t m = st->mask[lane];
+  const bool hang = st->hang != 0;
+  df h;
+  {
+    const int c = ti.cell_begin + min(lane, ti.n_cells - 1);
+    const double hd = ldexp(A.dom, -(int)st->level[lane]);
+    h = df_from(A.coef ? hd * A.coef[c] : hd);
+  }
+  char* xb = reinterpret_cast<char*>(xs);
+  const int nxl = c_ll.nx[K][w];
+  __syncthreads();
+
+  // G_e (+ C_x on hanging tiles, else the forward x sweep)
+#pragma unroll 1
+  for (int i = 0; i < nxl; ++i) {
+    const int r = c_ll.xw[K][w][i];
+    const uint32_t li = c_ll.line[K][r];
+    const int s0 = li & 0xff, o0 = (li >> 8) & 0xff, o1 = li >> 16;
+    const df* p0 = reinterpret_cast<const df*>(xb + 2 * (st->ls[s0][lane] + o0));
+    const df* p1 = reinterpret_cast<const df*>(xb + 2 * (st->ls[s0 + 1][lane] + o1));
+    const df* p2 = reinterpret_cast<const df*>(xb + 2 * (st->ls[s0 + 2][lane] + o0));
+    df v[N];
+    v[0] = *p0;
+#pragma unroll
+    for (int a = 1; a < K; ++a) v[a] = p1[a - 1];
+    v[K] = *p2;
+    if (!hang)
+      df_eo_fwd_fast<K>(v);
+    else if (line_hangs<K, 0>(m, r % N, r / N))
+      interp_line_df<K, false>(v, m & 1);
+    df* p = cb + N * r * 32 + lane;
+#pragma unroll
+    for (int a = 0; a < N; ++a) p[a * 32] = v[a];
+  }
+  __syncthreads();
+  if (hang) {
+    hang_pass_df<K, 1, false>(cb, m, w, lane);  // C_y
+    __syncthreads();
+    hang_pass_df<K, 2, false, true>(cb, m, w, lane);  // C_z, forward z sweep
+    __syncthreads();
+  }
+  {  // the tile DoFs are dead: clear the accumulator
+    float4* z4 = reinterpret_cast<float4*>(xd0);
+    for (int i = threadIdx.x; i < (sh + nloc + 1) / 2; i += NT) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  sweep_y_df<K, true>(cb, w, lane);
+  __syncthreads();
+  if (!hang)
+    sweep_scale_df<K, 2>(cb, w, lane, h);
+  else
+    sweep_scale_df<K, 0>(cb, w, lane, h);
+  __syncthreads();
+  sweep_y_df<K, false>(cb, w, lane);
+  __syncthreads();
+  if (hang) {
+    hang_pass_df<K, 2, true, true>(cb, m, w, lane);  // backward z sweep, C_z^T
+    __syncthreads();
+    hang_pass_df<K, 1, true>(cb, m, w, lane);  // C_y^T
+    __syncthreads();
+  }
+  // backward x sweep (tiles without hanging cells) or C_x^T, then G_e^T on the warp's class of x-lines
+  const uint32_t hs = hang ? hanging_slot_set(m) : 0u;
+  const int zb = nloc * 4;
+#pragma unroll 1
+  for (int i = 0; i < nxl; ++i) {
+    const int r = c_ll.xw[K][w][i];
+    const df* p = cb + N * r * 32 + lane;
+    df v[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) v[a] = p[a * 32];
+    if (!hang)
+      df_eo_bwd_fast<K>(v);
+    else if (line_hangs<K, 0>(m, r % N, r / N))
+      interp_line_df<K, true>(v, m & 1);
+    const uint32_t li = c_ll.line[K][r];
+    const int s0 = li & 0xff, o0 = (li >> 8) & 0xff, o1 = li >> 16;
+    const int b0 = st->ls[s0][lane], b1 = st->ls[s0 + 1][lane], b2 = st->ls[s0 + 2][lane];
+    df* q0 = reinterpret_cast<df*>(xb + 2 * (b0 + o0));
+    df* q1 = reinterpret_cast<df*>(xb + 2 * (b1 + o1));
+    df* q2 = reinterpret_cast<df*>(xb + 2 * (b2 + o0));
+    if (!hang) {
+      *q0 = df_add(*q0, v[0]);
+#pragma unroll
+      for (int a = 1; a < K; ++a) q1[a - 1] = df_add(q1[a - 1], v[a]);
+      *q2 = df_add(*q2, v[K]);
+    } else {
+      const bool g0 = __any_sync(0xffffffffu, (hs >> s0) & 1u), g1 = __any_sync(0xffffffffu, (hs >> (s0 + 1)) & 1u),
+                 g2 = __any_sync(0xffffffffu, (hs >> (s0 + 2)) & 1u);
+      add_ordered_df(q0, v[0], b0 != zb, lane, g0);
+#pragma unroll
+      for (int a = 1; a < K; ++a) add_ordered_df(q1 + a - 1, v[a], b1 != zb, lane, g1);
+      add_ordered_df(q2, v[K], b2 != zb, lane, g2);
+    }
+  }
+  __syncthreads();
+  double* d = A.dst + ti.dof_begin;
+  if (A.add)
+    for (int i = threadIdx.x; i < ti.n_owned; i += NT) d[i] += df_to(xs[i]);
+  else
+    for (int i = threadIdx.x; i < ti.n_owned; i += NT) d[i] = df_to(xs[i]);
+  const int32_t* hp = A.halo_pos + ti.foreign_begin;
+  for (int i = threadIdx.x; i < ti.n_foreign; i += NT) A.halo[hp[i]] = df_to(xs[ti.n_owned + i]);
+}
+
 // host: entity slot and offset of local node (a, b, c) of a degree-k cell
 // (the numbering of the level set-up: slot cx + 3 cy + 9 cz, DoFs of an
 // entity lexicographic over its interior axes)
@@ -495,6 +829,22 @@ size_t lanes_smem(int max_local) {
 }
 
 template <int K>
+size_t lanes_df_smem(int max_local) {
+  constexpr int N3 = (K + 1) * (K + 1) * (K + 1);
+  return sizeof(LaneTile) + ((size_t)N3 * 32 + (size_t)max_local + LANE_ZERO + 4) * sizeof(double);
+}
+
+template <int K>
+cudaError_t run_lanes_df(const CellLaunch& L, const LaneArgsT<double>& A, int n_tiles, cudaStream_t s) {
+  const size_t sm = lanes_df_smem<K>(L.max_local);
+  cudaError_t e = smem_allow(vmult_lanes_df<K>, sm);
+  if (e != cudaSuccess) return e;
+  e = launch_pdl(vmult_lanes_df<K>, n_tiles, (K + 1) * 32, sm, s, A);
+  note_launches(1);
+  return e;
+}
+
+template <int K>
 cudaError_t run_lanes(const CellLaunch& L, const LaneArgs& A, int n_tiles, cudaStream_t s) {
   const size_t sm = lanes_smem<K>(L.max_local);
   cudaError_t e = smem_allow(vmult_lanes<K>, sm);
@@ -514,6 +864,31 @@ void upload_tables_lanes() {
 }
 
 bool lanes_ok(const CellLaunch& L) { return L.lane_tiles && L.tc <= 32 && !L.geom && L.k >= 1 && L.k <= KMAX; }
+
+void launch_vmult_lanes_df(const CellLaunch& L, const double* src, double* dst, int add, int t0, int t1,
+                           cudaStream_t s) {
+  if (t1 <= t0 || !lanes_ok(L)) return;
+  LaneArgsT<double> A{};
+  A.tiles = L.tiles;
+  A.lt = static_cast<const LaneTile*>(L.lane_tiles);
+  A.order = (t0 == 0 && t1 == L.n_tiles) ? L.lane_order : nullptr;
+  A.foreign = L.foreign;
+  A.halo_pos = L.halo_pos;
+  A.src = src;
+  A.dst = dst;
+  A.halo = static_cast<double*>(L.halo);
+  A.coef = L.coef;
+  A.dom = L.dom;
+  A.add = add;
+  A.tile0 = t0;
+  switch (L.k) {
+    case 1: run_lanes_df<1>(L, A, t1 - t0, s); break;
+    case 2: run_lanes_df<2>(L, A, t1 - t0, s); break;
+    case 3: run_lanes_df<3>(L, A, t1 - t0, s); break;
+    case 4: run_lanes_df<4>(L, A, t1 - t0, s); break;
+    default: break;
+  }
+}
 
 void launch_vmult_lanes(const CellLaunch& L, const void* src, void* dst, int add, int t0, int t1, cudaStream_t s) {
   if (t1 <= t0 || !lanes_ok(L)) return;

@@ -89,12 +89,13 @@ def test_batch_maxit(batch):
 def test_autotune(gcmg):
     probe = gcmg.Mesh.from_recipe(synth.cube_octant(3, 1))
     best, cands = gcmg.autotune(probe, 2, mg_fp32=True, reps=5)
-    assert len(cands) == 5
+    assert len(cands) == 14  # lane, line and slab mappings over tile sizes 8..128
     assert all(c.gdofs > 0 for c in cands)
     assert best.gdofs == max(c.gdofs for c in cands)
     assert (best.tile_cells, best.cell_kernel) in [(c.tile_cells, c.cell_kernel) for c in cands]
     # the tuned configuration computes the same operator
-    a = gcmg.Multigrid(probe, 2, tile_cells=best.tile_cells, cell_kernel=best.cell_kernel)
+    a = gcmg.Multigrid(probe, 2, tile_cells=best.tile_cells, cell_kernel=best.cell_kernel,
+                       cell_threads=best.cell_threads)
     b = gcmg.Multigrid(probe, 2)
     x = torch.tensor(synth.point_values(a.dof_coords(a.finest), 5), dtype=torch.float32, device="cuda")
     xb = torch.tensor(synth.point_values(b.dof_coords(b.finest), 5), dtype=torch.float32, device="cuda")
