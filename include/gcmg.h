@@ -464,8 +464,8 @@ typedef struct {
  * candidate configuration over `reps` applications with CUDA events and
  * returns the fastest in *best; all (optional, GCMG_AUTOTUNE_MAX entries)
  * and n_all get every candidate.  Candidates (tile cells, cell_kernel,
- * cell_threads): the default; one lane per cell on 8-, 16- and 32-cell
- * tiles; one thread per line on 8- to 128-cell tiles (256 or 512 threads
+ * cell_threads): the default (one lane per cell on 32-cell tiles); one
+ * lane per cell on 8- and 16-cell tiles; one thread per line on 8- to 128-cell tiles (256 or 512 threads
  * for tiles above 32 cells); slab threads on 16- to 64-cell tiles (fp32).
  * The probe's finest level needs at least 2 x SMs x 128 cells, or the
  * larger tile sizes are halved like on any small level.  Synchronises

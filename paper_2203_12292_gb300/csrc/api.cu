@@ -607,6 +607,7 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
     L->perm.upload(lh.perm, H.stream);
     L->lane_tiles.upload(lh.lane, H.stream);
     L->lane_order.upload(lh.lane_order, H.stream);
+    L->lane_hang.upload(lh.lane_hang, H.stream);
     std::vector<int32_t> ijk(lh.cells.size() * 3);
     for (size_t c = 0; c < lh.cells.size(); ++c) {
       ijk[3 * c] = lh.cells[c].i;
@@ -632,6 +633,8 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
     c.perm = L->perm.as<uint8_t>();
     c.lane_tiles = lh.lane.empty() ? nullptr : L->lane_tiles.p;
     c.lane_order = lh.lane.empty() ? nullptr : L->lane_order.as<int32_t>();
+    c.lane_hang = lh.lane.empty() ? nullptr : L->lane_hang.p;
+    c.n_hang_tiles = lh.n_hang_tiles;
     c.cell_ijk = L->cell_ijk.as<int32_t>();
     c.k = k;
     c.tc = tc;

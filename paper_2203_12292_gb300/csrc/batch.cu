@@ -231,13 +231,15 @@ int gcmg_autotune(const gcmg_mesh* probe, int degree, int mg_fp32, int reps, voi
     if (!probe || !best || degree < 1 || degree > KMAX || reps < 1) throw Error(GCMG_ERR_ARG, "bad arguments");
     upload_all_tables();
     // candidates (tile cells, kernel, threads): the default (one lane per cell on 32-cell tiles), one lane
-    // per cell on 8/16/32-cell tiles, one thread per line on 8..128-cell tiles (lines per thread follow
+    // per cell on 8/16-cell tiles, one thread per line on 8..128-cell tiles (lines per thread follow
     // from the tile size; 256 or 512 threads for the chunked kernel of tiles above 32 cells), slab
     // threads on 16..64-cell tiles (fp32 only).  The probe's finest level must keep every size
     // (at least 2 x SMs x 128 cells).
-    static const int c32[][3] = {{32, 0, 0},   {8, 3, 0},   {16, 3, 0},  {32, 3, 0},  {8, 1, 0},
-                                 {16, 1, 0},   {32, 1, 0},  {64, 1, 256}, {64, 1, 512}, {128, 1, 256},
-                                 {128, 1, 512}, {16, 2, 0}, {32, 2, 0},  {64, 2, 0}};
+    // (one lane per cell on 32-cell tiles is the default's finest-level kernel; forcing it onto the
+    // coarse levels' smaller tiles as well is slower there, which this probe does not time)
+    static const int c32[][3] = {{32, 0, 0},   {8, 3, 0},   {16, 3, 0},   {8, 1, 0},     {16, 1, 0},
+                                 {32, 1, 0},   {64, 1, 256}, {64, 1, 512}, {128, 1, 256}, {128, 1, 512},
+                                 {16, 2, 0},   {32, 2, 0},   {64, 2, 0}};
     static const int c64[][3] = {{32, 0, 0}, {8, 1, 0}, {16, 1, 0}, {32, 1, 0}, {64, 1, 0}, {128, 1, 0}};
     const int nc = mg_fp32 ? (int)(sizeof(c32) / sizeof(c32[0])) : (int)(sizeof(c64) / sizeof(c64[0]));
     static_assert(sizeof(c32) / sizeof(c32[0]) <= GCMG_AUTOTUNE_MAX, "candidate list");

@@ -53,6 +53,14 @@ struct LaneTile {
   uint8_t pad[31];
 };
 static_assert(sizeof(LaneTile) % 64 == 0, "LaneTile is copied in 16-byte pieces");
+// per tile, for the tiles with hanging cells: per lane the lines of its cell
+// on a hanging face or edge, one set per direction D (bit u + (k+1) v for the
+// line through the other two coordinates (u, v), in increasing axis order),
+// and the 27-bit set of its slots on a hanging face or edge
+struct LaneHang {
+  uint32_t hl[3][32];
+  uint32_t hs[32];
+};
 
 struct TileInfo {
   int32_t cell_begin;
@@ -141,6 +149,8 @@ struct LevelHost {
   int max_local = 0;               // max tile-local DoF count
   std::vector<LaneTile> lane;      // per tile (tiles of at most 32 cells): lane-per-cell metadata
   std::vector<int32_t> lane_order; // tiles with hanging cells, then the others (launch order)
+  std::vector<LaneHang> lane_hang; // per tile (zero for tiles without hanging cells)
+  int n_hang_tiles = 0;            // tiles with hanging cells (the first entries of lane_order)
   int max_sub = 0;
   // dof coordinates (host) for checks
   std::vector<double> dof_xyz_cache;

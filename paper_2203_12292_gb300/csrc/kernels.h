@@ -40,6 +40,8 @@ struct CellLaunch {
   int use_lanes;  // 1: fp32 operator with the lane-per-cell kernel (tiles of at most 32 cells)
   const void* lane_tiles;  // per tile LaneTile (null: level without them)
   const int32_t* lane_order;  // launch order of the tiles: those with hanging cells first
+  const void* lane_hang;      // per tile LaneHang
+  int n_hang_tiles;           // tiles with hanging cells
   double lo, dom;
   const double* coef;  // per cell coefficient nu_e (element matrix nu_e h A_ref); null: 1
   int geom;            // 0: Cartesian cells; GEOM_WARP: the cells mapped by the warp below

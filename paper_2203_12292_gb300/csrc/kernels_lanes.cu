@@ -60,7 +60,9 @@ template <typename T>
 struct LaneArgsT {
   const TileInfo* tiles;
   const LaneTile* lt;
+  const LaneHang* lh;    // per tile: hanging lines and slots of every lane
   const int32_t* order;  // tile of block b: order[b] (null: tile0 + b)
+  int n_hang;            // with order: blocks below n_hang have tiles with hanging cells
   const int32_t* foreign;
   const int32_t* halo_pos;
   const T* src;
@@ -110,16 +112,15 @@ __device__ __forceinline__ void interp_line_reg(float* v, int p) {
 // of its cell.  SWEEP (D = 2 only): the z sweep follows (forward after C_z) or
 // precedes (backward before C_z^T) the interpolation on the same lines.
 template <int K, int D, bool TRANS, bool SWEEP = false>
-__device__ __forceinline__ void hang_pass(float* cb, uint16_t m, int w, int lane) {
+__device__ __forceinline__ void hang_pass(float* cb, uint16_t m, uint32_t hlD, int w, int lane) {
   constexpr int N = K + 1, N2 = N * N;
   constexpr int S = (D == 0 ? 1 : (D == 1 ? N : N2)) * 32;
   const DevTables<float>& tb = tab<float>(K);
   const int p = (m >> D) & 1;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    const int q = i + N * w;
-    const int u = q % N, v = q / N;
-    const bool hl = line_hangs<K, D>(m, u, v);
+    const int u = i, v = w;  // line (u, v): the other two coordinates
+    const bool hl = (hlD >> (u + N * v)) & 1u;
     if (!SWEEP && !hl) continue;
     const int base = D == 0 ? N * u + N2 * v : (D == 1 ? u + N2 * v : u + N * v);
     float* ptr = cb + base * 32 + lane;
@@ -132,22 +133,6 @@ __device__ __forceinline__ void hang_pass(float* cb, uint16_t m, int w, int lane
 #pragma unroll
     for (int a = 0; a < N; ++a) ptr[a * S] = x[a];
   }
-}
-
-// 27-bit set of the slots of a cell (mask m) that lie on a hanging face or edge
-__device__ __forceinline__ uint32_t hanging_slot_set(uint16_t m) {
-  if (!(m & MASK_HANG)) return 0u;
-  const int p0 = m & 1, p1 = (m >> 1) & 1, p2 = (m >> 2) & 1;
-  uint32_t hs = 0;
-#pragma unroll
-  for (int s = 0; s < NSLOT; ++s) {
-    const int c0 = s % 3, c1 = (s / 3) % 3, c2 = s / 9;
-    const bool on0 = c0 == 2 * p0, on1 = c1 == 2 * p1, on2 = c2 == 2 * p2;
-    const bool h = (((m >> 3) & 1) && on0) || (((m >> 4) & 1) && on1) || (((m >> 5) & 1) && on2) ||
-                   (((m >> 6) & 1) && on1 && on2) || (((m >> 7) & 1) && on0 && on2) || (((m >> 8) & 1) && on0 && on1);
-    if (h) hs |= 1u << s;
-  }
-  return hs;
 }
 
 // *x += v where lanes with the same address (siblings behind one hanging face
@@ -208,7 +193,8 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
   constexpr int N = G::N, N2 = G::N2, N3 = G::N3, NT = G::NT, NXW = G::NXW;
   extern __shared__ __align__(16) unsigned char smem[];
   LaneTile* st = reinterpret_cast<LaneTile*>(smem);
-  float* cb = reinterpret_cast<float*>(smem + sizeof(LaneTile));
+  LaneHang* hg = reinterpret_cast<LaneHang*>(smem + sizeof(LaneTile));
+  float* cb = reinterpret_cast<float*>(smem + sizeof(LaneTile) + sizeof(LaneHang));
   float* xs0 = cb + N3 * 32;  // 16-byte aligned
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int tile = A.order ? A.order[blockIdx.x] : A.tile0 + blockIdx.x;
@@ -224,6 +210,11 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
     const uint4* g = reinterpret_cast<const uint4*>(A.lt + tile);
     uint4* s = reinterpret_cast<uint4*>(st);
     for (int i = threadIdx.x; i < (int)(sizeof(LaneTile) / 16); i += NT) cp_async16(s + i, g + i);
+    if (!A.order || (int)blockIdx.x < A.n_hang) {  // the tile has hanging cells (or may have)
+      const uint4* gh = reinterpret_cast<const uint4*>(A.lh + tile);
+      uint4* shh = reinterpret_cast<uint4*>(hg);
+      for (int i = threadIdx.x; i < (int)(sizeof(LaneHang) / 16); i += NT) cp_async16(shh + i, gh + i);
+    }
     if (threadIdx.x < h0) cp_async(xs + threadIdx.x, so + threadIdx.x);
 #pragma unroll 4
     for (int j = threadIdx.x; j < nv; j += NT) cp_async16(xs + h0 + 4 * j, so + h0 + 4 * j);
@@ -340,15 +331,15 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
 #pragma unroll
       for (int a = 1; a < K; ++a) v[a] = p1[a - 1];
       v[K] = *p2;
-      if (line_hangs<K, 0>(m, r % N, r / N)) interp_line_reg<K, false>(v, m & 1);
+      if ((hg->hl[0][lane] >> r) & 1u) interp_line_reg<K, false>(v, m & 1);
       float* p = cb + N * r * 32 + lane;
 #pragma unroll
       for (int a = 0; a < N; ++a) p[a * 32] = v[a];
     }
     __syncthreads();
-    hang_pass<K, 1, false>(cb, m, w, lane);  // C_y
+    hang_pass<K, 1, false>(cb, m, hg->hl[1][lane], w, lane);  // C_y
     __syncthreads();
-    hang_pass<K, 2, false, true>(cb, m, w, lane);  // C_z, forward z sweep
+    hang_pass<K, 2, false, true>(cb, m, hg->hl[2][lane], w, lane);  // C_z, forward z sweep
     __syncthreads();
     {
       float4* z4 = reinterpret_cast<float4*>(xs0);
@@ -377,12 +368,12 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
     __syncthreads();
     sweep_y<K, false>(cb, w, lane);
     __syncthreads();
-    hang_pass<K, 2, true, true>(cb, m, w, lane);  // backward z sweep, C_z^T
+    hang_pass<K, 2, true, true>(cb, m, hg->hl[2][lane], w, lane);  // backward z sweep, C_z^T
     __syncthreads();
-    hang_pass<K, 1, true>(cb, m, w, lane);  // C_y^T
+    hang_pass<K, 1, true>(cb, m, hg->hl[1][lane], w, lane);  // C_y^T
     __syncthreads();
     // C_x^T and G_e^T on the warp's class of x-lines
-    const uint32_t hs = hanging_slot_set(m);
+    const uint32_t hs = hg->hs[lane];
     const int zb = nloc * 4;  // byte offset of the zero region
 #pragma unroll 1
     for (int i = 0; i < nxl; ++i) {
@@ -391,7 +382,7 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
       float v[N];
 #pragma unroll
       for (int a = 0; a < N; ++a) v[a] = p[a * 32];
-      if (line_hangs<K, 0>(m, r % N, r / N)) interp_line_reg<K, true>(v, m & 1);
+      if ((hg->hl[0][lane] >> r) & 1u) interp_line_reg<K, true>(v, m & 1);
       const uint32_t li = c_ll.line[K][r];
       const int s0 = li & 0xff, o0 = (li >> 8) & 0xff, o1 = li >> 16;
       const int b0 = st->ls[s0][lane], b1 = st->ls[s0 + 1][lane], b2 = st->ls[s0 + 2][lane];
@@ -523,27 +514,29 @@ __device__ __forceinline__ void interp_line_df(df* v, int p) {
   df x[N], y[N];
 #pragma unroll
   for (int a = 0; a < N; ++a) x[a] = df_sel(p, v[K - a], v[a]);
+  float ch[NMAX], cl[NMAX];
 #pragma unroll
   for (int r = 0; r < N; ++r) {
-    df s{0.f, 0.f};
 #pragma unroll
-    for (int a = 0; a < N; ++a) s = TRANS ? df_fma(s, x[a], Ih[a][r], Il[a][r]) : df_fma(s, x[a], Ih[r][a], Il[r][a]);
-    y[r] = s;
+    for (int a = 0; a < N; ++a) {
+      ch[a] = TRANS ? Ih[a][r] : Ih[r][a];
+      cl[a] = TRANS ? Il[a][r] : Il[r][a];
+    }
+    y[r] = df_dot<N>(x, ch, cl);
   }
 #pragma unroll
   for (int a = 0; a < N; ++a) v[a] = df_sel(p, y[K - a], y[a]);
 }
 
 template <int K, int D, bool TRANS, bool SWEEP = false>
-__device__ __forceinline__ void hang_pass_df(df* cb, uint16_t m, int w, int lane) {
+__device__ __forceinline__ void hang_pass_df(df* cb, uint16_t m, uint32_t hlD, int w, int lane) {
   constexpr int N = K + 1, N2 = N * N;
   constexpr int S = (D == 0 ? 1 : (D == 1 ? N : N2)) * 32;
   const int p = (m >> D) & 1;
 #pragma unroll 1
   for (int i = 0; i < N; ++i) {
-    const int q = i + N * w;
-    const int u = q % N, v = q / N;
-    const bool hl = line_hangs<K, D>(m, u, v);
+    const int u = i, v = w;  // line (u, v): the other two coordinates
+    const bool hl = (hlD >> (u + N * v)) & 1u;
     if (!SWEEP && !hl) continue;
     const int base = D == 0 ? N * u + N2 * v : (D == 1 ? u + N2 * v : u + N * v);
     df* ptr = cb + base * 32 + lane;
@@ -622,7 +615,8 @@ __global__ void __launch_bounds__((K + 1) * 32) vmult_lanes_df(LaneArgsT<double>
   constexpr int N = K + 1, N3 = N * N * N, NT = N * 32;
   extern __shared__ __align__(16) unsigned char smem[];
   LaneTile* st = reinterpret_cast<LaneTile*>(smem);
-  df* cb = reinterpret_cast<df*>(smem + sizeof(LaneTile));
+  LaneHang* hg = reinterpret_cast<LaneHang*>(smem + sizeof(LaneTile));
+  df* cb = reinterpret_cast<df*>(smem + sizeof(LaneTile) + sizeof(LaneHang));
   double* xd0 = reinterpret_cast<double*>(cb + N3 * 32);  // 16-byte aligned
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int tile = A.order ? A.order[blockIdx.x] : A.tile0 + blockIdx.x;
@@ -638,6 +632,11 @@ __global__ void __launch_bounds__((K + 1) * 32) vmult_lanes_df(LaneArgsT<double>
     const uint4* g = reinterpret_cast<const uint4*>(A.lt + tile);
     uint4* s = reinterpret_cast<uint4*>(st);
     for (int i = threadIdx.x; i < (int)(sizeof(LaneTile) / 16); i += NT) cp_async16(s + i, g + i);
+    if (!A.order || (int)blockIdx.x < A.n_hang) {  // the tile has hanging cells (or may have)
+      const uint4* gh = reinterpret_cast<const uint4*>(A.lh + tile);
+      uint4* shh = reinterpret_cast<uint4*>(hg);
+      for (int i = threadIdx.x; i < (int)(sizeof(LaneHang) / 16); i += NT) cp_async16(shh + i, gh + i);
+    }
     if (threadIdx.x < h0) cp_async(xd + threadIdx.x, so + threadIdx.x);
 #pragma unroll 4
     for (int j = threadIdx.x; j < nv; j += NT) cp_async16(xd + h0 + 2 * j, so + h0 + 2 * j);
@@ -685,7 +684,7 @@ __global__ void __launch_bounds__((K + 1) * 32) vmult_lanes_df(LaneArgsT<double>
     v[K] = *p2;
     if (!hang)
       df_eo_fwd_fast<K>(v);
-    else if (line_hangs<K, 0>(m, r % N, r / N))
+    else if ((hg->hl[0][lane] >> r) & 1u)
       interp_line_df<K, false>(v, m & 1);
     df* p = cb + N * r * 32 + lane;
 #pragma unroll
@@ -693,9 +692,9 @@ __global__ void __launch_bounds__((K + 1) * 32) vmult_lanes_df(LaneArgsT<double>
   }
   __syncthreads();
   if (hang) {
-    hang_pass_df<K, 1, false>(cb, m, w, lane);  // C_y
+    hang_pass_df<K, 1, false>(cb, m, hg->hl[1][lane], w, lane);  // C_y
     __syncthreads();
-    hang_pass_df<K, 2, false, true>(cb, m, w, lane);  // C_z, forward z sweep
+    hang_pass_df<K, 2, false, true>(cb, m, hg->hl[2][lane], w, lane);  // C_z, forward z sweep
     __syncthreads();
   }
   {  // the tile DoFs are dead: clear the accumulator
@@ -712,13 +711,13 @@ __global__ void __launch_bounds__((K + 1) * 32) vmult_lanes_df(LaneArgsT<double>
   sweep_y_df<K, false>(cb, w, lane);
   __syncthreads();
   if (hang) {
-    hang_pass_df<K, 2, true, true>(cb, m, w, lane);  // backward z sweep, C_z^T
+    hang_pass_df<K, 2, true, true>(cb, m, hg->hl[2][lane], w, lane);  // backward z sweep, C_z^T
     __syncthreads();
-    hang_pass_df<K, 1, true>(cb, m, w, lane);  // C_y^T
+    hang_pass_df<K, 1, true>(cb, m, hg->hl[1][lane], w, lane);  // C_y^T
     __syncthreads();
   }
   // backward x sweep (tiles without hanging cells) or C_x^T, then G_e^T on the warp's class of x-lines
-  const uint32_t hs = hang ? hanging_slot_set(m) : 0u;
+  const uint32_t hs = hang ? hg->hs[lane] : 0u;
   const int zb = nloc * 4;
 #pragma unroll 1
   for (int i = 0; i < nxl; ++i) {
@@ -729,7 +728,7 @@ __global__ void __launch_bounds__((K + 1) * 32) vmult_lanes_df(LaneArgsT<double>
     for (int a = 0; a < N; ++a) v[a] = p[a * 32];
     if (!hang)
       df_eo_bwd_fast<K>(v);
-    else if (line_hangs<K, 0>(m, r % N, r / N))
+    else if ((hg->hl[0][lane] >> r) & 1u)
       interp_line_df<K, true>(v, m & 1);
     const uint32_t li = c_ll.line[K][r];
     const int s0 = li & 0xff, o0 = (li >> 8) & 0xff, o1 = li >> 16;
@@ -825,13 +824,13 @@ template <int K>
 size_t lanes_smem(int max_local) {
   constexpr int N3 = (K + 1) * (K + 1) * (K + 1);
   // tile DoFs shifted by up to 3 for the 16-byte copies, the zero region, and the float4 clearing
-  return sizeof(LaneTile) + ((size_t)N3 * 32 + (size_t)max_local + LANE_ZERO + 8) * sizeof(float);
+  return sizeof(LaneTile) + sizeof(LaneHang) + ((size_t)N3 * 32 + (size_t)max_local + LANE_ZERO + 8) * sizeof(float);
 }
 
 template <int K>
 size_t lanes_df_smem(int max_local) {
   constexpr int N3 = (K + 1) * (K + 1) * (K + 1);
-  return sizeof(LaneTile) + ((size_t)N3 * 32 + (size_t)max_local + LANE_ZERO + 4) * sizeof(double);
+  return sizeof(LaneTile) + sizeof(LaneHang) + ((size_t)N3 * 32 + (size_t)max_local + LANE_ZERO + 4) * sizeof(double);
 }
 
 template <int K>
@@ -871,6 +870,8 @@ void launch_vmult_lanes_df(const CellLaunch& L, const double* src, double* dst, 
   LaneArgsT<double> A{};
   A.tiles = L.tiles;
   A.lt = static_cast<const LaneTile*>(L.lane_tiles);
+  A.lh = static_cast<const LaneHang*>(L.lane_hang);
+  A.n_hang = L.n_hang_tiles;
   A.order = (t0 == 0 && t1 == L.n_tiles) ? L.lane_order : nullptr;
   A.foreign = L.foreign;
   A.halo_pos = L.halo_pos;
@@ -895,6 +896,8 @@ void launch_vmult_lanes(const CellLaunch& L, const void* src, void* dst, int add
   LaneArgs A{};
   A.tiles = L.tiles;
   A.lt = static_cast<const LaneTile*>(L.lane_tiles);
+  A.lh = static_cast<const LaneHang*>(L.lane_hang);
+  A.n_hang = L.n_hang_tiles;
   // a whole level: tiles with hanging cells first (their longer code path then
   // runs mostly on its own instead of interleaved with the regular tiles')
   A.order = (t0 == 0 && t1 == L.n_tiles) ? L.lane_order : nullptr;

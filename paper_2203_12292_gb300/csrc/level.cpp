@@ -307,6 +307,8 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
   // lane-per-cell metadata of tiles of at most 32 cells
   L.lane.clear();
   L.lane_order.clear();
+  L.lane_hang.clear();
+  L.n_hang_tiles = 0;
   if (tile_cells <= 32) {
     L.lane.assign(nt, LaneTile{});
     for (int t = 0; t < nt; ++t) {
@@ -328,6 +330,33 @@ void build_level(const Octree& mesh, int k, int tile_cells, int LM, LevelHost& L
     for (int pass = 1; pass >= 0; --pass)
       for (int t = 0; t < nt; ++t)
         if (L.lane[t].hang == pass) L.lane_order.push_back(t);
+    // hanging lines and slots of every lane of the tiles with hanging cells
+    L.lane_hang.assign(nt, LaneHang{});
+    L.n_hang_tiles = 0;
+    const int n = k + 1;
+    for (int t = 0; t < nt; ++t) {
+      if (!L.lane[t].hang) continue;
+      ++L.n_hang_tiles;
+      LaneHang& lh = L.lane_hang[t];
+      for (int j = 0; j < L.tiles[t].n_cells; ++j) {
+        const uint16_t m = L.mask[L.tiles[t].cell_begin + j];
+        if (!(m & MASK_HANG)) continue;
+        for (int D = 0; D < 3; ++D) {
+          const int A1 = D == 0 ? 1 : 0, A2 = D == 2 ? 1 : 2;  // the other two axes, increasing
+          const int p1 = (m >> A1) & 1, p2 = (m >> A2) & 1;
+          const bool f1 = (m >> (3 + A1)) & 1, f2 = (m >> (3 + A2)) & 1, ed = (m >> (6 + D)) & 1;
+          for (int v = 0; v < n; ++v)
+            for (int u = 0; u < n; ++u) {
+              const bool on1 = u == p1 * k, on2 = v == p2 * k;
+              if ((f1 && on1) || (f2 && on2) || (ed && on1 && on2)) lh.hl[D][j] |= 1u << (u + n * v);
+            }
+        }
+        for (int s2 = 0; s2 < NSLOT; ++s2) {
+          const int cl[3] = {s2 % 3, (s2 / 3) % 3, s2 / 9};
+          if (slot_hanging(m, cl)) lh.hs[j] |= 1u << s2;
+        }
+      }
+    }
   }
   L.n_free = next;
   for (int e = 0; e < ne; ++e)

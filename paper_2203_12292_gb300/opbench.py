@@ -1,12 +1,13 @@
 """Kernel microbenchmark: time one operation of one level.
 
     python -m paper_2203_12292_gb300.opbench [--workload q4octant] [--level -1]
-        [--op vmult|restrict|prolong|mlp] [--dtype f32|f64] [--reps 20]
+        [--op vmult|restrict|prolong|mlp|diag|coarse] [--dtype f32|f64] [--reps 20]
         [--tile-cells 0] [--cell-kernel 0|1|2|3] [--cell-threads 0] [--warp EPS]
 
 vmult: the level's operator; restrict/prolong: the transfer between the
 level and the next coarser one; mlp: the learned-smoother correction (Q4,
-random initial network).  The timed calls run inside an NVTX range named
+random initial network); diag: the level's Jacobi diagonal (Eqs. 3-4, the
+per-mask table and the tile loop); coarse: the level-0 solve.  The timed calls run inside an NVTX range named
 "opbench", so a profiler can select exactly them.  Prints one JSON line
 (ms per call, GDoF/s of the level's free DoFs).
 """
@@ -33,7 +34,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="q4octant", choices=sorted(WORKLOADS))
     ap.add_argument("--level", type=int, default=-1)
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--op", default="vmult", choices=["vmult", "restrict", "prolong", "mlp"])
+    ap.add_argument("--op", default="vmult", choices=["vmult", "restrict", "prolong", "mlp", "diag", "coarse"])
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--tile-cells", type=int, default=0)
     ap.add_argument("--cell-kernel", type=int, default=0, choices=[0, 1, 2, 3])
@@ -60,6 +61,8 @@ def main(argv=None):
     x = torch.rand(n, dtype=dt, device="cuda")
     y = torch.empty_like(x)
     xc = torch.rand(mg.n_free(max(lev - 1, 0)), dtype=dt, device="cuda")
+    b0 = torch.rand(mg.n_free(0), dtype=dt, device="cuda")
+    x0 = torch.empty_like(b0)
     if a.op == "mlp":
         net = MLP(*sy.mlp_shape(w.degree))
         net.set_params(torch.tensor(sy.mlp_init(*sy.mlp_shape(w.degree), 1), dtype=torch.float32, device="cuda"))
@@ -71,6 +74,10 @@ def main(argv=None):
             mg.restrict_add(lev, x, xc)
         elif a.op == "prolong":
             mg.prolongate_add(lev, xc, y)
+        elif a.op == "diag":
+            mg.diagonal(lev)
+        elif a.op == "coarse":
+            mg.coarse_solve(b0, x0)
         else:
             mg.mlp_correct(lev, net, x, y)
 
