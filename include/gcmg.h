@@ -424,8 +424,23 @@ int gcmg_cell_gather(gcmg_handle* h, int level, const double* x, int64_t n_cells
  */
 int gcmg_mlp_samples(gcmg_handle* h, int level, const double* b, const double* x, const double* xstar,
                      int64_t n_cells, const int32_t* cells, float* X, float* T, float* W);
-/* x += the owner-selected corrections of `net` for the residual r (Q4 only) */
+/*
+ * x += the owner-selected corrections of `net` for the residual r (Q4 only).
+ * r, x: device vectors of n_free(level) entries, fp64 when fp64 != 0, else
+ * fp32; r and x must not overlap.  The first call with a network (and the
+ * first after its parameters changed) packs its weights and computes the
+ * diagonal part of its first layer for every cell of the level; later calls
+ * reuse them.
+ */
 int gcmg_mlp_correct(gcmg_handle* h, int level, const gcmg_mlp* net, int fp64, const void* r, void* x);
+/*
+ * Number of bounded device waits of the tensor-core kernels (learned
+ * smoother inference and training products) that gave up since the library
+ * was loaded or last reset; a kernel whose wait gives up counts it, leaves
+ * its remaining output unwritten, frees its tensor memory and returns.
+ * Synchronises the device.  reset != 0 sets the count back to zero.
+ */
+int gcmg_wait_timeouts(unsigned int* count, int reset);
 
 #define GCMG_SMOOTHER_CHEBYSHEV 0   /* Chebyshev around point Jacobi (default) */
 #define GCMG_SMOOTHER_MLP_AUGMENT 1 /* postsmoothing, then one learned correction */

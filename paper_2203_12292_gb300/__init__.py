@@ -120,6 +120,7 @@ _SIGS = {
                                   _c_void_p, _c_void_p, _c_void_p]),
     "gcmg_mlp_correct": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_int, _c_void_p, _c_void_p]),
     "gcmg_set_smoother": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p]),
+    "gcmg_wait_timeouts": (_c_int, [ctypes.POINTER(ctypes.c_uint), _c_int]),
     "gcmg_point_values": (_c_int, [_c_void_p, _c_int64, ctypes.c_uint64, _c_void_p]),
     "gcmg_autotune": (_c_int, [_c_void_p, _c_int, _c_int, _c_int, _c_void_p, ctypes.POINTER(Tuning),
                                ctypes.POINTER(Tuning), ctypes.POINTER(_c_int)]),
@@ -162,6 +163,14 @@ def fma_peak(fp64: bool, iters: int = 1 << 16) -> float:
     out = _c_double()
     _check(lib().gcmg_fma_peak(int(fp64), iters, _c_void_p(torch.cuda.current_stream().cuda_stream),
                                ctypes.byref(out)))
+    return out.value
+
+
+def wait_timeouts(reset: bool = False) -> int:
+    """Bounded tensor-core waits that gave up since the library was loaded
+    (or the last reset); synchronises the device."""
+    out = ctypes.c_uint()
+    _check(lib().gcmg_wait_timeouts(ctypes.byref(out), int(reset)))
     return out.value
 
 

@@ -325,10 +325,20 @@ void ensure_dfeat(Handle& H, int l) {
   ck(cudaStreamSynchronize(H.stream), "diagonal features");
 }
 
-void mlp_correct(Handle& H, int l, const void* image, bool fp64, const void* r, void* x) {
+// weight image and per-cell diagonal projection of a Q4 network for level l
+void mlp_prepare(Handle& H, int l, const gcmg_mlp* net, DevBuf& image, DevBuf& dproj) {
+  LevelDev& L = *H.lev[l];
+  ensure_dfeat(H, l);
+  if (!image.p) image.alloc(mlp_image_bytes());
+  if (!dproj.p) dproj.alloc(L.host.cells.size() * 128 * sizeof(float));
+  launch_mlp_prepare(net->net.params.as<float>(), L.dfeat.as<uint16_t>(), (int64_t)L.host.cells.size(), image.p,
+                     dproj.as<float>(), H.stream);
+}
+
+void mlp_correct(Handle& H, int l, const void* image, const float* dproj, bool fp64, const void* r, void* x) {
   LevelDev& L = *H.lev[l];
   MlpFused P{image,
-             L.dfeat.as<uint16_t>(),
+             dproj,
              L.gstart.as<int32_t>(),
              L.own.as<uint32_t>(),
              L.meta.as<CellMeta>(),
@@ -348,7 +358,7 @@ void learned_step(Handle& H, int l) {
   vmult(H, l, f64, L.x.p, L.t.p);
   launch_residual(f64, L.t.p, L.b.p, L.t.p, L.n(), H.stream);
   launch_zero(f64, L.d.p, L.n(), H.stream);
-  mlp_correct(H, l, L.mlp_image.p, f64, L.t.p, L.d.p);
+  mlp_correct(H, l, L.mlp_image.p, L.mlp_dproj.as<float>(), f64, L.t.p, L.d.p);
   void* w = f64 ? L.w64a.p : L.w32a.p;
   vmult(H, l, f64, L.d.p, w);
   if (!H.lscratch.p) throw Error(GCMG_ERR_INTERNAL, "learned step without its scratch");
@@ -1363,11 +1373,21 @@ int gcmg_mlp_correct(gcmg_handle* h, int level, const gcmg_mlp* net, int fp64, c
     check_q4_net(L, net);
     if (L.n() == 0) return;
     if (!r || !x) throw Error(GCMG_ERR_ARG, "bad vectors");
-    ensure_dfeat(h->h, level);
     Handle& H = h->h;
-    if (!H.mlp_scratch.p) H.mlp_scratch.alloc(mlp_image_bytes());
-    launch_mlp_pack(net->net.params.as<float>(), H.mlp_scratch.p, H.stream);
-    mlp_correct(H, level, H.mlp_scratch.p, fp64 != 0, r, x);
+    if (L.mlp_call_version != net->net.version) {
+      mlp_prepare(H, level, net, L.mlp_image_call, L.mlp_dproj_call);
+      L.mlp_call_version = net->net.version;
+    }
+    mlp_correct(H, level, L.mlp_image_call.p, L.mlp_dproj_call.as<float>(), fp64 != 0, r, x);
+  });
+}
+
+int gcmg_wait_timeouts(unsigned int* count, int reset) {
+  return guarded([&] {
+    if (!count) throw Error(GCMG_ERR_ARG, "null count");
+    const unsigned int n = wait_timeouts(reset != 0);
+    if (n == ~0u) throw Error(GCMG_ERR_CUDA, "reading the wait counter");
+    *count = n;
   });
 }
 
@@ -1384,9 +1404,7 @@ int gcmg_set_smoother(gcmg_handle* h, int level, int kind, const gcmg_mlp* net) 
       if (L.cl.coef) throw Error(GCMG_ERR_ARG, "the learned smoother assumes a unit coefficient");
       if (L.cl.geom) throw Error(GCMG_ERR_ARG, "the learned smoother assumes Cartesian cells");
       check_q4_net(L, net);
-      ensure_dfeat(H, level);
-      if (!L.mlp_image.p) L.mlp_image.alloc(mlp_image_bytes());
-      launch_mlp_pack(net->net.params.as<float>(), L.mlp_image.p, H.stream);
+      mlp_prepare(H, level, net, L.mlp_image, L.mlp_dproj);
       if (!H.lscratch.p) H.lscratch.alloc((2 * DOT_BLOCKS + 2) * sizeof(double));
     }
     L.smoother = kind;

@@ -26,7 +26,10 @@ struct LevelDev {
   double lam = 1.0;
   // learned smoother: kind, parameter copy, bf16 diagonal features per cell
   int smoother = GCMG_SMOOTHER_CHEBYSHEV;
-  DevBuf mlp_image, dfeat;  // packed bf16 weights of the fused kernel
+  DevBuf mlp_image, dfeat;  // packed bf16 weights of the fused kernel, bf16 diagonal features
+  DevBuf mlp_dproj;         // diagonal part of the first layer per cell (the smoother's network)
+  DevBuf mlp_image_call, mlp_dproj_call;  // the same for gcmg_mlp_correct calls
+  uint64_t mlp_call_version = 0;          // network version they were built from
   DevBuf coef;              // per cell coefficient nu_e (allocated once one is set)
   // local smoothing: refinement-edge DoFs; Algorithm 1's copy pairs (active DoF, level DoF)
   DevBuf edge_idx, cp_g, cp_idx;
@@ -104,7 +107,6 @@ struct Handle {
   int n0 = 0;
   DevBuf scratch, scal, modes;
   DevBuf cg_r, cg_p, cg_q, cg_z, cg_x;
-  DevBuf mlp_scratch;  // weight image of gcmg_mlp_correct calls
   DevBuf lscratch;     // inner products of the learned step's Galerkin step length
   // host-buffer operator: the input copy in DoF order on its own stream, overlapped with the tiles
   cudaStream_t copy_stream = nullptr;

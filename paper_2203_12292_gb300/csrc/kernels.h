@@ -204,6 +204,7 @@ struct GemmArgs {
   int64_t ldc;
   const float* bias;
   int M, N, K;
+  const uint16_t* Ab = nullptr;  // bf16 A (row stride sam, k contiguous) in place of A
 };
 void launch_gemm_bf16(const GemmArgs& g, cudaStream_t s);
 void launch_gelu(const float* Z, float* H, int64_t n, cudaStream_t s);
@@ -220,8 +221,8 @@ void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float 
 
 // fused per-cell correction x += owner-selected MLP(r) for Q4 (250-128-128-125)
 struct MlpFused {
-  const void* wimg;        // packed bf16 weight image (launch_mlp_pack), 16-byte aligned
-  const uint16_t* dfeat;   // bf16 diagonal features, MLP_DF per cell
+  const void* wimg;        // packed bf16 weight image (launch_mlp_prepare), 16-byte aligned
+  const float* dproj;      // per cell: b1 + the diagonal features times their W1 columns (128)
   const int32_t* gstart;   // cells x 27
   const uint32_t* own;     // per cell: owned slots
   const CellMeta* meta;
@@ -231,8 +232,15 @@ struct MlpFused {
 };
 size_t mlp_fused_smem_bytes();
 size_t mlp_image_bytes();
-// weight image of a 250-128-128-125 network from its packed fp32 parameters
-void launch_mlp_pack(const float* params, void* image, cudaStream_t s);
+// weight image of a 250-128-128-125 network from its packed fp32 parameters,
+// and the diagonal part of its first layer for every cell of a level (dproj:
+// n_cells x 128 fp32, from the bf16 diagonal features dfeat)
+void launch_mlp_prepare(const float* params, const uint16_t* dfeat, int64_t n_cells, void* image, float* dproj,
+                        cudaStream_t s);
+// bounded tensor-core waits that gave up since the last reset (synchronous)
+unsigned int wait_timeouts(bool reset);
+// multiprocessors of the current device (152 without a usable device)
+int device_sm_count();
 cudaError_t launch_mlp_correct(const MlpFused& P, bool fp64, const void* r, void* x, cudaStream_t s);
 
 }  // namespace gcmg

@@ -4,20 +4,24 @@
 // * cell gather: the values of a free-DoF vector at the (k+1)^3 support
 //   points of a list of cells, hanging points interpolated (G_e, then C_e of
 //   Eq. 2), in fp64.
-// * training: a bf16 tensor-core GEMM (mma.sync m16n8k16, fp32 accumulation)
-//   with arbitrary operand strides, so that every product of the forward and
-//   backward passes (X W^T, dY^T H, dY W) is one launch; GELU, loss, column
-//   sums and Adam as elementwise kernels.
+// * training: a bf16 GEMM on the fifth-generation tensor cores (tcgen05.mma,
+//   fp32 accumulators in TMEM) with arbitrary operand strides, so that every
+//   product of the forward and backward passes (X W^T, dY^T H, dY W) is one
+//   launch; GELU, loss, column sums and Adam as elementwise kernels.
 // * inference: one persistent kernel per application.  Each CTA keeps the
-//   three weight matrices in shared memory (bf16) and loops over batches of
-//   64 cells: gather the residual, interpolate hanging points, scale by the
-//   cell norm, run the three layers on the tensor cores, and add the
-//   correction to the DoFs the cell owns (each DoF has exactly one owner
-//   cell, so there are no races and no atomics).
+//   bf16 weights in shared memory (one bulk copy) and loops over batches of
+//   128 cells: gather the residual, interpolate hanging points, scale by the
+//   cell norm, run the three layers as 128 x 128 x 128 tcgen05 products with
+//   the accumulators in TMEM, and add the correction to the DoFs the cell
+//   owns (each DoF has exactly one owner cell, so there are no races and no
+//   atomics).  The diagonal half of the first layer depends only on the cell
+//   and the network, so it is computed once per network (a GEMM over all
+//   cells) and read back per application.
 #include <cuda_bf16.h>
 
 #include "device.cuh"
 #include "kernels.h"
+#include "tc.cuh"
 
 namespace gcmg {
 
@@ -32,42 +36,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-__device__ __forceinline__ uint32_t lds32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+// bounded tensor-core waits that gave up (read by gcmg_wait_timeouts)
+__device__ unsigned int g_wait_timeouts;
 
-// D = A B + D for one 16x8 tile, A 16x16 (row-major fragments), B 16x8
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// one warp: acc[nt] += A[16 x K] * Bt[8 nt .. 8 nt + 7][K]^T, both operands
-// in shared memory with k contiguous (row strides lda, ldb even, K multiple
-// of 16).  Fragment layout of m16n8k16: lane = 4 g + t holds A rows g, g + 8
-// at columns 2t, 2t+1, 2t+8, 2t+9, B column g at rows 2t, 2t+1, 2t+8, 2t+9,
-// and D rows g, g + 8 at columns 2t, 2t+1.
-template <int NT>
-__device__ __forceinline__ void warp_gemm(const bf16* A, int lda, const bf16* Bt, int ldb, int K,
-                                          float (&acc)[NT][4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const bf16* pa = A + g * lda + 2 * t;
-  const bf16* pb = Bt + g * ldb + 2 * t;
-#pragma unroll 2
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    uint32_t a[4];
-    a[0] = lds32(pa + k0);
-    a[1] = lds32(pa + 8 * lda + k0);
-    a[2] = lds32(pa + k0 + 8);
-    a[3] = lds32(pa + 8 * lda + k0 + 8);
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      const bf16* q = pb + nt * 8 * ldb + k0;
-      mma_bf16(acc[nt], a, lds32(q), lds32(q + 8));
-    }
-  }
-}
+__device__ __forceinline__ float bf16_bits_to_float(uint16_t u) { return __uint_as_float((uint32_t)u << 16); }
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_f(float z) {
@@ -143,40 +115,93 @@ __global__ void dfeat_kernel(const double* D, int64_t n, int n3, const CellMeta*
 // ---------------------------------------------------------------------------
 // training kernels
 // ---------------------------------------------------------------------------
-constexpr int GT = 64, GK = 32, GKS = GK + 8;
+// C = A B (+ bias) with A (M x K) and B (K x N) at arbitrary strides, operands
+// rounded to bf16, fp32 accumulation.  One CTA per 128 x 128 tile of C: the
+// threads convert a 128 x 64 chunk of A and of B^T into the K-major core
+// layout, one thread issues four 128 x 128 x 16 tcgen05 products into TMEM,
+// and the chunk's completion (mbarrier, bounded wait) frees the buffers for
+// the next one; the eight warps then read the accumulator back (warp w: TMEM
+// lanes 32 (w % 4) .., columns 64 (w / 4) ..) and store C.
+constexpr int GM = 128, GN = 128, GKC = 64, GTH = 256;
 
-__global__ void __launch_bounds__(256) gemm_bf16_kernel(GemmArgs g) {
-  __shared__ __align__(16) bf16 As[GT * GKS];
-  __shared__ __align__(16) bf16 Bs[GT * GKS];
-  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
-  const int warp = threadIdx.x >> 5, rb = warp & 3, ch = warp >> 2;
-  float acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-  for (int k0 = 0; k0 < g.K; k0 += GK) {
-    for (int e = threadIdx.x; e < GT * GK; e += blockDim.x) {
-      const int i = e / GK, kk = e - i * GK, k = k0 + kk;
-      const int m = m0 + i, nn = n0 + i;
-      const float va = (m < g.M && k < g.K) ? g.A[(int64_t)m * g.sam + (int64_t)k * g.sak] : 0.0f;
-      const float vb = (nn < g.N && k < g.K) ? g.B[(int64_t)k * g.sbk + (int64_t)nn * g.sbn] : 0.0f;
-      As[i * GKS + kk] = __float2bfloat16_rn(va);
-      Bs[i * GKS + kk] = __float2bfloat16_rn(vb);
+__global__ void __launch_bounds__(GTH) gemm_tc_kernel(GemmArgs g) {
+  __shared__ __align__(1024) bf16 As[GM * GKC];
+  __shared__ __align__(1024) bf16 Bs[GN * GKC];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+  if (warp == 0) tc::tmem_alloc(&tslot, GN);
+  if (tid == 0) tc::mbar_init(&bar, 1);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tslot;
+  constexpr uint32_t SBO = GKC / 8 * 128;  // row-group stride of a chunk
+  const bool a_kfast = g.Ab != nullptr || g.sak == 1, b_kfast = g.sbk == 1;
+  const int nk = (g.K + GKC - 1) / GKC;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int c = 0; c < nk; ++c) {
+    const int k0 = c * GKC;
+    for (int e = tid; e < GM * GKC; e += GTH) {
+      // consecutive threads along the operand's contiguous dimension
+      const int i = a_kfast ? e / GKC : e % GM, kk = a_kfast ? e % GKC : e / GM;
+      const int m = m0 + i, k = k0 + kk;
+      float v = 0.0f;
+      if (m < g.M && k < g.K)
+        v = g.Ab ? bf16_bits_to_float(g.Ab[(int64_t)m * g.sam + k]) : g.A[(int64_t)m * g.sam + (int64_t)k * g.sak];
+      As[tc::core_off(i, kk, GKC)] = __float2bfloat16_rn(v);
     }
+    for (int e = tid; e < GN * GKC; e += GTH) {
+      const int i = b_kfast ? e / GKC : e % GN, kk = b_kfast ? e % GKC : e / GN;
+      const int n = n0 + i, k = k0 + kk;
+      const float v = (n < g.N && k < g.K) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : 0.0f;
+      Bs[tc::core_off(i, kk, GKC)] = __float2bfloat16_rn(v);
+    }
+    tc::fence_async_smem();
+    tc::fence_before();
     __syncthreads();
-    warp_gemm<4>(As + rb * 16 * GKS, GKS, Bs + ch * 32 * GKS, GKS, GK, acc);
-    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t a0 = tc::saddr(As), b0 = tc::saddr(Bs);
+#pragma unroll
+      for (int s = 0; s < GKC / 16; ++s)
+        tc::mma_bf16(tmem, tc::sdesc(a0 + s * 256, 128, SBO), tc::sdesc(b0 + s * 256, 128, SBO),
+                     tc::idesc_bf16(GM, GN), (c > 0 || s > 0) ? 1u : 0u);
+      tc::commit(&bar);
+    }
+    ok = __syncthreads_and(tc::mbar_wait(&bar, phase));
+    phase ^= 1u;
+    tc::fence_after();
+    if (!ok) break;
   }
-  const int lane = threadIdx.x & 31, gg = lane >> 2, t = lane & 3;
+  if (!ok) {
+    if (tid == 0) atomicAdd(&g_wait_timeouts, 1u);
+    tc::mbar_wait(&bar, phase ^ 1u);  // once more for the products in flight
+  } else {
+    const int q = warp & 3, h = warp >> 2, m = m0 + 32 * q + lane;
 #pragma unroll
-  for (int nt = 0; nt < 4; ++nt)
+    for (int part = 0; part < 2; ++part) {
+      const int col0 = 64 * h + 32 * part;
+      float v[32];
+      if (nk > 0) {
+        tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col0, v);
+      } else {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int m = m0 + rb * 16 + gg + (e >> 1) * 8;
-      const int nn = n0 + ch * 32 + nt * 8 + 2 * t + (e & 1);
-      if (m < g.M && nn < g.N) g.C[(int64_t)m * g.ldc + nn] = acc[nt][e] + (g.bias ? g.bias[nn] : 0.0f);
+        for (int j = 0; j < 32; ++j) v[j] = 0.0f;
+      }
+      if (m < g.M)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + col0 + j;
+          if (n < g.N) g.C[(int64_t)m * g.ldc + n] = v[j] + (g.bias ? g.bias[n] : 0.0f);
+        }
     }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, GN);
 }
 
 __global__ void gelu_kernel(const float* Z, float* H, int64_t n) {
@@ -252,30 +277,33 @@ __global__ void adam_kernel(float* p, const float* g, float* m, float* v, int64_
 // ---------------------------------------------------------------------------
 // fused inference for Q4: 250 -> 128 -> 128 -> 125
 // ---------------------------------------------------------------------------
-constexpr int FK = 4, FN3 = 125, FC = 64, FT = 512;  // degree, nodes, cells per batch, threads
-constexpr int XS = 264, HS = 136, SS = 128;           // row strides: X / W1 (bf16), H / W2 / W3 (bf16), staging (fp32)
-// shared memory = [weight image (W1, W2, W3 bf16, biases fp32) | X | H | staging | per-cell data]
-constexpr size_t F_W1 = 0;
-constexpr size_t F_W2 = F_W1 + 128 * XS * 2;
-constexpr size_t F_W3 = F_W2 + 128 * HS * 2;
-constexpr size_t F_B = F_W3 + 128 * HS * 2;
-constexpr size_t F_IMG = F_B + 3 * 128 * 4;  // bytes of the packed weight image
-constexpr size_t F_X = F_IMG;
-constexpr size_t F_H = F_X + FC * XS * 2;
-constexpr size_t F_ST = F_H + FC * HS * 2;
-constexpr size_t F_SC = F_ST + FC * SS * 4;
-constexpr size_t F_SI = F_SC + FC * 4;
-constexpr size_t F_GS = F_SI + FC * 4;
-constexpr size_t F_OWN = F_GS + FC * NSLOT * 4;
+constexpr int FK = 4, FN3 = 125, FC = 128, FT = 512;  // degree, nodes, cells per batch, threads
+constexpr int SS = 129;                                // row stride of the fp32 cell buffer (odd: no bank conflicts)
+constexpr int GH = 16;                                 // gathered values in flight per thread
+// shared memory (offsets from a 1024-byte aligned base):
+// [W1 residual columns | W2 | W3 (bf16 operand tiles, 128 x 128 each) | b2, b3 (fp32)] = the weight image,
+// then the activation tile A (bf16 128 x 128: features, then H1, then H2), the fp32 cell buffer, per-cell data
+constexpr size_t F_W1 = 0, F_W2 = 32768, F_W3 = 65536, F_B = 98304;
+constexpr size_t F_IMG = F_B + 2 * 128 * 4;  // bytes of the weight image
+constexpr size_t F_A = F_IMG;
+constexpr size_t F_ST = F_A + 32768;
+constexpr size_t F_GS = F_ST + (size_t)FC * SS * 4;
+constexpr size_t F_OWN = F_GS + (size_t)FC * NSLOT * 4;
 constexpr size_t F_MK = F_OWN + FC * 4;
-constexpr size_t F_BYTES = F_MK + FC * 2;
+constexpr size_t F_SI = F_MK + FC * 2;
+constexpr size_t F_SC = F_SI + FC * 4;
+constexpr size_t F_TAB = F_SC + FC * 4;
+constexpr size_t F_BAR = F_TAB + 128 * 2;
+constexpr size_t F_END = F_BAR + 32;
+constexpr size_t F_BYTES = F_END + 1024;  // room to align the base
 static_assert(F_BYTES <= 232448, "fused MLP kernel exceeds the shared memory of a CTA");
-static_assert(F_IMG % 16 == 0 && F_X % 16 == 0 && (XS * 2) % 16 == 0, "16-byte aligned rows");
-constexpr int GPT = (FC * FN3 + FT - 1) / FT;  // gathered values per thread and batch
-constexpr int GH = 8;                            // of them in flight at once
+static_assert(F_A % 1024 == 0 && F_BAR % 8 == 0, "aligned operand tiles and barriers");
+static_assert(F_IMG % 16 == 0, "the weight image moves in one bulk copy");
+constexpr uint32_t ASBO = 128 / 8 * 128;  // row-group stride of a 128-column operand tile
 
-// packed bf16 weight image in the shared-memory layout of the fused kernel
-// (feature columns: residual 0..124, diagonal 128..252; padding zero)
+// weight image in the shared-memory layout of the fused kernel: the first
+// layer's residual columns (125, padded to 128), W2 and W3 (rows 125..127
+// zero) as K-major operand tiles, then b2 and b3
 __global__ void mlp_pack_kernel(const float* __restrict__ P, unsigned char* img) {
   const float* W1 = P;
   const float* b1 = W1 + 128 * 250;
@@ -288,61 +316,87 @@ __global__ void mlp_pack_kernel(const float* __restrict__ P, unsigned char* img)
   bf16* W3s = reinterpret_cast<bf16*>(img + F_W3);
   float* bs = reinterpret_cast<float*>(img + F_B);
   const int stride = gridDim.x * blockDim.x;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 128 * XS; e += stride) {
-    const int n = e / XS, k = e - n * XS;
-    const float v = k < 125 ? W1[n * 250 + k] : ((k >= 128 && k < 253) ? W1[n * 250 + k - 3] : 0.0f);
-    W1s[e] = __float2bfloat16_rn(v);
-  }
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 128 * HS; e += stride) {
-    const int n = e / HS, k = e - n * HS;
-    W2s[e] = __float2bfloat16_rn(k < 128 ? W2[n * 128 + k] : 0.0f);
-    W3s[e] = __float2bfloat16_rn((k < 128 && n < 125) ? W3[n * 128 + k] : 0.0f);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 128 * 128; e += stride) {
+    const int n = e >> 7, k = e & 127, o = tc::core_off(n, k, 128);
+    W1s[o] = __float2bfloat16_rn(k < FN3 ? W1[n * 250 + k] : 0.0f);
+    W2s[o] = __float2bfloat16_rn(W2[n * 128 + k]);
+    W3s[o] = __float2bfloat16_rn(n < FN3 ? W3[n * 128 + k] : 0.0f);
   }
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 128; e += stride) {
-    bs[e] = b1[e];
-    bs[128 + e] = b2[e];
-    bs[256 + e] = e < 125 ? b3[e] : 0.0f;
+    bs[e] = b2[e];
+    bs[128 + e] = e < FN3 ? b3[e] : 0.0f;
   }
+}
+
+// the 32 columns col0.. of this thread's TMEM lane, GELU, as bf16 into row i
+// of the activation tile
+__device__ __forceinline__ void act_store(uint32_t taddr, const float (&add)[32], unsigned char* A, int i, int col0) {
+  float v[32];
+  tc::tmem_ld32(taddr, v);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    uint4 w;
+    w.x = pack_bf16(gelu_f(v[8 * u + 0] + add[8 * u + 0]), gelu_f(v[8 * u + 1] + add[8 * u + 1]));
+    w.y = pack_bf16(gelu_f(v[8 * u + 2] + add[8 * u + 2]), gelu_f(v[8 * u + 3] + add[8 * u + 3]));
+    w.z = pack_bf16(gelu_f(v[8 * u + 4] + add[8 * u + 4]), gelu_f(v[8 * u + 5] + add[8 * u + 5]));
+    w.w = pack_bf16(gelu_f(v[8 * u + 6] + add[8 * u + 6]), gelu_f(v[8 * u + 7] + add[8 * u + 7]));
+    *reinterpret_cast<uint4*>(A + 2 * tc::core_off(i, col0 + 8 * u, 128)) = w;
+  }
+}
+
+// one layer on the tensor cores: D (TMEM columns dcol..) = A W^T over K = 128
+__device__ __forceinline__ void layer_mma(uint32_t tmem, uint32_t dcol, const unsigned char* A,
+                                          const unsigned char* W, uint64_t* bar) {
+  tc::fence_after();
+  const uint32_t a0 = tc::saddr(A), w0 = tc::saddr(W);
+#pragma unroll
+  for (int s = 0; s < 8; ++s)
+    tc::mma_bf16(tmem + dcol, tc::sdesc(a0 + s * 256, 128, ASBO), tc::sdesc(w0 + s * 256, 128, ASBO),
+                 tc::idesc_bf16(128, 128), s > 0 ? 1u : 0u);
+  tc::commit(bar);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T* __restrict__ r, T* x) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const bf16* W1s = reinterpret_cast<const bf16*>(smem + F_W1);
-  const bf16* W2s = reinterpret_cast<const bf16*>(smem + F_W2);
-  const bf16* W3s = reinterpret_cast<const bf16*>(smem + F_W3);
-  const float* bs = reinterpret_cast<const float*>(smem + F_B);
-  bf16* Xs = reinterpret_cast<bf16*>(smem + F_X);
-  bf16* Hs = reinterpret_cast<bf16*>(smem + F_H);
-  float* St = reinterpret_cast<float*>(smem + F_ST);
-  float* sc = reinterpret_cast<float*>(smem + F_SC);
-  float* si = reinterpret_cast<float*>(smem + F_SI);
-  int32_t* gs = reinterpret_cast<int32_t*>(smem + F_GS);
-  uint32_t* own = reinterpret_cast<uint32_t*>(smem + F_OWN);
-  uint16_t* mk = reinterpret_cast<uint16_t*>(smem + F_MK);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* sm = smem_raw + ((1024u - (tc::saddr(smem_raw) & 1023u)) & 1023u);
+  const float* bs = reinterpret_cast<const float*>(sm + F_B);
+  unsigned char* Atile = sm + F_A;
+  float* St = reinterpret_cast<float*>(sm + F_ST);
+  int32_t* gs = reinterpret_cast<int32_t*>(sm + F_GS);
+  uint32_t* own = reinterpret_cast<uint32_t*>(sm + F_OWN);
+  uint16_t* mk = reinterpret_cast<uint16_t*>(sm + F_MK);
+  float* si = reinterpret_cast<float*>(sm + F_SI);
+  float* sc = reinterpret_cast<float*>(sm + F_SC);
+  uint16_t* ntab = reinterpret_cast<uint16_t*>(sm + F_TAB);
+  uint64_t* wbar = reinterpret_cast<uint64_t*>(sm + F_BAR);
+  uint64_t* mbar = wbar + 1;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(wbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // the packed weight image, once per CTA (16-byte copies, all in flight)
-  {
-    constexpr int NV = (int)(F_IMG / 16), PER = (NV + FT - 1) / FT, CH = 6;
-    const uint4* src = reinterpret_cast<const uint4*>(P.wimg);
-    uint4* dst = reinterpret_cast<uint4*>(smem);
-#pragma unroll 1
-    for (int u0 = 0; u0 < PER; u0 += CH) {
-      uint4 v[CH];
-#pragma unroll
-      for (int u = 0; u < CH; ++u)
-        if (u0 + u < PER && tid + (u0 + u) * FT < NV) v[u] = src[tid + (u0 + u) * FT];
-#pragma unroll
-      for (int u = 0; u < CH; ++u)
-        if (u0 + u < PER && tid + (u0 + u) * FT < NV) dst[tid + (u0 + u) * FT] = v[u];
-    }
+  if (warp == 0) tc::tmem_alloc(tslot, 256);
+  if (tid == 0) {
+    tc::mbar_init(wbar, 1);
+    tc::mbar_init(mbar, 1);
   }
+  if (tid < FN3) {  // entity slot (bits 0..4) and offset (bits 8..) of node tid
+    int slot, off;
+    node_slot<FK>(tid % 5, (tid / 5) % 5, tid / 25, slot, off);
+    ntab[tid] = (uint16_t)(slot | (off << 8));
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  if (tid == 0) tc::bulk_g2s(sm, P.wimg, (uint32_t)F_IMG, wbar);
+  bool ok = __syncthreads_and(tc::mbar_wait(wbar, 0));
 
-  const int rb = warp & 3, cq = warp >> 2;  // rows 16 rb .., columns 32 cq ..
-  const int g = lane >> 2, t4 = lane & 3;
+  const int q = warp & 3, cg = warp >> 2;  // TMEM lanes 32 q .., columns 32 cg ..
+  const int row = 32 * q + lane, col0 = 32 * cg;
+  const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+  uint32_t phase = 0;
   const int64_t nbatch = (P.n_cells + FC - 1) / FC;
-  for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
+  for (int64_t bt = blockIdx.x; ok && bt < nbatch; bt += gridDim.x) {
     const int64_t c0 = bt * FC;
     const int nc = (int)(P.n_cells - c0 < FC ? P.n_cells - c0 : FC);
     for (int e = tid; e < FC * NSLOT; e += FT) gs[e] = e < nc * NSLOT ? P.gstart[c0 * NSLOT + e] : -1;
@@ -351,9 +405,9 @@ __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T*
       own[tid] = tid < nc ? P.own[c0 + tid] : 0u;
     }
     __syncthreads();
-    // gather the residual at the 125 nodes of every cell (GH loads in flight per thread)
+    // gather the residual at the 125 nodes of every cell
 #pragma unroll 1
-    for (int u0 = 0; u0 < GPT; u0 += GH) {
+    for (int u0 = 0; u0 * FT < FC * FN3; u0 += GH) {
       float v[GH];
 #pragma unroll
       for (int u = 0; u < GH; ++u) {
@@ -361,27 +415,26 @@ __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T*
         v[u] = 0.0f;
         if (e < FC * FN3) {
           const int i = e / FN3, j = e - i * FN3;
-          int slot, off;
-          node_slot<FK>(j % 5, (j / 5) % 5, j / 25, slot, off);
-          const int32_t base = gs[i * NSLOT + slot];
-          if (base >= 0) v[u] = (float)r[base + off];
+          const int t = ntab[j];
+          const int32_t base = gs[i * NSLOT + (t & 31)];
+          if (base >= 0) v[u] = (float)r[base + (t >> 8)];
         }
       }
 #pragma unroll
       for (int u = 0; u < GH; ++u) {
         const int e = tid + (u0 + u) * FT;
         if (e < FC * FN3) {
-          const int i = e / FN3, j = e - i * FN3;
-          St[i * SS + j] = v[u];
+          const int i = e / FN3;
+          St[i * SS + (e - i * FN3)] = v[u];
         }
       }
     }
     const int hang = __syncthreads_or(tid < nc && (mk[tid] & MASK_HANG));
     if (hang) hanging_all<FK, false, float, SS>(St, mk, nc);
-    // cell norms and scales: warp w handles cells 4w .. 4w + 3
-#pragma unroll
-    for (int q = 0; q < FC / (FT / 32); ++q) {
-      const int i = warp * (FC / (FT / 32)) + q;
+    // cell norms and scales: warp w handles cells 8 w .. 8 w + 7
+#pragma unroll 1
+    for (int c = 0; c < FC / (FT / 32); ++c) {
+      const int i = warp * (FC / (FT / 32)) + c;
       float ss = 0.0f;
       for (int j = lane; j < FN3; j += 32) ss += St[i * SS + j] * St[i * SS + j];
 #pragma unroll
@@ -390,68 +443,74 @@ __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T*
         const float s = sqrtf(ss);
         const float h = i < nc ? (float)(P.dom / (double)(1u << P.meta[c0 + i].level)) : 1.0f;
         si[i] = s > 0.0f ? 1.0f / s : 0.0f;
-        sc[i] = s / (h * (float)P.abar);
+        sc[i] = i < nc ? s / (h * (float)P.abar) : 0.0f;
       }
     }
     __syncthreads();
-    // features: bf16(r / s) in columns 0..127, the diagonal features in 128..255
+    // features bf16(r / s) as the A operand; each warp writes whole core matrices
     for (int e = tid; e < FC * 64; e += FT) {
-      const int i = e >> 6, j = (e & 63) * 2;
-      const float v0 = j < FN3 ? St[i * SS + j] * si[i] : 0.0f;
-      const float v1 = j + 1 < FN3 ? St[i * SS + j + 1] * si[i] : 0.0f;
-      *reinterpret_cast<uint32_t*>(Xs + i * XS + j) = pack_bf16(v0, v1);
+      const int blk = e >> 5, l = e & 31;
+      const int i = 8 * (blk >> 4) + (l & 7), k = 8 * (blk & 15) + 2 * (l >> 3);
+      const float v0 = k < FN3 ? St[i * SS + k] * si[i] : 0.0f;
+      const float v1 = k + 1 < FN3 ? St[i * SS + k + 1] * si[i] : 0.0f;
+      *reinterpret_cast<uint32_t*>(Atile + 2 * tc::core_off(i, k, 128)) = pack_bf16(v0, v1);
     }
-    for (int e = tid; e < FC * 16; e += FT) {
-      const int i = e >> 4, q = e & 15;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (i < nc) v = reinterpret_cast<const uint4*>(P.dfeat + (c0 + i) * MLP_DF)[q];
-      *reinterpret_cast<uint4*>(Xs + i * XS + 128 + q * 8) = v;
-    }
+    tc::fence_async_smem();
+    tc::fence_before();
     __syncthreads();
-    // layer 1: H = gelu(X W1^T + b1)
-    {
-      float acc[4][4] = {};
-      warp_gemm<4>(Xs + rb * 16 * XS, XS, W1s + cq * 32 * XS, XS, 256, acc);
+    // layer 1: H1 = gelu(X W1r^T + dproj), dproj holding b1 and the diagonal features' part
+    if (tid == 0) layer_mma(tmem, 0, Atile, sm + F_W1, mbar);
+    float add[32];
+    if (row < nc) {
+      const float4* dp = reinterpret_cast<const float4*>(P.dproj + (c0 + row) * 128 + col0);
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int col = cq * 32 + nt * 8 + 2 * t4, row = rb * 16 + g;
-        *reinterpret_cast<uint32_t*>(Hs + row * HS + col) =
-            pack_bf16(gelu_f(acc[nt][0] + bs[col]), gelu_f(acc[nt][1] + bs[col + 1]));
-        *reinterpret_cast<uint32_t*>(Hs + (row + 8) * HS + col) =
-            pack_bf16(gelu_f(acc[nt][2] + bs[col]), gelu_f(acc[nt][3] + bs[col + 1]));
+      for (int u = 0; u < 8; ++u) {
+        const float4 w = dp[u];
+        add[4 * u] = w.x, add[4 * u + 1] = w.y, add[4 * u + 2] = w.z, add[4 * u + 3] = w.w;
       }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) add[j] = 0.0f;
     }
+    ok = __syncthreads_and(tc::mbar_wait(mbar, phase));
+    phase ^= 1u;
+    tc::fence_after();
+    if (!ok) break;
+    act_store(tl + (uint32_t)col0, add, Atile, row, col0);
+    tc::fence_async_smem();
+    tc::fence_before();
     __syncthreads();
-    // layer 2: X[:, 0..127] = gelu(H W2^T + b2)
+    // layer 2: H2 = gelu(H1 W2^T + b2), accumulated in TMEM columns 128..
+    if (tid == 0) layer_mma(tmem, 128, Atile, sm + F_W2, mbar);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) add[j] = bs[col0 + j];
+    ok = __syncthreads_and(tc::mbar_wait(mbar, phase));
+    phase ^= 1u;
+    tc::fence_after();
+    if (!ok) break;
+    act_store(tl + 128u + (uint32_t)col0, add, Atile, row, col0);
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    // layer 3: correction c = (H2 W3^T + b3) s / (h a) into the cell buffer
+    if (tid == 0) layer_mma(tmem, 0, Atile, sm + F_W3, mbar);
+    ok = __syncthreads_and(tc::mbar_wait(mbar, phase));
+    phase ^= 1u;
+    tc::fence_after();
+    if (!ok) break;
     {
-      float acc[4][4] = {};
-      warp_gemm<4>(Hs + rb * 16 * HS, HS, W2s + cq * 32 * HS, HS, 128, acc);
+      float v[32];
+      tc::tmem_ld32(tl + (uint32_t)col0, v);
+      const float scale = sc[row];
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int col = cq * 32 + nt * 8 + 2 * t4, row = rb * 16 + g;
-        *reinterpret_cast<uint32_t*>(Xs + row * XS + col) =
-            pack_bf16(gelu_f(acc[nt][0] + bs[128 + col]), gelu_f(acc[nt][1] + bs[128 + col + 1]));
-        *reinterpret_cast<uint32_t*>(Xs + (row + 8) * XS + col) =
-            pack_bf16(gelu_f(acc[nt][2] + bs[128 + col]), gelu_f(acc[nt][3] + bs[128 + col + 1]));
-      }
+      for (int j = 0; j < 32; ++j)
+        if (col0 + j < FN3) St[row * SS + col0 + j] = (v[j] + bs[128 + col0 + j]) * scale;
     }
+    tc::fence_before();
     __syncthreads();
-    // layer 3: correction c = (X W3^T + b3) s / (h a)
-    {
-      float acc[4][4] = {};
-      warp_gemm<4>(Xs + rb * 16 * XS, XS, W3s + cq * 32 * HS, HS, 128, acc);
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int col = cq * 32 + nt * 8 + 2 * t4 + (e & 1), row = rb * 16 + g + (e >> 1) * 8;
-          if (col < FN3) St[row * SS + col] = (acc[nt][e] + bs[256 + col]) * sc[row];
-        }
-    }
-    __syncthreads();
-    // owner-selected update of x (GH loads in flight per thread)
+    // owner-selected update of x
 #pragma unroll 1
-    for (int u0 = 0; u0 < GPT; u0 += GH) {
+    for (int u0 = 0; u0 * FT < FC * FN3; u0 += GH) {
       int idx[GH];
       T xv[GH];
 #pragma unroll
@@ -460,9 +519,8 @@ __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T*
         idx[u] = -1;
         if (e < FC * FN3) {
           const int i = e / FN3, j = e - i * FN3;
-          int slot, off;
-          node_slot<FK>(j % 5, (j / 5) % 5, j / 25, slot, off);
-          if (i < nc && ((own[i] >> slot) & 1u)) idx[u] = gs[i * NSLOT + slot] + off;
+          const int t = ntab[j];
+          if ((own[i] >> (t & 31)) & 1u) idx[u] = gs[i * NSLOT + (t & 31)] + (t >> 8);
         }
         if (idx[u] >= 0) xv[u] = x[idx[u]];
       }
@@ -470,13 +528,20 @@ __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T*
       for (int u = 0; u < GH; ++u) {
         const int e = tid + (u0 + u) * FT;
         if (idx[u] >= 0) {
-          const int i = e / FN3, j = e - i * FN3;
-          x[idx[u]] = xv[u] + (T)St[i * SS + j];
+          const int i = e / FN3;
+          x[idx[u]] = xv[u] + (T)St[i * SS + (e - i * FN3)];
         }
       }
     }
     __syncthreads();
   }
+  if (!ok) {
+    if (tid == 0) atomicAdd(&g_wait_timeouts, 1u);
+    tc::mbar_wait(mbar, phase ^ 1u);  // once more for the products in flight
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
 inline int grid_for(int64_t n, int block) {
@@ -517,8 +582,8 @@ void launch_mlp_dfeat(const double* D, int64_t n, int n3, const CellMeta* meta, 
 
 void launch_gemm_bf16(const GemmArgs& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0) return;
-  dim3 grid((g.N + GT - 1) / GT, (g.M + GT - 1) / GT);
-  gemm_bf16_kernel<<<grid, 256, 0, s>>>(g);
+  dim3 grid((g.N + GN - 1) / GN, (g.M + GM - 1) / GM);
+  gemm_tc_kernel<<<grid, GTH, 0, s>>>(g);
   note_launches(1);
 }
 
@@ -558,37 +623,42 @@ void launch_adam(float* p, const float* g, float* m, float* v, int64_t n, float 
 size_t mlp_fused_smem_bytes() { return F_BYTES; }
 size_t mlp_image_bytes() { return F_IMG; }
 
-void launch_mlp_pack(const float* params, void* image, cudaStream_t s) {
+void launch_mlp_prepare(const float* params, const uint16_t* dfeat, int64_t n_cells, void* image, float* dproj,
+                        cudaStream_t s) {
   mlp_pack_kernel<<<64, 256, 0, s>>>(params, static_cast<unsigned char*>(image));
   note_launches(1);
+  // dproj = b1 + dfeat[:, 0..124] W1[:, 125..249]^T (bf16 operands, fp32 accumulation)
+  const float* W1 = params;
+  const float* b1 = W1 + 128 * 250;
+  GemmArgs g{nullptr, MLP_DF, 1, W1 + FN3, 1, 250, dproj, 128, b1, (int)n_cells, 128, FN3};
+  g.Ab = dfeat;
+  launch_gemm_bf16(g, s);
+}
+
+unsigned int wait_timeouts(bool reset) {
+  unsigned int n = 0;
+  if (cudaMemcpyFromSymbol(&n, g_wait_timeouts, sizeof(n)) != cudaSuccess) return ~0u;
+  if (reset) {
+    const unsigned int z = 0;
+    if (cudaMemcpyToSymbol(g_wait_timeouts, &z, sizeof(z)) != cudaSuccess) return ~0u;
+  }
+  return n;
 }
 
 cudaError_t launch_mlp_correct(const MlpFused& P, bool fp64, const void* r, void* x, cudaStream_t s) {
   if (P.n_cells <= 0) return cudaSuccess;
-  static int n_sm = 0;
-  static bool attr_set[2] = {false, false};
-  if (!n_sm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (n_sm <= 0) n_sm = 152;
-  }
+  if ((reinterpret_cast<uintptr_t>(P.wimg) & 15) || (reinterpret_cast<uintptr_t>(P.dproj) & 15))
+    return cudaErrorMisalignedAddress;
   const int64_t nb = (P.n_cells + FC - 1) / FC;
-  const int grid = (int)std::min<int64_t>(nb, n_sm);
+  const int grid = (int)std::min<int64_t>(nb, device_sm_count());
   cudaError_t e;
   if (fp64) {
-    if (!attr_set[1]) {
-      e = cudaFuncSetAttribute(mlp_correct_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_BYTES);
-      if (e != cudaSuccess) return e;
-      attr_set[1] = true;
-    }
+    e = smem_allow(mlp_correct_kernel<double>, F_BYTES);
+    if (e != cudaSuccess) return e;
     mlp_correct_kernel<double><<<grid, FT, F_BYTES, s>>>(P, static_cast<const double*>(r), static_cast<double*>(x));
   } else {
-    if (!attr_set[0]) {
-      e = cudaFuncSetAttribute(mlp_correct_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_BYTES);
-      if (e != cudaSuccess) return e;
-      attr_set[0] = true;
-    }
+    e = smem_allow(mlp_correct_kernel<float>, F_BYTES);
+    if (e != cudaSuccess) return e;
     mlp_correct_kernel<float><<<grid, FT, F_BYTES, s>>>(P, static_cast<const float*>(r), static_cast<float*>(x));
   }
   note_launches(1);

@@ -2,6 +2,7 @@
 // (forward pass, backward pass by the chain rule, Adam) and its C ABI.
 // The network and the update rule are an extension outside the paper: the
 // paper smooths with Chebyshev around point Jacobi (Sec. 3.3).
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <memory>
@@ -66,7 +67,13 @@ void MlpNet::gradient(const float* X, const float* T, const float* W, int B, flo
   launch_colsum(dB.as<float>(), B, n_h, G + ob1(), s);
 }
 
+void MlpNet::touch() {
+  static std::atomic<uint64_t> counter{0};
+  version = ++counter;
+}
+
 void MlpNet::adam(float lr, cudaStream_t s) {
+  touch();
   ++steps;
   const float bc1 = (float)(1.0 - std::pow((double)MLP_BETA1, (double)steps));
   const float bc2 = (float)(1.0 - std::pow((double)MLP_BETA2, (double)steps));
@@ -100,6 +107,7 @@ int gcmg_mlp_create(int n_in, int n_hidden, int n_out, gcmg_mlp** out) {
     ck(cudaMemset(N.grad.p, 0, b), "memset");
     ck(cudaMemset(N.m.p, 0, b), "memset");
     ck(cudaMemset(N.v.p, 0, b), "memset");
+    N.touch();
     *out = net.release();
   });
 }
@@ -123,6 +131,7 @@ int gcmg_mlp_set_params(gcmg_mlp* net, const float* params, void* stream) {
     ck(cudaMemsetAsync(N.m.p, 0, b, s), "memset");
     ck(cudaMemsetAsync(N.v.p, 0, b, s), "memset");
     N.steps = 0;
+    N.touch();
   });
 }
 

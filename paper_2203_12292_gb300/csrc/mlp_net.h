@@ -14,6 +14,11 @@ struct MlpNet {
   int64_t n_params = 0;
   DevBuf params, grad, m, v;
   int64_t steps = 0;  // Adam steps taken since the parameters were set
+  // process-wide unique tag of the current parameter values (new on creation,
+  // gcmg_mlp_set_params and every Adam step), so that derived data (the
+  // inference weight image) is rebuilt only when the parameters changed
+  uint64_t version = 0;
+  void touch();
   // work buffers for `cap` rows
   int64_t cap = 0;
   DevBuf Xb, Tb, Wb, Z1, H1, Z2, H2, Y, dY, dA, dB, loss;

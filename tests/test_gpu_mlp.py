@@ -12,6 +12,11 @@ Tolerances:
   significand bits, through three layers);
 * a constant network (zero weights, output bias v) has no bf16 operand that
   matters, so owners and scaling are checked to 1e-6.
+
+The inference kernel works on batches of 128 cells; the 120-cell mesh is one
+ragged batch, the 960-cell mesh (cube refined three times, octant once more)
+seven full batches and a ragged one.  Every tensor-core wait is bounded, and
+the count of waits that gave up must stay zero.
 """
 import numpy as np
 import pytest
@@ -202,6 +207,52 @@ def test_correct(gcmg, q4, dtype):
     x2 = torch.zeros_like(r)
     q4.gm.mlp_correct(q4.L, net, 4 * r, x2)
     assert rel_err(x2.double().cpu().numpy(), 4 * x.double().cpu().numpy()) < 1e-6
+    assert gcmg.wait_timeouts() == 0
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_correct_several_batches(gcmg, dtype):
+    case = Q4Case(gcmg, synth.cube_octant(3, 1))
+    assert case.gm.n_cells(case.L) == 960
+    theta = synth.mlp_init(250, 128, 125, 43)
+    net = _net(gcmg, theta)
+    dt = torch.float64 if dtype == "f64" else torch.float32
+    rv = case.ovec(44)
+    if dtype == "f32":
+        rv = rv.astype(np.float32).astype(np.float64)
+    x = torch.zeros(case.gm.n_free(case.L), dtype=dt, device="cuda")
+    case.gm.mlp_correct(case.L, net, case.gvec(44, dt), x)
+    got = case.to_oracle(x)
+    ref_b = omlp.correction(case.space, case.shape, theta, rv, case.space.diagonal(), bf16=True)
+    assert np.abs(got - ref_b).max() <= 5e-3 * np.abs(ref_b).max()
+    assert gcmg.wait_timeouts() == 0
+
+
+def test_correct_follows_parameter_changes(gcmg, q4):
+    """the weight image and the first layer's diagonal part are rebuilt when
+    the parameters change (set_params, Adam steps), and only then"""
+    ta, tb = synth.mlp_init(250, 128, 125, 45), synth.mlp_init(250, 128, 125, 46)
+    r = q4.gvec(47)
+    net = _net(gcmg, ta)
+    xa = torch.zeros_like(r)
+    q4.gm.mlp_correct(q4.L, net, r, xa)
+    xa2 = torch.zeros_like(r)
+    q4.gm.mlp_correct(q4.L, net, r, xa2)
+    assert torch.equal(xa, xa2)
+    net.set_params(torch.tensor(tb, dtype=torch.float32, device="cuda"))
+    xb = torch.zeros_like(r)
+    q4.gm.mlp_correct(q4.L, net, r, xb)
+    xb_ref = torch.zeros_like(r)
+    q4.gm.mlp_correct(q4.L, _net(gcmg, tb), r, xb_ref)
+    assert torch.equal(xb, xb_ref) and not torch.equal(xa, xb)
+    # one Adam step changes the parameters, hence the correction
+    X = torch.rand(64, 250, dtype=torch.float32, device="cuda")
+    T = torch.rand(64, 125, dtype=torch.float32, device="cuda")
+    net.train(X, T, torch.arange(64, dtype=torch.int32, device="cuda"), 64, 1e-3)
+    xc = torch.zeros_like(r)
+    q4.gm.mlp_correct(q4.L, net, r, xc)
+    assert not torch.equal(xb, xc)
+    assert gcmg.wait_timeouts() == 0
 
 
 def test_smoother_arguments(gcmg, q4):
