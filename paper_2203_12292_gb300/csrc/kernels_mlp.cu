@@ -42,6 +42,18 @@ __device__ unsigned int g_wait_timeouts;
 __device__ __forceinline__ float bf16_bits_to_float(uint16_t u) { return __uint_as_float((uint32_t)u << 16); }
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU of the inference kernel, z Phi(z) with erf from the rational
+// approximation of Abramowitz & Stegun, Handbook of Mathematical Functions,
+// formula 7.1.26 (|error| <= 1.5e-7 for x >= 0; odd extension), far below the
+// bf16 rounding (2^-9 relative) its result goes through
+__device__ __forceinline__ float gelu_as(float z) {
+  const float x = fabsf(z) * 0.70710678118654752f;
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+  const float p =
+      t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+  const float erf_abs = fmaf(-p, __expf(-x * x), 1.0f);
+  return 0.5f * z * (1.0f + copysignf(erf_abs, z));
+}
 __device__ __forceinline__ float gelu_grad_f(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
@@ -278,26 +290,31 @@ __global__ void adam_kernel(float* p, const float* g, float* m, float* v, int64_
 // fused inference for Q4: 250 -> 128 -> 128 -> 125
 // ---------------------------------------------------------------------------
 constexpr int FK = 4, FN3 = 125, FC = 128, FT = 512;  // degree, nodes, cells per batch, threads
-constexpr int SS = 129;                                // row stride of the fp32 cell buffer (odd: no bank conflicts)
-constexpr int GH = 16;                                 // gathered values in flight per thread
+// row stride of the fp32 cell buffer: 16-byte rows for the async copies of
+// the first layer's diagonal part, four-row bank period
+constexpr int SS = 132;
 // shared memory (offsets from a 1024-byte aligned base):
 // [W1 residual columns | W2 | W3 (bf16 operand tiles, 128 x 128 each) | b2, b3 (fp32)] = the weight image,
-// then the activation tile A (bf16 128 x 128: features, then H1, then H2), the fp32 cell buffer, per-cell data
+// then the activation tile A (bf16 128 x 128: features, then H1, then H2), the fp32 cell buffer
+// (residual, then the diagonal part of layer 1, then the correction), two buffers of slot starts
+// (the next batch's arrive by bulk copy while this one runs), per-cell data, barriers
 constexpr size_t F_W1 = 0, F_W2 = 32768, F_W3 = 65536, F_B = 98304;
 constexpr size_t F_IMG = F_B + 2 * 128 * 4;  // bytes of the weight image
 constexpr size_t F_A = F_IMG;
 constexpr size_t F_ST = F_A + 32768;
 constexpr size_t F_GS = F_ST + (size_t)FC * SS * 4;
-constexpr size_t F_OWN = F_GS + (size_t)FC * NSLOT * 4;
+constexpr size_t GS_BYTES = (size_t)FC * NSLOT * 4;
+constexpr size_t F_OWN = F_GS + 2 * GS_BYTES;
 constexpr size_t F_MK = F_OWN + FC * 4;
-constexpr size_t F_SI = F_MK + FC * 2;
+constexpr size_t F_LV = F_MK + FC * 2;
+constexpr size_t F_SI = F_LV + FC * 4;
 constexpr size_t F_SC = F_SI + FC * 4;
-constexpr size_t F_TAB = F_SC + FC * 4;
-constexpr size_t F_BAR = F_TAB + 128 * 2;
-constexpr size_t F_END = F_BAR + 32;
+constexpr size_t F_BAR = F_SC + FC * 4;
+constexpr size_t F_END = F_BAR + 48;
 constexpr size_t F_BYTES = F_END + 1024;  // room to align the base
 static_assert(F_BYTES <= 232448, "fused MLP kernel exceeds the shared memory of a CTA");
-static_assert(F_A % 1024 == 0 && F_BAR % 8 == 0, "aligned operand tiles and barriers");
+static_assert(F_A % 1024 == 0 && F_ST % 16 == 0 && F_GS % 16 == 0 && GS_BYTES % 16 == 0 && F_BAR % 8 == 0,
+              "aligned operand tiles, copies and barriers");
 static_assert(F_IMG % 16 == 0, "the weight image moves in one bulk copy");
 constexpr uint32_t ASBO = 128 / 8 * 128;  // row-group stride of a 128-column operand tile
 
@@ -336,10 +353,10 @@ __device__ __forceinline__ void act_store(uint32_t taddr, const float (&add)[32]
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     uint4 w;
-    w.x = pack_bf16(gelu_f(v[8 * u + 0] + add[8 * u + 0]), gelu_f(v[8 * u + 1] + add[8 * u + 1]));
-    w.y = pack_bf16(gelu_f(v[8 * u + 2] + add[8 * u + 2]), gelu_f(v[8 * u + 3] + add[8 * u + 3]));
-    w.z = pack_bf16(gelu_f(v[8 * u + 4] + add[8 * u + 4]), gelu_f(v[8 * u + 5] + add[8 * u + 5]));
-    w.w = pack_bf16(gelu_f(v[8 * u + 6] + add[8 * u + 6]), gelu_f(v[8 * u + 7] + add[8 * u + 7]));
+    w.x = pack_bf16(gelu_as(v[8 * u + 0] + add[8 * u + 0]), gelu_as(v[8 * u + 1] + add[8 * u + 1]));
+    w.y = pack_bf16(gelu_as(v[8 * u + 2] + add[8 * u + 2]), gelu_as(v[8 * u + 3] + add[8 * u + 3]));
+    w.z = pack_bf16(gelu_as(v[8 * u + 4] + add[8 * u + 4]), gelu_as(v[8 * u + 5] + add[8 * u + 5]));
+    w.w = pack_bf16(gelu_as(v[8 * u + 6] + add[8 * u + 6]), gelu_as(v[8 * u + 7] + add[8 * u + 7]));
     *reinterpret_cast<uint4*>(A + 2 * tc::core_off(i, col0 + 8 * u, 128)) = w;
   }
 }
@@ -356,6 +373,15 @@ __device__ __forceinline__ void layer_mma(uint32_t tmem, uint32_t dcol, const un
   tc::commit(bar);
 }
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::saddr(dst)), "l"(src) : "memory");
+}
+
+// x += v with no value returned (each DoF has one owner: no contention, the
+// same sum as a plain read-modify-write, and no wait on the read)
+__device__ __forceinline__ void add_global(float* p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void add_global(double* p, double v) { atomicAdd(p, v); }
+
 template <typename T>
 __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T* __restrict__ r, T* x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -363,87 +389,122 @@ __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T*
   const float* bs = reinterpret_cast<const float*>(sm + F_B);
   unsigned char* Atile = sm + F_A;
   float* St = reinterpret_cast<float*>(sm + F_ST);
-  int32_t* gs = reinterpret_cast<int32_t*>(sm + F_GS);
   uint32_t* own = reinterpret_cast<uint32_t*>(sm + F_OWN);
   uint16_t* mk = reinterpret_cast<uint16_t*>(sm + F_MK);
+  float* hs = reinterpret_cast<float*>(sm + F_LV);
   float* si = reinterpret_cast<float*>(sm + F_SI);
   float* sc = reinterpret_cast<float*>(sm + F_SC);
-  uint16_t* ntab = reinterpret_cast<uint16_t*>(sm + F_TAB);
   uint64_t* wbar = reinterpret_cast<uint64_t*>(sm + F_BAR);
   uint64_t* mbar = wbar + 1;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(wbar + 2);
+  uint64_t* gbar = wbar + 2;  // two: one per slot-start buffer
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(wbar + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) tc::tmem_alloc(tslot, 256);
   if (tid == 0) {
     tc::mbar_init(wbar, 1);
     tc::mbar_init(mbar, 1);
-  }
-  if (tid < FN3) {  // entity slot (bits 0..4) and offset (bits 8..) of node tid
-    int slot, off;
-    node_slot<FK>(tid % 5, (tid / 5) % 5, tid / 25, slot, off);
-    ntab[tid] = (uint16_t)(slot | (off << 8));
+    tc::mbar_init(gbar, 1);
+    tc::mbar_init(gbar + 1, 1);
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
-  if (tid == 0) tc::bulk_g2s(sm, P.wimg, (uint32_t)F_IMG, wbar);
+  const int64_t nbatch = (P.n_cells + FC - 1) / FC;
+  // slot starts of batch bt: a bulk copy for full batches, plain loads for the ragged one
+  auto full = [&](int64_t bt) { return bt < nbatch && (bt + 1) * FC <= P.n_cells; };
+  // copies of slot starts in flight (bit b: buffer b) and the parity each buffer's next completion has
+  uint32_t gout = 0, gpar = 0;
+  if (tid == 0) {
+    tc::bulk_g2s(sm, P.wimg, (uint32_t)F_IMG, wbar);
+    if (full(blockIdx.x)) tc::bulk_g2s(sm + F_GS, P.gstart + (int64_t)blockIdx.x * FC * NSLOT, (uint32_t)GS_BYTES, gbar);
+  }
+  if (full(blockIdx.x)) gout = 1u;
+  // per-cell data of the next batch, one cell per thread, prefetched into registers
+  uint32_t pm = 0, po = 0;
+  if (tid < FC && (int64_t)blockIdx.x < nbatch && (int64_t)blockIdx.x * FC + tid < P.n_cells) {
+    const CellMeta& m = P.meta[(int64_t)blockIdx.x * FC + tid];
+    pm = m.mask | ((uint32_t)m.level << 16);
+    po = P.own[(int64_t)blockIdx.x * FC + tid];
+  }
   bool ok = __syncthreads_and(tc::mbar_wait(wbar, 0));
 
+  // gather and update: node jn (entity slot nslot, offset noff) of cells cq, cq + 4, ..
+  const int jn = tid & 127, cq = tid >> 7;
+  const bool node_ok = jn < FN3;
+  int nslot = 0, noff = 0;
+  if (node_ok) node_slot<FK>(jn % 5, (jn / 5) % 5, jn / 25, nslot, noff);
+  const float dom = (float)P.dom, abar = (float)P.abar;
   const int q = warp & 3, cg = warp >> 2;  // TMEM lanes 32 q .., columns 32 cg ..
   const int row = 32 * q + lane, col0 = 32 * cg;
   const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
   uint32_t phase = 0;
-  const int64_t nbatch = (P.n_cells + FC - 1) / FC;
-  for (int64_t bt = blockIdx.x; ok && bt < nbatch; bt += gridDim.x) {
+  int it = 0;
+  for (int64_t bt = blockIdx.x; ok && bt < nbatch; bt += gridDim.x, ++it) {
     const int64_t c0 = bt * FC;
     const int nc = (int)(P.n_cells - c0 < FC ? P.n_cells - c0 : FC);
-    for (int e = tid; e < FC * NSLOT; e += FT) gs[e] = e < nc * NSLOT ? P.gstart[c0 * NSLOT + e] : -1;
+    const int buf = it & 1;
+    int32_t* gs = reinterpret_cast<int32_t*>(sm + F_GS + buf * GS_BYTES);
     if (tid < FC) {
-      mk[tid] = tid < nc ? P.meta[c0 + tid].mask : 0;
-      own[tid] = tid < nc ? P.own[c0 + tid] : 0u;
+      mk[tid] = (uint16_t)(pm & 0xFFFFu);
+      hs[tid] = dom * __int_as_float((127 - (int)(pm >> 16)) << 23);  // dom 2^-level, exact
+      own[tid] = po;
     }
-    __syncthreads();
-    // gather the residual at the 125 nodes of every cell
-#pragma unroll 1
-    for (int u0 = 0; u0 * FT < FC * FN3; u0 += GH) {
-      float v[GH];
-#pragma unroll
-      for (int u = 0; u < GH; ++u) {
-        const int e = tid + (u0 + u) * FT;
-        v[u] = 0.0f;
-        if (e < FC * FN3) {
-          const int i = e / FN3, j = e - i * FN3;
-          const int t = ntab[j];
-          const int32_t base = gs[i * NSLOT + (t & 31)];
-          if (base >= 0) v[u] = (float)r[base + (t >> 8)];
-        }
+    if (gout >> buf & 1u) {
+      ok = tc::mbar_wait(gbar + buf, gpar >> buf & 1u);
+      if (ok) {
+        gout &= ~(1u << buf);
+        gpar ^= 1u << buf;
       }
-#pragma unroll
-      for (int u = 0; u < GH; ++u) {
-        const int e = tid + (u0 + u) * FT;
-        if (e < FC * FN3) {
-          const int i = e / FN3;
-          St[i * SS + (e - i * FN3)] = v[u];
-        }
+    } else {
+      for (int e = tid; e < FC * NSLOT; e += FT) gs[e] = e < nc * NSLOT ? P.gstart[c0 * NSLOT + e] : -1;
+    }
+    // the next batch of this CTA: slot starts into the other buffer (its last
+    // reader, the previous batch, has passed the barrier at its end)
+    const int64_t nb = bt + gridDim.x;
+    if (full(nb)) {
+      if (tid == 0) {
+        tc::fence_async_smem();
+        tc::bulk_g2s(sm + F_GS + (buf ^ 1) * GS_BYTES, P.gstart + nb * FC * NSLOT, (uint32_t)GS_BYTES,
+                     gbar + (buf ^ 1));
       }
+      gout |= 1u << (buf ^ 1);
+    }
+    pm = 0, po = 0;
+    if (tid < FC && nb < nbatch && nb * FC + tid < P.n_cells) {
+      const CellMeta& m = P.meta[nb * FC + tid];
+      pm = m.mask | ((uint32_t)m.level << 16);
+      po = P.own[nb * FC + tid];
+    }
+    ok = __syncthreads_and(ok);
+    if (!ok) break;
+    // gather the residual: thread (jn, cq) fetches node jn of cells cq, cq + 4, ..
+    {
+      float v[FC / 4];
+#pragma unroll
+      for (int u = 0; u < FC / 4; ++u) {
+        const int32_t base = node_ok ? gs[(cq + 4 * u) * NSLOT + nslot] : -1;
+        v[u] = base >= 0 ? (float)r[base + noff] : 0.0f;
+      }
+      if (node_ok)
+#pragma unroll
+        for (int u = 0; u < FC / 4; ++u) St[(cq + 4 * u) * SS + jn] = v[u];
     }
     const int hang = __syncthreads_or(tid < nc && (mk[tid] & MASK_HANG));
     if (hang) hanging_all<FK, false, float, SS>(St, mk, nc);
-    // cell norms and scales: warp w handles cells 8 w .. 8 w + 7
-#pragma unroll 1
-    for (int c = 0; c < FC / (FT / 32); ++c) {
-      const int i = warp * (FC / (FT / 32)) + c;
+    // cell norms and scales: four threads per cell
+    {
+      const int i = tid >> 2, p = tid & 3;
       float ss = 0.0f;
-      for (int j = lane; j < FN3; j += 32) ss += St[i * SS + j] * St[i * SS + j];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-      if (lane == 0) {
+#pragma unroll 8
+      for (int j = p; j < FN3; j += 4) ss = fmaf(St[i * SS + j], St[i * SS + j], ss);
+      ss += __shfl_xor_sync(0xffffffffu, ss, 1);
+      ss += __shfl_xor_sync(0xffffffffu, ss, 2);
+      if (p == 0) {
         const float s = sqrtf(ss);
-        const float h = i < nc ? (float)(P.dom / (double)(1u << P.meta[c0 + i].level)) : 1.0f;
         si[i] = s > 0.0f ? 1.0f / s : 0.0f;
-        sc[i] = i < nc ? s / (h * (float)P.abar) : 0.0f;
+        sc[i] = i < nc ? s / (hs[i] * abar) : 0.0f;
       }
     }
     __syncthreads();
@@ -458,37 +519,47 @@ __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T*
     tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
-    // layer 1: H1 = gelu(X W1r^T + dproj), dproj holding b1 and the diagonal features' part
+    // layer 1: H1 = gelu(X W1r^T + dproj), dproj holding b1 and the diagonal features' part;
+    // dproj rows move into the (now free) cell buffer while the tensor cores run
     if (tid == 0) layer_mma(tmem, 0, Atile, sm + F_W1, mbar);
-    float add[32];
-    if (row < nc) {
-      const float4* dp = reinterpret_cast<const float4*>(P.dproj + (c0 + row) * 128 + col0);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float4 w = dp[u];
-        add[4 * u] = w.x, add[4 * u + 1] = w.y, add[4 * u + 2] = w.z, add[4 * u + 3] = w.w;
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) add[j] = 0.0f;
+    for (int u = 0; u < FC * 32 / FT; ++u) {
+      const int e = tid + u * FT, i = e >> 5, c = e & 31;
+      float* d = St + i * SS + 4 * c;
+      if (i < nc)
+        cp_async16(d, P.dproj + (c0 + i) * 128 + 4 * c);
+      else
+        *reinterpret_cast<float4*>(d) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     ok = __syncthreads_and(tc::mbar_wait(mbar, phase));
     phase ^= 1u;
     tc::fence_after();
     if (!ok) break;
-    act_store(tl + (uint32_t)col0, add, Atile, row, col0);
+    {
+      float add[32];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 w = *reinterpret_cast<const float4*>(St + row * SS + col0 + 4 * u);
+        add[4 * u] = w.x, add[4 * u + 1] = w.y, add[4 * u + 2] = w.z, add[4 * u + 3] = w.w;
+      }
+      act_store(tl + (uint32_t)col0, add, Atile, row, col0);
+    }
     tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
     // layer 2: H2 = gelu(H1 W2^T + b2), accumulated in TMEM columns 128..
     if (tid == 0) layer_mma(tmem, 128, Atile, sm + F_W2, mbar);
-#pragma unroll
-    for (int j = 0; j < 32; ++j) add[j] = bs[col0 + j];
     ok = __syncthreads_and(tc::mbar_wait(mbar, phase));
     phase ^= 1u;
     tc::fence_after();
     if (!ok) break;
-    act_store(tl + 128u + (uint32_t)col0, add, Atile, row, col0);
+    {
+      float add[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) add[j] = bs[col0 + j];
+      act_store(tl + 128u + (uint32_t)col0, add, Atile, row, col0);
+    }
     tc::fence_async_smem();
     tc::fence_before();
     __syncthreads();
@@ -503,41 +574,33 @@ __global__ void __launch_bounds__(FT, 1) mlp_correct_kernel(MlpFused P, const T*
       tc::tmem_ld32(tl + (uint32_t)col0, v);
       const float scale = sc[row];
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (col0 + j < FN3) St[row * SS + col0 + j] = (v[j] + bs[128 + col0 + j]) * scale;
+      for (int u = 0; u < 8; ++u) {
+        float4 w;
+        w.x = (v[4 * u] + bs[128 + col0 + 4 * u]) * scale;
+        w.y = (v[4 * u + 1] + bs[128 + col0 + 4 * u + 1]) * scale;
+        w.z = (v[4 * u + 2] + bs[128 + col0 + 4 * u + 2]) * scale;
+        w.w = (v[4 * u + 3] + bs[128 + col0 + 4 * u + 3]) * scale;
+        *reinterpret_cast<float4*>(St + row * SS + col0 + 4 * u) = w;
+      }
     }
     tc::fence_before();
     __syncthreads();
-    // owner-selected update of x
-#pragma unroll 1
-    for (int u0 = 0; u0 * FT < FC * FN3; u0 += GH) {
-      int idx[GH];
-      T xv[GH];
-#pragma unroll
-      for (int u = 0; u < GH; ++u) {
-        const int e = tid + (u0 + u) * FT;
-        idx[u] = -1;
-        if (e < FC * FN3) {
-          const int i = e / FN3, j = e - i * FN3;
-          const int t = ntab[j];
-          if ((own[i] >> (t & 31)) & 1u) idx[u] = gs[i * NSLOT + (t & 31)] + (t >> 8);
-        }
-        if (idx[u] >= 0) xv[u] = x[idx[u]];
+    // owner-selected update of x, node jn of cells cq, cq + 4, ..
+    if (node_ok)
+#pragma unroll 8
+      for (int u = 0; u < FC / 4; ++u) {
+        const int i = cq + 4 * u;
+        if ((own[i] >> nslot) & 1u) add_global(x + gs[i * NSLOT + nslot] + noff, (T)St[i * SS + jn]);
       }
-#pragma unroll
-      for (int u = 0; u < GH; ++u) {
-        const int e = tid + (u0 + u) * FT;
-        if (idx[u] >= 0) {
-          const int i = e / FN3;
-          x[idx[u]] = xv[u] + (T)St[i * SS + (e - i * FN3)];
-        }
-      }
-    }
     __syncthreads();
   }
   if (!ok) {
     if (tid == 0) atomicAdd(&g_wait_timeouts, 1u);
-    tc::mbar_wait(mbar, phase ^ 1u);  // once more for the products in flight
+    // once more for the copies and products in flight
+    tc::mbar_wait(wbar, 0);
+    for (int b = 0; b < 2; ++b)
+      if (gout >> b & 1u) tc::mbar_wait(gbar + b, gpar >> b & 1u);
+    tc::mbar_wait(mbar, phase ^ 1u);
   }
   tc::fence_before();
   __syncthreads();
