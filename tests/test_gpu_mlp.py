@@ -228,6 +228,23 @@ def test_correct_several_batches(gcmg, dtype):
     assert gcmg.wait_timeouts() == 0
 
 
+def test_correct_fp64_equals_fp32_on_the_rounded_residual(gcmg):
+    """the network runs in fp32/bf16 either way: with x = 0 the fp64 result is
+    the fp32 result widened, bit for bit, when r is rounded to fp32 first
+    (this pins the fp64 <-> fp32 conversions of the kernel)"""
+    case = Q4Case(gcmg, synth.cube_octant(3, 1))
+    net = _net(gcmg, synth.mlp_init(250, 128, 125, 48))
+    r64 = case.gvec(49) * torch.logspace(-30, 15, case.gm.n_free(case.L), dtype=torch.float64, device="cuda")
+    r64[::97] = 0.0
+    x64 = torch.zeros_like(r64)
+    case.gm.mlp_correct(case.L, net, r64, x64)
+    r32 = r64.float()
+    x32 = torch.zeros_like(r32)
+    case.gm.mlp_correct(case.L, net, r32, x32)
+    assert torch.equal(x64, x32.double())
+    assert gcmg.wait_timeouts() == 0
+
+
 def test_correct_follows_parameter_changes(gcmg, q4):
     """the weight image and the first layer's diagonal part are rebuilt when
     the parameters change (set_params, Adam steps), and only then"""
