@@ -508,6 +508,31 @@ int gcmg_batch_handle(gcmg_batch* b, int i, gcmg_handle** h);
  */
 int gcmg_batch_cg_solve(gcmg_batch* b, const double* const* rhs, double* const* x, double rtol, int maxit,
                         gcmg_solve_stats* stats);
+/*
+ * The same solve with the whole batch in one persistent kernel: every
+ * problem's launch sequence (CG prologue, one CG iteration with its V-cycle,
+ * epilogue) is recorded once as a device work list, and one cooperative
+ * launch, captured in a CUDA graph, runs all of it: in each step every
+ * unfinished problem performs its next operation, the operations' thread
+ * blocks spread over all CTAs, then a grid barrier (bounded waits; a wait
+ * that gives up fails the call with GCMG_ERR_INTERNAL).  The operators run
+ * the line-parallel kernels on every level (the work list's CTAs have 256
+ * threads), and the CG reductions sum the same chunks with 256 threads, so
+ * results agree with gcmg_batch_cg_solve to rounding.  At most 1024
+ * problems; the list is rebuilt when the pointers, rtol or maxit change.
+ * Synchronises the batch's stream.
+ */
+int gcmg_batch_cg_solve_persistent(gcmg_batch* b, const double* const* rhs, double* const* x, double rtol, int maxit,
+                                   gcmg_solve_stats* stats);
+typedef struct gcmg_persistent_info {
+  int grid;        /* CTAs of the persistent kernel (all resident) */
+  int smem_bytes;  /* its dynamic shared memory */
+  long long ops;   /* operations in the work list (all problems, one copy of each CG iteration) */
+  int steps;       /* lockstep steps of the last solve */
+  int in_graph;    /* 1: the launch is a captured CUDA graph */
+} gcmg_persistent_info;
+/* the work list of the last persistent solve (GCMG_ERR_ARG before the first) */
+int gcmg_batch_persistent_info(const gcmg_batch* b, gcmg_persistent_info* info);
 
 /*
  * Host utility: out[i] = a uniform value in [-1, 1) attached to the point

@@ -57,6 +57,11 @@ class SolveStats(ctypes.Structure):
     _fields_ = [("iterations", _c_int), ("r0", _c_double), ("rel_residual", _c_double), ("status", _c_int)]
 
 
+class PersistentInfo(ctypes.Structure):
+    _fields_ = [("grid", _c_int), ("smem_bytes", _c_int), ("ops", ctypes.c_longlong), ("steps", _c_int),
+                ("in_graph", _c_int)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("degree", _c_int), ("tile_cells", _c_int), ("cell_kernel", _c_int), ("cell_threads", _c_int),
                 ("gdofs", _c_double)]
@@ -131,6 +136,9 @@ _SIGS = {
     "gcmg_batch_handle": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(_c_void_p)]),
     "gcmg_batch_cg_solve": (_c_int, [_c_void_p, ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p), _c_double,
                                      _c_int, ctypes.POINTER(SolveStats)]),
+    "gcmg_batch_cg_solve_persistent": (_c_int, [_c_void_p, ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p),
+                                                _c_double, _c_int, ctypes.POINTER(SolveStats)]),
+    "gcmg_batch_persistent_info": (_c_int, [_c_void_p, ctypes.POINTER(PersistentInfo)]),
 }
 
 _lib = None
@@ -651,8 +659,9 @@ class Batch:
     def __len__(self) -> int:
         return len(self.problems)
 
-    def cg_solve(self, bs, xs, rtol: float = 1e-8, maxit: int = 100):
-        """CG to rtol for every problem in one graph launch; returns the per-problem stats."""
+    def cg_solve(self, bs, xs, rtol: float = 1e-8, maxit: int = 100, persistent: bool = False):
+        """CG to rtol for every problem in one graph launch (persistent: the
+        whole batch in one persistent kernel); returns the per-problem stats."""
         import torch
         n = len(self.problems)
         assert len(bs) == n and len(xs) == n
@@ -663,5 +672,12 @@ class Batch:
         barr = (_c_void_p * n)(*[b.data_ptr() if b.numel() else None for b in bs])
         xarr = (_c_void_p * n)(*[x.data_ptr() if x.numel() else None for x in xs])
         st = (SolveStats * n)()
-        _check(lib().gcmg_batch_cg_solve(self._p, barr, xarr, rtol, maxit, st))
+        fn = lib().gcmg_batch_cg_solve_persistent if persistent else lib().gcmg_batch_cg_solve
+        _check(fn(self._p, barr, xarr, rtol, maxit, st))
         return [st[i] for i in range(n)]
+
+    def persistent_info(self) -> PersistentInfo:
+        """grid, shared memory, operations and steps of the last persistent solve"""
+        out = PersistentInfo()
+        _check(lib().gcmg_batch_persistent_info(self._p, ctypes.byref(out)))
+        return out

@@ -16,7 +16,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgcmg.so")
 
 SOURCES = ["basis.cpp", "mesh.cpp", "level.cpp", "kernels_cell.cu", "kernels_lanes.cu", "kernels_transfer.cu",
-           "kernels_vec.cu", "kernels_peak.cu", "kernels_mlp.cu", "mlp_net.cu", "batch.cu", "api.cu"]
+           "kernels_vec.cu", "kernels_peak.cu", "kernels_mlp.cu", "mlp_net.cu", "kernels_dwl.cu", "batch.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", f"-I{INCLUDE}", f"-I{CSRC}"]
 

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "dwl.h"
 #include "handle.h"
 #include "splitmix.h"
 
@@ -537,6 +538,7 @@ void upload_all_tables() {
   upload_tables_lanes();
   upload_tables_transfer();
   upload_tables_mlp();
+  upload_tables_dwl();
   ck(cudaDeviceSynchronize(), "upload tables");
   done[dev] = 1;
 }

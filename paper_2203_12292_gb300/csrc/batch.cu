@@ -14,14 +14,36 @@
 #include <atomic>
 #include <cmath>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
+#include "dwl.h"
 #include "handle.h"
+
+// the device work list of a batch: every problem's recorded prologue, CG
+// iteration and epilogue, run by one persistent cooperative kernel
+struct DwlState {
+  gcmg::DevBuf ops, probs, go, ctl;  // ctl: barrier (2 unsigned) and status (2 int)
+  int np = 0, grid = 0;
+  size_t smem = 0;
+  long long max_steps = 0, n_ops = 0;
+  cudaGraphExec_t exec = nullptr;  // the launch captured in a graph (null: launched directly)
+  int steps = 0;
+  std::vector<const double*> key_b;
+  std::vector<double*> key_x;
+  double key_rtol = -1.0;
+  int key_maxit = -1;
+  ~DwlState() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
 
 struct gcmg_batch {
   std::vector<std::unique_ptr<gcmg_handle>> probs;
+  std::unique_ptr<DwlState> dwl;
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -41,6 +63,38 @@ struct gcmg_batch {
 namespace gcmg {
 
 long long launch_counter();
+
+DwlRecorder*& dwl_recorder() {
+  thread_local DwlRecorder* r = nullptr;
+  return r;
+}
+
+namespace {
+std::mutex g_dwl_mu;
+std::unordered_map<const void*, std::pair<int, size_t>> g_dwl_reg;
+}  // namespace
+
+void dwl_register(const void* kernel, int id, size_t arg_bytes) {
+  std::lock_guard<std::mutex> lock(g_dwl_mu);
+  g_dwl_reg[kernel] = {id, arg_bytes};
+}
+
+int dwl_lookup(const void* kernel, size_t* bytes) {
+  std::lock_guard<std::mutex> lock(g_dwl_mu);
+  const auto it = g_dwl_reg.find(kernel);
+  if (it == g_dwl_reg.end()) return -1;
+  *bytes = it->second.second;
+  return it->second.first;
+}
+
+void dwl_register_all() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    dwl_register_cell();
+    dwl_register_transfer();
+    dwl_register_vec();
+  });
+}
 
 namespace {
 
@@ -191,6 +245,116 @@ void build_graph(gcmg_batch& B, const double* const* b, double* const* x, double
   const cudaError_t e = cudaGraphInstantiate(&B.exec, G, 0);
   cudaGraphDestroy(G);
   ck(e, "graph instantiate");
+}
+
+// ---------------------------------------------------------------------------
+// device work list
+// ---------------------------------------------------------------------------
+
+// the launches of f recorded (not run) as device-work-list operations
+template <typename F>
+std::vector<DwlOp> record_ops(Handle& H, F&& f) {
+  DwlRecorder rec;
+  const bool prof = H.prof.on;
+  H.prof.on = false;
+  const long long before = launch_counter();
+  g_launch_err = cudaSuccess;
+  dwl_recorder() = &rec;
+  try {
+    f();
+  } catch (...) {
+    dwl_recorder() = nullptr;
+    H.prof.on = prof;
+    note_launches((int)-(launch_counter() - before));
+    throw;
+  }
+  dwl_recorder() = nullptr;
+  H.prof.on = prof;
+  note_launches((int)-(launch_counter() - before));  // recorded, not run
+  if (g_launch_err != cudaSuccess) {
+    g_launch_err = cudaSuccess;
+    throw Error(GCMG_ERR_ARG, "the persistent batch runs the line-parallel operators and the kernels of the "
+                              "plain V-cycle and CG only (a launch of this problem has no device-work-list form)");
+  }
+  return std::move(rec.ops);
+}
+
+void build_dwl(gcmg_batch& B, const double* const* b, double* const* x, double rtol, int maxit) {
+  const int np = (int)B.probs.size();
+  if (np > DWL_MAX_PROBS) throw Error(GCMG_ERR_ARG, "the persistent batch takes at most 1024 problems");
+  dwl_register_all();
+  const double rtol2 = rtol * rtol;
+  std::vector<DwlOp> all;
+  std::vector<DwlProb> pr(np);
+  long long longest = 0;
+  auto append = [&](std::vector<DwlOp>&& v, int prob) {
+    for (auto& op : v) {
+      if (op.type == DWL_OP_CHECK) op.prob = prob;
+      all.push_back(op);
+    }
+  };
+  for (int i = 0; i < np; ++i) {
+    Handle& H = B.probs[i]->h;
+    const CgVecs v = vecs(H);
+    DwlProb q{};
+    q.pro = (int32_t)all.size();
+    if (v.n == 0) {
+      append(record_ops(H, [&] {
+               launch_scalar_set(v.S, 7, 0.0, H.stream);
+               launch_scalar_set(v.S, 8, 0.0, H.stream);
+               launch_cg_stats(v.S, rtol2, B.stats.as<double>() + 4 * i, H.stream);
+             }),
+             i);
+      q.body = q.epi = q.end = (int32_t)all.size();
+    } else {
+      append(record_ops(H, [&] { cg_prologue(H, b[i], rtol2, maxit, 0); }), i);
+      q.body = (int32_t)all.size();
+      append(record_ops(H, [&] { cg_body(H, rtol2, maxit, 0); }), i);
+      q.epi = (int32_t)all.size();
+      append(record_ops(H, [&] {
+               launch_copy(v.x, x[i], v.n, H.stream);
+               launch_cg_stats(v.S, rtol2, B.stats.as<double>() + 4 * i, H.stream);
+             }),
+             i);
+      q.end = (int32_t)all.size();
+      if (q.body == q.pro || all[q.body - 1].type != DWL_OP_CHECK || q.epi == q.body ||
+          all[q.epi - 1].type != DWL_OP_CHECK)
+        throw Error(GCMG_ERR_INTERNAL, "recorded CG without its loop test");
+    }
+    pr[i] = q;
+    longest = std::max(longest, (long long)(q.body - q.pro) + (long long)maxit * (q.epi - q.body) + (q.end - q.epi));
+  }
+  auto D = std::make_unique<DwlState>();
+  D->np = np;
+  D->n_ops = (long long)all.size();
+  D->max_steps = longest + 8;
+  for (const auto& op : all) D->smem = std::max(D->smem, (size_t)op.smem);
+  D->grid = dwl_grid(D->smem, B.probs.empty() ? 152 : B.probs[0]->h.n_sm);
+  if (D->grid < 1) throw Error(GCMG_ERR_CUDA, "the persistent batch kernel does not fit on this device");
+  D->ops.upload(all, B.stream);
+  D->probs.upload(pr, B.stream);
+  D->go.alloc((size_t)std::max(np, 1) * sizeof(int));
+  D->ctl.alloc(4 * sizeof(unsigned));
+  ck(cudaStreamSynchronize(B.stream), "upload");
+  // one launch of the persistent kernel, captured in a graph with the reset of its barrier
+  DwlParams P{D->ops.as<DwlOp>(), D->probs.as<DwlProb>(), np, D->go.as<int>(), D->ctl.as<unsigned>(),
+              D->ctl.as<int>() + 2, D->max_steps};
+  cudaGraph_t G = nullptr;
+  ck(cudaStreamBeginCapture(B.cap, cudaStreamCaptureModeRelaxed), "capture");
+  cudaError_t e = cudaMemsetAsync(D->ctl.p, 0, 4 * sizeof(unsigned), B.cap);
+  if (e == cudaSuccess) e = launch_dwl(P, D->grid, D->smem, B.cap);
+  const cudaError_t e2 = cudaStreamEndCapture(B.cap, &G);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&D->exec, G, 0);
+  if (G) cudaGraphDestroy(G);
+  g_launch_err = cudaSuccess;
+  note_launches(-1);  // captured, not run
+  ck(e, "persistent batch graph");
+  D->key_b.assign(b, b + np);
+  D->key_x.assign(x, x + np);
+  D->key_rtol = rtol;
+  D->key_maxit = maxit;
+  B.dwl = std::move(D);
 }
 
 // fp32 (or fp64) operator of the finest level: GDoF/s over `reps` applications
@@ -375,6 +539,49 @@ int gcmg_batch_cg_solve(gcmg_batch* b, const double* const* rhs, double* const* 
       }
     }
     note_launches((int)std::min<long long>(kernels, 1LL << 30));
+  });
+}
+
+int gcmg_batch_cg_solve_persistent(gcmg_batch* b, const double* const* rhs, double* const* x, double rtol, int maxit,
+                                   gcmg_solve_stats* stats) {
+  return guarded([&] {
+    if (!b || !rhs || !x || !(rtol > 0) || maxit < 1) throw Error(GCMG_ERR_ARG, "bad arguments");
+    const int np = (int)b->probs.size();
+    for (int i = 0; i < np; ++i) {
+      if (b->probs[i]->h.lev.back()->n() && (!rhs[i] || !x[i])) throw Error(GCMG_ERR_ARG, "bad vectors");
+      b->probs[i]->h.stream = b->stream;
+    }
+    DwlState* D = b->dwl.get();
+    const bool same = D && D->key_rtol == rtol && D->key_maxit == maxit &&
+                      std::equal(D->key_b.begin(), D->key_b.end(), rhs) && std::equal(D->key_x.begin(), D->key_x.end(), x);
+    if (!same) {
+      build_dwl(*b, rhs, x, rtol, maxit);
+      D = b->dwl.get();
+    }
+    ck(cudaGraphLaunch(D->exec, b->stream), "graph launch");
+    note_launches(1);
+    std::vector<double> h((size_t)np * 4);
+    int st[2] = {0, 0};
+    ck(cudaMemcpyAsync(h.data(), b->stats.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "stats");
+    ck(cudaMemcpyAsync(st, D->ctl.as<int>() + 2, sizeof(st), cudaMemcpyDeviceToHost, b->stream), "status");
+    ck(cudaStreamSynchronize(b->stream), "batch solve");
+    if (st[0] == 1) throw Error(GCMG_ERR_INTERNAL, "persistent batch: a grid-barrier wait gave up");
+    if (st[0] == 2) throw Error(GCMG_ERR_INTERNAL, "persistent batch: the schedule exceeded its bound");
+    D->steps = st[1];
+    for (int i = 0; i < np && stats; ++i) {
+      const double nb2 = h[4 * i + 2];
+      stats[i] = gcmg_solve_stats{(int)h[4 * i], std::sqrt(nb2), nb2 > 0 ? std::sqrt(h[4 * i + 1] / nb2) : 0.0,
+                                  (int)h[4 * i + 3]};
+    }
+  });
+}
+
+int gcmg_batch_persistent_info(const gcmg_batch* b, gcmg_persistent_info* info) {
+  return guarded([&] {
+    if (!b || !info) throw Error(GCMG_ERR_ARG, "null argument");
+    const DwlState* D = b->dwl.get();
+    if (!D) throw Error(GCMG_ERR_ARG, "no persistent solve yet");
+    *info = gcmg_persistent_info{D->grid, (int)D->smem, D->n_ops, D->steps, D->exec ? 1 : 0};
   });
 }
 

@@ -12,6 +12,7 @@
 #include <stdexcept>
 #include <unordered_map>
 
+#include "dwl.h"
 #include "host.h"
 #include "internal.h"
 
@@ -98,10 +99,21 @@ inline cudaError_t smem_allow(KERN kernel, size_t bytes) {
 }
 
 // launch with programmatic stream serialisation (see pdl_begin); a rejected
-// launch is returned and recorded for the calling entry point
+// launch is returned and recorded for the calling entry point.  While a
+// device-work-list recorder is installed on this thread, the launch is
+// recorded instead (cudaErrorNotSupported for a kernel the persistent kernel
+// does not run).
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args... args) {
+  if (dwl_recording()) {
+    const bool ok = grid.y == 1 && grid.z == 1 && block.y == 1 && block.z == 1 &&
+                    dwl_record<KArgs...>(reinterpret_cast<const void*>(kernel), grid.x, block.x, smem,
+                                         static_cast<KArgs>(args)...);
+    const cudaError_t e = ok ? cudaSuccess : cudaErrorNotSupported;
+    note_launch_error(e);
+    return e;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;

@@ -35,7 +35,9 @@
 
 namespace gcmg {
 
+#ifndef GCMG_BODIES_ONLY
 GCMG_DEFINE_UPLOAD(upload_tables_cell)
+#endif
 
 namespace {
 
@@ -1437,6 +1439,7 @@ __global__ void __launch_bounds__(BLOCK) diag_table_kernel(double* out, int tc) 
   }
 }
 
+#ifndef GCMG_BODIES_ONLY  // host code: launchers (the device work list compiles the kernels only)
 template <typename KERN>
 void ensure_smem(KERN kernel, size_t bytes) {
   smem_allow(kernel, bytes);
@@ -1497,7 +1500,8 @@ void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
   }
   const size_t sm = smem_layout<T>((K + 1) * (K + 1) * (K + 1), L.tc, L.max_local).total;
   if constexpr (MODE == MODE_VMULT && sizeof(T) == 8) {
-    if (L.use_lanes && lanes_ok(L)) {  // one lane per cell, double-float arithmetic (default)
+    // (a recorded launch list takes the BLOCK-thread line kernels: the persistent kernel has BLOCK threads)
+    if (L.use_lanes && lanes_ok(L) && !dwl_recording()) {  // one lane per cell, double-float arithmetic (default)
       launch_vmult_lanes_df(L, A.src, A.dst, A.add, 0, L.n_tiles, s);
       run_halo<T>(L, A.dst, s);
       return;
@@ -1512,12 +1516,12 @@ void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
     }
   }
   if constexpr (MODE == MODE_VMULT && sizeof(T) == 4) {
-    if (L.use_lanes && lanes_ok(L)) {  // one lane per cell (default)
+    if (L.use_lanes && lanes_ok(L) && !dwl_recording()) {  // one lane per cell (default)
       launch_vmult_lanes(L, A.src, A.dst, A.add, 0, L.n_tiles, s);
       run_halo<T>(L, A.dst, s);
       return;
     }
-    if (L.tc <= CHUNK && L.threads == BLOCK) {
+    if (L.tc <= CHUNK && (L.threads == BLOCK || dwl_recording())) {
       // vmult_lines keeps one tile-DoF buffer (input, then accumulator) plus K-1 <= 4 zero slots
       const size_t sm1 = sm - (size_t)L.max_local * sizeof(T) + 16;
       launch_lines_f32<K>(L, L.n_tiles, sm1, s, A);
@@ -1527,7 +1531,7 @@ void run_cells(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
     }
   }
   // the thread count is a tuning parameter of the fp32 operator only
-  const int nt = (MODE == MODE_VMULT && sizeof(T) == 4) ? L.threads : BLOCK;
+  const int nt = (MODE == MODE_VMULT && sizeof(T) == 4 && !dwl_recording()) ? L.threads : BLOCK;
   if (nt == 128)
     launch_cells_nt<K, T, MODE, 128>(L, A, sm, s);
   else if (nt == 384)
@@ -1582,8 +1586,10 @@ void dispatch(const CellLaunch& L, CellArgs<T> A, cudaStream_t s) {
   }
 }
 
+#endif  // GCMG_BODIES_ONLY
 }  // namespace
 
+#ifndef GCMG_BODIES_ONLY
 size_t cell_smem_bytes(int k, bool fp64, int tc, int max_local, bool mapped) {
   const int n3 = (k + 1) * (k + 1) * (k + 1);
   return fp64 ? smem_layout<double>(n3, tc, max_local, mapped, mapped).total
@@ -1603,7 +1609,7 @@ void launch_vmult(const CellLaunch& L, bool fp64, const void* src, void* dst, in
     A.src = static_cast<const float*>(src);
     A.dst = static_cast<float*>(dst);
     A.add = add;
-    if (L.tc > 64 || L.use_lines || L.geom) {
+    if (L.tc > 64 || L.use_lines || L.geom || dwl_recording()) {
       dispatch<float, MODE_VMULT>(L, A, s);
       return;
     }
@@ -1805,4 +1811,12 @@ void launch_quadrature_points(const CellLaunch& L, int64_t n_cells, double* xyz,
   note_launches(1);
 }
 
+void dwl_register_cell() {
+  int id = DWL_BASE_CELL;
+#define GCMG_DWL_REG(fn) dwl_register(reinterpret_cast<const void*>(fn), id++, dwl_args_size(fn));
+  GCMG_DWL_CELL(GCMG_DWL_REG)
+#undef GCMG_DWL_REG
+}
+
+#endif  // GCMG_BODIES_ONLY
 }  // namespace gcmg

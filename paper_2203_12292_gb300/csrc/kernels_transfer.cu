@@ -20,7 +20,9 @@
 
 namespace gcmg {
 
+#ifndef GCMG_BODIES_ONLY
 GCMG_DEFINE_UPLOAD(upload_tables_transfer)
+#endif
 
 namespace {
 
@@ -112,7 +114,12 @@ __global__ void __launch_bounds__(BLOCK) prolong_h(TArgs<T> A) {
   __shared__ int32_t sm_fine[TP];
   __shared__ int32_t sm_gsc[TP * NSLOT];       // coarse cells' global slot starts
   __shared__ uint32_t sm_own[TP * 8];          // ownership masks of the fine cells
+#ifdef GCMG_DWL_POOL  // the persistent kernel: one pool for every kernel's largest array
+  int32_t* sm_gs = reinterpret_cast<int32_t*>(GCMG_DWL_POOL);
+  static_assert(TP * 8 * NSLOT * 4 <= GCMG_DWL_POOL_BYTES, "pool");
+#else
   __shared__ int32_t sm_gs[TP * 8 * NSLOT];    // their global slot starts (-1: none)
+#endif
   __shared__ uint16_t s_so[N3];                // per local node: entity slot | offset << 5
   __shared__ uint16_t s_e3[8 * N3];            // child q, node n -> position in the 2k+1 lattice
   extern __shared__ __align__(16) unsigned char smem[];
@@ -257,7 +264,12 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
   __shared__ uint16_t sm_mask[TPC];
   __shared__ uint16_t sm_cell[TPC];
   __shared__ uint32_t sm_own[TPC * 8];          // ownership masks of the fine cells
+#ifdef GCMG_DWL_POOL
+  int32_t* sm_gs = reinterpret_cast<int32_t*>(GCMG_DWL_POOL);
+  static_assert(TPC * 8 * NSLOT * 4 <= GCMG_DWL_POOL_BYTES, "pool");
+#else
   __shared__ int32_t sm_gs[TPC * 8 * NSLOT];    // their global slot starts (-1: none)
+#endif
   __shared__ uint16_t s_so[N3];                // per local node: entity slot | offset << 5
   __shared__ uint16_t s_e3[8 * N3];            // child q, node n -> position in the 2k+1 lattice
   extern __shared__ __align__(16) unsigned char smem[];
@@ -477,6 +489,7 @@ TArgs<T> targs(const TransferLaunch& L) {
   return A;
 }
 
+#ifndef GCMG_BODIES_ONLY  // host code: launchers (the device work list compiles the kernels only)
 template <typename K_>
 void set_smem(K_ kernel, size_t bytes) {
   smem_allow(kernel, bytes);
@@ -578,8 +591,10 @@ void restrict_any(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s)
   }
 }
 
+#endif  // GCMG_BODIES_ONLY
 }  // namespace
 
+#ifndef GCMG_BODIES_ONLY
 void launch_prolongate_add(const TransferLaunch& L, bool fp64, const void* coarse, void* fine, cudaStream_t s) {
   if (fp64)
     prolong_any<double>(L, static_cast<const double*>(coarse), static_cast<double*>(fine), s);
@@ -594,4 +609,12 @@ void launch_restrict_add(const TransferLaunch& L, bool fp64, const void* fine, v
     restrict_any<float>(L, static_cast<const float*>(fine), static_cast<float*>(coarse), s);
 }
 
+void dwl_register_transfer() {
+  int id = DWL_BASE_TRANSFER;
+#define GCMG_DWL_REG(fn) dwl_register(reinterpret_cast<const void*>(fn), id++, dwl_args_size(fn));
+  GCMG_DWL_TRANSFER(GCMG_DWL_REG)
+#undef GCMG_DWL_REG
+}
+
+#endif  // GCMG_BODIES_ONLY
 }  // namespace gcmg

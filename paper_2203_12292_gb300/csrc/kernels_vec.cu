@@ -349,7 +349,49 @@ __global__ void copy_kernel(const double* src, double* dst, int64_t n) {
     dst[i] = src[i];
 }
 
+// the two CG reductions with BLOCK threads, for the persistent kernel of the
+// device work list (its CTAs have BLOCK threads): the same fixed chunks of the
+// same DOT_BLOCKS partial sums, each summed in a fixed order
+template <typename TY>
+__global__ void __launch_bounds__(BLOCK) dot_partial_b(const double* x, const TY* y, int64_t n, double* part) {
+  pdl_begin();
+  __shared__ double sh[BLOCK];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  double s[RU] = {};
+  int64_t i = i0 + threadIdx.x;
+  for (; i + (RU - 1) * BLOCK < i1; i += RU * BLOCK) {
+#pragma unroll
+    for (int u = 0; u < RU; ++u) s[u] += x[i + u * BLOCK] * (double)y[i + u * BLOCK];
+  }
+  for (; i < i1; i += BLOCK) s[0] += x[i] * (double)y[i];
+  const double v = block_sum((s[0] + s[1]) + (s[2] + s[3]), sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+template <bool CAST>
+__global__ void __launch_bounds__(BLOCK) cg_xr_b(double* x, double* r, const double* p, const double* q,
+                                                 const double* scal, int64_t n, double* part, float* r32) {
+  pdl_begin();
+  __shared__ double sh[BLOCK];
+  const double alpha = scal[3];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+  double s = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += BLOCK) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    if (CAST) r32[i] = (float)ri;
+    s += ri * ri;
+  }
+  const double v = block_sum(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
 }  // namespace
+
+#ifndef GCMG_BODIES_ONLY
 
 void launch_fill(double* x, double v, int64_t n, cudaStream_t s) {
   if (n > 0) { launch_pdl(fill_kernel, grid_for(n), BLOCK, 0, s, x, v, n); note_launches(1); }
@@ -490,22 +532,37 @@ void launch_coarse_solve(bool fp64, const double* Ainv, int n, const void* b, vo
 
 void launch_dot(const double* x, const double* y, int64_t n, double* scratch, double* scal, int slot, int op,
                 cudaStream_t s) {
-  { launch_pdl(dot_partial<double>, DOT_BLOCKS, RB, 0, s, x, y, n, scratch); note_launches(1); }
+  if (dwl_recording())
+    launch_pdl(dot_partial_b<double>, DOT_BLOCKS, BLOCK, 0, s, x, y, n, scratch);
+  else
+    launch_pdl(dot_partial<double>, DOT_BLOCKS, RB, 0, s, x, y, n, scratch);
+  note_launches(1);
   { launch_pdl(dot_final, 1, BLOCK, 0, s, scratch, DOT_BLOCKS, scal, slot, op); note_launches(1); }
 }
 
 void launch_dot(const double* x, const float* y, int64_t n, double* scratch, double* scal, int slot, int op,
                 cudaStream_t s) {
-  { launch_pdl(dot_partial<float>, DOT_BLOCKS, RB, 0, s, x, y, n, scratch); note_launches(1); }
+  if (dwl_recording())
+    launch_pdl(dot_partial_b<float>, DOT_BLOCKS, BLOCK, 0, s, x, y, n, scratch);
+  else
+    launch_pdl(dot_partial<float>, DOT_BLOCKS, RB, 0, s, x, y, n, scratch);
+  note_launches(1);
   { launch_pdl(dot_final, 1, BLOCK, 0, s, scratch, DOT_BLOCKS, scal, slot, op); note_launches(1); }
 }
 
 void launch_cg_update_xr(double* x, double* r, const double* p, const double* q, const double* scal, int64_t n,
                          double* scratch, double* scal_out, cudaStream_t s, float* r32) {
-  if (r32)
-    { launch_pdl(cg_xr_kernel<true>, DOT_BLOCKS, XB, 0, s, x, r, p, q, scal, n, scratch, r32); note_launches(1); }
-  else
-    { launch_pdl(cg_xr_kernel<false>, DOT_BLOCKS, XB, 0, s, x, r, p, q, scal, n, scratch, r32); note_launches(1); }
+  if (dwl_recording()) {
+    if (r32)
+      launch_pdl(cg_xr_b<true>, DOT_BLOCKS, BLOCK, 0, s, x, r, p, q, scal, n, scratch, r32);
+    else
+      launch_pdl(cg_xr_b<false>, DOT_BLOCKS, BLOCK, 0, s, x, r, p, q, scal, n, scratch, r32);
+  } else if (r32) {
+    launch_pdl(cg_xr_kernel<true>, DOT_BLOCKS, XB, 0, s, x, r, p, q, scal, n, scratch, r32);
+  } else {
+    launch_pdl(cg_xr_kernel<false>, DOT_BLOCKS, XB, 0, s, x, r, p, q, scal, n, scratch, r32);
+  }
+  note_launches(1);
   { launch_pdl(dot_final, 1, BLOCK, 0, s, scratch, DOT_BLOCKS, scal_out, 2, DOT_STORE); note_launches(1); }
 }
 
@@ -611,4 +668,14 @@ void launch_copy(const double* src, double* dst, int64_t n, cudaStream_t s) {
   note_launches(1);
 }
 
+void dwl_register_vec() {
+  int id = DWL_BASE_VEC;
+#define GCMG_DWL_REG(fn) dwl_register(reinterpret_cast<const void*>(fn), id++, dwl_args_size(fn));
+  GCMG_DWL_VEC(GCMG_DWL_REG)
+  GCMG_DWL_VEC_SERIAL(GCMG_DWL_REG)
+#undef GCMG_DWL_REG
+  dwl_register(reinterpret_cast<const void*>(cg_check_kernel), DWL_OP_CHECK, dwl_args_size(cg_check_kernel));
+}
+
+#endif  // GCMG_BODIES_ONLY
 }  // namespace gcmg

@@ -1,10 +1,15 @@
-"""Batched solve (one graph launch for many independent problems) and the
-operator autotuner, through the C ABI.
+"""Batched solve (one graph launch for many independent problems; or the
+whole batch in one persistent kernel) and the operator autotuner, through
+the C ABI.
 
 The batched CG runs the same kernels in the same order as the single-problem
 solve, so every problem's iterate must equal its own single solve bit for
 bit; a few problems are also checked against the oracle (relative residual
 of the returned x with the oracle's operator and right-hand side <= 1e-8).
+The persistent kernel runs the line-parallel operators on every level and
+sums the CG reductions with 256 threads, so its iterates agree with the
+graph's to rounding: the same convergence (iterations within one, relative
+residual <= 1e-8, also by the oracle), and bit-identical repeats.
 """
 import numpy as np
 import pytest
@@ -82,6 +87,54 @@ def test_batch_maxit(batch):
     bs = [_rhs(m, 300 + i) for i, m in enumerate(batch.problems)]
     xs = [torch.zeros_like(b) for b in bs]
     stats = batch.cg_solve(bs, xs, 1e-14, maxit=2)
+    for s in stats:
+        assert s.iterations == 2 and s.status == 4  # GCMG_ERR_NOT_CONVERGED
+
+
+def test_persistent_batch(gcmg, batch):
+    bs = [_rhs(m, 100 + i) for i, m in enumerate(batch.problems)]
+    xg = [torch.zeros_like(b) for b in bs]
+    sg = batch.cg_solve(bs, xg, 1e-8)
+    xp = [torch.zeros_like(b) for b in bs]
+    sp = batch.cg_solve(bs, xp, 1e-8, persistent=True)
+    for i in range(len(bs)):
+        assert sp[i].status == 0 and sp[i].rel_residual <= 1e-8, i
+        assert abs(sp[i].iterations - sg[i].iterations) <= 1, (i, sp[i].iterations, sg[i].iterations)
+        assert float((xp[i] - xg[i]).norm() / xg[i].norm()) < 1e-5, i
+    info = batch.persistent_info()
+    assert info.grid >= 1 and info.in_graph == 1 and info.ops > 0
+    assert info.steps >= max(s.iterations for s in sp)
+    # a second launch of the captured persistent kernel repeats the solve bit for bit
+    xp2 = [torch.zeros_like(b) for b in bs]
+    sp2 = batch.cg_solve(bs, xp2, 1e-8, persistent=True)
+    assert [s.iterations for s in sp2] == [s.iterations for s in sp]
+    assert all(torch.equal(a, c) for a, c in zip(xp, xp2))
+
+
+@pytest.mark.parametrize("i", [0, 3])
+def test_persistent_residual_by_oracle(batch, i):
+    k, d, e = PROBLEMS[i]
+    mg = batch.problems[i]
+    bs = [torch.zeros_like(_rhs(m, 1)) for m in batch.problems]
+    bs[i] = _rhs(mg, 200 + i)
+    xs = [torch.zeros_like(v) for v in bs]
+    stats = batch.cg_solve(bs, xs, 1e-8, persistent=True)
+    for j, s in enumerate(stats):
+        if j != i:
+            assert s.iterations == 0 and s.status == 0 and not torch.any(xs[j])
+    s = Space(omesh.build_mesh(synth.cube_octant(d, e)), k)
+    perm = match(mg.dof_coords(mg.finest), s.free_coordinates())
+    from oracle.space import fourier_function
+    bo = s.rhs(fourier_function(synth.fourier_rhs(200 + i)))
+    xo = np.empty(len(perm))
+    xo[perm] = xs[i].cpu().numpy()
+    assert np.linalg.norm(bo - s.apply(xo)) <= 1.01e-8 * np.linalg.norm(bo)
+
+
+def test_persistent_maxit(batch):
+    bs = [_rhs(m, 300 + i) for i, m in enumerate(batch.problems)]
+    xs = [torch.zeros_like(b) for b in bs]
+    stats = batch.cg_solve(bs, xs, 1e-14, maxit=2, persistent=True)
     for s in stats:
         assert s.iterations == 2 and s.status == 4  # GCMG_ERR_NOT_CONVERGED
 
