@@ -70,21 +70,33 @@ DwlRecorder*& dwl_recorder() {
 }
 
 namespace {
+struct DwlEntry {
+  int id;
+  size_t bytes;
+  int coarsen;
+};
 std::mutex g_dwl_mu;
-std::unordered_map<const void*, std::pair<int, size_t>> g_dwl_reg;
+std::unordered_map<const void*, DwlEntry> g_dwl_reg;
 }  // namespace
 
 void dwl_register(const void* kernel, int id, size_t arg_bytes) {
   std::lock_guard<std::mutex> lock(g_dwl_mu);
-  g_dwl_reg[kernel] = {id, arg_bytes};
+  g_dwl_reg[kernel] = DwlEntry{id, arg_bytes, 1};
 }
 
-int dwl_lookup(const void* kernel, size_t* bytes) {
+void dwl_set_coarsen(const void* kernel, int factor) {
+  std::lock_guard<std::mutex> lock(g_dwl_mu);
+  const auto it = g_dwl_reg.find(kernel);
+  if (it != g_dwl_reg.end() && factor >= 1) it->second.coarsen = factor;
+}
+
+int dwl_lookup(const void* kernel, size_t* bytes, int* coarsen) {
   std::lock_guard<std::mutex> lock(g_dwl_mu);
   const auto it = g_dwl_reg.find(kernel);
   if (it == g_dwl_reg.end()) return -1;
-  *bytes = it->second.second;
-  return it->second.first;
+  *bytes = it->second.bytes;
+  *coarsen = it->second.coarsen;
+  return it->second.id;
 }
 
 void dwl_register_all() {

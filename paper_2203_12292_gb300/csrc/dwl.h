@@ -92,8 +92,11 @@ inline bool dwl_recording() { return dwl_recorder() != nullptr; }
 
 // registry of the kernels the persistent kernel runs: id and packed size
 void dwl_register(const void* kernel, int id, size_t arg_bytes);
-// id of a registered kernel, -1 when absent; *bytes its packed size
-int dwl_lookup(const void* kernel, size_t* bytes);
+// a registered grid-stride kernel runs with `factor` times fewer virtual
+// blocks (its results do not depend on the grid)
+void dwl_set_coarsen(const void* kernel, int factor);
+// id of a registered kernel, -1 when absent; *bytes its packed size, *coarsen its factor
+int dwl_lookup(const void* kernel, size_t* bytes, int* coarsen);
 // fills the registry (once per process)
 void dwl_register_all();
 
@@ -106,11 +109,12 @@ void dwl_pack(unsigned char* buf, std::index_sequence<I...>, const KArgs&... a) 
 template <typename... KArgs>
 bool dwl_record(const void* kernel, unsigned grid, unsigned block, size_t smem, const KArgs&... a) {
   size_t bytes = 0;
-  const int id = dwl_lookup(kernel, &bytes);
+  int coarsen = 1;
+  const int id = dwl_lookup(kernel, &bytes, &coarsen);
   if (id < 0 || bytes != dwl_size<KArgs...>() || bytes > (size_t)DWL_ARG_BYTES || block > 256u) return false;
   DwlOp op{};
   op.type = id;
-  op.items = (int32_t)grid;
+  op.items = (int32_t)((grid + coarsen - 1) / coarsen);
   op.block = (int32_t)block;
   op.smem = (int32_t)smem;
   op.prob = -1;

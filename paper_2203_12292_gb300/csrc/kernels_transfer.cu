@@ -522,7 +522,8 @@ void restrict_h_launch(const TransferLaunch& L, const T* src, T* dst, cudaStream
 
 template <int K, typename T>
 void restrict_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
-  if (L.coarse.chunk == 4 || (L.coarse.chunk == 0 && L.coarse.n_tiles > 4 * L.coarse.n_sm))
+  // (a recorded launch list takes 4-cell chunks: less shared memory per CTA of the persistent kernel)
+  if (L.coarse.chunk == 4 || dwl_recording() || (L.coarse.chunk == 0 && L.coarse.n_tiles > 4 * L.coarse.n_sm))
     restrict_h_launch<K, T, 4>(L, src, dst, s);
   else
     restrict_h_launch<K, T, TP>(L, src, dst, s);

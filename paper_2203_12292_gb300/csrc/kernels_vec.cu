@@ -25,11 +25,28 @@ inline int grid_for(int64_t n) {
   return (int)std::max<int64_t>(g, 1);
 }
 
+// grid-stride loop over [0, n) that loads four elements' operands (i, i + S,
+// i + 2S, i + 3S) before it stores any of them: four memory round trips in
+// flight per thread instead of one.  Every element is read and written at its
+// own index only, so the results are those of the plain loop.
+template <typename LOAD, typename STORE>
+__device__ __forceinline__ void grid_stride4(int64_t n, LOAD load, STORE store) {
+  const int64_t S = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * S < n; i += 4 * S) {
+    const auto v0 = load(i), v1 = load(i + S), v2 = load(i + 2 * S), v3 = load(i + 3 * S);
+    store(i, v0);
+    store(i + S, v1);
+    store(i + 2 * S, v2);
+    store(i + 3 * S, v3);
+  }
+  for (; i < n; i += S) store(i, load(i));
+}
+
 template <typename A, typename B>
 __global__ void cast_kernel(const A* src, B* dst, int64_t n) {
   pdl_begin();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = (B)src[i];
+  grid_stride4(n, [&](int64_t i) { return src[i]; }, [&](int64_t i, A v) { dst[i] = (B)v; });
 }
 
 template <typename T>
@@ -110,8 +127,7 @@ __global__ void axpy_ratio_kernel(T* x, const T* c, const double* nd, int64_t n)
 template <typename T>
 __global__ void zero_kernel(T* x, int64_t n) {
   pdl_begin();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] = T(0);
+  grid_stride4(n, [&](int64_t) { return 0; }, [&](int64_t i, int) { x[i] = T(0); });
 }
 
 __global__ void invert_kernel(const double* d, double* i64, float* i32, int64_t n) {
@@ -126,29 +142,33 @@ __global__ void invert_kernel(const double* d, double* i64, float* i32, int64_t 
 template <typename T>
 __global__ void cheb_init_kernel(T* x, T* d, const T* b, const T* dinv, T c2, int64_t n) {
   pdl_begin();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const T v = c2 * dinv[i] * b[i];
-    d[i] = v;
-    x[i] = v;
-  }
+  grid_stride4(
+      n, [&](int64_t i) { return c2 * dinv[i] * b[i]; },
+      [&](int64_t i, T v) {
+        d[i] = v;
+        x[i] = v;
+      });
 }
 
 template <typename T, bool FIRST>
 __global__ void cheb_step_kernel(T* x, T* d, const T* b, const T* Ax, const T* dinv, T c1, T c2, int64_t n) {
   pdl_begin();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const T r = b[i] - Ax[i];
-    const T v = FIRST ? c2 * dinv[i] * r : c1 * d[i] + c2 * dinv[i] * r;
-    d[i] = v;
-    x[i] += v;
-  }
+  struct V {
+    T r, di, d, x;
+  };
+  grid_stride4(
+      n, [&](int64_t i) { return V{b[i] - Ax[i], dinv[i], FIRST ? T(0) : d[i], x[i]}; },
+      [&](int64_t i, V e) {
+        const T v = FIRST ? c2 * e.di * e.r : c1 * e.d + c2 * e.di * e.r;
+        d[i] = v;
+        x[i] = e.x + v;
+      });
 }
 
 template <typename T>
 __global__ void residual_kernel(T* r, const T* b, const T* Ax, int64_t n) {
   pdl_begin();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    r[i] = b[i] - Ax[i];
+  grid_stride4(n, [&](int64_t i) { return b[i] - Ax[i]; }, [&](int64_t i, T v) { r[i] = v; });
 }
 
 template <typename T>
@@ -291,8 +311,11 @@ template <typename TZ>
 __global__ void cg_p_kernel(double* p, const TZ* z, const double* scal, int64_t n) {
   pdl_begin();
   const double beta = scal[4];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = (double)z[i] + beta * p[i];
+  struct V {
+    double z, p;
+  };
+  grid_stride4(
+      n, [&](int64_t i) { return V{(double)z[i], p[i]}; }, [&](int64_t i, V e) { p[i] = e.z + beta * e.p; });
 }
 
 __global__ void fill_kernel(double* x, double v, int64_t n) {
@@ -345,8 +368,7 @@ __global__ void scalar_set_kernel(double* scal, int slot, double v) {
 
 __global__ void copy_kernel(const double* src, double* dst, int64_t n) {
   pdl_begin();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = src[i];
+  grid_stride4(n, [&](int64_t i) { return src[i]; }, [&](int64_t i, double v) { dst[i] = v; });
 }
 
 // the two CG reductions with BLOCK threads, for the persistent kernel of the
@@ -674,6 +696,14 @@ void dwl_register_vec() {
   GCMG_DWL_VEC(GCMG_DWL_REG)
   GCMG_DWL_VEC_SERIAL(GCMG_DWL_REG)
 #undef GCMG_DWL_REG
+  // grid-stride elementwise kernels: a quarter of the launch's blocks, four elements per thread each
+#define GCMG_DWL_COARSEN(fn) dwl_set_coarsen(reinterpret_cast<const void*>(fn), 4);
+  GCMG_DWL_COARSEN((cast_kernel<float, double>)) GCMG_DWL_COARSEN((cast_kernel<double, float>))
+  GCMG_DWL_COARSEN((copy_kernel)) GCMG_DWL_COARSEN((zero_kernel<float>)) GCMG_DWL_COARSEN((zero_kernel<double>))
+  GCMG_DWL_COARSEN((cheb_init_kernel<float>)) GCMG_DWL_COARSEN((cheb_step_kernel<float, true>))
+  GCMG_DWL_COARSEN((cheb_step_kernel<float, false>)) GCMG_DWL_COARSEN((residual_kernel<float>))
+  GCMG_DWL_COARSEN((cg_p_kernel<double>)) GCMG_DWL_COARSEN((cg_p_kernel<float>))
+#undef GCMG_DWL_COARSEN
   dwl_register(reinterpret_cast<const void*>(cg_check_kernel), DWL_OP_CHECK, dwl_args_size(cg_check_kernel));
 }
 
