@@ -604,7 +604,7 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
     build_level(meshes[spec[l].first], k, tc, lmax, L->host);
     L->fp32 = cfg.mg_fp32 != 0;
     L->cl.use_lines = cfg.cell_kernel != 2;
-    L->cl.use_lanes = cfg.cell_kernel == 0 || cfg.cell_kernel == 3;
+    L->cl.use_lanes = (cfg.cell_kernel == 0 && tc == 32) || cfg.cell_kernel == 3;
     L->cl.threads = cfg.cell_threads ? cfg.cell_threads : 256;
     LevelHost& lh = L->host;
     L->tiles.upload(lh.tiles, H.stream);
