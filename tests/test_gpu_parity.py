@@ -339,6 +339,29 @@ def test_vmult_fp32_slab_kernel(gcmg, rec, k, tc):
         assert c.cmp(l, y, ref) < 2e-6, l
 
 
+@pytest.mark.parametrize("rec,k", [(synth.octant(3), 4), (synth.cube_octant(2, 1), 4), (synth.sphere(4), 3),
+                                   (synth.octant(4), 2)], ids=["octant3-Q4", "cube2+1-Q4", "sphere4-Q3", "octant4-Q2"])
+def test_vmult_lane_kernel_on_every_tile_size(gcmg, rec, k):
+    """cell_kernel 3 runs the one-lane-per-cell kernels (fp32 and double-float)
+    on every level, also on the coarse levels' 8- and 16-cell tiles (the
+    default takes the line kernels there): Eq. 2 on every level against the
+    oracle, fp64 to 1e-12 and fp32 to 2e-6."""
+    c = Case(gcmg, rec, k, cell_kernel=3)
+    for l in range(c.mg.num_levels):
+        if c.mg.n_free(l) == 0:
+            continue
+        x = c.gvec(l, 800 + l)
+        y = torch.empty_like(x)
+        c.mg.vmult(l, x, y)
+        x32 = c.gvec(l, 900 + l, torch.float32)
+        y32 = torch.empty_like(x32)
+        c.mg.vmult(l, x32, y32)
+        torch.cuda.synchronize()
+        lev = c.levels[l]
+        assert c.cmp(l, y, lev.apply64(c.ovec(l, 800 + l))) < 1e-12, l
+        assert c.cmp(l, y32, lev.apply64(c.ovec(l, 900 + l).astype(np.float32).astype(np.float64))) < 2e-6, l
+
+
 @pytest.mark.parametrize("tc", [20, 24, 12])
 def test_tile_sizes_compute_the_same_operator(gcmg, tc):
     """Tiles of 20 cells put the fp64 kernel's dynamic shared memory just
