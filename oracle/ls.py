@@ -162,7 +162,13 @@ def set_precision(levels: List[LSLevel], dtype) -> None:
 
 
 def vcycle(levels: List[LSLevel], l: int, b: List[np.ndarray], x: List[np.ndarray]) -> None:
-    """Algorithm 2 with refinement edges on level l (b[l] has zero edge entries)."""
+    """The V-cycle with local smoothing (Sec. 2.2; Algorithm 2 with
+    refinement edges) on level l, in residual-correction form.  Smoothing acts
+    on A_SS of the level's own cells (b[l] has zero entries on the edge E).  The
+    defect of the smoothed iterate, (b_S - A_SS x_S, -A_ES x_S), is restricted
+    and added to the coarser level's right-hand side (which already holds that
+    level's share of b).  The coarse solution interpolated back supplies x_E,
+    and the second smoothing sees b_S - A_SE x_E.  Level 0 is solved exactly."""
     lev = levels[l]
     dt = b[l].dtype
     if l == 0:
@@ -170,13 +176,11 @@ def vcycle(levels: List[LSLevel], l: int, b: List[np.ndarray], x: List[np.ndarra
             x[0] = sla.cho_solve(lev.chol, b[0].astype(np.float64)).astype(dt)
         return
     dinv = lev.dinv.astype(dt)
-    xl = chebyshev(lev.apply, dinv, b[l], None, lev.lam_max)       # presmoothing on A_SS
-    r = b[l] - lev.apply(xl)                                        # (b_S - A_SS x_S, -A_ES x_S)
     P = lev.P.astype(dt) if dt == np.float32 else lev.P
-    b[l - 1] = b[l - 1] + P.T @ r                                   # restriction
-    vcycle(levels, l - 1, b, x)                                     # recursion
-    xl = xl + P @ x[l - 1]                                          # prolongation (sets x_E)
-    x[l] = chebyshev(lev.apply, dinv, b[l], xl, lev.lam_max)        # postsmoothing: b_S - A_SE x_E
+    xs = chebyshev(lev.apply, dinv, b[l], None, lev.lam_max)
+    b[l - 1] = b[l - 1] + P.T @ (b[l] - lev.apply(xs))
+    vcycle(levels, l - 1, b, x)
+    x[l] = chebyshev(lev.apply, dinv, b[l], xs + P @ x[l - 1], lev.lam_max)
 
 
 def multigrid_vcycle(levels: List[LSLevel], cmap: CopyMap, b: np.ndarray, dtype=np.float64) -> np.ndarray:

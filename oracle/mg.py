@@ -200,7 +200,11 @@ def _dense(lev: Level) -> np.ndarray:
 
 
 def vcycle(levels: List[Level], l: int, b: np.ndarray) -> np.ndarray:
-    """Algorithm 2 on level l."""
+    """The multigrid V-cycle on level l for A_l x = b, written as a
+    residual-correction method (the cycle of Sec. 2.1 / Algorithm 2): a
+    smoothed start from zero, the coarse-grid correction P e_c with e_c the
+    V-cycle's solution of R = P^T applied to the defect, and a second smoothing
+    from the corrected iterate; on level 0 the exact solve."""
     lev = levels[l]
     dt = b.dtype
     if l == 0:
@@ -208,18 +212,18 @@ def vcycle(levels: List[Level], l: int, b: np.ndarray) -> np.ndarray:
             return np.zeros_like(b)
         return sla.cho_solve(lev.chol, b.astype(np.float64)).astype(dt)
     dinv = (1.0 / lev.diag).astype(dt)
-    x = chebyshev(lev.apply, dinv, b, None, lev.lam_max)          # presmoothing
-    r = b - lev.apply(x)                                           # residual
+
+    def smooth(x0):
+        return chebyshev(lev.apply, dinv, b, x0, lev.lam_max)
+
     P = lev.P.astype(dt) if dt == np.float32 else lev.P
-    bc = P.T @ r                                                   # restriction
-    xc = vcycle(levels, l - 1, bc)                                 # recursion
-    x = x + P @ xc                                                 # prolongation
+    x = smooth(None)
+    defect = b - lev.apply(x)
+    x = x + P @ vcycle(levels, l - 1, P.T @ defect)
     if lev.learned is not None and lev.learned_mode == "replace":
-        return learned_step(lev, b, x)                             # learned step only
-    x = chebyshev(lev.apply, dinv, b, x, lev.lam_max)             # postsmoothing
-    if lev.learned is not None:
-        x = learned_step(lev, b, x)                                # learned step after it
-    return x
+        return learned_step(lev, b, x)  # the learned step takes the second smoothing's place
+    x = smooth(x)
+    return learned_step(lev, b, x) if lev.learned is not None else x
 
 
 def learned_step(lev: Level, b: np.ndarray, x: np.ndarray) -> np.ndarray:
