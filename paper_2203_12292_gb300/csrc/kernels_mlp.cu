@@ -156,20 +156,45 @@ __global__ void __launch_bounds__(GTH) gemm_tc_kernel(GemmArgs g) {
   bool ok = true;
   for (int c = 0; c < nk; ++c) {
     const int k0 = c * GKC;
-    for (int e = tid; e < GM * GKC; e += GTH) {
-      // consecutive threads along the operand's contiguous dimension
-      const int i = a_kfast ? e / GKC : e % GM, kk = a_kfast ? e % GKC : e / GM;
-      const int m = m0 + i, k = k0 + kk;
-      float v = 0.0f;
-      if (m < g.M && k < g.K)
-        v = g.Ab ? bf16_bits_to_float(g.Ab[(int64_t)m * g.sam + k]) : g.A[(int64_t)m * g.sam + (int64_t)k * g.sak];
-      As[tc::core_off(i, kk, GKC)] = __float2bfloat16_rn(v);
+    // every thread issues eight loads of the chunk before it converts and
+    // stores them (consecutive threads along the operand's contiguous dimension)
+    constexpr int PER = GM * GKC / GTH, INF = 8;
+    static_assert(GM == GN && PER * GTH == GM * GKC && PER % INF == 0, "chunk split");
+#pragma unroll 1
+    for (int u0 = 0; u0 < PER; u0 += INF) {
+      float v[INF];
+#pragma unroll
+      for (int u = 0; u < INF; ++u) {
+        const int e = tid + (u0 + u) * GTH;
+        const int i = a_kfast ? e / GKC : e % GM, kk = a_kfast ? e % GKC : e / GM;
+        const int m = m0 + i, k = k0 + kk;
+        v[u] = 0.0f;
+        if (m < g.M && k < g.K)
+          v[u] = g.Ab ? bf16_bits_to_float(g.Ab[(int64_t)m * g.sam + k]) : g.A[(int64_t)m * g.sam + (int64_t)k * g.sak];
+      }
+#pragma unroll
+      for (int u = 0; u < INF; ++u) {
+        const int e = tid + (u0 + u) * GTH;
+        const int i = a_kfast ? e / GKC : e % GM, kk = a_kfast ? e % GKC : e / GM;
+        As[tc::core_off(i, kk, GKC)] = __float2bfloat16_rn(v[u]);
+      }
     }
-    for (int e = tid; e < GN * GKC; e += GTH) {
-      const int i = b_kfast ? e / GKC : e % GN, kk = b_kfast ? e % GKC : e / GN;
-      const int n = n0 + i, k = k0 + kk;
-      const float v = (n < g.N && k < g.K) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : 0.0f;
-      Bs[tc::core_off(i, kk, GKC)] = __float2bfloat16_rn(v);
+#pragma unroll 1
+    for (int u0 = 0; u0 < PER; u0 += INF) {
+      float v[INF];
+#pragma unroll
+      for (int u = 0; u < INF; ++u) {
+        const int e = tid + (u0 + u) * GTH;
+        const int i = b_kfast ? e / GKC : e % GN, kk = b_kfast ? e % GKC : e / GN;
+        const int n = n0 + i, k = k0 + kk;
+        v[u] = (n < g.N && k < g.K) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < INF; ++u) {
+        const int e = tid + (u0 + u) * GTH;
+        const int i = b_kfast ? e / GKC : e % GN, kk = b_kfast ? e % GKC : e / GN;
+        Bs[tc::core_off(i, kk, GKC)] = __float2bfloat16_rn(v[u]);
+      }
     }
     tc::fence_async_smem();
     tc::fence_before();
