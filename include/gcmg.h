@@ -309,6 +309,16 @@ int gcmg_dot_noalloc(const double* x, const double* y, int64_t n, double* result
  * synchronises.  Pinned host memory gives full copy bandwidth.
  */
 int gcmg_vmult_host(gcmg_handle* h, int level, int fp64, const void* src, void* dst);
+/*
+ * The operator applied to n host vectors: dst[i] = A src[i] (host arrays of
+ * n pointers to n_free values each, fp64 when fp64 != 0, else fp32).  The
+ * copies to the device, the operators and the copies back of neighbouring
+ * vectors overlap: vector i + 1 arrives and vector i - 1 leaves while the
+ * operator runs on vector i (two device buffer pairs, three streams).  The
+ * results equal gcmg_vmult's bit for bit.  Pinned host memory gives full
+ * copy bandwidth; synchronises before returning.
+ */
+int gcmg_vmult_host_many(gcmg_handle* h, int level, int fp64, int n, const void* const* src, void* const* dst);
 
 /* stages of the per-level timers (CUDA events on the handle's stream) */
 #define GCMG_STAGE_VMULT 0       /* each operator application of the V-cycle levels */

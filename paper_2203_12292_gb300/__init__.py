@@ -87,6 +87,8 @@ _SIGS = {
     "gcmg_level_edge_dofs": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p]),
     "gcmg_vmult": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
     "gcmg_vmult_host": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, _c_void_p]),
+    "gcmg_vmult_host_many": (_c_int, [_c_void_p, _c_int, _c_int, _c_int, ctypes.POINTER(_c_void_p),
+                                      ctypes.POINTER(_c_void_p)]),
     "gcmg_dot": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int64, _c_void_p]),
     "gcmg_dot_noalloc": (_c_int, [_c_void_p, _c_void_p, _c_int64, _c_void_p, _c_void_p]),
     "gcmg_set_profiling": (_c_int, [_c_void_p, _c_int]),
@@ -355,6 +357,23 @@ class Multigrid:
             raise ValueError("host vectors must be contiguous")
         _check(lib().gcmg_vmult_host(self._h, level, int(src.dtype == np.float64), src.ctypes.data_as(_c_void_p),
                                      dst.ctypes.data_as(_c_void_p)))
+
+    def vmult_host_many(self, level: int, srcs: Sequence[np.ndarray], dsts: Sequence[np.ndarray]) -> None:
+        """Operator on several host (numpy) vectors, the copies of neighbouring
+        vectors overlapped with the operators; synchronous."""
+        n = self.n_free(level)
+        if len(srcs) != len(dsts):
+            raise ValueError("as many outputs as inputs")
+        for a, b in zip(srcs, dsts):
+            if a.dtype not in (np.float32, np.float64) or b.dtype != a.dtype or a.dtype != srcs[0].dtype:
+                raise ValueError("host vectors must all be float32 or all float64")
+            if len(a) != n or len(b) != n or not (a.flags.c_contiguous and b.flags.c_contiguous):
+                raise ValueError("host vectors must be contiguous with n_free values")
+        k = len(srcs)
+        sarr = (_c_void_p * max(k, 1))(*[a.ctypes.data_as(_c_void_p) for a in srcs])
+        darr = (_c_void_p * max(k, 1))(*[b.ctypes.data_as(_c_void_p) for b in dsts])
+        f64 = int(k > 0 and srcs[0].dtype == np.float64)
+        _check(lib().gcmg_vmult_host_many(self._h, level, f64, k, sarr, darr))
 
     def dot(self, x, y, out=None):
         """fp64 inner product on the device (deterministic); returns a 1-element tensor."""

@@ -946,6 +946,54 @@ int gcmg_dot_noalloc(const double* x, const double* y, int64_t n, double* result
   });
 }
 
+int gcmg_vmult_host_many(gcmg_handle* h, int level, int fp64, int n, const void* const* src, void* const* dst) {
+  return guarded([&] {
+    if (!h || n < 0 || (n > 0 && (!src || !dst))) throw Error(GCMG_ERR_ARG, "bad arguments");
+    check_level(h->h, level);
+    Handle& H = h->h;
+    LevelDev& L = *H.lev[level];
+    if (L.n() == 0 || n == 0) return;
+    for (int i = 0; i < n; ++i)
+      if (!src[i] || !dst[i]) throw Error(GCMG_ERR_ARG, "bad vectors");
+    const bool f64 = fp64 != 0;
+    const size_t bytes = L.n() * (f64 ? sizeof(double) : sizeof(float));
+    if (!H.copy_stream) ck(cudaStreamCreateWithFlags(&H.copy_stream, cudaStreamNonBlocking), "stream");
+    if (!H.out_stream) ck(cudaStreamCreateWithFlags(&H.out_stream, cudaStreamNonBlocking), "stream");
+    for (cudaEvent_t& e : H.many_ev)
+      if (!e) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    for (int k = 0; k < 2; ++k) {
+      if (H.many_in[k].bytes < bytes) H.many_in[k].alloc(bytes);
+      if (H.many_out[k].bytes < bytes) H.many_out[k].alloc(bytes);
+    }
+    cudaEvent_t* ev_in = H.many_ev;
+    cudaEvent_t* ev_comp = H.many_ev + 2;
+    cudaEvent_t* ev_out = H.many_ev + 4;
+    // everything queued on the handle's stream before comes first
+    ck(cudaEventRecord(H.many_ev[6], H.stream), "event");
+    ck(cudaStreamWaitEvent(H.copy_stream, H.many_ev[6], 0), "wait");
+    ck(cudaStreamWaitEvent(H.out_stream, H.many_ev[6], 0), "wait");
+    // vector i uses buffer pair k = i % 2: its input copy waits for the operator of vector i - 2
+    // (the last reader of in[k]), its operator for the output copy of vector i - 2 (the last
+    // reader of out[k]); so copies in, operators and copies out of neighbouring vectors overlap
+    for (int i = 0; i < n; ++i) {
+      const int k = i & 1;
+      if (i >= 2) ck(cudaStreamWaitEvent(H.copy_stream, ev_comp[k], 0), "wait");
+      ck(cudaMemcpyAsync(H.many_in[k].p, src[i], bytes, cudaMemcpyHostToDevice, H.copy_stream), "copy in");
+      ck(cudaEventRecord(ev_in[k], H.copy_stream), "event");
+      ck(cudaStreamWaitEvent(H.stream, ev_in[k], 0), "wait");
+      if (i >= 2) ck(cudaStreamWaitEvent(H.stream, ev_out[k], 0), "wait");
+      vmult(H, level, f64, H.many_in[k].p, H.many_out[k].p);
+      ck(cudaEventRecord(ev_comp[k], H.stream), "event");
+      ck(cudaStreamWaitEvent(H.out_stream, ev_comp[k], 0), "wait");
+      ck(cudaMemcpyAsync(dst[i], H.many_out[k].p, bytes, cudaMemcpyDeviceToHost, H.out_stream), "copy out");
+      ck(cudaEventRecord(ev_out[k], H.out_stream), "event");
+    }
+    ck(cudaStreamSynchronize(H.out_stream), "vmult_host_many");
+    ck(cudaStreamSynchronize(H.copy_stream), "vmult_host_many");
+    ck(cudaStreamSynchronize(H.stream), "vmult_host_many");
+  });
+}
+
 int gcmg_vmult_host(gcmg_handle* h, int level, int fp64, const void* src, void* dst) {
   return guarded([&] {
     if (!h) throw Error(GCMG_ERR_ARG, "null handle");

@@ -111,12 +111,20 @@ struct Handle {
   // host-buffer operator: the input copy in DoF order on its own stream, overlapped with the tiles
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> pipe_ev;
+  // operator on several host vectors: two device input and output buffers,
+  // the output copies on a stream of their own, events per buffer pair
+  cudaStream_t out_stream = nullptr;
+  DevBuf many_in[2], many_out[2];
+  cudaEvent_t many_ev[7] = {};  // in[2], comp[2], out[2], start
   ~Handle() {
     g_core.reset();
     g_a.reset();
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (cudaEvent_t e : pipe_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : many_ev)
+      if (e) cudaEventDestroy(e);
     if (copy_stream) cudaStreamDestroy(copy_stream);
+    if (out_stream) cudaStreamDestroy(out_stream);
   }
 };
 
