@@ -543,6 +543,16 @@ typedef struct gcmg_persistent_info {
 } gcmg_persistent_info;
 /* the work list of the last persistent solve (GCMG_ERR_ARG before the first) */
 int gcmg_batch_persistent_info(const gcmg_batch* b, gcmg_persistent_info* info);
+/*
+ * Test of the persistent kernel's failure path, without a GPU fault: from the
+ * next persistent solve on, CTA absent_cta (-1: none) leaves the kernel
+ * before the first grid barrier, and a barrier wait gives up after
+ * spin_limit polls (default 2^25).  The other CTAs' waits then run out, the
+ * kernel records the failure and returns, and the solve fails with
+ * GCMG_ERR_INTERNAL; the context stays usable.  (-1, 1 << 25) restores the
+ * normal launch.
+ */
+int gcmg_batch_persistent_wait_test(gcmg_batch* b, int absent_cta, unsigned spin_limit);
 
 /*
  * Host utility: out[i] = a uniform value in [-1, 1) attached to the point

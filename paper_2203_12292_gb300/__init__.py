@@ -141,6 +141,7 @@ _SIGS = {
     "gcmg_batch_cg_solve_persistent": (_c_int, [_c_void_p, ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p),
                                                 _c_double, _c_int, ctypes.POINTER(SolveStats)]),
     "gcmg_batch_persistent_info": (_c_int, [_c_void_p, ctypes.POINTER(PersistentInfo)]),
+    "gcmg_batch_persistent_wait_test": (_c_int, [_c_void_p, _c_int, ctypes.c_uint]),
 }
 
 _lib = None
@@ -694,6 +695,11 @@ class Batch:
         fn = lib().gcmg_batch_cg_solve_persistent if persistent else lib().gcmg_batch_cg_solve
         _check(fn(self._p, barr, xarr, rtol, maxit, st))
         return [st[i] for i in range(n)]
+
+    def persistent_wait_test(self, absent_cta: int = -1, spin_limit: int = 1 << 25) -> None:
+        """Test of the persistent kernel's bounded waits: CTA absent_cta leaves
+        before the first grid barrier; (-1, 1 << 25) restores the normal launch."""
+        _check(lib().gcmg_batch_persistent_wait_test(self._p, absent_cta, spin_limit))
 
     def persistent_info(self) -> PersistentInfo:
         """grid, shared memory, operations and steps of the last persistent solve"""

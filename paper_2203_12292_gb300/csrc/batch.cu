@@ -44,6 +44,9 @@ struct DwlState {
 struct gcmg_batch {
   std::vector<std::unique_ptr<gcmg_handle>> probs;
   std::unique_ptr<DwlState> dwl;
+  // test of the persistent kernel's bounded waits (gcmg_batch_persistent_wait_test)
+  int absent_cta = -1;
+  unsigned spin_limit = 1u << 25;
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -74,6 +77,7 @@ struct DwlEntry {
   int id;
   size_t bytes;
   int coarsen;
+  bool serial;
 };
 std::mutex g_dwl_mu;
 std::unordered_map<const void*, DwlEntry> g_dwl_reg;
@@ -81,7 +85,7 @@ std::unordered_map<const void*, DwlEntry> g_dwl_reg;
 
 void dwl_register(const void* kernel, int id, size_t arg_bytes) {
   std::lock_guard<std::mutex> lock(g_dwl_mu);
-  g_dwl_reg[kernel] = DwlEntry{id, arg_bytes, 1};
+  g_dwl_reg[kernel] = DwlEntry{id, arg_bytes, 1, false};
 }
 
 void dwl_set_coarsen(const void* kernel, int factor) {
@@ -90,12 +94,19 @@ void dwl_set_coarsen(const void* kernel, int factor) {
   if (it != g_dwl_reg.end() && factor >= 1) it->second.coarsen = factor;
 }
 
-int dwl_lookup(const void* kernel, size_t* bytes, int* coarsen) {
+void dwl_set_serial(const void* kernel) {
+  std::lock_guard<std::mutex> lock(g_dwl_mu);
+  const auto it = g_dwl_reg.find(kernel);
+  if (it != g_dwl_reg.end()) it->second.serial = true;
+}
+
+int dwl_lookup(const void* kernel, size_t* bytes, int* coarsen, bool* serial) {
   std::lock_guard<std::mutex> lock(g_dwl_mu);
   const auto it = g_dwl_reg.find(kernel);
   if (it == g_dwl_reg.end()) return -1;
   *bytes = it->second.bytes;
   *coarsen = it->second.coarsen;
+  *serial = it->second.serial;
   return it->second.id;
 }
 
@@ -350,7 +361,7 @@ void build_dwl(gcmg_batch& B, const double* const* b, double* const* x, double r
   ck(cudaStreamSynchronize(B.stream), "upload");
   // one launch of the persistent kernel, captured in a graph with the reset of its barrier
   DwlParams P{D->ops.as<DwlOp>(), D->probs.as<DwlProb>(), np, D->go.as<int>(), D->ctl.as<unsigned>(),
-              D->ctl.as<int>() + 2, D->max_steps};
+              D->ctl.as<int>() + 2, D->max_steps, B.spin_limit, B.absent_cta};
   cudaGraph_t G = nullptr;
   ck(cudaStreamBeginCapture(B.cap, cudaStreamCaptureModeRelaxed), "capture");
   cudaError_t e = cudaMemsetAsync(D->ctl.p, 0, 4 * sizeof(unsigned), B.cap);
@@ -585,6 +596,15 @@ int gcmg_batch_cg_solve_persistent(gcmg_batch* b, const double* const* rhs, doub
       stats[i] = gcmg_solve_stats{(int)h[4 * i], std::sqrt(nb2), nb2 > 0 ? std::sqrt(h[4 * i + 1] / nb2) : 0.0,
                                   (int)h[4 * i + 3]};
     }
+  });
+}
+
+int gcmg_batch_persistent_wait_test(gcmg_batch* b, int absent_cta, unsigned spin_limit) {
+  return guarded([&] {
+    if (!b || spin_limit < 1) throw Error(GCMG_ERR_ARG, "bad arguments");
+    b->absent_cta = absent_cta;
+    b->spin_limit = spin_limit;
+    b->dwl.reset();  // the next persistent solve rebuilds its launch with these parameters
   });
 }
 

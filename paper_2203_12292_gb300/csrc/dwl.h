@@ -71,6 +71,8 @@ struct DwlParams {
   unsigned* bar;        // grid barrier: arrivals, generation (zero at launch)
   int* status;          // [0]: 0, 1 barrier wait gave up, 2 step bound reached; [1]: steps taken
   long long max_steps;  // bound on the schedule's length
+  unsigned spin_limit;  // polls of a grid-barrier wait before it gives up
+  int absent_cta;       // test of the bounded waits: this CTA leaves before the first barrier (-1: none)
 };
 
 // CTAs of the persistent kernel with `smem` bytes of dynamic shared memory
@@ -95,8 +97,12 @@ void dwl_register(const void* kernel, int id, size_t arg_bytes);
 // a registered grid-stride kernel runs with `factor` times fewer virtual
 // blocks (its results do not depend on the grid)
 void dwl_set_coarsen(const void* kernel, int factor);
-// id of a registered kernel, -1 when absent; *bytes its packed size, *coarsen its factor
-int dwl_lookup(const void* kernel, size_t* bytes, int* coarsen);
+// a registered kernel without block barriers, which may be recorded with
+// fewer than 256 threads (the others must be launched with exactly 256)
+void dwl_set_serial(const void* kernel);
+// id of a registered kernel, -1 when absent; *bytes its packed size, *coarsen
+// its factor, *serial whether it may run on fewer threads
+int dwl_lookup(const void* kernel, size_t* bytes, int* coarsen, bool* serial);
 // fills the registry (once per process)
 void dwl_register_all();
 
@@ -110,8 +116,10 @@ template <typename... KArgs>
 bool dwl_record(const void* kernel, unsigned grid, unsigned block, size_t smem, const KArgs&... a) {
   size_t bytes = 0;
   int coarsen = 1;
-  const int id = dwl_lookup(kernel, &bytes, &coarsen);
-  if (id < 0 || bytes != dwl_size<KArgs...>() || bytes > (size_t)DWL_ARG_BYTES || block > 256u) return false;
+  bool serial = false;
+  const int id = dwl_lookup(kernel, &bytes, &coarsen, &serial);
+  if (id < 0 || bytes != dwl_size<KArgs...>() || bytes > (size_t)DWL_ARG_BYTES) return false;
+  if (serial ? (block > 256u) : (block != 256u)) return false;
   DwlOp op{};
   op.type = id;
   op.items = (int32_t)((grid + coarsen - 1) / coarsen);

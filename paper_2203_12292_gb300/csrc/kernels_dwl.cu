@@ -113,7 +113,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 
 // grid barrier (all CTAs resident: cooperative launch); false after a bounded wait
-__device__ bool dwl_grid_sync(unsigned* bar, unsigned& gen, int* ok_sh) {
+__device__ bool dwl_grid_sync(unsigned* bar, unsigned& gen, int* ok_sh, unsigned spin_limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
@@ -128,7 +128,7 @@ __device__ bool dwl_grid_sync(unsigned* bar, unsigned& gen, int* ok_sh) {
     // generation, so that its later loads see what the other CTAs wrote
     unsigned it = 0;
     while (ld_acquire(&bar[1]) == g) {
-      if (++it > (1u << 25)) {
+      if (++it > spin_limit) {
         ok = 0;
         break;
       }
@@ -211,7 +211,8 @@ __global__ void __launch_bounds__(BLOCK, 2) dwl_kernel(DwlParams P) {
       }
       __syncthreads();  // the next item reuses the shared memory
     }
-    if (!dwl_grid_sync(P.bar, gen, &s_ok)) {
+    if (step == 0 && (int)blockIdx.x == P.absent_cta) return;  // its peers' waits run out
+    if (!dwl_grid_sync(P.bar, gen, &s_ok, P.spin_limit)) {
       if (threadIdx.x == 0) atomicExch(&P.status[0], 1);
       return;
     }

@@ -705,6 +705,10 @@ void dwl_register_vec() {
   GCMG_DWL_COARSEN((cg_p_kernel<double>)) GCMG_DWL_COARSEN((cg_p_kernel<float>))
 #undef GCMG_DWL_COARSEN
   dwl_register(reinterpret_cast<const void*>(cg_check_kernel), DWL_OP_CHECK, dwl_args_size(cg_check_kernel));
+#define GCMG_DWL_SERIAL(fn) dwl_set_serial(reinterpret_cast<const void*>(fn));
+  GCMG_DWL_VEC_SERIAL(GCMG_DWL_SERIAL)
+  dwl_set_serial(reinterpret_cast<const void*>(cg_check_kernel));  // run by thread 0 of the persistent kernel
+#undef GCMG_DWL_SERIAL
 }
 
 #endif  // GCMG_BODIES_ONLY

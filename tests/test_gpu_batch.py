@@ -139,6 +139,21 @@ def test_persistent_maxit(batch):
         assert s.iterations == 2 and s.status == 4  # GCMG_ERR_NOT_CONVERGED
 
 
+def test_persistent_barrier_wait_gives_up(gcmg, batch):
+    """one CTA leaves before the first grid barrier: the others' bounded waits
+    run out, the kernel records it and returns, the call fails with an error,
+    and the next normal persistent solve still converges (no GPU fault, no hang)"""
+    bs = [_rhs(m, 400 + i) for i, m in enumerate(batch.problems)]
+    xs = [torch.zeros_like(b) for b in bs]
+    batch.persistent_wait_test(absent_cta=0, spin_limit=1 << 14)
+    with pytest.raises(gcmg.GcmgError, match="grid-barrier wait gave up"):
+        batch.cg_solve(bs, xs, 1e-8, persistent=True)
+    batch.persistent_wait_test()
+    xs = [torch.zeros_like(b) for b in bs]
+    stats = batch.cg_solve(bs, xs, 1e-8, persistent=True)
+    assert all(s.status == 0 and s.rel_residual <= 1e-8 for s in stats)
+
+
 def test_autotune(gcmg):
     probe = gcmg.Mesh.from_recipe(synth.cube_octant(3, 1))
     best, cands = gcmg.autotune(probe, 2, mg_fp32=True, reps=5)
