@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(BLOCK) prolong_h(TArgs<T> A) {
   const int ntot = nc * 8 * N3;
   for (int t0 = threadIdx.x; t0 < ntot; t0 += RG * BLOCK) {
     int idx[RG];
-    T val[RG], old[RG];
+    T val[RG];
 #pragma unroll
     for (int u = 0; u < RG; ++u) {
       const int t = t0 + u * BLOCK;
@@ -208,11 +208,10 @@ __global__ void __launch_bounds__(BLOCK) prolong_h(TArgs<T> A) {
           val[u] = sm_ref[j] ? e3[j * M3 + s_e3[r]] : cb[j * N3 + n];
         }
       }
-      if (idx[u] >= 0) old[u] = A.dst[idx[u]];
     }
 #pragma unroll
     for (int u = 0; u < RG; ++u)
-      if (idx[u] >= 0) A.dst[idx[u]] = old[u] + val[u];
+      if (idx[u] >= 0) atomicAdd(A.dst + idx[u], val[u]);
   }
 }
 
@@ -392,12 +391,24 @@ __global__ void __launch_bounds__(BLOCK) prolong_p(TArgs<T> A) {
   const int c0 = blockIdx.x * TP;
   const int nc = min(TP, A.n_coarse - c0);
   for (int c = threadIdx.x; c < nc; c += blockDim.x) sm_mask[c] = A.mask_c[c0 + c];
-  for (int t = threadIdx.x; t < nc * NC3; t += blockDim.x) {
-    const int cell = t / NC3, n = t - cell * NC3;
-    int slot, off;
-    node_slot<KC>(n % NC, (n / NC) % NC, n / (NC * NC), slot, off);
-    const int32_t g = A.gstart_c[(size_t)(c0 + cell) * NSLOT + slot];
-    cb[t] = g < 0 ? T(0) : A.src[g + off];
+  constexpr int RG = 8;  // independent chains of loads in flight per thread
+  for (int t0 = threadIdx.x; t0 < nc * NC3; t0 += RG * BLOCK) {
+    T v[RG];
+#pragma unroll
+    for (int u = 0; u < RG; ++u) {
+      const int t = t0 + u * BLOCK;
+      v[u] = T(0);
+      if (t < nc * NC3) {
+        const int cell = t / NC3, n = t - cell * NC3;
+        int slot, off;
+        node_slot<KC>(n % NC, (n / NC) % NC, n / (NC * NC), slot, off);
+        const int32_t g = A.gstart_c[(size_t)(c0 + cell) * NSLOT + slot];
+        if (g >= 0) v[u] = A.src[g + off];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RG; ++u)
+      if (t0 + u * BLOCK < nc * NC3) cb[t0 + u * BLOCK] = v[u];
   }
   __syncthreads();
   hanging_all<KC, false>(cb, sm_mask, nc);
@@ -407,12 +418,24 @@ __global__ void __launch_bounds__(BLOCK) prolong_p(TArgs<T> A) {
   __syncthreads();
   tsweep<KF, 1, NC, NF, 2, false>(e2, e3, NF, NF, NC, nc, S2, NF3, nullptr);
   __syncthreads();
-  for (int t = threadIdx.x; t < nc * NF3; t += blockDim.x) {
-    const int cell = t / NF3, n = t - cell * NF3;
-    const int f = c0 + cell;
-    int slot, off;
-    node_slot<KF>(n % NF, (n / NF) % NF, n / (NF * NF), slot, off);
-    if ((A.own_f[f] >> slot) & 1u) A.dst[A.gstart_f[(size_t)f * NSLOT + slot] + off] += e3[t];
+  // owner-selected additions (each fine DoF once: red.add gives the read-modify-write's sum)
+  for (int t0 = threadIdx.x; t0 < nc * NF3; t0 += RG * BLOCK) {
+    int idx[RG];
+#pragma unroll
+    for (int u = 0; u < RG; ++u) {
+      const int t = t0 + u * BLOCK;
+      idx[u] = -1;
+      if (t < nc * NF3) {
+        const int cell = t / NF3, n = t - cell * NF3;
+        const int f = c0 + cell;
+        int slot, off;
+        node_slot<KF>(n % NF, (n / NF) % NF, n / (NF * NF), slot, off);
+        if ((A.own_f[f] >> slot) & 1u) idx[u] = A.gstart_f[(size_t)f * NSLOT + slot] + off;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RG; ++u)
+      if (idx[u] >= 0) atomicAdd(A.dst + idx[u], e3[t0 + u * BLOCK]);
   }
 }
 
@@ -447,12 +470,24 @@ __global__ void __launch_bounds__(BLOCK) restrict_p(TArgs<T> A) {
       sm_mask[j] = A.mask_c[ti.cell_begin + cell];
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < np * NF3; t += blockDim.x) {
-      const int j = t / NF3, n = t - j * NF3;
-      const int f = ti.cell_begin + sm_cell[j];
-      int slot, off;
-      node_slot<KF>(n % NF, (n / NF) % NF, n / (NF * NF), slot, off);
-      e3[t] = ((A.own_f[f] >> slot) & 1u) ? A.src[A.gstart_f[(size_t)f * NSLOT + slot] + off] : T(0);
+    constexpr int RG = 8;  // independent chains of loads in flight per thread
+    for (int t0 = threadIdx.x; t0 < np * NF3; t0 += RG * BLOCK) {
+      T v[RG];
+#pragma unroll
+      for (int u = 0; u < RG; ++u) {
+        const int t = t0 + u * BLOCK;
+        v[u] = T(0);
+        if (t < np * NF3) {
+          const int j = t / NF3, n = t - j * NF3;
+          const int f = ti.cell_begin + sm_cell[j];
+          int slot, off;
+          node_slot<KF>(n % NF, (n / NF) % NF, n / (NF * NF), slot, off);
+          if ((A.own_f[f] >> slot) & 1u) v[u] = A.src[A.gstart_f[(size_t)f * NSLOT + slot] + off];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < RG; ++u)
+        if (t0 + u * BLOCK < np * NF3) e3[t0 + u * BLOCK] = v[u];
     }
     __syncthreads();
     tsweep<KF, 1, NF, NC, 2, true>(e3, e2, NF, NF, NF, np, NF3, S2, nullptr);
