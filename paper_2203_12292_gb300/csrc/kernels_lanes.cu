@@ -154,6 +154,14 @@ __device__ __forceinline__ void add_ordered(float* x, float v, bool real, int la
   }
 }
 
+// named barrier `id` of n threads: producers arrive, consumers wait
+__device__ __forceinline__ void named_bar_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 // the three gather/scatter addresses of x-line r of the cell in this lane:
 // node (0, b, c), first interior node (1, b, c), node (k, b, c)
 template <int K>
@@ -247,35 +255,48 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
   const int nxl = c_ll.nx[K][w];
 
   if (!hang) {
-    // G_e fused with the forward x sweep: all loads of the warp's x-lines first
+    // Warp w holds the plane c = w of its cell in registers: G_e, the x and y
+    // sweeps forward; the z phase through the cell buffer; the y and x sweeps
+    // backward and G_e^T, again on the plane in registers.
+    //   Plane x-lines (b, w): node (0, b, w) lies in slot 9 cls(w) + 3 cls(b),
+    // nodes (1..k-1, b, w) in the slot after it, node (k, b, w) two after it;
+    // their offsets in the entities are the same for b = 0 and b = k and grow
+    // by one x-step (node (0, .)) or one x-line of the entity (node (1, .)) per
+    // interior b (entity DoFs lexicographic over the interior axes).
+    const uint32_t l0 = c_ll.line[K][N * w], l1 = c_ll.line[K][(K > 1 ? 1 : 0) + N * w];
+    const uint16_t* lsw = &st->ls[l0 & 0xff][lane];
+    const char* xA0 = xb + ((l0 >> 8) & 0xff);  // node (0, b, w), b = 0 or k
+    const char* xA1 = xb + (l0 >> 16);          // node (1, b, w), b = 0 or k
+    const char* xB0 = xb + ((l1 >> 8) & 0xff);  // node (0, 1, w)
+    const char* xB1 = xb + (l1 >> 16);          // node (1, 1, w)
+    float u[N2];
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+      const bool in = b > 0 && b < K;
+      const int sb = b == 0 ? 0 : (b == K ? 6 : 3);
+      const int q0 = lsw[(sb + 0) * 32], q1 = lsw[(sb + 1) * 32], q2 = lsw[(sb + 2) * 32];
+      const float* p0 = reinterpret_cast<const float*>((in ? xB0 : xA0) + q0) + (in ? b - 1 : 0);
+      const float* p1 = reinterpret_cast<const float*>((in ? xB1 : xA1) + q1) + (in ? (b - 1) * (K - 1) : 0);
+      const float* p2 = reinterpret_cast<const float*>((in ? xB0 : xA0) + q2) + (in ? b - 1 : 0);
+      u[N * b] = *p0;
+#pragma unroll
+      for (int a = 1; a < K; ++a) u[N * b + a] = p1[a - 1];
+      u[N * b + K] = *p2;
+    }
+#pragma unroll
+    for (int b = 0; b < N; ++b) eo_forward<N, 0, 1>(u + N * b, tb.Be);  // x-lines of the plane
+#pragma unroll
+    for (int a = 0; a < N; ++a) eo_forward<N, 0, N>(u + a, tb.Be);  // y-lines
     {
-      float v[NXW][N];
+      float* p = cb + (N2 * w) * 32 + lane;
 #pragma unroll
-      for (int i = 0; i < NXW; ++i)
-        if (G::BAL || i < nxl) {
-          float *p0, *p1, *p2;
-          xline_ptrs<K>(st, xb, c_ll.xw[K][w][i], lane, p0, p1, p2);
-          v[i][0] = *p0;
-#pragma unroll
-          for (int a = 1; a < K; ++a) v[i][a] = p1[a - 1];
-          v[i][K] = *p2;
-        }
-#pragma unroll
-      for (int i = 0; i < NXW; ++i)
-        if (G::BAL || i < nxl) {
-          eo_forward<N, 0, 1>(v[i], tb.Be);
-          float* p = cb + N * c_ll.xw[K][w][i] * 32 + lane;
-#pragma unroll
-          for (int a = 0; a < N; ++a) p[a * 32] = v[i][a];
-        }
+      for (int n = 0; n < N2; ++n) p[n * 32] = u[n];
     }
     __syncthreads();
     {  // the tile DoFs are dead: clear the accumulator
       float4* z4 = reinterpret_cast<float4*>(xs0);
       for (int i = threadIdx.x; i < (sh + nloc + 3) / 4; i += NT) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    sweep_y<K, true>(cb, w, lane);
-    __syncthreads();
     // z: forward sweep, h (lam_a + lam_b + lam_c) in mode order, backward sweep (lines (a, b) = (i, w))
     {
       const float hb = h * tb.lame[w];
@@ -295,30 +316,34 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
       }
     }
     __syncthreads();
-    sweep_y<K, false>(cb, w, lane);
-    __syncthreads();
-    // backward x sweep fused with G_e^T: each warp adds its class of x-lines in program order
     {
-      float v[NXW][N];
+      const float* p = cb + (N2 * w) * 32 + lane;
 #pragma unroll
-      for (int i = 0; i < NXW; ++i)
-        if (G::BAL || i < nxl) {
-          const float* p = cb + N * c_ll.xw[K][w][i] * 32 + lane;
-#pragma unroll
-          for (int a = 0; a < N; ++a) v[i][a] = p[a * 32];
-        }
-#pragma unroll
-      for (int i = 0; i < NXW; ++i)
-        if (G::BAL || i < nxl) {
-          eo_backward<N, 0, 1>(v[i], tb.Be);
-          float *p0, *p1, *p2;
-          xline_ptrs<K>(st, xb, c_ll.xw[K][w][i], lane, p0, p1, p2);
-          *p0 += v[i][0];
-#pragma unroll
-          for (int a = 1; a < K; ++a) p1[a - 1] += v[i][a];
-          *p2 += v[i][K];
-        }
+      for (int n = 0; n < N2; ++n) u[n] = p[n * 32];
     }
+#pragma unroll
+    for (int a = 0; a < N; ++a) eo_backward<N, 0, N>(u + a, tb.Be);
+#pragma unroll
+    for (int b = 0; b < N; ++b) eo_backward<N, 0, 1>(u + N * b, tb.Be);
+    // G_e^T.  Nodes of two cells are one DoF only where every coordinate is
+    // equal or both lie on the cell boundary: between planes only c = 0 and
+    // c = k meet, so warp k adds after warp 0 (named barrier 1); within a
+    // plane the x-lines and their nodes add in program order.
+    if (w == K) named_bar_sync(1, 64);
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+      const bool in = b > 0 && b < K;
+      const int sb = b == 0 ? 0 : (b == K ? 6 : 3);
+      const int q0 = lsw[(sb + 0) * 32], q1 = lsw[(sb + 1) * 32], q2 = lsw[(sb + 2) * 32];
+      float* p0 = reinterpret_cast<float*>(const_cast<char*>(in ? xB0 : xA0) + q0) + (in ? b - 1 : 0);
+      float* p1 = reinterpret_cast<float*>(const_cast<char*>(in ? xB1 : xA1) + q1) + (in ? (b - 1) * (K - 1) : 0);
+      float* p2 = reinterpret_cast<float*>(const_cast<char*>(in ? xB0 : xA0) + q2) + (in ? b - 1 : 0);
+      *p0 += u[N * b];
+#pragma unroll
+      for (int a = 1; a < K; ++a) p1[a - 1] += u[N * b + a];
+      *p2 += u[N * b + K];
+    }
+    if (w == 0) named_bar_arrive(1, 64);
   } else {
     // G_e and C_x on the warp's x-lines
 #pragma unroll 1
