@@ -6,7 +6,7 @@
 // lines of each direction.  All lanes of a warp therefore touch the same
 // local node of 32 different cells at once, so
 //   * the cell buffer is node-major (node n of cell j at n * 32 + j): every
-//     sweep, in every direction, reads and writes 32 consecutive words
+//     access to it, in every direction, reads or writes 32 consecutive words
 //     (no bank conflicts), and all indexing except the DoF gather/scatter is
 //     uniform across the warp;
 //   * the entity starts of the tile are stored transposed (slot s of cell j
@@ -20,16 +20,20 @@
 // different cells can be the same DoF only if, along every axis, their
 // coordinates are equal or both lie on the cell boundary (0 or k); the same
 // holds through hanging faces and edges, whose slots point to the coarse
-// entity with the same local offsets.  The x-lines (b, c) are grouped into
-// classes by (b or "boundary", c or "boundary"); each class is given to one
-// warp, so two warps never add to the same DoF, and a warp adds in program
-// order.  Within one instruction two lanes add to the same DoF only through
-// hanging slots (siblings behind one coarse face or edge); tiles with hanging
-// cells add such groups one lane after another in lane order.  The sums are
-// therefore reproducible bit for bit.  Tiles without hanging cells fuse the
-// gather with the first x sweep and the last x sweep with the scatter; tiles
-// with hanging cells apply C_e and C_e^T (Sec. 3.2, direction by direction)
-// between separate passes.
+// entity with the same local offsets.
+//   * fp32, tiles without hanging cells: warp w keeps the z-plane c = w of
+//     its lane's cell in registers (gather, x and y sweeps forward; the z
+//     phase through the cell buffer; y and x sweeps backward and the scatter).
+//     Planes c = 0 and c = k are the only ones that meet, so warp k adds after
+//     warp 0 (a named barrier); a warp adds its nodes in program order.
+//   * tiles with hanging cells, and the double-float kernel: the x-lines
+//     (b, c) are grouped into classes by (b or "boundary", c or "boundary");
+//     each class is given to one warp, so two warps never add to the same
+//     DoF.  Within one instruction two lanes add to the same DoF only through
+//     hanging slots (siblings behind one coarse face or edge), added one lane
+//     after another in lane order.  These tiles apply C_e and C_e^T (Sec. 3.2,
+//     direction by direction) between separate passes.
+// The sums are therefore reproducible bit for bit.
 #include <algorithm>
 #include <map>
 #include <vector>
