@@ -620,6 +620,20 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
     L->lane_tiles.upload(lh.lane, H.stream);
     L->lane_order.upload(lh.lane_order, H.stream);
     L->lane_hang.upload(lh.lane_hang, H.stream);
+    {  // the lane kernels' records in launch order
+      std::vector<TileInfo> ti_lo;
+      std::vector<LaneTile> lt_lo;
+      std::vector<LaneHang> lh_lo;
+      for (size_t b = 0; b < lh.lane_order.size(); ++b) {
+        const int32_t t = lh.lane_order[b];
+        ti_lo.push_back(lh.tiles[t]);
+        lt_lo.push_back(lh.lane[t]);
+        if ((int)b < lh.n_hang_tiles) lh_lo.push_back(lh.lane_hang[t]);
+      }
+      L->tiles_lo.upload(ti_lo, H.stream);
+      L->lane_tiles_lo.upload(lt_lo, H.stream);
+      L->lane_hang_lo.upload(lh_lo, H.stream);
+    }
     std::vector<int32_t> ijk(lh.cells.size() * 3);
     for (size_t c = 0; c < lh.cells.size(); ++c) {
       ijk[3 * c] = lh.cells[c].i;
@@ -646,6 +660,9 @@ void setup_handle(Handle& H, const std::vector<Octree>& gc_meshes, int lmax, con
     c.lane_tiles = lh.lane.empty() ? nullptr : L->lane_tiles.p;
     c.lane_order = lh.lane.empty() ? nullptr : L->lane_order.as<int32_t>();
     c.lane_hang = lh.lane.empty() ? nullptr : L->lane_hang.p;
+    c.tiles_lo = lh.lane.empty() ? nullptr : L->tiles_lo.as<TileInfo>();
+    c.lane_tiles_lo = lh.lane.empty() ? nullptr : L->lane_tiles_lo.p;
+    c.lane_hang_lo = lh.lane.empty() ? nullptr : L->lane_hang_lo.p;
     c.n_hang_tiles = lh.n_hang_tiles;
     c.cell_ijk = L->cell_ijk.as<int32_t>();
     c.k = k;

@@ -16,7 +16,8 @@ namespace gcmg {
 struct LevelDev {
   LevelHost host;
   bool fp32 = true;
-  DevBuf tiles, meta, foreign, subptr, perm, cell_ijk, gstart, own, mask, lane_tiles, lane_order, lane_hang;
+  DevBuf tiles, meta, foreign, subptr, perm, cell_ijk, gstart, own, mask, lane_tiles, lane_order, lane_hang, tiles_lo,
+      lane_tiles_lo, lane_hang_lo;
   DevBuf halo, halo_dofs, halo_ptr, halo_src, halo_pos;
   DevBuf diag64, dinv64, dinv32;
   DevBuf x, b, d, t;        // V-cycle vectors in level precision

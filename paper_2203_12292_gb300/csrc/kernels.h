@@ -41,6 +41,11 @@ struct CellLaunch {
   const void* lane_tiles;  // per tile LaneTile (null: level without them)
   const int32_t* lane_order;  // launch order of the tiles: those with hanging cells first
   const void* lane_hang;      // per tile LaneHang
+  // the same in launch order (block b runs tile lane_order[b]): TileInfo and
+  // LaneTile of every tile, LaneHang of the first n_hang_tiles
+  const TileInfo* tiles_lo;
+  const void* lane_tiles_lo;
+  const void* lane_hang_lo;
   int n_hang_tiles;           // tiles with hanging cells
   double lo, dom;
   const double* coef;  // per cell coefficient nu_e (element matrix nu_e h A_ref); null: 1

@@ -66,6 +66,9 @@ struct LaneArgsT {
   const LaneTile* lt;
   const LaneHang* lh;    // per tile: hanging lines and slots of every lane
   const int32_t* order;  // tile of block b: order[b] (null: tile0 + b)
+  const TileInfo* tiles_lo;  // with order: block b's TileInfo, LaneTile, LaneHang at [b]
+  const LaneTile* lt_lo;
+  const LaneHang* lh_lo;
   int n_hang;            // with order: blocks below n_hang have tiles with hanging cells
   const int32_t* foreign;
   const int32_t* halo_pos;
@@ -209,8 +212,11 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
   float* cb = reinterpret_cast<float*>(smem + sizeof(LaneTile) + sizeof(LaneHang));
   float* xs0 = cb + N3 * 32;  // 16-byte aligned
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int tile = A.order ? A.order[blockIdx.x] : A.tile0 + blockIdx.x;
-  const TileInfo ti = A.tiles[tile];
+  // block b's tile: records in launch order at [b] (no dependent load of the tile index) or tile0 + b
+  const int bx = blockIdx.x, tl = A.tile0 + bx;
+  const LaneTile* ltp = A.order ? A.lt_lo + bx : A.lt + tl;
+  const LaneHang* lhp = A.order ? A.lh_lo + bx : A.lh + tl;
+  const TileInfo ti = A.order ? A.tiles_lo[bx] : A.tiles[tl];
   const int nloc = ti.n_owned + ti.n_foreign;
   // tile DoF i at xs[i] (then the zero region; later the accumulator): xs + i is 16-byte aligned
   // exactly where src + dof_begin + i is, so the owned range moves in 16-byte pieces
@@ -219,11 +225,11 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
   float* xs = xs0 + sh;
   const int h0 = min((4 - sh) & 3, ti.n_owned), nv = (ti.n_owned - h0) >> 2;
   {  // asynchronous copies of the lane metadata and the tile's DoFs, all in flight at once
-    const uint4* g = reinterpret_cast<const uint4*>(A.lt + tile);
+    const uint4* g = reinterpret_cast<const uint4*>(ltp);
     uint4* s = reinterpret_cast<uint4*>(st);
     for (int i = threadIdx.x; i < (int)(sizeof(LaneTile) / 16); i += NT) cp_async16(s + i, g + i);
     if (!A.order || (int)blockIdx.x < A.n_hang) {  // the tile has hanging cells (or may have)
-      const uint4* gh = reinterpret_cast<const uint4*>(A.lh + tile);
+      const uint4* gh = reinterpret_cast<const uint4*>(lhp);
       uint4* shh = reinterpret_cast<uint4*>(hg);
       for (int i = threadIdx.x; i < (int)(sizeof(LaneHang) / 16); i += NT) cp_async16(shh + i, gh + i);
     }
@@ -648,8 +654,11 @@ __global__ void __launch_bounds__((K + 1) * 32) vmult_lanes_df(LaneArgsT<double>
   df* cb = reinterpret_cast<df*>(smem + sizeof(LaneTile) + sizeof(LaneHang));
   double* xd0 = reinterpret_cast<double*>(cb + N3 * 32);  // 16-byte aligned
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int tile = A.order ? A.order[blockIdx.x] : A.tile0 + blockIdx.x;
-  const TileInfo ti = A.tiles[tile];
+  // block b's tile: records in launch order at [b] (no dependent load of the tile index) or tile0 + b
+  const int bx = blockIdx.x, tl = A.tile0 + bx;
+  const LaneTile* ltp = A.order ? A.lt_lo + bx : A.lt + tl;
+  const LaneHang* lhp = A.order ? A.lh_lo + bx : A.lh + tl;
+  const TileInfo ti = A.order ? A.tiles_lo[bx] : A.tiles[tl];
   const int nloc = ti.n_owned + ti.n_foreign;
   // tile DoF i at xd[i] (fp64 on arrival, then df in place; the zero region after it)
   const double* so = A.src + ti.dof_begin;
@@ -658,11 +667,11 @@ __global__ void __launch_bounds__((K + 1) * 32) vmult_lanes_df(LaneArgsT<double>
   df* xs = reinterpret_cast<df*>(xd);
   const int h0 = min(sh, ti.n_owned), nv = (ti.n_owned - h0) >> 1;
   {
-    const uint4* g = reinterpret_cast<const uint4*>(A.lt + tile);
+    const uint4* g = reinterpret_cast<const uint4*>(ltp);
     uint4* s = reinterpret_cast<uint4*>(st);
     for (int i = threadIdx.x; i < (int)(sizeof(LaneTile) / 16); i += NT) cp_async16(s + i, g + i);
     if (!A.order || (int)blockIdx.x < A.n_hang) {  // the tile has hanging cells (or may have)
-      const uint4* gh = reinterpret_cast<const uint4*>(A.lh + tile);
+      const uint4* gh = reinterpret_cast<const uint4*>(lhp);
       uint4* shh = reinterpret_cast<uint4*>(hg);
       for (int i = threadIdx.x; i < (int)(sizeof(LaneHang) / 16); i += NT) cp_async16(shh + i, gh + i);
     }
@@ -902,6 +911,9 @@ void launch_vmult_lanes_df(const CellLaunch& L, const double* src, double* dst, 
   A.lh = static_cast<const LaneHang*>(L.lane_hang);
   A.n_hang = L.n_hang_tiles;
   A.order = (t0 == 0 && t1 == L.n_tiles) ? L.lane_order : nullptr;
+  A.tiles_lo = L.tiles_lo;
+  A.lt_lo = static_cast<const LaneTile*>(L.lane_tiles_lo);
+  A.lh_lo = static_cast<const LaneHang*>(L.lane_hang_lo);
   A.foreign = L.foreign;
   A.halo_pos = L.halo_pos;
   A.src = src;
@@ -930,6 +942,9 @@ void launch_vmult_lanes(const CellLaunch& L, const void* src, void* dst, int add
   // a whole level: tiles with hanging cells first (their longer code path then
   // runs mostly on its own instead of interleaved with the regular tiles')
   A.order = (t0 == 0 && t1 == L.n_tiles) ? L.lane_order : nullptr;
+  A.tiles_lo = L.tiles_lo;
+  A.lt_lo = static_cast<const LaneTile*>(L.lane_tiles_lo);
+  A.lh_lo = static_cast<const LaneHang*>(L.lane_hang_lo);
   A.foreign = L.foreign;
   A.halo_pos = L.halo_pos;
   A.src = static_cast<const float*>(src);
