@@ -82,15 +82,6 @@ struct LaneArgsT {
 };
 using LaneArgs = LaneArgsT<float>;
 
-template <int K>
-struct LaneGeom {
-  static constexpr int N = K + 1, N2 = N * N, N3 = N2 * N, NT = N * 32;
-  // x-lines per warp in the class-partitioned table: at most NXW, exactly NXW
-  // on every warp for k >= 3 (balanced); k = 1: one class of 4 lines
-  static constexpr int NXW = K <= 2 ? 4 : N;
-  static constexpr bool BAL = K >= 3;
-};
-
 // child-side interpolation I_p (TRANS: its transpose) on one line in
 // registers.  I_1[a][b] = I_0[k-a][k-b] (Gauss-Lobatto points and Lagrange
 // basis are symmetric under x -> 1 - x), so p = 1 reverses the line, applies
@@ -204,8 +195,7 @@ __device__ __forceinline__ void sweep_y(float* cb, int w, int lane) {
 template <int K>
 __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(LaneArgs A) {
   pdl_begin();
-  using G = LaneGeom<K>;
-  constexpr int N = G::N, N2 = G::N2, N3 = G::N3, NT = G::NT, NXW = G::NXW;
+  constexpr int N = K + 1, N2 = N * N, N3 = N2 * N, NT = N * 32;
   extern __shared__ __align__(16) unsigned char smem[];
   LaneTile* st = reinterpret_cast<LaneTile*>(smem);
   LaneHang* hg = reinterpret_cast<LaneHang*>(smem + sizeof(LaneTile));
