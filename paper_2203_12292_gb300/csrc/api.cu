@@ -387,15 +387,14 @@ void vcycle_level(Handle& H, int l) {
   smooth(H, l, f64, L.x.p, L.b.p, L.d.p, L.t.p, dinv, true);  // presmoothing
   prof_end(H, r);
   r = prof_begin(H, l, GCMG_STAGE_RESIDUAL);
-  vmult(H, l, f64, L.x.p, L.t.p);  // residual
-  launch_residual(f64, L.t.p, L.b.p, L.t.p, L.n(), H.stream);
+  vmult(H, l, f64, L.x.p, L.t.p);  // A x for the residual
   prof_end(H, r);
   LevelDev& C = *H.lev[l - 1];
   r = prof_begin(H, l, GCMG_STAGE_RESTRICT);
-  // global coarsening: b^(l-1) = R r; local smoothing: b^(l-1) += R (r_S, r_E) on top of the
-  // values Algorithm 1 copied to level l-1 (r_E = -A_ES x_S: b_E is zero on level l)
-  if (!H.ls) launch_zero(!C.fp32, C.b.p, C.n(), H.stream);
-  if (C.n()) launch_restrict_add(H.tr[l]->tl, f64, L.t.p, C.b.p, H.stream);  // restriction
+  // the residual r = b - A x is formed in the restriction's gather; global coarsening:
+  // b^(l-1) = R r; local smoothing: b^(l-1) += R (r_S, r_E) on top of the values Algorithm 1
+  // copied to level l-1 (r_E = -A_ES x_S: b_E is zero on level l)
+  if (C.n()) launch_restrict_residual(H.tr[l]->tl, f64, L.b.p, L.t.p, C.b.p, !H.ls, H.stream);
   prof_end(H, r);
   vcycle_level(H, l - 1);
   r = prof_begin(H, l, GCMG_STAGE_PROLONGATE);

@@ -123,6 +123,11 @@ struct TransferLaunch {
 };
 void launch_prolongate_add(const TransferLaunch& T, bool fp64, const void* coarse, void* fine, cudaStream_t s);
 void launch_restrict_add(const TransferLaunch& T, bool fp64, const void* fine, void* coarse, cudaStream_t s);
+// coarse (+)= R (b - Ax): the residual formed inside the restriction's gather
+// (the same subtraction as launch_residual, so the same values); overwrite:
+// coarse = R (b - Ax), no zeroing of coarse needed
+void launch_restrict_residual(const TransferLaunch& T, bool fp64, const void* b, const void* Ax, void* coarse,
+                              bool overwrite, cudaStream_t s);
 
 // vector kernels
 void upload_tables();

@@ -88,6 +88,11 @@ struct TArgs {
   const uint16_t* mask_c;
   const T* src;
   T* dst;
+  // restriction: rhs set: restrict rhs - src (the residual b - A x, the same
+  // subtraction as the residual kernel) instead of src; overwrite: dst = R r
+  // instead of dst += R r (before the halo pass adds the foreign slots)
+  const T* rhs;
+  int overwrite;
   // restriction: coarse tiles
   const TileInfo* tiles;
   T* halo;
@@ -245,7 +250,10 @@ __device__ __forceinline__ void restrict_scatter(const TArgs<T>& A, const TileIn
 template <typename T>
 __device__ __forceinline__ void restrict_write(const TArgs<T>& A, const TileInfo& ti, const T* ys) {
   T* dst = A.dst + ti.dof_begin;
-  for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) dst[i] += ys[i];
+  if (A.overwrite)
+    for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) dst[i] = ys[i];
+  else
+    for (int i = threadIdx.x; i < ti.n_owned; i += blockDim.x) dst[i] += ys[i];
   const int32_t* hp = A.halo_pos + ti.foreign_begin;
   for (int i = threadIdx.x; i < ti.n_foreign; i += blockDim.x) A.halo[hp[i]] = ys[ti.n_owned + i];
 }
@@ -344,7 +352,8 @@ __global__ void __launch_bounds__(BLOCK) restrict_h(TArgs<T> A) {
           const int q = r / N3, n = r - q * N3;
           const int so = s_so[n], slot = so & 31;
           if ((sm_own[j * 8 + q] >> slot) & 1u) {
-            val[u] = A.src[sm_gs[(j * 8 + q) * NSLOT + slot] + (so >> 5)];
+            const int gi = sm_gs[(j * 8 + q) * NSLOT + slot] + (so >> 5);
+            val[u] = A.rhs ? A.rhs[gi] - A.src[gi] : A.src[gi];
             // refined: position in the children's 2k+1 lattice; else the
             // identity category (marked by the offset TPC M3): into cb
             dst[u] = sm_ref[j] ? j * M3 + s_e3[r] : TPC * M3 + j * N3 + n;
@@ -482,7 +491,10 @@ __global__ void __launch_bounds__(BLOCK) restrict_p(TArgs<T> A) {
           const int f = ti.cell_begin + sm_cell[j];
           int slot, off;
           node_slot<KF>(n % NF, (n / NF) % NF, n / (NF * NF), slot, off);
-          if ((A.own_f[f] >> slot) & 1u) v[u] = A.src[A.gstart_f[(size_t)f * NSLOT + slot] + off];
+          if ((A.own_f[f] >> slot) & 1u) {
+            const int gi = A.gstart_f[(size_t)f * NSLOT + slot] + off;
+            v[u] = A.rhs ? A.rhs[gi] - A.src[gi] : A.src[gi];
+          }
         }
       }
 #pragma unroll
@@ -544,7 +556,7 @@ void prolong_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s
 }
 
 template <int K, typename T, int TPC>
-void restrict_h_launch(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
+void restrict_h_launch(const TransferLaunch& L, const T* src, T* dst, const T* rhs, bool ow, cudaStream_t s) {
   constexpr int N = K + 1, M = 2 * K + 1;
   const size_t sm = (size_t)L.coarse.tc * sizeof(CellMeta) +
                     ((size_t)TPC * (N * N * N + M * M * N + M * M * M) + L.coarse.max_local) * sizeof(T);
@@ -552,17 +564,19 @@ void restrict_h_launch(const TransferLaunch& L, const T* src, T* dst, cudaStream
   TArgs<T> A = targs<T>(L);
   A.src = src;
   A.dst = dst;
+  A.rhs = rhs;
+  A.overwrite = ow;
   launch_pdl(restrict_h<K, T, TPC>, L.coarse.n_tiles, BLOCK, sm, s, A);
   note_launches(1);
 }
 
 template <int K, typename T>
-void restrict_h_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
+void restrict_h_run(const TransferLaunch& L, const T* src, T* dst, const T* rhs, bool ow, cudaStream_t s) {
   // (a recorded launch list takes 4-cell chunks: less shared memory per CTA of the persistent kernel)
   if (L.coarse.chunk == 4 || dwl_recording() || (L.coarse.chunk == 0 && L.coarse.n_tiles > 4 * L.coarse.n_sm))
-    restrict_h_launch<K, T, 4>(L, src, dst, s);
+    restrict_h_launch<K, T, 4>(L, src, dst, rhs, ow, s);
   else
-    restrict_h_launch<K, T, TP>(L, src, dst, s);
+    restrict_h_launch<K, T, TP>(L, src, dst, rhs, ow, s);
   launch_halo_add(L.coarse, sizeof(T) == 8, dst, s);
 }
 
@@ -579,7 +593,7 @@ void prolong_p_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s
 }
 
 template <int KF, typename T>
-void restrict_p_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
+void restrict_p_run(const TransferLaunch& L, const T* src, T* dst, const T* rhs, bool ow, cudaStream_t s) {
   constexpr int NF = KF + 1, NC = KF / 2 + 1;
   const size_t sm = (size_t)L.coarse.tc * sizeof(CellMeta) +
                     ((size_t)TP * (NC * NC * NC + NF * NC * NC + NF * NF * NC + NF * NF * NF) + L.coarse.max_local) *
@@ -588,6 +602,8 @@ void restrict_p_run(const TransferLaunch& L, const T* src, T* dst, cudaStream_t 
   TArgs<T> A = targs<T>(L);
   A.src = src;
   A.dst = dst;
+  A.rhs = rhs;
+  A.overwrite = ow;
   { launch_pdl(restrict_p<KF, T>, L.coarse.n_tiles, BLOCK, sm, s, A); note_launches(1); }
   launch_halo_add(L.coarse, sizeof(T) == 8, dst, s);
 }
@@ -611,19 +627,19 @@ void prolong_any(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) 
 }
 
 template <typename T>
-void restrict_any(const TransferLaunch& L, const T* src, T* dst, cudaStream_t s) {
+void restrict_any(const TransferLaunch& L, const T* src, T* dst, const T* rhs, bool ow, cudaStream_t s) {
   if (L.kind == 0) {
     switch (L.kf) {
-      case 1: restrict_h_run<1>(L, src, dst, s); break;
-      case 2: restrict_h_run<2>(L, src, dst, s); break;
-      case 3: restrict_h_run<3>(L, src, dst, s); break;
-      case 4: restrict_h_run<4>(L, src, dst, s); break;
+      case 1: restrict_h_run<1>(L, src, dst, rhs, ow, s); break;
+      case 2: restrict_h_run<2>(L, src, dst, rhs, ow, s); break;
+      case 3: restrict_h_run<3>(L, src, dst, rhs, ow, s); break;
+      case 4: restrict_h_run<4>(L, src, dst, rhs, ow, s); break;
     }
   } else {
     switch (L.kf) {
-      case 2: restrict_p_run<2>(L, src, dst, s); break;
-      case 3: restrict_p_run<3>(L, src, dst, s); break;
-      case 4: restrict_p_run<4>(L, src, dst, s); break;
+      case 2: restrict_p_run<2>(L, src, dst, rhs, ow, s); break;
+      case 3: restrict_p_run<3>(L, src, dst, rhs, ow, s); break;
+      case 4: restrict_p_run<4>(L, src, dst, rhs, ow, s); break;
     }
   }
 }
@@ -641,9 +657,19 @@ void launch_prolongate_add(const TransferLaunch& L, bool fp64, const void* coars
 
 void launch_restrict_add(const TransferLaunch& L, bool fp64, const void* fine, void* coarse, cudaStream_t s) {
   if (fp64)
-    restrict_any<double>(L, static_cast<const double*>(fine), static_cast<double*>(coarse), s);
+    restrict_any<double>(L, static_cast<const double*>(fine), static_cast<double*>(coarse), nullptr, false, s);
   else
-    restrict_any<float>(L, static_cast<const float*>(fine), static_cast<float*>(coarse), s);
+    restrict_any<float>(L, static_cast<const float*>(fine), static_cast<float*>(coarse), nullptr, false, s);
+}
+
+void launch_restrict_residual(const TransferLaunch& L, bool fp64, const void* b, const void* Ax, void* coarse,
+                              bool overwrite, cudaStream_t s) {
+  if (fp64)
+    restrict_any<double>(L, static_cast<const double*>(Ax), static_cast<double*>(coarse),
+                         static_cast<const double*>(b), overwrite, s);
+  else
+    restrict_any<float>(L, static_cast<const float*>(Ax), static_cast<float*>(coarse), static_cast<const float*>(b),
+                        overwrite, s);
 }
 
 void dwl_register_transfer() {
