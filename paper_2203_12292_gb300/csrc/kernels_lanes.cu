@@ -24,6 +24,11 @@
 //   * fp32, tiles without hanging cells: warp w keeps the z-plane c = w of
 //     its lane's cell in registers (gather, x and y sweeps forward; the z
 //     phase through the cell buffer; y and x sweeps backward and the scatter).
+//     The cell buffer and the tile's DoF buffer share one shared-memory
+//     region (gathers finish before the cell buffer is written, the
+//     accumulator is cleared after its last read; the tiles with hanging
+//     cells hold their x-lines in registers across those points), so 8
+//     blocks of 48 registers fit an SM at k = 4.
 //     Planes c = 0 and c = k are the only ones that meet, so warp k adds after
 //     warp 0 (a named barrier); a warp adds its nodes in program order.
 //   * tiles with hanging cells, and the double-float kernel: the x-lines
@@ -137,11 +142,7 @@ __device__ __forceinline__ void hang_pass(float* cb, uint16_t m, uint32_t hlD, i
 // or edge) add one after another in lane order; absent DoFs (the zero region)
 // add nothing.  Only lanes whose slot hangs can share an address within one
 // instruction: without such a lane (hang_any = 0) the plain addition is exact.
-__device__ __forceinline__ void add_ordered(float* x, float v, bool real, int lane, bool hang_any) {
-  if (!hang_any) {
-    *x += v;
-    return;
-  }
+__device__ __noinline__ void add_ordered_slow(float* x, float v, bool real, int lane) {
   const unsigned key = real ? (unsigned)__cvta_generic_to_shared(x) : ~(unsigned)lane;
   const unsigned peers = __match_any_sync(0xffffffffu, key);
   const int rank = __popc(peers & ((1u << lane) - 1u));
@@ -150,6 +151,21 @@ __device__ __forceinline__ void add_ordered(float* x, float v, bool real, int la
     if (real && rank == q) *x += v;
     __syncwarp();
   }
+}
+
+// (the ordered path out of line: the unrolled scatter of the tiles with hanging cells calls it
+// at every node, and inlined it would multiply that code)
+__device__ __forceinline__ void add_ordered(float* x, float v, bool real, int lane, bool hang_any) {
+  if (!hang_any)
+    *x += v;
+  else
+    add_ordered_slow(x, v, real, lane);
+}
+
+// zero the accumulator (n floats from the 16-byte aligned x0)
+__device__ __forceinline__ void clear_acc(float* x0, int n, int nt) {
+  float4* z4 = reinterpret_cast<float4*>(x0);
+  for (int i = threadIdx.x; i < (n + 3) / 4; i += nt) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // named barrier `id` of n threads: producers arrive, consumers wait
@@ -193,14 +209,17 @@ __device__ __forceinline__ void sweep_y(float* cb, int w, int lane) {
 }
 
 template <int K>
-__global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(LaneArgs A) {
+__global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 8 : 1) vmult_lanes(LaneArgs A) {
   pdl_begin();
   constexpr int N = K + 1, N2 = N * N, N3 = N2 * N, NT = N * 32;
   extern __shared__ __align__(16) unsigned char smem[];
   LaneTile* st = reinterpret_cast<LaneTile*>(smem);
   LaneHang* hg = reinterpret_cast<LaneHang*>(smem + sizeof(LaneTile));
+  // the cell buffer and the tile's DoF buffer (input, then accumulator) share one region: the
+  // DoFs are gathered into registers before the cell buffer is written, and the accumulator
+  // is cleared after the cell buffer's last read (8 instead of 7 blocks per SM at k = 4)
   float* cb = reinterpret_cast<float*>(smem + sizeof(LaneTile) + sizeof(LaneHang));
-  float* xs0 = cb + N3 * 32;  // 16-byte aligned
+  float* xs0 = cb;  // 16-byte aligned
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   // block b's tile: records in launch order at [b] (no dependent load of the tile index) or tile0 + b
   const int bx = blockIdx.x, tl = A.tile0 + bx;
@@ -283,6 +302,7 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
       for (int a = 1; a < K; ++a) u[N * b + a] = p1[a - 1];
       u[N * b + K] = *p2;
     }
+    __syncthreads();  // every plane gathered: the DoF buffer is dead
 #pragma unroll
     for (int b = 0; b < N; ++b) eo_forward<N, 0, 1>(u + N * b, tb.Be);  // x-lines of the plane
 #pragma unroll
@@ -293,10 +313,6 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
       for (int n = 0; n < N2; ++n) p[n * 32] = u[n];
     }
     __syncthreads();
-    {  // the tile DoFs are dead: clear the accumulator
-      float4* z4 = reinterpret_cast<float4*>(xs0);
-      for (int i = threadIdx.x; i < (sh + nloc + 3) / 4; i += NT) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
     // z: forward sweep, h (lam_a + lam_b + lam_c) in mode order, backward sweep (lines (a, b) = (i, w))
     {
       const float hb = h * tb.lame[w];
@@ -325,6 +341,9 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
     for (int a = 0; a < N; ++a) eo_backward<N, 0, N>(u + a, tb.Be);
 #pragma unroll
     for (int b = 0; b < N; ++b) eo_backward<N, 0, 1>(u + N * b, tb.Be);
+    __syncthreads();  // every plane loaded: the cell buffer is dead
+    clear_acc(xs0, sh + nloc, NT);
+    __syncthreads();
     // G_e^T.  Nodes of two cells are one DoF only where every coordinate is
     // equal or both lie on the cell boundary: between planes only c = 0 and
     // c = k meet, so warp k adds after warp 0 (named barrier 1); within a
@@ -345,31 +364,34 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
     }
     if (w == 0) named_bar_arrive(1, 64);
   } else {
-    // G_e and C_x on the warp's x-lines
-#pragma unroll 1
-    for (int i = 0; i < nxl; ++i) {
-      const int r = c_ll.xw[K][w][i];
-      float *p0, *p1, *p2;
-      xline_ptrs<K>(st, xb, r, lane, p0, p1, p2);
-      float v[N];
-      v[0] = *p0;
+    // G_e and C_x on the warp's x-lines, all gathered before the cell buffer is written
+    constexpr int NXW = K <= 2 ? 4 : N;  // x-lines per warp at most
+    float v[NXW][N];
 #pragma unroll
-      for (int a = 1; a < K; ++a) v[a] = p1[a - 1];
-      v[K] = *p2;
-      if ((hg->hl[0][lane] >> r) & 1u) interp_line_reg<K, false>(v, m & 1);
-      float* p = cb + N * r * 32 + lane;
+    for (int i = 0; i < NXW; ++i)
+      if (i < nxl) {
+        const int r = c_ll.xw[K][w][i];
+        float *p0, *p1, *p2;
+        xline_ptrs<K>(st, xb, r, lane, p0, p1, p2);
+        v[i][0] = *p0;
 #pragma unroll
-      for (int a = 0; a < N; ++a) p[a * 32] = v[a];
-    }
+        for (int a = 1; a < K; ++a) v[i][a] = p1[a - 1];
+        v[i][K] = *p2;
+        if ((hg->hl[0][lane] >> r) & 1u) interp_line_reg<K, false>(v[i], m & 1);
+      }
+    __syncthreads();  // the DoF buffer is dead
+#pragma unroll
+    for (int i = 0; i < NXW; ++i)
+      if (i < nxl) {
+        float* p = cb + N * c_ll.xw[K][w][i] * 32 + lane;
+#pragma unroll
+        for (int a = 0; a < N; ++a) p[a * 32] = v[i][a];
+      }
     __syncthreads();
     hang_pass<K, 1, false>(cb, m, hg->hl[1][lane], w, lane);  // C_y
     __syncthreads();
     hang_pass<K, 2, false, true>(cb, m, hg->hl[2][lane], w, lane);  // C_z, forward z sweep
     __syncthreads();
-    {
-      float4* z4 = reinterpret_cast<float4*>(xs0);
-      for (int i = threadIdx.x; i < (sh + nloc + 3) / 4; i += NT) z4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
     sweep_y<K, true>(cb, w, lane);
     __syncthreads();
     // x: forward sweep, h (lam_a + lam_b + lam_c) in mode order, backward sweep (lines (b, c) = (i, w))
@@ -397,17 +419,25 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
     __syncthreads();
     hang_pass<K, 1, true>(cb, m, hg->hl[1][lane], w, lane);  // C_y^T
     __syncthreads();
-    // C_x^T and G_e^T on the warp's class of x-lines
+    // C_x^T and G_e^T on the warp's class of x-lines: all lines read before the accumulator
+    // (the same region) is cleared
+#pragma unroll
+    for (int i = 0; i < NXW; ++i)
+      if (i < nxl) {
+        const float* p = cb + N * c_ll.xw[K][w][i] * 32 + lane;
+#pragma unroll
+        for (int a = 0; a < N; ++a) v[i][a] = p[a * 32];
+      }
+    __syncthreads();  // the cell buffer is dead
+    clear_acc(xs0, sh + nloc, NT);
+    __syncthreads();
     const uint32_t hs = hg->hs[lane];
     const int zb = nloc * 4;  // byte offset of the zero region
-#pragma unroll 1
-    for (int i = 0; i < nxl; ++i) {
-      const int r = c_ll.xw[K][w][i];
-      const float* p = cb + N * r * 32 + lane;
-      float v[N];
 #pragma unroll
-      for (int a = 0; a < N; ++a) v[a] = p[a * 32];
-      if ((hg->hl[0][lane] >> r) & 1u) interp_line_reg<K, true>(v, m & 1);
+    for (int i = 0; i < NXW; ++i) {
+      if (i >= nxl) break;
+      const int r = c_ll.xw[K][w][i];
+      if ((hg->hl[0][lane] >> r) & 1u) interp_line_reg<K, true>(v[i], m & 1);
       const uint32_t li = c_ll.line[K][r];
       const int s0 = li & 0xff, o0 = (li >> 8) & 0xff, o1 = li >> 16;
       const int b0 = st->ls[s0][lane], b1 = st->ls[s0 + 1][lane], b2 = st->ls[s0 + 2][lane];
@@ -416,10 +446,10 @@ __global__ void __launch_bounds__((K + 1) * 32, K == 4 ? 7 : 1) vmult_lanes(Lane
       float* p2 = reinterpret_cast<float*>(xb + b2 + o0);
       const bool h0 = __any_sync(0xffffffffu, (hs >> s0) & 1u), h1 = __any_sync(0xffffffffu, (hs >> (s0 + 1)) & 1u),
                  h2 = __any_sync(0xffffffffu, (hs >> (s0 + 2)) & 1u);
-      add_ordered(p0, v[0], b0 != zb, lane, h0);
+      add_ordered(p0, v[i][0], b0 != zb, lane, h0);
 #pragma unroll
-      for (int a = 1; a < K; ++a) add_ordered(p1 + a - 1, v[a], b1 != zb, lane, h1);
-      add_ordered(p2, v[K], b2 != zb, lane, h2);
+      for (int a = 1; a < K; ++a) add_ordered(p1 + a - 1, v[i][a], b1 != zb, lane, h1);
+      add_ordered(p2, v[i][K], b2 != zb, lane, h2);
     }
   }
   __syncthreads();
@@ -851,8 +881,10 @@ void fill_lane_lines(LaneLines& t) {
 template <int K>
 size_t lanes_smem(int max_local) {
   constexpr int N3 = (K + 1) * (K + 1) * (K + 1);
-  // tile DoFs shifted by up to 3 for the 16-byte copies, the zero region, and the float4 clearing
-  return sizeof(LaneTile) + sizeof(LaneHang) + ((size_t)N3 * 32 + (size_t)max_local + LANE_ZERO + 8) * sizeof(float);
+  // one region for the cell buffer and the tile DoFs (shifted by up to 3 for the 16-byte
+  // copies, the zero region, and the float4 clearing)
+  return sizeof(LaneTile) + sizeof(LaneHang) +
+         std::max((size_t)N3 * 32, (size_t)max_local + LANE_ZERO + 8) * sizeof(float);
 }
 
 template <int K>
