@@ -73,9 +73,9 @@ BYTES_PER_DOF = {"fp32": 9.8, "fp64": 17.8}
 # this workload, both of its launches, from one ncu capture of
 # dram__bytes_read.sum + dram__bytes_write.sum with caches flushed before each
 # kernel (ncu's default), mean of two applications: tile kernel vmult_lanes<4>
-# 136.9 MB read + 57.3 MB written, halo pass 89.8 MB + 0.6 MB; set to 0
+# 136.9 MB read + 56.5 MB written, halo pass 89.8 MB + 0.7 MB; set to 0
 # (reported as null) when the kernels change until they are captured again
-VMULT_TRAFFIC_BYTES = 284.6e6
+VMULT_TRAFFIC_BYTES = 283.8e6
 # V-cycle bytes per finest-level DoF (fp32): six operator applications and
 # five vector updates per level, the transfers, summed over the levels with
 # the 1/(1 - 1/8) factor of the coarser levels
