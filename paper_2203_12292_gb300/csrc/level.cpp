@@ -505,6 +505,72 @@ void validate_level(const LevelHost& L) {
       if (L.foreign[src] != L.halo_dofs[u]) fail("halo slot under the wrong DoF");
     }
   }
+  // the lane kernels' order of accumulation (tiles of at most 32 cells).  Node (a, b, c) of the
+  // cell in lane j adds to tile-local DoF ls[slot][j] / 4 + offset (absent slots: the zero region).
+  //  * tiles without hanging cells (fp32 kernel, warp c holds plane c): the planes whose nodes
+  //    add to one DoF are one plane or lie in {0, k} (warp k adds after warp 0), and no two cells
+  //    add to one DoF through the same node (one instruction of one warp);
+  //  * tiles with hanging cells and the double-float kernel (x-lines dealt to warps by class):
+  //    the classes (b or boundary, c or boundary) of the x-lines that add to one DoF are one class.
+  if (!L.lane.empty()) {
+    const int n = k + 1;
+    auto cls = [k](int x) { return x == 0 ? 0 : (x == k ? 2 : 1); };
+    std::vector<int> nslot(n * n * n), noff(n * n * n);
+    for (int c = 0; c < n; ++c)
+      for (int b = 0; b < n; ++b)
+        for (int a = 0; a < n; ++a) {
+          const int ca = cls(a), cb = cls(b), cc = cls(c);
+          int o = 0, mul = 1;
+          if (ca == 1) {
+            o += a - 1;
+            mul *= k - 1;
+          }
+          if (cb == 1) {
+            o += (b - 1) * mul;
+            mul *= k - 1;
+          }
+          if (cc == 1) o += (c - 1) * mul;
+          nslot[a + n * (b + n * c)] = ca + 3 * cb + 9 * cc;
+          noff[a + n * (b + n * c)] = o;
+        }
+    std::vector<uint32_t> planes;
+    std::vector<uint64_t> classes;
+    std::vector<int64_t> stamp;
+    for (int t = 0; t < nt; ++t) {
+      const TileInfo& T = L.tiles[t];
+      const LaneTile& lt = L.lane[t];
+      const int nloc = T.n_owned + T.n_foreign;
+      planes.assign(nloc, 0u);
+      classes.assign(nloc, 0u);
+      stamp.assign(nloc, -1);
+      for (int nd = 0; nd < n * n * n; ++nd) {
+        const int a = nd % n, b = (nd / n) % n, c = nd / (n * n);
+        // the x-line's class: b and c, each either its interior value or "boundary" (0 or k)
+        const int xcls = (cls(b) == 1 ? b : n) + (n + 1) * (cls(c) == 1 ? c : n);
+        (void)a;
+        for (int j = 0; j < T.n_cells; ++j) {
+          const int off = lt.ls[nslot[nd]][j];
+          if (off % 4 || off / 4 > nloc) fail("lane offset");
+          if (off / 4 == nloc) continue;  // the zero region
+          const int dof = off / 4 + noff[nd];
+          if (dof >= nloc) fail("lane DoF outside the tile");
+          planes[dof] |= 1u << c;
+          classes[dof] |= uint64_t(1) << xcls;
+          if (!lt.hang) {
+            const int64_t key = (int64_t)t * 1024 + nd;
+            if (stamp[dof] == key) fail("two cells add to one DoF through one node");
+            stamp[dof] = key;
+          }
+        }
+      }
+      const uint32_t ends = 1u | (1u << k);
+      for (int d = 0; d < nloc; ++d) {
+        if (!lt.hang && (planes[d] & (planes[d] - 1u)) && (planes[d] & ~ends))
+          fail("a DoF added from two planes other than 0 and k");
+        if (classes[d] & (classes[d] - 1)) fail("a DoF added from two x-line classes");
+      }
+    }
+  }
   // transfer ownership: every DoF owned by exactly one (cell, slot)
   std::vector<int8_t> owned(L.n_free, 0);
   for (int ci = 0; ci < nc; ++ci)
