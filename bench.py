@@ -438,6 +438,25 @@ def run_other_config(g, w, hbm):
     return out
 
 
+def ranks_max(dist, v: float, device: str) -> float:
+    """The largest of the ranks' values (the timed region's milliseconds: the
+    slowest replica sets the time)."""
+    import torch
+
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def ranks_sum(dist, v: float, device: str) -> float:
+    """The sum of the ranks' values (whole-job throughput of the replicas)."""
+    import torch
+
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
 def finite(v):
     """The JSON line with non-finite numbers (a diverged variant) as null."""
     if isinstance(v, float):
@@ -544,9 +563,7 @@ def main():
     launches = g.launch_count() - launches0
     ms_total = e0.elapsed_time(e1)
     if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+        ms_total = ranks_max(dist, ms_total, "cuda")
     ms_step = ms_total / args.steps
     # one more solve with the per-level, per-stage timers (event nodes in the
     # graphs): the duration of every fine-level operator application and the
@@ -586,9 +603,7 @@ def main():
     value = n / (t_vmult * 1e-3) / 1e9
     value64 = n / (vms64 / cnt64 * 1e-3) / 1e9
     if dist is not None:
-        t = torch.tensor([value], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t)
-        value = float(t.item())
+        value = ranks_sum(dist, value, "cuda")
 
     # plain fp64 variant (fp64 V-cycle) of the same solve
     mg64 = g.Multigrid(mesh, WORKLOAD.degree, mg_fp32=False)
